@@ -1,0 +1,754 @@
+/*
+ * mpld_oracle.c -- CPU oracle for the exact-cover (EC) layout decomposition
+ * search of "GPU-Accelerated Matrix Cover Algorithm for Multiple Patterning
+ * Layout Decomposition" (Chen, Yang, Yu).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * reference that the CUDA path is checked against.  Only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it; the
+ * product library never calls it and shares no code with it.
+ *
+ * What it computes
+ * ----------------
+ * Objective (Sec. 2.1, Eq. 1a-1d): for a graph with conflict edges CE and
+ * stitch edges SE and k masks, minimise
+ *     cost(x) = Cc * sum_{(i,j) in CE} [x_i == x_j] + Cs * sum_{(i,j) in SE} [x_i != x_j]
+ * over x in {0..k-1}^n.  The paper writes the weights as 1 and alpha = 0.1;
+ * integer weights Cc = 10, Cs = 1 are the same objective scaled by 10.
+ *
+ * Search (Sec. 2.3, Eq. 2, Algorithm 1): Knuth's Algorithm X with dancing
+ * links over the EC matrix whose rows are (segment v, mask c), whose primary
+ * column P_v must be covered exactly once and whose secondary column S_{e,c}
+ * (conflict edge e, mask c) may be covered at most once.  Conflicts the
+ * paper marks as "conflict candidates" (Algorithm 1, steps after the column
+ * cover) are taken here as selectable inactive rows that pay their penalty,
+ * which makes the search exact.  Stitch edges carry cost only; they have no
+ * columns.
+ *
+ * Canonical order (the reading this build fixes where the paper is silent):
+ *   - node = one call of search(); the root counts;
+ *   - leaf: every primary column covered; a leaf with cost g < best becomes
+ *     the incumbent; best == 0 ends the search;
+ *   - bound: Z = number of uncovered primary columns of size 0; prune when
+ *     g + Cc * Z >= best (admissible: such a segment sees every mask taken by
+ *     a distinct conflict neighbour, so it will pay at least Cc);
+ *   - column: minimum size S, lowest segment index on ties (Knuth's S
+ *     heuristic over a ring kept in index order);
+ *   - rows of the chosen segment v: all k masks, visited in ascending
+ *     (inc(c), c) with inc(c) = Cc * #{conflict nbr u: x_u = c}
+ *                            + Cs * #{stitch nbr u: x_u assigned, x_u != c};
+ *   - node budget B > 0: once an incumbent exists and B nodes have been
+ *     counted, the next call of search() stops the whole search (status
+ *     BUDGET) and the incumbent is returned.  The first descent always
+ *     reaches a leaf, so an incumbent always exists.
+ * The answer is the first minimum-cost leaf in this depth-first order; no
+ * admissible bound can change it, only the node count.
+ *
+ * Simplification (Sec. 2.2, the flow's simplify and recover steps; the
+ * paper does not give the rule, this is the reading used): a unit is a
+ * polygon together with every segment joined to it by a stitch edge.  Units
+ * whose number of conflict edges to remaining units is below k are removed
+ * in FIFO order (queue seeded in ascending unit id = lowest segment id; a
+ * removal decrements its neighbours, which join the queue when they drop
+ * below k).  A unit with a conflict edge inside itself is never removed.
+ * Recovery walks the removal order backwards and gives all segments of a
+ * unit the lowest mask not used by an already coloured conflict neighbour,
+ * which costs nothing.  The remaining segments are split into connected
+ * components (conflict + stitch edges), each searched on its own with
+ * component-local ids in ascending global id.
+ */
+#include <limits.h>
+#include <pthread.h>
+#include <stdatomic.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_BUDGET 1
+#define OR_E_INVALID (-1)
+#define OR_E_OOM (-2)
+
+#define OR_NO_SIMPLIFY 1u
+#define OR_SINGLE_INSTANCE 2u
+
+#define OR_INF INT64_MAX
+
+/* ------------------------------------------------------------------ */
+/* Dancing-links matrix for one instance                                */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int n, k, ne;
+  int ncol;          /* 1 (root) + n primaries + k*ne secondaries */
+  int nnode;
+  int *L, *R, *U, *D, *C, *S;
+  int *rownode;      /* node of row (v,c) in column P_v */
+  char *covered;     /* secondary column covered flag */
+  /* graph adjacency (for the row costs) */
+  int *cptr, *cadj;  /* conflict neighbours */
+  int *sptr, *sadj;  /* stitch neighbours */
+  int64_t Cc, Cs;
+  /* search state */
+  signed char *x, *bestx;
+  int64_t best, nodes, budget;
+  int done, budget_hit;
+  int *colstack;     /* columns covered by the rows on the current path */
+  int coltop;
+} dlx_t;
+
+static void dlx_free(dlx_t *d) {
+  free(d->L); free(d->R); free(d->U); free(d->D); free(d->C); free(d->S);
+  free(d->rownode); free(d->covered);
+  free(d->cptr); free(d->cadj); free(d->sptr); free(d->sadj);
+  free(d->x); free(d->bestx); free(d->colstack);
+  memset(d, 0, sizeof(*d));
+}
+
+/* CSR adjacency from an edge list (both directions), neighbours ascending. */
+static int build_adj(int n, int m, const int *eu, const int *ev, int **ptr_out, int **adj_out) {
+  int *ptr = calloc((size_t)n + 1, sizeof(int));
+  int *adj = malloc(sizeof(int) * (size_t)(2 * m + 1));
+  int *fill = calloc((size_t)n + 1, sizeof(int));
+  if (!ptr || !adj || !fill) { free(ptr); free(adj); free(fill); return OR_E_OOM; }
+  for (int e = 0; e < m; ++e) { ptr[eu[e] + 1]++; ptr[ev[e] + 1]++; }
+  for (int v = 0; v < n; ++v) ptr[v + 1] += ptr[v];
+  /* edges are sorted by (u, v) with u < v: scanning them in order and
+   * appending gives each list in ascending neighbour order only for the
+   * "v side"; sort each list afterwards (insertion sort, lists are short) */
+  for (int e = 0; e < m; ++e) {
+    adj[ptr[eu[e]] + fill[eu[e]]++] = ev[e];
+    adj[ptr[ev[e]] + fill[ev[e]]++] = eu[e];
+  }
+  for (int v = 0; v < n; ++v) {
+    for (int i = ptr[v] + 1; i < ptr[v + 1]; ++i) {
+      int t = adj[i], j = i - 1;
+      while (j >= ptr[v] && adj[j] > t) { adj[j + 1] = adj[j]; --j; }
+      adj[j + 1] = t;
+    }
+  }
+  free(fill);
+  *ptr_out = ptr;
+  *adj_out = adj;
+  return OR_OK;
+}
+
+/* Build the EC matrix.  Columns: 0 = root, 1+v = P_v, 1+n+e*k+c = S_{e,c}.
+ * Row (v,c) has a node in P_v and one in S_{e,c} for every conflict edge e
+ * incident to v, in ascending e; rows are appended in ascending v*k+c, so
+ * every column lists its rows in ascending row index. */
+static int dlx_build(dlx_t *d, int n, int k, int ne, const int *eu, const int *ev,
+                     int ns, const int *su, const int *sv, int64_t Cc, int64_t Cs) {
+  memset(d, 0, sizeof(*d));
+  d->n = n; d->k = k; d->ne = ne; d->Cc = Cc; d->Cs = Cs;
+  d->ncol = 1 + n + k * ne;
+  d->nnode = d->ncol + k * (n + 2 * ne);
+  size_t nn = (size_t)d->nnode;
+  d->L = malloc(nn * sizeof(int)); d->R = malloc(nn * sizeof(int));
+  d->U = malloc(nn * sizeof(int)); d->D = malloc(nn * sizeof(int));
+  d->C = malloc(nn * sizeof(int)); d->S = calloc((size_t)d->ncol, sizeof(int));
+  d->rownode = malloc(sizeof(int) * (size_t)(n * k + 1));
+  d->covered = calloc((size_t)d->ncol, 1);
+  d->x = malloc((size_t)n + 1); d->bestx = malloc((size_t)n + 1);
+  d->colstack = malloc(sizeof(int) * (size_t)(k * ne + 1));
+  if (!d->L || !d->R || !d->U || !d->D || !d->C || !d->S || !d->rownode || !d->covered ||
+      !d->x || !d->bestx || !d->colstack) { dlx_free(d); return OR_E_OOM; }
+  if (build_adj(n, ne, eu, ev, &d->cptr, &d->cadj) != OR_OK ||
+      build_adj(n, ns, su, sv, &d->sptr, &d->sadj) != OR_OK) { dlx_free(d); return OR_E_OOM; }
+
+  /* headers */
+  for (int c = 0; c < d->ncol; ++c) { d->U[c] = d->D[c] = c; d->C[c] = c; }
+  /* ring: root and the primaries in index order */
+  for (int c = 0; c <= n; ++c) { d->R[c] = (c == n) ? 0 : c + 1; d->L[c] = (c == 0) ? n : c - 1; }
+  /* secondaries stay out of the ring */
+  for (int c = n + 1; c < d->ncol; ++c) { d->L[c] = d->R[c] = c; }
+
+  /* incident edge lists in ascending edge index */
+  int *iptr = calloc((size_t)n + 1, sizeof(int));
+  int *iedge = malloc(sizeof(int) * (size_t)(2 * ne + 1));
+  int *ifill = calloc((size_t)n + 1, sizeof(int));
+  if (!iptr || !iedge || !ifill) { free(iptr); free(iedge); free(ifill); dlx_free(d); return OR_E_OOM; }
+  for (int e = 0; e < ne; ++e) { iptr[eu[e] + 1]++; iptr[ev[e] + 1]++; }
+  for (int v = 0; v < n; ++v) iptr[v + 1] += iptr[v];
+  for (int e = 0; e < ne; ++e) {
+    iedge[iptr[eu[e]] + ifill[eu[e]]++] = e;
+    iedge[iptr[ev[e]] + ifill[ev[e]]++] = e;
+  }
+
+  int next = d->ncol;
+  for (int v = 0; v < n; ++v) {
+    for (int c = 0; c < k; ++c) {
+      int first = -1, prev = -1;
+      int ncols_row = 1 + (iptr[v + 1] - iptr[v]);
+      for (int t = 0; t < ncols_row; ++t) {
+        int col = (t == 0) ? 1 + v : 1 + n + iedge[iptr[v] + t - 1] * k + c;
+        int node = next++;
+        d->C[node] = col;
+        /* vertical: append at the bottom of the column */
+        d->U[node] = d->U[col]; d->D[node] = col;
+        d->D[d->U[col]] = node; d->U[col] = node;
+        d->S[col]++;
+        /* horizontal: append to the row's circular list */
+        if (first < 0) { first = node; d->L[node] = d->R[node] = node; }
+        else { d->L[node] = prev; d->R[node] = first; d->R[prev] = node; d->L[first] = node; }
+        prev = node;
+      }
+      d->rownode[v * k + c] = first;
+    }
+  }
+  free(iptr); free(iedge); free(ifill);
+  for (int v = 0; v < n; ++v) d->x[v] = -1;
+  d->best = OR_INF;
+  return OR_OK;
+}
+
+/* Knuth's cover / uncover (Eq. 2). */
+static void dlx_cover(dlx_t *d, int c) {
+  int *L = d->L, *R = d->R, *U = d->U, *D = d->D, *C = d->C, *S = d->S;
+  L[R[c]] = L[c];
+  R[L[c]] = R[c];
+  for (int i = D[c]; i != c; i = D[i])
+    for (int j = R[i]; j != i; j = R[j]) {
+      U[D[j]] = U[j];
+      D[U[j]] = D[j];
+      S[C[j]]--;
+    }
+}
+
+static void dlx_uncover(dlx_t *d, int c) {
+  int *L = d->L, *R = d->R, *U = d->U, *D = d->D, *C = d->C, *S = d->S;
+  for (int i = U[c]; i != c; i = U[i])
+    for (int j = L[i]; j != i; j = L[j]) {
+      S[C[j]]++;
+      U[D[j]] = j;
+      D[U[j]] = j;
+    }
+  L[R[c]] = c;
+  R[L[c]] = c;
+}
+
+/* Cost added by giving segment v mask c, against the current assignment. */
+static int64_t row_inc(const dlx_t *d, int v, int c) {
+  int64_t inc = 0;
+  for (int i = d->cptr[v]; i < d->cptr[v + 1]; ++i)
+    if (d->x[d->cadj[i]] == c) inc += d->Cc;
+  for (int i = d->sptr[v]; i < d->sptr[v + 1]; ++i) {
+    int xs = d->x[d->sadj[i]];
+    if (xs >= 0 && xs != c) inc += d->Cs;
+  }
+  return inc;
+}
+
+static void dlx_search(dlx_t *d, int64_t g) {
+  if (d->budget > 0 && d->best < OR_INF && d->nodes >= d->budget) {
+    d->budget_hit = 1;
+    d->done = 1;
+    return;
+  }
+  d->nodes++;
+  if (d->R[0] == 0) {                      /* every primary column covered */
+    if (g < d->best) {
+      d->best = g;
+      memcpy(d->bestx, d->x, (size_t)d->n);
+      if (g == 0) d->done = 1;
+    }
+    return;
+  }
+  int64_t Z = 0;
+  int cmin = 0, smin = INT_MAX;
+  for (int c = d->R[0]; c != 0; c = d->R[c]) {
+    if (d->S[c] == 0) Z++;
+    if (d->S[c] < smin) { smin = d->S[c]; cmin = c; }
+  }
+  if (g + d->Cc * Z >= d->best) return;    /* admissible bound */
+
+  const int v = cmin - 1, k = d->k;
+  int64_t inc[8];
+  int order[8];
+  for (int c = 0; c < k; ++c) inc[c] = row_inc(d, v, c);
+  for (int c = 0; c < k; ++c) {            /* insertion sort by (inc, c) */
+    int j = c - 1;
+    while (j >= 0 && inc[order[j]] > inc[c]) { order[j + 1] = order[j]; --j; }
+    order[j + 1] = c;
+  }
+
+  dlx_cover(d, cmin);
+  for (int t = 0; t < k && !d->done; ++t) {
+    const int c = order[t];
+    const int r = d->rownode[v * k + c];
+    const int base = d->coltop;
+    for (int j = d->R[r]; j != r; j = d->R[j]) {
+      int col = d->C[j];
+      if (!d->covered[col]) {              /* skip columns a neighbour took */
+        dlx_cover(d, col);
+        d->covered[col] = 1;
+        d->colstack[d->coltop++] = col;
+      }
+    }
+    d->x[v] = (signed char)c;
+    dlx_search(d, g + inc[c]);
+    d->x[v] = -1;
+    while (d->coltop > base) {
+      int col = d->colstack[--d->coltop];
+      d->covered[col] = 0;
+      dlx_uncover(d, col);
+    }
+  }
+  dlx_uncover(d, cmin);
+}
+
+/* Textbook Algorithm X: count exact covers (active rows only). */
+static void dlx_count(dlx_t *d, int64_t limit, int64_t *count) {
+  if (*count >= limit) return;
+  if (d->R[0] == 0) { (*count)++; return; }
+  int cmin = 0, smin = INT_MAX;
+  for (int c = d->R[0]; c != 0; c = d->R[c])
+    if (d->S[c] < smin) { smin = d->S[c]; cmin = c; }
+  if (smin == 0) return;
+  dlx_cover(d, cmin);
+  for (int r = d->D[cmin]; r != cmin; r = d->D[r]) {
+    for (int j = d->R[r]; j != r; j = d->R[j]) dlx_cover(d, d->C[j]);
+    dlx_count(d, limit, count);
+    for (int j = d->L[r]; j != r; j = d->L[j]) dlx_uncover(d, d->C[j]);
+  }
+  dlx_uncover(d, cmin);
+}
+
+/* ------------------------------------------------------------------ */
+/* Input validation and normalisation                                   */
+/* ------------------------------------------------------------------ */
+
+static int cmp_pair(const void *a, const void *b) {
+  const int *p = a, *q = b;
+  if (p[0] != q[0]) return p[0] < q[0] ? -1 : 1;
+  if (p[1] != q[1]) return p[1] < q[1] ? -1 : 1;
+  return 0;
+}
+
+/* (min,max)-normalised, sorted, de-duplicated copy of an edge list. */
+static int norm_edges(int n, int m, const int *u, const int *v, int **ou, int **ov, int *om) {
+  int *pairs = malloc(sizeof(int) * (size_t)(2 * m + 2));
+  if (!pairs) return OR_E_OOM;
+  for (int e = 0; e < m; ++e) {
+    int a = u[e], b = v[e];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) { free(pairs); return OR_E_INVALID; }
+    pairs[2 * e] = a < b ? a : b;
+    pairs[2 * e + 1] = a < b ? b : a;
+  }
+  qsort(pairs, (size_t)m, 2 * sizeof(int), cmp_pair);
+  int w = 0;
+  for (int e = 0; e < m; ++e) {
+    if (w > 0 && pairs[2 * (w - 1)] == pairs[2 * e] && pairs[2 * (w - 1) + 1] == pairs[2 * e + 1]) continue;
+    pairs[2 * w] = pairs[2 * e];
+    pairs[2 * w + 1] = pairs[2 * e + 1];
+    ++w;
+  }
+  *ou = malloc(sizeof(int) * (size_t)(w + 1));
+  *ov = malloc(sizeof(int) * (size_t)(w + 1));
+  if (!*ou || !*ov) { free(pairs); free(*ou); free(*ov); return OR_E_OOM; }
+  for (int e = 0; e < w; ++e) { (*ou)[e] = pairs[2 * e]; (*ov)[e] = pairs[2 * e + 1]; }
+  *om = w;
+  free(pairs);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Single-instance entry points                                         */
+/* ------------------------------------------------------------------ */
+
+/* Search one instance (the whole given graph, connected or not).
+ * x_out: n masks; returns OR_OK / OR_BUDGET / error. */
+int oracle_solve_instance(int n, int k, int ne, const int *eu, const int *ev,
+                          int ns, const int *su, const int *sv,
+                          int64_t cost_conflict, int64_t cost_stitch, int64_t budget,
+                          signed char *x_out, int64_t *cost_out, int64_t *nodes_out) {
+  if (n < 0 || k < 2 || k > 8 || ne < 0 || ns < 0) return OR_E_INVALID;
+  int *cu, *cv, *tu, *tv, mc, ms, rc;
+  if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) return rc;
+  if ((rc = norm_edges(n, ns, su, sv, &tu, &tv, &ms)) != OR_OK) { free(cu); free(cv); return rc; }
+  dlx_t d;
+  rc = dlx_build(&d, n, k, mc, cu, cv, ms, tu, tv, cost_conflict, cost_stitch);
+  free(cu); free(cv); free(tu); free(tv);
+  if (rc != OR_OK) return rc;
+  d.budget = budget;
+  dlx_search(&d, 0);
+  memcpy(x_out, d.bestx, (size_t)n);
+  *cost_out = d.best;
+  *nodes_out = d.nodes;
+  rc = d.budget_hit ? OR_BUDGET : OR_OK;
+  dlx_free(&d);
+  return rc;
+}
+
+/* Number of exact covers of the EC matrix (primary columns exactly once,
+ * secondary columns at most once), stopping at `limit`. */
+int oracle_count_exact_covers(int n, int k, int ne, const int *eu, const int *ev,
+                              int64_t limit, int64_t *count_out) {
+  if (n < 0 || k < 2 || k > 8 || ne < 0) return OR_E_INVALID;
+  int *cu, *cv, mc, rc;
+  if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) return rc;
+  dlx_t d;
+  rc = dlx_build(&d, n, k, mc, cu, cv, 0, NULL, NULL, 10, 1);
+  free(cu); free(cv);
+  if (rc != OR_OK) return rc;
+  int64_t cnt = 0;
+  dlx_count(&d, limit, &cnt);
+  *count_out = cnt;
+  dlx_free(&d);
+  return OR_OK;
+}
+
+/* The EC matrix as a dense 0/1 array, row-major [n*k][1 + n + k*ne]
+ * (column 0, the root, stays 0), read back from the dancing links. */
+int oracle_export_matrix(int n, int k, int ne, const int *eu, const int *ev, unsigned char *dense) {
+  if (n < 0 || k < 2 || k > 8 || ne < 0) return OR_E_INVALID;
+  int *cu, *cv, mc, rc;
+  if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) return rc;
+  dlx_t d;
+  rc = dlx_build(&d, n, k, mc, cu, cv, 0, NULL, NULL, 10, 1);
+  free(cu); free(cv);
+  if (rc != OR_OK) return rc;
+  const size_t ncol = (size_t)d.ncol;
+  memset(dense, 0, (size_t)n * (size_t)k * ncol);
+  for (int row = 0; row < n * k; ++row) {
+    int r = d.rownode[row];
+    int j = r;
+    do { dense[(size_t)row * ncol + (size_t)d.C[j]] = 1; j = d.R[j]; } while (j != r);
+  }
+  dlx_free(&d);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Whole-layout decomposition: simplify, split, search, recover          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t n_components, n_removed_segments;
+  int64_t n_conflicts, n_stitches, cost, nodes;
+  int64_t component_cost_sum, n_budget_components;
+  int32_t status, max_component;
+} oracle_totals;
+
+typedef struct {
+  /* shared, read-only */
+  int k, n_comp;
+  int64_t Cc, Cs, budget;
+  const int *comp_ptr, *comp_seg;     /* segments of component i, ascending */
+  const int *local_of;                /* global segment -> local id */
+  const int *comp_of;                 /* global segment -> component, -1 removed */
+  const int *cptr, *cadj, *sptr, *sadj; /* global adjacency */
+  const int *work_order;              /* components by descending size */
+  /* outputs */
+  signed char *mask;                  /* global masks */
+  int64_t *comp_cost, *comp_nodes;
+  int32_t *comp_status;
+  atomic_int next;
+  atomic_int error;
+} pool_t;
+
+static void solve_component(pool_t *P, int ci) {
+  const int a = P->comp_ptr[ci], b = P->comp_ptr[ci + 1], n = b - a;
+  /* local edge lists, sorted by (min, max) local id: local ids keep the
+   * global order, so walking segments ascending and their larger
+   * neighbours ascending gives the sorted order */
+  int ne = 0, ns = 0;
+  for (int t = a; t < b; ++t) {
+    int g = P->comp_seg[t];
+    for (int i = P->cptr[g]; i < P->cptr[g + 1]; ++i)
+      if (P->cadj[i] > g && P->comp_of[P->cadj[i]] == ci) ne++;
+    for (int i = P->sptr[g]; i < P->sptr[g + 1]; ++i)
+      if (P->sadj[i] > g && P->comp_of[P->sadj[i]] == ci) ns++;
+  }
+  int *eu = malloc(sizeof(int) * (size_t)(ne + 1)), *ev = malloc(sizeof(int) * (size_t)(ne + 1));
+  int *su = malloc(sizeof(int) * (size_t)(ns + 1)), *sv = malloc(sizeof(int) * (size_t)(ns + 1));
+  signed char *x = malloc((size_t)n + 1);
+  if (!eu || !ev || !su || !sv || !x) { atomic_store(&P->error, OR_E_OOM); goto out; }
+  ne = ns = 0;
+  for (int t = a; t < b; ++t) {
+    int g = P->comp_seg[t];
+    for (int i = P->cptr[g]; i < P->cptr[g + 1]; ++i)
+      if (P->cadj[i] > g && P->comp_of[P->cadj[i]] == ci) {
+        eu[ne] = P->local_of[g]; ev[ne] = P->local_of[P->cadj[i]]; ne++;
+      }
+    for (int i = P->sptr[g]; i < P->sptr[g + 1]; ++i)
+      if (P->sadj[i] > g && P->comp_of[P->sadj[i]] == ci) {
+        su[ns] = P->local_of[g]; sv[ns] = P->local_of[P->sadj[i]]; ns++;
+      }
+  }
+  int64_t cost = 0, nodes = 0;
+  int rc = oracle_solve_instance(n, P->k, ne, eu, ev, ns, su, sv, P->Cc, P->Cs, P->budget, x, &cost, &nodes);
+  if (rc < 0) { atomic_store(&P->error, rc); goto out; }
+  for (int t = a; t < b; ++t) P->mask[P->comp_seg[t]] = x[t - a];
+  P->comp_cost[ci] = cost;
+  P->comp_nodes[ci] = nodes;
+  P->comp_status[ci] = rc;
+out:
+  free(eu); free(ev); free(su); free(sv); free(x);
+}
+
+static void *pool_worker(void *arg) {
+  pool_t *P = arg;
+  for (;;) {
+    int i = atomic_fetch_add(&P->next, 1);
+    if (i >= P->n_comp || atomic_load(&P->error)) break;
+    solve_component(P, P->work_order[i]);
+  }
+  return NULL;
+}
+
+/* (size, id) pairs: larger components first, then ascending id */
+static int cmp_comp(const void *a, const void *b) {
+  const int *p = a, *q = b;
+  if (p[0] != q[0]) return p[0] > q[0] ? -1 : 1;
+  return p[1] < q[1] ? -1 : (p[1] > q[1]);
+}
+
+static int find_root(int *parent, int a) {
+  while (parent[a] != a) { parent[a] = parent[parent[a]]; a = parent[a]; }
+  return a;
+}
+
+/*
+ * Decompose a whole layout.
+ *   polygon_of: segment -> polygon id in [0, n_seg), or NULL (each segment
+ *               its own polygon);
+ *   flags: OR_NO_SIMPLIFY, OR_SINGLE_INSTANCE;
+ *   nthreads: worker threads for the per-component searches (>= 1);
+ *   mask_out[n_seg]; comp_of_out[n_seg] (nullable): component of each
+ *   segment, -1 if removed by simplification; comp_nodes_out /
+ *   comp_cost_out / comp_status_out (nullable, n_seg entries each).
+ */
+int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int *conf_v,
+                     int n_st, const int *st_u, const int *st_v, const int *polygon_of,
+                     int64_t cost_conflict, int64_t cost_stitch, uint32_t flags, int64_t budget,
+                     int nthreads, signed char *mask_out, int32_t *comp_of_out,
+                     int64_t *comp_nodes_out, int64_t *comp_cost_out, int32_t *comp_status_out,
+                     oracle_totals *tot) {
+  if (n_seg < 0 || k < 2 || k > 8 || n_conf < 0 || n_st < 0 || nthreads < 1) return OR_E_INVALID;
+  if (polygon_of)
+    for (int s = 0; s < n_seg; ++s)
+      if (polygon_of[s] < 0 || polygon_of[s] >= n_seg) return OR_E_INVALID;
+  int rc;
+  int *cu = NULL, *cv = NULL, *tu = NULL, *tv = NULL, mc = 0, ms = 0;
+  int *cptr = NULL, *cadj = NULL, *sptr = NULL, *sadj = NULL;
+  int *unit = NULL, *udeg = NULL, *queue = NULL, *removed_order = NULL, *uptr = NULL, *useg = NULL;
+  char *removed = NULL, *queued = NULL, *selfc = NULL;
+  int *parent = NULL, *comp_of = NULL, *comp_ptr = NULL, *comp_seg = NULL, *local_of = NULL, *order = NULL;
+  int64_t *ccost = NULL, *cnodes = NULL;
+  int32_t *cstat = NULL;
+  memset(tot, 0, sizeof(*tot));
+
+  if ((rc = norm_edges(n_seg, n_conf, conf_u, conf_v, &cu, &cv, &mc)) != OR_OK) goto done;
+  if ((rc = norm_edges(n_seg, n_st, st_u, st_v, &tu, &tv, &ms)) != OR_OK) goto done;
+  if ((rc = build_adj(n_seg, mc, cu, cv, &cptr, &cadj)) != OR_OK) goto done;
+  if ((rc = build_adj(n_seg, ms, tu, tv, &sptr, &sadj)) != OR_OK) goto done;
+  rc = OR_E_OOM;
+
+  /* units: polygons merged along stitch edges; unit id = lowest segment */
+  parent = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  unit = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  if (!parent || !unit) goto done;
+  for (int s = 0; s < n_seg; ++s) parent[s] = s;
+  {
+    int *first_of_poly = malloc(sizeof(int) * (size_t)(n_seg + 1));
+    if (!first_of_poly) goto done;
+    for (int p = 0; p < n_seg; ++p) first_of_poly[p] = -1;
+    for (int s = 0; s < n_seg; ++s) {
+      int p = polygon_of ? polygon_of[s] : s;
+      if (first_of_poly[p] < 0) first_of_poly[p] = s;
+      else {
+        int ra = find_root(parent, first_of_poly[p]), rb = find_root(parent, s);
+        if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+      }
+    }
+    free(first_of_poly);
+  }
+  for (int e = 0; e < ms; ++e) {
+    int ra = find_root(parent, tu[e]), rb = find_root(parent, tv[e]);
+    if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+  }
+  for (int s = 0; s < n_seg; ++s) unit[s] = find_root(parent, s);
+
+  /* unit member lists (segments ascending) */
+  uptr = calloc((size_t)n_seg + 1, sizeof(int));
+  useg = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  if (!uptr || !useg) goto done;
+  for (int s = 0; s < n_seg; ++s) uptr[unit[s] + 1]++;
+  for (int u = 0; u < n_seg; ++u) uptr[u + 1] += uptr[u];
+  {
+    int *fill = calloc((size_t)n_seg + 1, sizeof(int));
+    if (!fill) goto done;
+    for (int s = 0; s < n_seg; ++s) useg[uptr[unit[s]] + fill[unit[s]]++] = s;
+    free(fill);
+  }
+
+  removed = calloc((size_t)n_seg + 1, 1);
+  queued = calloc((size_t)n_seg + 1, 1);
+  selfc = calloc((size_t)n_seg + 1, 1);
+  udeg = calloc((size_t)n_seg + 1, sizeof(int));
+  queue = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  removed_order = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  if (!removed || !queued || !selfc || !udeg || !queue || !removed_order) goto done;
+  int n_removed_units = 0;
+  if (!(flags & OR_NO_SIMPLIFY)) {
+    for (int e = 0; e < mc; ++e) {
+      int ua = unit[cu[e]], ub = unit[cv[e]];
+      if (ua == ub) selfc[ua] = 1;
+      else { udeg[ua]++; udeg[ub]++; }
+    }
+    int qh = 0, qt = 0;
+    for (int u = 0; u < n_seg; ++u)
+      if (unit[u] == u && !selfc[u] && udeg[u] < k) { queue[qt++] = u; queued[u] = 1; }
+    while (qh < qt) {
+      int u = queue[qh++];
+      removed[u] = 1;
+      removed_order[n_removed_units++] = u;
+      for (int t = uptr[u]; t < uptr[u + 1]; ++t) {
+        int s = useg[t];
+        for (int i = cptr[s]; i < cptr[s + 1]; ++i) {
+          int w = unit[cadj[i]];
+          if (w == u || removed[w]) continue;
+          udeg[w]--;
+          if (!queued[w] && !selfc[w] && udeg[w] < k) { queue[qt++] = w; queued[w] = 1; }
+        }
+      }
+    }
+  }
+
+  /* components of the remaining segments */
+  comp_of = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  local_of = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  if (!comp_of || !local_of) goto done;
+  for (int s = 0; s < n_seg; ++s) parent[s] = s;
+  if (!(flags & OR_SINGLE_INSTANCE)) {
+    for (int e = 0; e < mc; ++e)
+      if (!removed[unit[cu[e]]] && !removed[unit[cv[e]]]) {
+        int ra = find_root(parent, cu[e]), rb = find_root(parent, cv[e]);
+        if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+      }
+    for (int e = 0; e < ms; ++e)
+      if (!removed[unit[tu[e]]]) {
+        int ra = find_root(parent, tu[e]), rb = find_root(parent, tv[e]);
+        if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+      }
+  }
+  int n_comp = 0;
+  {
+    int *id_of_root = malloc(sizeof(int) * (size_t)(n_seg + 1));
+    if (!id_of_root) goto done;
+    for (int s = 0; s < n_seg; ++s) id_of_root[s] = -1;
+    int single_id = -1;
+    for (int s = 0; s < n_seg; ++s) {
+      if (removed[unit[s]]) { comp_of[s] = -1; continue; }
+      if (flags & OR_SINGLE_INSTANCE) {
+        if (single_id < 0) single_id = n_comp++;
+        comp_of[s] = single_id;
+      } else {
+        int r = find_root(parent, s);   /* roots are the lowest segment */
+        if (id_of_root[r] < 0) id_of_root[r] = n_comp++;
+        comp_of[s] = id_of_root[r];
+      }
+    }
+    free(id_of_root);
+  }
+  comp_ptr = calloc((size_t)n_comp + 2, sizeof(int));
+  comp_seg = malloc(sizeof(int) * (size_t)(n_seg + 1));
+  order = malloc(sizeof(int) * (size_t)(n_comp + 1));
+  ccost = calloc((size_t)n_comp + 1, sizeof(int64_t));
+  cnodes = calloc((size_t)n_comp + 1, sizeof(int64_t));
+  cstat = calloc((size_t)n_comp + 1, sizeof(int32_t));
+  if (!comp_ptr || !comp_seg || !order || !ccost || !cnodes || !cstat) goto done;
+  for (int s = 0; s < n_seg; ++s) if (comp_of[s] >= 0) comp_ptr[comp_of[s] + 1]++;
+  for (int c = 0; c < n_comp; ++c) comp_ptr[c + 1] += comp_ptr[c];
+  {
+    int *fill = calloc((size_t)n_comp + 1, sizeof(int));
+    if (!fill) goto done;
+    for (int s = 0; s < n_seg; ++s)
+      if (comp_of[s] >= 0) {
+        int c = comp_of[s];
+        local_of[s] = fill[c];
+        comp_seg[comp_ptr[c] + fill[c]++] = s;
+      } else local_of[s] = -1;
+    free(fill);
+  }
+  {
+    int *keys = malloc(sizeof(int) * (size_t)(2 * n_comp + 2));
+    if (!keys) goto done;
+    for (int c = 0; c < n_comp; ++c) { keys[2 * c] = comp_ptr[c + 1] - comp_ptr[c]; keys[2 * c + 1] = c; }
+    qsort(keys, (size_t)n_comp, 2 * sizeof(int), cmp_comp);
+    for (int c = 0; c < n_comp; ++c) order[c] = keys[2 * c + 1];
+    free(keys);
+  }
+
+  for (int s = 0; s < n_seg; ++s) mask_out[s] = -1;
+  {
+    pool_t P;
+    memset(&P, 0, sizeof(P));
+    P.k = k; P.n_comp = n_comp; P.Cc = cost_conflict; P.Cs = cost_stitch; P.budget = budget;
+    P.comp_ptr = comp_ptr; P.comp_seg = comp_seg; P.local_of = local_of; P.comp_of = comp_of;
+    P.cptr = cptr; P.cadj = cadj; P.sptr = sptr; P.sadj = sadj; P.work_order = order;
+    P.mask = mask_out; P.comp_cost = ccost; P.comp_nodes = cnodes; P.comp_status = cstat;
+    atomic_init(&P.next, 0);
+    atomic_init(&P.error, 0);
+    int nt = nthreads < n_comp ? nthreads : (n_comp > 0 ? n_comp : 1);
+    pthread_t *th = malloc(sizeof(pthread_t) * (size_t)nt);
+    if (!th) goto done;
+    pthread_attr_t attr;
+    pthread_attr_init(&attr);
+    pthread_attr_setstacksize(&attr, (size_t)256 << 20);   /* deep recursion */
+    int started = 0;
+    for (int t = 0; t < nt; ++t)
+      if (pthread_create(&th[t], &attr, pool_worker, &P) == 0) started++;
+      else break;
+    pthread_attr_destroy(&attr);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th);
+    if (started == 0) goto done;
+    if (atomic_load(&P.error)) { rc = atomic_load(&P.error); goto done; }
+  }
+
+  /* recovery: reverse removal order, lowest mask unused by coloured nbrs */
+  for (int t = n_removed_units - 1; t >= 0; --t) {
+    int u = removed_order[t];
+    unsigned used = 0;
+    for (int q = uptr[u]; q < uptr[u + 1]; ++q) {
+      int s = useg[q];
+      for (int i = cptr[s]; i < cptr[s + 1]; ++i) {
+        int m = mask_out[cadj[i]];
+        if (m >= 0) used |= 1u << m;
+      }
+    }
+    int c = 0;
+    while (c < k && (used >> c) & 1u) ++c;
+    if (c == k) { rc = OR_E_INVALID; goto done; }   /* cannot happen for a k-core peel */
+    for (int q = uptr[u]; q < uptr[u + 1]; ++q) mask_out[useg[q]] = (signed char)c;
+    tot->n_removed_segments += uptr[u + 1] - uptr[u];
+  }
+
+  /* totals over the whole layout (Eq. 1) */
+  for (int e = 0; e < mc; ++e) if (mask_out[cu[e]] == mask_out[cv[e]]) tot->n_conflicts++;
+  for (int e = 0; e < ms; ++e) if (mask_out[tu[e]] != mask_out[tv[e]]) tot->n_stitches++;
+  tot->cost = cost_conflict * tot->n_conflicts + cost_stitch * tot->n_stitches;
+  tot->n_components = n_comp;
+  tot->status = OR_OK;
+  for (int c = 0; c < n_comp; ++c) {
+    tot->nodes += cnodes[c];
+    tot->component_cost_sum += ccost[c];
+    if (cstat[c] == OR_BUDGET) { tot->n_budget_components++; tot->status = OR_BUDGET; }
+    int sz = comp_ptr[c + 1] - comp_ptr[c];
+    if (sz > tot->max_component) tot->max_component = sz;
+    if (comp_nodes_out) comp_nodes_out[c] = cnodes[c];
+    if (comp_cost_out) comp_cost_out[c] = ccost[c];
+    if (comp_status_out) comp_status_out[c] = cstat[c];
+  }
+  if (comp_of_out) for (int s = 0; s < n_seg; ++s) comp_of_out[s] = comp_of[s];
+  rc = tot->status;
+
+done:
+  free(cu); free(cv); free(tu); free(tv); free(cptr); free(cadj); free(sptr); free(sadj);
+  free(unit); free(udeg); free(queue); free(removed_order); free(uptr); free(useg);
+  free(removed); free(queued); free(selfc); free(parent); free(comp_of); free(comp_ptr);
+  free(comp_seg); free(local_of); free(order); free(ccost); free(cnodes); free(cstat);
+  return rc;
+}

@@ -1,0 +1,144 @@
+"""Independent pure-Python restatements of the canonical search, used to pin the oracle.
+
+Nothing here touches dancing links or bitsets: the state is the partial
+assignment ``x`` itself.  A segment's "column size" is the number of masks
+not used by an assigned conflict neighbour (the active rows of its primary
+column in the EC matrix of Sec. 2.3); a row's added cost is the Eq. 1 cost of
+its edges to assigned neighbours.  Only for tiny graphs.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def adjacency(n, edges):
+    adj = [[] for _ in range(n)]
+    for a, b in edges:
+        adj[a].append(b)
+        adj[b].append(a)
+    return [sorted(set(l)) for l in adj]
+
+
+def eq1_cost(x, conf, stitch, cc=10, cs=1):
+    """Eq. 1 written out: Cc * #monochromatic conflict edges + Cs * #cut stitch edges."""
+    return cc * sum(1 for a, b in conf if x[a] == x[b]) + cs * sum(1 for a, b in stitch if x[a] != x[b])
+
+
+def brute_force(n, k, conf, stitch, cc=10, cs=1):
+    """(min cost, number of optimal assignments) over all k^n assignments (numpy)."""
+    if n == 0:
+        return 0, 1
+    X = np.array(list(itertools.product(range(k), repeat=n)), dtype=np.int8)
+    cost = np.zeros(X.shape[0], dtype=np.int64)
+    for a, b in conf:
+        cost += cc * (X[:, a] == X[:, b])
+    for a, b in stitch:
+        cost += cs * (X[:, a] != X[:, b])
+    m = int(cost.min())
+    return m, int((cost == m).sum())
+
+
+class _Search:
+    def __init__(self, n, k, conf, stitch, cc, cs):
+        self.n, self.k, self.cc, self.cs = n, k, cc, cs
+        self.cadj = adjacency(n, conf)
+        self.sadj = adjacency(n, stitch)
+        self.x = [-1] * n
+
+    def avail(self, v):
+        used = {self.x[u] for u in self.cadj[v] if self.x[u] >= 0}
+        return self.k - len(used)
+
+    def pick(self):
+        """Unassigned segment with fewest available masks, lowest index on ties; and Z."""
+        best_v, best_a, z = -1, None, 0
+        for v in range(self.n):
+            if self.x[v] >= 0:
+                continue
+            a = self.avail(v)
+            if a == 0:
+                z += 1
+            if best_a is None or a < best_a:
+                best_v, best_a = v, a
+        return best_v, z
+
+    def row_order(self, v):
+        inc = []
+        for c in range(self.k):
+            t = self.cc * sum(1 for u in self.cadj[v] if self.x[u] == c)
+            t += self.cs * sum(1 for u in self.sadj[v] if self.x[u] >= 0 and self.x[u] != c)
+            inc.append(t)
+        return sorted(range(self.k), key=lambda c: (inc[c], c)), inc
+
+
+def canonical_leaves(n, k, conf, stitch, cc=10, cs=1):
+    """Every leaf of the bound-free canonical search tree, in depth-first order.
+
+    Returns a list of (cost, x).  The method's answer is the first leaf of
+    minimum cost in this list.
+    """
+    S = _Search(n, k, conf, stitch, cc, cs)
+    out = []
+
+    def rec(g):
+        v, _ = S.pick()
+        if v < 0:
+            out.append((g, list(S.x)))
+            return
+        order, inc = S.row_order(v)
+        for c in order:
+            S.x[v] = c
+            rec(g + inc[c])
+            S.x[v] = -1
+
+    rec(0)
+    return out
+
+
+def first_min_leaf(n, k, conf, stitch, cc=10, cs=1):
+    leaves = canonical_leaves(n, k, conf, stitch, cc, cs)
+    m = min(c for c, _ in leaves)
+    for c, x in leaves:
+        if c == m:
+            return c, x
+
+
+def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0):
+    """The canonical search with the dead-segment bound and node budget.
+
+    node = one call; leaf with g < best is the new incumbent and best == 0
+    stops; prune when g + cc * (#unassigned segments with no available mask)
+    >= best; with budget B > 0, a call made when an incumbent exists and B
+    nodes have been counted stops everything.  Returns (cost, x, nodes,
+    budget_hit).
+    """
+    S = _Search(n, k, conf, stitch, cc, cs)
+    st = dict(best=None, bestx=None, nodes=0, done=False, hit=False)
+
+    def rec(g):
+        if budget > 0 and st["best"] is not None and st["nodes"] >= budget:
+            st["hit"] = True
+            st["done"] = True
+            return
+        st["nodes"] += 1
+        v, z = S.pick()
+        if v < 0:
+            if st["best"] is None or g < st["best"]:
+                st["best"], st["bestx"] = g, list(S.x)
+                if g == 0:
+                    st["done"] = True
+            return
+        if st["best"] is not None and g + cc * z >= st["best"]:
+            return
+        order, inc = S.row_order(v)
+        for c in order:
+            if st["done"]:
+                break
+            S.x[v] = c
+            rec(g + inc[c])
+            S.x[v] = -1
+
+    rec(0)
+    return st["best"], st["bestx"], st["nodes"], st["hit"]
