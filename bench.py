@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the batched EC layout-decomposition search on one GB300.
+
+One step = the whole search path over one synthetic layout (unit-disk
+conflict graph, 200,000 polygons, mean degree 3, stitch p = 0.2, k = 3,
+seed 2): every connected sub-graph left after simplification is searched by
+the persistent batched kernel (one launch, device work queue, replayed from a
+CUDA graph).  ``value`` = decomposed segments per second with the EC
+matrices already resident in HBM; ``e2e`` = the same metric through the C
+ABI from host graph arrays to host masks (build + upload + search + copy
+back + recovery + counts).  Every search instance has the same node budget
+on the GPU and in the CPU oracle, so both compute the same answer.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank decomposes its own layout (seed + 1000 *
+rank): the units are independent, no data-path collective; the max over
+ranks of the timed region is used (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+
+METRIC = "EC search nodes/s & segments/s (batched vs plain GPU vs CPU DLX); p99 latency"
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="k3_n200k_p02_batched")
+    ap.add_argument("--budget", type=int, default=1 << 16)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--plain-scale", type=int, default=20,
+                    help="the plain one-launch-per-instance path runs on the same workload with "
+                         "polygons / plain-scale (same density and degree)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def workload_layout(name: str, rank: int, scale: int = 1):
+    from paper_2303_14335_gb300 import synth
+    cfg = dict(synth.WORKLOADS[name])
+    mode = cfg.pop("mode")
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    if scale > 1:
+        cfg["n_poly"] = max(cfg["n_poly"] // scale, 100)
+    return synth.unit_disk_layout(name=name, **cfg), mode
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle (Knuth dancing links on all host cores) on the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    layout, mode = workload_layout(args.workload, 0)
+    flags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
+    cores = os.cpu_count() or 1
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.decompose(layout, flags=flags, budget=args.budget, nthreads=cores)
+    times = []
+    res = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = oracle.decompose(layout, flags=flags, budget=args.budget, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = layout.n_seg * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "segments/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "segments": layout.n_seg, "k": layout.k,
+                   "node_budget": args.budget},
+        "nodes_per_s": res.nodes * args.steps / total,
+        "cpu_baseline": {"value": value, "unit": "segments/s", "cores": cores, "kind": "oracle",
+                         "sample": f"whole layout ({layout.n_seg} segments, "
+                                   f"{res.n_components} instances) per step"},
+        "e2e": {"value": value, "unit": "segments/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2303_14335_gb300 import mpld
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    layout, mode = workload_layout(args.workload, rank)
+    flags = (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE) if mode == "single" else 0
+    prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
+    info = mpld.mpld_problem_info(prob)
+    prm = mpld.make_params(node_budget=args.budget)
+    tune = None
+    if not args.no_tune:
+        tune = mpld.mpld_autotune([prob], prm, s)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up
+    for _ in range(max(args.warmup, 1)):
+        mpld.mpld_search_batch_async([prob], prm, s)
+        stream.synchronize()
+
+    # timed: K steps, each bracketed by events on the launching stream, L2
+    # flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        mpld.mpld_search_batch_async([prob], prm, s)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        segs = torch.tensor([layout.n_seg], dtype=torch.float64, device="cuda")
+        dist.all_reduce(segs)
+        all_segments = float(segs.item())
+    else:
+        all_segments = float(layout.n_seg)
+    rc, mask, res = mpld.mpld_fetch(prob, s)
+    value = all_segments * args.steps / total_s
+    nodes_per_s = res.nodes * world * args.steps / total_s
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "segments": layout.n_seg, "polygons": layout.n_poly,
+                   "k": layout.k, "node_budget": args.budget, "instances": info.n_components,
+                   "max_instance": info.max_component,
+                   "removed_segments": info.n_removed_segments,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"weak: {world} independent layouts" if world > 1 else "1 GPU",
+                   "launch": ({"warps_per_cta": tune.warps_per_cta, "slot_bytes": tune.slot_bytes,
+                               "ctas_per_sm": tune.ctas_per_sm,
+                               "spilled_instances": tune.n_instances_spilled}
+                              if tune else "default")},
+        "nodes_per_s": nodes_per_s,
+        "search": {"nodes": res.nodes, "cost": res.cost, "conflicts": res.n_conflicts,
+                   "stitches": res.n_stitches, "budget_instances": res.n_budget_components,
+                   "status": rc, "step_ms": step_ms},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+
+    # roofline of the dominant kernel (the persistent search kernel): integer
+    # ALU work per launch / launch duration vs the SM integer-lane peak
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local_rank)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak_gops = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9
+    achieved = res.work / (total_s / args.steps) / 1e9
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak_gops,
+                       "unit": "Gop/s", "frac": achieved / alu_peak_gops, "traffic": None,
+                       "peak_source": f"{props.multi_processor_count} SMs x 128 int32 lanes x "
+                                      f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json)",
+                       "work_ops_per_launch": res.work}
+
+    if not args.no_e2e:
+        # end to end through the C ABI: host arrays in, host masks out
+        e2e_t = []
+        for i in range(args.warmup + args.steps):
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
+            rc2, masks2, res2 = mpld.mpld_solve_batch([p2], prm, s)
+            t1 = time.perf_counter()
+            inf2 = mpld.mpld_problem_info(p2)
+            p2.close()
+            if i >= args.warmup:
+                e2e_t.append(t1 - t0)
+            assert np.array_equal(masks2[0], mask)
+        e2e_total = sum(e2e_t)
+        if dist:
+            t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        # bytes copied per step: read-only blocks + descriptors + order up;
+        # instance results + instance masks + status word down
+        h2d = inf2.arena_bytes + 80 * inf2.n_components + 4 * inf2.n_components
+        d2h = 32 * inf2.n_components + inf2.instance_segments + 4
+        out["e2e"] = {"value": all_segments * len(e2e_t) / e2e_total, "unit": "segments/s",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": 1000 * e2e_total / len(e2e_t),
+                      "gpu_launches_per_step": 1}
+
+    if rank == 0 and not args.no_plain:
+        # plain one-launch-per-instance path vs the batched one on a smaller
+        # layout of the same workload (same density and degree)
+        small, _ = workload_layout(args.workload, 0, scale=args.plain_scale)
+        ps = mpld.mpld_build_matrix(small, mpld.make_params(flags=flags), s)
+        pinfo = mpld.mpld_problem_info(ps)
+        times = {}
+        for name in ("plain", "batched"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for rep in range(2):
+                e0.record(stream)
+                if name == "plain":
+                    mpld.mpld_search_plain_async(ps, prm, s)
+                else:
+                    mpld.mpld_search_batch_async([ps], prm, s)
+                e1.record(stream)
+                stream.synchronize()
+            times[name] = e0.elapsed_time(e1) / 1000.0
+        ps.close()
+        out["plain"] = {"segments": small.n_seg, "instances": pinfo.n_components,
+                        "plain_segments_per_s": small.n_seg / times["plain"],
+                        "batched_segments_per_s": small.n_seg / times["batched"],
+                        "batched_over_plain": times["plain"] / times["batched"],
+                        "gpu_launches_plain": pinfo.n_components}
+
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ref = oracle.decompose(layout, flags=flags, budget=args.budget, nthreads=cores)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": layout.n_seg / dt, "unit": "segments/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"whole layout ({layout.n_seg} segments, "
+                                         f"{ref.n_components} instances), one decomposition",
+                               "nodes_per_s": ref.nodes / dt,
+                               "matches_gpu": bool(np.array_equal(ref.mask, mask) and
+                                                   ref.nodes == res.nodes)}
+    prob.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

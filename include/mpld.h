@@ -1,0 +1,239 @@
+/*
+ * mpld.h -- C ABI of libmpld: exact-cover (EC) multiple patterning layout
+ * decomposition on one GB300 (sm_103a).
+ *
+ * Paper: G. Chen, H. Yang, B. Yu, "GPU-Accelerated Matrix Cover Algorithm for
+ * Multiple Patterning Layout Decomposition".
+ *
+ * Problem (Sec. 2.1, Eq. 1a-1d): a layout graph with conflict edges CE and
+ * stitch edges SE and k masks in; a mask x_i in {0..k-1} per segment out,
+ * minimising  cost_conflict * #{(i,j) in CE : x_i == x_j}
+ *           + cost_stitch   * #{(i,j) in SE : x_i != x_j}.
+ * The paper's weights are 1 and alpha = 0.1 (Sec. 2.1); the defaults 10 and
+ * 1 are the same objective in integers.  (Eq. 1d prints the mask domain as
+ * {0..k}; k masks are meant.)
+ *
+ * Flow (Sec. 2.2): simplify the graph, split it into sub-graphs, solve each
+ * with the matrix-cover search (Sec. 2.3, Algorithm 1), recover the removed
+ * nodes, count conflicts and stitches.
+ *
+ * Conventions for every call:
+ *   - all pointers in structs and arguments are HOST pointers unless named
+ *     otherwise; the library never keeps a caller pointer after a call
+ *     returns;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); all device work of a call is ordered on it;
+ *   - return value: MPLD_OK (0), MPLD_BUDGET (1: at least one search
+ *     instance hit its node budget or time limit and returned its best
+ *     assignment so far), or a negative MPLD_E_* error code; on an error no
+ *     output is written and the handle is left as it was.
+ *   - calls on different handles may run concurrently from different host
+ *     threads; calls on one handle must not.
+ */
+#ifndef MPLD_H
+#define MPLD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPLD_OK 0
+#define MPLD_BUDGET 1
+#define MPLD_TIMEOUT 2         /* per-instance status: time limit reached */
+#define MPLD_E_INVALID (-1)    /* malformed input: id out of range, self-loop, k not in [2,8], ... */
+#define MPLD_E_OOM (-2)        /* host or device allocation failed */
+#define MPLD_E_CUDA (-3)       /* a CUDA runtime call failed */
+#define MPLD_E_TIMEOUT (-4)    /* a device-side wait ran out (status word set by the kernel) */
+#define MPLD_E_TOO_LARGE (-5)  /* a search instance exceeds the supported size */
+#define MPLD_E_STATE (-6)      /* call out of order (e.g. fetch before any solve) */
+
+/* mpld_params.flags */
+#define MPLD_NO_SIMPLIFY 1u      /* skip the simplification step (Sec. 2.2) */
+#define MPLD_SINGLE_INSTANCE 2u  /* search all remaining segments as ONE instance (no sub-graph split) */
+#define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
+                                    mpld_problem_info / mpld_component_results / mpld_export_matrix;
+                                    the solve calls then return MPLD_E_STATE */
+
+/* Largest search instance (segments of one sub-graph). */
+#define MPLD_MAX_INSTANCE_SEGMENTS 65535
+
+/*
+ * Layout graph (Sec. 2.1: G = {V, E}, E = CE u SE).  Caller-owned, read only
+ * during mpld_build_matrix.
+ *   n_seg        segments (nodes), ids 0..n_seg-1;
+ *   k            masks, 2 <= k <= 8;
+ *   conf_u/v     n_conf conflict edges; duplicates and (v,u) repeats are
+ *                merged; self-loops and ids outside [0,n_seg) are errors;
+ *   st_u/v       n_stitch stitch edges, same rules;
+ *   polygon_of   segment -> polygon id in [0,n_seg), or NULL (each segment
+ *                its own polygon).  A polygon together with everything joined
+ *                to it by stitch edges is one unit of simplification;
+ *   cost_conflict, cost_stitch   integer weights in [0, 10000].
+ */
+typedef struct {
+  int32_t n_seg, k;
+  int32_t n_conf;
+  const int32_t *conf_u, *conf_v;
+  int32_t n_stitch;
+  const int32_t *st_u, *st_v;
+  const int32_t *polygon_of;
+  int32_t cost_conflict, cost_stitch;
+} mpld_graph;
+
+/*
+ * Search parameters.
+ *   node_budget    per search instance; 0 = unlimited.  A node is one step
+ *                  of Algorithm 1 (one recursive call); once an instance has
+ *                  an incumbent and has counted node_budget nodes, its
+ *                  search stops with status MPLD_BUDGET;
+ *   time_limit_ms  per search instance, measured on the device from the
+ *                  start of its search; 0 = 60000.  An instance still
+ *                  searching when it runs out stops with status MPLD_TIMEOUT
+ *                  and keeps its incumbent (the layout status is then
+ *                  MPLD_BUDGET);
+ *   flags          MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_HOST_ONLY
+ *                  (used by mpld_build_matrix);
+ *   warps_per_cta, slot_bytes   launch shape of the batched kernel; 0 = the
+ *                  tuned or default shape (see mpld_autotune).
+ */
+typedef struct {
+  int64_t node_budget;
+  int64_t time_limit_ms;
+  uint32_t flags;
+  int32_t warps_per_cta;
+  int32_t slot_bytes;
+  int32_t reserved;
+} mpld_params;
+
+/* Layout-level result (Sec. 3: st# and cn# are n_stitches and n_conflicts). */
+typedef struct {
+  int32_t status;               /* MPLD_OK / MPLD_BUDGET (worst over instances) */
+  int32_t n_components;         /* search instances */
+  int64_t n_conflicts, n_stitches;
+  int64_t cost;                 /* cost_conflict*n_conflicts + cost_stitch*n_stitches */
+  int64_t nodes;                /* search nodes over all instances */
+  int64_t n_removed_segments;   /* removed by simplification, recovered after the search */
+  int32_t max_component;        /* segments in the largest instance */
+  int32_t n_budget_components;  /* instances that stopped on budget or time */
+  int64_t work;                 /* algorithmic integer operations of the search: 2 per
+                                   uncovered column per node, k per neighbour of each
+                                   expanded segment, 5 per column of each covered row */
+} mpld_result;
+
+typedef struct mpld_problem mpld_problem;
+
+/*
+ * Build the EC matrices of a layout (Sec. 2.2 simplification and sub-graph
+ * split; Sec. 2.3 "homogeneous graph to binary matrix"; Algorithm 1 steps
+ * that split the DG into sub-graphs) and upload them to the device.
+ * Rows of instance i are (segment v, mask c); primary column P_v; secondary
+ * column S_{e,c} per conflict edge e and mask c.  The matrices and search
+ * stacks live in one device arena owned by the returned handle.
+ *   graph   caller-owned, read during the call only;
+ *   params  only `flags` is read; NULL = defaults;
+ *   stream  the upload is enqueued on it; the call returns once the host
+ *           staging buffer may be reused (it synchronises the stream);
+ *   out     receives the handle; free it with mpld_free.
+ * Errors: MPLD_E_INVALID, MPLD_E_TOO_LARGE (a sub-graph with more than
+ * MPLD_MAX_INSTANCE_SEGMENTS segments), MPLD_E_OOM, MPLD_E_CUDA.
+ */
+int mpld_build_matrix(const mpld_graph *graph, const mpld_params *params, void *stream,
+                      mpld_problem **out);
+
+/*
+ * Plain path: one kernel launch per search instance (Sec. 3: "one block for
+ * each sub-graph"), one after the other on `stream`, then the copy back,
+ * recovery of the removed segments (Sec. 2.2) and the counts.
+ *   mask_out  host, n_seg int8 masks (may be NULL);
+ *   result    host (may be NULL).
+ * Synchronous with respect to the host outputs.
+ */
+int mpld_solve(mpld_problem *p, const mpld_params *params, int8_t *mask_out, mpld_result *result,
+               void *stream);
+
+/*
+ * Batched path: the instances of all `n` problems in ONE persistent launch
+ * fed by a device work queue ordered largest first (Sec. 2.3 task
+ * parallelism over sub-graphs), replayed from a captured CUDA graph; then
+ * the copy back, recovery and counts per problem.
+ *   ps         n problem handles (distinct);
+ *   masks_out  n host pointers (each n_seg of its problem) or NULL / NULL
+ *              entries to skip;
+ *   results    n host results or NULL.
+ * Synchronous with respect to the host outputs.
+ */
+int mpld_solve_batch(mpld_problem *const *ps, int32_t n, const mpld_params *params,
+                     int8_t *const *masks_out, mpld_result *results, void *stream);
+
+/*
+ * Device-only halves of mpld_solve_batch, for callers that keep the work on
+ * the device: mpld_search_batch_async enqueues the batched search on
+ * `stream` and returns without waiting; the per-instance results stay in
+ * device memory until mpld_fetch copies them back (it synchronises
+ * `stream`), recovers the removed segments and counts.
+ */
+int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const mpld_params *params,
+                            void *stream);
+int mpld_fetch(mpld_problem *p, int8_t *mask_out, mpld_result *result, void *stream);
+
+/* Device-only half of mpld_solve (one launch per instance, enqueued only). */
+int mpld_search_plain_async(mpld_problem *p, const mpld_params *params, void *stream);
+
+/* Release every host and device resource of the handle.  NULL is a no-op.
+ * The caller must make sure no work of the handle is still in flight. */
+void mpld_free(mpld_problem *p);
+
+/* Static string for a status or error code. */
+const char *mpld_status_string(int code);
+
+/* Sizes of a built problem. */
+typedef struct {
+  int32_t n_seg, k, n_components, max_component;
+  int64_t n_removed_segments;
+  int64_t arena_bytes;          /* device bytes of EC matrices and graph data */
+  int64_t state_bytes;          /* device bytes reserved for search stacks */
+  int64_t instance_segments;    /* segments inside search instances */
+} mpld_info;
+int mpld_problem_info(const mpld_problem *p, mpld_info *info);
+
+/*
+ * Per-instance results of the last fetch (instance order = ascending lowest
+ * segment id).  Each array holds n_components entries; any may be NULL.
+ * comp_of (n_seg entries): instance of each segment, -1 if removed.
+ */
+int mpld_component_results(const mpld_problem *p, int64_t *nodes, int64_t *cost, int32_t *status,
+                           int32_t *comp_of);
+
+/*
+ * EC matrix of instance `comp` as a dense 0/1 array, row-major
+ * [n*k][1 + n + k*|E_c|]: column 0 unused, column 1+v = P_v, column
+ * 1+n+e*k+c = S_{e,c} with conflict edges e sorted by (min,max) local id.
+ * Rebuilt on the host from the handle's packed form, for inspection;
+ * `dense` must hold n*k*(1+n+k*|E_c|) bytes; query the sizes with
+ * dims = {n, k, n_conf_edges} first by passing dense = NULL.
+ */
+int mpld_export_matrix(const mpld_problem *p, int32_t comp, uint8_t *dense, int32_t *dims);
+
+/*
+ * Launch shape of the batched kernel.  mpld_autotune times the candidate
+ * shapes on the given problems (results are the same for every shape) and
+ * stores the fastest in a process-wide cache keyed by (k, size histogram),
+ * which mpld_solve_batch uses when params leave the shape at 0.
+ */
+typedef struct {
+  int32_t warps_per_cta;
+  int32_t slot_bytes;
+  int32_t ctas_per_sm;
+  int32_t n_instances_spilled;  /* instances whose state did not fit the slot */
+  float ms;                     /* measured time of the chosen shape */
+} mpld_tune;
+int mpld_autotune(mpld_problem *const *ps, int32_t n, const mpld_params *params, void *stream,
+                  mpld_tune *best);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPLD_H */

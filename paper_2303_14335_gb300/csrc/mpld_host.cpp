@@ -1,0 +1,923 @@
+// mpld_host.cpp -- host half of libmpld: input checks, simplification and
+// sub-graph split (Sec. 2.2; Algorithm 1 steps that split the DG), EC matrix
+// packing (Sec. 2.3), launches of the search kernels, copy back, recovery of
+// removed nodes (Sec. 2.2) and the conflict / stitch counts (Eq. 1).
+//
+// Simplification rule (the paper names the step but not its rule): a unit is
+// a polygon together with every segment joined to it by a stitch edge.  A
+// unit with fewer than k conflict edges to remaining units is removed; the
+// queue is FIFO, seeded in ascending unit id (its lowest segment), and a
+// removal decrements its neighbours, which join the queue when they drop
+// below k.  A unit with a conflict edge inside itself is never removed.
+// Recovery walks the removal order backwards and gives every segment of a
+// unit the lowest mask unused by its coloured conflict neighbours, which
+// costs nothing, so the layout optimum equals the sum of instance optima.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mpld.h"
+#include "mpld_internal.h"
+
+using mpld::InstDesc;
+using mpld::InstResult;
+
+namespace {
+
+constexpr int MAX_COST = 10000;
+constexpr int64_t DEFAULT_TIME_LIMIT_MS = 60000;
+
+struct GraphKey {
+  int nw = 0, slot = 0, ctas = 0;
+  int64_t budget = 0, tl = 0;
+  bool operator==(const GraphKey &o) const {
+    return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl;
+  }
+};
+
+struct Shape {
+  int nw, slot, ctas;
+};
+
+}  // namespace
+
+struct mpld_problem {
+  int n_seg = 0, k = 0;
+  int64_t Cc = 10, Cs = 1;
+  uint32_t flags = 0;
+  // normalised input
+  std::vector<int32_t> cu, cv, su, sv;
+  std::vector<int32_t> cptr, cadj;  // global conflict adjacency
+  // simplification
+  std::vector<int32_t> unit_of, uptr, useg, removed_order;
+  int64_t n_removed_segments = 0;
+  // sub-graphs (search instances)
+  int n_comp = 0;
+  std::vector<int32_t> comp_ptr, comp_seg, comp_of;
+  std::vector<int32_t> inst_ne2;
+  int max_component = 0;
+  int64_t instance_segments = 0;
+  // packed instances
+  std::vector<uint8_t> h_arena;        // host copy of the read-only blocks
+  std::vector<uint64_t> ro_off;
+  std::vector<uint32_t> footprint;     // state + read-only bytes
+  std::vector<InstDesc> h_desc;
+  std::vector<int32_t> h_order;        // largest first
+  // device memory: one allocation
+  uint8_t *d_base = nullptr;
+  size_t d_bytes = 0;
+  uint8_t *d_arena = nullptr, *d_scratch = nullptr;
+  size_t arena_bytes = 0, scratch_bytes = 0;
+  InstDesc *d_desc = nullptr;
+  int32_t *d_order = nullptr;
+  InstResult *d_res = nullptr;
+  int8_t *d_masks = nullptr;
+  uint32_t *d_queue = nullptr;
+  int32_t *d_err = nullptr;
+  // pinned host mirrors of the results
+  InstResult *h_res = nullptr;
+  int8_t *h_masks = nullptr;
+  int32_t *h_err = nullptr;
+  size_t mask_bytes = 0;
+  bool searched = false;      // a search was enqueued since the last fetch
+  bool have_results = false;  // a fetch completed
+  bool results_copied = false;  // the enqueued work already copies results back
+  std::vector<int64_t> r_nodes, r_cost;
+  std::vector<int32_t> r_status;
+  // captured launch sequence
+  cudaGraphExec_t gexec = nullptr;
+  GraphKey gkey;
+  void *gstream = nullptr;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+
+int find_root(std::vector<int32_t> &parent, int a) {
+  while (parent[a] != a) {
+    parent[a] = parent[parent[a]];
+    a = parent[a];
+  }
+  return a;
+}
+
+void unite_min(std::vector<int32_t> &parent, int a, int b) {
+  int ra = find_root(parent, a), rb = find_root(parent, b);
+  if (ra == rb) return;
+  if (ra < rb) parent[rb] = ra;
+  else parent[ra] = rb;
+}
+
+// (min,max)-normalised, sorted, unique edges; returns false on a bad edge.
+bool normalise(int n, int m, const int32_t *u, const int32_t *v, std::vector<int32_t> &ou,
+               std::vector<int32_t> &ov) {
+  std::vector<int64_t> keys;
+  keys.reserve((size_t)m);
+  for (int e = 0; e < m; ++e) {
+    const int a = u[e], b = v[e];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) return false;
+    keys.push_back((int64_t)std::min(a, b) * n + std::max(a, b));
+  }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  ou.resize(keys.size());
+  ov.resize(keys.size());
+  for (size_t e = 0; e < keys.size(); ++e) {
+    ou[e] = (int32_t)(keys[e] / n);
+    ov[e] = (int32_t)(keys[e] % n);
+  }
+  return true;
+}
+
+// Adjacency with neighbours ascending (edges come sorted by (min,max)).
+void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
+         std::vector<int32_t> &ptr, std::vector<int32_t> &adj) {
+  ptr.assign((size_t)n + 1, 0);
+  for (size_t e = 0; e < u.size(); ++e) { ptr[u[e] + 1]++; ptr[v[e] + 1]++; }
+  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+  adj.resize(2 * u.size());
+  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+  // smaller neighbours of x arrive (as u of edges (u,x)) in ascending u, then
+  // larger ones (as v of edges (x,v)) in ascending v -- but interleaved in
+  // edge order; two passes keep each list sorted.
+  for (size_t e = 0; e < u.size(); ++e) adj[fill[v[e]]++] = u[e];
+  for (size_t e = 0; e < u.size(); ++e) adj[fill[u[e]]++] = v[e];
+}
+
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, mpld_tune> g_tune_cache;
+
+// Process-wide cache key of a problem set: k and a coarse size histogram.
+std::tuple<int, int, int, int> tune_key(mpld_problem *const *ps, int n) {
+  int kmax = 0;
+  int64_t inst = 0;
+  uint32_t fmax = 0;
+  int64_t fsum = 0;
+  for (int i = 0; i < n; ++i) {
+    kmax = std::max(kmax, ps[i]->k);
+    inst += ps[i]->n_comp;
+    for (uint32_t f : ps[i]->footprint) { fmax = std::max(fmax, f); fsum += f; }
+  }
+  auto lg = [](int64_t x) { int b = 0; while (x > 1) { x >>= 1; ++b; } return b; };
+  return {kmax, lg(inst), lg(fmax), lg(inst ? fsum / inst : 0)};
+}
+
+}  // namespace
+
+// ================================================================= build
+
+extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params, void *stream,
+                                 mpld_problem **out) {
+  if (!g || !out) return MPLD_E_INVALID;
+  *out = nullptr;
+  const int n = g->n_seg, k = g->k;
+  if (n < 0 || k < 2 || k > 8 || g->n_conf < 0 || g->n_stitch < 0) return MPLD_E_INVALID;
+  if ((g->n_conf > 0 && (!g->conf_u || !g->conf_v)) ||
+      (g->n_stitch > 0 && (!g->st_u || !g->st_v)))
+    return MPLD_E_INVALID;
+  if (g->cost_conflict < 0 || g->cost_conflict > MAX_COST || g->cost_stitch < 0 ||
+      g->cost_stitch > MAX_COST)
+    return MPLD_E_INVALID;
+  if (g->polygon_of)
+    for (int s = 0; s < n; ++s)
+      if (g->polygon_of[s] < 0 || g->polygon_of[s] >= n) return MPLD_E_INVALID;
+
+  mpld_problem *p = new (std::nothrow) mpld_problem();
+  if (!p) return MPLD_E_OOM;
+  p->n_seg = n;
+  p->k = k;
+  p->Cc = g->cost_conflict;
+  p->Cs = g->cost_stitch;
+  p->flags = params ? params->flags : 0u;
+  try {
+    if (!normalise(n, g->n_conf, g->conf_u, g->conf_v, p->cu, p->cv) ||
+        !normalise(n, g->n_stitch, g->st_u, g->st_v, p->su, p->sv)) {
+      delete p;
+      return MPLD_E_INVALID;
+    }
+    std::vector<int32_t> sptr, sadj;
+    csr(n, p->cu, p->cv, p->cptr, p->cadj);
+    csr(n, p->su, p->sv, sptr, sadj);
+
+    // ---- units: polygons merged along stitch edges, id = lowest segment
+    std::vector<int32_t> parent((size_t)n);
+    std::iota(parent.begin(), parent.end(), 0);
+    {
+      std::vector<int32_t> first_of((size_t)n, -1);
+      for (int s = 0; s < n; ++s) {
+        const int poly = g->polygon_of ? g->polygon_of[s] : s;
+        if (first_of[poly] < 0) first_of[poly] = s;
+        else unite_min(parent, first_of[poly], s);
+      }
+    }
+    for (size_t e = 0; e < p->su.size(); ++e) unite_min(parent, p->su[e], p->sv[e]);
+    p->unit_of.resize((size_t)n);
+    for (int s = 0; s < n; ++s) p->unit_of[s] = find_root(parent, s);
+    p->uptr.assign((size_t)n + 1, 0);
+    for (int s = 0; s < n; ++s) p->uptr[p->unit_of[s] + 1]++;
+    for (int u = 0; u < n; ++u) p->uptr[u + 1] += p->uptr[u];
+    p->useg.resize((size_t)n);
+    {
+      std::vector<int32_t> fill(p->uptr.begin(), p->uptr.end() - 1);
+      for (int s = 0; s < n; ++s) p->useg[fill[p->unit_of[s]]++] = s;
+    }
+
+    // ---- simplification: FIFO peel of units with < k external conflict edges
+    std::vector<uint8_t> removed((size_t)n, 0);
+    if (!(p->flags & MPLD_NO_SIMPLIFY)) {
+      std::vector<int32_t> udeg((size_t)n, 0);
+      std::vector<uint8_t> selfc((size_t)n, 0), queued((size_t)n, 0);
+      for (size_t e = 0; e < p->cu.size(); ++e) {
+        const int a = p->unit_of[p->cu[e]], b = p->unit_of[p->cv[e]];
+        if (a == b) selfc[a] = 1;
+        else { udeg[a]++; udeg[b]++; }
+      }
+      std::vector<int32_t> queue;
+      queue.reserve((size_t)n);
+      for (int u = 0; u < n; ++u)
+        if (p->unit_of[u] == u && !selfc[u] && udeg[u] < k) { queue.push_back(u); queued[u] = 1; }
+      for (size_t h = 0; h < queue.size(); ++h) {
+        const int u = queue[h];
+        removed[u] = 1;
+        p->removed_order.push_back(u);
+        for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) {
+          const int s = p->useg[t];
+          for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
+            const int w = p->unit_of[p->cadj[i]];
+            if (w == u || removed[w]) continue;
+            if (--udeg[w] < k && !queued[w] && !selfc[w]) { queue.push_back(w); queued[w] = 1; }
+          }
+        }
+      }
+    }
+
+    // ---- sub-graphs: connected components of what remains
+    std::iota(parent.begin(), parent.end(), 0);
+    const bool single = (p->flags & MPLD_SINGLE_INSTANCE) != 0;
+    if (!single) {
+      for (size_t e = 0; e < p->cu.size(); ++e)
+        if (!removed[p->unit_of[p->cu[e]]] && !removed[p->unit_of[p->cv[e]]])
+          unite_min(parent, p->cu[e], p->cv[e]);
+      for (size_t e = 0; e < p->su.size(); ++e)
+        if (!removed[p->unit_of[p->su[e]]]) unite_min(parent, p->su[e], p->sv[e]);
+    }
+    p->comp_of.assign((size_t)n, -1);
+    {
+      std::vector<int32_t> id_of((size_t)n, -1);
+      int single_id = -1;
+      for (int s = 0; s < n; ++s) {
+        if (removed[p->unit_of[s]]) continue;
+        if (single) {
+          if (single_id < 0) single_id = p->n_comp++;
+          p->comp_of[s] = single_id;
+        } else {
+          const int r = find_root(parent, s);
+          if (id_of[r] < 0) id_of[r] = p->n_comp++;
+          p->comp_of[s] = id_of[r];
+        }
+      }
+    }
+    for (int u : p->removed_order) p->n_removed_segments += p->uptr[u + 1] - p->uptr[u];
+    const int C = p->n_comp;
+    p->comp_ptr.assign((size_t)C + 1, 0);
+    for (int s = 0; s < n; ++s)
+      if (p->comp_of[s] >= 0) p->comp_ptr[p->comp_of[s] + 1]++;
+    for (int c = 0; c < C; ++c) p->comp_ptr[c + 1] += p->comp_ptr[c];
+    p->comp_seg.resize((size_t)p->comp_ptr[C]);
+    std::vector<int32_t> local_of((size_t)n, -1);
+    {
+      std::vector<int32_t> fill(p->comp_ptr.begin(), p->comp_ptr.end() - 1);
+      for (int s = 0; s < n; ++s)
+        if (p->comp_of[s] >= 0) {
+          const int c = p->comp_of[s];
+          local_of[s] = fill[c] - p->comp_ptr[c];
+          p->comp_seg[fill[c]++] = s;
+        }
+    }
+    for (int c = 0; c < C; ++c) {
+      const int sz = p->comp_ptr[c + 1] - p->comp_ptr[c];
+      p->max_component = std::max(p->max_component, sz);
+      if (sz > MPLD_MAX_INSTANCE_SEGMENTS) { delete p; return MPLD_E_TOO_LARGE; }
+    }
+    p->instance_segments = p->comp_ptr[C];
+
+    // ---- pack each instance: read-only block + descriptor
+    p->ro_off.resize((size_t)C);
+    p->footprint.resize((size_t)C);
+    p->inst_ne2.resize((size_t)C);
+    p->h_desc.resize((size_t)C);
+    std::vector<int32_t> ns2v((size_t)C), mask_off((size_t)C);
+    uint64_t arena = 0, scratch = 0;
+    std::vector<uint64_t> scratch_off((size_t)C);
+    const int kp = mpld::kp_for(k);
+    for (int c = 0; c < C; ++c) {
+      int ne2 = 0, ns2 = 0;
+      for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
+        const int s = p->comp_seg[t];
+        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) ne2 += p->comp_of[p->cadj[i]] == c;
+        for (int i = sptr[s]; i < sptr[s + 1]; ++i) ns2 += p->comp_of[sadj[i]] == c;
+      }
+      const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
+      const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2);
+      const mpld::StateLayout L = mpld::state_layout(nc, mpld::words_for(nc, kp), ne2, kp);
+      p->inst_ne2[c] = ne2;
+      ns2v[c] = ns2;
+      p->ro_off[c] = arena;
+      arena += R.bytes;
+      scratch_off[c] = scratch;
+      scratch += L.bytes;
+      p->footprint[c] = L.bytes + R.bytes;
+      mask_off[c] = p->comp_ptr[c];
+    }
+    p->arena_bytes = (size_t)arena;
+    p->scratch_bytes = (size_t)scratch;
+    p->h_arena.assign((size_t)arena, 0);
+    for (int c = 0; c < C; ++c) {
+      const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
+      const mpld::RoLayout R = mpld::ro_layout(nc, p->inst_ne2[c], ns2v[c]);
+      uint8_t *blk = p->h_arena.data() + p->ro_off[c];
+      int32_t *cptr = (int32_t *)(blk + R.cptr);
+      int32_t *sp = (int32_t *)(blk + R.sptr);
+      uint16_t *cn = (uint16_t *)(blk + R.cnbr);
+      uint16_t *sn = (uint16_t *)(blk + R.snbr);
+      int ci = 0, si = 0;
+      for (int t = a; t < b; ++t) {
+        const int s = p->comp_seg[t];
+        cptr[t - a] = ci;
+        sp[t - a] = si;
+        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i)
+          if (p->comp_of[p->cadj[i]] == c) cn[ci++] = (uint16_t)local_of[p->cadj[i]];
+        for (int i = sptr[s]; i < sptr[s + 1]; ++i)
+          if (p->comp_of[sadj[i]] == c) sn[si++] = (uint16_t)local_of[sadj[i]];
+      }
+      cptr[nc] = ci;
+      sp[nc] = si;
+    }
+    // largest first (ties: lower instance id first)
+    p->h_order.resize((size_t)C);
+    std::iota(p->h_order.begin(), p->h_order.end(), 0);
+    std::stable_sort(p->h_order.begin(), p->h_order.end(), [&](int x, int y) {
+      const int sx = p->comp_ptr[x + 1] - p->comp_ptr[x], sy = p->comp_ptr[y + 1] - p->comp_ptr[y];
+      if (sx != sy) return sx > sy;
+      return p->inst_ne2[x] > p->inst_ne2[y];
+    });
+
+    for (int c = 0; c < C; ++c) {
+      InstDesc &d = p->h_desc[c];
+      std::memset(&d, 0, sizeof(d));
+      const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
+      d.n = nc;
+      d.W = mpld::words_for(nc, kp);
+      d.ne2 = p->inst_ne2[c];
+      d.ns2 = ns2v[c];
+      d.ro_bytes = (int32_t)mpld::ro_layout(nc, d.ne2, d.ns2).bytes;
+      d.state_bytes = (int32_t)mpld::state_layout(nc, d.W, d.ne2, kp).bytes;
+      d.k = k;
+      d.cost_conflict = (int32_t)p->Cc;
+      d.cost_stitch = (int32_t)p->Cs;
+    }
+    if (p->flags & MPLD_HOST_ONLY) {
+      *out = p;
+      return MPLD_OK;
+    }
+    // ---- device memory: one allocation, 256-byte aligned sections
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    p->mask_bytes = (size_t)std::max<int64_t>(p->instance_segments, 1);
+    const size_t o_arena = 0;
+    const size_t o_scratch = al(o_arena + std::max<size_t>(p->arena_bytes, 16));
+    const size_t o_desc = al(o_scratch + std::max<size_t>(p->scratch_bytes, 16));
+    const size_t o_order = al(o_desc + sizeof(InstDesc) * (size_t)std::max(C, 1));
+    const size_t o_res = al(o_order + sizeof(int32_t) * (size_t)std::max(C, 1));
+    const size_t o_masks = al(o_res + sizeof(InstResult) * (size_t)std::max(C, 1));
+    const size_t o_queue = al(o_masks + p->mask_bytes);
+    const size_t total = al(o_queue + 256);
+    const cudaError_t me = cudaMalloc((void **)&p->d_base, total);
+    if (me != cudaSuccess) {
+      cudaGetLastError();
+      delete p;
+      return me == cudaErrorMemoryAllocation ? MPLD_E_OOM : MPLD_E_CUDA;
+    }
+    p->d_bytes = total;
+    p->d_arena = p->d_base + o_arena;
+    p->d_scratch = p->d_base + o_scratch;
+    p->d_desc = (InstDesc *)(p->d_base + o_desc);
+    p->d_order = (int32_t *)(p->d_base + o_order);
+    p->d_res = (InstResult *)(p->d_base + o_res);
+    p->d_masks = (int8_t *)(p->d_base + o_masks);
+    p->d_queue = (uint32_t *)(p->d_base + o_queue);
+    p->d_err = (int32_t *)(p->d_base + o_queue + 64);
+    if (cudaMallocHost((void **)&p->h_res, sizeof(InstResult) * (size_t)std::max(C, 1)) != cudaSuccess ||
+        cudaMallocHost((void **)&p->h_masks, p->mask_bytes) != cudaSuccess ||
+        cudaMallocHost((void **)&p->h_err, 64) != cudaSuccess) {
+      cudaGetLastError();
+      mpld_free(p);
+      return MPLD_E_OOM;
+    }
+    for (int c = 0; c < C; ++c) {
+      InstDesc &d = p->h_desc[c];
+      d.ro = p->d_arena + p->ro_off[c];
+      d.scratch = p->d_scratch + scratch_off[c];
+      d.mask = p->d_masks + mask_off[c];
+      d.res = p->d_res + c;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = MPLD_OK;
+    if (p->arena_bytes)
+      rc |= cuda_ok(cudaMemcpyAsync(p->d_arena, p->h_arena.data(), p->arena_bytes,
+                                    cudaMemcpyHostToDevice, st));
+    if (C) {
+      rc |= cuda_ok(cudaMemcpyAsync(p->d_desc, p->h_desc.data(), sizeof(InstDesc) * (size_t)C,
+                                    cudaMemcpyHostToDevice, st));
+      rc |= cuda_ok(cudaMemcpyAsync(p->d_order, p->h_order.data(), sizeof(int32_t) * (size_t)C,
+                                    cudaMemcpyHostToDevice, st));
+    }
+    rc |= cuda_ok(cudaMemsetAsync(p->d_queue, 0, 256, st));
+    rc |= cuda_ok(cudaStreamSynchronize(st));
+    if (rc != MPLD_OK) {
+      mpld_free(p);
+      return MPLD_E_CUDA;
+    }
+  } catch (const std::bad_alloc &) {
+    delete p;
+    return MPLD_E_OOM;
+  }
+  *out = p;
+  return MPLD_OK;
+}
+
+extern "C" void mpld_free(mpld_problem *p) {
+  if (!p) return;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->d_base) cudaFree(p->d_base);
+  if (p->h_res) cudaFreeHost(p->h_res);
+  if (p->h_masks) cudaFreeHost(p->h_masks);
+  if (p->h_err) cudaFreeHost(p->h_err);
+  delete p;
+}
+
+// ================================================================= launch
+
+namespace {
+
+int64_t time_limit_ns(const mpld_params *prm) {
+  const int64_t ms = (prm && prm->time_limit_ms > 0) ? prm->time_limit_ms : DEFAULT_TIME_LIMIT_MS;
+  return ms * 1000000ll;
+}
+int64_t budget_of(const mpld_params *prm) { return prm ? std::max<int64_t>(prm->node_budget, 0) : 0; }
+
+uint32_t max_footprint(mpld_problem *const *ps, int n) {
+  uint32_t m = 0;
+  for (int i = 0; i < n; ++i)
+    for (uint32_t f : ps[i]->footprint) m = std::max(m, f);
+  return m;
+}
+
+// Launch shape: explicit params, else the tuned cache entry, else a default
+// that fits every instance of the batch in shared memory when possible.
+Shape pick_shape(mpld_problem *const *ps, int n, const mpld_params *prm) {
+  int nw = prm && prm->warps_per_cta > 0 ? prm->warps_per_cta : 0;
+  int slot = prm && prm->slot_bytes > 0 ? prm->slot_bytes : 0;
+  if (!nw || !slot) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(ps, n));
+    if (it != g_tune_cache.end()) {
+      if (!nw) nw = it->second.warps_per_cta;
+      if (!slot) slot = it->second.slot_bytes;
+    }
+  }
+  if (!nw) nw = 4;
+  nw = std::max(1, std::min(nw, 32));
+  const int maxslot = mpld_internal_max_slot_bytes(nw);
+  if (!slot) slot = (int)mpld::align16(std::max<uint32_t>(max_footprint(ps, n), 16));
+  slot = std::max(16, std::min(slot, maxslot)) & ~15;
+  int per_sm = mpld_internal_ctas_per_sm(nw, slot);
+  if (per_sm < 1) per_sm = 1;
+  const int sms = std::max(1, mpld_internal_num_sms());
+  return Shape{nw, slot, per_sm * sms};
+}
+
+int launch_batch(const mpld::LaunchArgs &a, const Shape &sh, cudaStream_t st, uint32_t *queue,
+                 int32_t *err) {
+  int rc = cuda_ok(cudaMemsetAsync(queue, 0, 4, st));
+  rc |= cuda_ok(cudaMemsetAsync(err, 0, 4, st));
+  if (rc) return MPLD_E_CUDA;
+  if (a.n_inst == 0) return MPLD_OK;
+  const int ctas = std::min(sh.ctas, (a.n_inst + sh.nw - 1) / sh.nw);
+  return mpld_internal_launch(&a, std::max(ctas, 1), sh.nw, st);
+}
+
+bool capturable(void *stream) {
+  return stream != nullptr && stream != (void *)cudaStreamLegacy &&
+         stream != (void *)cudaStreamPerThread;
+}
+
+// Enqueue reset -> persistent search -> copy-back for one problem, as a
+// captured CUDA graph when the stream allows capture.
+int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool copy_back) {
+  cudaStream_t st = (cudaStream_t)stream;
+  mpld_problem *ps[1] = {p};
+  const Shape sh = pick_shape(ps, 1, prm);
+  mpld::LaunchArgs a;
+  a.desc = p->d_desc;
+  a.order = p->d_order;
+  a.n_inst = p->n_comp;
+  a.slot_bytes = sh.slot;
+  a.queue = p->d_queue;
+  a.err = p->d_err;
+  a.budget = budget_of(prm);
+  a.time_limit_ns = time_limit_ns(prm);
+  auto body = [&]() -> int {
+    int rc = cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
+    if (rc) return rc;
+    rc = launch_batch(a, sh, st, p->d_queue, p->d_err);
+    if (rc) return rc;
+    if (copy_back) {
+      if (p->n_comp)
+        rc |= cuda_ok(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(InstResult) * (size_t)p->n_comp,
+                                      cudaMemcpyDeviceToHost, st));
+      if (p->instance_segments)
+        rc |= cuda_ok(cudaMemcpyAsync(p->h_masks, p->d_masks, (size_t)p->instance_segments,
+                                      cudaMemcpyDeviceToHost, st));
+      rc |= cuda_ok(cudaMemcpyAsync(p->h_err, p->d_err, 4, cudaMemcpyDeviceToHost, st));
+    }
+    return rc;
+  };
+  if (!capturable(stream)) return body();
+  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns};
+  key.ctas = copy_back ? sh.ctas : -sh.ctas;  // copy-back variant is a different graph
+  if (!p->gexec || !(p->gkey == key) || p->gstream != stream) {
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return body();
+    }
+    const int rc = body();
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc != MPLD_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return MPLD_E_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&p->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { p->gexec = nullptr; cudaGetLastError(); return MPLD_E_CUDA; }
+    p->gkey = key;
+    p->gstream = stream;
+  }
+  return cuda_ok(cudaGraphLaunch(p->gexec, st));
+}
+
+// Host side after the results are in pinned memory: scatter, recover, count.
+int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
+  const int C = p->n_comp;
+  p->r_nodes.resize((size_t)C);
+  p->r_cost.resize((size_t)C);
+  p->r_status.resize((size_t)C);
+  int status = MPLD_OK, nbud = 0;
+  int64_t nodes = 0, csum = 0, work = 0;
+  for (int c = 0; c < C; ++c) {
+    const InstResult &r = p->h_res[c];
+    p->r_nodes[c] = r.nodes;
+    p->r_cost[c] = r.cost;
+    p->r_status[c] = r.status;
+    if (r.status < 0 || r.status > MPLD_TIMEOUT) return MPLD_E_STATE;
+    if (r.status != MPLD_OK) { status = MPLD_BUDGET; ++nbud; }
+    nodes += r.nodes;
+    csum += r.cost;
+    work += r.work;
+  }
+  p->have_results = true;
+  std::vector<int8_t> m((size_t)p->n_seg, (int8_t)-1);
+  for (int c = 0; c < C; ++c)
+    for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) m[p->comp_seg[t]] = p->h_masks[t];
+  // recovery: reverse removal order, lowest mask unused by coloured neighbours
+  for (auto it = p->removed_order.rbegin(); it != p->removed_order.rend(); ++it) {
+    const int u = *it;
+    unsigned used = 0;
+    for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) {
+      const int s = p->useg[t];
+      for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
+        const int x = m[p->cadj[i]];
+        if (x >= 0) used |= 1u << x;
+      }
+    }
+    int c = 0;
+    while (c < p->k && ((used >> c) & 1u)) ++c;
+    if (c == p->k) return MPLD_E_STATE;
+    for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) m[p->useg[t]] = (int8_t)c;
+  }
+  int64_t nconf = 0, nst = 0;
+  for (size_t e = 0; e < p->cu.size(); ++e) nconf += m[p->cu[e]] == m[p->cv[e]];
+  for (size_t e = 0; e < p->su.size(); ++e) nst += m[p->su[e]] != m[p->sv[e]];
+  const int64_t cost = p->Cc * nconf + p->Cs * nst;
+  if (cost != csum) return MPLD_E_STATE;  // removed units must cost nothing
+  if (mask_out && p->n_seg) std::memcpy(mask_out, m.data(), (size_t)p->n_seg);
+  if (res) {
+    res->status = status;
+    res->n_components = C;
+    res->n_conflicts = nconf;
+    res->n_stitches = nst;
+    res->cost = cost;
+    res->nodes = nodes;
+    res->n_removed_segments = p->n_removed_segments;
+    res->max_component = p->max_component;
+    res->n_budget_components = nbud;
+    res->work = work;
+  }
+  if (*p->h_err) return *p->h_err;
+  return status;
+}
+
+}  // namespace
+
+extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, void *stream) {
+  if (!p) return MPLD_E_INVALID;
+  if (!p->d_base) return MPLD_E_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
+  rc |= cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
+  const int maxslot = mpld_internal_max_slot_bytes(1);
+  for (int c = 0; c < p->n_comp && rc == MPLD_OK; ++c) {
+    mpld::LaunchArgs a;
+    a.desc = p->d_desc + c;
+    a.order = nullptr;
+    a.n_inst = 1;
+    const int fp = (int)mpld::align16(p->footprint[c]);
+    a.slot_bytes = fp <= maxslot ? fp : 0;  // too large: state in global memory
+    a.queue = nullptr;
+    a.err = p->d_err;
+    a.budget = budget_of(prm);
+    a.time_limit_ns = time_limit_ns(prm);
+    rc = mpld_internal_launch(&a, 1, 1, st);
+  }
+  p->searched = rc == MPLD_OK;
+  p->results_copied = false;
+  return rc;
+}
+
+extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const mpld_params *prm,
+                                       void *stream) {
+  if (!ps || n < 1) return MPLD_E_INVALID;
+  for (int i = 0; i < n; ++i) {
+    if (!ps[i]) return MPLD_E_INVALID;
+    if (!ps[i]->d_base) return MPLD_E_STATE;
+  }
+  if (n == 1) {
+    const int rc = enqueue_single(ps[0], prm, stream, false);
+    ps[0]->searched = rc == MPLD_OK;
+    ps[0]->results_copied = false;
+    return rc;
+  }
+  // several problems: one launch over the concatenated instance lists
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<InstDesc> desc;
+  std::vector<int32_t> sizes;
+  for (int i = 0; i < n; ++i) {
+    desc.insert(desc.end(), ps[i]->h_desc.begin(), ps[i]->h_desc.end());
+    for (int c = 0; c < ps[i]->n_comp; ++c) sizes.push_back(ps[i]->h_desc[c].n);
+  }
+  const int total = (int)desc.size();
+  std::vector<int32_t> order((size_t)total);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sizes[x] > sizes[y]; });
+  const Shape sh = pick_shape(ps, n, prm);
+  void *buf = nullptr;
+  const size_t dbytes = sizeof(InstDesc) * (size_t)std::max(total, 1);
+  const size_t bytes = dbytes + sizeof(int32_t) * (size_t)std::max(total, 1) + 256;
+  if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess) { cudaGetLastError(); return MPLD_E_OOM; }
+  uint8_t *b = (uint8_t *)buf;
+  int rc = MPLD_OK;
+  if (total) {
+    rc |= cuda_ok(cudaMemcpyAsync(b, desc.data(), sizeof(InstDesc) * (size_t)total,
+                                  cudaMemcpyHostToDevice, st));
+    rc |= cuda_ok(cudaMemcpyAsync(b + dbytes, order.data(), sizeof(int32_t) * (size_t)total,
+                                  cudaMemcpyHostToDevice, st));
+  }
+  uint32_t *queue = (uint32_t *)(b + dbytes + sizeof(int32_t) * (size_t)std::max(total, 1));
+  mpld::LaunchArgs a;
+  a.desc = (const InstDesc *)b;
+  a.order = (const int32_t *)(b + dbytes);
+  a.n_inst = total;
+  a.slot_bytes = sh.slot;
+  a.queue = queue;
+  a.err = ps[0]->d_err;
+  a.budget = budget_of(prm);
+  a.time_limit_ns = time_limit_ns(prm);
+  for (int i = 0; i < n; ++i) {
+    if (i) rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_err, 0, 4, st));
+    rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_res, 0xFF,
+                                  sizeof(InstResult) * (size_t)std::max(ps[i]->n_comp, 1), st));
+  }
+  if (!rc) rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
+  rc |= cuda_ok(cudaFreeAsync(buf, st));
+  for (int i = 0; i < n; ++i) {
+    ps[i]->searched = rc == MPLD_OK;
+    ps[i]->results_copied = false;
+  }
+  return rc ? MPLD_E_CUDA : MPLD_OK;
+}
+
+extern "C" int mpld_fetch(mpld_problem *p, int8_t *mask_out, mpld_result *res, void *stream) {
+  if (!p) return MPLD_E_INVALID;
+  if (!p->searched) return MPLD_E_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = MPLD_OK;
+  if (!p->results_copied) {
+    if (p->n_comp)
+      rc |= cuda_ok(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(InstResult) * (size_t)p->n_comp,
+                                    cudaMemcpyDeviceToHost, st));
+    if (p->instance_segments)
+      rc |= cuda_ok(cudaMemcpyAsync(p->h_masks, p->d_masks, (size_t)p->instance_segments,
+                                    cudaMemcpyDeviceToHost, st));
+    rc |= cuda_ok(cudaMemcpyAsync(p->h_err, p->d_err, 4, cudaMemcpyDeviceToHost, st));
+  }
+  rc |= cuda_ok(cudaStreamSynchronize(st));
+  if (rc) return MPLD_E_CUDA;
+  p->searched = false;
+  return finish(p, mask_out, res);
+}
+
+extern "C" int mpld_solve(mpld_problem *p, const mpld_params *prm, int8_t *mask_out,
+                          mpld_result *res, void *stream) {
+  const int rc = mpld_search_plain_async(p, prm, stream);
+  if (rc < 0) return rc;
+  return mpld_fetch(p, mask_out, res, stream);
+}
+
+extern "C" int mpld_solve_batch(mpld_problem *const *ps, int32_t n, const mpld_params *prm,
+                                int8_t *const *masks_out, mpld_result *results, void *stream) {
+  if (!ps || n < 1) return MPLD_E_INVALID;
+  int rc;
+  if (n == 1) {
+    if (!ps[0]) return MPLD_E_INVALID;
+    if (!ps[0]->d_base) return MPLD_E_STATE;
+    rc = enqueue_single(ps[0], prm, stream, true);
+    if (rc) return rc;
+    ps[0]->searched = true;
+    ps[0]->results_copied = true;
+  } else {
+    rc = mpld_search_batch_async(ps, n, prm, stream);
+    if (rc) return rc;
+  }
+  int worst = MPLD_OK;
+  for (int i = 0; i < n; ++i) {
+    const int r = mpld_fetch(ps[i], masks_out ? masks_out[i] : nullptr,
+                             results ? &results[i] : nullptr, stream);
+    if (r < 0) return r;
+    worst = std::max(worst, r);
+  }
+  return worst;
+}
+
+extern "C" const char *mpld_status_string(int code) {
+  switch (code) {
+    case MPLD_OK: return "ok";
+    case MPLD_BUDGET: return "node budget or time limit reached; best assignment returned";
+    case MPLD_TIMEOUT: return "time limit reached; best assignment returned";
+    case MPLD_E_INVALID: return "invalid input";
+    case MPLD_E_OOM: return "out of memory";
+    case MPLD_E_CUDA: return "CUDA error";
+    case MPLD_E_TIMEOUT: return "device-side wait timed out";
+    case MPLD_E_TOO_LARGE: return "search instance too large";
+    case MPLD_E_STATE: return "call out of order or inconsistent state";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int mpld_problem_info(const mpld_problem *p, mpld_info *info) {
+  if (!p || !info) return MPLD_E_INVALID;
+  info->n_seg = p->n_seg;
+  info->k = p->k;
+  info->n_components = p->n_comp;
+  info->max_component = p->max_component;
+  info->n_removed_segments = p->n_removed_segments;
+  info->arena_bytes = (int64_t)p->arena_bytes;
+  info->state_bytes = (int64_t)p->scratch_bytes;
+  info->instance_segments = p->instance_segments;
+  return MPLD_OK;
+}
+
+extern "C" int mpld_component_results(const mpld_problem *p, int64_t *nodes, int64_t *cost,
+                                      int32_t *status, int32_t *comp_of) {
+  if (!p) return MPLD_E_INVALID;
+  if (comp_of && p->n_seg) std::memcpy(comp_of, p->comp_of.data(), sizeof(int32_t) * (size_t)p->n_seg);
+  if (!nodes && !cost && !status) return MPLD_OK;
+  if (!p->have_results) return MPLD_E_STATE;
+  const size_t C = (size_t)p->n_comp;
+  if (nodes && C) std::memcpy(nodes, p->r_nodes.data(), sizeof(int64_t) * C);
+  if (cost && C) std::memcpy(cost, p->r_cost.data(), sizeof(int64_t) * C);
+  if (status && C) std::memcpy(status, p->r_status.data(), sizeof(int32_t) * C);
+  return MPLD_OK;
+}
+
+extern "C" int mpld_export_matrix(const mpld_problem *p, int32_t comp, uint8_t *dense,
+                                  int32_t *dims) {
+  if (!p || comp < 0 || comp >= p->n_comp) return MPLD_E_INVALID;
+  const InstDesc &d = p->h_desc[comp];
+  const int n = d.n, k = p->k, ne = d.ne2 / 2;
+  if (dims) { dims[0] = n; dims[1] = k; dims[2] = ne; }
+  if (!dense) return MPLD_OK;
+  // decode the packed read-only block as stored in the arena
+  const mpld::RoLayout R = mpld::ro_layout(n, d.ne2, d.ns2);
+  const uint8_t *blk = p->h_arena.data() + p->ro_off[comp];
+  const int32_t *cptr = (const int32_t *)(blk + R.cptr);
+  const uint16_t *cn = (const uint16_t *)(blk + R.cnbr);
+  const size_t ncol = (size_t)(1 + n + k * ne);
+  std::memset(dense, 0, (size_t)n * (size_t)k * ncol);
+  // conflict edges numbered in ascending (min, max) local id
+  std::vector<int32_t> eid((size_t)std::max(d.ne2, 1), -1);
+  int e = 0;
+  for (int v = 0; v < n; ++v)
+    for (int i = cptr[v]; i < cptr[v + 1]; ++i)
+      if (cn[i] > v) eid[i] = e++;
+  for (int v = 0; v < n; ++v)
+    for (int i = cptr[v]; i < cptr[v + 1]; ++i)
+      if (cn[i] < v) {
+        const int u = cn[i];
+        for (int j = cptr[u]; j < cptr[u + 1]; ++j)
+          if (cn[j] == v) { eid[i] = eid[j]; break; }
+      }
+  for (int v = 0; v < n; ++v)
+    for (int c = 0; c < k; ++c) {
+      uint8_t *row = dense + ((size_t)v * k + c) * ncol;
+      row[1 + v] = 1;
+      for (int i = cptr[v]; i < cptr[v + 1]; ++i) row[1 + n + (size_t)eid[i] * k + c] = 1;
+    }
+  return MPLD_OK;
+}
+
+extern "C" int mpld_autotune(mpld_problem *const *ps, int32_t n, const mpld_params *prm,
+                             void *stream, mpld_tune *best_out) {
+  if (!ps || n < 1) return MPLD_E_INVALID;
+  for (int i = 0; i < n; ++i) {
+    if (!ps[i]) return MPLD_E_INVALID;
+    if (!ps[i]->d_base) return MPLD_E_STATE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // candidate shapes: warps per CTA x slot size (fit-all, or the 90th
+  // percentile footprint so that the largest instances spill)
+  std::vector<uint32_t> fp;
+  for (int i = 0; i < n; ++i) fp.insert(fp.end(), ps[i]->footprint.begin(), ps[i]->footprint.end());
+  if (fp.empty()) return MPLD_OK;
+  std::sort(fp.begin(), fp.end());
+  const uint32_t fmax = fp.back(), f90 = fp[(fp.size() * 9) / 10];
+  const int nws[] = {1, 2, 4, 8, 16};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MPLD_E_CUDA;
+  mpld_tune best{};
+  best.ms = 1e30f;
+  int rc = MPLD_OK;
+  for (int nw : nws) {
+    const int maxslot = mpld_internal_max_slot_bytes(nw);
+    std::vector<int> slots = {(int)mpld::align16(fmax), (int)mpld::align16(f90)};
+    for (size_t si = 0; si < slots.size(); ++si) {
+      int slot = std::min(std::max(slots[si], 16), maxslot) & ~15;
+      if (si == 1 && slot == (std::min(std::max(slots[0], 16), maxslot) & ~15)) continue;
+      mpld_params q = prm ? *prm : mpld_params{};
+      q.warps_per_cta = nw;
+      q.slot_bytes = slot;
+      rc = mpld_search_batch_async(ps, n, &q, stream);  // warm-up (captures the graph)
+      if (rc) break;
+      cudaEventRecord(e0, st);
+      rc = mpld_search_batch_async(ps, n, &q, stream);
+      cudaEventRecord(e1, st);
+      if (rc) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = MPLD_E_CUDA; break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      int spilled = 0;
+      for (uint32_t f : fp) spilled += (int)mpld::align16(f) > slot;
+      if (ms < best.ms) {
+        best.ms = ms;
+        best.warps_per_cta = nw;
+        best.slot_bytes = slot;
+        best.ctas_per_sm = mpld_internal_ctas_per_sm(nw, slot);
+        best.n_instances_spilled = spilled;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < n; ++i) ps[i]->searched = false;
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(ps, n)] = best;
+  }
+  if (best_out) *best_out = best;
+  return MPLD_OK;
+}

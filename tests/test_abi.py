@@ -1,0 +1,138 @@
+"""libmpld without a GPU: exported symbols and the host half of the flow.
+
+The host-only build (MPLD_HOST_ONLY) runs the simplification, the sub-graph
+split and the EC packing without touching the device, so they can be
+checked here against the oracle's independent implementation.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_14335_gb300 import mpld, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mpld.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpld_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["mpld_build_matrix", "mpld_solve", "mpld_solve_batch", "mpld_free"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = mpld.library()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_has_the_same_names():
+    for name in declared_functions():
+        assert callable(getattr(mpld, name)), name
+
+
+def test_status_strings():
+    assert mpld.mpld_status_string(0) == "ok"
+    assert "too large" in mpld.mpld_status_string(mpld.MPLD_E_TOO_LARGE)
+
+
+def host_only(layout, flags=0):
+    return mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags | mpld.MPLD_HOST_ONLY))
+
+
+def edges(L):
+    return list(zip(L.conf_u.tolist(), L.conf_v.tolist())), list(zip(L.st_u.tolist(), L.st_v.tolist()))
+
+
+@pytest.mark.parametrize("k,deg,p,seed", [(3, 3.0, 0.2, 1), (4, 5.0, 0.3, 2), (3, 4.5, 0.25, 3),
+                                          (5, 6.0, 0.1, 4), (2, 2.5, 0.2, 5)])
+def test_host_split_matches_oracle(k, deg, p, seed):
+    L = synth.unit_disk_layout(4000, k, seed=seed, mean_deg=deg, p_stitch=p)
+    prob = host_only(L)
+    info = mpld.mpld_problem_info(prob)
+    _, _, _, comp_of = mpld.mpld_component_results(prob, results=False)
+    ref = oracle.decompose(L, budget=50, nthreads=4)
+    assert info.n_components == ref.n_components
+    assert info.n_removed_segments == ref.n_removed_segments
+    assert info.max_component == ref.max_component
+    assert np.array_equal(comp_of, ref.comp_of)
+
+
+def test_host_single_instance_mode():
+    L, mode = synth.workload("k3_n400_p025_plain")
+    prob = host_only(L, mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE)
+    info = mpld.mpld_problem_info(prob)
+    assert info.n_components == 1 and info.max_component == L.n_seg and info.n_removed_segments == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_packed_matrix_is_the_ec_matrix(seed):
+    # the packed block-sparse columns decode to exactly the oracle's DLX matrix
+    L = synth.random_graph(9, 3 + seed % 3, seed=60 + seed, p_edge=0.45, n_stitch=2)
+    prob = host_only(L, mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE)
+    conf, _ = edges(L)
+    M = mpld.mpld_export_matrix(prob, 0)
+    R = oracle.export_matrix(L.n_seg, L.k, conf)
+    assert np.array_equal(M, R)
+
+
+def test_packed_matrices_of_components():
+    L = synth.unit_disk_layout(3000, 3, seed=17, mean_deg=3.0, p_stitch=0.2)
+    prob = host_only(L)
+    _, _, _, comp_of = mpld.mpld_component_results(prob, results=False)
+    conf, _ = edges(L)
+    for c in range(0, int(comp_of.max()) + 1, 7):
+        segs = np.nonzero(comp_of == c)[0]
+        loc = {int(s): i for i, s in enumerate(segs)}
+        cc = [(loc[a], loc[b]) for a, b in conf if a in loc and b in loc]
+        assert np.array_equal(mpld.mpld_export_matrix(prob, c), oracle.export_matrix(len(segs), 3, cc))
+
+
+def test_invalid_inputs_rejected():
+    bad = [synth.graph_from_edges(3, 3, [(0, 1)]), synth.graph_from_edges(3, 3, [(0, 1)])]
+    bad[0].conf_v = np.array([0], dtype=np.int32)          # self-loop
+    bad[1].conf_v = np.array([7], dtype=np.int32)          # out of range
+    for L in bad:
+        with pytest.raises(mpld.MpldError) as e:
+            host_only(L)
+        assert e.value.code == mpld.MPLD_E_INVALID
+    for k in (1, 9):
+        with pytest.raises(mpld.MpldError):
+            host_only(synth.graph_from_edges(3, k, [(0, 1)]))
+    L = synth.graph_from_edges(3, 3, [(0, 1)], cost_conflict=20000)
+    with pytest.raises(mpld.MpldError):
+        host_only(L)
+    L = synth.graph_from_edges(3, 3, [(0, 1)], polygon_of=[0, 5, 1])
+    with pytest.raises(mpld.MpldError):
+        host_only(L)
+
+
+def test_too_large_instance_rejected():
+    n = 70000
+    L = synth.graph_from_edges(n, 3, [(i, i + 1) for i in range(n - 1)])
+    with pytest.raises(mpld.MpldError) as e:
+        host_only(L, mpld.MPLD_NO_SIMPLIFY)
+    assert e.value.code == mpld.MPLD_E_TOO_LARGE
+
+
+def test_solve_on_host_only_handle_is_a_state_error():
+    prob = host_only(synth.graph_from_edges(3, 3, [(0, 1), (1, 2), (0, 2)]))
+    with pytest.raises(mpld.MpldError) as e:
+        mpld.mpld_solve(prob)
+    assert e.value.code == mpld.MPLD_E_STATE
+    with pytest.raises(mpld.MpldError) as e:
+        mpld.mpld_fetch(prob)
+    assert e.value.code == mpld.MPLD_E_STATE
+
+
+def test_empty_layout():
+    prob = host_only(synth.graph_from_edges(0, 3, []))
+    assert mpld.mpld_problem_info(prob).n_components == 0

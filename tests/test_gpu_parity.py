@@ -1,0 +1,252 @@
+"""CUDA path vs the CPU oracle, element by element (integer work: bit-exact).
+
+Every comparison covers the per-segment masks, the integer cost, the
+conflict and stitch counts, the per-instance search node counts and the
+status.  The oracle and the library get the same seeded inputs and the same
+node budget; their search order is the same by construction (first
+minimum-cost leaf of the canonical depth-first order), so the node counts
+match too.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_14335_gb300 import mpld, synth
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+SINGLE = mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def stream(torch_cuda):
+    return torch_cuda.cuda.Stream()
+
+
+def edges(L):
+    return list(zip(L.conf_u.tolist(), L.conf_v.tolist())), list(zip(L.st_u.tolist(), L.st_v.tolist()))
+
+
+def gpu_run(L, flags=0, budget=0, path="batch", stream=0, warps=0, slot=0, time_limit_ms=0):
+    prob = mpld.mpld_build_matrix(L, mpld.make_params(flags=flags), stream)
+    prm = mpld.make_params(node_budget=budget, warps_per_cta=warps, slot_bytes=slot,
+                           time_limit_ms=time_limit_ms)
+    if path == "plain":
+        rc, mask, res = mpld.mpld_solve(prob, prm, stream)
+    else:
+        rc, masks, ress = mpld.mpld_solve_batch([prob], prm, stream)
+        mask, res = masks[0], ress[0]
+    nodes, cost, status, comp_of = mpld.mpld_component_results(prob)
+    prob.close()
+    return dict(rc=rc, mask=mask, res=res, nodes=nodes, cost=cost, status=status, comp_of=comp_of)
+
+
+def assert_same(g, ref, L):
+    assert np.array_equal(g["mask"], ref.mask), "masks differ"
+    assert g["res"].cost == ref.cost
+    assert g["res"].n_conflicts == ref.n_conflicts and g["res"].n_stitches == ref.n_stitches
+    assert g["res"].nodes == ref.nodes
+    assert g["res"].n_components == ref.n_components
+    assert g["res"].n_removed_segments == ref.n_removed_segments
+    assert np.array_equal(g["comp_of"], ref.comp_of)
+    assert np.array_equal(g["nodes"], ref.comp_nodes)
+    assert np.array_equal(g["cost"], ref.comp_cost)
+    st = np.where(g["status"] == mpld.MPLD_OK, oracle.OK, oracle.BUDGET)
+    assert np.array_equal(st, ref.comp_status)
+    assert (g["rc"] == mpld.MPLD_BUDGET) == (ref.status == oracle.BUDGET)
+    conf, stt = edges(L)
+    x = g["mask"]
+    assert np.all((x >= 0) & (x < L.k))
+    assert g["res"].cost == L.cost_conflict * sum(x[a] == x[b] for a, b in conf) + \
+        L.cost_stitch * sum(x[a] != x[b] for a, b in stt)
+
+
+# ---------------------------------------------------------------- small graphs
+
+def small_cases():
+    out = []
+    for s in range(48):
+        d = synth.uniform(4242, np.arange(3 * s, 3 * s + 3, dtype=np.uint64))
+        k = 2 + int(d[0] * 7)            # 2..8: both field widths
+        n = 3 + int(d[1] * 16)
+        out.append((n, k, 7000 + s, 0.25 + 0.5 * d[2]))
+    return out
+
+
+@pytest.mark.parametrize("n,k,seed,p", small_cases())
+def test_small_single_instance(n, k, seed, p, stream):
+    L = synth.random_graph(n, k, seed=seed, p_edge=p, n_stitch=n // 4, identity_polygons=False)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=200000)
+    for path in ("batch", "plain"):
+        g = gpu_run(L, flags=SINGLE, budget=200000, path=path, stream=stream.cuda_stream)
+        assert_same(g, ref, L)
+
+
+def test_golden_cases(stream):
+    import json
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    for fn in ("hand_traces.json", "fig1_four_clique.json"):
+        for c in json.load(open(os.path.join(here, fn)))["cases"]:
+            L = synth.graph_from_edges(c["n"], c["k"], c["conf"], c["stitch"])
+            g = gpu_run(L, flags=SINGLE, stream=stream.cuda_stream)
+            want = c.get("cost", c.get("min_cost"))
+            assert g["res"].cost == want
+            if "x" in c:
+                assert g["mask"].tolist() == c["x"] and g["res"].nodes == c["nodes"]
+
+
+@pytest.mark.parametrize("budget", [1, 40, 333, 5000])
+def test_budget_parity(budget, stream):
+    L = synth.unit_disk_layout(40, 3, seed=91, mean_deg=5.0, p_stitch=0.25)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=budget)
+    g = gpu_run(L, flags=SINGLE, budget=budget, stream=stream.cuda_stream)
+    assert_same(g, ref, L)
+
+
+# ---------------------------------------------------------------- workloads
+
+def test_workload_k3_n24_plain_exact(stream):
+    L, mode = synth.workload("k3_n24_plain")
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE)
+    for path in ("batch", "plain"):
+        g = gpu_run(L, flags=SINGLE, path=path, stream=stream.cuda_stream)
+        assert_same(g, ref, L)
+        assert g["rc"] == mpld.MPLD_OK
+
+
+def test_workload_k3_n400_budgeted(stream):
+    L, mode = synth.workload("k3_n400_p025_plain")
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=300000)
+    g = gpu_run(L, flags=SINGLE, budget=300000, stream=stream.cuda_stream)
+    assert_same(g, ref, L)
+
+
+@pytest.mark.parametrize("name", ["k3_n200k_p02_batched", "k4_n100k_p03_batched"])
+def test_batched_workloads_full_size(name, stream):
+    L, mode = synth.workload(name)
+    ref = oracle.decompose(L, budget=3000, nthreads=NTHREADS)
+    g = gpu_run(L, budget=3000, stream=stream.cuda_stream)
+    assert_same(g, ref, L)
+
+
+@pytest.mark.parametrize("name", ["k3_n200k_p02_batched", "k4_n100k_p03_batched"])
+def test_batched_workloads_bench_budget_sampled(name, stream):
+    # the benchmark's budget: whole-layout invariants plus a sample of
+    # instances solved one by one by the oracle
+    budget = 1 << 16
+    L, mode = synth.workload(name)
+    g = gpu_run(L, budget=budget, stream=stream.cuda_stream)
+    conf, st = edges(L)
+    comp_of = g["comp_of"]
+    assert g["res"].cost == int(g["cost"].sum())
+    C = len(g["nodes"])
+    order = np.argsort(-np.bincount(comp_of[comp_of >= 0], minlength=C), kind="stable")
+    sample = list(order[:6]) + list(range(0, C, max(1, C // 40)))
+    cu, cv = L.conf_u, L.conf_v
+    su, sv = L.st_u, L.st_v
+    for c in sorted(set(int(s) for s in sample)):
+        segs = np.nonzero(comp_of == c)[0]
+        loc = np.full(L.n_seg, -1, dtype=np.int64)
+        loc[segs] = np.arange(len(segs))
+        mc = (loc[cu] >= 0) & (loc[cv] >= 0)
+        ms = (loc[su] >= 0) & (loc[sv] >= 0)
+        r = oracle.solve_instance(len(segs), L.k, np.stack([loc[cu[mc]], loc[cv[mc]]], 1),
+                                  np.stack([loc[su[ms]], loc[sv[ms]]], 1), budget=budget)
+        assert r.cost == g["cost"][c] and r.nodes == g["nodes"][c]
+        assert np.array_equal(r.x, g["mask"][segs])
+
+
+# ---------------------------------------------------------------- launch forms
+
+def test_results_independent_of_launch_shape(stream):
+    L = synth.unit_disk_layout(30000, 3, seed=12, mean_deg=3.2, p_stitch=0.2)
+    base = gpu_run(L, budget=4000, stream=stream.cuda_stream)
+    for warps, slot in [(1, 0), (2, 0), (8, 0), (16, 0), (4, 1024), (4, 16)]:
+        g = gpu_run(L, budget=4000, stream=stream.cuda_stream, warps=warps, slot=slot)
+        assert np.array_equal(g["mask"], base["mask"]) and np.array_equal(g["nodes"], base["nodes"])
+
+
+def test_plain_equals_batched_and_default_stream():
+    L = synth.unit_disk_layout(6000, 4, seed=13, mean_deg=5.0, p_stitch=0.3)
+    a = gpu_run(L, budget=2000, path="plain", stream=0)
+    b = gpu_run(L, budget=2000, path="batch", stream=0)
+    assert np.array_equal(a["mask"], b["mask"]) and np.array_equal(a["nodes"], b["nodes"])
+
+
+def test_multi_problem_batch(stream):
+    Ls = [synth.unit_disk_layout(3000 + 500 * i, 3 + (i % 2), seed=30 + i, mean_deg=4.0, p_stitch=0.2)
+          for i in range(4)]
+    probs = [mpld.mpld_build_matrix(L, None, stream.cuda_stream) for L in Ls]
+    prm = mpld.make_params(node_budget=3000)
+    rc, masks, ress = mpld.mpld_solve_batch(probs, prm, stream.cuda_stream)
+    for L, m, r in zip(Ls, masks, ress):
+        ref = oracle.decompose(L, budget=3000, nthreads=NTHREADS)
+        assert np.array_equal(m, ref.mask) and r.nodes == ref.nodes and r.cost == ref.cost
+    for p in probs:
+        p.close()
+
+
+def test_repeated_calls_and_graph_replay(stream):
+    L = synth.unit_disk_layout(8000, 3, seed=14, mean_deg=3.0, p_stitch=0.2)
+    prob = mpld.mpld_build_matrix(L, None, stream.cuda_stream)
+    prm = mpld.make_params(node_budget=1000)
+    outs = [mpld.mpld_solve_batch([prob], prm, stream.cuda_stream) for _ in range(3)]
+    for rc, m, r in outs[1:]:
+        assert np.array_equal(m[0], outs[0][1][0]) and r[0].nodes == outs[0][2][0].nodes
+    # device-only search + fetch gives the same
+    mpld.mpld_search_batch_async([prob], prm, stream.cuda_stream)
+    rc, m, r = mpld.mpld_fetch(prob, stream.cuda_stream)
+    assert np.array_equal(m, outs[0][1][0])
+    prob.close()
+
+
+def test_time_limit_stops_search(stream):
+    # unlimited budget, 1 ms per instance: the search must stop by itself and
+    # still return a consistent incumbent
+    L, mode = synth.workload("k3_n400_p025_plain")
+    g = gpu_run(L, flags=SINGLE, budget=0, time_limit_ms=1, stream=stream.cuda_stream)
+    assert g["rc"] == mpld.MPLD_BUDGET
+    assert g["status"][0] == mpld.MPLD_TIMEOUT
+    conf, st = edges(L)
+    x = g["mask"]
+    assert g["res"].cost == 10 * sum(x[a] == x[b] for a, b in conf) + sum(x[a] != x[b] for a, b in st)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_edge_cases(stream):
+    s = stream.cuda_stream
+    g = gpu_run(synth.graph_from_edges(0, 3, []), stream=s)
+    assert g["res"].n_components == 0 and g["res"].cost == 0
+    g = gpu_run(synth.graph_from_edges(5, 3, []), stream=s)          # all simplified away
+    assert g["res"].n_removed_segments == 5 and np.all(g["mask"] == 0)
+    g = gpu_run(synth.graph_from_edges(5, 3, []), flags=mpld.MPLD_NO_SIMPLIFY, stream=s)
+    assert g["res"].n_components == 5 and g["res"].nodes == 10
+    g = gpu_run(synth.graph_from_edges(1, 2, []), flags=SINGLE, stream=s)
+    assert g["mask"].tolist() == [0] and g["res"].nodes == 2
+    # even cycle, k = 2: bipartite, cost 0
+    L = synth.graph_from_edges(10, 2, [(i, (i + 1) % 10) for i in range(10)])
+    g = gpu_run(L, flags=SINGLE, stream=s)
+    assert g["res"].cost == 0
+    # duplicates merged
+    a = gpu_run(synth.graph_from_edges(4, 3, [(0, 1), (1, 2), (0, 2), (2, 3)]), flags=SINGLE, stream=s)
+    L = synth.graph_from_edges(4, 3, [(0, 1), (1, 2), (0, 2), (2, 3)])
+    L.conf_u = np.concatenate([L.conf_u, [1, 2]]).astype(np.int32)
+    L.conf_v = np.concatenate([L.conf_v, [0, 0]]).astype(np.int32)
+    b = gpu_run(L, flags=SINGLE, stream=s)
+    assert np.array_equal(a["mask"], b["mask"]) and a["res"].nodes == b["res"].nodes
+    # a large k=8 instance exercises several words per lane
+    L = synth.unit_disk_layout(700, 8, seed=3, mean_deg=9.0)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=20000)
+    assert_same(gpu_run(L, flags=SINGLE, budget=20000, stream=s), ref, L)
