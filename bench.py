@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="divide the workload's polygon count (same density and degree); "
+                         "for small profiling cases")
     ap.add_argument("--plain-scale", type=int, default=20,
                     help="the plain one-launch-per-instance path runs on the same workload with "
                          "polygons / plain-scale (same density and degree)")
@@ -184,7 +187,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     stream = torch.cuda.Stream()
     s = stream.cuda_stream
-    layout, mode = workload_layout(args.workload, rank)
+    layout, mode = workload_layout(args.workload, rank, scale=args.scale)
     flags = (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE) if mode == "single" else 0
     prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
     info = mpld.mpld_problem_info(prob)
@@ -237,7 +240,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "segments": layout.n_seg, "polygons": layout.n_poly,
+        "config": {"workload": args.workload + (f"/scale{args.scale}" if args.scale > 1 else ""),
+                   "segments": layout.n_seg, "polygons": layout.n_poly,
                    "k": layout.k, "node_budget": args.budget, "instances": info.n_components,
                    "max_instance": info.max_component,
                    "removed_segments": info.n_removed_segments,

@@ -324,11 +324,18 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     const int kp = mpld::kp_for(k);
     for (int c = 0; c < C; ++c) {
       int ne2 = 0, ns2 = 0;
+      int64_t max_inc = 0;
       for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
         const int s = p->comp_seg[t];
-        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) ne2 += p->comp_of[p->cadj[i]] == c;
-        for (int i = sptr[s]; i < sptr[s + 1]; ++i) ns2 += p->comp_of[sadj[i]] == c;
+        int dc = 0, ds = 0;
+        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) dc += p->comp_of[p->cadj[i]] == c;
+        for (int i = sptr[s]; i < sptr[s + 1]; ++i) ds += p->comp_of[sadj[i]] == c;
+        ne2 += dc;
+        ns2 += ds;
+        max_inc = std::max(max_inc, p->Cc * dc + p->Cs * ds);
       }
+      // the kernel orders a segment's rows by 32-bit keys (added cost << 3 | mask)
+      if (max_inc >= (int64_t)1 << 28) { delete p; return MPLD_E_TOO_LARGE; }
       const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
       const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2);
       const mpld::StateLayout L = mpld::state_layout(nc, mpld::words_for(nc, kp), ne2, kp);

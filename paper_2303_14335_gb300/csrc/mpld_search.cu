@@ -25,6 +25,12 @@
 // device work counter over a largest-first order (Sec. 2.3 / Sec. 3 run one
 // block per sub-graph; here the sub-graphs are the work queue).  The plain
 // form launches the same kernel once per instance.
+//
+// Memory spaces: an instance whose state and read-only block fit the warp's
+// slot runs entirely in shared memory (the SM = true instantiation, whose
+// pointers all derive from the shared array, so every access is a shared
+// access); a larger one keeps its state in its own global scratch region
+// (SM = false).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,6 +39,8 @@
 
 namespace mpld {
 namespace {
+
+extern __shared__ __align__(16) uint8_t g_smem[];
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int64_t INF = INT64_MAX;
@@ -73,25 +81,24 @@ __device__ __forceinline__ uint64_t fields_le(uint64_t key, uint32_t t) {
   return ~((key | F::HI) - (uint64_t)(t + 1) * F::LO) & F::HI;
 }
 
-__device__ __forceinline__ void cas_u64(uint64_t &a, uint64_t &b) {
-  const uint64_t lo = a < b ? a : b;
-  const uint64_t hi = a < b ? b : a;
+__device__ __forceinline__ void cas_u32(uint32_t &a, uint32_t &b) {
+  const uint32_t lo = min(a, b), hi = max(a, b);
   a = lo;
   b = hi;
 }
 
-// Sort keys ((inc << 8) | mask) ascending with a fixed network.
-template <int KP> __device__ __forceinline__ void sort_keys(uint64_t (&k)[KP]);
-template <> __device__ __forceinline__ void sort_keys<4>(uint64_t (&k)[4]) {
-  cas_u64(k[0], k[1]); cas_u64(k[2], k[3]); cas_u64(k[0], k[2]); cas_u64(k[1], k[3]);
-  cas_u64(k[1], k[2]);
+// Sort keys ((inc << 3) | mask) ascending with a fixed network.
+template <int KP> __device__ __forceinline__ void sort_keys(uint32_t (&k)[KP]);
+template <> __device__ __forceinline__ void sort_keys<4>(uint32_t (&k)[4]) {
+  cas_u32(k[0], k[1]); cas_u32(k[2], k[3]); cas_u32(k[0], k[2]); cas_u32(k[1], k[3]);
+  cas_u32(k[1], k[2]);
 }
-template <> __device__ __forceinline__ void sort_keys<8>(uint64_t (&k)[8]) {
-  cas_u64(k[0], k[2]); cas_u64(k[1], k[3]); cas_u64(k[4], k[6]); cas_u64(k[5], k[7]);
-  cas_u64(k[0], k[4]); cas_u64(k[1], k[5]); cas_u64(k[2], k[6]); cas_u64(k[3], k[7]);
-  cas_u64(k[0], k[1]); cas_u64(k[2], k[3]); cas_u64(k[4], k[5]); cas_u64(k[6], k[7]);
-  cas_u64(k[2], k[4]); cas_u64(k[3], k[5]); cas_u64(k[1], k[4]); cas_u64(k[3], k[6]);
-  cas_u64(k[1], k[2]); cas_u64(k[3], k[4]); cas_u64(k[5], k[6]);
+template <> __device__ __forceinline__ void sort_keys<8>(uint32_t (&k)[8]) {
+  cas_u32(k[0], k[2]); cas_u32(k[1], k[3]); cas_u32(k[4], k[6]); cas_u32(k[5], k[7]);
+  cas_u32(k[0], k[4]); cas_u32(k[1], k[5]); cas_u32(k[2], k[6]); cas_u32(k[3], k[7]);
+  cas_u32(k[0], k[1]); cas_u32(k[2], k[3]); cas_u32(k[4], k[5]); cas_u32(k[6], k[7]);
+  cas_u32(k[2], k[4]); cas_u32(k[3], k[5]); cas_u32(k[1], k[4]); cas_u32(k[3], k[6]);
+  cas_u32(k[1], k[2]); cas_u32(k[3], k[4]); cas_u32(k[5], k[6]);
 }
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -136,7 +143,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // ---- the search ----------------------------------------------------------
 
-template <int KP>
 struct State {
   uint64_t *active, *unas;
   int64_t *lv_g;
@@ -151,47 +157,55 @@ struct State {
   const uint16_t *cnbr, *snbr;
 };
 
+// 32-bit half of activeRows holding bit position p of word w.
+__device__ __forceinline__ uint32_t *half_of(uint64_t *active, int w, int p) {
+  return reinterpret_cast<uint32_t *>(active + w) + (p >> 5);
+}
+
 template <int KP>
-__device__ __forceinline__ void cover_row(const State<KP> &s, int v, int c, int lane) {
+__device__ __forceinline__ void cover_row(const State &s, int v, int c, int lane) {
   using F = Fields<KP>;
   if (lane == 0) {
-    const int wv = (v * KP) >> 6, sv = (v * KP) & 63;
-    const uint64_t old = atomicAnd((unsigned long long *)&s.active[wv], ~(F::FM << sv));
-    s.oldnib[v] = (uint8_t)((old >> sv) & F::FM);
-    s.unas[wv] &= ~(F::FM << sv);
+    const int p = v * KP;
+    const uint32_t fm = (uint32_t)F::FM << (p & 31);
+    const uint32_t old = atomicAnd(half_of(s.active, p >> 6, p & 63), ~fm);
+    s.oldnib[v] = (uint8_t)((old & fm) >> (p & 31));
+    uint32_t *uh = half_of(s.unas, p >> 6, p & 63);
+    *uh &= ~fm;
     s.x[v] = (int8_t)c;
   }
   const int ce = s.cptr[v + 1];
   for (int i = s.cptr[v] + lane; i < ce; i += 32) {
-    const int u = s.cnbr[i];
-    const uint64_t bit = 1ull << (((u * KP) & 63) + c);
-    const uint64_t old = atomicAnd((unsigned long long *)&s.active[(u * KP) >> 6], ~bit);
+    const int p = (int)s.cnbr[i] * KP + c;
+    const uint32_t bit = 1u << (p & 31);
+    const uint32_t old = atomicAnd(half_of(s.active, p >> 6, p & 63), ~bit);
     s.clrb[i] = (old & bit) ? 1 : 0;
   }
   __syncwarp();
 }
 
 template <int KP>
-__device__ __forceinline__ void uncover_row(const State<KP> &s, int v, int c, int lane) {
+__device__ __forceinline__ void uncover_row(const State &s, int v, int c, int lane) {
   using F = Fields<KP>;
   const int ce = s.cptr[v + 1];
   for (int i = s.cptr[v] + lane; i < ce; i += 32) {
     if (s.clrb[i]) {
-      const int u = s.cnbr[i];
-      atomicOr((unsigned long long *)&s.active[(u * KP) >> 6], 1ull << (((u * KP) & 63) + c));
+      const int p = (int)s.cnbr[i] * KP + c;
+      atomicOr(half_of(s.active, p >> 6, p & 63), 1u << (p & 31));
     }
   }
   if (lane == 0) {
-    const int wv = (v * KP) >> 6, sv = (v * KP) & 63;
-    atomicOr((unsigned long long *)&s.active[wv], (uint64_t)s.oldnib[v] << sv);
-    s.unas[wv] |= F::FM << sv;
+    const int p = v * KP;
+    atomicOr(half_of(s.active, p >> 6, p & 63), (uint32_t)s.oldnib[v] << (p & 31));
+    uint32_t *uh = half_of(s.unas, p >> 6, p & 63);
+    *uh |= (uint32_t)F::FM << (p & 31);
     s.x[v] = -1;
   }
   __syncwarp();
 }
 
-// Packed per-mask counts of neighbours holding each mask (8 bits per mask),
-// summed over the warp; lanes beyond the list add nothing.
+// Per-mask counts of neighbours holding each mask, summed over the warp
+// (8-bit packed lanes contributions, one reduction per 4 masks).
 template <int KP>
 __device__ __forceinline__ void count_masks(const uint16_t *nbr, int b, int e, const int8_t *x,
                                             int lane, int (&cnt)[KP]) {
@@ -214,15 +228,13 @@ __device__ __forceinline__ void count_masks(const uint16_t *nbr, int b, int e, c
 }
 
 // Depth-first search of one instance; the state is initialised already.
-// Returns the status; writes best cost / node count through the refs and the
-// best assignment to d.mask.
 template <int KP>
-__device__ int search(const State<KP> &s, const InstDesc &d, int lane, int64_t budget,
-                      int64_t time_limit_ns, int64_t &best_out, int64_t &nodes_out,
-                      int64_t &work_out) {
+__device__ __forceinline__ int search(const State &s, const InstDesc &d, int lane, int64_t budget,
+                                      int64_t time_limit_ns, int64_t &best_out,
+                                      int64_t &nodes_out, int64_t &work_out) {
   using F = Fields<KP>;
   const int n = d.n, W = d.W, k = d.k;
-  const int64_t Cc = d.cost_conflict, Cs = d.cost_stitch;
+  const int Cc = d.cost_conflict, Cs = d.cost_stitch;
   int64_t best = INF, nodes = 0, g = 0, work = 0;
   int level = 0;
   int status = MPLD_OK;
@@ -245,15 +257,14 @@ __device__ int search(const State<KP> &s, const InstDesc &d, int lane, int64_t b
       for (int w = lane; w < W; w += 32) {
         const uint64_t a = s.active[w], um = s.unas[w];
         const uint64_t key4 = field_counts<KP>(a) | (~um & F::FILL);
-        z += __popcll(fields_le<KP>(key4, 0));
-        for (uint32_t t = 0; t <= (uint32_t)k; ++t) {
-          const uint64_t le = fields_le<KP>(key4, t);
-          if (le) {
-            const uint32_t seg = (uint32_t)(w * F::PER_WORD) + (uint32_t)((__ffsll((long long)le) - 1) / KP);
-            const uint32_t cand = (t << 24) | seg;
-            key = cand < key ? cand : key;
-            break;
-          }
+        uint64_t le = fields_le<KP>(key4, 0);
+        z += __popcll(le);
+        uint32_t t = 0;
+        while (!le && t < (uint32_t)k) le = fields_le<KP>(key4, ++t);
+        if (le) {
+          const uint32_t seg =
+              (uint32_t)(w * F::PER_WORD) + (uint32_t)((__ffsll((long long)le) - 1) / KP);
+          key = min(key, (t << 24) | seg);
         }
       }
       key = __reduce_min_sync(FULL, key);
@@ -268,41 +279,41 @@ __device__ int search(const State<KP> &s, const InstDesc &d, int lane, int64_t b
         enter = false;
         continue;
       }
-      if (best < INF && g + Cc * (int64_t)z >= best) { enter = false; continue; }
+      if (best < INF && g + (int64_t)Cc * z >= best) { enter = false; continue; }
       const int v = (int)(key & 0xFFFFFFu);
       // added cost of each row (v, c) against the current assignment (Eq. 1)
       int cc[KP], sc[KP];
 #pragma unroll
       for (int c = 0; c < KP; ++c) { cc[c] = 0; sc[c] = 0; }
-      count_masks<KP>(s.cnbr, s.cptr[v], s.cptr[v + 1], s.x, lane, cc);
-      count_masks<KP>(s.snbr, s.sptr[v], s.sptr[v + 1], s.x, lane, sc);
+      const int cb = s.cptr[v], ce = s.cptr[v + 1];
+      const int sb = s.sptr[v], se = s.sptr[v + 1];
+      count_masks<KP>(s.cnbr, cb, ce, s.x, lane, cc);
+      count_masks<KP>(s.snbr, sb, se, s.x, lane, sc);
       int stot = 0;
 #pragma unroll
       for (int c = 0; c < KP; ++c) stot += sc[c];
-      const int dcv = s.cptr[v + 1] - s.cptr[v];
-      work += (int64_t)k * (dcv + s.sptr[v + 1] - s.sptr[v]) + 5 * (1 + dcv);
-      uint64_t keys[KP];
+      work += (int64_t)k * (ce - cb + se - sb) + 5 * (1 + ce - cb);
+      uint32_t keys[KP];
 #pragma unroll
       for (int c = 0; c < KP; ++c) {
-        const int64_t inc = Cc * cc[c] + Cs * (stot - sc[c]);
-        keys[c] = c < k ? (((uint64_t)inc << 8) | (uint64_t)c) : ~0ull;
+        const uint32_t inc = (uint32_t)(Cc * cc[c] + Cs * (stot - sc[c]));
+        keys[c] = c < k ? ((inc << 3) | (uint32_t)c) : 0xFFFFFFFFu;
       }
       sort_keys<KP>(keys);
       uint32_t ord = 0;
 #pragma unroll
-      for (int i = 0; i < KP; ++i) ord |= (uint32_t)(keys[i] & 0xFu) << (4 * i);
+      for (int i = 0; i < KP; ++i) ord |= (keys[i] & 7u) << (4 * i);
       if (lane == 0) {
         s.lv_g[level] = g;
         s.lv_v[level] = v;
         s.lv_ord[level] = ord;
         s.lv_next[level] = 1;
 #pragma unroll
-        for (int i = 0; i < KP; ++i)
-          if (i < k) s.lv_inc[level * KP + i] = (int32_t)(keys[i] >> 8);
+        for (int i = 1; i < KP; ++i)
+          if (i < k) s.lv_inc[level * KP + i] = (int32_t)(keys[i] >> 3);
       }
-      const int c0 = (int)(ord & 0xFu);
-      cover_row<KP>(s, v, c0, lane);
-      g += (int64_t)(keys[0] >> 8);
+      cover_row<KP>(s, v, (int)(ord & 0xFu), lane);
+      g += (int64_t)(keys[0] >> 3);
       ++level;
       continue;
     }
@@ -317,7 +328,6 @@ __device__ int search(const State<KP> &s, const InstDesc &d, int lane, int64_t b
     const int c = (int)((ord >> (4 * nxt)) & 0xFu);
     g = s.lv_g[level] + s.lv_inc[level * KP + nxt];
     work += 5 * (1 + s.cptr[v + 1] - s.cptr[v]);
-    __syncwarp();
     if (lane == 0) s.lv_next[level] = (uint8_t)(nxt + 1);
     cover_row<KP>(s, v, c, lane);
     ++level;
@@ -329,52 +339,16 @@ __device__ int search(const State<KP> &s, const InstDesc &d, int lane, int64_t b
   return status;
 }
 
-// Returns false when the warp's shared-memory slot must not be used again
-// (a bulk copy into it did not complete within the wait limit).
-template <int KP>
-__device__ bool run_instance(const InstDesc &d, uint8_t *slot, int slot_bytes, uint64_t *bar,
-                             uint32_t &phase, const LaunchArgs &a, int lane) {
+// Initialise the state at `base` and search; SM selects the memory space of
+// `base` and `ro` at compile time.
+template <int KP, bool SM>
+__device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
+                                       const LaunchArgs &a, int lane) {
   using F = Fields<KP>;
   const int n = d.n, W = d.W;
   const StateLayout L = state_layout(n, W, d.ne2, KP);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2);
-  bool in_smem = slot != nullptr && (int)(L.bytes + R.bytes) <= slot_bytes;
-  bool slot_ok = true;
-  uint8_t *base = in_smem ? slot : d.scratch;
-  const uint8_t *ro = d.ro;
-  if (in_smem) {
-    uint8_t *dst = slot + L.bytes;
-    if (R.bytes >= TMA_MIN_BYTES) {
-      // one bulk copy of the whole read-only block into shared memory
-      __syncwarp();
-      if (lane == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(bar, R.bytes);
-        bulk_copy_g2s(dst, ro, R.bytes, bar);
-      }
-      uint32_t it = 0;
-      bool ok = false;
-      for (; it < WAIT_LIMIT; ++it)
-        if ((ok = mbar_try_wait(bar, phase))) break;
-      phase ^= 1u;
-      if (!ok) {
-        if (lane == 0) atomicExch(a.err, MPLD_E_TIMEOUT);
-        // the copy is still in flight: read the instance from global memory
-        // instead and leave this slot alone
-        base = d.scratch;
-        in_smem = false;
-        slot_ok = false;
-        for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
-          if (mbar_try_wait(bar, phase ^ 1u)) break;
-      }
-    } else {
-      const uint4 *src = (const uint4 *)ro;
-      uint4 *d4 = (uint4 *)dst;
-      for (uint32_t i = lane; i < R.bytes / 16; i += 32) d4[i] = __ldg(src + i);
-    }
-    if (in_smem) ro = dst;
-  }
-  State<KP> s;
+  State s;
   s.active = (uint64_t *)(base + L.active);
   s.unas = (uint64_t *)(base + L.unas);
   s.lv_g = (int64_t *)(base + L.lv_g);
@@ -416,17 +390,58 @@ __device__ bool run_instance(const InstDesc &d, uint8_t *slot, int slot_bytes, u
     d.res->work = work;
   }
   __syncwarp();
-  return slot_ok;
 }
 
-__global__ void __launch_bounds__(1024) mpld_search_kernel(const LaunchArgs a) {
-  extern __shared__ __align__(16) uint8_t smem[];
+// Stage and run one instance.  Returns false when the warp's slot must not
+// be used again (a bulk copy into it did not complete within the wait limit;
+// the instance then runs from global memory).
+template <int KP>
+__device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, int slot_bytes,
+                                             uint64_t *bar, uint32_t &phase, const LaunchArgs &a,
+                                             int lane) {
+  const StateLayout L = state_layout(d.n, d.W, d.ne2, KP);
+  const RoLayout R = ro_layout(d.n, d.ne2, d.ns2);
+  if (slot_bytes <= 0 || (int)(L.bytes + R.bytes) > slot_bytes) {
+    run_in<KP, false>(d, d.scratch, d.ro, a, lane);
+    return true;
+  }
+  uint8_t *slot = g_smem + slot_off;
+  uint8_t *dst = slot + L.bytes;
+  if (R.bytes >= TMA_MIN_BYTES) {
+    // one bulk copy of the whole read-only block into shared memory
+    __syncwarp();
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(bar, R.bytes);
+      bulk_copy_g2s(dst, d.ro, R.bytes, bar);
+    }
+    bool ok = false;
+    for (uint32_t it = 0; it < WAIT_LIMIT && !ok; ++it) ok = mbar_try_wait(bar, phase);
+    phase ^= 1u;
+    if (!ok) {
+      if (lane == 0) atomicExch(a.err, MPLD_E_TIMEOUT);
+      for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, phase ^ 1u)) break;
+      run_in<KP, false>(d, d.scratch, d.ro, a, lane);
+      return false;
+    }
+  } else {
+    const uint4 *src = (const uint4 *)d.ro;
+    uint4 *d4 = (uint4 *)dst;
+    for (uint32_t i = lane; i < R.bytes / 16; i += 32) d4[i] = __ldg(src + i);
+  }
+  run_in<KP, true>(d, slot, dst, a, lane);
+  return true;
+}
+
+__global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  uint64_t *bars = (uint64_t *)smem;
+  uint64_t *bars = (uint64_t *)g_smem;
   const uint32_t bar_bytes = align16(8u * (uint32_t)nw);
-  uint8_t *slot = a.slot_bytes > 0 ? smem + bar_bytes + (size_t)warp * a.slot_bytes : nullptr;
+  const uint32_t slot_off = bar_bytes + (uint32_t)warp * (uint32_t)(a.slot_bytes > 0 ? a.slot_bytes : 0);
+  int slot_bytes = a.slot_bytes;
   uint64_t *bar = bars + warp;
   if (lane == 0) mbar_init(bar);
   __syncwarp();
@@ -443,19 +458,13 @@ __global__ void __launch_bounds__(1024) mpld_search_kernel(const LaunchArgs a) {
     }
     if (idx >= a.n_inst) break;
     const InstDesc d = a.desc[a.order ? a.order[idx] : idx];
-    const bool ok = d.k <= 4 ? run_instance<4>(d, slot, a.slot_bytes, bar, phase, a, lane)
-                             : run_instance<8>(d, slot, a.slot_bytes, bar, phase, a, lane);
-    if (!ok) slot = nullptr;
+    const bool ok = d.k <= 4 ? run_instance<4>(d, slot_off, slot_bytes, bar, phase, a, lane)
+                             : run_instance<8>(d, slot_off, slot_bytes, bar, phase, a, lane);
+    if (!ok) slot_bytes = 0;
     if (!a.queue) break;
   }
 }
 
-}  // namespace
-}  // namespace mpld
-
-using mpld::LaunchArgs;
-
-namespace {
 // Largest dynamic shared memory size already granted to the kernel; the
 // attribute is only raised, and only outside stream capture (the shape is
 // chosen, and the attribute set, before any capture begins).
@@ -463,7 +472,7 @@ int g_smem_granted = 48 * 1024;
 
 int ensure_smem(size_t smem) {
   if ((int)smem <= g_smem_granted) return MPLD_OK;
-  if (cudaFuncSetAttribute(mpld::mpld_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(mpld_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return MPLD_E_CUDA;
@@ -471,13 +480,17 @@ int ensure_smem(size_t smem) {
   g_smem_granted = (int)smem;
   return MPLD_OK;
 }
+
 }  // namespace
+}  // namespace mpld
+
+using mpld::LaunchArgs;
 
 extern "C" int mpld_internal_launch(const LaunchArgs *a, int ctas, int warps_per_cta,
                                     void *stream) {
   const size_t smem = mpld::align16(8u * (uint32_t)warps_per_cta) +
                       (size_t)warps_per_cta * (size_t)(a->slot_bytes > 0 ? a->slot_bytes : 0);
-  if (ensure_smem(smem) != MPLD_OK) return MPLD_E_CUDA;
+  if (mpld::ensure_smem(smem) != MPLD_OK) return MPLD_E_CUDA;
   mpld::mpld_search_kernel<<<ctas, warps_per_cta * 32, smem, (cudaStream_t)stream>>>(*a);
   return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
 }
@@ -502,7 +515,7 @@ extern "C" int mpld_internal_max_slot_bytes(int warps_per_cta) {
 extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes) {
   const size_t smem =
       mpld::align16(8u * (uint32_t)warps_per_cta) + (size_t)warps_per_cta * (size_t)slot_bytes;
-  if (ensure_smem(smem) != MPLD_OK) return 0;
+  if (mpld::ensure_smem(smem) != MPLD_OK) return 0;
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mpld::mpld_search_kernel,
                                                     warps_per_cta * 32, smem) != cudaSuccess)
