@@ -321,7 +321,6 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     std::vector<int32_t> ns2v((size_t)C), mask_off((size_t)C);
     uint64_t arena = 0, scratch = 0;
     std::vector<uint64_t> scratch_off((size_t)C);
-    const int kp = mpld::kp_for(k);
     for (int c = 0; c < C; ++c) {
       int ne2 = 0, ns2 = 0;
       int64_t max_inc = 0;
@@ -334,11 +333,16 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
         ns2 += ds;
         max_inc = std::max(max_inc, p->Cc * dc + p->Cs * ds);
       }
-      // the kernel orders a segment's rows by 32-bit keys (added cost << 3 | mask)
-      if (max_inc >= (int64_t)1 << 28) { delete p; return MPLD_E_TOO_LARGE; }
+      // the kernel orders a segment's rows by 32-bit keys (added cost << 3 |
+      // mask) and keeps path costs in 32 bits
+      if (max_inc >= (int64_t)1 << 28 ||
+          p->Cc * (ne2 / 2) + p->Cs * (ns2 / 2) >= ((int64_t)1 << 31) - 1) {
+        delete p;
+        return MPLD_E_TOO_LARGE;
+      }
       const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
       const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2);
-      const mpld::StateLayout L = mpld::state_layout(nc, mpld::words_for(nc, kp), ne2, kp);
+      const mpld::StateLayout L = mpld::state_layout(nc, ne2, k);
       p->inst_ne2[c] = ne2;
       ns2v[c] = ns2;
       p->ro_off[c] = arena;
@@ -355,22 +359,21 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
       const mpld::RoLayout R = mpld::ro_layout(nc, p->inst_ne2[c], ns2v[c]);
       uint8_t *blk = p->h_arena.data() + p->ro_off[c];
-      int32_t *cptr = (int32_t *)(blk + R.cptr);
-      int32_t *sp = (int32_t *)(blk + R.sptr);
+      int32_t *ptr = (int32_t *)(blk + R.ptr);   // {conflict, stitch} offset pairs
       uint16_t *cn = (uint16_t *)(blk + R.cnbr);
       uint16_t *sn = (uint16_t *)(blk + R.snbr);
       int ci = 0, si = 0;
       for (int t = a; t < b; ++t) {
         const int s = p->comp_seg[t];
-        cptr[t - a] = ci;
-        sp[t - a] = si;
+        ptr[2 * (t - a)] = ci;
+        ptr[2 * (t - a) + 1] = si;
         for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i)
           if (p->comp_of[p->cadj[i]] == c) cn[ci++] = (uint16_t)local_of[p->cadj[i]];
         for (int i = sptr[s]; i < sptr[s + 1]; ++i)
           if (p->comp_of[sadj[i]] == c) sn[si++] = (uint16_t)local_of[sadj[i]];
       }
-      cptr[nc] = ci;
-      sp[nc] = si;
+      ptr[2 * nc] = ci;
+      ptr[2 * nc + 1] = si;
     }
     // largest first (ties: lower instance id first)
     p->h_order.resize((size_t)C);
@@ -386,11 +389,10 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       std::memset(&d, 0, sizeof(d));
       const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
       d.n = nc;
-      d.W = mpld::words_for(nc, kp);
       d.ne2 = p->inst_ne2[c];
       d.ns2 = ns2v[c];
       d.ro_bytes = (int32_t)mpld::ro_layout(nc, d.ne2, d.ns2).bytes;
-      d.state_bytes = (int32_t)mpld::state_layout(nc, d.W, d.ne2, kp).bytes;
+      d.state_bytes = (int32_t)mpld::state_layout(nc, d.ne2, k).bytes;
       d.k = k;
       d.cost_conflict = (int32_t)p->Cc;
       d.cost_stitch = (int32_t)p->Cs;
@@ -840,7 +842,9 @@ extern "C" int mpld_export_matrix(const mpld_problem *p, int32_t comp, uint8_t *
   // decode the packed read-only block as stored in the arena
   const mpld::RoLayout R = mpld::ro_layout(n, d.ne2, d.ns2);
   const uint8_t *blk = p->h_arena.data() + p->ro_off[comp];
-  const int32_t *cptr = (const int32_t *)(blk + R.cptr);
+  const int32_t *ptr = (const int32_t *)(blk + R.ptr);
+  std::vector<int32_t> cptr((size_t)n + 1);
+  for (int v = 0; v <= n; ++v) cptr[v] = ptr[2 * v];
   const uint16_t *cn = (const uint16_t *)(blk + R.cnbr);
   const size_t ncol = (size_t)(1 + n + k * ne);
   std::memset(dense, 0, (size_t)n * (size_t)k * ncol);

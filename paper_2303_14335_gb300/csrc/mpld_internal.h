@@ -12,31 +12,30 @@
 
 namespace mpld {
 
-// Rows of the EC matrix (Sec. 2.3): row (v, c) is bit v*KP + c of the
-// activeRows bitset, KP = 4 for k <= 4 and 8 for 5 <= k <= 8.  The KP bits
-// of segment v form the row set of primary column P_v and always sit inside
-// one 64-bit word; secondary column S_{e,c} of conflict edge e = (u, w) is
-// the two bits u*KP + c and w*KP + c.  The columns are therefore one- or
-// two-word masks generated from the conflict adjacency below, which is the
+// Rows of the EC matrix (Sec. 2.3): the activeRows bitset holds one field of
+// FB bits per segment v (FB = 8 for k <= 7, 16 for k = 8).  Bit c < k of
+// field v is row (v, c); the top bit of the field is set while primary
+// column P_v is uncovered (the column-header bit).  The k row bits of field
+// v are the row set of P_v; secondary column S_{e,c} of conflict edge
+// e = (u, w) is bit c of fields u and w.  Columns are therefore one- or
+// two-bit masks generated from the conflict adjacency below, which is the
 // block-sparse form of the column-major bitset matrix colRows[j][W].
-MPLD_HD int kp_for(int k) { return k <= 4 ? 4 : 8; }
-MPLD_HD int words_for(int n, int kp) { return (n * kp + 63) >> 6; }
+MPLD_HD int field_bytes_for(int k) { return k <= 7 ? 1 : 2; }
+MPLD_HD int mk_for(int k) { return k <= 4 ? 4 : 8; }   // width of the row sort
 MPLD_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 // Read-only block of one instance, 16-byte aligned in the device arena and
 // copied as one piece into shared memory (cp.async.bulk for large blocks):
-//   cptr[n+1] int32   conflict CSR offsets (component-local ids)
-//   sptr[n+1] int32   stitch CSR offsets
-//   cnbr[ne2] uint16  conflict neighbours, ascending per segment
-//   snbr[ns2] uint16  stitch neighbours
+//   ptr[n+1]  int2    {conflict CSR offset, stitch CSR offset} per segment
+//   cnbr[ne2] uint16  conflict neighbours (component-local), ascending
+//   snbr[ns2] uint16  stitch neighbours, ascending
 struct RoLayout {
-  uint32_t cptr, sptr, cnbr, snbr, bytes;
+  uint32_t ptr, cnbr, snbr, bytes;
 };
 MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
   RoLayout L;
   uint32_t o = 0;
-  L.cptr = o; o += align16(4u * (uint32_t)(n + 1));
-  L.sptr = o; o += align16(4u * (uint32_t)(n + 1));
+  L.ptr = o; o += align16(8u * (uint32_t)(n + 1));
   L.cnbr = o; o += align16(2u * (uint32_t)ne2);
   L.snbr = o; o += align16(2u * (uint32_t)ns2);
   L.bytes = o;
@@ -45,34 +44,27 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
 
 // Mutable search state of one instance (shared memory, or the instance's
 // global scratch region when it does not fit the warp's slot).  The DFS
-// depth is at most n, so every per-level array has n entries; undo data is
-// kept per segment / per adjacency entry because each segment appears at
-// most once on the current path.
-//   active[W]   u64  activeRows
-//   unas[W]     u64  KP-bit field all ones while segment v is uncovered
-//   lv_g[n]     i64  path cost at each level
-//   lv_inc[n*KP] i32 added cost of the level's rows, in visiting order
-//   lv_ord[n]   u32  visiting order of the masks, 4 bits each
-//   lv_v[n]     i32  segment (column) chosen at each level
-//   lv_next[n]  u8   rows of the level already visited
+// depth is at most n; undo data is kept per segment and per adjacency entry
+// because each segment appears at most once on the current path.
+//   rows[n]     FB-bit fields: activeRows + uncovered-column bits
+//   oldf[n]     field of v before v's row was covered
 //   x[n]        i8   current mask per segment (-1 = none)
-//   oldnib[n]   u8   active rows of P_v before v's row was covered
 //   clrb[ne2]   u8   1 if covering v's row cleared neighbour row (u, c)
+//   lv[n]       16-byte level record {path cost, v | rows tried << 16,
+//               visiting order (4 bits per row), added cost of row 1}
+//   lvx[n*mk]   added cost of rows 2.. in visiting order
 struct StateLayout {
-  uint32_t active, unas, lv_g, lv_inc, lv_ord, lv_v, lv_next, x, oldnib, clrb, bytes;
+  uint32_t rows, oldf, x, clrb, lv, lvx, bytes;
 };
-MPLD_HD StateLayout state_layout(int n, int W, int ne2, int kp) {
+MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
+  const uint32_t fb = (uint32_t)field_bytes_for(k), mk = (uint32_t)mk_for(k);
   StateLayout L;
   uint32_t o = 0;
-  L.active = o; o += align16(8u * (uint32_t)W);
-  L.unas = o; o += align16(8u * (uint32_t)W);
-  L.lv_g = o; o += align16(8u * (uint32_t)n);
-  L.lv_inc = o; o += align16(4u * (uint32_t)(n * kp));
-  L.lv_ord = o; o += align16(4u * (uint32_t)n);
-  L.lv_v = o; o += align16(4u * (uint32_t)n);
-  L.lv_next = o; o += align16((uint32_t)n);
+  L.lv = o; o += 16u * (uint32_t)n;
+  L.lvx = o; o += align16(4u * mk * (uint32_t)n);
+  L.rows = o; o += align16(fb * (uint32_t)n);
+  L.oldf = o; o += align16(fb * (uint32_t)n);
   L.x = o; o += align16((uint32_t)n);
-  L.oldnib = o; o += align16((uint32_t)n);
   L.clrb = o; o += align16((uint32_t)ne2);
   L.bytes = o;
   return L;
@@ -85,7 +77,7 @@ struct InstDesc {
   uint8_t *scratch;        // global state region (state_bytes), used when spilled
   int8_t *mask;            // n bytes: best assignment found
   struct InstResult *res;  // result record
-  int32_t n, W, ne2, ns2;
+  int32_t n, pad2, ne2, ns2;
   int32_t ro_bytes, state_bytes;
   int32_t k, cost_conflict;
   int32_t cost_stitch, pad0;

@@ -2,17 +2,19 @@
 // sm_103a.
 //
 // One warp runs one search instance (a sub-graph of the layout).  The EC
-// matrix's active rows are a bitset in shared memory; the three operations
-// of Algorithm 1 become word operations:
-//   * column choice (Algorithm 1, "select an uncovered column"): for every
-//     uncovered primary column P_v, popc(activeRows & colRows[P_v]); the
-//     KP-bit fields of a word are counted at once with a SWAR popcount, and
-//     the warp takes the minimum of (count, v) with __reduce_min_sync, so
-//     ties go to the lowest segment index;
+// matrix's active rows are a bitset in shared memory with one field per
+// segment (its k row bits plus a top "column uncovered" bit), and the three
+// operations of Algorithm 1 become bit operations on it:
+//   * column choice (Algorithm 1, "select an uncovered column"): lane l
+//     takes the uncovered primary columns P_v, v = l, l+32, ..., computes
+//     popc(activeRows & colRows[P_v]) on v's field, and the warp takes the
+//     minimum of (count, v) with __reduce_min_sync, so ties go to the lowest
+//     segment index;
 //   * cover of row (v, c) (Eq. 2 "Cover", Algorithm 1 "cover rw and its
 //     affected rows"): activeRows &= ~colRows[j] for every column j of the
-//     row, i.e. v's field and the (u, c) bit of every conflict neighbour u;
-//     the cleared bits are recorded per adjacency entry;
+//     row -- v's field, and bit c of every conflict neighbour u (column
+//     S_{(v,u),c}); lane i handles neighbour i with a 32-bit shared atomic
+//     AND and records whether it cleared the bit;
 //   * uncover (Eq. 2 "Uncover"): OR the recorded bits back, newest level
 //     first, through an explicit per-level stack instead of recursion.
 // Rows of the chosen column are visited in ascending (added cost, mask),
@@ -43,43 +45,9 @@ namespace {
 extern __shared__ __align__(16) uint8_t g_smem[];
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int64_t INF = INT64_MAX;
+constexpr int32_t INF32 = 0x7FFFFFFF;
 constexpr uint32_t TMA_MIN_BYTES = 1024;     // smaller blocks use vector loads
 constexpr uint32_t WAIT_LIMIT = 1u << 22;    // bounded mbarrier wait
-
-template <int KP> struct Fields;
-template <> struct Fields<4> {
-  static constexpr uint64_t LO = 0x1111111111111111ull;
-  static constexpr uint64_t HI = 0x8888888888888888ull;
-  static constexpr uint64_t FILL = 0x7777777777777777ull;  // > any count for k <= 4
-  static constexpr uint64_t FM = 0xFull;
-  static constexpr int PER_WORD = 16;
-};
-template <> struct Fields<8> {
-  static constexpr uint64_t LO = 0x0101010101010101ull;
-  static constexpr uint64_t HI = 0x8080808080808080ull;
-  static constexpr uint64_t FILL = 0x0F0F0F0F0F0F0F0Full;  // 15 > any count for k <= 8
-  static constexpr uint64_t FM = 0xFFull;
-  static constexpr int PER_WORD = 8;
-};
-
-// Number of set bits in every KP-bit field of a (SWAR popcount).
-template <int KP>
-__device__ __forceinline__ uint64_t field_counts(uint64_t a) {
-  a = a - ((a >> 1) & 0x5555555555555555ull);
-  a = (a & 0x3333333333333333ull) + ((a >> 2) & 0x3333333333333333ull);
-  if (KP == 8) a = (a + (a >> 4)) & 0x0F0F0F0F0F0F0F0Full;
-  return a;
-}
-
-// Fields whose value is <= t (top bit of each selected field set).  Field
-// values are < 2^(KP-1), so OR-ing the top bit and subtracting t+1 never
-// borrows across fields.
-template <int KP>
-__device__ __forceinline__ uint64_t fields_le(uint64_t key, uint32_t t) {
-  using F = Fields<KP>;
-  return ~((key | F::HI) - (uint64_t)(t + 1) * F::LO) & F::HI;
-}
 
 __device__ __forceinline__ void cas_u32(uint32_t &a, uint32_t &b) {
   const uint32_t lo = min(a, b), hi = max(a, b);
@@ -88,7 +56,7 @@ __device__ __forceinline__ void cas_u32(uint32_t &a, uint32_t &b) {
 }
 
 // Sort keys ((inc << 3) | mask) ascending with a fixed network.
-template <int KP> __device__ __forceinline__ void sort_keys(uint32_t (&k)[KP]);
+template <int MK> __device__ __forceinline__ void sort_keys(uint32_t (&k)[MK]);
 template <> __device__ __forceinline__ void sort_keys<4>(uint32_t (&k)[4]) {
   cas_u32(k[0], k[1]); cas_u32(k[2], k[3]); cas_u32(k[0], k[2]); cas_u32(k[1], k[3]);
   cas_u32(k[1], k[2]);
@@ -143,248 +111,227 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // ---- the search ----------------------------------------------------------
 
-struct State {
-  uint64_t *active, *unas;
-  int64_t *lv_g;
-  int32_t *lv_inc;
-  uint32_t *lv_ord;
-  int32_t *lv_v;
-  uint8_t *lv_next;
+// FT: field type of the activeRows bitset (uint8_t for k <= 7, uint16_t for
+// k = 8); MK: width of the row sort (4 for k <= 4, else 8).
+template <typename FT, int MK>
+struct Search {
+  static constexpr uint32_t FB = 8 * sizeof(FT);   // bits per field
+  static constexpr uint32_t FLAG = 1u << (FB - 1);  // column P_v uncovered
+  static constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
+
+  FT *rows;        // activeRows fields
+  FT *oldf;        // field of v before its row was covered
   int8_t *x;
-  uint8_t *oldnib;
   uint8_t *clrb;
-  const int32_t *cptr, *sptr;
+  uint4 *lv;       // {g, v | tried << 16, order, inc of row 1}
+  int32_t *lvx;    // inc of rows 2.. per level (MK entries per level)
+  const int2 *ptr; // {conflict offset, stitch offset} per segment
   const uint16_t *cnbr, *snbr;
-};
+  int n, k;
+  int Cc, Cs;
+  uint32_t kmask;
 
-// 32-bit half of activeRows holding bit position p of word w.
-__device__ __forceinline__ uint32_t *half_of(uint64_t *active, int w, int p) {
-  return reinterpret_cast<uint32_t *>(active + w) + (p >> 5);
-}
-
-template <int KP>
-__device__ __forceinline__ void cover_row(const State &s, int v, int c, int lane) {
-  using F = Fields<KP>;
-  if (lane == 0) {
-    const int p = v * KP;
-    const uint32_t fm = (uint32_t)F::FM << (p & 31);
-    const uint32_t old = atomicAnd(half_of(s.active, p >> 6, p & 63), ~fm);
-    s.oldnib[v] = (uint8_t)((old & fm) >> (p & 31));
-    uint32_t *uh = half_of(s.unas, p >> 6, p & 63);
-    *uh &= ~fm;
-    s.x[v] = (int8_t)c;
+  __device__ __forceinline__ uint32_t *word_of(int v) const {
+    return reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(rows) +
+                                        (((uint32_t)v * sizeof(FT)) & ~3u));
   }
-  const int ce = s.cptr[v + 1];
-  for (int i = s.cptr[v] + lane; i < ce; i += 32) {
-    const int p = (int)s.cnbr[i] * KP + c;
-    const uint32_t bit = 1u << (p & 31);
-    const uint32_t old = atomicAnd(half_of(s.active, p >> 6, p & 63), ~bit);
-    s.clrb[i] = (old & bit) ? 1 : 0;
+  __device__ __forceinline__ uint32_t shift_of(int v) const {
+    return (((uint32_t)v * sizeof(FT)) & 3u) * 8u;
   }
-  __syncwarp();
-}
 
-template <int KP>
-__device__ __forceinline__ void uncover_row(const State &s, int v, int c, int lane) {
-  using F = Fields<KP>;
-  const int ce = s.cptr[v + 1];
-  for (int i = s.cptr[v] + lane; i < ce; i += 32) {
-    if (s.clrb[i]) {
-      const int p = (int)s.cnbr[i] * KP + c;
-      atomicOr(half_of(s.active, p >> 6, p & 63), 1u << (p & 31));
+  // Cover row (v, c): clear v's field and bit c of every conflict neighbour;
+  // `u` is lane's neighbour (valid for lane < ce - cb, first 32 only).
+  __device__ __forceinline__ void cover(int v, int c, int cb, int ce, int u, int lane) const {
+    if (lane == 0) {
+      const uint32_t sh = shift_of(v);
+      const uint32_t old = atomicAnd(word_of(v), ~(FMASK << sh));
+      oldf[v] = (FT)((old >> sh) & FMASK);
+      x[v] = (int8_t)c;
     }
+    for (int i = cb + lane; i < ce; i += 32) {
+      if (i >= cb + 32) u = cnbr[i];
+      const uint32_t bit = 1u << (shift_of(u) + (uint32_t)c);
+      const uint32_t old = atomicAnd(word_of(u), ~bit);
+      clrb[i] = (old & bit) ? 1 : 0;
+    }
+    __syncwarp();
   }
-  if (lane == 0) {
-    const int p = v * KP;
-    atomicOr(half_of(s.active, p >> 6, p & 63), (uint32_t)s.oldnib[v] << (p & 31));
-    uint32_t *uh = half_of(s.unas, p >> 6, p & 63);
-    *uh |= (uint32_t)F::FM << (p & 31);
-    s.x[v] = -1;
-  }
-  __syncwarp();
-}
 
-// Per-mask counts of neighbours holding each mask, summed over the warp
-// (8-bit packed lanes contributions, one reduction per 4 masks).
-template <int KP>
-__device__ __forceinline__ void count_masks(const uint16_t *nbr, int b, int e, const int8_t *x,
-                                            int lane, int (&cnt)[KP]) {
-  for (int base = b; base < e; base += 32) {
-    const int i = base + lane;
-    uint32_t lo = 0, hi = 0;
-    if (i < e) {
-      const int xu = x[nbr[i]];
-      if (xu >= 0) {
-        if (KP == 4 || xu < 4) lo = 1u << (8 * xu);
-        else hi = 1u << (8 * (xu - 4));
+  // Uncover row (v, c); leaves lane's first neighbour in `u`.
+  __device__ __forceinline__ void uncover(int v, int c, int cb, int ce, int &u, int lane) const {
+    for (int i = cb + lane; i < ce; i += 32) {
+      const int w = cnbr[i];
+      if (i < cb + 32) u = w;
+      if (clrb[i]) atomicOr(word_of(w), 1u << (shift_of(w) + (uint32_t)c));
+    }
+    if (lane == 0) {
+      atomicOr(word_of(v), (uint32_t)oldf[v] << shift_of(v));
+      x[v] = -1;
+    }
+    __syncwarp();
+  }
+
+  // Per-mask counts of a neighbour list, packed 8 bits per mask, warp-summed.
+  __device__ __forceinline__ void count(const uint16_t *nbr, int b, int e, int lane, int &first,
+                                        uint32_t &lo, uint32_t &hi) const {
+    lo = 0;
+    hi = 0;
+    for (int base = b; base < e; base += 32) {
+      const int i = base + lane;
+      uint32_t l = 0, h = 0;
+      if (i < e) {
+        const int w = nbr[i];
+        if (base == b) first = w;
+        const int xu = x[w];
+        if (xu >= 0) {
+          if (MK == 4 || xu < 4) l = 1u << (8 * xu);
+          else h = 1u << (8 * (xu - 4));
+        }
       }
+      lo += __reduce_add_sync(FULL, l);
+      if (MK == 8) hi += __reduce_add_sync(FULL, h);
     }
-    lo = __reduce_add_sync(FULL, lo);
-    if (KP == 8) hi = __reduce_add_sync(FULL, hi);
+  }
+
+  __device__ __forceinline__ int run(int lane, int64_t budget, int64_t time_limit_ns,
+                                     int8_t *best_mask, int32_t &best_out, int64_t &nodes_out,
+                                     int64_t &work_out) const {
+    int32_t best = INF32, g = 0;
+    int64_t nodes = 0, work = 0;
+    int level = 0;
+    int status = MPLD_OK;
+    const uint64_t t0 = globaltimer();
+    bool enter = true;
+    for (;;) {
+      if (enter) {
+        // ---- a node: one call of the recursive search ----
+        if (budget > 0 && best < INF32 && nodes >= budget) { status = MPLD_BUDGET; break; }
+        ++nodes;
+        work += 2 * (int64_t)(n - level);
+        if ((nodes & 1023) == 0) {
+          uint64_t now = lane == 0 ? globaltimer() : 0;
+          now = __shfl_sync(FULL, now, 0);
+          if ((int64_t)(now - t0) > time_limit_ns) { status = MPLD_TIMEOUT; break; }
+        }
+        // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v])
+        uint32_t key = 0xFFFFFFFFu, z = 0;
+        for (int v = lane; v < n; v += 32) {
+          const uint32_t f = rows[v];
+          const uint32_t cnt = __popc(f & kmask);
+          const uint32_t kv = (f & FLAG) ? ((cnt << 16) | (uint32_t)v) : 0xFFFFFFFFu;
+          key = min(key, kv);
+          z += kv <= 0xFFFFu;  // uncovered with no active row
+        }
+        key = __reduce_min_sync(FULL, key);
+        if (key == 0xFFFFFFFFu) {
+          // leaf: every primary column covered
+          if (g < best) {
+            best = g;
+            for (int i = lane; i < n; i += 32) best_mask[i] = x[i];
+            if (best == 0) break;
+          }
+          enter = false;
+          continue;
+        }
+        if (best < INF32) {
+          z = __reduce_add_sync(FULL, z);
+          if ((int64_t)g + (int64_t)Cc * z >= best) { enter = false; continue; }
+        }
+        const int v = (int)(key & 0xFFFFu);
+        // added cost of each row (v, c) against the current assignment (Eq. 1)
+        const int2 p0 = ptr[v], p1 = ptr[v + 1];
+        int u = 0, us = 0;
+        uint32_t clo, chi, slo, shi;
+        count(cnbr, p0.x, p1.x, lane, u, clo, chi);
+        count(snbr, p0.y, p1.y, lane, us, slo, shi);
+        work += (int64_t)k * (p1.x - p0.x + p1.y - p0.y) + 5 * (1 + p1.x - p0.x);
+        int stot = 0;
 #pragma unroll
-    for (int c = 0; c < KP; ++c)
-      cnt[c] += (int)(((c < 4) ? (lo >> (8 * c)) : (hi >> (8 * (c - 4)))) & 0xFFu);
-  }
-}
-
-// Depth-first search of one instance; the state is initialised already.
-template <int KP>
-__device__ __forceinline__ int search(const State &s, const InstDesc &d, int lane, int64_t budget,
-                                      int64_t time_limit_ns, int64_t &best_out,
-                                      int64_t &nodes_out, int64_t &work_out) {
-  using F = Fields<KP>;
-  const int n = d.n, W = d.W, k = d.k;
-  const int Cc = d.cost_conflict, Cs = d.cost_stitch;
-  int64_t best = INF, nodes = 0, g = 0, work = 0;
-  int level = 0;
-  int status = MPLD_OK;
-  const uint64_t t0 = globaltimer();
-  bool enter = true;
-
-  for (;;) {
-    if (enter) {
-      // ---- a node: one call of the recursive search ----
-      if (budget > 0 && best < INF && nodes >= budget) { status = MPLD_BUDGET; break; }
-      ++nodes;
-      work += 2 * (int64_t)(n - level);
-      if ((nodes & 1023) == 0) {
-        uint64_t now = lane == 0 ? globaltimer() : 0;
-        now = __shfl_sync(FULL, now, 0);
-        if ((int64_t)(now - t0) > time_limit_ns) { status = MPLD_TIMEOUT; break; }
-      }
-      // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v])
-      uint32_t key = 0xFFFFFFFFu, z = 0;
-      for (int w = lane; w < W; w += 32) {
-        const uint64_t a = s.active[w], um = s.unas[w];
-        const uint64_t key4 = field_counts<KP>(a) | (~um & F::FILL);
-        uint64_t le = fields_le<KP>(key4, 0);
-        z += __popcll(le);
-        uint32_t t = 0;
-        while (!le && t < (uint32_t)k) le = fields_le<KP>(key4, ++t);
-        if (le) {
-          const uint32_t seg =
-              (uint32_t)(w * F::PER_WORD) + (uint32_t)((__ffsll((long long)le) - 1) / KP);
-          key = min(key, (t << 24) | seg);
+        for (int c = 0; c < MK; ++c)
+          stot += (int)((((c < 4) ? (slo >> (8 * c)) : (shi >> (8 * (c - 4))))) & 0xFFu);
+        uint32_t keys[MK];
+#pragma unroll
+        for (int c = 0; c < MK; ++c) {
+          const int cc = (int)((((c < 4) ? (clo >> (8 * c)) : (chi >> (8 * (c - 4))))) & 0xFFu);
+          const int sc = (int)((((c < 4) ? (slo >> (8 * c)) : (shi >> (8 * (c - 4))))) & 0xFFu);
+          const uint32_t inc = (uint32_t)(Cc * cc + Cs * (stot - sc));
+          keys[c] = c < k ? ((inc << 3) | (uint32_t)c) : 0xFFFFFFFFu;
         }
-      }
-      key = __reduce_min_sync(FULL, key);
-      z = __reduce_add_sync(FULL, z);
-      if (key == 0xFFFFFFFFu) {
-        // leaf: every primary column covered
-        if (g < best) {
-          best = g;
-          for (int i = lane; i < n; i += 32) d.mask[i] = s.x[i];
-          if (best == 0) break;
+        sort_keys<MK>(keys);
+        uint32_t ord = 0;
+#pragma unroll
+        for (int i = 0; i < MK; ++i) ord |= (keys[i] & 7u) << (4 * i);
+        if (lane == 0) {
+          lv[level] = make_uint4((uint32_t)g, (uint32_t)v | (1u << 16), ord, keys[1] >> 3);
+#pragma unroll
+          for (int i = 2; i < MK; ++i)
+            if (i < k) lvx[level * MK + i] = (int32_t)(keys[i] >> 3);
         }
-        enter = false;
+        cover(v, (int)(ord & 7u), p0.x, p1.x, u, lane);
+        g += (int32_t)(keys[0] >> 3);
+        ++level;
         continue;
       }
-      if (best < INF && g + (int64_t)Cc * z >= best) { enter = false; continue; }
-      const int v = (int)(key & 0xFFFFFFu);
-      // added cost of each row (v, c) against the current assignment (Eq. 1)
-      int cc[KP], sc[KP];
-#pragma unroll
-      for (int c = 0; c < KP; ++c) { cc[c] = 0; sc[c] = 0; }
-      const int cb = s.cptr[v], ce = s.cptr[v + 1];
-      const int sb = s.sptr[v], se = s.sptr[v + 1];
-      count_masks<KP>(s.cnbr, cb, ce, s.x, lane, cc);
-      count_masks<KP>(s.snbr, sb, se, s.x, lane, sc);
-      int stot = 0;
-#pragma unroll
-      for (int c = 0; c < KP; ++c) stot += sc[c];
-      work += (int64_t)k * (ce - cb + se - sb) + 5 * (1 + ce - cb);
-      uint32_t keys[KP];
-#pragma unroll
-      for (int c = 0; c < KP; ++c) {
-        const uint32_t inc = (uint32_t)(Cc * cc[c] + Cs * (stot - sc[c]));
-        keys[c] = c < k ? ((inc << 3) | (uint32_t)c) : 0xFFFFFFFFu;
-      }
-      sort_keys<KP>(keys);
-      uint32_t ord = 0;
-#pragma unroll
-      for (int i = 0; i < KP; ++i) ord |= (keys[i] & 7u) << (4 * i);
-      if (lane == 0) {
-        s.lv_g[level] = g;
-        s.lv_v[level] = v;
-        s.lv_ord[level] = ord;
-        s.lv_next[level] = 1;
-#pragma unroll
-        for (int i = 1; i < KP; ++i)
-          if (i < k) s.lv_inc[level * KP + i] = (int32_t)(keys[i] >> 3);
-      }
-      cover_row<KP>(s, v, (int)(ord & 0xFu), lane);
-      g += (int64_t)(keys[0] >> 3);
+      // ---- backtrack: uncover the row of the level above, try its next row ----
+      if (level == 0) break;
+      --level;
+      const uint4 rec = lv[level];
+      const int v = (int)(rec.y & 0xFFFFu);
+      const int nxt = (int)(rec.y >> 16);
+      const int2 p0 = ptr[v], p1 = ptr[v + 1];
+      int u = 0;
+      uncover(v, (int)((rec.z >> (4 * (nxt - 1))) & 7u), p0.x, p1.x, u, lane);
+      if (nxt >= k) continue;  // every row of this column tried
+      const int c = (int)((rec.z >> (4 * nxt)) & 7u);
+      g = (int32_t)rec.x + (nxt == 1 ? (int32_t)rec.w : lvx[level * MK + nxt]);
+      work += 5 * (1 + p1.x - p0.x);
+      if (lane == 0) lv[level].y = (uint32_t)v | ((uint32_t)(nxt + 1) << 16);
+      cover(v, c, p0.x, p1.x, u, lane);
       ++level;
-      continue;
+      enter = true;
     }
-    // ---- backtrack: uncover the row of the level above, try its next row ----
-    if (level == 0) break;
-    --level;
-    const int v = s.lv_v[level];
-    const int nxt = s.lv_next[level];
-    const uint32_t ord = s.lv_ord[level];
-    uncover_row<KP>(s, v, (int)((ord >> (4 * (nxt - 1))) & 0xFu), lane);
-    if (nxt >= k) continue;  // every row of this column tried
-    const int c = (int)((ord >> (4 * nxt)) & 0xFu);
-    g = s.lv_g[level] + s.lv_inc[level * KP + nxt];
-    work += 5 * (1 + s.cptr[v + 1] - s.cptr[v]);
-    if (lane == 0) s.lv_next[level] = (uint8_t)(nxt + 1);
-    cover_row<KP>(s, v, c, lane);
-    ++level;
-    enter = true;
+    best_out = best;
+    nodes_out = nodes;
+    work_out = work;
+    return status;
   }
-  best_out = best;
-  nodes_out = nodes;
-  work_out = work;
-  return status;
-}
+};
 
-// Initialise the state at `base` and search; SM selects the memory space of
-// `base` and `ro` at compile time.
-template <int KP, bool SM>
+// Initialise the state at `base` and search.  SM says at compile time
+// whether `base` and `ro` point into shared memory.
+template <typename FT, int MK, bool SM>
 __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
                                        const LaunchArgs &a, int lane) {
-  using F = Fields<KP>;
-  const int n = d.n, W = d.W;
-  const StateLayout L = state_layout(n, W, d.ne2, KP);
+  const int n = d.n;
+  const StateLayout L = state_layout(n, d.ne2, d.k);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2);
-  State s;
-  s.active = (uint64_t *)(base + L.active);
-  s.unas = (uint64_t *)(base + L.unas);
-  s.lv_g = (int64_t *)(base + L.lv_g);
-  s.lv_inc = (int32_t *)(base + L.lv_inc);
-  s.lv_ord = (uint32_t *)(base + L.lv_ord);
-  s.lv_v = (int32_t *)(base + L.lv_v);
-  s.lv_next = base + L.lv_next;
+  Search<FT, MK> s;
+  s.rows = (FT *)(base + L.rows);
+  s.oldf = (FT *)(base + L.oldf);
   s.x = (int8_t *)(base + L.x);
-  s.oldnib = base + L.oldnib;
   s.clrb = base + L.clrb;
-  s.cptr = (const int32_t *)(ro + R.cptr);
-  s.sptr = (const int32_t *)(ro + R.sptr);
+  s.lv = (uint4 *)(base + L.lv);
+  s.lvx = (int32_t *)(base + L.lvx);
+  s.ptr = (const int2 *)(ro + R.ptr);
   s.cnbr = (const uint16_t *)(ro + R.cnbr);
   s.snbr = (const uint16_t *)(ro + R.snbr);
-
+  s.n = n;
+  s.k = d.k;
+  s.Cc = d.cost_conflict;
+  s.Cs = d.cost_stitch;
+  s.kmask = (1u << d.k) - 1u;
   // initial state: every row active, every primary column uncovered
-  const uint64_t kmask = (1ull << d.k) - 1ull;
-  uint64_t rowpat = 0, fieldpat = 0;
-#pragma unroll
-  for (int j = 0; j < F::PER_WORD; ++j) {
-    rowpat |= kmask << (j * KP);
-    fieldpat |= F::FM << (j * KP);
+  const FT init = (FT)(s.kmask | Search<FT, MK>::FLAG);
+  for (int i = lane; i < n; i += 32) {
+    s.rows[i] = init;
+    s.x[i] = -1;
   }
-  for (int w = lane; w < W; w += 32) {
-    const int segs = n - w * F::PER_WORD;
-    const uint64_t keep = segs >= F::PER_WORD ? ~0ull : ((1ull << (segs * KP)) - 1ull);
-    s.active[w] = rowpat & keep;
-    s.unas[w] = fieldpat & keep;
-  }
-  for (int i = lane; i < n; i += 32) s.x[i] = -1;
   __syncwarp();
-
-  int64_t best = INF, nodes = 0, work = 0;
-  const int st = search<KP>(s, d, lane, a.budget, a.time_limit_ns, best, nodes, work);
+  int32_t best = INF32;
+  int64_t nodes = 0, work = 0;
+  const int st = s.run(lane, a.budget, a.time_limit_ns, d.mask, best, nodes, work);
   if (lane == 0) {
-    d.res->cost = best;
+    d.res->cost = best == INF32 ? INT64_MAX : (int64_t)best;
     d.res->nodes = nodes;
     d.res->status = st;
     d.res->work = work;
@@ -392,17 +339,14 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   __syncwarp();
 }
 
-// Stage and run one instance.  Returns false when the warp's slot must not
-// be used again (a bulk copy into it did not complete within the wait limit;
-// the instance then runs from global memory).
-template <int KP>
+template <typename FT, int MK>
 __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, int slot_bytes,
                                              uint64_t *bar, uint32_t &phase, const LaunchArgs &a,
                                              int lane) {
-  const StateLayout L = state_layout(d.n, d.W, d.ne2, KP);
+  const StateLayout L = state_layout(d.n, d.ne2, d.k);
   const RoLayout R = ro_layout(d.n, d.ne2, d.ns2);
   if (slot_bytes <= 0 || (int)(L.bytes + R.bytes) > slot_bytes) {
-    run_in<KP, false>(d, d.scratch, d.ro, a, lane);
+    run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
     return true;
   }
   uint8_t *slot = g_smem + slot_off;
@@ -419,10 +363,12 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
     for (uint32_t it = 0; it < WAIT_LIMIT && !ok; ++it) ok = mbar_try_wait(bar, phase);
     phase ^= 1u;
     if (!ok) {
+      // the copy did not land: record it, wait (bounded) for the copy still
+      // in flight, run from global memory and give up the slot
       if (lane == 0) atomicExch(a.err, MPLD_E_TIMEOUT);
       for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
         if (mbar_try_wait(bar, phase ^ 1u)) break;
-      run_in<KP, false>(d, d.scratch, d.ro, a, lane);
+      run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
       return false;
     }
   } else {
@@ -430,7 +376,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
     uint4 *d4 = (uint4 *)dst;
     for (uint32_t i = lane; i < R.bytes / 16; i += 32) d4[i] = __ldg(src + i);
   }
-  run_in<KP, true>(d, slot, dst, a, lane);
+  run_in<FT, MK, true>(d, slot, dst, a, lane);
   return true;
 }
 
@@ -440,7 +386,8 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
   const int nw = blockDim.x >> 5;
   uint64_t *bars = (uint64_t *)g_smem;
   const uint32_t bar_bytes = align16(8u * (uint32_t)nw);
-  const uint32_t slot_off = bar_bytes + (uint32_t)warp * (uint32_t)(a.slot_bytes > 0 ? a.slot_bytes : 0);
+  const uint32_t slot_off =
+      bar_bytes + (uint32_t)warp * (uint32_t)(a.slot_bytes > 0 ? a.slot_bytes : 0);
   int slot_bytes = a.slot_bytes;
   uint64_t *bar = bars + warp;
   if (lane == 0) mbar_init(bar);
@@ -458,8 +405,10 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
     }
     if (idx >= a.n_inst) break;
     const InstDesc d = a.desc[a.order ? a.order[idx] : idx];
-    const bool ok = d.k <= 4 ? run_instance<4>(d, slot_off, slot_bytes, bar, phase, a, lane)
-                             : run_instance<8>(d, slot_off, slot_bytes, bar, phase, a, lane);
+    bool ok;
+    if (d.k <= 4) ok = run_instance<uint8_t, 4>(d, slot_off, slot_bytes, bar, phase, a, lane);
+    else if (d.k <= 7) ok = run_instance<uint8_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
+    else ok = run_instance<uint16_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
     if (!ok) slot_bytes = 0;
     if (!a.queue) break;
   }
