@@ -49,12 +49,13 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
 //   rows[n]     FB-bit fields: activeRows + uncovered-column bits
 //   oldf[n]     field of v before v's row was covered
 //   x[n]        i8   current mask per segment (-1 = none)
-//   clrb[ne2]   u8   1 if covering v's row cleared neighbour row (u, c)
+//   savf[ne2]   field of neighbour u before v's row cleared its bit (the
+//               undo record of the cover, one per adjacency entry of v)
 //   lv[n]       16-byte level record {path cost, v | rows tried << 16,
 //               visiting order (4 bits per row), added cost of row 1}
 //   lvx[n*mk]   added cost of rows 2.. in visiting order
 struct StateLayout {
-  uint32_t rows, oldf, x, clrb, lv, lvx, bytes;
+  uint32_t rows, oldf, x, savf, lv, lvx, bytes;
 };
 MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
   const uint32_t fb = (uint32_t)field_bytes_for(k), mk = (uint32_t)mk_for(k);
@@ -65,7 +66,7 @@ MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
   L.rows = o; o += align16(fb * (uint32_t)n);
   L.oldf = o; o += align16(fb * (uint32_t)n);
   L.x = o; o += align16((uint32_t)n);
-  L.clrb = o; o += align16((uint32_t)ne2);
+  L.savf = o; o += align16(fb * (uint32_t)ne2);
   L.bytes = o;
   return L;
 }

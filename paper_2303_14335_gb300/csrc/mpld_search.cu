@@ -13,10 +13,10 @@
 //   * cover of row (v, c) (Eq. 2 "Cover", Algorithm 1 "cover rw and its
 //     affected rows"): activeRows &= ~colRows[j] for every column j of the
 //     row -- v's field, and bit c of every conflict neighbour u (column
-//     S_{(v,u),c}); lane i handles neighbour i with a 32-bit shared atomic
-//     AND and records whether it cleared the bit;
-//   * uncover (Eq. 2 "Uncover"): OR the recorded bits back, newest level
-//     first, through an explicit per-level stack instead of recursion.
+//     S_{(v,u),c}); lane i handles neighbour i and saves u's field first;
+//   * uncover (Eq. 2 "Uncover"): the saved fields are written back, newest
+//     level first, through an explicit per-level stack instead of
+//     recursion.
 // Rows of the chosen column are visited in ascending (added cost, mask),
 // including rows that are no longer active: those are the "conflict
 // candidates" of Algorithm 1 and pay the conflict cost of Eq. 1.  A node is
@@ -57,6 +57,10 @@ __device__ __forceinline__ void cas_u32(uint32_t &a, uint32_t &b) {
 
 // Sort keys ((inc << 3) | mask) ascending with a fixed network.
 template <int MK> __device__ __forceinline__ void sort_keys(uint32_t (&k)[MK]);
+template <> __device__ __forceinline__ void sort_keys<2>(uint32_t (&k)[2]) { cas_u32(k[0], k[1]); }
+template <> __device__ __forceinline__ void sort_keys<3>(uint32_t (&k)[3]) {
+  cas_u32(k[0], k[1]); cas_u32(k[1], k[2]); cas_u32(k[0], k[1]);
+}
 template <> __device__ __forceinline__ void sort_keys<4>(uint32_t (&k)[4]) {
   cas_u32(k[0], k[1]); cas_u32(k[2], k[3]); cas_u32(k[0], k[2]); cas_u32(k[1], k[3]);
   cas_u32(k[1], k[2]);
@@ -112,18 +116,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // ---- the search ----------------------------------------------------------
 
 // FT: field type of the activeRows bitset (uint8_t for k <= 7, uint16_t for
-// k = 8); MK: width of the row sort (4 for k <= 4, else 8).
+// k = 8); MK: width of the row sort (k for k <= 4, else 8).  Each segment's
+// field is written by one lane at a time, so covers are plain loads and
+// stores: the cover of row (v, c) saves every neighbour's field before
+// clearing bit c, and the undo writes the saved fields back.
 template <typename FT, int MK>
 struct Search {
   static constexpr uint32_t FB = 8 * sizeof(FT);   // bits per field
   static constexpr uint32_t FLAG = 1u << (FB - 1);  // column P_v uncovered
-  static constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
 
   FT *rows;        // activeRows fields
-  FT *oldf;        // field of v before its row was covered
+  FT *oldf;        // field of v before its first row was covered
+  FT *savf;        // neighbour fields saved by the cover of v's row
   int8_t *x;
-  uint8_t *clrb;
-  uint4 *lv;       // {g, v | tried << 16, order, inc of row 1}
+  uint4 *lv;       // {g, v | rows tried << 16, order, inc of row 1}
   int32_t *lvx;    // inc of rows 2.. per level (MK entries per level)
   const int2 *ptr; // {conflict offset, stitch offset} per segment
   const uint16_t *cnbr, *snbr;
@@ -131,66 +137,86 @@ struct Search {
   int Cc, Cs;
   uint32_t kmask;
 
-  __device__ __forceinline__ uint32_t *word_of(int v) const {
-    return reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(rows) +
-                                        (((uint32_t)v * sizeof(FT)) & ~3u));
-  }
-  __device__ __forceinline__ uint32_t shift_of(int v) const {
-    return (((uint32_t)v * sizeof(FT)) & 3u) * 8u;
-  }
-
-  // Cover row (v, c): clear v's field and bit c of every conflict neighbour;
-  // `u` is lane's neighbour (valid for lane < ce - cb, first 32 only).
-  __device__ __forceinline__ void cover(int v, int c, int cb, int ce, int u, int lane) const {
+  // First row (v, c) of v's column: save and clear v's field (column P_v
+  // and all its rows), clear bit c of every conflict neighbour (column
+  // S_{(v,u),c}), saving each neighbour's field.  `u` = lane's neighbour.
+  __device__ __forceinline__ void cover_first(int v, int c, int cb, int dc, int u,
+                                              int lane) const {
     if (lane == 0) {
-      const uint32_t sh = shift_of(v);
-      const uint32_t old = atomicAnd(word_of(v), ~(FMASK << sh));
-      oldf[v] = (FT)((old >> sh) & FMASK);
+      oldf[v] = rows[v];
+      rows[v] = 0;
       x[v] = (int8_t)c;
     }
-    for (int i = cb + lane; i < ce; i += 32) {
-      if (i >= cb + 32) u = cnbr[i];
-      const uint32_t bit = 1u << (shift_of(u) + (uint32_t)c);
-      const uint32_t old = atomicAnd(word_of(u), ~bit);
-      clrb[i] = (old & bit) ? 1 : 0;
+    const uint32_t clr = ~(1u << c);
+    if (lane < dc) {
+      const FT f = rows[u];
+      savf[cb + lane] = f;
+      rows[u] = (FT)(f & clr);
+    }
+    if (dc > 32) {
+      for (int i = cb + 32 + lane; i < cb + dc; i += 32) {
+        const int w = cnbr[i];
+        const FT f = rows[w];
+        savf[i] = f;
+        rows[w] = (FT)(f & clr);
+      }
     }
     __syncwarp();
   }
 
-  // Uncover row (v, c); leaves lane's first neighbour in `u`.
-  __device__ __forceinline__ void uncover(int v, int c, int cb, int ce, int &u, int lane) const {
-    for (int i = cb + lane; i < ce; i += 32) {
-      const int w = cnbr[i];
-      if (i < cb + 32) u = w;
-      if (clrb[i]) atomicOr(word_of(w), 1u << (shift_of(w) + (uint32_t)c));
-    }
+  // Next row (v, c) of the same column: every neighbour gets its saved
+  // field with bit c cleared (the previous row's clear is undone at once).
+  __device__ __forceinline__ void switch_row(int v, int c, int cb, int dc, int lane) const {
+    if (lane == 0) x[v] = (int8_t)c;
+    const uint32_t clr = ~(1u << c);
+    for (int i = cb + lane; i < cb + dc; i += 32) rows[cnbr[i]] = (FT)(savf[i] & clr);
+    __syncwarp();
+  }
+
+  // Every row of v's column tried: put v's field and its neighbours back.
+  __device__ __forceinline__ void restore(int v, int cb, int dc, int lane) const {
     if (lane == 0) {
-      atomicOr(word_of(v), (uint32_t)oldf[v] << shift_of(v));
+      rows[v] = oldf[v];
       x[v] = -1;
     }
+    for (int i = cb + lane; i < cb + dc; i += 32) rows[cnbr[i]] = savf[i];
     __syncwarp();
   }
 
-  // Per-mask counts of a neighbour list, packed 8 bits per mask, warp-summed.
-  __device__ __forceinline__ void count(const uint16_t *nbr, int b, int e, int lane, int &first,
+  // Per-mask counts of a neighbour list, 8 bits per mask, warp-summed.
+  // Lane's first neighbour id is left in `first`.
+  __device__ __forceinline__ void count(const uint16_t *nbr, int b, int d, int lane, int &first,
                                         uint32_t &lo, uint32_t &hi) const {
-    lo = 0;
-    hi = 0;
-    for (int base = b; base < e; base += 32) {
-      const int i = base + lane;
-      uint32_t l = 0, h = 0;
-      if (i < e) {
-        const int w = nbr[i];
-        if (base == b) first = w;
-        const int xu = x[w];
-        if (xu >= 0) {
-          if (MK == 4 || xu < 4) l = 1u << (8 * xu);
-          else h = 1u << (8 * (xu - 4));
-        }
+    uint32_t l = 0, h = 0;
+    if (lane < d) {
+      first = nbr[b + lane];
+      const int xu = x[first];
+      if (xu >= 0) {
+        if (MK <= 4 || xu < 4) l = 1u << (8 * xu);
+        else h = 1u << (8 * (xu - 4));
       }
-      lo += __reduce_add_sync(FULL, l);
-      if (MK == 8) hi += __reduce_add_sync(FULL, h);
     }
+    lo = __reduce_add_sync(FULL, l);
+    hi = (MK == 8) ? __reduce_add_sync(FULL, h) : 0u;
+    if (d > 32) {
+      for (int base = 32; base < d; base += 32) {
+        l = 0;
+        h = 0;
+        if (base + lane < d) {
+          const int xu = x[nbr[b + base + lane]];
+          if (xu >= 0) {
+            if (MK <= 4 || xu < 4) l = 1u << (8 * xu);
+            else h = 1u << (8 * (xu - 4));
+          }
+        }
+        lo += __reduce_add_sync(FULL, l);
+        if (MK == 8) hi += __reduce_add_sync(FULL, h);
+      }
+    }
+  }
+
+  __device__ __forceinline__ static uint32_t lane_of(uint32_t lo, uint32_t hi, int c) {
+    return ((c < 4) ? (lo >> (8 * c)) : (hi >> (8 * (c - 4)))) & 0xFFu;
   }
 
   __device__ __forceinline__ int run(int lane, int64_t budget, int64_t time_limit_ns,
@@ -198,6 +224,7 @@ struct Search {
                                      int64_t &work_out) const {
     int32_t best = INF32, g = 0;
     int64_t nodes = 0, work = 0;
+    uint32_t work32 = 0;
     int level = 0;
     int status = MPLD_OK;
     const uint64_t t0 = globaltimer();
@@ -207,20 +234,23 @@ struct Search {
         // ---- a node: one call of the recursive search ----
         if (budget > 0 && best < INF32 && nodes >= budget) { status = MPLD_BUDGET; break; }
         ++nodes;
-        work += 2 * (int64_t)(n - level);
+        work32 += 2u * (uint32_t)(n - level);
         if ((nodes & 1023) == 0) {
+          work += work32;
+          work32 = 0;
           uint64_t now = lane == 0 ? globaltimer() : 0;
           now = __shfl_sync(FULL, now, 0);
           if ((int64_t)(now - t0) > time_limit_ns) { status = MPLD_TIMEOUT; break; }
         }
         // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v])
         uint32_t key = 0xFFFFFFFFu, z = 0;
-        for (int v = lane; v < n; v += 32) {
-          const uint32_t f = rows[v];
-          const uint32_t cnt = __popc(f & kmask);
-          const uint32_t kv = (f & FLAG) ? ((cnt << 16) | (uint32_t)v) : 0xFFFFFFFFu;
+        for (int base = 0; base < n; base += 32) {
+          const int v = base + lane;
+          const uint32_t f = v < n ? (uint32_t)rows[v] : 0u;
+          const uint32_t kv =
+              (f & FLAG) ? ((uint32_t)__popc(f & kmask) << 16) | (uint32_t)v : 0xFFFFFFFFu;
           key = min(key, kv);
-          z += kv <= 0xFFFFu;  // uncovered with no active row
+          z += kv <= 0xFFFFu;  // uncovered column with no active row
         }
         key = __reduce_min_sync(FULL, key);
         if (key == 0xFFFFFFFFu) {
@@ -240,22 +270,20 @@ struct Search {
         const int v = (int)(key & 0xFFFFu);
         // added cost of each row (v, c) against the current assignment (Eq. 1)
         const int2 p0 = ptr[v], p1 = ptr[v + 1];
+        const int dc = p1.x - p0.x, ds = p1.y - p0.y;
         int u = 0, us = 0;
-        uint32_t clo, chi, slo, shi;
-        count(cnbr, p0.x, p1.x, lane, u, clo, chi);
-        count(snbr, p0.y, p1.y, lane, us, slo, shi);
-        work += (int64_t)k * (p1.x - p0.x + p1.y - p0.y) + 5 * (1 + p1.x - p0.x);
+        uint32_t clo, chi, slo = 0, shi = 0;
+        count(cnbr, p0.x, dc, lane, u, clo, chi);
+        if (ds > 0) count(snbr, p0.y, ds, lane, us, slo, shi);
+        work32 += (uint32_t)(k * (dc + ds) + 5 * (1 + dc));
         int stot = 0;
 #pragma unroll
-        for (int c = 0; c < MK; ++c)
-          stot += (int)((((c < 4) ? (slo >> (8 * c)) : (shi >> (8 * (c - 4))))) & 0xFFu);
+        for (int c = 0; c < MK; ++c) stot += (int)lane_of(slo, shi, c);
         uint32_t keys[MK];
 #pragma unroll
         for (int c = 0; c < MK; ++c) {
-          const int cc = (int)((((c < 4) ? (clo >> (8 * c)) : (chi >> (8 * (c - 4))))) & 0xFFu);
-          const int sc = (int)((((c < 4) ? (slo >> (8 * c)) : (shi >> (8 * (c - 4))))) & 0xFFu);
-          const uint32_t inc = (uint32_t)(Cc * cc + Cs * (stot - sc));
-          keys[c] = c < k ? ((inc << 3) | (uint32_t)c) : 0xFFFFFFFFu;
+          const int inc = Cc * (int)lane_of(clo, chi, c) + Cs * (stot - (int)lane_of(slo, shi, c));
+          keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
         }
         sort_keys<MK>(keys);
         uint32_t ord = 0;
@@ -267,32 +295,33 @@ struct Search {
           for (int i = 2; i < MK; ++i)
             if (i < k) lvx[level * MK + i] = (int32_t)(keys[i] >> 3);
         }
-        cover(v, (int)(ord & 7u), p0.x, p1.x, u, lane);
+        cover_first(v, (int)(ord & 7u), p0.x, dc, u, lane);
         g += (int32_t)(keys[0] >> 3);
         ++level;
         continue;
       }
-      // ---- backtrack: uncover the row of the level above, try its next row ----
+      // ---- backtrack: next row of the level above, or undo its column ----
       if (level == 0) break;
       --level;
       const uint4 rec = lv[level];
       const int v = (int)(rec.y & 0xFFFFu);
       const int nxt = (int)(rec.y >> 16);
-      const int2 p0 = ptr[v], p1 = ptr[v + 1];
-      int u = 0;
-      uncover(v, (int)((rec.z >> (4 * (nxt - 1))) & 7u), p0.x, p1.x, u, lane);
-      if (nxt >= k) continue;  // every row of this column tried
+      const int cb = ptr[v].x, dc = ptr[v + 1].x - cb;
+      if (nxt >= k) {  // every row of this column tried
+        restore(v, cb, dc, lane);
+        continue;
+      }
       const int c = (int)((rec.z >> (4 * nxt)) & 7u);
       g = (int32_t)rec.x + (nxt == 1 ? (int32_t)rec.w : lvx[level * MK + nxt]);
-      work += 5 * (1 + p1.x - p0.x);
+      work32 += 5u * (uint32_t)(1 + dc);
       if (lane == 0) lv[level].y = (uint32_t)v | ((uint32_t)(nxt + 1) << 16);
-      cover(v, c, p0.x, p1.x, u, lane);
+      switch_row(v, c, cb, dc, lane);
       ++level;
       enter = true;
     }
     best_out = best;
     nodes_out = nodes;
-    work_out = work;
+    work_out = work + work32;
     return status;
   }
 };
@@ -308,8 +337,8 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   Search<FT, MK> s;
   s.rows = (FT *)(base + L.rows);
   s.oldf = (FT *)(base + L.oldf);
+  s.savf = (FT *)(base + L.savf);
   s.x = (int8_t *)(base + L.x);
-  s.clrb = base + L.clrb;
   s.lv = (uint4 *)(base + L.lv);
   s.lvx = (int32_t *)(base + L.lvx);
   s.ptr = (const int2 *)(ro + R.ptr);
@@ -406,7 +435,9 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
     if (idx >= a.n_inst) break;
     const InstDesc d = a.desc[a.order ? a.order[idx] : idx];
     bool ok;
-    if (d.k <= 4) ok = run_instance<uint8_t, 4>(d, slot_off, slot_bytes, bar, phase, a, lane);
+    if (d.k == 3) ok = run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, a, lane);
+    else if (d.k == 4) ok = run_instance<uint8_t, 4>(d, slot_off, slot_bytes, bar, phase, a, lane);
+    else if (d.k == 2) ok = run_instance<uint8_t, 2>(d, slot_off, slot_bytes, bar, phase, a, lane);
     else if (d.k <= 7) ok = run_instance<uint8_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
     else ok = run_instance<uint16_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
     if (!ok) slot_bytes = 0;
