@@ -232,6 +232,70 @@ typedef struct {
 int mpld_autotune(mpld_problem *const *ps, int32_t n, const mpld_params *params, void *stream,
                   mpld_tune *best);
 
+/*
+ * Search of one instance that allocates no memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate GPU memory themselves.  Examples are a plug-in running inside
+ * a host application whose caching allocator already owns the device's
+ * memory, and a latency-bound caller that cannot accept the device-wide
+ * synchronisation cudaMalloc / cudaFree can cause.  Such a caller passes the
+ * instance and the outputs in device buffers it already has; everything
+ * else the search needs (the packed EC matrix and the search stacks) lives
+ * in one fixed array inside the library, MPLD_NOALLOC_SCRATCH_BYTES bytes,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * The instance is the whole given graph (no simplification, no split into
+ * sub-graphs), searched exactly as mpld_solve searches an instance: the same
+ * column and row order, node budget and time limit, so mask, cost and node
+ * count equal those of mpld_solve on the same graph built with
+ * MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE.
+ *
+ *   inst        host struct holding sizes and DEVICE pointers: conflict and
+ *               stitch adjacency in CSR form (ptr[n+1], nbr[ptr[n]]), both
+ *               directions of every edge, no self-loops or duplicates;
+ *   params      node_budget and time_limit_ms are used; NULL = defaults;
+ *   mask_out    DEVICE, n int8: best assignment found;
+ *   result_out  DEVICE: cost, node count and status (status MPLD_E_INVALID
+ *               if the kernel found a neighbour id out of range, a
+ *               self-loop or a bad offset; the mask is then not written);
+ *   stream      all work is enqueued on it; the call does not wait.
+ * Returns MPLD_E_INVALID for bad sizes, k or costs, MPLD_E_TOO_LARGE when the
+ * instance needs more than MPLD_NOALLOC_SCRATCH_BYTES bytes or has more than
+ * MPLD_MAX_INSTANCE_SEGMENTS segments (nothing is launched then),
+ * MPLD_E_CUDA on a failed launch.
+ *
+ * The first call on a device (the device current at the call) looks up the
+ * array's device address and sets the kernel's shared-memory limit; make
+ * that first call before any stream capture on that device.  Every call
+ * shares the one array and leaves its contents behind (each call rewrites
+ * what it reads, and clears its status word); calls whose GPU work overlaps
+ * (on different streams, or from different host threads) race on the array
+ * and give wrong results, so order them on one stream.
+ */
+#define MPLD_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+typedef struct {
+  int32_t n, k;
+  int32_t n_conf_entries;       /* conf_ptr[n] */
+  int32_t n_stitch_entries;     /* st_ptr[n] */
+  const int32_t *conf_ptr, *conf_nbr;
+  const int32_t *st_ptr, *st_nbr;
+  int32_t cost_conflict, cost_stitch;
+} mpld_device_instance;
+
+typedef struct {
+  int64_t cost;
+  int64_t nodes;
+  int32_t status;               /* MPLD_OK, MPLD_BUDGET, MPLD_TIMEOUT or MPLD_E_INVALID */
+  int32_t reserved;
+  int64_t work;                 /* as mpld_result.work */
+} mpld_instance_result;
+
+int mpld_search_instance_noalloc(const mpld_device_instance *inst, const mpld_params *params,
+                                 int8_t *mask_out, mpld_instance_result *result_out,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

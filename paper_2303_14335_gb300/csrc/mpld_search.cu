@@ -502,3 +502,190 @@ extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes) {
     return 0;
   return blocks;
 }
+
+// ---- search of one instance without allocating --------------------------
+//
+// For callers that may not allocate device memory (see
+// mpld_search_instance_noalloc in mpld.h).  The packed instance and its
+// search state live in one file-scope device array; the host half below
+// looks its device address up once per device and passes it to the kernel.
+// Layout of the array: [0, 256) status word; then the read-only block of
+// the instance; then its mutable search state.
+
+#include <mutex>
+#include <stddef.h>
+
+namespace mpld {
+namespace {
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[MPLD_NOALLOC_SCRATCH_BYTES];
+
+constexpr uint32_t NOALLOC_CTRL = 256;
+
+__host__ __device__ __forceinline__ uint32_t align256(uint32_t x) { return (x + 255u) & ~255u; }
+
+static_assert(sizeof(mpld_instance_result) == sizeof(InstResult), "result layout");
+static_assert(offsetof(mpld_instance_result, cost) == offsetof(InstResult, cost), "result layout");
+static_assert(offsetof(mpld_instance_result, nodes) == offsetof(InstResult, nodes), "result layout");
+static_assert(offsetof(mpld_instance_result, status) == offsetof(InstResult, status), "result layout");
+static_assert(offsetof(mpld_instance_result, work) == offsetof(InstResult, work), "result layout");
+
+// One warp: check and pack the caller's adjacency into the array, then run
+// the same instance search as the batched and plain kernels.
+__global__ void __launch_bounds__(32, 1)
+    mpld_noalloc_kernel(const mpld_device_instance inst, uint8_t *scratch, int8_t *mask_out,
+                        InstResult *res_out, int64_t budget, int64_t time_limit_ns,
+                        int slot_bytes) {
+  const int lane = threadIdx.x & 31;
+  const int n = inst.n, ne2 = inst.n_conf_entries, ns2 = inst.n_stitch_entries;
+  const RoLayout R = ro_layout(n, ne2, ns2);
+  uint8_t *ro = scratch + NOALLOC_CTRL;
+  uint8_t *state = ro + align256(R.bytes);
+  int32_t *err = (int32_t *)scratch;
+  if (lane == 0) *err = 0;
+  int2 *ptr = (int2 *)(ro + R.ptr);
+  uint16_t *cn = (uint16_t *)(ro + R.cnbr);
+  uint16_t *sn = (uint16_t *)(ro + R.snbr);
+  bool bad = false;
+  for (int v = lane; v <= n; v += 32) {
+    const int c0 = inst.conf_ptr[v], s0 = inst.st_ptr[v];
+    ptr[v] = make_int2(c0, s0);
+    if (c0 < 0 || c0 > ne2 || s0 < 0 || s0 > ns2) bad = true;
+    if (v == 0 && (c0 != 0 || s0 != 0)) bad = true;
+    if (v == n && (c0 != ne2 || s0 != ns2)) bad = true;
+    if (v == n || bad) continue;
+    const int c1 = inst.conf_ptr[v + 1], s1 = inst.st_ptr[v + 1];
+    if (c1 < c0 || c1 > ne2 || s1 < s0 || s1 > ns2) { bad = true; continue; }
+    int prev = -1;
+    for (int i = c0; i < c1; ++i) {   // ascending, in range, no self-loop
+      const int u = inst.conf_nbr[i];
+      if (u <= prev || u >= n || u == v) { bad = true; break; }
+      cn[i] = (uint16_t)u;
+      prev = u;
+    }
+    prev = -1;
+    for (int i = s0; i < s1; ++i) {
+      const int u = inst.st_nbr[i];
+      if (u <= prev || u >= n || u == v) { bad = true; break; }
+      sn[i] = (uint16_t)u;
+      prev = u;
+    }
+  }
+  if (__any_sync(FULL, bad)) {
+    if (lane == 0) {
+      res_out->cost = INT64_MAX;
+      res_out->nodes = 0;
+      res_out->status = MPLD_E_INVALID;
+      res_out->work = 0;
+    }
+    return;
+  }
+  // the packed block is read next by the bulk-copy engine (async proxy)
+  __threadfence();
+  asm volatile("fence.proxy.async;" ::: "memory");
+  __syncwarp();
+  uint64_t *bar = (uint64_t *)g_smem;
+  if (lane == 0) mbar_init(bar);
+  __syncwarp();
+  if (lane == 0) fence_proxy_async();
+  __syncwarp();
+  InstDesc d;
+  d.ro = ro;
+  d.scratch = state;
+  d.mask = mask_out;
+  d.res = res_out;
+  d.n = n;
+  d.pad2 = 0;
+  d.ne2 = ne2;
+  d.ns2 = ns2;
+  d.ro_bytes = (int32_t)R.bytes;
+  d.state_bytes = (int32_t)state_layout(n, ne2, inst.k).bytes;
+  d.k = inst.k;
+  d.cost_conflict = inst.cost_conflict;
+  d.cost_stitch = inst.cost_stitch;
+  d.pad0 = 0;
+  d.pad1 = 0;
+  LaunchArgs a;
+  a.desc = nullptr;
+  a.order = nullptr;
+  a.n_inst = 1;
+  a.slot_bytes = slot_bytes;
+  a.queue = nullptr;
+  a.err = err;
+  a.budget = budget;
+  a.time_limit_ns = time_limit_ns;
+  uint32_t phase = 0;
+  const uint32_t slot_off = align16(8u);
+  if (d.k == 3) run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, a, lane);
+  else if (d.k == 4) run_instance<uint8_t, 4>(d, slot_off, slot_bytes, bar, phase, a, lane);
+  else if (d.k == 2) run_instance<uint8_t, 2>(d, slot_off, slot_bytes, bar, phase, a, lane);
+  else if (d.k <= 7) run_instance<uint8_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
+  else run_instance<uint16_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
+}
+
+// Per-device set-up of the allocation-free path: the array's device address
+// and the kernel's shared-memory limit.
+struct NoallocDevice {
+  bool ready = false;
+  uint8_t *scratch = nullptr;
+  int max_slot = 0;
+};
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[64];
+
+}  // namespace
+}  // namespace mpld
+
+extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
+                                            const mpld_params *prm, int8_t *mask_out,
+                                            mpld_instance_result *result_out, void *stream) {
+  using namespace mpld;
+  if (!inst || !mask_out || !result_out || !inst->conf_ptr || !inst->st_ptr) return MPLD_E_INVALID;
+  const int n = inst->n, k = inst->k, ne2 = inst->n_conf_entries, ns2 = inst->n_stitch_entries;
+  if (n < 1 || k < 2 || k > 8 || ne2 < 0 || ns2 < 0) return MPLD_E_INVALID;
+  if ((ne2 > 0 && !inst->conf_nbr) || (ns2 > 0 && !inst->st_nbr)) return MPLD_E_INVALID;
+  if (inst->cost_conflict < 0 || inst->cost_conflict > 10000 || inst->cost_stitch < 0 ||
+      inst->cost_stitch > 10000)
+    return MPLD_E_INVALID;
+  if (n > MPLD_MAX_INSTANCE_SEGMENTS) return MPLD_E_TOO_LARGE;
+  // row keys and path costs are 32-bit in the kernel (bound without degrees)
+  if ((int64_t)inst->cost_conflict * ne2 + (int64_t)inst->cost_stitch * ns2 >= ((int64_t)1 << 28))
+    return MPLD_E_TOO_LARGE;
+  const RoLayout R = ro_layout(n, ne2, ns2);
+  const StateLayout L = state_layout(n, ne2, k);
+  if ((uint64_t)NOALLOC_CTRL + align256(R.bytes) + L.bytes > (uint64_t)MPLD_NOALLOC_SCRATCH_BYTES)
+    return MPLD_E_TOO_LARGE;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MPLD_E_CUDA;
+  NoallocDevice *nd;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    nd = &g_noalloc_dev[dev];
+    if (!nd->ready) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return MPLD_E_CUDA;
+      }
+      int optin = 0;
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+              cudaSuccess ||
+          cudaFuncSetAttribute(mpld_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin) != cudaSuccess) {
+        cudaGetLastError();
+        return MPLD_E_CUDA;
+      }
+      nd->scratch = (uint8_t *)p;
+      nd->max_slot = (optin - (int)align16(8u)) & ~15;
+      nd->ready = true;
+    }
+  }
+  const uint32_t fp = align16(L.bytes + R.bytes);
+  const int slot = (int)fp <= nd->max_slot ? (int)fp : 0;   // else state stays in the array
+  const int64_t budget = prm ? (prm->node_budget > 0 ? prm->node_budget : 0) : 0;
+  const int64_t tl = (prm && prm->time_limit_ms > 0 ? prm->time_limit_ms : 60000) * 1000000ll;
+  mpld_noalloc_kernel<<<1, 32, align16(8u) + (size_t)slot, (cudaStream_t)stream>>>(
+      *inst, nd->scratch, mask_out, reinterpret_cast<InstResult *>(result_out), budget, tl, slot);
+  return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
+}

@@ -64,6 +64,12 @@ class mpld_info(ctypes.Structure):
                 ("instance_segments", _i64)]
 
 
+class mpld_device_instance(ctypes.Structure):
+    _fields_ = [("n", _i32), ("k", _i32), ("n_conf_entries", _i32), ("n_stitch_entries", _i32),
+                ("conf_ptr", _P), ("conf_nbr", _P), ("st_ptr", _P), ("st_nbr", _P),
+                ("cost_conflict", _i32), ("cost_stitch", _i32)]
+
+
 class mpld_tune(ctypes.Structure):
     _fields_ = [("warps_per_cta", _i32), ("slot_bytes", _i32), ("ctas_per_sm", _i32),
                 ("n_instances_spilled", _i32), ("ms", ctypes.c_float)]
@@ -86,7 +92,11 @@ _SIGS = {
     "mpld_export_matrix": ([_P, _i32, _P, _P], _i32),
     "mpld_autotune": ([ctypes.POINTER(_P), _i32, ctypes.POINTER(mpld_params), _P,
                        ctypes.POINTER(mpld_tune)], _i32),
+    "mpld_search_instance_noalloc": ([ctypes.POINTER(mpld_device_instance),
+                                      ctypes.POINTER(mpld_params), _P, _P, _P], _i32),
 }
+
+MPLD_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 _lib = None
 
@@ -250,6 +260,30 @@ def mpld_autotune(ps, params: mpld_params | None = None, stream: int = 0) -> mpl
     _check(library().mpld_autotune(hs, len(ps), ctypes.byref(prm), _P(stream), ctypes.byref(t)),
            "mpld_autotune")
     return t
+
+
+def mpld_search_instance_noalloc(n: int, k: int, conf_ptr: int, conf_nbr: int, n_conf_entries: int,
+                                 st_ptr: int, st_nbr: int, n_stitch_entries: int, mask_out: int,
+                                 result_out: int, params: mpld_params | None = None,
+                                 stream: int = 0, cost_conflict: int = 10,
+                                 cost_stitch: int = 1) -> int:
+    """Allocation-free search of one instance given in device CSR buffers.
+
+    Every pointer is a device address the caller owns (for example
+    ``tensor.data_ptr()``): int32 CSR offsets and neighbours of the conflict
+    and stitch adjacency, an int8 mask buffer of n entries and a 32-byte
+    result record (int64 cost, int64 nodes, int32 status, int32 unused,
+    int64 work).  The library allocates nothing: its packed copy of the
+    instance and the search stacks live in a fixed array inside the
+    library.  Enqueues on ``stream`` and returns without waiting.
+    """
+    inst = mpld_device_instance(n, k, n_conf_entries, n_stitch_entries, _P(conf_ptr),
+                                _P(conf_nbr) if conf_nbr else None, _P(st_ptr),
+                                _P(st_nbr) if st_nbr else None, cost_conflict, cost_stitch)
+    prm = params if params is not None else make_params()
+    return _check(library().mpld_search_instance_noalloc(ctypes.byref(inst), ctypes.byref(prm),
+                                                          _P(mask_out), _P(result_out), _P(stream)),
+                  "mpld_search_instance_noalloc")
 
 
 class Problem:
