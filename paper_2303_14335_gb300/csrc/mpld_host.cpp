@@ -27,6 +27,7 @@
 
 #include "../../include/mpld.h"
 #include "mpld_internal.h"
+#include "mpld_problem.h"
 
 using mpld::InstDesc;
 using mpld::InstResult;
@@ -36,68 +37,13 @@ namespace {
 constexpr int MAX_COST = 10000;
 constexpr int64_t DEFAULT_TIME_LIMIT_MS = 60000;
 
-struct GraphKey {
-  int nw = 0, slot = 0, ctas = 0;
-  int64_t budget = 0, tl = 0;
-  bool operator==(const GraphKey &o) const {
-    return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl;
-  }
-};
+using mpld::GraphKey;
 
 struct Shape {
   int nw, slot, ctas;
 };
 
 }  // namespace
-
-struct mpld_problem {
-  int n_seg = 0, k = 0;
-  int64_t Cc = 10, Cs = 1;
-  uint32_t flags = 0;
-  // normalised input
-  std::vector<int32_t> cu, cv, su, sv;
-  std::vector<int32_t> cptr, cadj;  // global conflict adjacency
-  // simplification
-  std::vector<int32_t> unit_of, uptr, useg, removed_order;
-  int64_t n_removed_segments = 0;
-  // sub-graphs (search instances)
-  int n_comp = 0;
-  std::vector<int32_t> comp_ptr, comp_seg, comp_of;
-  std::vector<int32_t> inst_ne2;
-  int max_component = 0;
-  int64_t instance_segments = 0;
-  // packed instances
-  std::vector<uint8_t> h_arena;        // host copy of the read-only blocks
-  std::vector<uint64_t> ro_off;
-  std::vector<uint32_t> footprint;     // state + read-only bytes
-  std::vector<InstDesc> h_desc;
-  std::vector<int32_t> h_order;        // largest first
-  // device memory: one allocation
-  uint8_t *d_base = nullptr;
-  size_t d_bytes = 0;
-  uint8_t *d_arena = nullptr, *d_scratch = nullptr;
-  size_t arena_bytes = 0, scratch_bytes = 0;
-  InstDesc *d_desc = nullptr;
-  int32_t *d_order = nullptr;
-  InstResult *d_res = nullptr;
-  int8_t *d_masks = nullptr;
-  uint32_t *d_queue = nullptr;
-  int32_t *d_err = nullptr;
-  // pinned host mirrors of the results
-  InstResult *h_res = nullptr;
-  int8_t *h_masks = nullptr;
-  int32_t *h_err = nullptr;
-  size_t mask_bytes = 0;
-  bool searched = false;      // a search was enqueued since the last fetch
-  bool have_results = false;  // a fetch completed
-  bool results_copied = false;  // the enqueued work already copies results back
-  std::vector<int64_t> r_nodes, r_cost;
-  std::vector<int32_t> r_status;
-  // captured launch sequence
-  cudaGraphExec_t gexec = nullptr;
-  GraphKey gkey;
-  void *gstream = nullptr;
-};
 
 namespace {
 
@@ -589,8 +535,11 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   return cuda_ok(cudaGraphLaunch(p->gexec, st));
 }
 
-// Host side after the results are in pinned memory: scatter, recover, count.
-int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
+}  // namespace
+
+// Host side after the results are in host memory: scatter, recover, count.
+int mpld_internal_finish(mpld_problem *p, const InstResult *hres, const int8_t *hmasks,
+                         int32_t err, int8_t *mask_out, mpld_result *res) {
   const int C = p->n_comp;
   p->r_nodes.resize((size_t)C);
   p->r_cost.resize((size_t)C);
@@ -598,7 +547,7 @@ int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
   int status = MPLD_OK, nbud = 0;
   int64_t nodes = 0, csum = 0, work = 0;
   for (int c = 0; c < C; ++c) {
-    const InstResult &r = p->h_res[c];
+    const InstResult &r = hres[c];
     p->r_nodes[c] = r.nodes;
     p->r_cost[c] = r.cost;
     p->r_status[c] = r.status;
@@ -611,7 +560,7 @@ int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
   p->have_results = true;
   std::vector<int8_t> m((size_t)p->n_seg, (int8_t)-1);
   for (int c = 0; c < C; ++c)
-    for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) m[p->comp_seg[t]] = p->h_masks[t];
+    for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) m[p->comp_seg[t]] = hmasks[t];
   // recovery: reverse removal order, lowest mask unused by coloured neighbours
   for (auto it = p->removed_order.rbegin(); it != p->removed_order.rend(); ++it) {
     const int u = *it;
@@ -646,8 +595,14 @@ int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
     res->n_budget_components = nbud;
     res->work = work;
   }
-  if (*p->h_err) return *p->h_err;
+  if (err) return err;
   return status;
+}
+
+namespace {
+
+int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
+  return mpld_internal_finish(p, p->h_res, p->h_masks, *p->h_err, mask_out, res);
 }
 
 }  // namespace

@@ -73,7 +73,7 @@ MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
 
 // One search instance, as the kernel sees it (absolute device pointers so
 // that instances of several problems can share one launch).
-struct InstDesc {
+struct __align__(16) InstDesc {
   const uint8_t *ro;       // read-only block (16-byte aligned)
   uint8_t *scratch;        // global state region (state_bytes), used when spilled
   int8_t *mask;            // n bytes: best assignment found
@@ -82,7 +82,7 @@ struct InstDesc {
   int32_t ro_bytes, state_bytes;
   int32_t k, cost_conflict;
   int32_t cost_stitch, pad0;
-  int64_t pad1;
+  uint32_t *done;          // serving: request's completion counter (host-mapped), else NULL
 };
 
 struct InstResult {
@@ -109,6 +109,21 @@ struct LaunchArgs {
   int64_t time_limit_ns;
 };
 
+// Resident serving kernel: warps claim instances from a device ring that the
+// host appends to, until told to stop or idle for idle_ns.
+struct ServeArgs {
+  const InstDesc *ring;         // ring of instance descriptors (device)
+  uint32_t cap;                 // ring capacity
+  int32_t slot_bytes;
+  uint32_t *head;               // next ring index to claim (device)
+  const uint32_t *tail;         // one past the last published index (device, host-written)
+  const uint32_t *stop;         // host-mapped stop flag
+  int32_t *err;                 // device status word
+  int64_t budget;
+  int64_t time_limit_ns;
+  int64_t idle_ns;
+};
+
 }  // namespace mpld
 
 // Host-side launch wrappers implemented in mpld_search.cu.
@@ -117,3 +132,5 @@ extern "C" int mpld_internal_launch(const mpld::LaunchArgs *a, int ctas, int war
 extern "C" int mpld_internal_max_slot_bytes(int warps_per_cta);
 extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes);
 extern "C" int mpld_internal_num_sms(void);
+extern "C" int mpld_internal_serve_launch(const mpld::ServeArgs *a, int ctas, int warps_per_cta,
+                                          void *stream);

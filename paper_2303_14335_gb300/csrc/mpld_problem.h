@@ -1,0 +1,80 @@
+// mpld_problem.h -- the problem handle of libmpld, shared by the host
+// builder / launcher (mpld_host.cpp) and the serving loop (mpld_serve.cpp).
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/mpld.h"
+#include "mpld_internal.h"
+
+namespace mpld {
+
+struct GraphKey {
+  int nw = 0, slot = 0, ctas = 0;
+  int64_t budget = 0, tl = 0;
+  bool operator==(const GraphKey &o) const {
+    return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl;
+  }
+};
+
+}  // namespace mpld
+
+struct mpld_problem {
+  int n_seg = 0, k = 0;
+  int64_t Cc = 10, Cs = 1;
+  uint32_t flags = 0;
+  // normalised input
+  std::vector<int32_t> cu, cv, su, sv;
+  std::vector<int32_t> cptr, cadj;  // global conflict adjacency
+  // simplification
+  std::vector<int32_t> unit_of, uptr, useg, removed_order;
+  int64_t n_removed_segments = 0;
+  // sub-graphs (search instances)
+  int n_comp = 0;
+  std::vector<int32_t> comp_ptr, comp_seg, comp_of;
+  std::vector<int32_t> inst_ne2;
+  int max_component = 0;
+  int64_t instance_segments = 0;
+  // packed instances
+  std::vector<uint8_t> h_arena;        // host copy of the read-only blocks
+  std::vector<uint64_t> ro_off;
+  std::vector<uint32_t> footprint;     // state + read-only bytes
+  std::vector<mpld::InstDesc> h_desc;  // sizes filled; device pointers only when uploaded
+  std::vector<int32_t> h_order;        // largest first
+  // device memory: one allocation
+  uint8_t *d_base = nullptr;
+  size_t d_bytes = 0;
+  uint8_t *d_arena = nullptr, *d_scratch = nullptr;
+  size_t arena_bytes = 0, scratch_bytes = 0;
+  mpld::InstDesc *d_desc = nullptr;
+  int32_t *d_order = nullptr;
+  mpld::InstResult *d_res = nullptr;
+  int8_t *d_masks = nullptr;
+  uint32_t *d_queue = nullptr;
+  int32_t *d_err = nullptr;
+  // pinned host mirrors of the results
+  mpld::InstResult *h_res = nullptr;
+  int8_t *h_masks = nullptr;
+  int32_t *h_err = nullptr;
+  size_t mask_bytes = 0;
+  bool searched = false;      // a search was enqueued since the last fetch
+  bool have_results = false;  // a fetch completed
+  bool results_copied = false;  // the enqueued work already copies results back
+  std::vector<int64_t> r_nodes, r_cost;
+  std::vector<int32_t> r_status;
+  // captured launch sequence
+  cudaGraphExec_t gexec = nullptr;
+  mpld::GraphKey gkey;
+  void *gstream = nullptr;
+};
+
+// Scatter per-instance results (instance order) into the layout, recover
+// the removed segments, count conflicts and stitches; `err` is the device
+// status word of the search.
+int mpld_internal_finish(mpld_problem *p, const mpld::InstResult *res, const int8_t *masks,
+                         int32_t err, int8_t *mask_out, mpld_result *out);

@@ -70,6 +70,22 @@ class mpld_device_instance(ctypes.Structure):
                 ("cost_conflict", _i32), ("cost_stitch", _i32)]
 
 
+class mpld_server_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", _i64), ("result_pool_bytes", _i64), ("ring_capacity", _i32),
+                ("warps_per_cta", _i32), ("slot_bytes", _i32), ("worker_threads", _i32),
+                ("idle_exit_ms", _i64)]
+
+
+class mpld_server_stats(ctypes.Structure):
+    _fields_ = [(f, _i64) for f in ("submitted", "built", "admitted", "completed", "failed",
+                                    "waiting", "in_flight", "arena_used_bytes",
+                                    "arena_peak_bytes", "instances_published", "instances_done",
+                                    "kernel_launches")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class mpld_tune(ctypes.Structure):
     _fields_ = [("warps_per_cta", _i32), ("slot_bytes", _i32), ("ctas_per_sm", _i32),
                 ("n_instances_spilled", _i32), ("ms", ctypes.c_float)]
@@ -94,6 +110,14 @@ _SIGS = {
                        ctypes.POINTER(mpld_tune)], _i32),
     "mpld_search_instance_noalloc": ([ctypes.POINTER(mpld_device_instance),
                                       ctypes.POINTER(mpld_params), _P, _P, _P], _i32),
+    "mpld_server_create": ([ctypes.POINTER(mpld_server_config), ctypes.POINTER(mpld_params),
+                            ctypes.POINTER(_P)], _i32),
+    "mpld_server_submit": ([_P, ctypes.POINTER(mpld_graph), ctypes.c_uint32,
+                            ctypes.POINTER(_i64)], _i32),
+    "mpld_server_poll": ([_P, _P, _i32, ctypes.POINTER(_i32)], _i32),
+    "mpld_server_result": ([_P, _i64, _P, ctypes.POINTER(mpld_result)], _i32),
+    "mpld_server_stats_get": ([_P, ctypes.POINTER(mpld_server_stats)], _i32),
+    "mpld_server_destroy": ([_P], None),
 }
 
 MPLD_NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -284,6 +308,90 @@ def mpld_search_instance_noalloc(n: int, k: int, conf_ptr: int, conf_nbr: int, n
     return _check(library().mpld_search_instance_noalloc(ctypes.byref(inst), ctypes.byref(prm),
                                                           _P(mask_out), _P(result_out), _P(stream)),
                   "mpld_search_instance_noalloc")
+
+
+def _graph_struct(layout):
+    keep = dict(cu=_arr(layout.conf_u), cv=_arr(layout.conf_v), su=_arr(layout.st_u),
+                sv=_arr(layout.st_v))
+    poly = getattr(layout, "polygon_of", None)
+    keep["poly"] = _arr(poly) if poly is not None else None
+    g = mpld_graph(int(layout.n_seg), int(layout.k), len(keep["cu"]), _ptr(keep["cu"]),
+                   _ptr(keep["cv"]), len(keep["su"]), _ptr(keep["su"]), _ptr(keep["sv"]),
+                   _ptr(keep["poly"]), int(getattr(layout, "cost_conflict", 10)),
+                   int(getattr(layout, "cost_stitch", 1)))
+    return g, keep
+
+
+def mpld_server_create(config: mpld_server_config | None = None,
+                       search: mpld_params | None = None) -> "Server":
+    """Start a server (device arena, ring, pinned result pool, workers)."""
+    h = _P()
+    cfg = config if config is not None else mpld_server_config()
+    prm = search if search is not None else make_params()
+    _check(library().mpld_server_create(ctypes.byref(cfg), ctypes.byref(prm), ctypes.byref(h)),
+           "mpld_server_create")
+    return Server(h)
+
+
+def mpld_server_submit(server: "Server", layout, flags: int = 0) -> int:
+    g, keep = _graph_struct(layout)
+    t = _i64()
+    _check(library().mpld_server_submit(server.handle, ctypes.byref(g), flags, ctypes.byref(t)),
+           "mpld_server_submit")
+    server.n_seg[t.value] = int(layout.n_seg)
+    return t.value
+
+
+def mpld_server_poll(server: "Server", max_done: int = 1024) -> list:
+    buf = (_i64 * max(max_done, 1))()
+    n = _i32()
+    _check(library().mpld_server_poll(server.handle, ctypes.cast(buf, _P), max_done, ctypes.byref(n)),
+           "mpld_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def mpld_server_result(server: "Server", ticket: int):
+    """(status or error code, masks, result) of a finished ticket; releases it."""
+    n = server.n_seg.pop(ticket, 0)
+    mask = np.empty(max(n, 1), dtype=np.int8)
+    res = mpld_result()
+    rc = library().mpld_server_result(server.handle, ticket, _ptr(mask), ctypes.byref(res))
+    return rc, mask[:n], res
+
+
+def mpld_server_stats_get(server: "Server") -> mpld_server_stats:
+    st = mpld_server_stats()
+    _check(library().mpld_server_stats_get(server.handle, ctypes.byref(st)), "mpld_server_stats_get")
+    return st
+
+
+def mpld_server_destroy(server: "Server") -> None:
+    server.close()
+
+
+class Server:
+    """Owning wrapper of an ``mpld_server*``."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.n_seg = {}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            library().mpld_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Problem:

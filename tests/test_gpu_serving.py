@@ -1,0 +1,130 @@
+"""Serving loop: continuous batching of whole layouts (resident search kernel).
+
+Each request's result in the mix must equal its result alone (batched path,
+same node budget) and the oracle's, bit for bit: masks, cost, node count.
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_14335_gb300 import mpld, synth
+
+pytestmark = pytest.mark.gpu
+
+BUDGET = 3000
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def requests(n, seed=77, n_max=20000):
+    return [synth.serving_request(seed, i, n_min=500, n_max=n_max) for i in range(n)]
+
+
+def alone(L, stream):
+    prob = mpld.mpld_build_matrix(L, None, stream)
+    rc, masks, res = mpld.mpld_solve_batch([prob], mpld.make_params(node_budget=BUDGET), stream)
+    prob.close()
+    return rc, masks[0], res[0]
+
+
+def drain(server, tickets, timeout=300.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in mpld.mpld_server_poll(server):
+            out[t] = mpld.mpld_server_result(server, t)
+        if time.time() - t0 > timeout:
+            raise TimeoutError(f"{len(out)}/{len(tickets)} requests finished")
+        time.sleep(0.0005)
+    return out
+
+
+def test_mix_equals_alone_and_oracle(torch_cuda):
+    stream = torch_cuda.cuda.Stream().cuda_stream
+    Ls = requests(14)
+    cfg = mpld.mpld_server_config(arena_bytes=3 << 20, ring_capacity=1 << 14)  # forces waiting
+    with mpld.mpld_server_create(cfg, mpld.make_params(node_budget=BUDGET)) as srv:
+        tickets = [mpld.mpld_server_submit(srv, L) for L in Ls]
+        got = drain(srv, tickets)
+        st = mpld.mpld_server_stats_get(srv)
+    assert st.completed == len(Ls) and st.failed == 0
+    assert st.arena_peak_bytes <= 3 << 20
+    for t, L in zip(tickets, Ls):
+        rc, mask, res = got[t]
+        rc1, mask1, res1 = alone(L, stream)
+        assert rc == rc1 and np.array_equal(mask, mask1)
+        assert (res.cost, res.nodes, res.n_conflicts, res.n_stitches) == \
+            (res1.cost, res1.nodes, res1.n_conflicts, res1.n_stitches)
+    for t, L in list(zip(tickets, Ls))[:5]:
+        ref = oracle.decompose(L, budget=BUDGET, nthreads=NTHREADS)
+        rc, mask, res = got[t]
+        assert np.array_equal(mask, ref.mask) and res.nodes == ref.nodes and res.cost == ref.cost
+
+
+def test_staggered_arrivals_overlap(torch_cuda):
+    stream = torch_cuda.cuda.Stream().cuda_stream
+    Ls = requests(10, seed=78)
+    with mpld.mpld_server_create(None, mpld.make_params(node_budget=BUDGET)) as srv:
+        tickets, got = [], {}
+        for L in Ls:                 # submit while earlier requests are in flight
+            tickets.append(mpld.mpld_server_submit(srv, L))
+            for t in mpld.mpld_server_poll(srv):
+                got[t] = mpld.mpld_server_result(srv, t)
+            time.sleep(0.002)
+        rest = [t for t in tickets if t not in got]
+        got.update(drain(srv, rest))
+    for t, L in zip(tickets, Ls):
+        rc, mask, res = got[t]
+        rc1, mask1, res1 = alone(L, stream)
+        assert np.array_equal(mask, mask1) and res.nodes == res1.nodes
+
+
+def test_bad_and_oversized_requests_fail_alone(torch_cuda):
+    good = requests(3, seed=79)
+    bad = synth.graph_from_edges(4, 3, [(0, 1), (1, 2)])
+    bad.conf_v = np.array([0, 2], dtype=np.int32)          # self-loop (0, 0)
+    big = synth.unit_disk_layout(60000, 3, seed=5, mean_deg=4.5, p_stitch=0.2)
+    cfg = mpld.mpld_server_config(arena_bytes=1 << 20)
+    with mpld.mpld_server_create(cfg, mpld.make_params(node_budget=BUDGET)) as srv:
+        tb = mpld.mpld_server_submit(srv, bad)
+        tg = [mpld.mpld_server_submit(srv, L) for L in good]
+        tl = mpld.mpld_server_submit(srv, big)
+        got = drain(srv, [tb, tl] + tg)
+    assert got[tb][0] == mpld.MPLD_E_INVALID
+    assert got[tl][0] == mpld.MPLD_E_TOO_LARGE
+    for t in tg:
+        assert got[t][0] >= 0
+
+
+def test_idle_exit_and_relaunch(torch_cuda):
+    cfg = mpld.mpld_server_config(idle_exit_ms=20)
+    Ls = requests(2, seed=80)
+    with mpld.mpld_server_create(cfg, mpld.make_params(node_budget=BUDGET)) as srv:
+        t1 = mpld.mpld_server_submit(srv, Ls[0])
+        got = drain(srv, [t1])
+        time.sleep(0.2)              # the resident kernel leaves after 20 ms idle
+        t2 = mpld.mpld_server_submit(srv, Ls[1])
+        got.update(drain(srv, [t2]))
+        st = mpld.mpld_server_stats_get(srv)
+    assert st.kernel_launches >= 2 and st.completed == 2
+    assert got[t1][0] >= 0 and got[t2][0] >= 0
+
+
+def test_empty_and_fully_simplified_requests(torch_cuda):
+    with mpld.mpld_server_create(None, mpld.make_params(node_budget=BUDGET)) as srv:
+        t0 = mpld.mpld_server_submit(srv, synth.graph_from_edges(0, 3, []))
+        t1 = mpld.mpld_server_submit(srv, synth.graph_from_edges(6, 3, [(0, 1), (2, 3)]))
+        got = drain(srv, [t0, t1])
+    assert got[t0][0] == 0 and got[t0][2].n_components == 0
+    rc, mask, res = got[t1]
+    assert rc == 0 and res.cost == 0 and res.n_removed_segments == 6 and np.all(mask >= 0)
