@@ -120,7 +120,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // field is written by one lane at a time, so covers are plain loads and
 // stores: the cover of row (v, c) saves every neighbour's field before
 // clearing bit c, and the undo writes the saved fields back.
-template <typename FT, int MK>
+// Read-only data (adjacency) of an instance whose block stays in global
+// memory is read from L2: arena regions are reused while a resident grid
+// runs, and an SM's L1 may still hold lines of an earlier occupant.
+template <bool SM, typename T>
+__device__ __forceinline__ T ro_ld(const T *p) {
+  if constexpr (SM) return *p;
+  else return __ldcg(p);
+}
+
+template <typename FT, int MK, bool SM>
 struct Search {
   static constexpr uint32_t FB = 8 * sizeof(FT);   // bits per field
   static constexpr uint32_t FLAG = 1u << (FB - 1);  // column P_v uncovered
@@ -155,7 +164,7 @@ struct Search {
     }
     if (dc > 32) {
       for (int i = cb + 32 + lane; i < cb + dc; i += 32) {
-        const int w = cnbr[i];
+        const int w = ro_ld<SM>(cnbr + i);
         const FT f = rows[w];
         savf[i] = f;
         rows[w] = (FT)(f & clr);
@@ -169,7 +178,7 @@ struct Search {
   __device__ __forceinline__ void switch_row(int v, int c, int cb, int dc, int lane) const {
     if (lane == 0) x[v] = (int8_t)c;
     const uint32_t clr = ~(1u << c);
-    for (int i = cb + lane; i < cb + dc; i += 32) rows[cnbr[i]] = (FT)(savf[i] & clr);
+    for (int i = cb + lane; i < cb + dc; i += 32) rows[ro_ld<SM>(cnbr + i)] = (FT)(savf[i] & clr);
     __syncwarp();
   }
 
@@ -179,7 +188,7 @@ struct Search {
       rows[v] = oldf[v];
       x[v] = -1;
     }
-    for (int i = cb + lane; i < cb + dc; i += 32) rows[cnbr[i]] = savf[i];
+    for (int i = cb + lane; i < cb + dc; i += 32) rows[ro_ld<SM>(cnbr + i)] = savf[i];
     __syncwarp();
   }
 
@@ -189,7 +198,7 @@ struct Search {
                                         uint32_t &lo, uint32_t &hi) const {
     uint32_t l = 0, h = 0;
     if (lane < d) {
-      first = nbr[b + lane];
+      first = ro_ld<SM>(nbr + b + lane);
       const int xu = x[first];
       if (xu >= 0) {
         if (MK <= 4 || xu < 4) l = 1u << (8 * xu);
@@ -203,7 +212,7 @@ struct Search {
         l = 0;
         h = 0;
         if (base + lane < d) {
-          const int xu = x[nbr[b + base + lane]];
+          const int xu = x[ro_ld<SM>(nbr + b + base + lane)];
           if (xu >= 0) {
             if (MK <= 4 || xu < 4) l = 1u << (8 * xu);
             else h = 1u << (8 * (xu - 4));
@@ -269,7 +278,7 @@ struct Search {
         }
         const int v = (int)(key & 0xFFFFu);
         // added cost of each row (v, c) against the current assignment (Eq. 1)
-        const int2 p0 = ptr[v], p1 = ptr[v + 1];
+        const int2 p0 = ro_ld<SM>(ptr + v), p1 = ro_ld<SM>(ptr + v + 1);
         const int dc = p1.x - p0.x, ds = p1.y - p0.y;
         int u = 0, us = 0;
         uint32_t clo, chi, slo = 0, shi = 0;
@@ -306,7 +315,7 @@ struct Search {
       const uint4 rec = lv[level];
       const int v = (int)(rec.y & 0xFFFFu);
       const int nxt = (int)(rec.y >> 16);
-      const int cb = ptr[v].x, dc = ptr[v + 1].x - cb;
+      const int cb = ro_ld<SM>(ptr + v).x, dc = ro_ld<SM>(ptr + v + 1).x - cb;
       if (nxt >= k) {  // every row of this column tried
         restore(v, cb, dc, lane);
         continue;
@@ -334,7 +343,7 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   const int n = d.n;
   const StateLayout L = state_layout(n, d.ne2, d.k);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2);
-  Search<FT, MK> s;
+  Search<FT, MK, SM> s;
   s.rows = (FT *)(base + L.rows);
   s.oldf = (FT *)(base + L.oldf);
   s.savf = (FT *)(base + L.savf);
@@ -350,7 +359,7 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   s.Cs = d.cost_stitch;
   s.kmask = (1u << d.k) - 1u;
   // initial state: every row active, every primary column uncovered
-  const FT init = (FT)(s.kmask | Search<FT, MK>::FLAG);
+  const FT init = (FT)(s.kmask | Search<FT, MK, SM>::FLAG);
   for (int i = lane; i < n; i += 32) {
     s.rows[i] = init;
     s.x[i] = -1;
@@ -403,7 +412,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
   } else {
     const uint4 *src = (const uint4 *)d.ro;
     uint4 *d4 = (uint4 *)dst;
-    for (uint32_t i = lane; i < R.bytes / 16; i += 32) d4[i] = __ldg(src + i);
+    for (uint32_t i = lane; i < R.bytes / 16; i += 32) d4[i] = __ldcg(src + i);
   }
   run_in<FT, MK, true>(d, slot, dst, a, lane);
   return true;
@@ -703,8 +712,20 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
 namespace mpld {
 namespace {
 
-__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
-  return *(const volatile uint32_t *)p;
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_sys(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 // Descriptor read that bypasses L1: ring slots are rewritten by copies
@@ -747,9 +768,9 @@ __global__ void __launch_bounds__(512, 1) mpld_serve_kernel(const ServeArgs a) {
     if (lane == 0) {
       const uint64_t idle0 = globaltimer();
       for (;;) {
-        if (ld_volatile_u32(a.stop)) break;
-        const uint32_t t = ld_volatile_u32(a.tail);
-        const uint32_t h = ld_volatile_u32(a.head);
+        if (ld_relaxed_sys(a.stop)) break;
+        const uint32_t t = ld_acquire_gpu(a.tail);
+        const uint32_t h = ld_relaxed_gpu(a.head);
         if ((int32_t)(t - h) > 0) {
           if (atomicCAS(a.head, h, h + 1u) == h) { idx = h; break; }
           continue;

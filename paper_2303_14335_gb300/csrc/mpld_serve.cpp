@@ -240,6 +240,8 @@ int admit(mpld_server *s, Req &r) {
   }
   const uint32_t cap = (uint32_t)s->cfg.ring_capacity;
   const uint64_t first = s->published;
+  const uint8_t *region_end = base + r.arena_bytes;
+  const uint8_t *pool_end = dp + r.pool_bytes;
   for (int j = 0; j < C; ++j) {
     const int c = p->h_order[j];
     InstDesc d = p->h_desc[c];
@@ -248,6 +250,11 @@ int admit(mpld_server *s, Req &r) {
     d.mask = d_masks + p->comp_ptr[c];
     d.res = d_res + c;
     d.done = d_counter;
+    // every pointer the kernel will follow stays inside this request's regions
+    if (d.ro + d.ro_bytes > state_base || d.scratch + d.state_bytes > region_end ||
+        (const uint8_t *)(d.mask + d.n) > pool_end || (const uint8_t *)(d.res + 1) > pool_end ||
+        ((uintptr_t)d.ro & 15) || ((uintptr_t)d.scratch & 15))
+      return MPLD_E_STATE;
     s->h_ring[(first + j) % cap] = d;
   }
   // copy the new ring slots (one or two pieces), then publish the tail
