@@ -670,6 +670,9 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
     rc |= cuda_ok(cudaMemcpyAsync(b + dbytes, order.data(), sizeof(int32_t) * (size_t)total,
                                   cudaMemcpyHostToDevice, st));
   }
+  // the sources are pageable vectors local to this call: wait for the copies
+  // before they go out of scope (they may be read by the GPU directly)
+  rc |= cuda_ok(cudaStreamSynchronize(st));
   uint32_t *queue = (uint32_t *)(b + dbytes + sizeof(int32_t) * (size_t)std::max(total, 1));
   mpld::LaunchArgs a;
   a.desc = (const InstDesc *)b;

@@ -271,8 +271,9 @@ int admit(mpld_server *s, Req &r) {
   *tv = (uint32_t)s->published;
   rc |= cuda_ok(cudaMemcpyAsync(s->d_ctrl + 32, tv, 4, cudaMemcpyHostToDevice, s->cstream));
   if (++s->tail_copies % (TAIL_VALUES / 2) == 0) rc |= cuda_ok(cudaStreamSynchronize(s->cstream));
-  p->h_arena.clear();
-  p->h_arena.shrink_to_fit();
+  // p->h_arena stays alive until the request is finished: an asynchronous
+  // copy from pageable memory may read it after this call returns (on
+  // systems where the GPU reads host memory directly, nothing stages it)
   r.C = C;
   return rc ? MPLD_E_CUDA : MPLD_OK;
 }
