@@ -118,7 +118,9 @@ struct ServeArgs {
   uint32_t *head;               // next ring index to claim (device)
   const uint32_t *tail;         // one past the last published index (device, host-written)
   const uint32_t *stop;         // host-mapped stop flag
-  int32_t *err;                 // device status word
+  int32_t *err;                 // host-mapped status word (0 = fine)
+  const uint8_t *arena_lo, *arena_hi;  // device arena: every ro / scratch pointer
+  const uint8_t *pool_lo, *pool_hi;    // host-mapped results: every mask / res / done pointer
   int64_t budget;
   int64_t time_limit_ns;
   int64_t idle_ns;

@@ -728,15 +728,34 @@ __device__ __forceinline__ uint32_t ld_relaxed_sys(const uint32_t *p) {
   return v;
 }
 
-// Descriptor read that bypasses L1: ring slots are rewritten by copies
-// while the grid runs.
+// Descriptor read that bypasses L1 (ring slots are rewritten by copies
+// while the grid runs); the raw words are moved into the struct with memcpy.
 __device__ __forceinline__ InstDesc load_desc_cg(const InstDesc *p) {
-  InstDesc d;
+  uint4 raw[sizeof(InstDesc) / 16];
   const uint4 *src = reinterpret_cast<const uint4 *>(p);
-  uint4 *dst = reinterpret_cast<uint4 *>(&d);
 #pragma unroll
-  for (int i = 0; i < (int)(sizeof(InstDesc) / 16); ++i) dst[i] = __ldcg(src + i);
+  for (int i = 0; i < (int)(sizeof(InstDesc) / 16); ++i) raw[i] = __ldcg(src + i);
+  InstDesc d;
+  memcpy(&d, raw, sizeof(InstDesc));
   return d;
+}
+
+// A claimed descriptor must point inside the server's arena and result pool
+// with the sizes its counts imply; anything else is recorded and skipped.
+__device__ __forceinline__ bool desc_ok(const InstDesc &d, const ServeArgs &a) {
+  if (d.n < 1 || d.n > MPLD_MAX_INSTANCE_SEGMENTS || d.k < 2 || d.k > 8 || d.ne2 < 0 ||
+      d.ns2 < 0)
+    return false;
+  const uint32_t rb = ro_layout(d.n, d.ne2, d.ns2).bytes;
+  const uint32_t sb = state_layout(d.n, d.ne2, d.k).bytes;
+  if ((uint32_t)d.ro_bytes != rb || (uint32_t)d.state_bytes != sb) return false;
+  const uint8_t *mask = (const uint8_t *)d.mask, *res = (const uint8_t *)d.res;
+  const uint8_t *done = (const uint8_t *)d.done;
+  return d.ro >= a.arena_lo && d.ro + rb <= a.arena_hi && ((uintptr_t)d.ro & 15) == 0 &&
+         d.scratch >= a.arena_lo && d.scratch + sb <= a.arena_hi &&
+         ((uintptr_t)d.scratch & 15) == 0 && mask >= a.pool_lo && mask + d.n <= a.pool_hi &&
+         res >= a.pool_lo && res + sizeof(InstResult) <= a.pool_hi && ((uintptr_t)res & 7) == 0 &&
+         done >= a.pool_lo && done + 4 <= a.pool_hi && ((uintptr_t)done & 3) == 0;
 }
 
 __global__ void __launch_bounds__(512, 1) mpld_serve_kernel(const ServeArgs a) {
@@ -782,6 +801,10 @@ __global__ void __launch_bounds__(512, 1) mpld_serve_kernel(const ServeArgs a) {
     idx = __shfl_sync(FULL, idx, 0);
     if (idx == 0xFFFFFFFFu) break;
     const InstDesc d = load_desc_cg(a.ring + (idx % a.cap));
+    if (!desc_ok(d, a)) {
+      if (lane == 0) atomicCAS_system(a.err, 0, (int32_t)(0x40000000u | (idx & 0xFFFFFFu)));
+      continue;
+    }
     bool ok;
     if (d.k == 3) ok = run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, la, lane);
     else if (d.k == 4) ok = run_instance<uint8_t, 4>(d, slot_off, slot_bytes, bar, phase, la, lane);

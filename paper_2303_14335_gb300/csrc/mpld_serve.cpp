@@ -129,7 +129,7 @@ struct mpld_server {
   // pinned host
   InstDesc *h_ring = nullptr;       // staging copy of the ring
   uint32_t *h_tail = nullptr;       // TAIL_VALUES tail values
-  uint32_t *h_stop = nullptr;       // mapped stop flag
+  uint32_t *h_stop = nullptr;       // mapped stop flag, then the kernel's status word
   uint8_t *h_pool = nullptr;        // mapped results, masks, counters
   uint8_t *d_pool = nullptr;        // device address of h_pool
   uint32_t *d_stop = nullptr;
@@ -292,7 +292,11 @@ int relaunch_if_needed(mpld_server *s) {
   a.head = s->d_ctrl;
   a.tail = s->d_ctrl + 32;
   a.stop = s->d_stop;
-  a.err = reinterpret_cast<int32_t *>(s->d_ctrl + 64);
+  a.err = reinterpret_cast<int32_t *>(s->d_stop + 8);   // host-mapped (byte 32), read by every poll
+  a.arena_lo = s->d_arena;
+  a.arena_hi = s->d_arena + s->cfg.arena_bytes;
+  a.pool_lo = s->d_pool;
+  a.pool_hi = s->d_pool + s->cfg.result_pool_bytes;
   a.budget = s->budget;
   a.time_limit_ns = s->tl_ns;
   a.idle_ns = s->idle_ns;
@@ -353,7 +357,7 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
   }
   if (cudaMallocHost((void **)&s->h_ring, ring_bytes) != cudaSuccess ||
       cudaMallocHost((void **)&s->h_tail, sizeof(uint32_t) * TAIL_VALUES) != cudaSuccess ||
-      cudaHostAlloc((void **)&s->h_stop, 64, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void **)&s->h_stop, 128, cudaHostAllocMapped) != cudaSuccess ||
       cudaHostAlloc((void **)&s->h_pool, (size_t)cfg.result_pool_bytes, cudaHostAllocMapped) !=
           cudaSuccess) {
     cudaGetLastError();
@@ -364,7 +368,7 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
     cudaGetLastError();
     return fail(MPLD_E_CUDA);
   }
-  *s->h_stop = 0;
+  std::memset(s->h_stop, 0, 128);
   rc |= cuda_ok(cudaMemsetAsync(s->d_ctrl, 0, 512, s->cstream));
   rc |= cuda_ok(cudaStreamSynchronize(s->cstream));
   if (rc) return fail(MPLD_E_CUDA);
@@ -425,6 +429,10 @@ extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
                                 int32_t *n_done) {
   if (!s || (max_done > 0 && !done)) return MPLD_E_INVALID;
   int rc = MPLD_OK;
+  // status word of the resident kernel: a descriptor it refused, or a
+  // bulk copy that did not land
+  if (__atomic_load_n(reinterpret_cast<int32_t *>(s->h_stop + 8), __ATOMIC_ACQUIRE) != 0)
+    return MPLD_E_STATE;
   // finished requests: every instance counted by the kernel
   for (size_t i = 0; i < s->inflight.size();) {
     ReqPtr r = s->inflight[i];
