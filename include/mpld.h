@@ -241,14 +241,14 @@ int mpld_autotune(mpld_problem *const *ps, int32_t n, const mpld_params *params,
  *   - mpld_server_submit copies the layout and queues it; host worker
  *     threads simplify, split and pack it (as mpld_build_matrix);
  *   - mpld_server_poll admits built layouts in submission order while their
- *     device bytes (packed matrices + search state) fit the server's arena
- *     and their instances fit the ring; it uploads them and appends their
- *     instances to a device ring read by a resident search kernel, so work
- *     of layouts admitted at different times runs side by side;
- *   - the kernel writes each instance's result and assignment into pinned
- *     host memory and counts the layout's finished instances; the poll sees
- *     finished layouts, frees their device bytes (admitting waiting ones),
- *     and workers recover the removed segments and count (Sec. 2.2);
+ *     device bytes (packed matrices, search state, descriptors, results)
+ *     fit the server's arena and fewer than max_in_flight layouts are on
+ *     the device; each admitted layout is uploaded and searched by one
+ *     persistent launch of the batched kernel on one of the server's
+ *     streams, so layouts admitted at different times run side by side;
+ *   - finished layouts (their stream passed the copy-back) give their
+ *     device bytes back, which admits waiting layouts, and worker threads
+ *     recover the removed segments and count (Sec. 2.2);
  *   - mpld_server_result hands out a finished layout's masks and counts and
  *     forgets the ticket.
  * Each layout's result equals mpld_solve_batch's on that layout alone with
@@ -260,13 +260,10 @@ typedef struct mpld_server mpld_server;
 typedef struct {
   int64_t arena_bytes;        /* device bytes for admitted layouts; 0 = 1 GiB */
   int64_t result_pool_bytes;  /* pinned host bytes for results of admitted layouts; 0 = 256 MiB */
-  int32_t ring_capacity;      /* instances published and not yet finished; 0 = 1 << 20 */
-  int32_t warps_per_cta;      /* resident kernel: warps per CTA; 0 = 4 */
-  int32_t slot_bytes;         /* shared memory per warp; 0 = 12288 (larger instances run
-                                 with their state in device memory) */
+  int32_t max_in_flight;      /* layouts on the device at once; 0 = 64 */
+  int32_t streams;            /* CUDA streams the launches rotate over; 0 = 8 */
+  int32_t warps_per_cta;      /* batched kernel shape; 0 = 4 */
   int32_t worker_threads;     /* host build / recovery threads; 0 = half the hardware threads */
-  int64_t idle_exit_ms;       /* the resident kernel leaves after this long without work
-                                 (the next poll with work relaunches it); 0 = 200 */
 } mpld_server_config;
 
 typedef struct {
@@ -274,12 +271,13 @@ typedef struct {
   int64_t waiting;            /* built, not yet admitted */
   int64_t in_flight;          /* admitted, not yet finished */
   int64_t arena_used_bytes, arena_peak_bytes;
-  int64_t instances_published, instances_done;
+  int64_t instances_launched;
   int64_t kernel_launches;
+  int64_t max_concurrent;     /* most layouts on the device at one time */
 } mpld_server_stats;
 
-/* Create a server: allocates the device arena and ring and the pinned result pool, starts the
- * worker threads, on the current device.  search: node_budget and time_limit_ms for every
+/* Create a server on the current device: allocates the device arena, the pinned result pool
+ * and the streams, starts the worker threads.  search: node_budget and time_limit_ms for every
  * instance (NULL = defaults).  Errors: MPLD_E_INVALID, MPLD_E_OOM, MPLD_E_CUDA. */
 int mpld_server_create(const mpld_server_config *cfg, const mpld_params *search,
                        mpld_server **out);
@@ -289,9 +287,9 @@ int mpld_server_create(const mpld_server_config *cfg, const mpld_params *search,
  * surface later as the ticket's result code. */
 int mpld_server_submit(mpld_server *s, const mpld_graph *graph, uint32_t flags, int64_t *ticket);
 
-/* Non-blocking progress: admit, upload, publish, relaunch the resident kernel if needed,
- * detect finished layouts.  Writes up to max_done finished tickets (any order) to `done`
- * and their number to *n_done (done may be NULL when max_done is 0). */
+/* Non-blocking progress: admit, upload, launch, detect finished layouts.  Writes up to
+ * max_done finished tickets (any order) to `done` and their number to *n_done (done may be
+ * NULL when max_done is 0). */
 int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done, int32_t *n_done);
 
 /* Result of a finished ticket: n_seg masks (host) and the counts; releases the ticket.
@@ -301,8 +299,8 @@ int mpld_server_result(mpld_server *s, int64_t ticket, int8_t *mask_out, mpld_re
 
 int mpld_server_stats_get(const mpld_server *s, mpld_server_stats *stats);
 
-/* Stop the resident kernel (bounded by the instances' time limit), join the workers and free
- * everything.  Unfinished tickets are dropped.  NULL is a no-op. */
+/* Wait for the work on the device, join the workers and free everything.  Unfinished tickets
+ * are dropped.  NULL is a no-op. */
 void mpld_server_destroy(mpld_server *s);
 
 /*

@@ -82,7 +82,7 @@ struct __align__(16) InstDesc {
   int32_t ro_bytes, state_bytes;
   int32_t k, cost_conflict;
   int32_t cost_stitch, pad0;
-  uint32_t *done;          // serving: request's completion counter (host-mapped), else NULL
+  int64_t pad1;
 };
 
 struct InstResult {
@@ -109,23 +109,6 @@ struct LaunchArgs {
   int64_t time_limit_ns;
 };
 
-// Resident serving kernel: warps claim instances from a device ring that the
-// host appends to, until told to stop or idle for idle_ns.
-struct ServeArgs {
-  const InstDesc *ring;         // ring of instance descriptors (device)
-  uint32_t cap;                 // ring capacity
-  int32_t slot_bytes;
-  uint32_t *head;               // next ring index to claim (device)
-  const uint32_t *tail;         // one past the last published index (device, host-written)
-  const uint32_t *stop;         // host-mapped stop flag
-  int32_t *err;                 // host-mapped status word (0 = fine)
-  const uint8_t *arena_lo, *arena_hi;  // device arena: every ro / scratch pointer
-  const uint8_t *pool_lo, *pool_hi;    // host-mapped results: every mask / res / done pointer
-  int64_t budget;
-  int64_t time_limit_ns;
-  int64_t idle_ns;
-};
-
 }  // namespace mpld
 
 // Host-side launch wrappers implemented in mpld_search.cu.
@@ -134,5 +117,3 @@ extern "C" int mpld_internal_launch(const mpld::LaunchArgs *a, int ctas, int war
 extern "C" int mpld_internal_max_slot_bytes(int warps_per_cta);
 extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes);
 extern "C" int mpld_internal_num_sms(void);
-extern "C" int mpld_internal_serve_launch(const mpld::ServeArgs *a, int ctas, int warps_per_cta,
-                                          void *stream);

@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(32, 1)
   d.cost_conflict = inst.cost_conflict;
   d.cost_stitch = inst.cost_stitch;
   d.pad0 = 0;
-  d.done = nullptr;
+  d.pad1 = 0;
   LaunchArgs a;
   a.desc = nullptr;
   a.order = nullptr;
@@ -696,148 +696,5 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
   const int64_t tl = (prm && prm->time_limit_ms > 0 ? prm->time_limit_ms : 60000) * 1000000ll;
   mpld_noalloc_kernel<<<1, 32, align16(8u) + (size_t)slot, (cudaStream_t)stream>>>(
       *inst, nd->scratch, mask_out, reinterpret_cast<InstResult *>(result_out), budget, tl, slot);
-  return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
-}
-
-// ---- resident serving kernel ----------------------------------------------
-//
-// Continuous batching: warps of a persistent grid claim instances from a
-// device ring of descriptors that the host keeps appending to (each
-// admitted layout's sub-graphs), search them exactly as the batched kernel
-// does, write results into host-mapped memory and count the request's
-// finished instances.  Every wait is bounded: a warp that finds no work
-// for idle_ns, or sees the stop flag, leaves; the host relaunches the grid
-// when it publishes work and finds it gone.
-
-namespace mpld {
-namespace {
-
-__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_relaxed_sys(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Descriptor read that bypasses L1 (ring slots are rewritten by copies
-// while the grid runs); the raw words are moved into the struct with memcpy.
-__device__ __forceinline__ InstDesc load_desc_cg(const InstDesc *p) {
-  uint4 raw[sizeof(InstDesc) / 16];
-  const uint4 *src = reinterpret_cast<const uint4 *>(p);
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(InstDesc) / 16); ++i) raw[i] = __ldcg(src + i);
-  InstDesc d;
-  memcpy(&d, raw, sizeof(InstDesc));
-  return d;
-}
-
-// A claimed descriptor must point inside the server's arena and result pool
-// with the sizes its counts imply; anything else is recorded and skipped.
-__device__ __forceinline__ bool desc_ok(const InstDesc &d, const ServeArgs &a) {
-  if (d.n < 1 || d.n > MPLD_MAX_INSTANCE_SEGMENTS || d.k < 2 || d.k > 8 || d.ne2 < 0 ||
-      d.ns2 < 0)
-    return false;
-  const uint32_t rb = ro_layout(d.n, d.ne2, d.ns2).bytes;
-  const uint32_t sb = state_layout(d.n, d.ne2, d.k).bytes;
-  if ((uint32_t)d.ro_bytes != rb || (uint32_t)d.state_bytes != sb) return false;
-  const uint8_t *mask = (const uint8_t *)d.mask, *res = (const uint8_t *)d.res;
-  const uint8_t *done = (const uint8_t *)d.done;
-  return d.ro >= a.arena_lo && d.ro + rb <= a.arena_hi && ((uintptr_t)d.ro & 15) == 0 &&
-         d.scratch >= a.arena_lo && d.scratch + sb <= a.arena_hi &&
-         ((uintptr_t)d.scratch & 15) == 0 && mask >= a.pool_lo && mask + d.n <= a.pool_hi &&
-         res >= a.pool_lo && res + sizeof(InstResult) <= a.pool_hi && ((uintptr_t)res & 7) == 0 &&
-         done >= a.pool_lo && done + 4 <= a.pool_hi && ((uintptr_t)done & 3) == 0;
-}
-
-__global__ void __launch_bounds__(512, 1) mpld_serve_kernel(const ServeArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  uint64_t *bars = (uint64_t *)g_smem;
-  const uint32_t bar_bytes = align16(8u * (uint32_t)nw);
-  const uint32_t slot_off = bar_bytes + (uint32_t)warp * (uint32_t)a.slot_bytes;
-  int slot_bytes = a.slot_bytes;
-  uint64_t *bar = bars + warp;
-  if (lane == 0) mbar_init(bar);
-  __syncwarp();
-  if (lane == 0) fence_proxy_async();
-  __syncwarp();
-  uint32_t phase = 0;
-  LaunchArgs la;
-  la.desc = nullptr;
-  la.order = nullptr;
-  la.n_inst = 1;
-  la.slot_bytes = a.slot_bytes;
-  la.queue = nullptr;
-  la.err = a.err;
-  la.budget = a.budget;
-  la.time_limit_ns = a.time_limit_ns;
-
-  for (;;) {
-    uint32_t idx = 0xFFFFFFFFu;
-    if (lane == 0) {
-      const uint64_t idle0 = globaltimer();
-      for (;;) {
-        if (ld_relaxed_sys(a.stop)) break;
-        const uint32_t t = ld_acquire_gpu(a.tail);
-        const uint32_t h = ld_relaxed_gpu(a.head);
-        if ((int32_t)(t - h) > 0) {
-          if (atomicCAS(a.head, h, h + 1u) == h) { idx = h; break; }
-          continue;
-        }
-        if ((int64_t)(globaltimer() - idle0) > a.idle_ns) break;
-        __nanosleep(2000);
-      }
-    }
-    idx = __shfl_sync(FULL, idx, 0);
-    if (idx == 0xFFFFFFFFu) break;
-    const InstDesc d = load_desc_cg(a.ring + (idx % a.cap));
-    if (!desc_ok(d, a)) {
-      if (lane == 0) atomicCAS_system(a.err, 0, (int32_t)(0x40000000u | (idx & 0xFFFFFFu)));
-      continue;
-    }
-    bool ok;
-    if (d.k == 3) ok = run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, la, lane);
-    else if (d.k == 4) ok = run_instance<uint8_t, 4>(d, slot_off, slot_bytes, bar, phase, la, lane);
-    else if (d.k == 2) ok = run_instance<uint8_t, 2>(d, slot_off, slot_bytes, bar, phase, la, lane);
-    else if (d.k <= 7) ok = run_instance<uint8_t, 8>(d, slot_off, slot_bytes, bar, phase, la, lane);
-    else ok = run_instance<uint16_t, 8>(d, slot_off, slot_bytes, bar, phase, la, lane);
-    if (!ok) slot_bytes = 0;
-    if (lane == 0) {
-      // results and masks (host-mapped) before the request's counter
-      __threadfence_system();
-      atomicAdd_system(d.done, 1u);
-    }
-    __syncwarp();
-  }
-}
-
-int g_serve_smem_granted = 48 * 1024;
-
-}  // namespace
-}  // namespace mpld
-
-extern "C" int mpld_internal_serve_launch(const mpld::ServeArgs *a, int ctas, int warps_per_cta,
-                                          void *stream) {
-  const size_t smem = mpld::align16(8u * (uint32_t)warps_per_cta) +
-                      (size_t)warps_per_cta * (size_t)a->slot_bytes;
-  if ((int)smem > mpld::g_serve_smem_granted) {
-    if (cudaFuncSetAttribute(mpld::mpld_serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return MPLD_E_CUDA;
-    }
-    mpld::g_serve_smem_granted = (int)smem;
-  }
-  mpld::mpld_serve_kernel<<<ctas, warps_per_cta * 32, smem, (cudaStream_t)stream>>>(*a);
   return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
 }

@@ -1,15 +1,17 @@
 // mpld_serve.cpp -- serving loop of libmpld: continuous batching of whole
-// layouts onto one resident search kernel.
+// layouts on one GPU.
 //
-// Request life: submit (copy) -> worker builds it host-side (simplify, split,
-// pack, as mpld_build_matrix) -> poll admits it in submission order when its
-// device bytes fit the arena and its instances fit the ring -> upload of the
-// packed matrices, descriptors appended to the device ring, tail published ->
-// the resident kernel searches its instances next to those of every other
-// admitted request, writing results into pinned host memory and counting
-// finished instances -> poll sees the count complete, frees the device bytes
-// (which lets waiting requests in) -> a worker recovers removed segments and
-// counts (Sec. 2.2) -> mpld_server_result hands the masks out.
+// Request life: submit (copy) -> a worker builds it host-side (simplify,
+// split, pack, as mpld_build_matrix) -> poll admits it in submission order
+// when its device bytes fit the arena and fewer than max_in_flight layouts
+// are on the device -> on one of the server's streams: upload, one
+// persistent launch of the batched search kernel over its instances, copy of
+// the results into pinned memory, an event -> poll sees the event, returns
+// the device bytes (admitting waiting layouts) -> a worker recovers the
+// removed segments and counts (Sec. 2.2) -> mpld_server_result hands the
+// masks out.  Launches of layouts admitted at different times run side by
+// side on the device; each is the same kernel and search as
+// mpld_solve_batch, so results do not depend on the mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +34,6 @@ using mpld::InstResult;
 namespace {
 
 constexpr uint64_t ALIGN = 256;
-constexpr uint32_t TAIL_VALUES = 4096;  // pinned sources of in-flight tail copies
 
 uint64_t round_up(uint64_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
@@ -85,6 +86,34 @@ class FirstFit {
 
 enum class State { Building, Built, Admitted, Finishing, Done };
 
+// Byte layout of one admitted layout in the device arena and in the pinned
+// result pool (256-byte aligned sections).
+struct Sections {
+  uint64_t ro, state, desc, order, res, masks, ctrl, total;   // device
+  uint64_t h_res, h_masks, h_err, h_total;                    // pinned
+};
+
+Sections sections_of(const mpld_problem *p) {
+  const uint64_t C = (uint64_t)std::max(p->n_comp, 1);
+  const uint64_t segs = (uint64_t)std::max<int64_t>(p->instance_segments, 1);
+  Sections S;
+  uint64_t o = 0;
+  S.ro = o; o += round_up(std::max<uint64_t>(p->arena_bytes, 16));
+  S.state = o; o += round_up(std::max<uint64_t>(p->scratch_bytes, 16));
+  S.desc = o; o += round_up(sizeof(InstDesc) * C);
+  S.order = o; o += round_up(sizeof(int32_t) * C);
+  S.res = o; o += round_up(sizeof(InstResult) * C);
+  S.masks = o; o += round_up(segs);
+  S.ctrl = o; o += ALIGN;   // work counter at 0, status word at 16
+  S.total = o;
+  o = 0;
+  S.h_res = o; o += round_up(sizeof(InstResult) * C);
+  S.h_masks = o; o += round_up(segs);
+  S.h_err = o; o += ALIGN;
+  S.h_total = o;
+  return S;
+}
+
 struct Req {
   int64_t ticket = 0;
   State state = State::Building;
@@ -94,11 +123,10 @@ struct Req {
   mpld_problem *p = nullptr;
   int n_seg = 0;
   // admission
-  uint64_t arena_off = 0, arena_bytes = 0, pool_off = 0, pool_bytes = 0;
-  uint32_t *counter = nullptr;
-  InstResult *hres = nullptr;
-  int8_t *hmasks = nullptr;
-  int C = 0;
+  Sections sec{};
+  uint64_t arena_off = 0, pool_off = 0;
+  std::vector<InstDesc> desc;   // upload source, alive until the layout is finished
+  cudaEvent_t done = nullptr;
   // outcome
   std::vector<int8_t> mask;
   mpld_result res{};
@@ -117,24 +145,13 @@ int cuda_ok(cudaError_t e) {
 
 struct mpld_server {
   mpld_server_config cfg{};
-  int64_t budget = 0, tl_ns = 0, idle_ns = 0;
-  cudaStream_t kstream = nullptr, cstream = nullptr;
-  cudaEvent_t kdone = nullptr;
-  bool launched = false;
-  int ctas = 1;
-  // device
+  int64_t budget = 0, tl_ns = 0;
+  int nsm = 1, max_slot = 0;
+  std::vector<cudaStream_t> streams;
+  uint64_t next_stream = 0;
   uint8_t *d_arena = nullptr;
-  InstDesc *d_ring = nullptr;
-  uint32_t *d_ctrl = nullptr;  // [0] head, [32] tail, [64] status word
-  // pinned host
-  InstDesc *h_ring = nullptr;       // staging copy of the ring
-  uint32_t *h_tail = nullptr;       // TAIL_VALUES tail values
-  uint32_t *h_stop = nullptr;       // mapped stop flag, then the kernel's status word
-  uint8_t *h_pool = nullptr;        // mapped results, masks, counters
-  uint8_t *d_pool = nullptr;        // device address of h_pool
-  uint32_t *d_stop = nullptr;
+  uint8_t *h_pool = nullptr;   // pinned
   FirstFit arena, pool;
-  uint64_t published = 0, done_instances = 0, tail_copies = 0;
   // requests
   std::mutex mu;
   std::condition_variable cv;
@@ -174,11 +191,11 @@ void worker_loop(mpld_server *s) {
       mpld_problem *p = nullptr;
       const int rc = mpld_build_matrix(&r->g, &prm, nullptr, &p);
       std::lock_guard<std::mutex> lk(s->mu);
-      r->cu.clear(); r->cu.shrink_to_fit();
-      r->cv.clear(); r->cv.shrink_to_fit();
-      r->su.clear(); r->su.shrink_to_fit();
-      r->sv.clear(); r->sv.shrink_to_fit();
-      r->poly.clear(); r->poly.shrink_to_fit();
+      r->cu = {};
+      r->cv = {};
+      r->su = {};
+      r->sv = {};
+      r->poly = {};
       if (rc != MPLD_OK) {
         r->rc = rc;
         r->state = State::Done;
@@ -191,11 +208,16 @@ void worker_loop(mpld_server *s) {
       }
     } else {
       r->mask.assign((size_t)std::max(r->n_seg, 1), (int8_t)-1);
-      const int rc = mpld_internal_finish(r->p, r->hres, r->hmasks, 0, r->mask.data(), &r->res);
+      const uint8_t *hp = s->h_pool + r->pool_off;
+      const int32_t err = *reinterpret_cast<const int32_t *>(hp + r->sec.h_err);
+      const int rc = mpld_internal_finish(r->p, reinterpret_cast<const InstResult *>(hp + r->sec.h_res),
+                                          reinterpret_cast<const int8_t *>(hp + r->sec.h_masks), err,
+                                          r->mask.data(), &r->res);
       std::lock_guard<std::mutex> lk(s->mu);
-      s->pool.release(r->pool_off, r->pool_bytes);
+      s->pool.release(r->pool_off, r->sec.h_total);
       mpld_free(r->p);
       r->p = nullptr;
+      r->desc = {};
       r->rc = rc;
       r->state = State::Done;
       s->done_tickets.push_back(r->ticket);
@@ -204,108 +226,78 @@ void worker_loop(mpld_server *s) {
   }
 }
 
-// Device bytes of a built request: read-only blocks, then state regions.
-uint64_t device_bytes(const mpld_problem *p) {
-  return round_up(p->arena_bytes) + round_up(p->scratch_bytes);
-}
-uint64_t pool_bytes_of(const mpld_problem *p) {
-  return 64 + sizeof(InstResult) * (uint64_t)std::max(p->n_comp, 1) +
-         (uint64_t)std::max<int64_t>(p->instance_segments, 1);
-}
-
-// Upload one request and append its instances to the ring (largest first).
-int admit(mpld_server *s, Req &r) {
+// Upload one admitted layout and enqueue its search on the next stream:
+// upload, reset, one persistent launch of the batched kernel, copy back,
+// event.  Every host source stays alive until the layout is finished.
+int launch_request(mpld_server *s, Req &r) {
   mpld_problem *p = r.p;
   const int C = p->n_comp;
+  const Sections &S = r.sec;
   uint8_t *base = s->d_arena + r.arena_off;
-  uint8_t *state_base = base + round_up(p->arena_bytes);
-  int rc = MPLD_OK;
-  if (p->arena_bytes)
-    rc |= cuda_ok(cudaMemcpyAsync(base, p->h_arena.data(), p->arena_bytes, cudaMemcpyHostToDevice,
-                                  s->cstream));
   uint8_t *hp = s->h_pool + r.pool_off;
-  uint8_t *dp = s->d_pool + r.pool_off;
-  r.counter = reinterpret_cast<uint32_t *>(hp);
-  __atomic_store_n(r.counter, 0u, __ATOMIC_RELEASE);
-  r.hres = reinterpret_cast<InstResult *>(hp + 64);
-  r.hmasks = reinterpret_cast<int8_t *>(hp + 64 + sizeof(InstResult) * (size_t)std::max(C, 1));
-  uint32_t *d_counter = reinterpret_cast<uint32_t *>(dp);
-  InstResult *d_res = reinterpret_cast<InstResult *>(dp + 64);
-  int8_t *d_masks = reinterpret_cast<int8_t *>(dp + 64 + sizeof(InstResult) * (size_t)std::max(C, 1));
+  cudaStream_t st = s->streams[s->next_stream++ % s->streams.size()];
+  InstDesc *d_desc = reinterpret_cast<InstDesc *>(base + S.desc);
+  InstResult *d_res = reinterpret_cast<InstResult *>(base + S.res);
+  int8_t *d_masks = reinterpret_cast<int8_t *>(base + S.masks);
+  uint32_t *d_queue = reinterpret_cast<uint32_t *>(base + S.ctrl);
+  int32_t *d_err = reinterpret_cast<int32_t *>(base + S.ctrl + 16);
   std::vector<uint64_t> state_off((size_t)C);
   uint64_t so = 0;
+  uint32_t fmax = 16;
   for (int c = 0; c < C; ++c) {
     state_off[c] = so;
     so += (uint64_t)p->h_desc[c].state_bytes;
+    fmax = std::max(fmax, p->footprint[c]);
   }
-  const uint32_t cap = (uint32_t)s->cfg.ring_capacity;
-  const uint64_t first = s->published;
-  const uint8_t *region_end = base + r.arena_bytes;
-  const uint8_t *pool_end = dp + r.pool_bytes;
-  for (int j = 0; j < C; ++j) {
-    const int c = p->h_order[j];
+  r.desc.resize((size_t)C);
+  for (int c = 0; c < C; ++c) {
     InstDesc d = p->h_desc[c];
-    d.ro = base + p->ro_off[c];
-    d.scratch = state_base + state_off[c];
+    d.ro = base + S.ro + p->ro_off[c];
+    d.scratch = base + S.state + state_off[c];
     d.mask = d_masks + p->comp_ptr[c];
     d.res = d_res + c;
-    d.done = d_counter;
-    // every pointer the kernel will follow stays inside this request's regions
-    if (d.ro + d.ro_bytes > state_base || d.scratch + d.state_bytes > region_end ||
-        (const uint8_t *)(d.mask + d.n) > pool_end || (const uint8_t *)(d.res + 1) > pool_end ||
-        ((uintptr_t)d.ro & 15) || ((uintptr_t)d.scratch & 15))
-      return MPLD_E_STATE;
-    s->h_ring[(first + j) % cap] = d;
+    r.desc[c] = d;
   }
-  // copy the new ring slots (one or two pieces), then publish the tail
-  const uint32_t s0 = (uint32_t)(first % cap);
-  const uint32_t n0 = std::min<uint32_t>((uint32_t)C, cap - s0);
-  if (n0)
-    rc |= cuda_ok(cudaMemcpyAsync(s->d_ring + s0, s->h_ring + s0, sizeof(InstDesc) * n0,
-                                  cudaMemcpyHostToDevice, s->cstream));
-  if ((uint32_t)C > n0)
-    rc |= cuda_ok(cudaMemcpyAsync(s->d_ring, s->h_ring, sizeof(InstDesc) * ((uint32_t)C - n0),
-                                  cudaMemcpyHostToDevice, s->cstream));
-  s->published += (uint64_t)C;
-  uint32_t *tv = s->h_tail + (s->tail_copies % TAIL_VALUES);
-  *tv = (uint32_t)s->published;
-  rc |= cuda_ok(cudaMemcpyAsync(s->d_ctrl + 32, tv, 4, cudaMemcpyHostToDevice, s->cstream));
-  if (++s->tail_copies % (TAIL_VALUES / 2) == 0) rc |= cuda_ok(cudaStreamSynchronize(s->cstream));
-  // p->h_arena stays alive until the request is finished: an asynchronous
-  // copy from pageable memory may read it after this call returns (on
-  // systems where the GPU reads host memory directly, nothing stages it)
-  r.C = C;
-  return rc ? MPLD_E_CUDA : MPLD_OK;
-}
-
-int relaunch_if_needed(mpld_server *s) {
-  if (s->published == s->done_instances) return MPLD_OK;
-  if (s->launched) {
-    const cudaError_t q = cudaEventQuery(s->kdone);
-    if (q == cudaErrorNotReady) return MPLD_OK;  // still running
-    if (q != cudaSuccess) return cuda_ok(q);
-  }
-  mpld::ServeArgs a;
-  a.ring = s->d_ring;
-  a.cap = (uint32_t)s->cfg.ring_capacity;
-  a.slot_bytes = s->cfg.slot_bytes;
-  a.head = s->d_ctrl;
-  a.tail = s->d_ctrl + 32;
-  a.stop = s->d_stop;
-  a.err = reinterpret_cast<int32_t *>(s->d_stop + 8);   // host-mapped (byte 32), read by every poll
-  a.arena_lo = s->d_arena;
-  a.arena_hi = s->d_arena + s->cfg.arena_bytes;
-  a.pool_lo = s->d_pool;
-  a.pool_hi = s->d_pool + s->cfg.result_pool_bytes;
+  int rc = MPLD_OK;
+  if (p->arena_bytes)
+    rc |= cuda_ok(cudaMemcpyAsync(base + S.ro, p->h_arena.data(), p->arena_bytes,
+                                  cudaMemcpyHostToDevice, st));
+  rc |= cuda_ok(cudaMemcpyAsync(d_desc, r.desc.data(), sizeof(InstDesc) * (size_t)C,
+                                cudaMemcpyHostToDevice, st));
+  rc |= cuda_ok(cudaMemcpyAsync(base + S.order, p->h_order.data(), sizeof(int32_t) * (size_t)C,
+                                cudaMemcpyHostToDevice, st));
+  rc |= cuda_ok(cudaMemsetAsync(base + S.ctrl, 0, ALIGN, st));
+  rc |= cuda_ok(cudaMemsetAsync(d_res, 0xFF, sizeof(InstResult) * (size_t)C, st));
+  if (rc) return MPLD_E_CUDA;
+  const int nw = s->cfg.warps_per_cta;
+  const int slot = (int)std::min<uint32_t>(mpld::align16(fmax), (uint32_t)s->max_slot) & ~15;
+  const int per_sm = std::max(1, mpld_internal_ctas_per_sm(nw, slot));
+  const int ctas = std::max(1, std::min(s->nsm * per_sm, (C + nw - 1) / nw));
+  mpld::LaunchArgs a;
+  a.desc = d_desc;
+  a.order = reinterpret_cast<const int32_t *>(base + S.order);
+  a.n_inst = C;
+  a.slot_bytes = slot;
+  a.queue = d_queue;
+  a.err = d_err;
   a.budget = s->budget;
   a.time_limit_ns = s->tl_ns;
-  a.idle_ns = s->idle_ns;
-  int rc = mpld_internal_serve_launch(&a, s->ctas, s->cfg.warps_per_cta, s->kstream);
+  rc = mpld_internal_launch(&a, ctas, nw, st);
   if (rc) return rc;
-  rc = cuda_ok(cudaEventRecord(s->kdone, s->kstream));
-  s->launched = true;
+  rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_res, d_res, sizeof(InstResult) * (size_t)C,
+                                cudaMemcpyDeviceToHost, st));
+  if (p->instance_segments)
+    rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_masks, d_masks, (size_t)p->instance_segments,
+                                  cudaMemcpyDeviceToHost, st));
+  rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_err, d_err, 4, cudaMemcpyDeviceToHost, st));
+  if (cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return MPLD_E_CUDA;
+  }
+  rc |= cuda_ok(cudaEventRecord(r.done, st));
   s->st.kernel_launches++;
-  return rc;
+  s->st.instances_launched += C;
+  return rc ? MPLD_E_CUDA : MPLD_OK;
 }
 
 }  // namespace
@@ -315,74 +307,46 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
   if (!out) return MPLD_E_INVALID;
   *out = nullptr;
   mpld_server_config cfg = cfg_in ? *cfg_in : mpld_server_config{};
-  if (cfg.arena_bytes < 0 || cfg.result_pool_bytes < 0 || cfg.ring_capacity < 0 ||
-      cfg.warps_per_cta < 0 || cfg.warps_per_cta > 16 || cfg.slot_bytes < 0 ||
-      cfg.worker_threads < 0 || cfg.idle_exit_ms < 0)
+  if (cfg.arena_bytes < 0 || cfg.result_pool_bytes < 0 || cfg.max_in_flight < 0 ||
+      cfg.streams < 0 || cfg.warps_per_cta < 0 || cfg.warps_per_cta > 16 ||
+      cfg.worker_threads < 0)
     return MPLD_E_INVALID;
   if (!cfg.arena_bytes) cfg.arena_bytes = (int64_t)1 << 30;
   if (!cfg.result_pool_bytes) cfg.result_pool_bytes = (int64_t)256 << 20;
-  if (!cfg.ring_capacity) cfg.ring_capacity = 1 << 18;
+  if (!cfg.max_in_flight) cfg.max_in_flight = 64;
+  if (!cfg.streams) cfg.streams = 8;
   if (!cfg.warps_per_cta) cfg.warps_per_cta = 4;
-  if (!cfg.slot_bytes) cfg.slot_bytes = 12288;
-  cfg.slot_bytes = (cfg.slot_bytes + 15) & ~15;
-  if (cfg.slot_bytes > mpld_internal_max_slot_bytes(cfg.warps_per_cta))
-    cfg.slot_bytes = mpld_internal_max_slot_bytes(cfg.warps_per_cta);
   if (!cfg.worker_threads)
-    cfg.worker_threads = std::max(1u, std::thread::hardware_concurrency() / 2);
-  if (!cfg.idle_exit_ms) cfg.idle_exit_ms = 200;
+    cfg.worker_threads = (int32_t)std::max(1u, std::thread::hardware_concurrency() / 2);
 
   mpld_server *s = new (std::nothrow) mpld_server();
   if (!s) return MPLD_E_OOM;
   s->cfg = cfg;
   s->budget = search ? std::max<int64_t>(search->node_budget, 0) : 0;
   s->tl_ns = ((search && search->time_limit_ms > 0) ? search->time_limit_ms : 60000) * 1000000ll;
-  s->idle_ns = cfg.idle_exit_ms * 1000000ll;
-  int rc = MPLD_OK;
-  auto fail = [&](int code) {
-    mpld_server_destroy(s);
-    return code;
-  };
-  if (cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(MPLD_E_CUDA);
+  s->nsm = std::max(1, mpld_internal_num_sms());
+  s->max_slot = mpld_internal_max_slot_bytes(cfg.warps_per_cta);
+  if (s->max_slot <= 0) {
+    delete s;
+    return MPLD_E_CUDA;
   }
-  const size_t ring_bytes = sizeof(InstDesc) * (size_t)cfg.ring_capacity;
+  for (int i = 0; i < cfg.streams; ++i) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      mpld_server_destroy(s);
+      return MPLD_E_CUDA;
+    }
+    s->streams.push_back(st);
+  }
   if (cudaMalloc((void **)&s->d_arena, (size_t)cfg.arena_bytes) != cudaSuccess ||
-      cudaMalloc((void **)&s->d_ring, ring_bytes) != cudaSuccess ||
-      cudaMalloc((void **)&s->d_ctrl, 512) != cudaSuccess) {
+      cudaMallocHost((void **)&s->h_pool, (size_t)cfg.result_pool_bytes) != cudaSuccess) {
     cudaGetLastError();
-    return fail(MPLD_E_OOM);
+    mpld_server_destroy(s);
+    return MPLD_E_OOM;
   }
-  if (cudaMallocHost((void **)&s->h_ring, ring_bytes) != cudaSuccess ||
-      cudaMallocHost((void **)&s->h_tail, sizeof(uint32_t) * TAIL_VALUES) != cudaSuccess ||
-      cudaHostAlloc((void **)&s->h_stop, 128, cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostAlloc((void **)&s->h_pool, (size_t)cfg.result_pool_bytes, cudaHostAllocMapped) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return fail(MPLD_E_OOM);
-  }
-  if (cudaHostGetDevicePointer((void **)&s->d_pool, s->h_pool, 0) != cudaSuccess ||
-      cudaHostGetDevicePointer((void **)&s->d_stop, s->h_stop, 0) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(MPLD_E_CUDA);
-  }
-  std::memset(s->h_stop, 0, 128);
-  rc |= cuda_ok(cudaMemsetAsync(s->d_ctrl, 0, 512, s->cstream));
-  rc |= cuda_ok(cudaStreamSynchronize(s->cstream));
-  if (rc) return fail(MPLD_E_CUDA);
   s->arena.reset((uint64_t)cfg.arena_bytes);
   s->pool.reset((uint64_t)cfg.result_pool_bytes);
-  // one resident CTA per SM and occupancy slot of the chosen shape
-  int per_sm = 0;
-  {
-    const size_t smem = mpld::align16(8u * (uint32_t)cfg.warps_per_cta) +
-                        (size_t)cfg.warps_per_cta * (size_t)cfg.slot_bytes;
-    per_sm = std::max(1, std::min(mpld_internal_ctas_per_sm(cfg.warps_per_cta, cfg.slot_bytes),
-                                  (int)((227 * 1024) / std::max<size_t>(smem, 1))));
-  }
-  s->ctas = std::max(1, mpld_internal_num_sms()) * per_sm;
   for (int i = 0; i < cfg.worker_threads; ++i) s->workers.emplace_back(worker_loop, s);
   *out = s;
   return MPLD_OK;
@@ -428,28 +392,25 @@ extern "C" int mpld_server_submit(mpld_server *s, const mpld_graph *g, uint32_t 
 extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
                                 int32_t *n_done) {
   if (!s || (max_done > 0 && !done)) return MPLD_E_INVALID;
-  int rc = MPLD_OK;
-  // status word of the resident kernel: a descriptor it refused, or a
-  // bulk copy that did not land
-  if (__atomic_load_n(reinterpret_cast<int32_t *>(s->h_stop + 8), __ATOMIC_ACQUIRE) != 0)
-    return MPLD_E_STATE;
-  // finished requests: every instance counted by the kernel
+  // finished layouts: their stream passed the copy-back
   for (size_t i = 0; i < s->inflight.size();) {
     ReqPtr r = s->inflight[i];
-    const uint32_t c = __atomic_load_n(r->counter, __ATOMIC_ACQUIRE);
-    if ((int)c == r->C) {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->arena.release(r->arena_off, r->arena_bytes);
-      s->done_instances += (uint64_t)r->C;
-      s->st.instances_done += r->C;
-      r->state = State::Finishing;
-      s->finish_q.push_back(r);
-      s->cv.notify_one();
-      s->inflight[i] = s->inflight.back();
-      s->inflight.pop_back();
-    } else {
+    const cudaError_t q = cudaEventQuery(r->done);
+    if (q == cudaErrorNotReady) {
+      cudaGetLastError();
       ++i;
+      continue;
     }
+    if (q != cudaSuccess) return cuda_ok(q);
+    cudaEventDestroy(r->done);
+    r->done = nullptr;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->arena.release(r->arena_off, r->sec.total);
+    r->state = State::Finishing;
+    s->finish_q.push_back(r);
+    s->cv.notify_one();
+    s->inflight[i] = s->inflight.back();
+    s->inflight.pop_back();
   }
   // admission in submission order
   for (;;) {
@@ -467,10 +428,10 @@ extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
       if (s->admit_order.empty()) break;
       r = s->reqs[s->admit_order.front()];
       if (r->state != State::Built) break;
+      if ((int)s->inflight.size() >= s->cfg.max_in_flight) break;
       mpld_problem *p = r->p;
-      const uint64_t dbytes = device_bytes(p), pbytes = pool_bytes_of(p);
-      if (dbytes > s->arena.size() || pbytes > s->pool.size() ||
-          (int64_t)p->n_comp > (int64_t)s->cfg.ring_capacity) {
+      r->sec = sections_of(p);
+      if (r->sec.total > s->arena.size() || r->sec.h_total > s->pool.size()) {
         // can never fit: fail the ticket
         mpld_free(p);
         r->p = nullptr;
@@ -481,42 +442,32 @@ extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
         s->admit_order.pop_front();
         continue;
       }
-      if (s->published - s->done_instances + (uint64_t)p->n_comp > (uint64_t)s->cfg.ring_capacity)
-        break;
-      if (!s->arena.alloc(dbytes, &r->arena_off)) break;
-      if (!s->pool.alloc(pbytes, &r->pool_off)) {
-        s->arena.release(r->arena_off, dbytes);
+      if (!s->arena.alloc(r->sec.total, &r->arena_off)) break;
+      if (!s->pool.alloc(r->sec.h_total, &r->pool_off)) {
+        s->arena.release(r->arena_off, r->sec.total);
         break;
       }
-      r->arena_bytes = dbytes;
-      r->pool_bytes = pbytes;
       s->admit_order.pop_front();
       s->st.arena_used_bytes = (int64_t)s->arena.used();
       s->st.arena_peak_bytes = std::max(s->st.arena_peak_bytes, s->st.arena_used_bytes);
+      s->st.admitted++;
     }
     if (r->p->n_comp == 0) {
       // nothing to search: recover straight away
-      r->C = 0;
-      r->counter = reinterpret_cast<uint32_t *>(s->h_pool + r->pool_off);
-      r->hres = reinterpret_cast<InstResult *>(s->h_pool + r->pool_off + 64);
-      r->hmasks = reinterpret_cast<int8_t *>(s->h_pool + r->pool_off + 64 + sizeof(InstResult));
+      std::memset(s->h_pool + r->pool_off, 0, r->sec.h_total);
       std::lock_guard<std::mutex> lk(s->mu);
-      s->arena.release(r->arena_off, r->arena_bytes);
+      s->arena.release(r->arena_off, r->sec.total);
       r->state = State::Finishing;
-      s->st.admitted++;
       s->finish_q.push_back(r);
       s->cv.notify_one();
       continue;
     }
-    rc = admit(s, *r);
+    const int rc = launch_request(s, *r);
     if (rc) return rc;
     r->state = State::Admitted;
     s->inflight.push_back(r);
-    s->st.admitted++;
-    s->st.instances_published += r->C;
+    s->st.max_concurrent = std::max(s->st.max_concurrent, (int64_t)s->inflight.size());
   }
-  rc = relaunch_if_needed(s);
-  if (rc) return rc;
   int32_t nd = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -548,7 +499,8 @@ extern "C" int mpld_server_result(mpld_server *s, int64_t ticket, int8_t *mask_o
 
 extern "C" int mpld_server_stats_get(const mpld_server *s, mpld_server_stats *out) {
   if (!s || !out) return MPLD_E_INVALID;
-  std::lock_guard<std::mutex> lk(const_cast<mpld_server *>(s)->mu);
+  mpld_server *m = const_cast<mpld_server *>(s);
+  std::lock_guard<std::mutex> lk(m->mu);
   *out = s->st;
   int64_t waiting = 0;
   for (const auto &kv : s->reqs)
@@ -567,22 +519,15 @@ extern "C" void mpld_server_destroy(mpld_server *s) {
   }
   s->cv.notify_all();
   for (auto &t : s->workers) t.join();
-  if (s->h_stop) __atomic_store_n(s->h_stop, 1u, __ATOMIC_RELEASE);
-  if (s->kstream) cudaStreamSynchronize(s->kstream);
-  if (s->cstream) cudaStreamSynchronize(s->cstream);
+  for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
+  for (auto &r : s->inflight)
+    if (r->done) cudaEventDestroy(r->done);
   for (auto &kv : s->reqs)
     if (kv.second->p) mpld_free(kv.second->p);
   for (auto &r : s->finish_q)
     if (r->p) mpld_free(r->p);
-  if (s->kdone) cudaEventDestroy(s->kdone);
-  if (s->kstream) cudaStreamDestroy(s->kstream);
-  if (s->cstream) cudaStreamDestroy(s->cstream);
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   if (s->d_arena) cudaFree(s->d_arena);
-  if (s->d_ring) cudaFree(s->d_ring);
-  if (s->d_ctrl) cudaFree(s->d_ctrl);
-  if (s->h_ring) cudaFreeHost(s->h_ring);
-  if (s->h_tail) cudaFreeHost(s->h_tail);
-  if (s->h_stop) cudaFreeHost(s->h_stop);
   if (s->h_pool) cudaFreeHost(s->h_pool);
   delete s;
 }

@@ -71,16 +71,15 @@ class mpld_device_instance(ctypes.Structure):
 
 
 class mpld_server_config(ctypes.Structure):
-    _fields_ = [("arena_bytes", _i64), ("result_pool_bytes", _i64), ("ring_capacity", _i32),
-                ("warps_per_cta", _i32), ("slot_bytes", _i32), ("worker_threads", _i32),
-                ("idle_exit_ms", _i64)]
+    _fields_ = [("arena_bytes", _i64), ("result_pool_bytes", _i64), ("max_in_flight", _i32),
+                ("streams", _i32), ("warps_per_cta", _i32), ("worker_threads", _i32)]
 
 
 class mpld_server_stats(ctypes.Structure):
     _fields_ = [(f, _i64) for f in ("submitted", "built", "admitted", "completed", "failed",
                                     "waiting", "in_flight", "arena_used_bytes",
-                                    "arena_peak_bytes", "instances_published", "instances_done",
-                                    "kernel_launches")]
+                                    "arena_peak_bytes", "instances_launched", "kernel_launches",
+                                    "max_concurrent")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
