@@ -50,6 +50,11 @@ def parse_args():
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the workload's polygon count (same density and degree); "
                          "for small profiling cases")
+    ap.add_argument("--serve", action="store_true",
+                    help="also run the serving loop at 10, 100 and 1000 requests/s")
+    ap.add_argument("--serve-budget", type=int, default=1 << 12)
+    ap.add_argument("--serve-pool", type=int, default=48,
+                    help="distinct pre-generated requests the Poisson streams cycle through")
     ap.add_argument("--plain-scale", type=int, default=20,
                     help="the plain one-launch-per-instance path runs on the same workload with "
                          "polygons / plain-scale (same density and degree)")
@@ -121,13 +126,71 @@ def measured_peaks():
 
 
 def workload_layout(name: str, rank: int, scale: int = 1):
-    from paper_2303_14335_gb300 import synth
+    from paper_2303_14335_gb300 import shard, synth
     cfg = dict(synth.WORKLOADS[name])
     mode = cfg.pop("mode")
-    cfg["seed"] = cfg["seed"] + 1000 * rank
+    cfg["seed"] = shard.rank_seed(cfg["seed"], rank)
     if scale > 1:
         cfg["n_poly"] = max(cfg["n_poly"] // scale, 100)
     return synth.unit_disk_layout(name=name, **cfg), mode
+
+
+def run_serving(args, mpld, synth):
+    """Poisson streams of whole layouts through the server (continuous batching).
+
+    Requests: 1k-200k polygons (log-uniform), k in {3, 4}, stitch p = 0.2,
+    mean degree U[3, 5], seeded per request; a pool of distinct requests is
+    generated first and the stream cycles through it.  Latency = result in
+    host memory minus the request's scheduled arrival time.
+    """
+    import numpy as np
+    pool = [synth.serving_request(2023, i) for i in range(args.serve_pool)]
+    pool_segments = [L.n_seg for L in pool]
+    out = {"budget": args.serve_budget, "pool_requests": len(pool),
+           "pool_mean_segments": float(np.mean(pool_segments)), "loads": []}
+    for rate, duration in ((10, 12.0), (100, 6.0), (1000, 3.0)):
+        n = int(rate * duration)
+        arrivals = synth.poisson_arrivals(777 + rate, n, rate)
+        cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
+                                      max_in_flight=256, streams=16)
+        srv = mpld.mpld_server_create(cfg, mpld.make_params(node_budget=args.serve_budget))
+        arrival_of, lat, segs = {}, [], 0
+        t0 = time.perf_counter()
+        i = 0
+        deadline = duration * 6 + 60
+        while len(lat) < n:
+            now = time.perf_counter() - t0
+            while i < n and arrivals[i] <= now:
+                L = pool[i % len(pool)]
+                t = mpld.mpld_server_submit(srv, L)
+                arrival_of[t] = (arrivals[i], L.n_seg)
+                i += 1
+            busy = False
+            for t in mpld.mpld_server_poll(srv):
+                rc, mask, res = mpld.mpld_server_result(srv, t)
+                a, ns = arrival_of.pop(t)
+                lat.append(time.perf_counter() - t0 - a)
+                segs += ns
+                busy = True
+            if now > deadline:
+                break
+            if not busy and (i >= n or arrivals[i] > now + 0.0005):
+                time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        st = mpld.mpld_server_stats_get(srv)
+        srv.close()
+        lat_ms = np.array(lat) * 1000.0
+        achieved = len(lat) / wall
+        out["loads"].append({
+            "offered_req_per_s": rate, "requests": n, "completed": len(lat),
+            "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
+            "mean_ms": float(lat_ms.mean()) if len(lat) else None,
+            "achieved_req_per_s": achieved, "segments_per_s": segs / wall,
+            "saturated": bool(achieved < 0.9 * rate),
+            "max_concurrent_layouts": int(st.max_concurrent),
+            "arena_peak_bytes": int(st.arena_peak_bytes)})
+    return out
 
 
 def run_reference(args, rank, world):
@@ -223,12 +286,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1000.0
     if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        segs = torch.tensor([layout.n_seg], dtype=torch.float64, device="cuda")
-        dist.all_reduce(segs)
-        all_segments = float(segs.item())
+        from paper_2303_14335_gb300 import shard
+        all_segments, total_s = shard.aggregate(dist, layout.n_seg, total_s, "cuda")
     else:
         all_segments = float(layout.n_seg)
     rc, mask, res = mpld.mpld_fetch(prob, s)
@@ -290,9 +349,8 @@ def main():
             assert np.array_equal(masks2[0], mask)
         e2e_total = sum(e2e_t)
         if dist:
-            t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_total = float(t.item())
+            from paper_2303_14335_gb300 import shard
+            _, e2e_total = shard.aggregate(dist, layout.n_seg, e2e_total, "cuda")
         # bytes copied per step: read-only blocks + descriptors + order up;
         # instance results + instance masks + status word down
         h2d = inf2.arena_bytes + 80 * inf2.n_components + 4 * inf2.n_components
@@ -326,6 +384,10 @@ def main():
                         "batched_segments_per_s": small.n_seg / times["batched"],
                         "batched_over_plain": times["plain"] / times["batched"],
                         "gpu_launches_plain": pinfo.n_components}
+
+    if rank == 0 and args.serve:
+        from paper_2303_14335_gb300 import synth
+        out["serving"] = run_serving(args, mpld, synth)
 
     if rank == 0 and not args.no_cpu:
         import oracle
