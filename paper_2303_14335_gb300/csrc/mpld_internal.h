@@ -46,23 +46,31 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
 // global scratch region when it does not fit the warp's slot).  The DFS
 // depth is at most n; undo data is kept per segment and per adjacency entry
 // because each segment appears at most once on the current path.
-//   rows[n]     FB-bit fields: activeRows + uncovered-column bits
+//   lv[n]       32-byte level record {path cost, v | rows tried << 16,
+//               visiting order (4 bits per row), conflict offset, conflict
+//               degree | stitch degree << 16, stitch offset, added cost of
+//               rows 1 and 2}
+//   lvx[n*mk]   added cost of rows 3.. in visiting order
+//   ccnt[n*cw]  per segment, 16-bit counts of conflict neighbours holding
+//               each mask (cw = mk/4 64-bit words)
+//   scnt[n*cw]  the same for stitch neighbours
+//   rows[n]     FB-bit fields: activeRows + uncovered-column bits (padded
+//               with zero fields to a multiple of 4 bytes)
 //   oldf[n]     field of v before v's row was covered
 //   x[n]        i8   current mask per segment (-1 = none)
 //   savf[ne2]   field of neighbour u before v's row cleared its bit (the
 //               undo record of the cover, one per adjacency entry of v)
-//   lv[n]       16-byte level record {path cost, v | rows tried << 16,
-//               visiting order (4 bits per row), added cost of row 1}
-//   lvx[n*mk]   added cost of rows 2.. in visiting order
 struct StateLayout {
-  uint32_t rows, oldf, x, savf, lv, lvx, bytes;
+  uint32_t lv, lvx, ccnt, scnt, rows, oldf, x, savf, bytes;
 };
 MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
-  const uint32_t fb = (uint32_t)field_bytes_for(k), mk = (uint32_t)mk_for(k);
+  const uint32_t fb = (uint32_t)field_bytes_for(k), mk = (uint32_t)mk_for(k), cw = mk / 4u;
   StateLayout L;
   uint32_t o = 0;
-  L.lv = o; o += 16u * (uint32_t)n;
+  L.lv = o; o += 32u * (uint32_t)n;
   L.lvx = o; o += align16(4u * mk * (uint32_t)n);
+  L.ccnt = o; o += align16(8u * cw * (uint32_t)n);
+  L.scnt = o; o += align16(8u * cw * (uint32_t)n);
   L.rows = o; o += align16(fb * (uint32_t)n);
   L.oldf = o; o += align16(fb * (uint32_t)n);
   L.x = o; o += align16((uint32_t)n);

@@ -115,41 +115,69 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // ---- the search ----------------------------------------------------------
 
-// FT: field type of the activeRows bitset (uint8_t for k <= 7, uint16_t for
-// k = 8); MK: width of the row sort (k for k <= 4, else 8).  Each segment's
-// field is written by one lane at a time, so covers are plain loads and
-// stores: the cover of row (v, c) saves every neighbour's field before
-// clearing bit c, and the undo writes the saved fields back.
 // Read-only data (adjacency) of an instance whose block stays in global
-// memory is read from L2: arena regions are reused while a resident grid
-// runs, and an SM's L1 may still hold lines of an earlier occupant.
+// memory is read from L2: device memory of finished work may be rewritten
+// while a grid runs, and an SM's L1 may still hold lines of it.
 template <bool SM, typename T>
 __device__ __forceinline__ T ro_ld(const T *p) {
   if constexpr (SM) return *p;
   else return __ldcg(p);
 }
 
+// FT: field type of the activeRows bitset (uint8_t for k <= 7, uint16_t for
+// k = 8); MK: width of the row sort (k for k <= 4, else 8); SM: state and
+// read-only block in shared memory.  Each segment's field is written by one
+// lane at a time, so covers are plain loads and stores: the cover of row
+// (v, c) saves every neighbour's field before clearing bit c, and the undo
+// writes the saved fields back.  Next to the bitset, every segment keeps
+// 16-bit counts of its conflict and stitch neighbours per mask, updated by
+// the same lanes, so the added cost of a segment's rows (Eq. 1) is read in
+// one load instead of gathered from its neighbours.
 template <typename FT, int MK, bool SM>
 struct Search {
-  static constexpr uint32_t FB = 8 * sizeof(FT);   // bits per field
-  static constexpr uint32_t FLAG = 1u << (FB - 1);  // column P_v uncovered
+  static constexpr uint32_t FB = 8 * sizeof(FT);    // bits per field
+  static constexpr uint32_t FLAG = 1u << (FB - 1);   // column P_v uncovered
+  static constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
+  static constexpr int PER_WORD = 4 / (int)sizeof(FT);
+  static constexpr int CW = MK <= 4 ? 1 : 2;          // 64-bit count words per segment
 
-  FT *rows;        // activeRows fields
-  FT *oldf;        // field of v before its first row was covered
-  FT *savf;        // neighbour fields saved by the cover of v's row
+  uint4 *lv;          // two uint4 per level
+  int32_t *lvx;       // cost of rows 3.. per level (MK entries per level)
+  uint64_t *ccnt, *scnt;
+  FT *rows;           // activeRows fields
+  FT *oldf;           // field of v before its first row was covered
+  FT *savf;           // neighbour fields saved by the cover of v's row
   int8_t *x;
-  uint4 *lv;       // {g, v | rows tried << 16, order, inc of row 1}
-  int32_t *lvx;    // inc of rows 2.. per level (MK entries per level)
-  const int2 *ptr; // {conflict offset, stitch offset} per segment
+  const int2 *ptr;    // {conflict offset, stitch offset} per segment
   const uint16_t *cnbr, *snbr;
   int n, k;
   int Cc, Cs;
   uint32_t kmask;
 
+  __device__ __forceinline__ static uint64_t one(int c) { return 1ull << (16 * (c & 3)); }
+  __device__ __forceinline__ static int lane16(uint64_t w, int c) {
+    return (int)((w >> (16 * (c & 3))) & 0xFFFFull);
+  }
+  // count word holding mask c of segment u
+  __device__ __forceinline__ uint64_t *cw_of(uint64_t *cnt, int u, int c) const {
+    return cnt + (size_t)u * CW + (c >> 2);
+  }
+  // counts of segment u: mask c_new gains one neighbour, c_old (if >= 0) loses one
+  __device__ __forceinline__ void move_count(uint64_t *cnt, int u, int c_new, int c_old) const {
+    if (c_old < 0) {
+      *cw_of(cnt, u, c_new) += one(c_new);
+    } else if (CW == 1 || (c_new >> 2) == (c_old >> 2)) {
+      *cw_of(cnt, u, c_new) += one(c_new) - one(c_old);
+    } else {
+      *cw_of(cnt, u, c_new) += one(c_new);
+      *cw_of(cnt, u, c_old) -= one(c_old);
+    }
+  }
+
   // First row (v, c) of v's column: save and clear v's field (column P_v
   // and all its rows), clear bit c of every conflict neighbour (column
-  // S_{(v,u),c}), saving each neighbour's field.  `u` = lane's neighbour.
-  __device__ __forceinline__ void cover_first(int v, int c, int cb, int dc, int u,
+  // S_{(v,u),c}) saving its field, and count mask c at every neighbour.
+  __device__ __forceinline__ void cover_first(int v, int c, int cb, int dc, int sb, int ds,
                                               int lane) const {
     if (lane == 0) {
       oldf[v] = rows[v];
@@ -157,75 +185,47 @@ struct Search {
       x[v] = (int8_t)c;
     }
     const uint32_t clr = ~(1u << c);
-    if (lane < dc) {
+    for (int i = lane; i < dc; i += 32) {
+      const int u = ro_ld<SM>(cnbr + cb + i);
       const FT f = rows[u];
-      savf[cb + lane] = f;
+      savf[cb + i] = f;
       rows[u] = (FT)(f & clr);
+      move_count(ccnt, u, c, -1);
     }
-    if (dc > 32) {
-      for (int i = cb + 32 + lane; i < cb + dc; i += 32) {
-        const int w = ro_ld<SM>(cnbr + i);
-        const FT f = rows[w];
-        savf[i] = f;
-        rows[w] = (FT)(f & clr);
-      }
-    }
+    for (int i = lane; i < ds; i += 32) move_count(scnt, ro_ld<SM>(snbr + sb + i), c, -1);
     __syncwarp();
   }
 
-  // Next row (v, c) of the same column: every neighbour gets its saved
-  // field with bit c cleared (the previous row's clear is undone at once).
-  __device__ __forceinline__ void switch_row(int v, int c, int cb, int dc, int lane) const {
+  // Next row (v, c) of the same column, replacing row (v, c_old): every
+  // neighbour gets its saved field with bit c cleared.
+  __device__ __forceinline__ void switch_row(int v, int c_old, int c, int cb, int dc, int sb,
+                                             int ds, int lane) const {
     if (lane == 0) x[v] = (int8_t)c;
     const uint32_t clr = ~(1u << c);
-    for (int i = cb + lane; i < cb + dc; i += 32) rows[ro_ld<SM>(cnbr + i)] = (FT)(savf[i] & clr);
+    for (int i = lane; i < dc; i += 32) {
+      const int u = ro_ld<SM>(cnbr + cb + i);
+      rows[u] = (FT)(savf[cb + i] & clr);
+      move_count(ccnt, u, c, c_old);
+    }
+    for (int i = lane; i < ds; i += 32) move_count(scnt, ro_ld<SM>(snbr + sb + i), c, c_old);
     __syncwarp();
   }
 
-  // Every row of v's column tried: put v's field and its neighbours back.
-  __device__ __forceinline__ void restore(int v, int cb, int dc, int lane) const {
+  // Every row of v's column tried (the last was c_last): put v's field and
+  // its neighbours back.
+  __device__ __forceinline__ void restore(int v, int c_last, int cb, int dc, int sb, int ds,
+                                          int lane) const {
     if (lane == 0) {
       rows[v] = oldf[v];
       x[v] = -1;
     }
-    for (int i = cb + lane; i < cb + dc; i += 32) rows[ro_ld<SM>(cnbr + i)] = savf[i];
+    for (int i = lane; i < dc; i += 32) {
+      const int u = ro_ld<SM>(cnbr + cb + i);
+      rows[u] = savf[cb + i];
+      *cw_of(ccnt, u, c_last) -= one(c_last);
+    }
+    for (int i = lane; i < ds; i += 32) *cw_of(scnt, ro_ld<SM>(snbr + sb + i), c_last) -= one(c_last);
     __syncwarp();
-  }
-
-  // Per-mask counts of a neighbour list, 8 bits per mask, warp-summed.
-  // Lane's first neighbour id is left in `first`.
-  __device__ __forceinline__ void count(const uint16_t *nbr, int b, int d, int lane, int &first,
-                                        uint32_t &lo, uint32_t &hi) const {
-    uint32_t l = 0, h = 0;
-    if (lane < d) {
-      first = ro_ld<SM>(nbr + b + lane);
-      const int xu = x[first];
-      if (xu >= 0) {
-        if (MK <= 4 || xu < 4) l = 1u << (8 * xu);
-        else h = 1u << (8 * (xu - 4));
-      }
-    }
-    lo = __reduce_add_sync(FULL, l);
-    hi = (MK == 8) ? __reduce_add_sync(FULL, h) : 0u;
-    if (d > 32) {
-      for (int base = 32; base < d; base += 32) {
-        l = 0;
-        h = 0;
-        if (base + lane < d) {
-          const int xu = x[ro_ld<SM>(nbr + b + base + lane)];
-          if (xu >= 0) {
-            if (MK <= 4 || xu < 4) l = 1u << (8 * xu);
-            else h = 1u << (8 * (xu - 4));
-          }
-        }
-        lo += __reduce_add_sync(FULL, l);
-        if (MK == 8) hi += __reduce_add_sync(FULL, h);
-      }
-    }
-  }
-
-  __device__ __forceinline__ static uint32_t lane_of(uint32_t lo, uint32_t hi, int c) {
-    return ((c < 4) ? (lo >> (8 * c)) : (hi >> (8 * (c - 4)))) & 0xFFu;
   }
 
   __device__ __forceinline__ int run(int lane, int64_t budget, int64_t time_limit_ns,
@@ -237,6 +237,8 @@ struct Search {
     int level = 0;
     int status = MPLD_OK;
     const uint64_t t0 = globaltimer();
+    const uint32_t *rows32 = reinterpret_cast<const uint32_t *>(rows);
+    const int nwords = (n + PER_WORD - 1) / PER_WORD;
     bool enter = true;
     for (;;) {
       if (enter) {
@@ -251,15 +253,21 @@ struct Search {
           now = __shfl_sync(FULL, now, 0);
           if ((int64_t)(now - t0) > time_limit_ns) { status = MPLD_TIMEOUT; break; }
         }
-        // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v])
+        // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v]),
+        // PER_WORD fields per 32-bit load
         uint32_t key = 0xFFFFFFFFu, z = 0;
-        for (int base = 0; base < n; base += 32) {
-          const int v = base + lane;
-          const uint32_t f = v < n ? (uint32_t)rows[v] : 0u;
-          const uint32_t kv =
-              (f & FLAG) ? ((uint32_t)__popc(f & kmask) << 16) | (uint32_t)v : 0xFFFFFFFFu;
-          key = min(key, kv);
-          z += kv <= 0xFFFFu;  // uncovered column with no active row
+        for (int wi = lane; wi < nwords; wi += 32) {
+          const uint32_t w = rows32[wi];
+#pragma unroll
+          for (int j = 0; j < PER_WORD; ++j) {
+            const uint32_t f = (w >> (FB * j)) & FMASK;
+            const uint32_t kv = (f & FLAG)
+                                    ? ((uint32_t)__popc(f & kmask) << 16) |
+                                          (uint32_t)(wi * PER_WORD + j)
+                                    : 0xFFFFFFFFu;
+            key = min(key, kv);
+            z += kv <= 0xFFFFu;  // uncovered column with no active row
+          }
         }
         key = __reduce_min_sync(FULL, key);
         if (key == 0xFFFFFFFFu) {
@@ -273,25 +281,26 @@ struct Search {
           continue;
         }
         if (best < INF32) {
-          z = __reduce_add_sync(FULL, z);
+          // the bound needs the number of uncovered columns with no active
+          // row only when there is one (the minimum count is then 0)
+          z = (key >> 16) == 0 ? __reduce_add_sync(FULL, z) : 0u;
           if ((int64_t)g + (int64_t)Cc * z >= best) { enter = false; continue; }
         }
         const int v = (int)(key & 0xFFFFu);
         // added cost of each row (v, c) against the current assignment (Eq. 1)
         const int2 p0 = ro_ld<SM>(ptr + v), p1 = ro_ld<SM>(ptr + v + 1);
-        const int dc = p1.x - p0.x, ds = p1.y - p0.y;
-        int u = 0, us = 0;
-        uint32_t clo, chi, slo = 0, shi = 0;
-        count(cnbr, p0.x, dc, lane, u, clo, chi);
-        if (ds > 0) count(snbr, p0.y, ds, lane, us, slo, shi);
+        const uint64_t cc0 = ccnt[(size_t)v * CW], sc0 = scnt[(size_t)v * CW];
+        const uint64_t cc1 = CW == 2 ? ccnt[(size_t)v * CW + 1] : 0ull;
+        const uint64_t sc1 = CW == 2 ? scnt[(size_t)v * CW + 1] : 0ull;
+        const int cb = p0.x, dc = p1.x - p0.x, sb = p0.y, ds = p1.y - p0.y;
         work32 += (uint32_t)(k * (dc + ds) + 5 * (1 + dc));
         int stot = 0;
 #pragma unroll
-        for (int c = 0; c < MK; ++c) stot += (int)lane_of(slo, shi, c);
+        for (int c = 0; c < MK; ++c) stot += lane16(c < 4 ? sc0 : sc1, c);
         uint32_t keys[MK];
 #pragma unroll
         for (int c = 0; c < MK; ++c) {
-          const int inc = Cc * (int)lane_of(clo, chi, c) + Cs * (stot - (int)lane_of(slo, shi, c));
+          const int inc = Cc * lane16(c < 4 ? cc0 : cc1, c) + Cs * (stot - lane16(c < 4 ? sc0 : sc1, c));
           keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
         }
         sort_keys<MK>(keys);
@@ -299,12 +308,14 @@ struct Search {
 #pragma unroll
         for (int i = 0; i < MK; ++i) ord |= (keys[i] & 7u) << (4 * i);
         if (lane == 0) {
-          lv[level] = make_uint4((uint32_t)g, (uint32_t)v | (1u << 16), ord, keys[1] >> 3);
+          lv[2 * level] = make_uint4((uint32_t)g, (uint32_t)v | (1u << 16), ord, (uint32_t)cb);
+          lv[2 * level + 1] = make_uint4((uint32_t)dc | ((uint32_t)ds << 16), (uint32_t)sb,
+                                         MK > 1 ? keys[1] >> 3 : 0u, MK > 2 ? keys[MK > 2 ? 2 : 0] >> 3 : 0u);
 #pragma unroll
-          for (int i = 2; i < MK; ++i)
+          for (int i = 3; i < MK; ++i)
             if (i < k) lvx[level * MK + i] = (int32_t)(keys[i] >> 3);
         }
-        cover_first(v, (int)(ord & 7u), p0.x, dc, u, lane);
+        cover_first(v, (int)(ord & 7u), cb, dc, sb, ds, lane);
         g += (int32_t)(keys[0] >> 3);
         ++level;
         continue;
@@ -312,19 +323,20 @@ struct Search {
       // ---- backtrack: next row of the level above, or undo its column ----
       if (level == 0) break;
       --level;
-      const uint4 rec = lv[level];
-      const int v = (int)(rec.y & 0xFFFFu);
-      const int nxt = (int)(rec.y >> 16);
-      const int cb = ro_ld<SM>(ptr + v).x, dc = ro_ld<SM>(ptr + v + 1).x - cb;
+      const uint4 r0 = lv[2 * level], r1 = lv[2 * level + 1];
+      const int v = (int)(r0.y & 0xFFFFu);
+      const int nxt = (int)(r0.y >> 16);
+      const int cb = (int)r0.w, dc = (int)(r1.x & 0xFFFFu), sb = (int)r1.y, ds = (int)(r1.x >> 16);
+      const int c_last = (int)((r0.z >> (4 * (nxt - 1))) & 7u);
       if (nxt >= k) {  // every row of this column tried
-        restore(v, cb, dc, lane);
+        restore(v, c_last, cb, dc, sb, ds, lane);
         continue;
       }
-      const int c = (int)((rec.z >> (4 * nxt)) & 7u);
-      g = (int32_t)rec.x + (nxt == 1 ? (int32_t)rec.w : lvx[level * MK + nxt]);
+      const int c = (int)((r0.z >> (4 * nxt)) & 7u);
+      g = (int32_t)r0.x + (nxt == 1 ? (int32_t)r1.z : nxt == 2 ? (int32_t)r1.w : lvx[level * MK + nxt]);
       work32 += 5u * (uint32_t)(1 + dc);
-      if (lane == 0) lv[level].y = (uint32_t)v | ((uint32_t)(nxt + 1) << 16);
-      switch_row(v, c, cb, dc, lane);
+      if (lane == 0) lv[2 * level].y = (uint32_t)v | ((uint32_t)(nxt + 1) << 16);
+      switch_row(v, c_last, c, cb, dc, sb, ds, lane);
       ++level;
       enter = true;
     }
@@ -340,16 +352,19 @@ struct Search {
 template <typename FT, int MK, bool SM>
 __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
                                        const LaunchArgs &a, int lane) {
+  using S = Search<FT, MK, SM>;
   const int n = d.n;
   const StateLayout L = state_layout(n, d.ne2, d.k);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2);
-  Search<FT, MK, SM> s;
+  S s;
+  s.lv = (uint4 *)(base + L.lv);
+  s.lvx = (int32_t *)(base + L.lvx);
+  s.ccnt = (uint64_t *)(base + L.ccnt);
+  s.scnt = (uint64_t *)(base + L.scnt);
   s.rows = (FT *)(base + L.rows);
   s.oldf = (FT *)(base + L.oldf);
   s.savf = (FT *)(base + L.savf);
   s.x = (int8_t *)(base + L.x);
-  s.lv = (uint4 *)(base + L.lv);
-  s.lvx = (int32_t *)(base + L.lvx);
   s.ptr = (const int2 *)(ro + R.ptr);
   s.cnbr = (const uint16_t *)(ro + R.cnbr);
   s.snbr = (const uint16_t *)(ro + R.snbr);
@@ -358,11 +373,15 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   s.Cc = d.cost_conflict;
   s.Cs = d.cost_stitch;
   s.kmask = (1u << d.k) - 1u;
-  // initial state: every row active, every primary column uncovered
-  const FT init = (FT)(s.kmask | Search<FT, MK, SM>::FLAG);
-  for (int i = lane; i < n; i += 32) {
-    s.rows[i] = init;
-    s.x[i] = -1;
+  // initial state: every row active, every primary column uncovered, no
+  // neighbour holds a mask; fields past n (word padding) stay zero
+  const FT init = (FT)(s.kmask | S::FLAG);
+  const int nfields = ((n + S::PER_WORD - 1) / S::PER_WORD) * S::PER_WORD;
+  for (int i = lane; i < nfields; i += 32) s.rows[i] = i < n ? init : (FT)0;
+  for (int i = lane; i < n; i += 32) s.x[i] = -1;
+  for (int i = lane; i < n * S::CW; i += 32) {
+    s.ccnt[i] = 0;
+    s.scnt[i] = 0;
   }
   __syncwarp();
   int32_t best = INF32;
