@@ -264,11 +264,11 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     p->footprint.resize((size_t)C);
     p->inst_ne2.resize((size_t)C);
     p->h_desc.resize((size_t)C);
-    std::vector<int32_t> ns2v((size_t)C), mask_off((size_t)C);
+    std::vector<int32_t> ns2v((size_t)C), mask_off((size_t)C), maxdeg((size_t)C);
     uint64_t arena = 0, scratch = 0;
     std::vector<uint64_t> scratch_off((size_t)C);
     for (int c = 0; c < C; ++c) {
-      int ne2 = 0, ns2 = 0;
+      int ne2 = 0, ns2 = 0, mdc = 0, mds = 0;
       int64_t max_inc = 0;
       for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
         const int s = p->comp_seg[t];
@@ -277,6 +277,8 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
         for (int i = sptr[s]; i < sptr[s + 1]; ++i) ds += p->comp_of[sadj[i]] == c;
         ne2 += dc;
         ns2 += ds;
+        mdc = std::max(mdc, dc);
+        mds = std::max(mds, ds);
         max_inc = std::max(max_inc, p->Cc * dc + p->Cs * ds);
       }
       // the kernel orders a segment's rows by 32-bit keys (added cost << 3 |
@@ -291,6 +293,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       const mpld::StateLayout L = mpld::state_layout(nc, ne2, k);
       p->inst_ne2[c] = ne2;
       ns2v[c] = ns2;
+      maxdeg[c] = std::min(mdc, 0xFFFF) | (std::min(mds, 0x7FFF) << 16);
       p->ro_off[c] = arena;
       arena += R.bytes;
       scratch_off[c] = scratch;
@@ -335,6 +338,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       std::memset(&d, 0, sizeof(d));
       const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
       d.n = nc;
+      d.maxdeg = maxdeg[c];
       d.ne2 = p->inst_ne2[c];
       d.ns2 = ns2v[c];
       d.ro_bytes = (int32_t)mpld::ro_layout(nc, d.ne2, d.ns2).bytes;

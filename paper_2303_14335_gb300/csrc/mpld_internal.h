@@ -86,7 +86,7 @@ struct __align__(16) InstDesc {
   uint8_t *scratch;        // global state region (state_bytes), used when spilled
   int8_t *mask;            // n bytes: best assignment found
   struct InstResult *res;  // result record
-  int32_t n, pad2, ne2, ns2;
+  int32_t n, maxdeg, ne2, ns2;   // maxdeg: largest conflict degree | largest stitch degree << 16
   int32_t ro_bytes, state_bytes;
   int32_t k, cost_conflict;
   int32_t cost_stitch, pad0;

@@ -133,7 +133,10 @@ __device__ __forceinline__ T ro_ld(const T *p) {
 // 16-bit counts of its conflict and stitch neighbours per mask, updated by
 // the same lanes, so the added cost of a segment's rows (Eq. 1) is read in
 // one load instead of gathered from its neighbours.
-template <typename FT, int MK, bool SM>
+// SMALL: at most 32 words of fields (n <= 128 for byte fields) and every
+// degree <= 32, so the column scan and the neighbour updates are single
+// predicated passes without loops.
+template <typename FT, int MK, bool SM, bool SMALL>
 struct Search {
   static constexpr uint32_t FB = 8 * sizeof(FT);    // bits per field
   static constexpr uint32_t FLAG = 1u << (FB - 1);   // column P_v uncovered
@@ -158,6 +161,16 @@ struct Search {
   __device__ __forceinline__ static int lane16(uint64_t w, int c) {
     return (int)((w >> (16 * (c & 3))) & 0xFFFFull);
   }
+  // f(i) for i = lane, lane + 32, ... < d
+  template <typename F>
+  __device__ __forceinline__ static void each(int d, int lane, F &&f) {
+    if constexpr (SMALL) {
+      if (lane < d) f(lane);
+    } else {
+      for (int i = lane; i < d; i += 32) f(i);
+    }
+  }
+
   // count word holding mask c of segment u
   __device__ __forceinline__ uint64_t *cw_of(uint64_t *cnt, int u, int c) const {
     return cnt + (size_t)u * CW + (c >> 2);
@@ -185,14 +198,14 @@ struct Search {
       x[v] = (int8_t)c;
     }
     const uint32_t clr = ~(1u << c);
-    for (int i = lane; i < dc; i += 32) {
+    each(dc, lane, [&](int i) {
       const int u = ro_ld<SM>(cnbr + cb + i);
       const FT f = rows[u];
       savf[cb + i] = f;
       rows[u] = (FT)(f & clr);
       move_count(ccnt, u, c, -1);
-    }
-    for (int i = lane; i < ds; i += 32) move_count(scnt, ro_ld<SM>(snbr + sb + i), c, -1);
+    });
+    each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, -1); });
     __syncwarp();
   }
 
@@ -202,12 +215,12 @@ struct Search {
                                              int ds, int lane) const {
     if (lane == 0) x[v] = (int8_t)c;
     const uint32_t clr = ~(1u << c);
-    for (int i = lane; i < dc; i += 32) {
+    each(dc, lane, [&](int i) {
       const int u = ro_ld<SM>(cnbr + cb + i);
       rows[u] = (FT)(savf[cb + i] & clr);
       move_count(ccnt, u, c, c_old);
-    }
-    for (int i = lane; i < ds; i += 32) move_count(scnt, ro_ld<SM>(snbr + sb + i), c, c_old);
+    });
+    each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, c_old); });
     __syncwarp();
   }
 
@@ -219,12 +232,12 @@ struct Search {
       rows[v] = oldf[v];
       x[v] = -1;
     }
-    for (int i = lane; i < dc; i += 32) {
+    each(dc, lane, [&](int i) {
       const int u = ro_ld<SM>(cnbr + cb + i);
       rows[u] = savf[cb + i];
       *cw_of(ccnt, u, c_last) -= one(c_last);
-    }
-    for (int i = lane; i < ds; i += 32) *cw_of(scnt, ro_ld<SM>(snbr + sb + i), c_last) -= one(c_last);
+    });
+    each(ds, lane, [&](int i) { *cw_of(scnt, ro_ld<SM>(snbr + sb + i), c_last) -= one(c_last); });
     __syncwarp();
   }
 
@@ -256,8 +269,8 @@ struct Search {
         // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v]),
         // PER_WORD fields per 32-bit load
         uint32_t key = 0xFFFFFFFFu, z = 0;
-        for (int wi = lane; wi < nwords; wi += 32) {
-          const uint32_t w = rows32[wi];
+        for (int wi = lane; SMALL ? wi == lane : wi < nwords; wi += 32) {
+          const uint32_t w = (!SMALL || wi < nwords) ? rows32[wi] : 0u;
 #pragma unroll
           for (int j = 0; j < PER_WORD; ++j) {
             const uint32_t f = (w >> (FB * j)) & FMASK;
@@ -349,10 +362,10 @@ struct Search {
 
 // Initialise the state at `base` and search.  SM says at compile time
 // whether `base` and `ro` point into shared memory.
-template <typename FT, int MK, bool SM>
+template <typename FT, int MK, bool SM, bool SMALL>
 __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
                                        const LaunchArgs &a, int lane) {
-  using S = Search<FT, MK, SM>;
+  using S = Search<FT, MK, SM, SMALL>;
   const int n = d.n;
   const StateLayout L = state_layout(n, d.ne2, d.k);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2);
@@ -403,7 +416,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
   const StateLayout L = state_layout(d.n, d.ne2, d.k);
   const RoLayout R = ro_layout(d.n, d.ne2, d.ns2);
   if (slot_bytes <= 0 || (int)(L.bytes + R.bytes) > slot_bytes) {
-    run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
+    run_in<FT, MK, false, false>(d, d.scratch, d.ro, a, lane);
     return true;
   }
   uint8_t *slot = g_smem + slot_off;
@@ -425,7 +438,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
       if (lane == 0) atomicExch(a.err, MPLD_E_TIMEOUT);
       for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
         if (mbar_try_wait(bar, phase ^ 1u)) break;
-      run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
+      run_in<FT, MK, false, false>(d, d.scratch, d.ro, a, lane);
       return false;
     }
   } else {
@@ -433,7 +446,11 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
     uint4 *d4 = (uint4 *)dst;
     for (uint32_t i = lane; i < R.bytes / 16; i += 32) d4[i] = __ldcg(src + i);
   }
-  run_in<FT, MK, true>(d, slot, dst, a, lane);
+  constexpr int PER_WORD = 4 / (int)sizeof(FT);
+  if (d.n <= 32 * PER_WORD && (d.maxdeg & 0xFFFF) <= 32 && ((uint32_t)d.maxdeg >> 16) <= 32)
+    run_in<FT, MK, true, true>(d, slot, dst, a, lane);
+  else
+    run_in<FT, MK, true, false>(d, slot, dst, a, lane);
   return true;
 }
 
@@ -623,7 +640,7 @@ __global__ void __launch_bounds__(32, 1)
   d.mask = mask_out;
   d.res = res_out;
   d.n = n;
-  d.pad2 = 0;
+  d.maxdeg = 0x7FFFFFFF;   // unknown: no small-instance specialisation
   d.ne2 = ne2;
   d.ns2 = ns2;
   d.ro_bytes = (int32_t)R.bytes;
