@@ -32,6 +32,15 @@ if HERE not in sys.path:
     sys.path.insert(0, HERE)
 
 METRIC = "EC search nodes/s & segments/s (batched vs plain GPU vs CPU DLX); p99 latency"
+
+# DRAM bytes per launch of the search kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the workload scaled down
+# by 10 (23,960 segments: 307,968 B read, 0 written), per segment; traffic
+# grows with the packed matrices, i.e. with the segments.  Valid only for the
+# kernel source it was measured on.
+TRAFFIC = {"k3_n200k_p02_batched": {"bytes_per_segment": 307968 / 23960,
+                                    "kernel_sha256_16": "716b82860eec59d9",
+                                    "profile": "profiles/mpld_search_kernel_k3_n20k_budget64k.md"}}
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 
 
@@ -325,8 +334,17 @@ def main():
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak_gops = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9
     achieved = res.work / (total_s / args.steps) / 1e9
+    traffic = None
+    tr = TRAFFIC.get(args.workload)
+    if tr is not None:
+        import hashlib
+        src = os.path.join(HERE, "paper_2303_14335_gb300", "csrc", "mpld_search.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == tr["kernel_sha256_16"]:
+            traffic = tr["bytes_per_segment"] * layout.n_seg
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak_gops,
-                       "unit": "Gop/s", "frac": achieved / alu_peak_gops, "traffic": None,
+                       "unit": "Gop/s", "frac": achieved / alu_peak_gops, "traffic": traffic,
+                       "traffic_source": ("ncu capture at 1/10 scale, scaled by segments"
+                                          if traffic is not None else None),
                        "peak_source": f"{props.multi_processor_count} SMs x 128 int32 lanes x "
                                       f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json)",
                        "work_ops_per_launch": res.work}
