@@ -31,6 +31,7 @@ E_INVALID = -1
 E_OOM = -2
 NO_SIMPLIFY = 1
 SINGLE_INSTANCE = 2
+COLUMN_BFS = 8      # the paper's column rule (single-row column, else BFS order)
 INF = (1 << 63) - 1
 
 
@@ -65,6 +66,9 @@ def _load():
         i32, i64 = ctypes.c_int32, ctypes.c_int64
         lib.oracle_solve_instance.argtypes = [i32, i32, i32, P, P, i32, P, P, i64, i64, i64, P, P, P]
         lib.oracle_solve_instance.restype = i32
+        lib.oracle_solve_instance_rule.argtypes = [i32, i32, i32, P, P, i32, P, P, i64, i64, i64, i32,
+                                                   P, P, P]
+        lib.oracle_solve_instance_rule.restype = i32
         lib.oracle_count_exact_covers.argtypes = [i32, i32, i32, P, P, i64, P]
         lib.oracle_count_exact_covers.restype = i32
         lib.oracle_export_matrix.argtypes = [i32, i32, i32, P, P, P]
@@ -92,8 +96,13 @@ class InstanceResult:
     x: np.ndarray
 
 
-def solve_instance(n, k, conf, stitch=(), cost_conflict=10, cost_stitch=1, budget=0) -> InstanceResult:
-    """Search one instance (the whole graph), Algorithm X with dancing links."""
+def solve_instance(n, k, conf, stitch=(), cost_conflict=10, cost_stitch=1, budget=0,
+                   rule=0) -> InstanceResult:
+    """Search one instance (the whole graph), Algorithm X with dancing links.
+
+    rule 0: column with the fewest rows, lowest index on ties; rule 1: the
+    paper's rule (a column with one row left, else breadth-first order).
+    """
     lib = _load()
     conf = np.asarray(conf, dtype=np.int32).reshape(-1, 2)
     stitch = np.asarray(stitch, dtype=np.int32).reshape(-1, 2)
@@ -102,9 +111,9 @@ def solve_instance(n, k, conf, stitch=(), cost_conflict=10, cost_stitch=1, budge
     x = np.full(max(n, 1), -1, dtype=np.int8)
     cost = ctypes.c_int64(0)
     nodes = ctypes.c_int64(0)
-    rc = lib.oracle_solve_instance(n, k, len(cu), _ptr(cu), _ptr(cv), len(su), _ptr(su), _ptr(sv),
-                                   cost_conflict, cost_stitch, budget, _ptr(x),
-                                   ctypes.byref(cost), ctypes.byref(nodes))
+    rc = lib.oracle_solve_instance_rule(n, k, len(cu), _ptr(cu), _ptr(cv), len(su), _ptr(su),
+                                        _ptr(sv), cost_conflict, cost_stitch, budget, rule, _ptr(x),
+                                        ctypes.byref(cost), ctypes.byref(nodes))
     if rc < 0:
         raise ValueError(f"oracle_solve_instance failed: {rc}")
     return InstanceResult(status=rc, cost=cost.value, nodes=nodes.value, x=x[:n].copy())

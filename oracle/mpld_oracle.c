@@ -32,8 +32,13 @@
  *   - bound: Z = number of uncovered primary columns of size 0; prune when
  *     g + Cc * Z >= best (admissible: such a segment sees every mask taken by
  *     a distinct conflict neighbour, so it will pay at least Cc);
- *   - column: minimum size S, lowest segment index on ties (Knuth's S
- *     heuristic over a ring kept in index order);
+ *   - column, rule 0 (default): minimum size S, lowest segment index on
+ *     ties (Knuth's S heuristic over a ring kept in index order);
+ *   - column, rule 1 (the paper's rule, Algorithm 1: "a column with only
+ *     one related row or in BFS order of G"): the lowest-index uncovered
+ *     column with exactly one row left, else the uncovered column first in
+ *     breadth-first order of the instance graph (conflict and stitch edges;
+ *     roots in ascending id; neighbours in ascending id);
  *   - rows of the chosen segment v: all k masks, visited in ascending
  *     (inc(c), c) with inc(c) = Cc * #{conflict nbr u: x_u = c}
  *                            + Cs * #{stitch nbr u: x_u assigned, x_u != c};
@@ -71,6 +76,7 @@
 
 #define OR_NO_SIMPLIFY 1u
 #define OR_SINGLE_INSTANCE 2u
+#define OR_COLUMN_BFS 8u
 
 #define OR_INF INT64_MAX
 
@@ -95,13 +101,15 @@ typedef struct {
   int done, budget_hit;
   int *colstack;     /* columns covered by the rows on the current path */
   int coltop;
+  int rule;          /* column rule: 0 fewest rows, 1 single row else BFS order */
+  int *bfs_rank;     /* rule 1: breadth-first rank of each segment */
 } dlx_t;
 
 static void dlx_free(dlx_t *d) {
   free(d->L); free(d->R); free(d->U); free(d->D); free(d->C); free(d->S);
   free(d->rownode); free(d->covered);
   free(d->cptr); free(d->cadj); free(d->sptr); free(d->sadj);
-  free(d->x); free(d->bestx); free(d->colstack);
+  free(d->x); free(d->bestx); free(d->colstack); free(d->bfs_rank);
   memset(d, 0, sizeof(*d));
 }
 
@@ -130,6 +138,41 @@ static int build_adj(int n, int m, const int *eu, const int *ev, int **ptr_out, 
   free(fill);
   *ptr_out = ptr;
   *adj_out = adj;
+  return OR_OK;
+}
+
+/* Breadth-first rank of every segment over conflict and stitch edges:
+ * roots in ascending id, each segment's neighbours in ascending id (a
+ * neighbour by both kinds of edge once). */
+static int bfs_ranks(int n, const int *cptr, const int *cadj, const int *sptr, const int *sadj,
+                     int **out) {
+  int *rank = malloc(sizeof(int) * (size_t)(n + 1));
+  int *queue = malloc(sizeof(int) * (size_t)(n + 1));
+  if (!rank || !queue) { free(rank); free(queue); return OR_E_OOM; }
+  for (int v = 0; v < n; ++v) rank[v] = -1;
+  int next = 0;
+  for (int r = 0; r < n; ++r) {
+    if (rank[r] >= 0) continue;
+    int qh = 0, qt = 0;
+    rank[r] = next++;
+    queue[qt++] = r;
+    while (qh < qt) {
+      const int u = queue[qh++];
+      int i = cptr[u], j = sptr[u];
+      while (i < cptr[u + 1] || j < sptr[u + 1]) {
+        int w;
+        if (j >= sptr[u + 1] || (i < cptr[u + 1] && cadj[i] <= sadj[j])) {
+          w = cadj[i++];
+          if (j < sptr[u + 1] && sadj[j] == w) ++j;
+        } else {
+          w = sadj[j++];
+        }
+        if (rank[w] < 0) { rank[w] = next++; queue[qt++] = w; }
+      }
+    }
+  }
+  free(queue);
+  *out = rank;
   return OR_OK;
 }
 
@@ -258,7 +301,13 @@ static void dlx_search(dlx_t *d, int64_t g) {
   int cmin = 0, smin = INT_MAX;
   for (int c = d->R[0]; c != 0; c = d->R[c]) {
     if (d->S[c] == 0) Z++;
-    if (d->S[c] < smin) { smin = d->S[c]; cmin = c; }
+    if (d->rule == 0) {
+      if (d->S[c] < smin) { smin = d->S[c]; cmin = c; }
+    } else if (smin != 1) {
+      /* first single-row column in index order, else lowest BFS rank */
+      if (d->S[c] == 1) { smin = 1; cmin = c; }
+      else if (cmin == 0 || d->bfs_rank[c - 1] < d->bfs_rank[cmin - 1]) cmin = c;
+    }
   }
   if (g + d->Cc * Z >= d->best) return;    /* admissible bound */
 
@@ -358,10 +407,11 @@ static int norm_edges(int n, int m, const int *u, const int *v, int **ou, int **
 
 /* Search one instance (the whole given graph, connected or not).
  * x_out: n masks; returns OR_OK / OR_BUDGET / error. */
-int oracle_solve_instance(int n, int k, int ne, const int *eu, const int *ev,
-                          int ns, const int *su, const int *sv,
-                          int64_t cost_conflict, int64_t cost_stitch, int64_t budget,
-                          signed char *x_out, int64_t *cost_out, int64_t *nodes_out) {
+int oracle_solve_instance_rule(int n, int k, int ne, const int *eu, const int *ev,
+                               int ns, const int *su, const int *sv,
+                               int64_t cost_conflict, int64_t cost_stitch, int64_t budget, int rule,
+                               signed char *x_out, int64_t *cost_out, int64_t *nodes_out) {
+  if (rule < 0 || rule > 1) return OR_E_INVALID;
   if (n < 0 || k < 2 || k > 8 || ne < 0 || ns < 0) return OR_E_INVALID;
   int *cu, *cv, *tu, *tv, mc, ms, rc;
   if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) return rc;
@@ -371,6 +421,11 @@ int oracle_solve_instance(int n, int k, int ne, const int *eu, const int *ev,
   free(cu); free(cv); free(tu); free(tv);
   if (rc != OR_OK) return rc;
   d.budget = budget;
+  d.rule = rule;
+  if (rule == 1 && bfs_ranks(n, d.cptr, d.cadj, d.sptr, d.sadj, &d.bfs_rank) != OR_OK) {
+    dlx_free(&d);
+    return OR_E_OOM;
+  }
   dlx_search(&d, 0);
   memcpy(x_out, d.bestx, (size_t)n);
   *cost_out = d.best;
@@ -378,6 +433,14 @@ int oracle_solve_instance(int n, int k, int ne, const int *eu, const int *ev,
   rc = d.budget_hit ? OR_BUDGET : OR_OK;
   dlx_free(&d);
   return rc;
+}
+
+int oracle_solve_instance(int n, int k, int ne, const int *eu, const int *ev,
+                          int ns, const int *su, const int *sv,
+                          int64_t cost_conflict, int64_t cost_stitch, int64_t budget,
+                          signed char *x_out, int64_t *cost_out, int64_t *nodes_out) {
+  return oracle_solve_instance_rule(n, k, ne, eu, ev, ns, su, sv, cost_conflict, cost_stitch,
+                                    budget, 0, x_out, cost_out, nodes_out);
 }
 
 /* Number of exact covers of the EC matrix (primary columns exactly once,
@@ -432,7 +495,7 @@ typedef struct {
 
 typedef struct {
   /* shared, read-only */
-  int k, n_comp;
+  int k, n_comp, rule;
   int64_t Cc, Cs, budget;
   const int *comp_ptr, *comp_seg;     /* segments of component i, ascending */
   const int *local_of;                /* global segment -> local id */
@@ -477,7 +540,8 @@ static void solve_component(pool_t *P, int ci) {
       }
   }
   int64_t cost = 0, nodes = 0;
-  int rc = oracle_solve_instance(n, P->k, ne, eu, ev, ns, su, sv, P->Cc, P->Cs, P->budget, x, &cost, &nodes);
+  int rc = oracle_solve_instance_rule(n, P->k, ne, eu, ev, ns, su, sv, P->Cc, P->Cs, P->budget,
+                                      P->rule, x, &cost, &nodes);
   if (rc < 0) { atomic_store(&P->error, rc); goto out; }
   for (int t = a; t < b; ++t) P->mask[P->comp_seg[t]] = x[t - a];
   P->comp_cost[ci] = cost;
@@ -513,7 +577,7 @@ static int find_root(int *parent, int a) {
  * Decompose a whole layout.
  *   polygon_of: segment -> polygon id in [0, n_seg), or NULL (each segment
  *               its own polygon);
- *   flags: OR_NO_SIMPLIFY, OR_SINGLE_INSTANCE;
+ *   flags: OR_NO_SIMPLIFY, OR_SINGLE_INSTANCE, OR_COLUMN_BFS (column rule 1);
  *   nthreads: worker threads for the per-component searches (>= 1);
  *   mask_out[n_seg]; comp_of_out[n_seg] (nullable): component of each
  *   segment, -1 if removed by simplification; comp_nodes_out /
@@ -686,6 +750,7 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
     pool_t P;
     memset(&P, 0, sizeof(P));
     P.k = k; P.n_comp = n_comp; P.Cc = cost_conflict; P.Cs = cost_stitch; P.budget = budget;
+    P.rule = (flags & OR_COLUMN_BFS) ? 1 : 0;
     P.comp_ptr = comp_ptr; P.comp_seg = comp_seg; P.local_of = local_of; P.comp_of = comp_of;
     P.cptr = cptr; P.cadj = cadj; P.sptr = sptr; P.sadj = sadj; P.work_order = order;
     P.mask = mask_out; P.comp_cost = ccost; P.comp_nodes = cnodes; P.comp_status = cstat;

@@ -40,20 +40,49 @@ def brute_force(n, k, conf, stitch, cc=10, cs=1):
     return m, int((cost == m).sum())
 
 
+def bfs_rank(n, conf, stitch):
+    """Breadth-first rank over conflict and stitch edges: roots in ascending
+    id, each segment's neighbours (by either kind of edge) in ascending id."""
+    nb = adjacency(n, list(conf) + list(stitch))
+    rank = [-1] * n
+    nxt = 0
+    for r in range(n):
+        if rank[r] >= 0:
+            continue
+        rank[r] = nxt
+        nxt += 1
+        queue = [r]
+        while queue:
+            u = queue.pop(0)
+            for w in nb[u]:
+                if rank[w] < 0:
+                    rank[w] = nxt
+                    nxt += 1
+                    queue.append(w)
+    return rank
+
+
 class _Search:
-    def __init__(self, n, k, conf, stitch, cc, cs):
+    def __init__(self, n, k, conf, stitch, cc, cs, rule=0):
         self.n, self.k, self.cc, self.cs = n, k, cc, cs
         self.cadj = adjacency(n, conf)
         self.sadj = adjacency(n, stitch)
         self.x = [-1] * n
+        self.rule = rule
+        self.rank = bfs_rank(n, conf, stitch) if rule == 1 else None
 
     def avail(self, v):
         used = {self.x[u] for u in self.cadj[v] if self.x[u] >= 0}
         return self.k - len(used)
 
     def pick(self):
-        """Unassigned segment with fewest available masks, lowest index on ties; and Z."""
+        """Column to branch on, and Z (uncovered segments with no available mask).
+
+        rule 0: fewest available masks, lowest index on ties; rule 1: lowest
+        index with exactly one available mask, else lowest breadth-first rank.
+        """
         best_v, best_a, z = -1, None, 0
+        single, by_rank = -1, -1
         for v in range(self.n):
             if self.x[v] >= 0:
                 continue
@@ -62,6 +91,13 @@ class _Search:
                 z += 1
             if best_a is None or a < best_a:
                 best_v, best_a = v, a
+            if self.rule == 1:
+                if a == 1 and single < 0:
+                    single = v
+                if by_rank < 0 or self.rank[v] < self.rank[by_rank]:
+                    by_rank = v
+        if self.rule == 1 and best_v >= 0:
+            best_v = single if single >= 0 else by_rank
         return best_v, z
 
     def row_order(self, v):
@@ -73,13 +109,13 @@ class _Search:
         return sorted(range(self.k), key=lambda c: (inc[c], c)), inc
 
 
-def canonical_leaves(n, k, conf, stitch, cc=10, cs=1):
+def canonical_leaves(n, k, conf, stitch, cc=10, cs=1, rule=0):
     """Every leaf of the bound-free canonical search tree, in depth-first order.
 
     Returns a list of (cost, x).  The method's answer is the first leaf of
     minimum cost in this list.
     """
-    S = _Search(n, k, conf, stitch, cc, cs)
+    S = _Search(n, k, conf, stitch, cc, cs, rule)
     out = []
 
     def rec(g):
@@ -97,15 +133,15 @@ def canonical_leaves(n, k, conf, stitch, cc=10, cs=1):
     return out
 
 
-def first_min_leaf(n, k, conf, stitch, cc=10, cs=1):
-    leaves = canonical_leaves(n, k, conf, stitch, cc, cs)
+def first_min_leaf(n, k, conf, stitch, cc=10, cs=1, rule=0):
+    leaves = canonical_leaves(n, k, conf, stitch, cc, cs, rule)
     m = min(c for c, _ in leaves)
     for c, x in leaves:
         if c == m:
             return c, x
 
 
-def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0):
+def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0):
     """The canonical search with the dead-segment bound and node budget.
 
     node = one call; leaf with g < best is the new incumbent and best == 0
@@ -114,7 +150,7 @@ def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0):
     nodes have been counted stops everything.  Returns (cost, x, nodes,
     budget_hit).
     """
-    S = _Search(n, k, conf, stitch, cc, cs)
+    S = _Search(n, k, conf, stitch, cc, cs, rule)
     st = dict(best=None, bestx=None, nodes=0, done=False, hit=False)
 
     def rec(g):

@@ -320,3 +320,47 @@ def test_empty_and_isolated():
     assert res.n_removed_segments == 5 and np.all(res.mask == 0)
     res = oracle.decompose(L, flags=oracle.NO_SIMPLIFY)
     assert res.n_components == 5 and res.nodes == 10 and np.all(res.mask == 0)
+
+
+# ---------------------------------------------------------------- paper's column rule
+
+def test_bfs_rank_hand_example():
+    # path 0-1-2 plus stitch 0-3 and isolated 4: BFS from 0 visits 1, 3 (ascending), then 2
+    from graph_dfs import bfs_rank
+    assert bfs_rank(5, [(0, 1), (1, 2)], [(0, 3)]) == [0, 1, 3, 2, 4]
+
+
+@pytest.mark.parametrize("n,k,seed,p,ns", random_cases(40, 10))
+def test_paper_column_rule_matches_brute_force_and_independent_search(n, k, seed, p, ns):
+    L = synth.random_graph(n, k, seed=seed, p_edge=p, n_stitch=ns)
+    conf, st = edges(L)
+    r = oracle.solve_instance(n, k, conf, st, rule=1)
+    m, _ = brute_force(n, k, conf, st)
+    assert r.cost == m and eq1_cost(r.x, conf, st) == m
+    if k ** n <= 20000:
+        assert first_min_leaf(n, k, conf, st, rule=1) == (r.cost, r.x.tolist())
+    c2, x2, nodes2, _ = bounded_search(n, k, conf, st, rule=1)
+    assert (c2, x2, nodes2) == (r.cost, r.x.tolist(), r.nodes)
+
+
+@pytest.mark.parametrize("budget", [12, 50, 400])
+def test_paper_column_rule_budget(budget):
+    L = synth.unit_disk_layout(14, 3, seed=404, mean_deg=4.5, p_stitch=0.25)
+    conf, st = edges(L)
+    r = oracle.solve_instance(L.n_seg, 3, conf, st, budget=budget, rule=1)
+    c2, x2, nodes2, hit2 = bounded_search(L.n_seg, 3, conf, st, budget=budget, rule=1)
+    assert (r.cost, r.x.tolist(), r.nodes, r.status == oracle.BUDGET) == (c2, x2, nodes2, hit2)
+
+
+def test_paper_column_rule_in_layout_flow():
+    L = synth.unit_disk_layout(3000, 3, seed=21, mean_deg=3.5, p_stitch=0.2)
+    a = oracle.decompose(L, budget=3000, flags=oracle.COLUMN_BFS, nthreads=4)
+    conf, st = edges(L)
+    assert eq1_cost(a.mask, conf, st) == a.cost == a.component_cost_sum
+    for c in range(0, a.n_components, 9):
+        segs = np.nonzero(a.comp_of == c)[0]
+        loc = {int(s): i for i, s in enumerate(segs)}
+        cc = [(loc[u], loc[v]) for u, v in conf if u in loc and v in loc]
+        ss = [(loc[u], loc[v]) for u, v in st if u in loc and v in loc]
+        r = oracle.solve_instance(len(segs), 3, cc, ss, budget=3000, rule=1)
+        assert r.nodes == a.comp_nodes[c] and np.array_equal(r.x, a.mask[segs])
