@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="k3_n200k_p02_batched")
     ap.add_argument("--budget", type=int, default=1 << 16)
+    ap.add_argument("--column-rule", choices=["mrv", "bfs"], default="mrv",
+                    help="column to branch on: fewest rows (mrv) or the paper's rule "
+                         "(a single-row column, else breadth-first order)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -162,7 +165,9 @@ def run_serving(args, mpld, synth):
         arrivals = synth.poisson_arrivals(777 + rate, n, rate)
         cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
                                       max_in_flight=256, streams=16)
-        srv = mpld.mpld_server_create(cfg, mpld.make_params(node_budget=args.serve_budget))
+        srv = mpld.mpld_server_create(cfg, mpld.make_params(
+            node_budget=args.serve_budget,
+            flags=mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0))
         arrival_of, lat, segs = {}, [], 0
         t0 = time.perf_counter()
         i = 0
@@ -209,6 +214,8 @@ def run_reference(args, rank, world):
     import oracle
     layout, mode = workload_layout(args.workload, 0)
     flags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
+    if args.column_rule == "bfs":
+        flags |= oracle.COLUMN_BFS
     cores = os.cpu_count() or 1
     oracle.build()
     for _ in range(args.warmup):
@@ -227,7 +234,7 @@ def run_reference(args, rank, world):
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "segments": layout.n_seg, "k": layout.k,
-                   "node_budget": args.budget},
+                   "node_budget": args.budget, "column_rule": args.column_rule},
         "nodes_per_s": res.nodes * args.steps / total,
         "cpu_baseline": {"value": value, "unit": "segments/s", "cores": cores, "kind": "oracle",
                          "sample": f"whole layout ({layout.n_seg} segments, "
@@ -263,7 +270,8 @@ def main():
     flags = (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE) if mode == "single" else 0
     prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
     info = mpld.mpld_problem_info(prob)
-    prm = mpld.make_params(node_budget=args.budget)
+    rule_flag = mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0
+    prm = mpld.make_params(node_budget=args.budget, flags=rule_flag)
     tune = None
     if not args.no_tune:
         tune = mpld.mpld_autotune([prob], prm, s)
@@ -310,7 +318,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload + (f"/scale{args.scale}" if args.scale > 1 else ""),
                    "segments": layout.n_seg, "polygons": layout.n_poly,
-                   "k": layout.k, "node_budget": args.budget, "instances": info.n_components,
+                   "k": layout.k, "node_budget": args.budget, "column_rule": args.column_rule,
+                   "instances": info.n_components,
                    "max_instance": info.max_component,
                    "removed_segments": info.n_removed_segments,
                    "l2": "flushed between timed steps (256 MB write)",
@@ -412,7 +421,10 @@ def main():
         oracle.build()
         cores = os.cpu_count() or 1
         t0 = time.perf_counter()
-        ref = oracle.decompose(layout, flags=flags, budget=args.budget, nthreads=cores)
+        oflags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
+        if args.column_rule == "bfs":
+            oflags |= oracle.COLUMN_BFS
+        ref = oracle.decompose(layout, flags=oflags, budget=args.budget, nthreads=cores)
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": layout.n_seg / dt, "unit": "segments/s", "cores": cores,
                                "kind": "oracle",

@@ -52,6 +52,13 @@ extern "C" {
 /* mpld_params.flags */
 #define MPLD_NO_SIMPLIFY 1u      /* skip the simplification step (Sec. 2.2) */
 #define MPLD_SINGLE_INSTANCE 2u  /* search all remaining segments as ONE instance (no sub-graph split) */
+#define MPLD_COLUMN_BFS 8u       /* search with the paper's column rule (Algorithm 1): the lowest-index
+                                    uncovered column with a single row left, else the uncovered column
+                                    first in breadth-first order of the sub-graph (conflict and stitch
+                                    edges, roots and neighbours in ascending id).  Default: the column
+                                    with the fewest rows, lowest index on ties.  Read by the search
+                                    calls and by mpld_server_create; not available to
+                                    mpld_search_instance_noalloc. */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
                                     the solve calls then return MPLD_E_STATE */
@@ -94,7 +101,8 @@ typedef struct {
  *                  and keeps its incumbent (the layout status is then
  *                  MPLD_BUDGET);
  *   flags          MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_HOST_ONLY
- *                  (used by mpld_build_matrix);
+ *                  (used by mpld_build_matrix); MPLD_COLUMN_BFS (used by the
+ *                  search calls);
  *   warps_per_cta, slot_bytes   launch shape of the batched kernel; 0 = the
  *                  tuned or default shape (see mpld_autotune).
  */

@@ -323,6 +323,38 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       }
       ptr[2 * nc] = ci;
       ptr[2 * nc + 1] = si;
+      // breadth-first ranks over conflict and stitch edges (local ids):
+      // roots ascending, each segment's neighbours ascending, once each
+      uint16_t *rank = (uint16_t *)(blk + R.rank);
+      uint16_t *order = (uint16_t *)(blk + R.order);
+      std::vector<uint8_t> seen((size_t)nc, 0);
+      int nxt = 0, qh = 0;
+      for (int r = 0; r < nc; ++r) {
+        if (seen[r]) continue;
+        seen[r] = 1;
+        rank[r] = (uint16_t)nxt;
+        order[nxt++] = (uint16_t)r;
+        qh = nxt - 1;
+        while (qh < nxt) {
+          const int u = order[qh++];
+          int i = ptr[2 * u], j = ptr[2 * u + 1];
+          const int ie = ptr[2 * u + 2], je = ptr[2 * u + 3];
+          while (i < ie || j < je) {
+            int w;
+            if (j >= je || (i < ie && cn[i] <= sn[j])) {
+              w = cn[i++];
+              if (j < je && sn[j] == w) ++j;
+            } else {
+              w = sn[j++];
+            }
+            if (!seen[w]) {
+              seen[w] = 1;
+              rank[w] = (uint16_t)nxt;
+              order[nxt++] = (uint16_t)w;
+            }
+          }
+        }
+      }
     }
     // largest first (ties: lower instance id first)
     p->h_order.resize((size_t)C);
@@ -435,6 +467,7 @@ int64_t time_limit_ns(const mpld_params *prm) {
   return ms * 1000000ll;
 }
 int64_t budget_of(const mpld_params *prm) { return prm ? std::max<int64_t>(prm->node_budget, 0) : 0; }
+int rule_of(const mpld_params *prm) { return (prm && (prm->flags & MPLD_COLUMN_BFS)) ? 1 : 0; }
 
 uint32_t max_footprint(mpld_problem *const *ps, int n) {
   uint32_t m = 0;
@@ -497,6 +530,8 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   a.err = p->d_err;
   a.budget = budget_of(prm);
   a.time_limit_ns = time_limit_ns(prm);
+  a.rule = rule_of(prm);
+  a.pad = 0;
   auto body = [&]() -> int {
     int rc = cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
     if (rc) return rc;
@@ -514,7 +549,7 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     return rc;
   };
   if (!capturable(stream)) return body();
-  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns};
+  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns, a.rule};
   key.ctas = copy_back ? sh.ctas : -sh.ctas;  // copy-back variant is a different graph
   if (!p->gexec || !(p->gkey == key) || p->gstream != stream) {
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
@@ -629,6 +664,10 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
     a.err = p->d_err;
     a.budget = budget_of(prm);
     a.time_limit_ns = time_limit_ns(prm);
+    a.rule = rule_of(prm);
+    a.pad = 0;
+  a.rule = rule_of(prm);
+  a.pad = 0;
     rc = mpld_internal_launch(&a, 1, 1, st);
   }
   p->searched = rc == MPLD_OK;
@@ -687,6 +726,8 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   a.err = ps[0]->d_err;
   a.budget = budget_of(prm);
   a.time_limit_ns = time_limit_ns(prm);
+  a.rule = rule_of(prm);
+  a.pad = 0;
   for (int i = 0; i < n; ++i) {
     if (i) rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_err, 0, 4, st));
     rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_res, 0xFF,

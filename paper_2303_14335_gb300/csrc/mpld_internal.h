@@ -29,8 +29,13 @@ MPLD_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 //   ptr[n+1]  int2    {conflict CSR offset, stitch CSR offset} per segment
 //   cnbr[ne2] uint16  conflict neighbours (component-local), ascending
 //   snbr[ns2] uint16  stitch neighbours, ascending
+//   rank[n]   uint16  breadth-first rank of each segment over conflict and
+//                     stitch edges (roots ascending, neighbours ascending)
+//   order[n]  uint16  segment of each breadth-first rank
+// (rank / order serve the paper's column rule, Algorithm 1: a column with a
+// single row left, else the first uncovered column in BFS order of G.)
 struct RoLayout {
-  uint32_t ptr, cnbr, snbr, bytes;
+  uint32_t ptr, cnbr, snbr, rank, order, bytes;
 };
 MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
   RoLayout L;
@@ -38,6 +43,8 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
   L.ptr = o; o += align16(8u * (uint32_t)(n + 1));
   L.cnbr = o; o += align16(2u * (uint32_t)ne2);
   L.snbr = o; o += align16(2u * (uint32_t)ns2);
+  L.rank = o; o += align16(2u * (uint32_t)n);
+  L.order = o; o += align16(2u * (uint32_t)n);
   L.bytes = o;
   return L;
 }
@@ -115,6 +122,8 @@ struct LaunchArgs {
   int32_t *err;            // device status word (0 = fine)
   int64_t budget;
   int64_t time_limit_ns;
+  int32_t rule;            // column rule: 0 fewest rows, 1 single row else BFS order
+  int32_t pad;
 };
 
 }  // namespace mpld

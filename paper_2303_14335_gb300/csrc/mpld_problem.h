@@ -17,8 +17,10 @@ namespace mpld {
 struct GraphKey {
   int nw = 0, slot = 0, ctas = 0;
   int64_t budget = 0, tl = 0;
+  int rule = 0;
   bool operator==(const GraphKey &o) const {
-    return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl;
+    return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl &&
+           rule == o.rule;
   }
 };
 

@@ -153,9 +153,11 @@ struct Search {
   int8_t *x;
   const int2 *ptr;    // {conflict offset, stitch offset} per segment
   const uint16_t *cnbr, *snbr;
+  const uint16_t *rank, *order;   // breadth-first rank / segment of each rank
   int n, k;
   int Cc, Cs;
   uint32_t kmask;
+  int rule;           // 0: fewest rows, lowest index; 1: single row, else BFS order
 
   __device__ __forceinline__ static uint64_t one(int c) { return 1ull << (16 * (c & 3)); }
   __device__ __forceinline__ static int lane16(uint64_t w, int c) {
@@ -267,19 +269,37 @@ struct Search {
           if ((int64_t)(now - t0) > time_limit_ns) { status = MPLD_TIMEOUT; break; }
         }
         // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v]),
-        // PER_WORD fields per 32-bit load
+        // PER_WORD fields per 32-bit load.  Rule 0 keys (count, v); rule 1
+        // (the paper's) keys single-row columns by v ahead of all others,
+        // which go by breadth-first rank.
         uint32_t key = 0xFFFFFFFFu, z = 0;
-        for (int wi = lane; SMALL ? wi == lane : wi < nwords; wi += 32) {
-          const uint32_t w = (!SMALL || wi < nwords) ? rows32[wi] : 0u;
+        if (rule == 0) {
+          for (int wi = lane; SMALL ? wi == lane : wi < nwords; wi += 32) {
+            const uint32_t w = (!SMALL || wi < nwords) ? rows32[wi] : 0u;
 #pragma unroll
-          for (int j = 0; j < PER_WORD; ++j) {
-            const uint32_t f = (w >> (FB * j)) & FMASK;
-            const uint32_t kv = (f & FLAG)
-                                    ? ((uint32_t)__popc(f & kmask) << 16) |
-                                          (uint32_t)(wi * PER_WORD + j)
-                                    : 0xFFFFFFFFu;
-            key = min(key, kv);
-            z += kv <= 0xFFFFu;  // uncovered column with no active row
+            for (int j = 0; j < PER_WORD; ++j) {
+              const uint32_t f = (w >> (FB * j)) & FMASK;
+              const uint32_t kv = (f & FLAG)
+                                      ? ((uint32_t)__popc(f & kmask) << 16) |
+                                            (uint32_t)(wi * PER_WORD + j)
+                                      : 0xFFFFFFFFu;
+              key = min(key, kv);
+              z += kv <= 0xFFFFu;  // uncovered column with no active row
+            }
+          }
+        } else {
+          for (int wi = lane; SMALL ? wi == lane : wi < nwords; wi += 32) {
+            const uint32_t w = (!SMALL || wi < nwords) ? rows32[wi] : 0u;
+#pragma unroll
+            for (int j = 0; j < PER_WORD; ++j) {
+              const uint32_t f = (w >> (FB * j)) & FMASK;
+              const uint32_t seg = (uint32_t)(wi * PER_WORD + j);
+              const uint32_t cnt = (uint32_t)__popc(f & kmask);
+              uint32_t kv = 0xFFFFFFFFu;
+              if (f & FLAG) kv = cnt == 1 ? seg : 0x10000u | (uint32_t)ro_ld<SM>(rank + seg);
+              key = min(key, kv);
+              z += (f & FLAG) && cnt == 0;
+            }
           }
         }
         key = __reduce_min_sync(FULL, key);
@@ -295,11 +315,12 @@ struct Search {
         }
         if (best < INF32) {
           // the bound needs the number of uncovered columns with no active
-          // row only when there is one (the minimum count is then 0)
-          z = (key >> 16) == 0 ? __reduce_add_sync(FULL, z) : 0u;
+          // row; under rule 0 there is one only when the minimum count is 0
+          z = (rule != 0 || (key >> 16) == 0) ? __reduce_add_sync(FULL, z) : 0u;
           if ((int64_t)g + (int64_t)Cc * z >= best) { enter = false; continue; }
         }
-        const int v = (int)(key & 0xFFFFu);
+        const int v = (rule == 0 || key < 0x10000u) ? (int)(key & 0xFFFFu)
+                                                     : (int)ro_ld<SM>(order + (key & 0xFFFFu));
         // added cost of each row (v, c) against the current assignment (Eq. 1)
         const int2 p0 = ro_ld<SM>(ptr + v), p1 = ro_ld<SM>(ptr + v + 1);
         const uint64_t cc0 = ccnt[(size_t)v * CW], sc0 = scnt[(size_t)v * CW];
@@ -381,6 +402,9 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   s.ptr = (const int2 *)(ro + R.ptr);
   s.cnbr = (const uint16_t *)(ro + R.cnbr);
   s.snbr = (const uint16_t *)(ro + R.snbr);
+  s.rank = (const uint16_t *)(ro + R.rank);
+  s.order = (const uint16_t *)(ro + R.order);
+  s.rule = a.rule;
   s.n = n;
   s.k = d.k;
   s.Cc = d.cost_conflict;
@@ -421,13 +445,15 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
   }
   uint8_t *slot = g_smem + slot_off;
   uint8_t *dst = slot + L.bytes;
-  if (R.bytes >= TMA_MIN_BYTES) {
-    // one bulk copy of the whole read-only block into shared memory
+  // the breadth-first tables at the end of the block are read under rule 1 only
+  const uint32_t ro_copy = a.rule ? R.bytes : R.rank;
+  if (ro_copy >= TMA_MIN_BYTES) {
+    // one bulk copy of the read-only block into shared memory
     __syncwarp();
     if (lane == 0) {
       fence_proxy_async();
-      mbar_expect_tx(bar, R.bytes);
-      bulk_copy_g2s(dst, d.ro, R.bytes, bar);
+      mbar_expect_tx(bar, ro_copy);
+      bulk_copy_g2s(dst, d.ro, ro_copy, bar);
     }
     bool ok = false;
     for (uint32_t it = 0; it < WAIT_LIMIT && !ok; ++it) ok = mbar_try_wait(bar, phase);
@@ -444,7 +470,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
   } else {
     const uint4 *src = (const uint4 *)d.ro;
     uint4 *d4 = (uint4 *)dst;
-    for (uint32_t i = lane; i < R.bytes / 16; i += 32) d4[i] = __ldcg(src + i);
+    for (uint32_t i = lane; i < ro_copy / 16; i += 32) d4[i] = __ldcg(src + i);
   }
   constexpr int PER_WORD = 4 / (int)sizeof(FT);
   if (d.n <= 32 * PER_WORD && (d.maxdeg & 0xFFFF) <= 32 && ((uint32_t)d.maxdeg >> 16) <= 32)
@@ -659,6 +685,8 @@ __global__ void __launch_bounds__(32, 1)
   a.err = err;
   a.budget = budget;
   a.time_limit_ns = time_limit_ns;
+  a.rule = 0;
+  a.pad = 0;
   uint32_t phase = 0;
   const uint32_t slot_off = align16(8u);
   if (d.k == 3) run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, a, lane);
@@ -686,6 +714,7 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
                                             mpld_instance_result *result_out, void *stream) {
   using namespace mpld;
   if (!inst || !mask_out || !result_out || !inst->conf_ptr || !inst->st_ptr) return MPLD_E_INVALID;
+  if (prm && (prm->flags & MPLD_COLUMN_BFS)) return MPLD_E_INVALID;  // no breadth-first ranks here
   const int n = inst->n, k = inst->k, ne2 = inst->n_conf_entries, ns2 = inst->n_stitch_entries;
   if (n < 1 || k < 2 || k > 8 || ne2 < 0 || ns2 < 0) return MPLD_E_INVALID;
   if ((ne2 > 0 && !inst->conf_nbr) || (ns2 > 0 && !inst->st_nbr)) return MPLD_E_INVALID;

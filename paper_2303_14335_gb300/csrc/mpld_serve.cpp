@@ -146,6 +146,7 @@ int cuda_ok(cudaError_t e) {
 struct mpld_server {
   mpld_server_config cfg{};
   int64_t budget = 0, tl_ns = 0;
+  int rule = 0;
   int nsm = 1, max_slot = 0;
   std::vector<cudaStream_t> streams;
   uint64_t next_stream = 0;
@@ -282,6 +283,8 @@ int launch_request(mpld_server *s, Req &r) {
   a.err = d_err;
   a.budget = s->budget;
   a.time_limit_ns = s->tl_ns;
+  a.rule = s->rule;
+  a.pad = 0;
   rc = mpld_internal_launch(&a, ctas, nw, st);
   if (rc) return rc;
   rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_res, d_res, sizeof(InstResult) * (size_t)C,
@@ -324,6 +327,7 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
   s->cfg = cfg;
   s->budget = search ? std::max<int64_t>(search->node_budget, 0) : 0;
   s->tl_ns = ((search && search->time_limit_ms > 0) ? search->time_limit_ms : 60000) * 1000000ll;
+  s->rule = (search && (search->flags & MPLD_COLUMN_BFS)) ? 1 : 0;
   s->nsm = std::max(1, mpld_internal_num_sms());
   s->max_slot = mpld_internal_max_slot_bytes(cfg.warps_per_cta);
   if (s->max_slot <= 0) {

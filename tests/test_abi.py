@@ -115,6 +115,15 @@ def test_invalid_inputs_rejected():
         host_only(L)
 
 
+def test_noalloc_entry_rejects_the_column_rule_before_any_device_work():
+    # the allocation-free entry has no breadth-first ranks: the flag is an
+    # argument error, reported before a pointer is followed or a device used
+    prm = mpld.make_params(flags=mpld.MPLD_COLUMN_BFS)
+    with pytest.raises(mpld.MpldError) as e:
+        mpld.mpld_search_instance_noalloc(4, 3, 256, 512, 0, 768, 1024, 0, 1280, 1536, prm)
+    assert e.value.code == mpld.MPLD_E_INVALID
+
+
 def test_too_large_instance_rejected():
     n = 70000
     L = synth.graph_from_edges(n, 3, [(i, i + 1) for i in range(n - 1)])

@@ -38,10 +38,11 @@ def edges(L):
     return list(zip(L.conf_u.tolist(), L.conf_v.tolist())), list(zip(L.st_u.tolist(), L.st_v.tolist()))
 
 
-def gpu_run(L, flags=0, budget=0, path="batch", stream=0, warps=0, slot=0, time_limit_ms=0):
+def gpu_run(L, flags=0, budget=0, path="batch", stream=0, warps=0, slot=0, time_limit_ms=0,
+            search_flags=0):
     prob = mpld.mpld_build_matrix(L, mpld.make_params(flags=flags), stream)
     prm = mpld.make_params(node_budget=budget, warps_per_cta=warps, slot_bytes=slot,
-                           time_limit_ms=time_limit_ms)
+                           time_limit_ms=time_limit_ms, flags=search_flags)
     if path == "plain":
         rc, mask, res = mpld.mpld_solve(prob, prm, stream)
     else:
@@ -165,6 +166,65 @@ def test_batched_workloads_bench_budget_sampled(name, stream):
                                   np.stack([loc[su[ms]], loc[sv[ms]]], 1), budget=budget)
         assert r.cost == g["cost"][c] and r.nodes == g["nodes"][c]
         assert np.array_equal(r.x, g["mask"][segs])
+
+
+# ------------------------------------------- the paper's column rule (rule 1)
+
+BFS = mpld.MPLD_COLUMN_BFS
+
+
+@pytest.mark.parametrize("n,k,seed,p", small_cases()[::2])
+def test_rule1_small_single_instance(n, k, seed, p, stream):
+    L = synth.random_graph(n, k, seed=seed, p_edge=p, n_stitch=n // 4, identity_polygons=False)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | oracle.COLUMN_BFS,
+                           budget=200000)
+    for path in ("batch", "plain"):
+        g = gpu_run(L, flags=SINGLE, budget=200000, path=path, stream=stream.cuda_stream,
+                    search_flags=BFS)
+        assert_same(g, ref, L)
+
+
+@pytest.mark.parametrize("budget", [1, 40, 333, 5000])
+def test_rule1_budget_parity(budget, stream):
+    L = synth.unit_disk_layout(40, 3, seed=91, mean_deg=5.0, p_stitch=0.25)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | oracle.COLUMN_BFS,
+                           budget=budget)
+    g = gpu_run(L, flags=SINGLE, budget=budget, stream=stream.cuda_stream, search_flags=BFS)
+    assert_same(g, ref, L)
+
+
+def test_rule1_k8_several_words(stream):
+    L = synth.unit_disk_layout(700, 8, seed=3, mean_deg=9.0)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | oracle.COLUMN_BFS,
+                           budget=20000)
+    assert_same(gpu_run(L, flags=SINGLE, budget=20000, stream=stream.cuda_stream, search_flags=BFS),
+                ref, L)
+
+
+@pytest.mark.parametrize("name", ["k3_n200k_p02_batched", "k4_n100k_p03_batched"])
+def test_rule1_batched_workloads_full_size(name, stream):
+    L, mode = synth.workload(name)
+    ref = oracle.decompose(L, flags=oracle.COLUMN_BFS, budget=3000, nthreads=NTHREADS)
+    g = gpu_run(L, budget=3000, stream=stream.cuda_stream, search_flags=BFS)
+    assert_same(g, ref, L)
+    # the rule changes the search, not the problem: a plain-path run agrees
+    # with the batched one
+    p = gpu_run(L, budget=3000, path="plain", stream=stream.cuda_stream, search_flags=BFS)
+    assert np.array_equal(p["mask"], g["mask"]) and np.array_equal(p["nodes"], g["nodes"])
+
+
+def test_rule1_graph_cache_keeps_rules_apart(stream):
+    # same problem, same shape, the two rules alternately: a cached graph of
+    # one rule must never serve the other
+    L = synth.unit_disk_layout(8000, 3, seed=14, mean_deg=3.0, p_stitch=0.2)
+    prob = mpld.mpld_build_matrix(L, None, stream.cuda_stream)
+    refs = {f: oracle.decompose(L, flags=f and oracle.COLUMN_BFS, budget=1000, nthreads=NTHREADS)
+            for f in (0, BFS)}
+    for f in (0, BFS, 0, BFS):
+        rc, m, r = mpld.mpld_solve_batch([prob], mpld.make_params(node_budget=1000, flags=f),
+                                         stream.cuda_stream)
+        assert np.array_equal(m[0], refs[f].mask) and r[0].nodes == refs[f].nodes
+    prob.close()
 
 
 # ---------------------------------------------------------------- launch forms

@@ -129,3 +129,17 @@ def test_empty_and_fully_simplified_requests(torch_cuda):
     assert got[t0][0] == 0 and got[t0][2].n_components == 0
     rc, mask, res = got[t1]
     assert rc == 0 and res.cost == 0 and res.n_removed_segments == 6 and np.all(mask >= 0)
+
+
+def test_column_rule_flag_reaches_served_searches(torch_cuda):
+    # a server created with the paper's column rule searches every request
+    # with it: results equal the oracle's under the same rule
+    Ls = requests(4, seed=81, n_max=8000)
+    prm = mpld.make_params(node_budget=BUDGET, flags=mpld.MPLD_COLUMN_BFS)
+    with mpld.mpld_server_create(None, prm) as srv:
+        tickets = [mpld.mpld_server_submit(srv, L) for L in Ls]
+        got = drain(srv, tickets)
+    for t, L in zip(tickets, Ls):
+        ref = oracle.decompose(L, flags=oracle.COLUMN_BFS, budget=BUDGET, nthreads=NTHREADS)
+        rc, mask, res = got[t]
+        assert np.array_equal(mask, ref.mask) and res.nodes == ref.nodes and res.cost == ref.cost
