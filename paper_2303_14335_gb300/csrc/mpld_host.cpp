@@ -290,15 +290,15 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       }
       const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
       const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2);
-      const mpld::StateLayout L = mpld::state_layout(nc, ne2, k);
+      const uint32_t state_bytes = mpld::search_state_bytes(nc, ne2, k);
       p->inst_ne2[c] = ne2;
       ns2v[c] = ns2;
       maxdeg[c] = std::min(mdc, 0xFFFF) | (std::min(mds, 0x7FFF) << 16);
       p->ro_off[c] = arena;
       arena += R.bytes;
       scratch_off[c] = scratch;
-      scratch += L.bytes;
-      p->footprint[c] = L.bytes + R.bytes;
+      scratch += state_bytes;
+      p->footprint[c] = mpld::search_footprint(nc, ne2, ns2, k);
       mask_off[c] = p->comp_ptr[c];
     }
     p->arena_bytes = (size_t)arena;
@@ -374,7 +374,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       d.ne2 = p->inst_ne2[c];
       d.ns2 = ns2v[c];
       d.ro_bytes = (int32_t)mpld::ro_layout(nc, d.ne2, d.ns2).bytes;
-      d.state_bytes = (int32_t)mpld::state_layout(nc, d.ne2, k).bytes;
+      d.state_bytes = (int32_t)mpld::search_state_bytes(nc, d.ne2, k);
       d.k = k;
       d.cost_conflict = (int32_t)p->Cc;
       d.cost_stitch = (int32_t)p->Cs;

@@ -86,6 +86,46 @@ MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
   return L;
 }
 
+// Register-resident search, for instances of at most 32 words of fields
+// (n <= 128 for byte fields, n <= 64 for k = 8): lane l keeps the fields of
+// segments 4l..4l+3 (2l..2l+1 for k = 8) in one register, so the column
+// scan and the covers touch no memory.  Per-warp state:
+//   adj[n*32]    u8   per (segment v, lane l): bit j = segment l*P+j is a
+//                     conflict neighbour of v; bit 4+j = a stitch neighbour
+//   deg[n]       u32  conflict degree | stitch degree << 16
+//   rec[(n+1)*rs]     level record {v | next row << 8 | v's field << 12,
+//                     path cost, degrees, sorted row keys}; rs = 32 bytes
+//                     for k <= 4, else 48
+//   sav[(n+1)*32] u8  per (level, lane): which neighbour fields of the lane
+//                     lost a row bit to the level's cover (low nibble) and
+//                     the lane's neighbour bits of the level's segment
+//                     (high nibble)
+struct RegLayout {
+  uint32_t adj, deg, rec, sav, bytes;
+};
+MPLD_HD bool reg_fits(int n, int k) { return n <= 32 * (4 / field_bytes_for(k)); }
+MPLD_HD RegLayout reg_layout(int n, int k) {
+  const uint32_t rs = k <= 4 ? 32u : 48u;
+  RegLayout L;
+  uint32_t o = 0;
+  L.adj = o; o += align16(32u * (uint32_t)n);
+  L.deg = o; o += align16(4u * (uint32_t)n);
+  L.rec = o; o += rs * (uint32_t)(n + 1);
+  L.sav = o; o += 32u * (uint32_t)(n + 1);
+  L.bytes = o;
+  return L;
+}
+
+// Global scratch an instance needs when its state does not fit a slot, and
+// its shared-memory footprint when it does.
+MPLD_HD uint32_t search_state_bytes(int n, int ne2, int k) {
+  return reg_fits(n, k) ? reg_layout(n, k).bytes : state_layout(n, ne2, k).bytes;
+}
+MPLD_HD uint32_t search_footprint(int n, int ne2, int ns2, int k) {
+  return reg_fits(n, k) ? reg_layout(n, k).bytes
+                        : state_layout(n, ne2, k).bytes + ro_layout(n, ne2, ns2).bytes;
+}
+
 // One search instance, as the kernel sees it (absolute device pointers so
 // that instances of several problems can share one launch).
 struct __align__(16) InstDesc {

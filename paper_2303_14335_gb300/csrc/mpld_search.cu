@@ -133,10 +133,8 @@ __device__ __forceinline__ T ro_ld(const T *p) {
 // 16-bit counts of its conflict and stitch neighbours per mask, updated by
 // the same lanes, so the added cost of a segment's rows (Eq. 1) is read in
 // one load instead of gathered from its neighbours.
-// SMALL: at most 32 words of fields (n <= 128 for byte fields) and every
-// degree <= 32, so the column scan and the neighbour updates are single
-// predicated passes without loops.
-template <typename FT, int MK, bool SM, bool SMALL>
+// Instances of at most 32 words of fields go to reg_search below instead.
+template <typename FT, int MK, bool SM>
 struct Search {
   static constexpr uint32_t FB = 8 * sizeof(FT);    // bits per field
   static constexpr uint32_t FLAG = 1u << (FB - 1);   // column P_v uncovered
@@ -166,11 +164,7 @@ struct Search {
   // f(i) for i = lane, lane + 32, ... < d
   template <typename F>
   __device__ __forceinline__ static void each(int d, int lane, F &&f) {
-    if constexpr (SMALL) {
-      if (lane < d) f(lane);
-    } else {
-      for (int i = lane; i < d; i += 32) f(i);
-    }
+    for (int i = lane; i < d; i += 32) f(i);
   }
 
   // count word holding mask c of segment u
@@ -274,8 +268,8 @@ struct Search {
         // which go by breadth-first rank.
         uint32_t key = 0xFFFFFFFFu, z = 0;
         if (rule == 0) {
-          for (int wi = lane; SMALL ? wi == lane : wi < nwords; wi += 32) {
-            const uint32_t w = (!SMALL || wi < nwords) ? rows32[wi] : 0u;
+          for (int wi = lane; wi < nwords; wi += 32) {
+            const uint32_t w = rows32[wi];
 #pragma unroll
             for (int j = 0; j < PER_WORD; ++j) {
               const uint32_t f = (w >> (FB * j)) & FMASK;
@@ -288,8 +282,8 @@ struct Search {
             }
           }
         } else {
-          for (int wi = lane; SMALL ? wi == lane : wi < nwords; wi += 32) {
-            const uint32_t w = (!SMALL || wi < nwords) ? rows32[wi] : 0u;
+          for (int wi = lane; wi < nwords; wi += 32) {
+            const uint32_t w = rows32[wi];
 #pragma unroll
             for (int j = 0; j < PER_WORD; ++j) {
               const uint32_t f = (w >> (FB * j)) & FMASK;
@@ -358,6 +352,7 @@ struct Search {
       if (level == 0) break;
       --level;
       const uint4 r0 = lv[2 * level], r1 = lv[2 * level + 1];
+      __syncwarp();   // read by every lane before lane 0 rewrites it below
       const int v = (int)(r0.y & 0xFFFFu);
       const int nxt = (int)(r0.y >> 16);
       const int cb = (int)r0.w, dc = (int)(r1.x & 0xFFFFu), sb = (int)r1.y, ds = (int)(r1.x >> 16);
@@ -381,12 +376,276 @@ struct Search {
   }
 };
 
+// ---- register-resident search (n <= 32 words of fields) -------------------
+//
+// The same search as Search above, for instances whose fields fit one
+// 32-bit word per lane: lane l holds the fields of segments l*P .. l*P+P-1
+// (P = 4 byte fields, or 2 for k = 8) in a register `w`, and their masks in
+// `xw` (one byte per segment, 0xFF = none).  The conflict and stitch
+// adjacency is a bit matrix: adj[v*32 + l] says which of lane l's segments
+// neighbour v.  Per node:
+//   * column choice: popc of the lane's P fields, one __reduce_min_sync;
+//   * row costs (Eq. 1): per mask c, the lane counts its neighbours of v
+//     holding c (byte compare of xw under the adjacency byte mask); the
+//     counts of all masks travel packed in bytes through one
+//     __reduce_add_sync for conflicts and one for stitches;
+//   * cover of row (v, c): w &= ~(neighbour bits << c), and the owner lane
+//     clears v's field.  The undo record is one byte per lane: which of its
+//     neighbour fields had row c active (those get bit c back), plus its
+//     neighbour bits of v.
+// No field, count or neighbour list is read from memory on the way down.
+
+// bit j of a nibble -> bit 0 of field j (8-bit fields: bytes; 16-bit: halves)
+template <int FB> __device__ __forceinline__ uint32_t spread_bits(uint32_t b) {
+  if constexpr (FB == 8) return (b * 0x00204081u) & 0x01010101u;
+  else return (b & 1u) | ((b & 2u) << 15);
+}
+// inverse of spread_bits for words holding only bit 0 of each field
+template <int FB> __device__ __forceinline__ uint32_t gather_bits(uint32_t t) {
+  if constexpr (FB == 8) return (t * 0x10204080u) >> 28;
+  else return (t | (t >> 15)) & 3u;
+}
+
+template <typename FT, int MK>
+__device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
+                                           int lane) {
+  constexpr uint32_t FB = 8 * sizeof(FT);
+  constexpr uint32_t FLAG = 1u << (FB - 1);
+  constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
+  constexpr int P = 4 / (int)sizeof(FT);
+  constexpr int RS = MK <= 4 ? 8 : 12;   // words per level record
+  const int n = d.n, k = d.k;
+  const int Cc = d.cost_conflict, Cs = d.cost_stitch;
+  const int rule = a.rule;
+  const uint32_t kmask = (1u << k) - 1u;
+  const RegLayout R = reg_layout(n, k);
+  uint8_t *adj = base + R.adj;
+  uint32_t *deg = (uint32_t *)(base + R.deg);
+  uint32_t *rec = (uint32_t *)(base + R.rec);
+  uint8_t *sav = base + R.sav;
+
+  // adjacency bit matrix and degrees, from the read-only block (via L2)
+  {
+    const RoLayout Q = ro_layout(n, d.ne2, d.ns2);
+    const int2 *ptr = (const int2 *)(d.ro + Q.ptr);
+    const uint16_t *cnbr = (const uint16_t *)(d.ro + Q.cnbr);
+    const uint16_t *snbr = (const uint16_t *)(d.ro + Q.snbr);
+    uint32_t *adj32 = (uint32_t *)adj;
+    for (int i = lane; i < 8 * n; i += 32) adj32[i] = 0u;
+    __syncwarp();
+    for (int v = lane; v < n; v += 32) {
+      const int2 p0 = __ldcg(ptr + v), p1 = __ldcg(ptr + v + 1);
+      uint8_t *row = adj + v * 32;
+      for (int i = p0.x; i < p1.x; ++i) {
+        const int u = __ldcg(cnbr + i);
+        row[u / P] |= (uint8_t)(1u << (u % P));
+      }
+      for (int i = p0.y; i < p1.y; ++i) {
+        const int u = __ldcg(snbr + i);
+        row[u / P] |= (uint8_t)(1u << (4 + u % P));
+      }
+      deg[v] = (uint32_t)(p1.x - p0.x) | ((uint32_t)(p1.y - p0.y) << 16);
+    }
+  }
+  // every row active, every primary column uncovered, no mask assigned
+  uint32_t w = 0u, xw = 0xFFFFFFFFu, rk = 0u;
+  {
+    const RoLayout Q = ro_layout(n, d.ne2, d.ns2);
+    const uint16_t *rank = (const uint16_t *)(d.ro + Q.rank);
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const int s = lane * P + j;
+      if (s < n) {
+        w |= (kmask | FLAG) << (FB * j);
+        if (rule) rk |= (uint32_t)__ldcg(rank + s) << (8 * j);
+      }
+    }
+  }
+  __syncwarp();
+
+  int32_t best = INF32, g = 0;
+  int64_t nodes = 0, work = 0;
+  uint32_t work32 = 0;
+  int level = 0;
+  int status = MPLD_OK;
+  const int64_t budget = a.budget, time_limit_ns = a.time_limit_ns;
+  const uint64_t t0 = globaltimer();
+  bool enter = true;
+  for (;;) {
+    if (enter) {
+      // ---- a node: one call of the recursive search ----
+      if (budget > 0 && best < INF32 && nodes >= budget) { status = MPLD_BUDGET; break; }
+      ++nodes;
+      work32 += 2u * (uint32_t)(n - level);
+      if ((nodes & 1023) == 0) {
+        work += work32;
+        work32 = 0;
+        uint64_t now = lane == 0 ? globaltimer() : 0;
+        now = __shfl_sync(FULL, now, 0);
+        if ((int64_t)(now - t0) > time_limit_ns) { status = MPLD_TIMEOUT; break; }
+      }
+      // column choice.  Rule 0 keys (count, v); rule 1 keys single-row
+      // columns by v ahead of all others, which go by breadth-first rank.
+      uint32_t key = 0xFFFFFFFFu, z = 0;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const uint32_t f = (w >> (FB * j)) & FMASK;
+        const uint32_t cnt = (uint32_t)__popc(f & kmask);
+        const uint32_t sg = (uint32_t)(lane * P + j);
+        uint32_t kv;
+        if (rule == 0) kv = (cnt << 8) | sg;
+        else kv = cnt == 1 ? sg : (0x10000u | (((rk >> (8 * j)) & 0xFFu) << 8) | sg);
+        kv = (f & FLAG) ? kv : 0xFFFFFFFFu;
+        key = min(key, kv);
+        z += (f & FLAG) && cnt == 0;
+      }
+      key = __reduce_min_sync(FULL, key);
+      if (key == 0xFFFFFFFFu) {
+        // leaf: every primary column covered
+        if (g < best) {
+          best = g;
+#pragma unroll
+          for (int j = 0; j < P; ++j)
+            if (lane * P + j < n) d.mask[lane * P + j] = (int8_t)((xw >> (8 * j)) & 0xFFu);
+          if (best == 0) break;
+        }
+        enter = false;
+        continue;
+      }
+      if (best < INF32) {
+        // uncovered columns with no active row; under rule 0 there is one
+        // only when the minimum count is 0
+        z = (rule != 0 || key < 0x100u) ? __reduce_add_sync(FULL, z) : 0u;
+        if ((int64_t)g + (int64_t)Cc * z >= best) { enter = false; continue; }
+      }
+      const int v = (int)(key & 0xFFu);
+      const uint32_t ab = adj[v * 32 + lane];
+      const uint32_t cb = ab & 0xFu, sb = ab >> 4;
+      // added cost of each row (v, c) (Eq. 1): neighbours of v per mask
+      const uint32_t cm = spread_bits<8>(cb) * 0xFFu, sm = spread_bits<8>(sb) * 0xFFu;
+      uint32_t pc0 = 0, ps0 = 0, pc1 = 0, ps1 = 0;
+#pragma unroll
+      for (int c = 0; c < MK; ++c) {
+        if (MK == 8 && c >= k) continue;
+        const uint32_t eq = __vcmpeq4(xw, 0x01010101u * (uint32_t)c);
+        const uint32_t nc = (uint32_t)__popc(eq & cm) >> 3, ns = (uint32_t)__popc(eq & sm) >> 3;
+        if (c < 4) {
+          pc0 |= nc << (8 * c);
+          ps0 |= ns << (8 * c);
+        } else {
+          pc1 |= nc << (8 * (c - 4));
+          ps1 |= ns << (8 * (c - 4));
+        }
+      }
+      pc0 = __reduce_add_sync(FULL, pc0);
+      ps0 = __reduce_add_sync(FULL, ps0);
+      if (MK == 8) {
+        pc1 = __reduce_add_sync(FULL, pc1);
+        ps1 = __reduce_add_sync(FULL, ps1);
+      }
+      const int stot = (int)(((ps0 * 0x01010101u) >> 24) + ((ps1 * 0x01010101u) >> 24));
+      uint32_t keys[MK];
+#pragma unroll
+      for (int c = 0; c < MK; ++c) {
+        const uint32_t pc = c < 4 ? pc0 : pc1, ps = c < 4 ? ps0 : ps1;
+        const int sh = 8 * (c & 3);
+        const int inc = Cc * (int)((pc >> sh) & 0xFFu) + Cs * (stot - (int)((ps >> sh) & 0xFFu));
+        keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
+      }
+      sort_keys<MK>(keys);
+      const uint32_t dd = deg[v];
+      work32 += (uint32_t)(k * (int)((dd & 0xFFFFu) + (dd >> 16)) + 5 * (1 + (int)(dd & 0xFFFFu)));
+      // cover row (v, c): bit c of v's conflict neighbours, and v's field
+      const int c = (int)(keys[0] & 7u);
+      if (level >= n) {
+        // unreachable: each level covers one of the n columns (a guard for
+        // the per-level arrays)
+        if (lane == 0) atomicExch(a.err, MPLD_E_STATE);
+        break;
+      }
+      const uint32_t spc = spread_bits<FB>(cb);
+      const uint32_t was = gather_bits<FB>((w >> c) & spc);
+      const bool owner = (v / P) == lane;
+      const int jv = v % P;
+      sav[level * 32 + lane] = (uint8_t)(was | (cb << 4));
+      uint32_t *r = rec + level * RS;
+      if (owner) r[0] = (uint32_t)v | (1u << 8) | (((w >> (FB * jv)) & FMASK) << 12);
+      {
+        uint32_t val = lane == 1 ? (uint32_t)g : dd;
+#pragma unroll
+        for (int i = 0; i < MK; ++i)
+          if (lane == 3 + i) val = keys[i];
+        if (lane >= 1 && lane < 3 + MK) r[lane] = val;
+      }
+      w &= ~(spc << c);
+      if (owner) {
+        w &= ~(FMASK << (FB * jv));
+        xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+      }
+      g += (int32_t)(keys[0] >> 3);
+      ++level;
+      __syncwarp();
+      continue;
+    }
+    // ---- backtrack: next row of the level above, or undo its column ----
+    if (level == 0) break;
+    --level;
+    const uint32_t *r = rec + level * RS;
+    const uint4 r0 = *(const uint4 *)r, r1 = *(const uint4 *)(r + 4);
+    uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
+    if (MK == 8) r2 = *(const uint4 *)(r + 8);
+    const uint32_t sv = sav[level * 32 + lane];
+    // every lane has read the record before lane 0 rewrites its row index
+    // below (the paths that led here may have left the warp diverged)
+    __syncwarp();
+    const int v = (int)(r0.x & 0xFFu);
+    const int nxt = (int)((r0.x >> 8) & 0xFu);
+    // sorted row keys sit in words 3 .. 3+MK-1 of the record
+    auto key_at = [&](int i) -> uint32_t {
+      const uint32_t lo = i == 0 ? r0.w : i == 1 ? r1.x : i == 2 ? r1.y : r1.z;
+      const uint32_t hi = i == 4 ? r1.w : i == 5 ? r2.x : i == 6 ? r2.y : r2.z;
+      return i < 4 ? lo : hi;
+    };
+    const uint32_t klast = key_at(nxt - 1), knext = key_at(nxt < MK ? nxt : MK - 1);
+    const uint32_t spc = spread_bits<FB>(sv >> 4);
+    // give the neighbours back the row bit the last cover took
+    w |= spread_bits<FB>(sv & 0xFu) << (klast & 7u);
+    const bool owner = (v / P) == lane;
+    const int jv = v % P;
+    if (nxt >= k) {
+      // every row of this column tried: v's field and mask come back
+      if (owner) {
+        w |= (r0.x >> 12) << (FB * jv);
+        xw |= 0xFFu << (8 * jv);
+      }
+      continue;
+    }
+    const int c = (int)(knext & 7u);
+    g = (int32_t)r0.y + (int32_t)(knext >> 3);
+    work32 += 5u * (1u + (r0.z & 0xFFFFu));
+    sav[level * 32 + lane] = (uint8_t)(gather_bits<FB>((w >> c) & spc) | (sv & 0xF0u));
+    if (lane == 0) rec[level * RS] = (r0.x & ~0xF00u) | ((uint32_t)(nxt + 1) << 8);
+    w &= ~(spc << c);
+    if (owner) xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+    ++level;
+    enter = true;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    d.res->cost = best == INF32 ? INT64_MAX : (int64_t)best;
+    d.res->nodes = nodes;
+    d.res->status = status;
+    d.res->work = work + work32;
+  }
+  __syncwarp();
+}
+
 // Initialise the state at `base` and search.  SM says at compile time
 // whether `base` and `ro` point into shared memory.
-template <typename FT, int MK, bool SM, bool SMALL>
+template <typename FT, int MK, bool SM>
 __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
                                        const LaunchArgs &a, int lane) {
-  using S = Search<FT, MK, SM, SMALL>;
+  using S = Search<FT, MK, SM>;
   const int n = d.n;
   const StateLayout L = state_layout(n, d.ne2, d.k);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2);
@@ -437,10 +696,18 @@ template <typename FT, int MK>
 __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, int slot_bytes,
                                              uint64_t *bar, uint32_t &phase, const LaunchArgs &a,
                                              int lane) {
+  if (reg_fits(d.n, d.k)) {
+    // two call sites, so that each copy knows its state's memory space
+    if (slot_bytes > 0 && (int)reg_layout(d.n, d.k).bytes <= slot_bytes)
+      reg_search<FT, MK>(d, g_smem + slot_off, a, lane);
+    else
+      reg_search<FT, MK>(d, d.scratch, a, lane);
+    return true;
+  }
   const StateLayout L = state_layout(d.n, d.ne2, d.k);
   const RoLayout R = ro_layout(d.n, d.ne2, d.ns2);
   if (slot_bytes <= 0 || (int)(L.bytes + R.bytes) > slot_bytes) {
-    run_in<FT, MK, false, false>(d, d.scratch, d.ro, a, lane);
+    run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
     return true;
   }
   uint8_t *slot = g_smem + slot_off;
@@ -464,7 +731,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
       if (lane == 0) atomicExch(a.err, MPLD_E_TIMEOUT);
       for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
         if (mbar_try_wait(bar, phase ^ 1u)) break;
-      run_in<FT, MK, false, false>(d, d.scratch, d.ro, a, lane);
+      run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
       return false;
     }
   } else {
@@ -472,11 +739,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
     uint4 *d4 = (uint4 *)dst;
     for (uint32_t i = lane; i < ro_copy / 16; i += 32) d4[i] = __ldcg(src + i);
   }
-  constexpr int PER_WORD = 4 / (int)sizeof(FT);
-  if (d.n <= 32 * PER_WORD && (d.maxdeg & 0xFFFF) <= 32 && ((uint32_t)d.maxdeg >> 16) <= 32)
-    run_in<FT, MK, true, true>(d, slot, dst, a, lane);
-  else
-    run_in<FT, MK, true, false>(d, slot, dst, a, lane);
+  run_in<FT, MK, true>(d, slot, dst, a, lane);
   return true;
 }
 
@@ -670,7 +933,7 @@ __global__ void __launch_bounds__(32, 1)
   d.ne2 = ne2;
   d.ns2 = ns2;
   d.ro_bytes = (int32_t)R.bytes;
-  d.state_bytes = (int32_t)state_layout(n, ne2, inst.k).bytes;
+  d.state_bytes = (int32_t)search_state_bytes(n, ne2, inst.k);
   d.k = inst.k;
   d.cost_conflict = inst.cost_conflict;
   d.cost_stitch = inst.cost_stitch;
@@ -726,8 +989,8 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
   if ((int64_t)inst->cost_conflict * ne2 + (int64_t)inst->cost_stitch * ns2 >= ((int64_t)1 << 28))
     return MPLD_E_TOO_LARGE;
   const RoLayout R = ro_layout(n, ne2, ns2);
-  const StateLayout L = state_layout(n, ne2, k);
-  if ((uint64_t)NOALLOC_CTRL + align256(R.bytes) + L.bytes > (uint64_t)MPLD_NOALLOC_SCRATCH_BYTES)
+  if ((uint64_t)NOALLOC_CTRL + align256(R.bytes) + search_state_bytes(n, ne2, k) >
+      (uint64_t)MPLD_NOALLOC_SCRATCH_BYTES)
     return MPLD_E_TOO_LARGE;
 
   int dev = 0;
@@ -755,7 +1018,7 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
       nd->ready = true;
     }
   }
-  const uint32_t fp = align16(L.bytes + R.bytes);
+  const uint32_t fp = align16(search_footprint(n, ne2, ns2, k));
   const int slot = (int)fp <= nd->max_slot ? (int)fp : 0;   // else state stays in the array
   const int64_t budget = prm ? (prm->node_budget > 0 ? prm->node_budget : 0) : 0;
   const int64_t tl = (prm && prm->time_limit_ms > 0 ? prm->time_limit_ms : 60000) * 1000000ll;
