@@ -146,10 +146,11 @@ struct InstResult {
   int32_t status;   // MPLD_OK / MPLD_BUDGET / MPLD_TIMEOUT, -1 = not run
   int32_t pad0;
   // algorithmic integer operations of the search: 2 per uncovered column at
-  // every node (AND + popcount of the column choice), k per neighbour when a
-  // node's rows are costed, 5 per column of every covered row (AND-NOT,
-  // undo record, restore) -- the work the method must do, independent of
-  // how the kernel packs it
+  // every node that scans the columns (AND + popcount of the column choice;
+  // a node pruned by its path cost alone scans nothing), k per neighbour
+  // when a node's rows are costed, 5 per column of every covered row
+  // (AND-NOT, undo record, restore) -- the work the method must do,
+  // independent of how the kernel packs it
   int64_t work;
 };
 

@@ -248,6 +248,14 @@ struct Search {
     const uint64_t t0 = globaltimer();
     const uint32_t *rows32 = reinterpret_cast<const uint32_t *>(rows);
     const int nwords = (n + PER_WORD - 1) / PER_WORD;
+    int64_t next_check = 1024;
+    // m child nodes pruned on entry by their path cost alone, counted as
+    // the recursive search would (see reg_search); they add no work
+    auto count_pruned = [&](int m) -> bool {
+      const int64_t room = budget > 0 ? budget - nodes : (int64_t)m;
+      nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
+      return room < m;
+    };
     bool enter = true;
     for (;;) {
       if (enter) {
@@ -255,7 +263,8 @@ struct Search {
         if (budget > 0 && best < INF32 && nodes >= budget) { status = MPLD_BUDGET; break; }
         ++nodes;
         work32 += 2u * (uint32_t)(n - level);
-        if ((nodes & 1023) == 0) {
+        if (nodes >= next_check) {
+          next_check = nodes + 1024;
           work += work32;
           work32 = 0;
           uint64_t now = lane == 0 ? globaltimer() : 0;
@@ -332,6 +341,12 @@ struct Search {
           keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
         }
         sort_keys<MK>(keys);
+        if (best < INF32 && g + (int32_t)(keys[0] >> 3) >= best) {
+          // rows are in ascending cost: every child is pruned on entry
+          if (count_pruned(k)) { status = MPLD_BUDGET; break; }
+          enter = false;
+          continue;
+        }
         uint32_t ord = 0;
 #pragma unroll
         for (int i = 0; i < MK; ++i) ord |= (keys[i] & 7u) << (4 * i);
@@ -363,6 +378,12 @@ struct Search {
       }
       const int c = (int)((r0.z >> (4 * nxt)) & 7u);
       g = (int32_t)r0.x + (nxt == 1 ? (int32_t)r1.z : nxt == 2 ? (int32_t)r1.w : lvx[level * MK + nxt]);
+      if (best < INF32 && g >= best) {
+        // this row and the ones after it: children pruned on entry
+        if (count_pruned(k - nxt)) { status = MPLD_BUDGET; break; }
+        restore(v, c_last, cb, dc, sb, ds, lane);
+        continue;
+      }
       work32 += 5u * (uint32_t)(1 + dc);
       if (lane == 0) lv[2 * level].y = (uint32_t)v | ((uint32_t)(nxt + 1) << 16);
       switch_row(v, c_last, c, cb, dc, sb, ds, lane);
@@ -470,6 +491,16 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   int status = MPLD_OK;
   const int64_t budget = a.budget, time_limit_ns = a.time_limit_ns;
   const uint64_t t0 = globaltimer();
+  int64_t next_check = 1024;
+  // m child nodes that are pruned on entry (their path cost alone reaches
+  // the incumbent, so neither a cover nor a column scan is needed to know
+  // it): counted as the recursive search would, stopping where the node
+  // budget does.  They add no work: nothing is computed for them.
+  auto count_pruned = [&](int m) -> bool {
+    const int64_t room = budget > 0 ? budget - nodes : (int64_t)m;
+    nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
+    return room < m;
+  };
   bool enter = true;
   for (;;) {
     if (enter) {
@@ -477,7 +508,8 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       if (budget > 0 && best < INF32 && nodes >= budget) { status = MPLD_BUDGET; break; }
       ++nodes;
       work32 += 2u * (uint32_t)(n - level);
-      if ((nodes & 1023) == 0) {
+      if (nodes >= next_check) {
+        next_check = nodes + 1024;
         work += work32;
         work32 = 0;
         uint64_t now = lane == 0 ? globaltimer() : 0;
@@ -553,6 +585,12 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
         keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
       }
       sort_keys<MK>(keys);
+      if (best < INF32 && g + (int32_t)(keys[0] >> 3) >= best) {
+        // rows are in ascending cost: every child is pruned on entry
+        if (count_pruned(k)) { status = MPLD_BUDGET; break; }
+        enter = false;
+        continue;
+      }
       const uint32_t dd = deg[v];
       work32 += (uint32_t)(k * (int)((dd & 0xFFFFu) + (dd >> 16)) + 5 * (1 + (int)(dd & 0xFFFFu)));
       // cover row (v, c): bit c of v's conflict neighbours, and v's field
@@ -612,7 +650,14 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
     w |= spread_bits<FB>(sv & 0xFu) << (klast & 7u);
     const bool owner = (v / P) == lane;
     const int jv = v % P;
-    if (nxt >= k) {
+    bool last = nxt >= k;
+    if (!last && best < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= best) {
+      // this row and the ones after it cost at least as much: their nodes
+      // are pruned on entry, so count them and undo the column
+      if (count_pruned(k - nxt)) { status = MPLD_BUDGET; break; }
+      last = true;
+    }
+    if (last) {
       // every row of this column tried: v's field and mask come back
       if (owner) {
         w |= (r0.x >> 12) << (FB * jv);
