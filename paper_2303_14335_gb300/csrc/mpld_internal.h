@@ -94,12 +94,12 @@ MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
 //                     conflict neighbour of v; bit 4+j = a stitch neighbour
 //   deg[n]       u32  conflict degree | stitch degree << 16
 //   rec[(n+1)*rs]     level record {v | next row << 8 | v's field << 12,
-//                     path cost, degrees, sorted row keys}; rs = 32 bytes
+//                     path cost, degrees, -, sorted row keys}; rs = 32 bytes
 //                     for k <= 4, else 48
-//   sav[(n+1)*32] u8  per (level, lane): which neighbour fields of the lane
-//                     lost a row bit to the level's cover (low nibble) and
-//                     the lane's neighbour bits of the level's segment
-//                     (high nibble)
+//   sav[(n+1)*32] u16 per (level, lane): which neighbour fields of the lane
+//                     lost a row bit to the level's cover (bits 0-3), and
+//                     the lane's conflict (bits 4-7) and stitch (bits 8-11)
+//                     neighbour bits of the level's segment
 struct RegLayout {
   uint32_t adj, deg, rec, sav, bytes;
 };
@@ -111,7 +111,7 @@ MPLD_HD RegLayout reg_layout(int n, int k) {
   L.adj = o; o += align16(32u * (uint32_t)n);
   L.deg = o; o += align16(4u * (uint32_t)n);
   L.rec = o; o += rs * (uint32_t)(n + 1);
-  L.sav = o; o += 32u * (uint32_t)(n + 1);
+  L.sav = o; o += 64u * (uint32_t)(n + 1);
   L.bytes = o;
   return L;
 }

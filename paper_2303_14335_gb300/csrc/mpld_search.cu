@@ -401,19 +401,18 @@ struct Search {
 //
 // The same search as Search above, for instances whose fields fit one
 // 32-bit word per lane: lane l holds the fields of segments l*P .. l*P+P-1
-// (P = 4 byte fields, or 2 for k = 8) in a register `w`, and their masks in
-// `xw` (one byte per segment, 0xFF = none).  The conflict and stitch
-// adjacency is a bit matrix: adj[v*32 + l] says which of lane l's segments
-// neighbour v.  Per node:
+// (P = 4 byte fields, or 2 for k = 8) in a register `w`, their masks in `xw`
+// (one byte per segment, 0xFF = none), and, per mask c, the number of their
+// conflict and stitch neighbours holding c (`cc[c]`, `sc[c]`, one byte per
+// segment).  The adjacency is a bit matrix: adj[v*32 + l] says which of lane
+// l's segments neighbour v.  Per node:
 //   * column choice: popc of the lane's P fields, one __reduce_min_sync;
-//   * row costs (Eq. 1): per mask c, the lane counts its neighbours of v
-//     holding c (byte compare of xw under the adjacency byte mask); the
-//     counts of all masks travel packed in bytes through one
-//     __reduce_add_sync for conflicts and one for stitches;
-//   * cover of row (v, c): w &= ~(neighbour bits << c), and the owner lane
-//     clears v's field.  The undo record is one byte per lane: which of its
-//     neighbour fields had row c active (those get bit c back), plus its
-//     neighbour bits of v.
+//   * row costs (Eq. 1): the lane that holds v packs v's counts (byte
+//     permutes) and one shuffle per kind hands them to the warp;
+//   * cover of row (v, c): w &= ~(neighbour bits << c), the counts of mask c
+//     gain v's neighbours, and the owner lane clears v's field.  The undo
+//     record per lane is 16 bits: which neighbour fields had row c active,
+//     and the lane's conflict and stitch neighbour bits of v.
 // No field, count or neighbour list is read from memory on the way down.
 
 // bit j of a nibble -> bit 0 of field j (8-bit fields: bytes; 16-bit: halves)
@@ -427,7 +426,13 @@ template <int FB> __device__ __forceinline__ uint32_t gather_bits(uint32_t t) {
   else return (t | (t >> 15)) & 3u;
 }
 
-template <typename FT, int MK>
+// byte j (uniform) of four count words, packed as bytes 0..3
+__device__ __forceinline__ uint32_t pick_bytes(uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                               uint32_t sel) {
+  return __byte_perm(__byte_perm(a, b, sel), __byte_perm(c, d, sel), 0x5410u);
+}
+
+template <typename FT, int MK, int RULE>
 __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
                                            int lane) {
   constexpr uint32_t FB = 8 * sizeof(FT);
@@ -435,15 +440,15 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
   constexpr int P = 4 / (int)sizeof(FT);
   constexpr int RS = MK <= 4 ? 8 : 12;   // words per level record
+  constexpr int NC = MK <= 4 ? 4 : 8;    // count registers per kind
   const int n = d.n, k = d.k;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
-  const int rule = a.rule;
   const uint32_t kmask = (1u << k) - 1u;
   const RegLayout R = reg_layout(n, k);
   uint8_t *adj = base + R.adj;
   uint32_t *deg = (uint32_t *)(base + R.deg);
   uint32_t *rec = (uint32_t *)(base + R.rec);
-  uint8_t *sav = base + R.sav;
+  uint16_t *sav = (uint16_t *)(base + R.sav);
 
   // adjacency bit matrix and degrees, from the read-only block (via L2)
   {
@@ -470,6 +475,9 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   }
   // every row active, every primary column uncovered, no mask assigned
   uint32_t w = 0u, xw = 0xFFFFFFFFu, rk = 0u;
+  uint32_t cc[NC], sc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) cc[c] = sc[c] = 0u;
   {
     const RoLayout Q = ro_layout(n, d.ne2, d.ns2);
     const uint16_t *rank = (const uint16_t *)(d.ro + Q.rank);
@@ -478,7 +486,7 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       const int s = lane * P + j;
       if (s < n) {
         w |= (kmask | FLAG) << (FB * j);
-        if (rule) rk |= (uint32_t)__ldcg(rank + s) << (8 * j);
+        if (RULE) rk |= (uint32_t)__ldcg(rank + s) << (8 * j);
       }
     }
   }
@@ -500,6 +508,17 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
     const int64_t room = budget > 0 ? budget - nodes : (int64_t)m;
     nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
     return room < m;
+  };
+  // the counts of mask c gain (add) or lose the neighbours spread in cb8 /
+  // sb8 (bytes never go below zero, so a wrapped add is a bytewise one)
+  auto move_counts = [&](int c, uint32_t cb8, uint32_t sb8, bool add) {
+    const uint32_t dcw = add ? cb8 : 0u - cb8, dsw = add ? sb8 : 0u - sb8;
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const bool hit = m == c;
+      cc[m] += hit ? dcw : 0u;
+      sc[m] += hit ? dsw : 0u;
+    }
   };
   bool enter = true;
   for (;;) {
@@ -525,7 +544,7 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
         const uint32_t cnt = (uint32_t)__popc(f & kmask);
         const uint32_t sg = (uint32_t)(lane * P + j);
         uint32_t kv;
-        if (rule == 0) kv = (cnt << 8) | sg;
+        if constexpr (RULE == 0) kv = (cnt << 8) | sg;
         else kv = cnt == 1 ? sg : (0x10000u | (((rk >> (8 * j)) & 0xFFu) << 8) | sg);
         kv = (f & FLAG) ? kv : 0xFFFFFFFFu;
         key = min(key, kv);
@@ -547,42 +566,41 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       if (best < INF32) {
         // uncovered columns with no active row; under rule 0 there is one
         // only when the minimum count is 0
-        z = (rule != 0 || key < 0x100u) ? __reduce_add_sync(FULL, z) : 0u;
+        z = (RULE != 0 || key < 0x100u) ? __reduce_add_sync(FULL, z) : 0u;
         if ((int64_t)g + (int64_t)Cc * z >= best) { enter = false; continue; }
       }
       const int v = (int)(key & 0xFFu);
+      const int jv = v % P, src = v / P;
+      // the lane's neighbour bits of v (for the cover), loaded while the
+      // owner's counts travel
       const uint32_t ab = adj[v * 32 + lane];
-      const uint32_t cb = ab & 0xFu, sb = ab >> 4;
-      // added cost of each row (v, c) (Eq. 1): neighbours of v per mask
-      const uint32_t cm = spread_bits<8>(cb) * 0xFFu, sm = spread_bits<8>(sb) * 0xFFu;
-      uint32_t pc0 = 0, ps0 = 0, pc1 = 0, ps1 = 0;
-#pragma unroll
-      for (int c = 0; c < MK; ++c) {
-        if (MK == 8 && c >= k) continue;
-        const uint32_t eq = __vcmpeq4(xw, 0x01010101u * (uint32_t)c);
-        const uint32_t nc = (uint32_t)__popc(eq & cm) >> 3, ns = (uint32_t)__popc(eq & sm) >> 3;
-        if (c < 4) {
-          pc0 |= nc << (8 * c);
-          ps0 |= ns << (8 * c);
-        } else {
-          pc1 |= nc << (8 * (c - 4));
-          ps1 |= ns << (8 * (c - 4));
-        }
+      const uint32_t dd = deg[v];
+      // v's neighbours per mask (Eq. 1 row costs): one byte per mask
+      const uint32_t sel = (uint32_t)jv | ((uint32_t)(jv + 4) << 4);
+      uint32_t cw0 = pick_bytes(cc[0], cc[1], cc[2], cc[3], sel);
+      uint32_t sw0 = pick_bytes(sc[0], sc[1], sc[2], sc[3], sel);
+      uint32_t cw1 = 0u, sw1 = 0u;
+      if constexpr (NC == 8) {
+        cw1 = pick_bytes(cc[4], cc[5], cc[6], cc[7], sel);
+        sw1 = pick_bytes(sc[4], sc[5], sc[6], sc[7], sel);
       }
-      pc0 = __reduce_add_sync(FULL, pc0);
-      ps0 = __reduce_add_sync(FULL, ps0);
-      if (MK == 8) {
-        pc1 = __reduce_add_sync(FULL, pc1);
-        ps1 = __reduce_add_sync(FULL, ps1);
+      cw0 = __shfl_sync(FULL, cw0, src);
+      sw0 = __shfl_sync(FULL, sw0, src);
+      if constexpr (NC == 8) {
+        cw1 = __shfl_sync(FULL, cw1, src);
+        sw1 = __shfl_sync(FULL, sw1, src);
       }
-      const int stot = (int)(((ps0 * 0x01010101u) >> 24) + ((ps1 * 0x01010101u) >> 24));
+      const int stot = (int)(((sw0 * 0x01010101u) >> 24) + ((sw1 * 0x01010101u) >> 24));
       uint32_t keys[MK];
+      uint32_t oldf = FLAG;   // v's field: row c active iff no conflict neighbour holds c
 #pragma unroll
       for (int c = 0; c < MK; ++c) {
-        const uint32_t pc = c < 4 ? pc0 : pc1, ps = c < 4 ? ps0 : ps1;
+        const uint32_t cwd = c < 4 ? cw0 : cw1, swd = c < 4 ? sw0 : sw1;
         const int sh = 8 * (c & 3);
-        const int inc = Cc * (int)((pc >> sh) & 0xFFu) + Cs * (stot - (int)((ps >> sh) & 0xFFu));
+        const int ncf = (int)((cwd >> sh) & 0xFFu);
+        const int inc = Cc * ncf + Cs * (stot - (int)((swd >> sh) & 0xFFu));
         keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
+        if (c < k && ncf == 0) oldf |= 1u << c;
       }
       sort_keys<MK>(keys);
       if (best < INF32 && g + (int32_t)(keys[0] >> 3) >= best) {
@@ -591,32 +609,30 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
         enter = false;
         continue;
       }
-      const uint32_t dd = deg[v];
       work32 += (uint32_t)(k * (int)((dd & 0xFFFFu) + (dd >> 16)) + 5 * (1 + (int)(dd & 0xFFFFu)));
-      // cover row (v, c): bit c of v's conflict neighbours, and v's field
-      const int c = (int)(keys[0] & 7u);
       if (level >= n) {
         // unreachable: each level covers one of the n columns (a guard for
         // the per-level arrays)
         if (lane == 0) atomicExch(a.err, MPLD_E_STATE);
         break;
       }
-      const uint32_t spc = spread_bits<FB>(cb);
-      const uint32_t was = gather_bits<FB>((w >> c) & spc);
-      const bool owner = (v / P) == lane;
-      const int jv = v % P;
-      sav[level * 32 + lane] = (uint8_t)(was | (cb << 4));
-      uint32_t *r = rec + level * RS;
-      if (owner) r[0] = (uint32_t)v | (1u << 8) | (((w >> (FB * jv)) & FMASK) << 12);
-      {
-        uint32_t val = lane == 1 ? (uint32_t)g : dd;
-#pragma unroll
-        for (int i = 0; i < MK; ++i)
-          if (lane == 3 + i) val = keys[i];
-        if (lane >= 1 && lane < 3 + MK) r[lane] = val;
+      // level record: {v | next row << 8 | v's field << 12, path cost,
+      // degrees, -, sorted row keys}
+      if (lane == 0) {
+        uint4 *r4 = (uint4 *)(rec + level * RS);
+        r4[0] = make_uint4((uint32_t)v | (1u << 8) | (oldf << 12), (uint32_t)g, dd, 0u);
+        r4[1] = make_uint4(keys[0], MK > 1 ? keys[MK > 1 ? 1 : 0] : 0u,
+                           MK > 2 ? keys[MK > 2 ? 2 : 0] : 0u, MK > 3 ? keys[MK > 3 ? 3 : 0] : 0u);
+        if constexpr (MK == 8) r4[2] = make_uint4(keys[4 % MK], keys[5 % MK], keys[6 % MK], keys[7 % MK]);
       }
+      // cover row (v, c): bit c of v's conflict neighbours, and v's field
+      const int c = (int)(keys[0] & 7u);
+      const uint32_t cb = ab & 0xFu, sb = ab >> 4;
+      const uint32_t spc = spread_bits<FB>(cb);
+      sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (cb << 4) | (sb << 8));
       w &= ~(spc << c);
-      if (owner) {
+      move_counts(c, spread_bits<8>(cb), spread_bits<8>(sb), true);
+      if (lane == src) {
         w &= ~(FMASK << (FB * jv));
         xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
       }
@@ -631,25 +647,29 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
     const uint32_t *r = rec + level * RS;
     const uint4 r0 = *(const uint4 *)r, r1 = *(const uint4 *)(r + 4);
     uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
-    if (MK == 8) r2 = *(const uint4 *)(r + 8);
+    if constexpr (MK == 8) r2 = *(const uint4 *)(r + 8);
     const uint32_t sv = sav[level * 32 + lane];
     // every lane has read the record before lane 0 rewrites its row index
     // below (the paths that led here may have left the warp diverged)
     __syncwarp();
     const int v = (int)(r0.x & 0xFFu);
     const int nxt = (int)((r0.x >> 8) & 0xFu);
-    // sorted row keys sit in words 3 .. 3+MK-1 of the record
+    const int jv = v % P, src = v / P;
+    // sorted row keys sit in words 4 .. 4+MK-1 of the record
     auto key_at = [&](int i) -> uint32_t {
-      const uint32_t lo = i == 0 ? r0.w : i == 1 ? r1.x : i == 2 ? r1.y : r1.z;
-      const uint32_t hi = i == 4 ? r1.w : i == 5 ? r2.x : i == 6 ? r2.y : r2.z;
+      const uint32_t lo = i == 0 ? r1.x : i == 1 ? r1.y : i == 2 ? r1.z : r1.w;
+      const uint32_t hi = i == 4 ? r2.x : i == 5 ? r2.y : i == 6 ? r2.z : r2.w;
       return i < 4 ? lo : hi;
     };
     const uint32_t klast = key_at(nxt - 1), knext = key_at(nxt < MK ? nxt : MK - 1);
-    const uint32_t spc = spread_bits<FB>(sv >> 4);
-    // give the neighbours back the row bit the last cover took
-    w |= spread_bits<FB>(sv & 0xFu) << (klast & 7u);
-    const bool owner = (v / P) == lane;
-    const int jv = v % P;
+    const int cl = (int)(klast & 7u);
+    const uint32_t cb = (sv >> 4) & 0xFu, sb = sv >> 8;
+    const uint32_t spc = spread_bits<FB>(cb);
+    const uint32_t cb8 = spread_bits<8>(cb), sb8 = spread_bits<8>(sb);
+    // take back the last row: its neighbours regain row bit cl, the counts
+    // of mask cl lose v
+    w |= spread_bits<FB>(sv & 0xFu) << cl;
+    move_counts(cl, cb8, sb8, false);
     bool last = nxt >= k;
     if (!last && best < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= best) {
       // this row and the ones after it cost at least as much: their nodes
@@ -659,7 +679,7 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
     }
     if (last) {
       // every row of this column tried: v's field and mask come back
-      if (owner) {
+      if (lane == src) {
         w |= (r0.x >> 12) << (FB * jv);
         xw |= 0xFFu << (8 * jv);
       }
@@ -668,10 +688,11 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
     const int c = (int)(knext & 7u);
     g = (int32_t)r0.y + (int32_t)(knext >> 3);
     work32 += 5u * (1u + (r0.z & 0xFFFFu));
-    sav[level * 32 + lane] = (uint8_t)(gather_bits<FB>((w >> c) & spc) | (sv & 0xF0u));
+    sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (sv & 0xFF0u));
     if (lane == 0) rec[level * RS] = (r0.x & ~0xF00u) | ((uint32_t)(nxt + 1) << 8);
     w &= ~(spc << c);
-    if (owner) xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+    move_counts(c, cb8, sb8, true);
+    if (lane == src) xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
     ++level;
     enter = true;
     __syncwarp();
@@ -742,11 +763,15 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
                                              uint64_t *bar, uint32_t &phase, const LaunchArgs &a,
                                              int lane) {
   if (reg_fits(d.n, d.k)) {
-    // two call sites, so that each copy knows its state's memory space
-    if (slot_bytes > 0 && (int)reg_layout(d.n, d.k).bytes <= slot_bytes)
-      reg_search<FT, MK>(d, g_smem + slot_off, a, lane);
-    else
-      reg_search<FT, MK>(d, d.scratch, a, lane);
+    // one call site per memory space, so that each copy knows where its
+    // state lives; the column rule is a template argument
+    if (slot_bytes > 0 && (int)reg_layout(d.n, d.k).bytes <= slot_bytes) {
+      if (a.rule) reg_search<FT, MK, 1>(d, g_smem + slot_off, a, lane);
+      else reg_search<FT, MK, 0>(d, g_smem + slot_off, a, lane);
+    } else {
+      if (a.rule) reg_search<FT, MK, 1>(d, d.scratch, a, lane);
+      else reg_search<FT, MK, 0>(d, d.scratch, a, lane);
+    }
     return true;
   }
   const StateLayout L = state_layout(d.n, d.ne2, d.k);
