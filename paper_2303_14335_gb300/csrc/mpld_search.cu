@@ -21,7 +21,13 @@
 // including rows that are no longer active: those are the "conflict
 // candidates" of Algorithm 1 and pay the conflict cost of Eq. 1.  A node is
 // pruned when its cost plus cost_conflict times the number of uncovered
-// columns with no active row reaches the incumbent.
+// columns with no active row reaches the incumbent; children whose path
+// cost alone reaches it are counted without being entered.
+//
+// Instances of at most 32 words of fields (n <= 128 segments for k <= 7)
+// run a register-resident form of the same search (reg_search): each lane
+// keeps its four fields, masks and per-mask neighbour counts in registers
+// and the adjacency becomes a bit matrix; larger instances run Search.
 //
 // Batched form: a persistent grid whose warps pull instance indices from a
 // device work counter over a largest-first order (Sec. 2.3 / Sec. 3 run one
