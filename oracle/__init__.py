@@ -32,6 +32,7 @@ E_OOM = -2
 NO_SIMPLIFY = 1
 SINGLE_INSTANCE = 2
 COLUMN_BFS = 8      # the paper's column rule (single-row column, else BFS order)
+BICONNECTED = 16    # search the biconnected blocks of each component, merge at cut segments
 INF = (1 << 63) - 1
 
 
@@ -76,6 +77,8 @@ def _load():
         lib.oracle_decompose.argtypes = [i32, i32, i32, P, P, i32, P, P, P, i64, i64, ctypes.c_uint32,
                                          i64, i32, P, P, P, P, P, ctypes.POINTER(_Totals)]
         lib.oracle_decompose.restype = i32
+        lib.oracle_blocks.argtypes = [i32, i32, P, P, i32, P, P, P, P, P]
+        lib.oracle_blocks.restype = i32
         _lib = lib
     return _lib
 
@@ -142,6 +145,26 @@ def export_matrix(n, k, conf) -> np.ndarray:
     if rc < 0:
         raise ValueError(f"oracle_export_matrix failed: {rc}")
     return out
+
+
+def blocks(n, conf, stitch=()):
+    """Biconnected blocks of every component of the graph (no simplification),
+    in the canonical order the flow searches them: list of (segments ascending,
+    attach segment or -1)."""
+    lib = _load()
+    conf = np.asarray(conf, dtype=np.int32).reshape(-1, 2)
+    stitch = np.asarray(stitch, dtype=np.int32).reshape(-1, 2)
+    cu, cv = _i32(conf[:, 0]), _i32(conf[:, 1])
+    su, sv = _i32(stitch[:, 0]), _i32(stitch[:, 1])
+    cap = 2 * (n + len(cu) + len(su)) + 1
+    ip = np.zeros(n + 2, dtype=np.int32)
+    iseg = np.zeros(cap, dtype=np.int32)
+    iatt = np.zeros(cap, dtype=np.int32)
+    nb = lib.oracle_blocks(n, len(cu), _ptr(cu), _ptr(cv), len(su), _ptr(su), _ptr(sv), _ptr(ip),
+                           _ptr(iseg), _ptr(iatt))
+    if nb < 0:
+        raise ValueError(f"oracle_blocks failed: {nb}")
+    return [(iseg[ip[b]:ip[b + 1]].tolist(), int(iatt[b])) for b in range(nb)]
 
 
 @dataclass

@@ -77,6 +77,7 @@
 #define OR_NO_SIMPLIFY 1u
 #define OR_SINGLE_INSTANCE 2u
 #define OR_COLUMN_BFS 8u
+#define OR_BICONNECTED 16u
 
 #define OR_INF INT64_MAX
 
@@ -497,53 +498,62 @@ typedef struct {
   /* shared, read-only */
   int k, n_comp, rule;
   int64_t Cc, Cs, budget;
-  const int *comp_ptr, *comp_seg;     /* segments of component i, ascending */
-  const int *local_of;                /* global segment -> local id */
-  const int *comp_of;                 /* global segment -> component, -1 removed */
+  const int *comp_ptr, *comp_seg;     /* segments of instance i, ascending */
   const int *cptr, *cadj, *sptr, *sadj; /* global adjacency */
-  const int *work_order;              /* components by descending size */
+  const int *work_order;              /* instances by descending size */
   /* outputs */
-  signed char *mask;                  /* global masks */
+  signed char *imask;                 /* per instance entry (comp_ptr order) */
   int64_t *comp_cost, *comp_nodes;
   int32_t *comp_status;
   atomic_int next;
   atomic_int error;
 } pool_t;
 
+/* local id of global segment g in the sorted list seg[0..n), or -1 */
+static int local_id(const int *seg, int n, int g) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = lo + (hi - lo) / 2;
+    if (seg[mid] < g) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < n && seg[lo] == g) ? lo : -1;
+}
+
+/* Search instance ci: its segments are the sorted list comp_seg[a..b), its
+ * edges every conflict / stitch edge with both ends among them. */
 static void solve_component(pool_t *P, int ci) {
   const int a = P->comp_ptr[ci], b = P->comp_ptr[ci + 1], n = b - a;
-  /* local edge lists, sorted by (min, max) local id: local ids keep the
-   * global order, so walking segments ascending and their larger
-   * neighbours ascending gives the sorted order */
+  const int *seg = P->comp_seg + a;
   int ne = 0, ns = 0;
-  for (int t = a; t < b; ++t) {
-    int g = P->comp_seg[t];
+  for (int t = 0; t < n; ++t) {
+    int g = seg[t];
     for (int i = P->cptr[g]; i < P->cptr[g + 1]; ++i)
-      if (P->cadj[i] > g && P->comp_of[P->cadj[i]] == ci) ne++;
+      if (P->cadj[i] > g && local_id(seg, n, P->cadj[i]) >= 0) ne++;
     for (int i = P->sptr[g]; i < P->sptr[g + 1]; ++i)
-      if (P->sadj[i] > g && P->comp_of[P->sadj[i]] == ci) ns++;
+      if (P->sadj[i] > g && local_id(seg, n, P->sadj[i]) >= 0) ns++;
   }
   int *eu = malloc(sizeof(int) * (size_t)(ne + 1)), *ev = malloc(sizeof(int) * (size_t)(ne + 1));
   int *su = malloc(sizeof(int) * (size_t)(ns + 1)), *sv = malloc(sizeof(int) * (size_t)(ns + 1));
   signed char *x = malloc((size_t)n + 1);
   if (!eu || !ev || !su || !sv || !x) { atomic_store(&P->error, OR_E_OOM); goto out; }
   ne = ns = 0;
-  for (int t = a; t < b; ++t) {
-    int g = P->comp_seg[t];
-    for (int i = P->cptr[g]; i < P->cptr[g + 1]; ++i)
-      if (P->cadj[i] > g && P->comp_of[P->cadj[i]] == ci) {
-        eu[ne] = P->local_of[g]; ev[ne] = P->local_of[P->cadj[i]]; ne++;
-      }
-    for (int i = P->sptr[g]; i < P->sptr[g + 1]; ++i)
-      if (P->sadj[i] > g && P->comp_of[P->sadj[i]] == ci) {
-        su[ns] = P->local_of[g]; sv[ns] = P->local_of[P->sadj[i]]; ns++;
-      }
+  for (int t = 0; t < n; ++t) {
+    int g = seg[t];
+    for (int i = P->cptr[g]; i < P->cptr[g + 1]; ++i) {
+      int l = P->cadj[i] > g ? local_id(seg, n, P->cadj[i]) : -1;
+      if (l >= 0) { eu[ne] = t; ev[ne] = l; ne++; }
+    }
+    for (int i = P->sptr[g]; i < P->sptr[g + 1]; ++i) {
+      int l = P->sadj[i] > g ? local_id(seg, n, P->sadj[i]) : -1;
+      if (l >= 0) { su[ns] = t; sv[ns] = l; ns++; }
+    }
   }
   int64_t cost = 0, nodes = 0;
   int rc = oracle_solve_instance_rule(n, P->k, ne, eu, ev, ns, su, sv, P->Cc, P->Cs, P->budget,
                                       P->rule, x, &cost, &nodes);
   if (rc < 0) { atomic_store(&P->error, rc); goto out; }
-  for (int t = a; t < b; ++t) P->mask[P->comp_seg[t]] = x[t - a];
+  memcpy(P->imask + a, x, (size_t)n);
   P->comp_cost[ci] = cost;
   P->comp_nodes[ci] = nodes;
   P->comp_status[ci] = rc;
@@ -583,6 +593,303 @@ static int find_root(int *parent, int a) {
  *   segment, -1 if removed by simplification; comp_nodes_out /
  *   comp_cost_out / comp_status_out (nullable, n_seg entries each).
  */
+/* ------------------------------------------------------------------ */
+/* Biconnected blocks of one component (the flow's optional split)      */
+/* ------------------------------------------------------------------ */
+
+/* A block is a maximal 2-connected piece of the component's graph
+ * (conflict and stitch edges together); a bridge is a block of two, and a
+ * component without edges is one block of one segment.  Computed from a
+ * plain characterisation: two edges (v, a) and (v, b) at a vertex v lie in
+ * one block exactly when a and b are still connected once v is removed;
+ * blocks are the classes of the transitive closure of that relation.
+ *
+ * Canonical order: the blocks are visited breadth-first over the
+ * block-cut tree.  The first is, among the blocks holding the component's
+ * lowest segment, the one whose ascending segment list is lexicographically
+ * smallest.  From a visited block, its segments are taken in ascending id,
+ * and each unvisited block holding that segment is visited next (blocks in
+ * lexicographic order of their segment lists), attached at that segment.
+ * The merge gives a block's solution the transposition of masks that makes
+ * its attach segment agree with the mask it already has; cost is unchanged
+ * by renaming masks, and each edge lies in exactly one block. */
+
+typedef struct { int *v; int n; } vlist_t;
+
+static int lex_cmp(const vlist_t *x, const vlist_t *y) {
+  int m = x->n < y->n ? x->n : y->n;
+  for (int i = 0; i < m; ++i)
+    if (x->v[i] != y->v[i]) return x->v[i] < y->v[i] ? -1 : 1;
+  return x->n < y->n ? -1 : x->n > y->n ? 1 : 0;
+}
+static int find_uf(int *p, int a) {
+  while (p[a] != a) { p[a] = p[p[a]]; a = p[a]; }
+  return a;
+}
+
+/* Append the blocks of component seg[0..n) (ascending global ids) in
+ * canonical order: segments to *out_seg (grown), block boundaries to
+ * *out_ptr, attach segments (global id, -1 for the first) to *out_att. */
+static int component_blocks(const int *seg, int n, const int *cptr, const int *cadj,
+                            const int *sptr, const int *sadj, int **out_ptr, int **out_seg,
+                            int **out_att, int *n_out, int *cap_blocks, int *len_seg,
+                            int *cap_seg) {
+  int rc = OR_E_OOM;
+  /* local adjacency: union of conflict and stitch neighbours inside */
+  int *deg = calloc((size_t)n + 1, sizeof(int)), *lptr = NULL, *ladj = NULL;
+  int *eid = NULL, *ea = NULL, *eb = NULL, *uf = NULL, *lab = NULL, *stack = NULL;
+  int *bid = NULL, *mark = NULL, *bcount = NULL, *order = NULL, *visited = NULL, *queue = NULL;
+  int *attach = NULL, *vb_ptr = NULL, *vb = NULL;
+  vlist_t *blocks = NULL;
+  int nb = 0, ne = 0;
+  if (!deg) goto done;
+  for (int t = 0; t < n; ++t) {
+    int g = seg[t], i = cptr[g], j = sptr[g];
+    while (i < cptr[g + 1] || j < sptr[g + 1]) {
+      int w;
+      if (j >= sptr[g + 1] || (i < cptr[g + 1] && cadj[i] <= sadj[j])) {
+        w = cadj[i++];
+        if (j < sptr[g + 1] && sadj[j] == w) ++j;
+      } else w = sadj[j++];
+      if (local_id(seg, n, w) >= 0) deg[t]++;
+    }
+  }
+  lptr = calloc((size_t)n + 1, sizeof(int));
+  if (!lptr) goto done;
+  for (int t = 0; t < n; ++t) lptr[t + 1] = lptr[t] + deg[t];
+  ladj = malloc(sizeof(int) * (size_t)(lptr[n] + 1));
+  eid = malloc(sizeof(int) * (size_t)(lptr[n] + 1));
+  if (!ladj || !eid) goto done;
+  for (int t = 0, f = 0; t < n; ++t) {
+    int g = seg[t], i = cptr[g], j = sptr[g];
+    while (i < cptr[g + 1] || j < sptr[g + 1]) {
+      int w;
+      if (j >= sptr[g + 1] || (i < cptr[g + 1] && cadj[i] <= sadj[j])) {
+        w = cadj[i++];
+        if (j < sptr[g + 1] && sadj[j] == w) ++j;
+      } else w = sadj[j++];
+      int l = local_id(seg, n, w);
+      if (l >= 0) ladj[f++] = l;
+    }
+  }
+  /* edge ids: edge (t, l) with t < l gets the next id; the reverse entry shares it */
+  ne = lptr[n] / 2;
+  ea = malloc(sizeof(int) * (size_t)(ne + 1));
+  eb = malloc(sizeof(int) * (size_t)(ne + 1));
+  uf = malloc(sizeof(int) * (size_t)(ne + 1));
+  if (!ea || !eb || !uf) goto done;
+  for (int t = 0, e = 0; t < n; ++t)
+    for (int i = lptr[t]; i < lptr[t + 1]; ++i)
+      if (ladj[i] > t) { eid[i] = e; ea[e] = t; eb[e] = ladj[i]; uf[e] = e; ++e; }
+  for (int t = 0; t < n; ++t)
+    for (int i = lptr[t]; i < lptr[t + 1]; ++i)
+      if (ladj[i] < t) {
+        int u = ladj[i];
+        for (int j = lptr[u]; j < lptr[u + 1]; ++j)
+          if (ladj[j] == t) { eid[i] = eid[j]; break; }
+      }
+  /* for every v: components of the graph without v; join v's edges whose
+   * other ends share one */
+  lab = malloc(sizeof(int) * (size_t)(n + 1));
+  stack = malloc(sizeof(int) * (size_t)(n + 1));
+  if (!lab || !stack) goto done;
+  for (int v = 0; v < n; ++v) {
+    if (lptr[v + 1] - lptr[v] < 2) continue;
+    for (int t = 0; t < n; ++t) lab[t] = -1;
+    int nl = 0;
+    for (int s0 = 0; s0 < n; ++s0) {
+      if (s0 == v || lab[s0] >= 0) continue;
+      int top = 0;
+      stack[top++] = s0;
+      lab[s0] = nl;
+      while (top) {
+        int u = stack[--top];
+        for (int i = lptr[u]; i < lptr[u + 1]; ++i) {
+          int w = ladj[i];
+          if (w != v && lab[w] < 0) { lab[w] = nl; stack[top++] = w; }
+        }
+      }
+      ++nl;
+    }
+    for (int i = lptr[v]; i < lptr[v + 1]; ++i)
+      for (int j = i + 1; j < lptr[v + 1]; ++j)
+        if (lab[ladj[i]] == lab[ladj[j]]) {
+          int ra = find_uf(uf, eid[i]), rb = find_uf(uf, eid[j]);
+          if (ra != rb) uf[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+        }
+  }
+  /* blocks: one per edge class, or the lone segment */
+  bid = malloc(sizeof(int) * (size_t)(ne + 1));
+  mark = malloc(sizeof(int) * (size_t)(n + 1));
+  if (!bid || !mark) goto done;
+  for (int e = 0; e < ne; ++e) bid[e] = -1;
+  for (int e = 0; e < ne; ++e) {
+    int r = find_uf(uf, e);
+    if (bid[r] < 0) bid[r] = nb++;
+    bid[e] = bid[r];
+  }
+  if (ne == 0) nb = 1;
+  blocks = calloc((size_t)nb, sizeof(vlist_t));
+  if (!blocks) goto done;
+  if (ne == 0) {
+    blocks[0].v = malloc(sizeof(int));
+    if (!blocks[0].v) goto done;
+    blocks[0].v[0] = 0;
+    blocks[0].n = 1;
+  } else {
+    for (int b = 0; b < nb; ++b) {
+      for (int t = 0; t < n; ++t) mark[t] = 0;
+      int cnt = 0;
+      for (int e = 0; e < ne; ++e)
+        if (bid[e] == b) {
+          if (!mark[ea[e]]) { mark[ea[e]] = 1; ++cnt; }
+          if (!mark[eb[e]]) { mark[eb[e]] = 1; ++cnt; }
+        }
+      blocks[b].v = malloc(sizeof(int) * (size_t)cnt);
+      if (!blocks[b].v) goto done;
+      for (int t = 0; t < n; ++t) if (mark[t]) blocks[b].v[blocks[b].n++] = t;
+    }
+  }
+  /* blocks of each segment, in lexicographic order of their lists */
+  vb_ptr = calloc((size_t)n + 1, sizeof(int));
+  if (!vb_ptr) goto done;
+  for (int b = 0; b < nb; ++b) for (int i = 0; i < blocks[b].n; ++i) vb_ptr[blocks[b].v[i] + 1]++;
+  for (int t = 0; t < n; ++t) vb_ptr[t + 1] += vb_ptr[t];
+  vb = malloc(sizeof(int) * (size_t)(vb_ptr[n] + 1));
+  bcount = calloc((size_t)n + 1, sizeof(int));
+  if (!vb || !bcount) goto done;
+  for (int b = 0; b < nb; ++b)
+    for (int i = 0; i < blocks[b].n; ++i) {
+      int t = blocks[b].v[i];
+      vb[vb_ptr[t] + bcount[t]++] = b;
+    }
+  for (int t = 0; t < n; ++t)   /* insertion sort by segment list */
+    for (int i = vb_ptr[t] + 1; i < vb_ptr[t + 1]; ++i) {
+      int x = vb[i], j = i - 1;
+      while (j >= vb_ptr[t] && lex_cmp(&blocks[vb[j]], &blocks[x]) > 0) { vb[j + 1] = vb[j]; --j; }
+      vb[j + 1] = x;
+    }
+  /* breadth-first over the block-cut tree from the first block of segment 0 */
+  order = malloc(sizeof(int) * (size_t)nb);
+  attach = malloc(sizeof(int) * (size_t)nb);
+  visited = calloc((size_t)nb, sizeof(int));
+  if (!order || !attach || !visited) goto done;
+  int qn = 0;
+  order[qn] = vb[vb_ptr[0]];
+  attach[qn] = -1;
+  visited[order[qn]] = 1;
+  ++qn;
+  for (int h = 0; h < qn; ++h) {
+    const vlist_t *B = &blocks[order[h]];
+    for (int i = 0; i < B->n; ++i) {
+      int t = B->v[i];
+      for (int j = vb_ptr[t]; j < vb_ptr[t + 1]; ++j)
+        if (!visited[vb[j]]) {
+          visited[vb[j]] = 1;
+          order[qn] = vb[j];
+          attach[qn] = seg[t];
+          ++qn;
+        }
+    }
+  }
+  if (qn != nb) { rc = OR_E_INVALID; goto done; }   /* a component is connected */
+  for (int q = 0; q < nb; ++q) {
+    const vlist_t *B = &blocks[order[q]];
+    if (*n_out + 1 >= *cap_blocks) {
+      int nc = *cap_blocks * 2 + 16;
+      int *np = realloc(*out_ptr, sizeof(int) * (size_t)(nc + 1));
+      if (!np) goto done;
+      *out_ptr = np;
+      int *na = realloc(*out_att, sizeof(int) * (size_t)(nc + 1));
+      if (!na) goto done;
+      *out_att = na;
+      *cap_blocks = nc;
+    }
+    if (*len_seg + B->n > *cap_seg) {
+      int nc = (*cap_seg + B->n) * 2 + 16;
+      int *ns = realloc(*out_seg, sizeof(int) * (size_t)nc);
+      if (!ns) goto done;
+      *out_seg = ns;
+      *cap_seg = nc;
+    }
+    for (int i = 0; i < B->n; ++i) (*out_seg)[*len_seg + i] = seg[B->v[i]];
+    *len_seg += B->n;
+    (*out_att)[*n_out] = attach[q];
+    (*out_ptr)[*n_out + 1] = *len_seg;
+    *n_out += 1;
+  }
+  rc = OR_OK;
+done:
+  if (blocks) for (int b = 0; b < nb; ++b) free(blocks[b].v);
+  free(blocks); free(deg); free(lptr); free(ladj); free(eid); free(ea); free(eb); free(uf);
+  free(lab); free(stack); free(bid); free(mark); free(bcount); free(order); free(visited);
+  free(queue); free(attach); free(vb_ptr); free(vb);
+  return rc;
+}
+
+/* Components (conflict and stitch edges, numbered by lowest segment) and
+ * their blocks in canonical order, for the given graph as it stands (no
+ * simplification).  inst_ptr has room for n + 1 entries, inst_seg and
+ * inst_att for 2 * (n + ne + ns) + 1; returns the number of blocks. */
+int oracle_blocks(int n, int ne, const int *eu, const int *ev, int ns, const int *su,
+                  const int *sv, int *inst_ptr_out, int *inst_seg_out, int *inst_att_out) {
+  if (n < 0 || ne < 0 || ns < 0) return OR_E_INVALID;
+  int rc, *cu = NULL, *cv = NULL, *tu = NULL, *tv = NULL, mc = 0, ms = 0;
+  int *cptr = NULL, *cadj = NULL, *sptr = NULL, *sadj = NULL, *parent = NULL, *cid = NULL;
+  int *cseg = NULL, *cp = NULL, *ip = NULL, *is = NULL, *ia = NULL;
+  int n_inst = 0, cap_b = 16, cap_s = 16, len = 0;
+  if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) goto done;
+  if ((rc = norm_edges(n, ns, su, sv, &tu, &tv, &ms)) != OR_OK) goto done;
+  if ((rc = build_adj(n, mc, cu, cv, &cptr, &cadj)) != OR_OK) goto done;
+  if ((rc = build_adj(n, ms, tu, tv, &sptr, &sadj)) != OR_OK) goto done;
+  rc = OR_E_OOM;
+  parent = malloc(sizeof(int) * (size_t)(n + 1));
+  cid = malloc(sizeof(int) * (size_t)(n + 1));
+  cseg = malloc(sizeof(int) * (size_t)(n + 1));
+  cp = calloc((size_t)n + 2, sizeof(int));
+  ip = malloc(sizeof(int) * (size_t)(cap_b + 1));
+  ia = malloc(sizeof(int) * (size_t)(cap_b + 1));
+  is = malloc(sizeof(int) * (size_t)cap_s);
+  if (!parent || !cid || !cseg || !cp || !ip || !ia || !is) goto done;
+  for (int s = 0; s < n; ++s) parent[s] = s;
+  for (int e = 0; e < mc; ++e) {
+    int ra = find_root(parent, cu[e]), rb = find_root(parent, cv[e]);
+    if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+  }
+  for (int e = 0; e < ms; ++e) {
+    int ra = find_root(parent, tu[e]), rb = find_root(parent, tv[e]);
+    if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+  }
+  int nc = 0;
+  for (int s = 0; s < n; ++s) cid[s] = -1;
+  for (int s = 0; s < n; ++s) {
+    int r = find_root(parent, s);
+    if (cid[r] < 0) cid[r] = nc++;
+    cid[s] = cid[r];
+  }
+  for (int s = 0; s < n; ++s) cp[cid[s] + 1]++;
+  for (int c = 0; c < nc; ++c) cp[c + 1] += cp[c];
+  {
+    int *fill = calloc((size_t)nc + 1, sizeof(int));
+    if (!fill) goto done;
+    for (int s = 0; s < n; ++s) cseg[cp[cid[s]] + fill[cid[s]]++] = s;
+    free(fill);
+  }
+  ip[0] = 0;
+  for (int c = 0; c < nc; ++c)
+    if ((rc = component_blocks(cseg + cp[c], cp[c + 1] - cp[c], cptr, cadj, sptr, sadj, &ip, &is,
+                               &ia, &n_inst, &cap_b, &len, &cap_s)) != OR_OK)
+      goto done;
+  memcpy(inst_ptr_out, ip, sizeof(int) * (size_t)(n_inst + 1));
+  memcpy(inst_seg_out, is, sizeof(int) * (size_t)len);
+  memcpy(inst_att_out, ia, sizeof(int) * (size_t)n_inst);
+  rc = n_inst;
+done:
+  free(cu); free(cv); free(tu); free(tv); free(cptr); free(cadj); free(sptr); free(sadj);
+  free(parent); free(cid); free(cseg); free(cp); free(ip); free(is); free(ia);
+  return rc;
+}
+
 int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int *conf_v,
                      int n_st, const int *st_u, const int *st_v, const int *polygon_of,
                      int64_t cost_conflict, int64_t cost_stitch, uint32_t flags, int64_t budget,
@@ -590,6 +897,7 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
                      int64_t *comp_nodes_out, int64_t *comp_cost_out, int32_t *comp_status_out,
                      oracle_totals *tot) {
   if (n_seg < 0 || k < 2 || k > 8 || n_conf < 0 || n_st < 0 || nthreads < 1) return OR_E_INVALID;
+  if ((flags & OR_BICONNECTED) && (flags & OR_SINGLE_INSTANCE)) return OR_E_INVALID;
   if (polygon_of)
     for (int s = 0; s < n_seg; ++s)
       if (polygon_of[s] < 0 || polygon_of[s] >= n_seg) return OR_E_INVALID;
@@ -599,6 +907,8 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
   int *unit = NULL, *udeg = NULL, *queue = NULL, *removed_order = NULL, *uptr = NULL, *useg = NULL;
   char *removed = NULL, *queued = NULL, *selfc = NULL;
   int *parent = NULL, *comp_of = NULL, *comp_ptr = NULL, *comp_seg = NULL, *local_of = NULL, *order = NULL;
+  int *inst_ptr = NULL, *inst_seg = NULL, *inst_att = NULL;
+  signed char *imask = NULL;
   int64_t *ccost = NULL, *cnodes = NULL;
   int32_t *cstat = NULL;
   memset(tot, 0, sizeof(*tot));
@@ -718,11 +1028,7 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
   }
   comp_ptr = calloc((size_t)n_comp + 2, sizeof(int));
   comp_seg = malloc(sizeof(int) * (size_t)(n_seg + 1));
-  order = malloc(sizeof(int) * (size_t)(n_comp + 1));
-  ccost = calloc((size_t)n_comp + 1, sizeof(int64_t));
-  cnodes = calloc((size_t)n_comp + 1, sizeof(int64_t));
-  cstat = calloc((size_t)n_comp + 1, sizeof(int32_t));
-  if (!comp_ptr || !comp_seg || !order || !ccost || !cnodes || !cstat) goto done;
+  if (!comp_ptr || !comp_seg) goto done;
   for (int s = 0; s < n_seg; ++s) if (comp_of[s] >= 0) comp_ptr[comp_of[s] + 1]++;
   for (int c = 0; c < n_comp; ++c) comp_ptr[c + 1] += comp_ptr[c];
   {
@@ -736,12 +1042,46 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
       } else local_of[s] = -1;
     free(fill);
   }
+
+  /* search instances: the components, or their biconnected blocks */
+  int n_inst = 0, len_seg = 0;
+  if (flags & OR_BICONNECTED) {
+    int cap_b = 16, cap_s = 16;
+    inst_ptr = malloc(sizeof(int) * (size_t)(cap_b + 1));
+    inst_att = malloc(sizeof(int) * (size_t)(cap_b + 1));
+    inst_seg = malloc(sizeof(int) * (size_t)cap_s);
+    if (!inst_ptr || !inst_att || !inst_seg) goto done;
+    inst_ptr[0] = 0;
+    for (int c = 0; c < n_comp; ++c) {
+      rc = component_blocks(comp_seg + comp_ptr[c], comp_ptr[c + 1] - comp_ptr[c], cptr, cadj,
+                            sptr, sadj, &inst_ptr, &inst_seg, &inst_att, &n_inst, &cap_b,
+                            &len_seg, &cap_s);
+      if (rc != OR_OK) goto done;
+    }
+    rc = OR_E_OOM;
+  } else {
+    n_inst = n_comp;
+    len_seg = comp_ptr[n_comp];
+    inst_ptr = malloc(sizeof(int) * (size_t)(n_comp + 1));
+    inst_att = malloc(sizeof(int) * (size_t)(n_comp + 1));
+    inst_seg = malloc(sizeof(int) * (size_t)(len_seg + 1));
+    if (!inst_ptr || !inst_att || !inst_seg) goto done;
+    memcpy(inst_ptr, comp_ptr, sizeof(int) * (size_t)(n_comp + 1));
+    memcpy(inst_seg, comp_seg, sizeof(int) * (size_t)len_seg);
+    for (int c = 0; c < n_comp; ++c) inst_att[c] = -1;
+  }
+  order = malloc(sizeof(int) * (size_t)(n_inst + 1));
+  ccost = calloc((size_t)n_inst + 1, sizeof(int64_t));
+  cnodes = calloc((size_t)n_inst + 1, sizeof(int64_t));
+  cstat = calloc((size_t)n_inst + 1, sizeof(int32_t));
+  imask = malloc((size_t)len_seg + 1);
+  if (!order || !ccost || !cnodes || !cstat || !imask) goto done;
   {
-    int *keys = malloc(sizeof(int) * (size_t)(2 * n_comp + 2));
+    int *keys = malloc(sizeof(int) * (size_t)(2 * n_inst + 2));
     if (!keys) goto done;
-    for (int c = 0; c < n_comp; ++c) { keys[2 * c] = comp_ptr[c + 1] - comp_ptr[c]; keys[2 * c + 1] = c; }
-    qsort(keys, (size_t)n_comp, 2 * sizeof(int), cmp_comp);
-    for (int c = 0; c < n_comp; ++c) order[c] = keys[2 * c + 1];
+    for (int c = 0; c < n_inst; ++c) { keys[2 * c] = inst_ptr[c + 1] - inst_ptr[c]; keys[2 * c + 1] = c; }
+    qsort(keys, (size_t)n_inst, 2 * sizeof(int), cmp_comp);
+    for (int c = 0; c < n_inst; ++c) order[c] = keys[2 * c + 1];
     free(keys);
   }
 
@@ -749,14 +1089,14 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
   {
     pool_t P;
     memset(&P, 0, sizeof(P));
-    P.k = k; P.n_comp = n_comp; P.Cc = cost_conflict; P.Cs = cost_stitch; P.budget = budget;
+    P.k = k; P.n_comp = n_inst; P.Cc = cost_conflict; P.Cs = cost_stitch; P.budget = budget;
     P.rule = (flags & OR_COLUMN_BFS) ? 1 : 0;
-    P.comp_ptr = comp_ptr; P.comp_seg = comp_seg; P.local_of = local_of; P.comp_of = comp_of;
+    P.comp_ptr = inst_ptr; P.comp_seg = inst_seg;
     P.cptr = cptr; P.cadj = cadj; P.sptr = sptr; P.sadj = sadj; P.work_order = order;
-    P.mask = mask_out; P.comp_cost = ccost; P.comp_nodes = cnodes; P.comp_status = cstat;
+    P.imask = imask; P.comp_cost = ccost; P.comp_nodes = cnodes; P.comp_status = cstat;
     atomic_init(&P.next, 0);
     atomic_init(&P.error, 0);
-    int nt = nthreads < n_comp ? nthreads : (n_comp > 0 ? n_comp : 1);
+    int nt = nthreads < n_inst ? nthreads : (n_inst > 0 ? n_inst : 1);
     pthread_t *th = malloc(sizeof(pthread_t) * (size_t)nt);
     if (!th) goto done;
     pthread_attr_t attr;
@@ -772,6 +1112,27 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
     if (started == 0) goto done;
     if (atomic_load(&P.error)) { rc = atomic_load(&P.error); goto done; }
   }
+  /* instance masks into the layout, in instance order: a block attached at
+   * segment a takes the transposition of masks that keeps a's mask */
+  for (int c = 0; c < n_inst; ++c) {
+    const int a = inst_ptr[c], b = inst_ptr[c + 1];
+    int from = -1, to = -1;
+    if (inst_att[c] >= 0) {
+      int l = local_id(inst_seg + a, b - a, inst_att[c]);
+      if (l < 0 || mask_out[inst_att[c]] < 0) { rc = OR_E_INVALID; goto done; }
+      from = imask[a + l];
+      to = mask_out[inst_att[c]];
+    }
+    for (int t = a; t < b; ++t) {
+      int m = imask[t];
+      if (from >= 0) m = m == from ? to : m == to ? from : m;
+      mask_out[inst_seg[t]] = (signed char)m;
+    }
+  }
+  /* instance of each segment: the first one holding it */
+  for (int s = 0; s < n_seg; ++s) comp_of[s] = -1;
+  for (int c = n_inst - 1; c >= 0; --c)
+    for (int t = inst_ptr[c]; t < inst_ptr[c + 1]; ++t) comp_of[inst_seg[t]] = c;
 
   /* recovery: reverse removal order, lowest mask unused by coloured nbrs */
   for (int t = n_removed_units - 1; t >= 0; --t) {
@@ -795,13 +1156,13 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
   for (int e = 0; e < mc; ++e) if (mask_out[cu[e]] == mask_out[cv[e]]) tot->n_conflicts++;
   for (int e = 0; e < ms; ++e) if (mask_out[tu[e]] != mask_out[tv[e]]) tot->n_stitches++;
   tot->cost = cost_conflict * tot->n_conflicts + cost_stitch * tot->n_stitches;
-  tot->n_components = n_comp;
+  tot->n_components = n_inst;
   tot->status = OR_OK;
-  for (int c = 0; c < n_comp; ++c) {
+  for (int c = 0; c < n_inst; ++c) {
     tot->nodes += cnodes[c];
     tot->component_cost_sum += ccost[c];
     if (cstat[c] == OR_BUDGET) { tot->n_budget_components++; tot->status = OR_BUDGET; }
-    int sz = comp_ptr[c + 1] - comp_ptr[c];
+    int sz = inst_ptr[c + 1] - inst_ptr[c];
     if (sz > tot->max_component) tot->max_component = sz;
     if (comp_nodes_out) comp_nodes_out[c] = cnodes[c];
     if (comp_cost_out) comp_cost_out[c] = ccost[c];
@@ -815,5 +1176,6 @@ done:
   free(unit); free(udeg); free(queue); free(removed_order); free(uptr); free(useg);
   free(removed); free(queued); free(selfc); free(parent); free(comp_of); free(comp_ptr);
   free(comp_seg); free(local_of); free(order); free(ccost); free(cnodes); free(cstat);
+  free(inst_ptr); free(inst_seg); free(inst_att); free(imask);
   return rc;
 }
