@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="k3_n200k_p02_batched")
     ap.add_argument("--budget", type=int, default=1 << 16)
+    ap.add_argument("--biconnected", action="store_true",
+                    help="search the biconnected blocks of each sub-graph and join them at cut "
+                         "segments")
     ap.add_argument("--column-rule", choices=["mrv", "bfs"], default="mrv",
                     help="column to branch on: fewest rows (mrv) or the paper's rule "
                          "(a single-row column, else breadth-first order)")
@@ -176,7 +179,8 @@ def run_serving(args, mpld, synth):
             now = time.perf_counter() - t0
             while i < n and arrivals[i] <= now:
                 L = pool[i % len(pool)]
-                t = mpld.mpld_server_submit(srv, L)
+                t = mpld.mpld_server_submit(
+                    srv, L, flags=mpld.MPLD_BICONNECTED if args.biconnected else 0)
                 arrival_of[t] = (arrivals[i], L.n_seg)
                 i += 1
             busy = False
@@ -216,6 +220,8 @@ def run_reference(args, rank, world):
     flags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
     if args.column_rule == "bfs":
         flags |= oracle.COLUMN_BFS
+    if args.biconnected and mode != "single":
+        flags |= oracle.BICONNECTED
     cores = os.cpu_count() or 1
     oracle.build()
     for _ in range(args.warmup):
@@ -234,7 +240,8 @@ def run_reference(args, rank, world):
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "segments": layout.n_seg, "k": layout.k,
-                   "node_budget": args.budget, "column_rule": args.column_rule},
+                   "node_budget": args.budget, "column_rule": args.column_rule,
+                   "biconnected": bool(args.biconnected and mode != "single")},
         "nodes_per_s": res.nodes * args.steps / total,
         "cpu_baseline": {"value": value, "unit": "segments/s", "cores": cores, "kind": "oracle",
                          "sample": f"whole layout ({layout.n_seg} segments, "
@@ -268,6 +275,8 @@ def main():
     s = stream.cuda_stream
     layout, mode = workload_layout(args.workload, rank, scale=args.scale)
     flags = (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE) if mode == "single" else 0
+    if args.biconnected and mode != "single":
+        flags |= mpld.MPLD_BICONNECTED
     prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
     info = mpld.mpld_problem_info(prob)
     rule_flag = mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0
@@ -319,6 +328,7 @@ def main():
         "config": {"workload": args.workload + (f"/scale{args.scale}" if args.scale > 1 else ""),
                    "segments": layout.n_seg, "polygons": layout.n_poly,
                    "k": layout.k, "node_budget": args.budget, "column_rule": args.column_rule,
+                   "biconnected": bool(flags & mpld.MPLD_BICONNECTED),
                    "instances": info.n_components,
                    "max_instance": info.max_component,
                    "removed_segments": info.n_removed_segments,
@@ -424,6 +434,8 @@ def main():
         oflags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
         if args.column_rule == "bfs":
             oflags |= oracle.COLUMN_BFS
+        if flags & mpld.MPLD_BICONNECTED:
+            oflags |= oracle.BICONNECTED
         ref = oracle.decompose(layout, flags=oflags, budget=args.budget, nthreads=cores)
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": layout.n_seg / dt, "unit": "segments/s", "cores": cores,

@@ -59,6 +59,22 @@ extern "C" {
                                     with the fewest rows, lowest index on ties.  Read by the search
                                     calls and by mpld_server_create; not available to
                                     mpld_search_instance_noalloc. */
+#define MPLD_BICONNECTED 16u     /* search the biconnected blocks of each sub-graph instead of the
+                                    whole sub-graph (conflict and stitch edges together), then join
+                                    them at their cut segments: every edge lies in exactly one
+                                    block and renaming masks inside a block keeps its cost, so the
+                                    blocks' optima join into the sub-graph's optimum.  Blocks are
+                                    taken breadth-first over the block-cut tree (from the
+                                    lexicographically first block holding the sub-graph's lowest
+                                    segment; a block's segments in ascending id; at each, the
+                                    untaken blocks in lexicographic order of their ascending
+                                    segment lists), and a block's masks are renamed by the one
+                                    transposition that keeps its attach segment's mask.  With a
+                                    node budget each block has its own.  Read by
+                                    mpld_build_matrix; not with MPLD_SINGLE_INSTANCE
+                                    (MPLD_E_INVALID).  Instances are then blocks: a cut segment
+                                    belongs to several, and mpld_component_results reports the
+                                    first. */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
                                     the solve calls then return MPLD_E_STATE */
@@ -290,9 +306,10 @@ typedef struct {
 int mpld_server_create(const mpld_server_config *cfg, const mpld_params *search,
                        mpld_server **out);
 
-/* Queue a layout (copied; `graph` may be reused at once).  flags as mpld_params.flags
- * (MPLD_NO_SIMPLIFY, MPLD_SINGLE_INSTANCE).  Returns MPLD_OK and a ticket.  Input errors
- * surface later as the ticket's result code. */
+/* Queue a layout (copied; `graph` may be reused at once).  flags as mpld_params.flags for
+ * mpld_build_matrix (MPLD_NO_SIMPLIFY, MPLD_SINGLE_INSTANCE, MPLD_BICONNECTED; other bits are
+ * ignored).  Returns MPLD_OK and a ticket.  Input errors surface later as the ticket's result
+ * code. */
 int mpld_server_submit(mpld_server *s, const mpld_graph *graph, uint32_t flags, int64_t *ticket);
 
 /* Non-blocking progress: admit, upload, launch, detect finished layouts.  Writes up to

@@ -100,6 +100,118 @@ void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
   for (size_t e = 0; e < u.size(); ++e) adj[fill[u[e]]++] = v[e];
 }
 
+// Biconnected blocks of one component (MPLD_BICONNECTED), appended in the
+// canonical order: breadth-first over the block-cut tree, starting from the
+// lexicographically first block (ascending segment list) that holds the
+// component's lowest segment; from a block, its segments in ascending id,
+// and at each the blocks not yet taken in lexicographic order, attached at
+// that segment.  Blocks come from one iterative depth-first search with
+// discovery times and low points over conflict and stitch edges together;
+// a component without edges is one block of one segment.
+//   seg:  the component's segments, ascending; loc: scratch, -1 on entry
+//   and on return (global segment -> index in seg)
+//   iptr / iseg / iatt: block boundaries, segments, attach index within the
+//   block (-1 for the first block)
+void component_blocks(const std::vector<int32_t> &seg, const std::vector<int32_t> &cptr,
+                      const std::vector<int32_t> &cadj, const std::vector<int32_t> &sptr,
+                      const std::vector<int32_t> &sadj, std::vector<int32_t> &loc,
+                      std::vector<int32_t> &iptr, std::vector<int32_t> &iseg,
+                      std::vector<int32_t> &iatt) {
+  const int n = (int)seg.size();
+  for (int i = 0; i < n; ++i) loc[seg[i]] = i;
+  // union adjacency, local ids ascending
+  std::vector<int32_t> lptr((size_t)n + 1, 0), ladj;
+  for (int i = 0; i < n; ++i) {
+    const int g = seg[i];
+    int a = cptr[g], b = sptr[g];
+    while (a < cptr[g + 1] || b < sptr[g + 1]) {
+      int w;
+      if (b >= sptr[g + 1] || (a < cptr[g + 1] && cadj[a] <= sadj[b])) {
+        w = cadj[a++];
+        if (b < sptr[g + 1] && sadj[b] == w) ++b;
+      } else {
+        w = sadj[b++];
+      }
+      if (loc[w] >= 0) ladj.push_back(loc[w]);
+    }
+    lptr[i + 1] = (int32_t)ladj.size();
+  }
+  std::vector<std::vector<int32_t>> blocks;
+  if (ladj.empty()) {
+    blocks.push_back({0});
+  } else {
+    std::vector<int32_t> disc((size_t)n, -1), low((size_t)n, 0), mark((size_t)n, -1);
+    struct Frame { int v, parent, it; };
+    std::vector<Frame> st;
+    std::vector<std::pair<int32_t, int32_t>> es;
+    int timer = 0;
+    disc[0] = low[0] = timer++;
+    st.push_back({0, -1, lptr[0]});
+    while (!st.empty()) {
+      Frame &f = st.back();
+      const int v = f.v;
+      if (f.it < lptr[v + 1]) {
+        const int w = ladj[f.it++];
+        if (disc[w] < 0) {
+          es.emplace_back(v, w);
+          disc[w] = low[w] = timer++;
+          st.push_back({w, v, lptr[w]});
+        } else if (w != f.parent && disc[w] < disc[v]) {
+          es.emplace_back(v, w);
+          low[v] = std::min(low[v], disc[w]);
+        }
+        continue;
+      }
+      st.pop_back();
+      if (st.empty()) break;
+      const int u = st.back().v;
+      low[u] = std::min(low[u], low[v]);
+      if (low[v] >= disc[u]) {
+        // u separates v's subtree: its edges since (u, v) form a block
+        std::vector<int32_t> b;
+        const int id = (int)blocks.size();
+        for (;;) {
+          const auto e = es.back();
+          es.pop_back();
+          for (int x : {e.first, e.second})
+            if (mark[x] != id) { mark[x] = id; b.push_back(x); }
+          if (e.first == u && e.second == v) break;
+        }
+        std::sort(b.begin(), b.end());
+        blocks.push_back(std::move(b));
+      }
+    }
+  }
+  // blocks at each segment, lexicographic; breadth-first from segment 0's first
+  std::vector<std::vector<int32_t>> at((size_t)n);
+  for (int b = 0; b < (int)blocks.size(); ++b)
+    for (int x : blocks[b]) at[x].push_back(b);
+  for (auto &l : at)
+    std::sort(l.begin(), l.end(), [&](int x, int y) { return blocks[x] < blocks[y]; });
+  std::vector<uint8_t> taken(blocks.size(), 0);
+  std::vector<std::pair<int32_t, int32_t>> queue;   // block, attach segment (local) or -1
+  queue.emplace_back(at[0][0], -1);
+  taken[at[0][0]] = 1;
+  for (size_t h = 0; h < queue.size(); ++h)
+    for (int x : blocks[queue[h].first])
+      for (int b : at[x])
+        if (!taken[b]) {
+          taken[b] = 1;
+          queue.emplace_back(b, x);
+        }
+  for (const auto &q : queue) {
+    const auto &b = blocks[q.first];
+    int att = -1;
+    for (size_t i = 0; i < b.size(); ++i) {
+      if (b[i] == q.second) att = (int)i;
+      iseg.push_back(seg[b[i]]);
+    }
+    iatt.push_back(att);
+    iptr.push_back((int32_t)iseg.size());
+  }
+  for (int i = 0; i < n; ++i) loc[seg[i]] = -1;
+}
+
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
 
 std::mutex g_tune_mu;
@@ -140,6 +252,8 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     for (int s = 0; s < n; ++s)
       if (g->polygon_of[s] < 0 || g->polygon_of[s] >= n) return MPLD_E_INVALID;
 
+  if (params && (params->flags & MPLD_BICONNECTED) && (params->flags & MPLD_SINGLE_INSTANCE))
+    return MPLD_E_INVALID;
   mpld_problem *p = new (std::nothrow) mpld_problem();
   if (!p) return MPLD_E_OOM;
   p->n_seg = n;
@@ -236,28 +350,49 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       }
     }
     for (int u : p->removed_order) p->n_removed_segments += p->uptr[u + 1] - p->uptr[u];
-    const int C = p->n_comp;
+    int C = p->n_comp;
     p->comp_ptr.assign((size_t)C + 1, 0);
     for (int s = 0; s < n; ++s)
       if (p->comp_of[s] >= 0) p->comp_ptr[p->comp_of[s] + 1]++;
     for (int c = 0; c < C; ++c) p->comp_ptr[c + 1] += p->comp_ptr[c];
     p->comp_seg.resize((size_t)p->comp_ptr[C]);
-    std::vector<int32_t> local_of((size_t)n, -1);
     {
       std::vector<int32_t> fill(p->comp_ptr.begin(), p->comp_ptr.end() - 1);
       for (int s = 0; s < n; ++s)
-        if (p->comp_of[s] >= 0) {
-          const int c = p->comp_of[s];
-          local_of[s] = fill[c] - p->comp_ptr[c];
-          p->comp_seg[fill[c]++] = s;
-        }
+        if (p->comp_of[s] >= 0) p->comp_seg[fill[p->comp_of[s]]++] = s;
     }
+    if (p->flags & MPLD_BICONNECTED) {
+      // the search instances become the biconnected blocks of each component
+      std::vector<int32_t> iptr{0}, iseg, iatt, loc((size_t)n, -1);
+      for (int c = 0; c < C; ++c) {
+        const std::vector<int32_t> seg(p->comp_seg.begin() + p->comp_ptr[c],
+                                       p->comp_seg.begin() + p->comp_ptr[c + 1]);
+        component_blocks(seg, p->cptr, p->cadj, sptr, sadj, loc, iptr, iseg, iatt);
+      }
+      p->n_comp = (int)iatt.size();
+      p->comp_ptr = std::move(iptr);
+      p->comp_seg = std::move(iseg);
+      p->inst_attach = std::move(iatt);
+      std::fill(p->comp_of.begin(), p->comp_of.end(), -1);
+      for (int c = p->n_comp - 1; c >= 0; --c)
+        for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) p->comp_of[p->comp_seg[t]] = c;
+    }
+    C = p->n_comp;
     for (int c = 0; c < C; ++c) {
       const int sz = p->comp_ptr[c + 1] - p->comp_ptr[c];
       p->max_component = std::max(p->max_component, sz);
       if (sz > MPLD_MAX_INSTANCE_SEGMENTS) { delete p; return MPLD_E_TOO_LARGE; }
     }
     p->instance_segments = p->comp_ptr[C];
+    // membership of the instance being packed: a segment may sit in several
+    // blocks, so instance c marks its own segments and their local ids
+    std::vector<int32_t> stamp((size_t)n, -1), lid((size_t)n, -1);
+    auto mark_instance = [&](int c) {
+      for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
+        stamp[p->comp_seg[t]] = c;
+        lid[p->comp_seg[t]] = t - p->comp_ptr[c];
+      }
+    };
 
     // ---- pack each instance: read-only block + descriptor
     p->ro_off.resize((size_t)C);
@@ -270,11 +405,12 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     for (int c = 0; c < C; ++c) {
       int ne2 = 0, ns2 = 0, mdc = 0, mds = 0;
       int64_t max_inc = 0;
+      mark_instance(c);
       for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
         const int s = p->comp_seg[t];
         int dc = 0, ds = 0;
-        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) dc += p->comp_of[p->cadj[i]] == c;
-        for (int i = sptr[s]; i < sptr[s + 1]; ++i) ds += p->comp_of[sadj[i]] == c;
+        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) dc += stamp[p->cadj[i]] == c;
+        for (int i = sptr[s]; i < sptr[s + 1]; ++i) ds += stamp[sadj[i]] == c;
         ne2 += dc;
         ns2 += ds;
         mdc = std::max(mdc, dc);
@@ -312,14 +448,15 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       uint16_t *cn = (uint16_t *)(blk + R.cnbr);
       uint16_t *sn = (uint16_t *)(blk + R.snbr);
       int ci = 0, si = 0;
+      mark_instance(c);
       for (int t = a; t < b; ++t) {
         const int s = p->comp_seg[t];
         ptr[2 * (t - a)] = ci;
         ptr[2 * (t - a) + 1] = si;
         for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i)
-          if (p->comp_of[p->cadj[i]] == c) cn[ci++] = (uint16_t)local_of[p->cadj[i]];
+          if (stamp[p->cadj[i]] == c) cn[ci++] = (uint16_t)lid[p->cadj[i]];
         for (int i = sptr[s]; i < sptr[s + 1]; ++i)
-          if (p->comp_of[sadj[i]] == c) sn[si++] = (uint16_t)local_of[sadj[i]];
+          if (stamp[sadj[i]] == c) sn[si++] = (uint16_t)lid[sadj[i]];
       }
       ptr[2 * nc] = ci;
       ptr[2 * nc + 1] = si;
@@ -598,8 +735,24 @@ int mpld_internal_finish(mpld_problem *p, const InstResult *hres, const int8_t *
   }
   p->have_results = true;
   std::vector<int8_t> m((size_t)p->n_seg, (int8_t)-1);
-  for (int c = 0; c < C; ++c)
-    for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) m[p->comp_seg[t]] = hmasks[t];
+  for (int c = 0; c < C; ++c) {
+    // a block attached at a segment already coloured takes the transposition
+    // of masks that keeps that segment's mask (cost does not depend on the
+    // names of the masks); instances come in an order where the attach
+    // segment is always coloured first
+    int from = -1, to = -1;
+    const int att = p->inst_attach.empty() ? -1 : p->inst_attach[c];
+    if (att >= 0) {
+      from = hmasks[p->comp_ptr[c] + att];
+      to = m[p->comp_seg[p->comp_ptr[c] + att]];
+      if (to < 0) return MPLD_E_STATE;
+    }
+    for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
+      int x = hmasks[t];
+      if (from >= 0) x = x == from ? to : x == to ? from : x;
+      m[p->comp_seg[t]] = (int8_t)x;
+    }
+  }
   // recovery: reverse removal order, lowest mask unused by coloured neighbours
   for (auto it = p->removed_order.rbegin(); it != p->removed_order.rend(); ++it) {
     const int u = *it;

@@ -39,6 +39,7 @@ struct mpld_problem {
   // sub-graphs (search instances)
   int n_comp = 0;
   std::vector<int32_t> comp_ptr, comp_seg, comp_of;
+  std::vector<int32_t> inst_attach;   // biconnected blocks: attach segment's index, -1 first
   std::vector<int32_t> inst_ne2;
   int max_component = 0;
   int64_t instance_segments = 0;

@@ -31,6 +31,7 @@ MPLD_NO_SIMPLIFY = 1
 MPLD_SINGLE_INSTANCE = 2
 MPLD_HOST_ONLY = 4
 MPLD_COLUMN_BFS = 8
+MPLD_BICONNECTED = 16
 MPLD_MAX_INSTANCE_SEGMENTS = 65535
 
 _P = ctypes.c_void_p

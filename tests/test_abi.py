@@ -66,6 +66,40 @@ def test_host_split_matches_oracle(k, deg, p, seed):
     assert np.array_equal(comp_of, ref.comp_of)
 
 
+@pytest.mark.parametrize("k,deg,p,seed", [(3, 3.0, 0.2, 1), (4, 5.0, 0.3, 2), (3, 4.5, 0.25, 3),
+                                          (2, 2.5, 0.2, 5)])
+def test_host_block_split_matches_oracle(k, deg, p, seed):
+    # biconnected blocks as search instances: same count, order and sizes
+    L = synth.unit_disk_layout(4000, k, seed=seed, mean_deg=deg, p_stitch=p)
+    prob = host_only(L, mpld.MPLD_BICONNECTED)
+    info = mpld.mpld_problem_info(prob)
+    _, _, _, comp_of = mpld.mpld_component_results(prob, results=False)
+    ref = oracle.decompose(L, flags=oracle.BICONNECTED, budget=50, nthreads=4)
+    assert info.n_components == ref.n_components
+    assert info.max_component == ref.max_component
+    assert np.array_equal(comp_of, ref.comp_of)
+    # each packed block is the EC matrix of that block's sub-graph
+    keep = sorted(int(s) for s in np.nonzero(ref.comp_of >= 0)[0])
+    conf, st = edges(L)
+    sub = set(keep)
+    loc = {s: i for i, s in enumerate(keep)}
+    blocks = oracle.blocks(len(keep), [(loc[a], loc[b]) for a, b in conf if a in sub and b in sub],
+                           [(loc[a], loc[b]) for a, b in st if a in sub and b in sub])
+    assert len(blocks) == info.n_components
+    for c in range(0, len(blocks), 11):
+        g = [keep[v] for v in blocks[c][0]]
+        lb = {s: j for j, s in enumerate(g)}
+        cc = [(lb[a], lb[b]) for a, b in conf if a in lb and b in lb]
+        assert np.array_equal(mpld.mpld_export_matrix(prob, c), oracle.export_matrix(len(g), k, cc))
+
+
+def test_block_split_with_single_instance_rejected():
+    with pytest.raises(mpld.MpldError) as e:
+        host_only(synth.graph_from_edges(3, 3, [(0, 1)]),
+                  mpld.MPLD_BICONNECTED | mpld.MPLD_SINGLE_INSTANCE)
+    assert e.value.code == mpld.MPLD_E_INVALID
+
+
 def test_host_single_instance_mode():
     L, mode = synth.workload("k3_n400_p025_plain")
     prob = host_only(L, mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE)

@@ -227,6 +227,39 @@ def test_rule1_graph_cache_keeps_rules_apart(stream):
     prob.close()
 
 
+# ------------------------------------------- biconnected blocks as instances
+
+BIC = mpld.MPLD_BICONNECTED
+
+
+@pytest.mark.parametrize("n,k,seed,p", small_cases()[1::3])
+def test_blocks_small_graphs(n, k, seed, p, stream):
+    L = synth.random_graph(n, k, seed=seed, p_edge=p * 0.6, n_stitch=n // 4, identity_polygons=False)
+    for bflags, oflags in ((mpld.MPLD_NO_SIMPLIFY | BIC, oracle.NO_SIMPLIFY | oracle.BICONNECTED),
+                           (BIC, oracle.BICONNECTED)):
+        ref = oracle.decompose(L, flags=oflags, budget=200000)
+        for path in ("batch", "plain"):
+            assert_same(gpu_run(L, flags=bflags, budget=200000, path=path, stream=stream.cuda_stream),
+                        ref, L)
+
+
+@pytest.mark.parametrize("name", ["k3_n200k_p02_batched", "k4_n100k_p03_batched"])
+@pytest.mark.parametrize("budget", [3000, 1 << 16])
+def test_blocks_batched_workloads_full_size(name, budget, stream):
+    L, mode = synth.workload(name)
+    ref = oracle.decompose(L, flags=oracle.BICONNECTED, budget=budget, nthreads=NTHREADS)
+    g = gpu_run(L, flags=BIC, budget=budget, stream=stream.cuda_stream)
+    assert_same(g, ref, L)
+    assert ref.max_component < L.n_seg
+
+
+def test_blocks_with_column_rule(stream):
+    L = synth.unit_disk_layout(6000, 3, seed=21, mean_deg=4.5, p_stitch=0.2)
+    ref = oracle.decompose(L, flags=oracle.BICONNECTED | oracle.COLUMN_BFS, budget=2000,
+                           nthreads=NTHREADS)
+    assert_same(gpu_run(L, flags=BIC, budget=2000, stream=stream.cuda_stream, search_flags=BFS), ref, L)
+
+
 # ---------------------------------------------------------------- launch forms
 
 def test_results_independent_of_launch_shape(stream):

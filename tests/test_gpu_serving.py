@@ -143,3 +143,15 @@ def test_column_rule_flag_reaches_served_searches(torch_cuda):
         ref = oracle.decompose(L, flags=oracle.COLUMN_BFS, budget=BUDGET, nthreads=NTHREADS)
         rc, mask, res = got[t]
         assert np.array_equal(mask, ref.mask) and res.nodes == ref.nodes and res.cost == ref.cost
+
+
+def test_block_split_requests(torch_cuda):
+    # requests built with the biconnected split: results equal the oracle's
+    Ls = requests(4, seed=83, n_max=8000)
+    with mpld.mpld_server_create(None, mpld.make_params(node_budget=BUDGET)) as srv:
+        tickets = [mpld.mpld_server_submit(srv, L, flags=mpld.MPLD_BICONNECTED) for L in Ls]
+        got = drain(srv, tickets)
+    for t, L in zip(tickets, Ls):
+        ref = oracle.decompose(L, flags=oracle.BICONNECTED, budget=BUDGET, nthreads=NTHREADS)
+        rc, mask, res = got[t]
+        assert np.array_equal(mask, ref.mask) and res.nodes == ref.nodes and res.cost == ref.cost
