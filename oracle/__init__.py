@@ -33,6 +33,7 @@ NO_SIMPLIFY = 1
 SINGLE_INSTANCE = 2
 COLUMN_BFS = 8      # the paper's column rule (single-row column, else BFS order)
 BICONNECTED = 16    # search the biconnected blocks of each component, merge at cut segments
+CLIQUE_BOUND = 32   # second bound mode: dead columns plus untouched edge-disjoint (k+1)-cliques
 INF = (1 << 63) - 1
 
 
@@ -79,6 +80,8 @@ def _load():
         lib.oracle_decompose.restype = i32
         lib.oracle_blocks.argtypes = [i32, i32, P, P, i32, P, P, P, P, P]
         lib.oracle_blocks.restype = i32
+        lib.oracle_cliques.argtypes = [i32, i32, i32, P, P, i32, P]
+        lib.oracle_cliques.restype = i32
         _lib = lib
     return _lib
 
@@ -100,11 +103,13 @@ class InstanceResult:
 
 
 def solve_instance(n, k, conf, stitch=(), cost_conflict=10, cost_stitch=1, budget=0,
-                   rule=0) -> InstanceResult:
+                   rule=0, clique_bound=False) -> InstanceResult:
     """Search one instance (the whole graph), Algorithm X with dancing links.
 
     rule 0: column with the fewest rows, lowest index on ties; rule 1: the
     paper's rule (a column with one row left, else breadth-first order).
+    clique_bound: the second bound mode (dead columns plus untouched
+    edge-disjoint (k+1)-cliques).
     """
     lib = _load()
     conf = np.asarray(conf, dtype=np.int32).reshape(-1, 2)
@@ -115,11 +120,26 @@ def solve_instance(n, k, conf, stitch=(), cost_conflict=10, cost_stitch=1, budge
     cost = ctypes.c_int64(0)
     nodes = ctypes.c_int64(0)
     rc = lib.oracle_solve_instance_rule(n, k, len(cu), _ptr(cu), _ptr(cv), len(su), _ptr(su),
-                                        _ptr(sv), cost_conflict, cost_stitch, budget, rule, _ptr(x),
+                                        _ptr(sv), cost_conflict, cost_stitch, budget,
+                                        rule | (2 if clique_bound else 0), _ptr(x),
                                         ctypes.byref(cost), ctypes.byref(nodes))
     if rc < 0:
         raise ValueError(f"oracle_solve_instance failed: {rc}")
     return InstanceResult(status=rc, cost=cost.value, nodes=nodes.value, x=x[:n].copy())
+
+
+def cliques(n, k, conf) -> list:
+    """The clique bound's cliques: greedy edge-disjoint (k+1)-cliques of the
+    conflict graph in lexicographic order, each an ascending member list."""
+    lib = _load()
+    conf = np.asarray(conf, dtype=np.int32).reshape(-1, 2)
+    cu, cv = _i32(conf[:, 0]), _i32(conf[:, 1])
+    cap = max(1, len(cu))
+    out = np.zeros(cap * (k + 1), dtype=np.int32)
+    nq = lib.oracle_cliques(n, k, len(cu), _ptr(cu), _ptr(cv), cap, _ptr(out))
+    if nq < 0:
+        raise ValueError(f"oracle_cliques failed: {nq}")
+    return [out[q * (k + 1):(q + 1) * (k + 1)].tolist() for q in range(nq)]
 
 
 def count_exact_covers(n, k, conf, limit=1 << 62) -> int:

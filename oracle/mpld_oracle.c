@@ -32,6 +32,14 @@
  *   - bound: Z = number of uncovered primary columns of size 0; prune when
  *     g + Cc * Z >= best (admissible: such a segment sees every mask taken by
  *     a distinct conflict neighbour, so it will pay at least Cc);
+ *   - clique bound (optional, the second bound mode): the instance's
+ *     (k+1)-cliques of conflict edges, enumerated in lexicographic order of
+ *     their ascending member lists, are taken greedily when none of their
+ *     edges is in a clique already taken.  Q = number of taken cliques whose
+ *     members are all unassigned; prune when g + Cc * (Z + Q) >= best
+ *     (admissible: k + 1 unassigned members of a clique must repeat a mask,
+ *     on an edge between two unassigned segments, while Z's conflicts lie on
+ *     edges to assigned segments, and taken cliques share no edge);
  *   - column, rule 0 (default): minimum size S, lowest segment index on
  *     ties (Knuth's S heuristic over a ring kept in index order);
  *   - column, rule 1 (the paper's rule, Algorithm 1: "a column with only
@@ -78,6 +86,7 @@
 #define OR_SINGLE_INSTANCE 2u
 #define OR_COLUMN_BFS 8u
 #define OR_BICONNECTED 16u
+#define OR_CLIQUE_BOUND 32u
 
 #define OR_INF INT64_MAX
 
@@ -104,13 +113,15 @@ typedef struct {
   int coltop;
   int rule;          /* column rule: 0 fewest rows, 1 single row else BFS order */
   int *bfs_rank;     /* rule 1: breadth-first rank of each segment */
+  int nq;            /* clique bound: taken cliques, k + 1 members each */
+  int *qv;
 } dlx_t;
 
 static void dlx_free(dlx_t *d) {
   free(d->L); free(d->R); free(d->U); free(d->D); free(d->C); free(d->S);
   free(d->rownode); free(d->covered);
   free(d->cptr); free(d->cadj); free(d->sptr); free(d->sadj);
-  free(d->x); free(d->bestx); free(d->colstack); free(d->bfs_rank);
+  free(d->x); free(d->bestx); free(d->colstack); free(d->bfs_rank); free(d->qv);
   memset(d, 0, sizeof(*d));
 }
 
@@ -310,7 +321,13 @@ static void dlx_search(dlx_t *d, int64_t g) {
       else if (cmin == 0 || d->bfs_rank[c - 1] < d->bfs_rank[cmin - 1]) cmin = c;
     }
   }
-  if (g + d->Cc * Z >= d->best) return;    /* admissible bound */
+  int64_t Q = 0;                           /* taken cliques with no member assigned */
+  for (int q = 0; q < d->nq; ++q) {
+    int all = 1;
+    for (int i = 0; i <= d->k && all; ++i) all = d->x[d->qv[q * (d->k + 1) + i]] < 0;
+    Q += all;
+  }
+  if (g + d->Cc * (Z + Q) >= d->best) return;    /* admissible bound */
 
   const int v = cmin - 1, k = d->k;
   int64_t inc[8];
@@ -408,11 +425,90 @@ static int norm_edges(int n, int m, const int *u, const int *v, int **ou, int **
 
 /* Search one instance (the whole given graph, connected or not).
  * x_out: n masks; returns OR_OK / OR_BUDGET / error. */
+/* Greedy edge-disjoint (k+1)-cliques of the conflict graph: every clique in
+ * lexicographic order of its ascending member list, taken when none of its
+ * edges is in a clique already taken. */
+static int edge_slot(const dlx_t *d, int a, int b) {   /* adjacency entry of b in a's list */
+  int lo = d->cptr[a], hi = d->cptr[a + 1];
+  while (lo < hi) {
+    int mid = lo + (hi - lo) / 2;
+    if (d->cadj[mid] < b) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < d->cptr[a + 1] && d->cadj[lo] == b) ? lo : -1;
+}
+static int clique_extend(dlx_t *d, int *cur, int depth, char *used, int *cap) {
+  const int K = d->k + 1;
+  if (depth == K) {
+    for (int i = 0; i < K; ++i)
+      for (int j = i + 1; j < K; ++j)
+        if (used[edge_slot(d, cur[i], cur[j])]) return OR_OK;
+    for (int i = 0; i < K; ++i)
+      for (int j = i + 1; j < K; ++j) {
+        used[edge_slot(d, cur[i], cur[j])] = 1;
+        used[edge_slot(d, cur[j], cur[i])] = 1;
+      }
+    if (d->nq == *cap) {
+      int nc = *cap * 2 + 8;
+      int *nv = realloc(d->qv, sizeof(int) * (size_t)nc * (size_t)K);
+      if (!nv) return OR_E_OOM;
+      d->qv = nv;
+      *cap = nc;
+    }
+    memcpy(d->qv + (size_t)d->nq * (size_t)K, cur, sizeof(int) * (size_t)K);
+    d->nq++;
+    return OR_OK;
+  }
+  const int last = cur[depth - 1];
+  for (int i = d->cptr[last]; i < d->cptr[last + 1]; ++i) {
+    const int w = d->cadj[i];
+    if (w <= last) continue;
+    int ok = 1;
+    for (int j = 0; j < depth - 1 && ok; ++j) ok = edge_slot(d, cur[j], w) >= 0;
+    if (!ok) continue;
+    cur[depth] = w;
+    int rc = clique_extend(d, cur, depth + 1, used, cap);
+    if (rc != OR_OK) return rc;
+  }
+  return OR_OK;
+}
+static int build_cliques(dlx_t *d) {
+  char *used = calloc((size_t)d->cptr[d->n] + 1, 1);
+  if (!used) return OR_E_OOM;
+  int cur[9], cap = 0, rc = OR_OK;
+  for (int v = 0; v < d->n && rc == OR_OK; ++v) {
+    cur[0] = v;
+    rc = clique_extend(d, cur, 1, used, &cap);
+  }
+  free(used);
+  return rc;
+}
+
+/* Taken cliques of an instance (for tests): writes up to max_q * (k + 1)
+ * member ids; returns the number of cliques. */
+int oracle_cliques(int n, int k, int ne, const int *eu, const int *ev, int max_q, int *out) {
+  if (n < 0 || k < 2 || k > 8 || ne < 0) return OR_E_INVALID;
+  int *cu, *cv, mc, rc;
+  if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) return rc;
+  dlx_t d;
+  rc = dlx_build(&d, n, k, mc, cu, cv, 0, NULL, NULL, 10, 1);
+  free(cu); free(cv);
+  if (rc != OR_OK) return rc;
+  rc = build_cliques(&d);
+  if (rc == OR_OK) {
+    int m = d.nq < max_q ? d.nq : max_q;
+    if (m > 0) memcpy(out, d.qv, sizeof(int) * (size_t)m * (size_t)(k + 1));
+    rc = d.nq;
+  }
+  dlx_free(&d);
+  return rc;
+}
+
 int oracle_solve_instance_rule(int n, int k, int ne, const int *eu, const int *ev,
                                int ns, const int *su, const int *sv,
                                int64_t cost_conflict, int64_t cost_stitch, int64_t budget, int rule,
                                signed char *x_out, int64_t *cost_out, int64_t *nodes_out) {
-  if (rule < 0 || rule > 1) return OR_E_INVALID;
+  if (rule < 0 || rule > 3) return OR_E_INVALID;   /* bit 0: column rule, bit 1: clique bound */
   if (n < 0 || k < 2 || k > 8 || ne < 0 || ns < 0) return OR_E_INVALID;
   int *cu, *cv, *tu, *tv, mc, ms, rc;
   if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) return rc;
@@ -422,8 +518,12 @@ int oracle_solve_instance_rule(int n, int k, int ne, const int *eu, const int *e
   free(cu); free(cv); free(tu); free(tv);
   if (rc != OR_OK) return rc;
   d.budget = budget;
-  d.rule = rule;
-  if (rule == 1 && bfs_ranks(n, d.cptr, d.cadj, d.sptr, d.sadj, &d.bfs_rank) != OR_OK) {
+  d.rule = rule & 1;
+  if (d.rule == 1 && bfs_ranks(n, d.cptr, d.cadj, d.sptr, d.sadj, &d.bfs_rank) != OR_OK) {
+    dlx_free(&d);
+    return OR_E_OOM;
+  }
+  if ((rule & 2) && build_cliques(&d) != OR_OK) {
     dlx_free(&d);
     return OR_E_OOM;
   }
@@ -1090,7 +1190,7 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
     pool_t P;
     memset(&P, 0, sizeof(P));
     P.k = k; P.n_comp = n_inst; P.Cc = cost_conflict; P.Cs = cost_stitch; P.budget = budget;
-    P.rule = (flags & OR_COLUMN_BFS) ? 1 : 0;
+    P.rule = ((flags & OR_COLUMN_BFS) ? 1 : 0) | ((flags & OR_CLIQUE_BOUND) ? 2 : 0);
     P.comp_ptr = inst_ptr; P.comp_seg = inst_seg;
     P.cptr = cptr; P.cadj = cadj; P.sptr = sptr; P.sadj = sadj; P.work_order = order;
     P.imask = imask; P.comp_cost = ccost; P.comp_nodes = cnodes; P.comp_status = cstat;

@@ -62,6 +62,20 @@ def bfs_rank(n, conf, stitch):
     return rank
 
 
+def greedy_cliques(n, k, conf):
+    """Edge-disjoint (k+1)-cliques: all of them in lexicographic order of
+    their ascending member tuples (itertools.combinations order), each
+    taken when it shares no edge with one taken before."""
+    adj = [set(a) for a in adjacency(n, conf)]
+    used, out = set(), []
+    for t in itertools.combinations(range(n), k + 1):
+        pairs = list(itertools.combinations(t, 2))
+        if all(b in adj[a] for a, b in pairs) and not any(p in used for p in pairs):
+            used.update(pairs)
+            out.append(list(t))
+    return out
+
+
 class _Search:
     def __init__(self, n, k, conf, stitch, cc, cs, rule=0):
         self.n, self.k, self.cc, self.cs = n, k, cc, cs
@@ -141,16 +155,18 @@ def first_min_leaf(n, k, conf, stitch, cc=10, cs=1, rule=0):
             return c, x
 
 
-def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0):
+def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0, clique_bound=False):
     """The canonical search with the dead-segment bound and node budget.
 
     node = one call; leaf with g < best is the new incumbent and best == 0
     stops; prune when g + cc * (#unassigned segments with no available mask)
-    >= best; with budget B > 0, a call made when an incumbent exists and B
-    nodes have been counted stops everything.  Returns (cost, x, nodes,
-    budget_hit).
+    >= best; with clique_bound, the number of greedy cliques with no member
+    assigned is added to that count; with budget B > 0, a call made when an
+    incumbent exists and B nodes have been counted stops everything.
+    Returns (cost, x, nodes, budget_hit).
     """
     S = _Search(n, k, conf, stitch, cc, cs, rule)
+    cl = greedy_cliques(n, k, conf) if clique_bound else []
     st = dict(best=None, bestx=None, nodes=0, done=False, hit=False)
 
     def rec(g):
@@ -166,7 +182,8 @@ def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0):
                 if g == 0:
                     st["done"] = True
             return
-        if st["best"] is not None and g + cc * z >= st["best"]:
+        q = sum(1 for c in cl if all(S.x[v] < 0 for v in c))
+        if st["best"] is not None and g + cc * (z + q) >= st["best"]:
             return
         order, inc = S.row_order(v)
         for c in order:
