@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--biconnected", action="store_true",
                     help="search the biconnected blocks of each sub-graph and join them at cut "
                          "segments")
+    ap.add_argument("--clique-bound", action="store_true",
+                    help="second bound mode: also count untouched edge-disjoint (k+1)-cliques")
     ap.add_argument("--column-rule", choices=["mrv", "bfs"], default="mrv",
                     help="column to branch on: fewest rows (mrv) or the paper's rule "
                          "(a single-row column, else breadth-first order)")
@@ -180,7 +182,8 @@ def run_serving(args, mpld, synth):
             while i < n and arrivals[i] <= now:
                 L = pool[i % len(pool)]
                 t = mpld.mpld_server_submit(
-                    srv, L, flags=mpld.MPLD_BICONNECTED if args.biconnected else 0)
+                    srv, L, flags=(mpld.MPLD_BICONNECTED if args.biconnected else 0) |
+                    (mpld.MPLD_CLIQUE_BOUND if args.clique_bound else 0))
                 arrival_of[t] = (arrivals[i], L.n_seg)
                 i += 1
             busy = False
@@ -222,6 +225,8 @@ def run_reference(args, rank, world):
         flags |= oracle.COLUMN_BFS
     if args.biconnected and mode != "single":
         flags |= oracle.BICONNECTED
+    if args.clique_bound:
+        flags |= oracle.CLIQUE_BOUND
     cores = os.cpu_count() or 1
     oracle.build()
     for _ in range(args.warmup):
@@ -241,7 +246,8 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "segments": layout.n_seg, "k": layout.k,
                    "node_budget": args.budget, "column_rule": args.column_rule,
-                   "biconnected": bool(args.biconnected and mode != "single")},
+                   "biconnected": bool(args.biconnected and mode != "single"),
+                   "clique_bound": bool(args.clique_bound)},
         "nodes_per_s": res.nodes * args.steps / total,
         "cpu_baseline": {"value": value, "unit": "segments/s", "cores": cores, "kind": "oracle",
                          "sample": f"whole layout ({layout.n_seg} segments, "
@@ -277,6 +283,8 @@ def main():
     flags = (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE) if mode == "single" else 0
     if args.biconnected and mode != "single":
         flags |= mpld.MPLD_BICONNECTED
+    if args.clique_bound:
+        flags |= mpld.MPLD_CLIQUE_BOUND
     prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
     info = mpld.mpld_problem_info(prob)
     rule_flag = mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0
@@ -329,6 +337,7 @@ def main():
                    "segments": layout.n_seg, "polygons": layout.n_poly,
                    "k": layout.k, "node_budget": args.budget, "column_rule": args.column_rule,
                    "biconnected": bool(flags & mpld.MPLD_BICONNECTED),
+                   "clique_bound": bool(flags & mpld.MPLD_CLIQUE_BOUND),
                    "instances": info.n_components,
                    "max_instance": info.max_component,
                    "removed_segments": info.n_removed_segments,
@@ -436,6 +445,8 @@ def main():
             oflags |= oracle.COLUMN_BFS
         if flags & mpld.MPLD_BICONNECTED:
             oflags |= oracle.BICONNECTED
+        if flags & mpld.MPLD_CLIQUE_BOUND:
+            oflags |= oracle.CLIQUE_BOUND
         ref = oracle.decompose(layout, flags=oflags, budget=args.budget, nthreads=cores)
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": layout.n_seg / dt, "unit": "segments/s", "cores": cores,

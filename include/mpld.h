@@ -75,6 +75,17 @@ extern "C" {
                                     (MPLD_E_INVALID).  Instances are then blocks: a cut segment
                                     belongs to several, and mpld_component_results reports the
                                     first. */
+#define MPLD_CLIQUE_BOUND 32u    /* second bound mode: at build, each instance's (k+1)-cliques of
+                                    conflict edges are listed in lexicographic order of their
+                                    ascending member lists and taken greedily when they share no
+                                    edge with one taken before; the search then prunes when
+                                    path cost + cost_conflict * (uncovered columns with no active
+                                    row + taken cliques with no member assigned) reaches the
+                                    incumbent.  Admissible: an untouched clique must repeat a mask
+                                    on an edge between unassigned segments.  The first minimum-cost
+                                    leaf is unchanged; fewer nodes.  Read by mpld_build_matrix
+                                    (and mpld_server_submit); MPLD_E_TOO_LARGE above 65,535
+                                    cliques in one instance. */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
                                     the solve calls then return MPLD_E_STATE */
@@ -307,8 +318,8 @@ int mpld_server_create(const mpld_server_config *cfg, const mpld_params *search,
                        mpld_server **out);
 
 /* Queue a layout (copied; `graph` may be reused at once).  flags as mpld_params.flags for
- * mpld_build_matrix (MPLD_NO_SIMPLIFY, MPLD_SINGLE_INSTANCE, MPLD_BICONNECTED; other bits are
- * ignored).  Returns MPLD_OK and a ticket.  Input errors surface later as the ticket's result
+ * mpld_build_matrix (MPLD_NO_SIMPLIFY, MPLD_SINGLE_INSTANCE, MPLD_BICONNECTED,
+ * MPLD_CLIQUE_BOUND; other bits are ignored).  Returns MPLD_OK and a ticket.  Input errors surface later as the ticket's result
  * code. */
 int mpld_server_submit(mpld_server *s, const mpld_graph *graph, uint32_t flags, int64_t *ticket);
 

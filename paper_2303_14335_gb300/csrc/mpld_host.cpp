@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -212,6 +213,52 @@ void component_blocks(const std::vector<int32_t> &seg, const std::vector<int32_t
   for (int i = 0; i < n; ++i) loc[seg[i]] = -1;
 }
 
+// Cliques of the second bound mode (MPLD_CLIQUE_BOUND) of one instance:
+// every (k+1)-clique of its conflict graph, in lexicographic order of the
+// ascending member lists, is taken when it shares no edge with a clique
+// taken before.  lp / la: the instance's conflict adjacency, local ids,
+// ascending.  Returns the members of the taken cliques, k + 1 each.
+std::vector<uint16_t> greedy_cliques(int n, int K, const std::vector<int32_t> &lp,
+                                     const std::vector<int32_t> &la) {
+  std::vector<uint8_t> used(la.size(), 0);
+  auto slot = [&](int a, int b) -> int {
+    const auto first = la.begin() + lp[a], last = la.begin() + lp[a + 1];
+    const auto it = std::lower_bound(first, last, b);
+    return (it != last && *it == b) ? (int)(it - la.begin()) : -1;
+  };
+  std::vector<uint16_t> out;
+  int cur[9];
+  std::function<void(int)> extend = [&](int depth) {
+    if (depth == K) {
+      for (int i = 0; i < K; ++i)
+        for (int j = i + 1; j < K; ++j)
+          if (used[slot(cur[i], cur[j])]) return;
+      for (int i = 0; i < K; ++i)
+        for (int j = i + 1; j < K; ++j) {
+          used[slot(cur[i], cur[j])] = 1;
+          used[slot(cur[j], cur[i])] = 1;
+        }
+      for (int i = 0; i < K; ++i) out.push_back((uint16_t)cur[i]);
+      return;
+    }
+    const int last = cur[depth - 1];
+    for (int i = lp[last]; i < lp[last + 1]; ++i) {
+      const int w = la[i];
+      if (w <= last) continue;
+      bool ok = true;
+      for (int j = 0; j < depth - 1 && ok; ++j) ok = slot(cur[j], w) >= 0;
+      if (!ok) continue;
+      cur[depth] = w;
+      extend(depth + 1);
+    }
+  };
+  for (int v = 0; v < n; ++v) {
+    cur[0] = v;
+    extend(1);
+  }
+  return out;
+}
+
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
 
 std::mutex g_tune_mu;
@@ -397,15 +444,32 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     // ---- pack each instance: read-only block + descriptor
     p->ro_off.resize((size_t)C);
     p->footprint.resize((size_t)C);
+    p->inst_nq.assign((size_t)C, 0);
     p->inst_ne2.resize((size_t)C);
     p->h_desc.resize((size_t)C);
     std::vector<int32_t> ns2v((size_t)C), mask_off((size_t)C), maxdeg((size_t)C);
     uint64_t arena = 0, scratch = 0;
     std::vector<uint64_t> scratch_off((size_t)C);
+    const bool cliques = (p->flags & MPLD_CLIQUE_BOUND) != 0;
+    std::vector<std::vector<uint16_t>> inst_q((size_t)(cliques ? C : 0));
     for (int c = 0; c < C; ++c) {
       int ne2 = 0, ns2 = 0, mdc = 0, mds = 0;
       int64_t max_inc = 0;
       mark_instance(c);
+      if (cliques) {
+        // the instance's conflict adjacency in local ids (ascending, as the
+        // instance keeps the global order)
+        const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
+        std::vector<int32_t> lp((size_t)nc + 1, 0), la;
+        for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
+          const int s = p->comp_seg[t];
+          for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i)
+            if (stamp[p->cadj[i]] == c) la.push_back(lid[p->cadj[i]]);
+          lp[t - p->comp_ptr[c] + 1] = (int32_t)la.size();
+        }
+        inst_q[c] = greedy_cliques(nc, k + 1, lp, la);
+        if (inst_q[c].size() / (size_t)(k + 1) > 65535) { delete p; return MPLD_E_TOO_LARGE; }
+      }
       for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
         const int s = p->comp_seg[t];
         int dc = 0, ds = 0;
@@ -425,8 +489,9 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
         return MPLD_E_TOO_LARGE;
       }
       const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
-      const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2);
-      const uint32_t state_bytes = mpld::search_state_bytes(nc, ne2, k);
+      const int nq = cliques ? (int)(inst_q[c].size() / (size_t)(k + 1)) : 0;
+      const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2, nq * (k + 1));
+      const uint32_t state_bytes = mpld::search_state_bytes(nc, ne2, k, nq);
       p->inst_ne2[c] = ne2;
       ns2v[c] = ns2;
       maxdeg[c] = std::min(mdc, 0xFFFF) | (std::min(mds, 0x7FFF) << 16);
@@ -434,7 +499,8 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       arena += R.bytes;
       scratch_off[c] = scratch;
       scratch += state_bytes;
-      p->footprint[c] = mpld::search_footprint(nc, ne2, ns2, k);
+      p->footprint[c] = mpld::search_footprint(nc, ne2, ns2, k, nq);
+      p->inst_nq[c] = nq;
       mask_off[c] = p->comp_ptr[c];
     }
     p->arena_bytes = (size_t)arena;
@@ -442,8 +508,20 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     p->h_arena.assign((size_t)arena, 0);
     for (int c = 0; c < C; ++c) {
       const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
-      const mpld::RoLayout R = mpld::ro_layout(nc, p->inst_ne2[c], ns2v[c]);
+      const int nq = p->inst_nq[c];
+      const mpld::RoLayout R = mpld::ro_layout(nc, p->inst_ne2[c], ns2v[c], nq * (k + 1));
       uint8_t *blk = p->h_arena.data() + p->ro_off[c];
+      if (nq > 0) {
+        // each segment's cliques, in clique order
+        int32_t *qptr = (int32_t *)(blk + R.qptr);
+        uint16_t *qlist = (uint16_t *)(blk + R.qlist);
+        std::vector<int32_t> cnt((size_t)nc + 1, 0);
+        for (uint16_t m : inst_q[c]) cnt[m + 1]++;
+        for (int v = 0; v < nc; ++v) cnt[v + 1] += cnt[v];
+        for (int v = 0; v <= nc; ++v) qptr[v] = cnt[v];
+        for (int q = 0; q < nq; ++q)
+          for (int i = 0; i <= k; ++i) qlist[cnt[inst_q[c][q * (k + 1) + i]]++] = (uint16_t)q;
+      }
       int32_t *ptr = (int32_t *)(blk + R.ptr);   // {conflict, stitch} offset pairs
       uint16_t *cn = (uint16_t *)(blk + R.cnbr);
       uint16_t *sn = (uint16_t *)(blk + R.snbr);
@@ -510,8 +588,9 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       d.maxdeg = maxdeg[c];
       d.ne2 = p->inst_ne2[c];
       d.ns2 = ns2v[c];
-      d.ro_bytes = (int32_t)mpld::ro_layout(nc, d.ne2, d.ns2).bytes;
-      d.state_bytes = (int32_t)mpld::search_state_bytes(nc, d.ne2, k);
+      d.nq = p->inst_nq[c];
+      d.ro_bytes = (int32_t)mpld::ro_layout(nc, d.ne2, d.ns2, d.nq * (k + 1)).bytes;
+      d.state_bytes = (int32_t)mpld::search_state_bytes(nc, d.ne2, k, d.nq);
       d.k = k;
       d.cost_conflict = (int32_t)p->Cc;
       d.cost_stitch = (int32_t)p->Cs;

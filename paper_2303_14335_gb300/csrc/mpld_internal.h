@@ -32,12 +32,15 @@ MPLD_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 //   rank[n]   uint16  breadth-first rank of each segment over conflict and
 //                     stitch edges (roots ascending, neighbours ascending)
 //   order[n]  uint16  segment of each breadth-first rank
+//   qptr[n+1] int32   (nq > 0 only) each segment's range in qlist
+//   qlist[nq*(k+1)] uint16  the bound's cliques holding each segment
 // (rank / order serve the paper's column rule, Algorithm 1: a column with a
-// single row left, else the first uncovered column in BFS order of G.)
+// single row left, else the first uncovered column in BFS order of G; the
+// clique lists serve the second bound mode.)
 struct RoLayout {
-  uint32_t ptr, cnbr, snbr, rank, order, bytes;
+  uint32_t ptr, cnbr, snbr, rank, order, qptr, qlist, bytes;
 };
-MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
+MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
   RoLayout L;
   uint32_t o = 0;
   L.ptr = o; o += align16(8u * (uint32_t)(n + 1));
@@ -45,6 +48,8 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
   L.snbr = o; o += align16(2u * (uint32_t)ns2);
   L.rank = o; o += align16(2u * (uint32_t)n);
   L.order = o; o += align16(2u * (uint32_t)n);
+  L.qptr = o; o += nqe > 0 ? align16(4u * (uint32_t)(n + 1)) : 0u;
+  L.qlist = o; o += align16(2u * (uint32_t)nqe);
   L.bytes = o;
   return L;
 }
@@ -67,10 +72,13 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2) {
 //   x[n]        i8   current mask per segment (-1 = none)
 //   savf[ne2]   field of neighbour u before v's row cleared its bit (the
 //               undo record of the cover, one per adjacency entry of v)
+//   qcnt[nq]    u8 per clique of the second bound mode: members assigned
+//   qlev[n]     (nq > 0 only) per level, the cliques its segment's
+//               assignment took out of the untouched count
 struct StateLayout {
-  uint32_t lv, lvx, ccnt, scnt, rows, oldf, x, savf, bytes;
+  uint32_t lv, lvx, ccnt, scnt, rows, oldf, x, savf, qcnt, qlev, bytes;
 };
-MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
+MPLD_HD StateLayout state_layout(int n, int ne2, int k, int nq = 0) {
   const uint32_t fb = (uint32_t)field_bytes_for(k), mk = (uint32_t)mk_for(k), cw = mk / 4u;
   StateLayout L;
   uint32_t o = 0;
@@ -82,6 +90,8 @@ MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
   L.oldf = o; o += align16(fb * (uint32_t)n);
   L.x = o; o += align16((uint32_t)n);
   L.savf = o; o += align16(fb * (uint32_t)ne2);
+  L.qcnt = o; o += align16((uint32_t)nq);
+  L.qlev = o; o += nq > 0 ? align16(4u * (uint32_t)n) : 0u;
   L.bytes = o;
   return L;
 }
@@ -100,30 +110,39 @@ MPLD_HD StateLayout state_layout(int n, int ne2, int k) {
 //                     lost a row bit to the level's cover (bits 0-3), and
 //                     the lane's conflict (bits 4-7) and stitch (bits 8-11)
 //                     neighbour bits of the level's segment
+//   qptr[n+1]    u16  (nq > 0 only) clique ranges, copied from the block
+//   qlist[nq*(k+1)] u16  cliques holding each segment
+//   qcnt[nq]     u8   members of each clique assigned
 struct RegLayout {
-  uint32_t adj, deg, rec, sav, bytes;
+  uint32_t adj, deg, rec, sav, qptr, qlist, qcnt, bytes;
 };
 MPLD_HD bool reg_fits(int n, int k) { return n <= 32 * (4 / field_bytes_for(k)); }
-MPLD_HD RegLayout reg_layout(int n, int k) {
+MPLD_HD RegLayout reg_layout(int n, int k, int nq = 0) {
   const uint32_t rs = k <= 4 ? 32u : 48u;
+  const uint32_t nqe = (uint32_t)nq * (uint32_t)(k + 1);
   RegLayout L;
   uint32_t o = 0;
   L.adj = o; o += align16(32u * (uint32_t)n);
   L.deg = o; o += align16(4u * (uint32_t)n);
   L.rec = o; o += rs * (uint32_t)(n + 1);
   L.sav = o; o += 64u * (uint32_t)(n + 1);
+  L.qptr = o; o += nq > 0 ? align16(2u * (uint32_t)(n + 1)) : 0u;
+  L.qlist = o; o += align16(2u * nqe);
+  L.qcnt = o; o += align16((uint32_t)nq);
   L.bytes = o;
   return L;
 }
 
 // Global scratch an instance needs when its state does not fit a slot, and
-// its shared-memory footprint when it does.
-MPLD_HD uint32_t search_state_bytes(int n, int ne2, int k) {
-  return reg_fits(n, k) ? reg_layout(n, k).bytes : state_layout(n, ne2, k).bytes;
+// its shared-memory footprint when it does (nq: cliques of the second bound
+// mode, 0 without it).
+MPLD_HD uint32_t search_state_bytes(int n, int ne2, int k, int nq = 0) {
+  return reg_fits(n, k) ? reg_layout(n, k, nq).bytes : state_layout(n, ne2, k, nq).bytes;
 }
-MPLD_HD uint32_t search_footprint(int n, int ne2, int ns2, int k) {
-  return reg_fits(n, k) ? reg_layout(n, k).bytes
-                        : state_layout(n, ne2, k).bytes + ro_layout(n, ne2, ns2).bytes;
+MPLD_HD uint32_t search_footprint(int n, int ne2, int ns2, int k, int nq = 0) {
+  return reg_fits(n, k) ? reg_layout(n, k, nq).bytes
+                        : state_layout(n, ne2, k, nq).bytes +
+                              ro_layout(n, ne2, ns2, nq * (k + 1)).bytes;
 }
 
 // One search instance, as the kernel sees it (absolute device pointers so
@@ -136,7 +155,7 @@ struct __align__(16) InstDesc {
   int32_t n, maxdeg, ne2, ns2;   // maxdeg: largest conflict degree | largest stitch degree << 16
   int32_t ro_bytes, state_bytes;
   int32_t k, cost_conflict;
-  int32_t cost_stitch, pad0;
+  int32_t cost_stitch, nq;   // nq: cliques of the second bound mode (0: none)
   int64_t pad1;
 };
 

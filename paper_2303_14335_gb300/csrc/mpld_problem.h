@@ -41,6 +41,7 @@ struct mpld_problem {
   std::vector<int32_t> comp_ptr, comp_seg, comp_of;
   std::vector<int32_t> inst_attach;   // biconnected blocks: attach segment's index, -1 first
   std::vector<int32_t> inst_ne2;
+  std::vector<int32_t> inst_nq;       // cliques of the second bound mode per instance
   int max_component = 0;
   int64_t instance_segments = 0;
   // packed instances

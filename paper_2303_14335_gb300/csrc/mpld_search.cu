@@ -158,6 +158,11 @@ struct Search {
   const int2 *ptr;    // {conflict offset, stitch offset} per segment
   const uint16_t *cnbr, *snbr;
   const uint16_t *rank, *order;   // breadth-first rank / segment of each rank
+  const int32_t *qptr;            // second bound mode: each segment's cliques
+  const uint16_t *qlist;
+  uint8_t *qcnt;                  // members of each clique assigned
+  int32_t *qlev;                  // per level: cliques its assignment touched
+  int nq;
   int n, k;
   int Cc, Cs;
   uint32_t kmask;
@@ -262,6 +267,23 @@ struct Search {
       nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
       return room < m;
     };
+    int untouched = nq;   // cliques of the second bound mode with no member assigned
+    // member counts of v's cliques move (the caller keeps `untouched`)
+    auto clique_move = [&](int v, int dir) {
+      const int q0 = ro_ld<SM>(qptr + v), q1 = ro_ld<SM>(qptr + v + 1);
+      for (int i = q0 + lane; i < q1; i += 32) {
+        const int q = ro_ld<SM>(qlist + i);
+        qcnt[q] = (uint8_t)(qcnt[q] + dir);
+      }
+      __syncwarp();
+    };
+    auto untouched_after = [&](int v) -> int {
+      const int q0 = ro_ld<SM>(qptr + v), q1 = ro_ld<SM>(qptr + v + 1);
+      int left = untouched;
+      for (int i = q0 + lane; i - lane < q1; i += 32)
+        left -= __popc(__ballot_sync(FULL, i < q1 && qcnt[ro_ld<SM>(qlist + i)] == 0));
+      return left;
+    };
     bool enter = true;
     for (;;) {
       if (enter) {
@@ -326,7 +348,7 @@ struct Search {
           // the bound needs the number of uncovered columns with no active
           // row; under rule 0 there is one only when the minimum count is 0
           z = (rule != 0 || (key >> 16) == 0) ? __reduce_add_sync(FULL, z) : 0u;
-          if ((int64_t)g + (int64_t)Cc * z >= best) { enter = false; continue; }
+          if ((int64_t)g + (int64_t)Cc * (z + (uint32_t)untouched) >= best) { enter = false; continue; }
         }
         const int v = (rule == 0 || key < 0x10000u) ? (int)(key & 0xFFFFu)
                                                      : (int)ro_ld<SM>(order + (key & 0xFFFFu));
@@ -347,7 +369,11 @@ struct Search {
           keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
         }
         sort_keys<MK>(keys);
-        if (best < INF32 && g + (int32_t)(keys[0] >> 3) >= best) {
+        // each child's bound is at least its path cost plus cost_conflict
+        // times the cliques untouched once v is assigned
+        const int left = nq > 0 ? untouched_after(v) : 0;
+        const int32_t floor_c = Cc * left;
+        if (best < INF32 && g + (int32_t)(keys[0] >> 3) + floor_c >= best) {
           // rows are in ascending cost: every child is pruned on entry
           if (count_pruned(k)) { status = MPLD_BUDGET; break; }
           enter = false;
@@ -365,6 +391,11 @@ struct Search {
             if (i < k) lvx[level * MK + i] = (int32_t)(keys[i] >> 3);
         }
         cover_first(v, (int)(ord & 7u), cb, dc, sb, ds, lane);
+        if (nq > 0) {
+          if (lane == 0) qlev[level] = untouched - left;
+          clique_move(v, 1);
+          untouched = left;
+        }
         g += (int32_t)(keys[0] >> 3);
         ++level;
         continue;
@@ -380,14 +411,22 @@ struct Search {
       const int c_last = (int)((r0.z >> (4 * (nxt - 1))) & 7u);
       if (nxt >= k) {  // every row of this column tried
         restore(v, c_last, cb, dc, sb, ds, lane);
+        if (nq > 0) {
+          clique_move(v, -1);
+          untouched += qlev[level];
+        }
         continue;
       }
       const int c = (int)((r0.z >> (4 * nxt)) & 7u);
       g = (int32_t)r0.x + (nxt == 1 ? (int32_t)r1.z : nxt == 2 ? (int32_t)r1.w : lvx[level * MK + nxt]);
-      if (best < INF32 && g >= best) {
+      if (best < INF32 && g + Cc * untouched >= best) {
         // this row and the ones after it: children pruned on entry
         if (count_pruned(k - nxt)) { status = MPLD_BUDGET; break; }
         restore(v, c_last, cb, dc, sb, ds, lane);
+        if (nq > 0) {
+          clique_move(v, -1);
+          untouched += qlev[level];
+        }
         continue;
       }
       work32 += 5u * (uint32_t)(1 + dc);
@@ -450,11 +489,15 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   const int n = d.n, k = d.k;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
   const uint32_t kmask = (1u << k) - 1u;
-  const RegLayout R = reg_layout(n, k);
+  const int nq = d.nq;
+  const RegLayout R = reg_layout(n, k, nq);
   uint8_t *adj = base + R.adj;
   uint32_t *deg = (uint32_t *)(base + R.deg);
   uint32_t *rec = (uint32_t *)(base + R.rec);
   uint16_t *sav = (uint16_t *)(base + R.sav);
+  uint16_t *qptr = (uint16_t *)(base + R.qptr);
+  uint16_t *qlist = (uint16_t *)(base + R.qlist);
+  uint8_t *qcnt = base + R.qcnt;
 
   // adjacency bit matrix and degrees, from the read-only block (via L2)
   {
@@ -478,6 +521,16 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       }
       deg[v] = (uint32_t)(p1.x - p0.x) | ((uint32_t)(p1.y - p0.y) << 16);
     }
+  }
+  if (nq > 0) {
+    // the second bound mode's cliques: each segment's list, and per clique
+    // the number of members assigned
+    const RoLayout Q = ro_layout(n, d.ne2, d.ns2, nq * (k + 1));
+    const int32_t *gq = (const int32_t *)(d.ro + Q.qptr);
+    const uint16_t *gl = (const uint16_t *)(d.ro + Q.qlist);
+    for (int i = lane; i <= n; i += 32) qptr[i] = (uint16_t)__ldcg(gq + i);
+    for (int i = lane; i < nq * (k + 1); i += 32) qlist[i] = __ldcg(gl + i);
+    for (int i = lane; i < nq; i += 32) qcnt[i] = 0;
   }
   // every row active, every primary column uncovered, no mask assigned
   uint32_t w = 0u, xw = 0xFFFFFFFFu, rk = 0u;
@@ -506,6 +559,14 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   const int64_t budget = a.budget, time_limit_ns = a.time_limit_ns;
   const uint64_t t0 = globaltimer();
   int64_t next_check = 1024;
+  int untouched = nq;   // cliques with no member assigned
+  // v assigned (dir = +1) or released (-1): the member counts of its
+  // cliques move (the caller keeps `untouched`)
+  auto clique_move = [&](int v, int dir) {
+    const int q0 = qptr[v], q1 = qptr[v + 1];
+    for (int i = q0 + lane; i < q1; i += 32) qcnt[qlist[i]] = (uint8_t)(qcnt[qlist[i]] + dir);
+    __syncwarp();
+  };
   // m child nodes that are pruned on entry (their path cost alone reaches
   // the incumbent, so neither a cover nor a column scan is needed to know
   // it): counted as the recursive search would, stopping where the node
@@ -525,6 +586,14 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       cc[m] += hit ? dcw : 0u;
       sc[m] += hit ? dsw : 0u;
     }
+  };
+  // untouched cliques once v is assigned (v's untouched cliques drop out)
+  auto untouched_after = [&](int v) -> int {
+    const int q0 = qptr[v], q1 = qptr[v + 1];
+    int left = untouched;
+    for (int i = q0 + lane; i - lane < q1; i += 32)
+      left -= __popc(__ballot_sync(FULL, i < q1 && qcnt[qlist[i]] == 0));
+    return left;
   };
   bool enter = true;
   for (;;) {
@@ -573,7 +642,7 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
         // uncovered columns with no active row; under rule 0 there is one
         // only when the minimum count is 0
         z = (RULE != 0 || key < 0x100u) ? __reduce_add_sync(FULL, z) : 0u;
-        if ((int64_t)g + (int64_t)Cc * z >= best) { enter = false; continue; }
+        if ((int64_t)g + (int64_t)Cc * (z + (uint32_t)untouched) >= best) { enter = false; continue; }
       }
       const int v = (int)(key & 0xFFu);
       const int jv = v % P, src = v / P;
@@ -609,7 +678,11 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
         if (c < k && ncf == 0) oldf |= 1u << c;
       }
       sort_keys<MK>(keys);
-      if (best < INF32 && g + (int32_t)(keys[0] >> 3) >= best) {
+      // every child's bound is at least its path cost plus cost_conflict
+      // times the cliques still untouched once v is assigned
+      const int left = nq > 0 ? untouched_after(v) : 0;
+      const int32_t floor_c = Cc * left;
+      if (best < INF32 && g + (int32_t)(keys[0] >> 3) + floor_c >= best) {
         // rows are in ascending cost: every child is pruned on entry
         if (count_pruned(k)) { status = MPLD_BUDGET; break; }
         enter = false;
@@ -623,10 +696,11 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
         break;
       }
       // level record: {v | next row << 8 | v's field << 12, path cost,
-      // degrees, -, sorted row keys}
+      // degrees, cliques v touched, sorted row keys}
       if (lane == 0) {
         uint4 *r4 = (uint4 *)(rec + level * RS);
-        r4[0] = make_uint4((uint32_t)v | (1u << 8) | (oldf << 12), (uint32_t)g, dd, 0u);
+        r4[0] = make_uint4((uint32_t)v | (1u << 8) | (oldf << 12), (uint32_t)g, dd,
+                           (uint32_t)(untouched - left));
         r4[1] = make_uint4(keys[0], MK > 1 ? keys[MK > 1 ? 1 : 0] : 0u,
                            MK > 2 ? keys[MK > 2 ? 2 : 0] : 0u, MK > 3 ? keys[MK > 3 ? 3 : 0] : 0u);
         if constexpr (MK == 8) r4[2] = make_uint4(keys[4 % MK], keys[5 % MK], keys[6 % MK], keys[7 % MK]);
@@ -641,6 +715,10 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       if (lane == src) {
         w &= ~(FMASK << (FB * jv));
         xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+      }
+      if (nq > 0) {
+        clique_move(v, 1);
+        untouched = left;
       }
       g += (int32_t)(keys[0] >> 3);
       ++level;
@@ -677,7 +755,8 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
     w |= spread_bits<FB>(sv & 0xFu) << cl;
     move_counts(cl, cb8, sb8, false);
     bool last = nxt >= k;
-    if (!last && best < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= best) {
+    if (!last && best < INF32 &&
+        (int32_t)r0.y + (int32_t)(knext >> 3) + Cc * untouched >= best) {
       // this row and the ones after it cost at least as much: their nodes
       // are pruned on entry, so count them and undo the column
       if (count_pruned(k - nxt)) { status = MPLD_BUDGET; break; }
@@ -688,6 +767,10 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       if (lane == src) {
         w |= (r0.x >> 12) << (FB * jv);
         xw |= 0xFFu << (8 * jv);
+      }
+      if (nq > 0) {
+        clique_move(v, -1);
+        untouched += (int)r0.w;   // the cliques v's assignment had touched
       }
       continue;
     }
@@ -719,8 +802,8 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
                                        const LaunchArgs &a, int lane) {
   using S = Search<FT, MK, SM>;
   const int n = d.n;
-  const StateLayout L = state_layout(n, d.ne2, d.k);
-  const RoLayout R = ro_layout(n, d.ne2, d.ns2);
+  const StateLayout L = state_layout(n, d.ne2, d.k, d.nq);
+  const RoLayout R = ro_layout(n, d.ne2, d.ns2, d.nq * (d.k + 1));
   S s;
   s.lv = (uint4 *)(base + L.lv);
   s.lvx = (int32_t *)(base + L.lvx);
@@ -735,6 +818,12 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   s.snbr = (const uint16_t *)(ro + R.snbr);
   s.rank = (const uint16_t *)(ro + R.rank);
   s.order = (const uint16_t *)(ro + R.order);
+  s.qptr = (const int32_t *)(ro + R.qptr);
+  s.qlist = (const uint16_t *)(ro + R.qlist);
+  s.qcnt = base + L.qcnt;
+  s.qlev = (int32_t *)(base + L.qlev);
+  s.nq = d.nq;
+  for (int i = lane; i < d.nq; i += 32) s.qcnt[i] = 0;
   s.rule = a.rule;
   s.n = n;
   s.k = d.k;
@@ -771,7 +860,7 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
   if (reg_fits(d.n, d.k)) {
     // one call site per memory space, so that each copy knows where its
     // state lives; the column rule is a template argument
-    if (slot_bytes > 0 && (int)reg_layout(d.n, d.k).bytes <= slot_bytes) {
+    if (slot_bytes > 0 && (int)reg_layout(d.n, d.k, d.nq).bytes <= slot_bytes) {
       if (a.rule) reg_search<FT, MK, 1>(d, g_smem + slot_off, a, lane);
       else reg_search<FT, MK, 0>(d, g_smem + slot_off, a, lane);
     } else {
@@ -780,16 +869,17 @@ __device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_of
     }
     return true;
   }
-  const StateLayout L = state_layout(d.n, d.ne2, d.k);
-  const RoLayout R = ro_layout(d.n, d.ne2, d.ns2);
+  const StateLayout L = state_layout(d.n, d.ne2, d.k, d.nq);
+  const RoLayout R = ro_layout(d.n, d.ne2, d.ns2, d.nq * (d.k + 1));
   if (slot_bytes <= 0 || (int)(L.bytes + R.bytes) > slot_bytes) {
     run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
     return true;
   }
   uint8_t *slot = g_smem + slot_off;
   uint8_t *dst = slot + L.bytes;
-  // the breadth-first tables at the end of the block are read under rule 1 only
-  const uint32_t ro_copy = a.rule ? R.bytes : R.rank;
+  // the breadth-first tables and clique lists at the end of the block are
+  // read under rule 1 / the clique bound only
+  const uint32_t ro_copy = (a.rule || d.nq > 0) ? R.bytes : R.rank;
   if (ro_copy >= TMA_MIN_BYTES) {
     // one bulk copy of the read-only block into shared memory
     __syncwarp();
@@ -1013,7 +1103,7 @@ __global__ void __launch_bounds__(32, 1)
   d.k = inst.k;
   d.cost_conflict = inst.cost_conflict;
   d.cost_stitch = inst.cost_stitch;
-  d.pad0 = 0;
+  d.nq = 0;
   d.pad1 = 0;
   LaunchArgs a;
   a.desc = nullptr;

@@ -260,6 +260,56 @@ def test_blocks_with_column_rule(stream):
     assert_same(gpu_run(L, flags=BIC, budget=2000, stream=stream.cuda_stream, search_flags=BFS), ref, L)
 
 
+# ------------------------------------------------ second bound mode (cliques)
+
+CQ = mpld.MPLD_CLIQUE_BOUND
+
+
+@pytest.mark.parametrize("n,k,seed,p", small_cases()[2::3])
+def test_clique_bound_small_graphs(n, k, seed, p, stream):
+    L = synth.random_graph(n, k, seed=seed, p_edge=min(0.9, p + 0.2), n_stitch=n // 4,
+                           identity_polygons=False)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | oracle.CLIQUE_BOUND,
+                           budget=200000)
+    for path in ("batch", "plain"):
+        assert_same(gpu_run(L, flags=SINGLE | CQ, budget=200000, path=path, stream=stream.cuda_stream),
+                    ref, L)
+
+
+@pytest.mark.parametrize("budget", [1, 40, 333, 5000])
+def test_clique_bound_budgets(budget, stream):
+    L = synth.unit_disk_layout(40, 3, seed=91, mean_deg=6.0, p_stitch=0.25)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | oracle.CLIQUE_BOUND,
+                           budget=budget)
+    assert_same(gpu_run(L, flags=SINGLE | CQ, budget=budget, stream=stream.cuda_stream), ref, L)
+
+
+@pytest.mark.parametrize("k", [3, 4, 8])
+def test_clique_bound_large_instance(k, stream):
+    # instances above 32 field words take the shared-memory search
+    L = synth.unit_disk_layout(300, k, seed=5, mean_deg=2.0 * k)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | oracle.CLIQUE_BOUND,
+                           budget=20000)
+    assert ref.max_component > 128
+    assert_same(gpu_run(L, flags=SINGLE | CQ, budget=20000, stream=stream.cuda_stream), ref, L)
+
+
+@pytest.mark.parametrize("name", ["k3_n200k_p02_batched", "k4_n100k_p03_batched"])
+def test_clique_bound_batched_workloads(name, stream):
+    L, mode = synth.workload(name)
+    ref = oracle.decompose(L, flags=oracle.CLIQUE_BOUND, budget=3000, nthreads=NTHREADS)
+    assert_same(gpu_run(L, flags=CQ, budget=3000, stream=stream.cuda_stream), ref, L)
+
+
+def test_clique_bound_with_blocks_and_column_rule(stream):
+    L = synth.unit_disk_layout(6000, 3, seed=23, mean_deg=5.0, p_stitch=0.2)
+    for fl, ofl, sf in ((CQ | BIC, oracle.CLIQUE_BOUND | oracle.BICONNECTED, 0),
+                        (CQ, oracle.CLIQUE_BOUND | oracle.COLUMN_BFS, BFS)):
+        ref = oracle.decompose(L, flags=ofl, budget=2000, nthreads=NTHREADS)
+        assert_same(gpu_run(L, flags=fl, budget=2000, stream=stream.cuda_stream, search_flags=sf),
+                    ref, L)
+
+
 # ---------------------------------------------------------------- launch forms
 
 def test_results_independent_of_launch_shape(stream):
