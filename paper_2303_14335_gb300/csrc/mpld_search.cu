@@ -477,7 +477,7 @@ __device__ __forceinline__ uint32_t pick_bytes(uint32_t a, uint32_t b, uint32_t 
   return __byte_perm(__byte_perm(a, b, sel), __byte_perm(c, d, sel), 0x5410u);
 }
 
-template <typename FT, int MK, int RULE>
+template <typename FT, int MK, int RULE, bool CQ>
 __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
                                            int lane) {
   constexpr uint32_t FB = 8 * sizeof(FT);
@@ -489,7 +489,7 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   const int n = d.n, k = d.k;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
   const uint32_t kmask = (1u << k) - 1u;
-  const int nq = d.nq;
+  const int nq = CQ ? d.nq : 0;   // CQ: instances built with the clique bound
   const RegLayout R = reg_layout(n, k, nq);
   uint8_t *adj = base + R.adj;
   uint32_t *deg = (uint32_t *)(base + R.deg);
@@ -854,18 +854,25 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
 }
 
 template <typename FT, int MK>
-__device__ __forceinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, int slot_bytes,
+__device__ __noinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, int slot_bytes,
                                              uint64_t *bar, uint32_t &phase, const LaunchArgs &a,
                                              int lane) {
   if (reg_fits(d.n, d.k)) {
     // one call site per memory space, so that each copy knows where its
-    // state lives; the column rule is a template argument
+    // state lives; the column rule and the clique bound are template
+    // arguments of the shared-memory copies
     if (slot_bytes > 0 && (int)reg_layout(d.n, d.k, d.nq).bytes <= slot_bytes) {
-      if (a.rule) reg_search<FT, MK, 1>(d, g_smem + slot_off, a, lane);
-      else reg_search<FT, MK, 0>(d, g_smem + slot_off, a, lane);
+      uint8_t *slot = g_smem + slot_off;
+      if (d.nq > 0) {
+        if (a.rule) reg_search<FT, MK, 1, true>(d, slot, a, lane);
+        else reg_search<FT, MK, 0, true>(d, slot, a, lane);
+      } else {
+        if (a.rule) reg_search<FT, MK, 1, false>(d, slot, a, lane);
+        else reg_search<FT, MK, 0, false>(d, slot, a, lane);
+      }
     } else {
-      if (a.rule) reg_search<FT, MK, 1>(d, d.scratch, a, lane);
-      else reg_search<FT, MK, 0>(d, d.scratch, a, lane);
+      if (a.rule) reg_search<FT, MK, 1, true>(d, d.scratch, a, lane);
+      else reg_search<FT, MK, 0, true>(d, d.scratch, a, lane);
     }
     return true;
   }
