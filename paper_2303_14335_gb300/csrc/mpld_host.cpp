@@ -15,6 +15,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
+#include <deque>
+#include <condition_variable>
+#include <thread>
+#include <atomic>
 #include <functional>
 #include <chrono>
 #include <cstdio>
@@ -66,22 +71,32 @@ void unite_min(std::vector<int32_t> &parent, int a, int b) {
 }
 
 // (min,max)-normalised, sorted, unique edges; returns false on a bad edge.
+// The larger endpoints are bucketed by the smaller one (a counting sort),
+// then each (short) bucket is sorted and deduplicated.
 bool normalise(int n, int m, const int32_t *u, const int32_t *v, std::vector<int32_t> &ou,
                std::vector<int32_t> &ov) {
-  std::vector<int64_t> keys;
-  keys.reserve((size_t)m);
+  std::vector<int32_t> start((size_t)n + 1, 0);
   for (int e = 0; e < m; ++e) {
     const int a = u[e], b = v[e];
     if (a < 0 || b < 0 || a >= n || b >= n || a == b) return false;
-    keys.push_back((int64_t)std::min(a, b) * n + std::max(a, b));
+    start[std::min(a, b) + 1]++;
   }
-  std::sort(keys.begin(), keys.end());
-  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-  ou.resize(keys.size());
-  ov.resize(keys.size());
-  for (size_t e = 0; e < keys.size(); ++e) {
-    ou[e] = (int32_t)(keys[e] / n);
-    ov[e] = (int32_t)(keys[e] % n);
+  for (int i = 0; i < n; ++i) start[i + 1] += start[i];
+  std::vector<int32_t> hi((size_t)m), fill(start.begin(), start.end() - 1);
+  for (int e = 0; e < m; ++e) hi[fill[std::min(u[e], v[e])]++] = std::max(u[e], v[e]);
+  ou.clear();
+  ov.clear();
+  ou.reserve((size_t)m);
+  ov.reserve((size_t)m);
+  for (int a = 0; a < n; ++a) {
+    const auto first = hi.begin() + start[a], last = hi.begin() + start[a + 1];
+    if (first == last) continue;
+    std::sort(first, last);
+    for (auto it = first; it != last; ++it)
+      if (it == first || *it != *(it - 1)) {
+        ou.push_back(a);
+        ov.push_back(*it);
+      }
   }
   return true;
 }
@@ -259,6 +274,106 @@ std::vector<uint16_t> greedy_cliques(int n, int K, const std::vector<int32_t> &l
   return out;
 }
 
+// Host worker pool for the build and the result counting: up to 15 threads
+// started on first use and kept for the life of the process.  A parallel
+// loop puts helper tasks on the queue and works through its chunks on the
+// calling thread as well; it returns when every chunk is done, not when
+// every helper ran (a helper that starts late finds no chunk left and only
+// touches the loop's shared, reference-counted state).
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool pool;
+    return pool;
+  }
+  int helpers() const { return (int)th_.size(); }
+  void post(std::function<void()> task) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      q_.push_back(std::move(task));
+    }
+    cv_.notify_one();
+  }
+
+ private:
+  HostPool() {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int n = std::min(hw, 16) - 1;
+    for (int i = 0; i < n; ++i) th_.emplace_back([this] { loop(); });
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto &t : th_) t.join();
+  }
+  void loop() {
+    for (;;) {
+      std::function<void()> task;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || !q_.empty(); });
+        if (stop_ && q_.empty()) return;
+        task = std::move(q_.front());
+        q_.pop_front();
+      }
+      task();
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::deque<std::function<void()>> q_;
+  std::vector<std::thread> th_;
+  bool stop_ = false;
+};
+
+// f(i) for i in [0, count), in chunks of `grain`, on the calling thread and
+// the host pool.  An exception in f (out of memory) is rethrown as
+// std::bad_alloc once every chunk has finished.
+template <typename F>
+void parallel_for(int count, int grain, F f) {
+  const int chunks = (count + grain - 1) / grain;
+  HostPool &pool = HostPool::get();
+  const int nh = std::min(pool.helpers(), chunks - 1);
+  if (nh <= 0) {
+    for (int i = 0; i < count; ++i) f(i);
+    return;
+  }
+  struct State {
+    std::atomic<int> next{0}, done{0};
+    std::atomic<bool> failed{false};
+    std::mutex mu;
+    std::condition_variable cv;
+  };
+  auto st = std::make_shared<State>();
+  F *fp = &f;
+  auto work = [st, fp, count, grain, chunks] {
+    for (;;) {
+      const int q = st->next.fetch_add(1);
+      if (q >= chunks) return;
+      try {
+        if (!st->failed.load())
+          for (int i = q * grain, e = std::min(count, (q + 1) * grain); i < e; ++i) (*fp)(i);
+      } catch (...) {
+        st->failed = true;
+      }
+      if (st->done.fetch_add(1) + 1 == chunks) {
+        std::lock_guard<std::mutex> lk(st->mu);
+        st->cv.notify_all();
+      }
+    }
+  };
+  for (int t = 0; t < nh; ++t) pool.post(work);
+  work();
+  {
+    std::unique_lock<std::mutex> lk(st->mu);
+    st->cv.wait(lk, [&] { return st->done.load() == chunks; });
+  }
+  if (st->failed) throw std::bad_alloc();
+}
+
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
 
 std::mutex g_tune_mu;
@@ -344,27 +459,41 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     // ---- simplification: FIFO peel of units with < k external conflict edges
     std::vector<uint8_t> removed((size_t)n, 0);
     if (!(p->flags & MPLD_NO_SIMPLIFY)) {
-      std::vector<int32_t> udeg((size_t)n, 0);
-      std::vector<uint8_t> selfc((size_t)n, 0), queued((size_t)n, 0);
-      for (size_t e = 0; e < p->cu.size(); ++e) {
-        const int a = p->unit_of[p->cu[e]], b = p->unit_of[p->cv[e]];
-        if (a == b) selfc[a] = 1;
-        else { udeg[a]++; udeg[b]++; }
+      // per unit: external conflict degree, and a bit saying it may still
+      // join the queue (not queued yet, no conflict edge inside)
+      constexpr int32_t CAN = 1 << 30, DEG = CAN - 1;
+      // the conflict adjacency with each neighbour replaced by its unit
+      std::vector<int32_t> uadj(p->cadj.size());
+      parallel_for((int)p->cadj.size(), 1 << 16, [&](int i) { uadj[i] = p->unit_of[p->cadj[i]]; });
+      std::vector<int32_t> st((size_t)n, CAN);
+      for (int s = 0; s < n; ++s) {
+        const int a = p->unit_of[s];
+        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
+          if (uadj[i] == a) st[a] &= ~CAN;   // a conflict edge inside the unit
+          else st[a]++;
+        }
       }
-      std::vector<int32_t> queue;
+      std::vector<int32_t> &queue = p->removed_order;
       queue.reserve((size_t)n);
       for (int u = 0; u < n; ++u)
-        if (p->unit_of[u] == u && !selfc[u] && udeg[u] < k) { queue.push_back(u); queued[u] = 1; }
+        if (p->unit_of[u] == u && (st[u] & CAN) && (st[u] & DEG) < k) {
+          queue.push_back(u);
+          st[u] &= ~CAN;
+        }
+      // the queue is the removal order; a removed unit's degree is never
+      // read again, so its neighbours may still decrement it
       for (size_t h = 0; h < queue.size(); ++h) {
         const int u = queue[h];
         removed[u] = 1;
-        p->removed_order.push_back(u);
         for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) {
           const int s = p->useg[t];
           for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
-            const int w = p->unit_of[p->cadj[i]];
-            if (w == u || removed[w]) continue;
-            if (--udeg[w] < k && !queued[w] && !selfc[w]) { queue.push_back(w); queued[w] = 1; }
+            const int w = uadj[i];
+            const int32_t x = --st[w];
+            if ((x & CAN) && (x & DEG) < k) {
+              queue.push_back(w);
+              st[w] = x & ~CAN;
+            }
           }
         }
       }
@@ -431,74 +560,74 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       if (sz > MPLD_MAX_INSTANCE_SEGMENTS) { delete p; return MPLD_E_TOO_LARGE; }
     }
     p->instance_segments = p->comp_ptr[C];
-    // membership of the instance being packed: a segment may sit in several
-    // blocks, so instance c marks its own segments and their local ids
-    std::vector<int32_t> stamp((size_t)n, -1), lid((size_t)n, -1);
-    auto mark_instance = [&](int c) {
-      for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
-        stamp[p->comp_seg[t]] = c;
-        lid[p->comp_seg[t]] = t - p->comp_ptr[c];
-      }
+    // ---- pack each instance: read-only block + descriptor.  Instances are
+    // packed in parallel; a segment's local id in an instance is found by
+    // binary search in the instance's ascending segment list (a segment may
+    // sit in several blocks).
+    auto local_of = [&](int c, int g) -> int {
+      const int32_t *first = p->comp_seg.data() + p->comp_ptr[c];
+      const int32_t *last = p->comp_seg.data() + p->comp_ptr[c + 1];
+      const int32_t *it = std::lower_bound(first, last, g);
+      return (it != last && *it == g) ? (int)(it - first) : -1;
     };
-
-    // ---- pack each instance: read-only block + descriptor
     p->ro_off.resize((size_t)C);
     p->footprint.resize((size_t)C);
     p->inst_nq.assign((size_t)C, 0);
     p->inst_ne2.resize((size_t)C);
     p->h_desc.resize((size_t)C);
     std::vector<int32_t> ns2v((size_t)C), mask_off((size_t)C), maxdeg((size_t)C);
+    std::vector<int64_t> maxinc((size_t)C);
     uint64_t arena = 0, scratch = 0;
     std::vector<uint64_t> scratch_off((size_t)C);
     const bool cliques = (p->flags & MPLD_CLIQUE_BOUND) != 0;
     std::vector<std::vector<uint16_t>> inst_q((size_t)(cliques ? C : 0));
-    for (int c = 0; c < C; ++c) {
+    // pass 1: sizes, degrees, cliques
+    parallel_for(C, 64, [&](int c) {
+      const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
       int ne2 = 0, ns2 = 0, mdc = 0, mds = 0;
       int64_t max_inc = 0;
-      mark_instance(c);
-      if (cliques) {
-        // the instance's conflict adjacency in local ids (ascending, as the
-        // instance keeps the global order)
-        const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
-        std::vector<int32_t> lp((size_t)nc + 1, 0), la;
-        for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
-          const int s = p->comp_seg[t];
-          for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i)
-            if (stamp[p->cadj[i]] == c) la.push_back(lid[p->cadj[i]]);
-          lp[t - p->comp_ptr[c] + 1] = (int32_t)la.size();
-        }
-        inst_q[c] = greedy_cliques(nc, k + 1, lp, la);
-        if (inst_q[c].size() / (size_t)(k + 1) > 65535) { delete p; return MPLD_E_TOO_LARGE; }
-      }
-      for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) {
+      std::vector<int32_t> lp, la;
+      if (cliques) lp.assign((size_t)nc + 1, 0);
+      for (int t = a; t < b; ++t) {
         const int s = p->comp_seg[t];
         int dc = 0, ds = 0;
-        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) dc += stamp[p->cadj[i]] == c;
-        for (int i = sptr[s]; i < sptr[s + 1]; ++i) ds += stamp[sadj[i]] == c;
+        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
+          const int l = local_of(c, p->cadj[i]);
+          if (l < 0) continue;
+          ++dc;
+          if (cliques) la.push_back(l);
+        }
+        for (int i = sptr[s]; i < sptr[s + 1]; ++i) ds += local_of(c, sadj[i]) >= 0;
+        if (cliques) lp[t - a + 1] = (int32_t)la.size();
         ne2 += dc;
         ns2 += ds;
         mdc = std::max(mdc, dc);
         mds = std::max(mds, ds);
         max_inc = std::max(max_inc, p->Cc * dc + p->Cs * ds);
       }
-      // the kernel orders a segment's rows by 32-bit keys (added cost << 3 |
-      // mask) and keeps path costs in 32 bits
-      if (max_inc >= (int64_t)1 << 28 ||
-          p->Cc * (ne2 / 2) + p->Cs * (ns2 / 2) >= ((int64_t)1 << 31) - 1) {
-        delete p;
-        return MPLD_E_TOO_LARGE;
-      }
-      const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
-      const int nq = cliques ? (int)(inst_q[c].size() / (size_t)(k + 1)) : 0;
-      const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2, nq * (k + 1));
-      const uint32_t state_bytes = mpld::search_state_bytes(nc, ne2, k, nq);
+      if (cliques) inst_q[c] = greedy_cliques(nc, k + 1, lp, la);
       p->inst_ne2[c] = ne2;
       ns2v[c] = ns2;
       maxdeg[c] = std::min(mdc, 0xFFFF) | (std::min(mds, 0x7FFF) << 16);
+      maxinc[c] = max_inc;
+    });
+    for (int c = 0; c < C; ++c) {
+      const int nc = p->comp_ptr[c + 1] - p->comp_ptr[c];
+      const int ne2 = p->inst_ne2[c], ns2 = ns2v[c];
+      // the kernel orders a segment's rows by 32-bit keys (added cost << 3 |
+      // mask) and keeps path costs in 32 bits
+      if (maxinc[c] >= (int64_t)1 << 28 ||
+          p->Cc * (ne2 / 2) + p->Cs * (ns2 / 2) >= ((int64_t)1 << 31) - 1 ||
+          (cliques && inst_q[c].size() / (size_t)(k + 1) > 65535)) {
+        delete p;
+        return MPLD_E_TOO_LARGE;
+      }
+      const int nq = cliques ? (int)(inst_q[c].size() / (size_t)(k + 1)) : 0;
+      const mpld::RoLayout R = mpld::ro_layout(nc, ne2, ns2, nq * (k + 1));
       p->ro_off[c] = arena;
       arena += R.bytes;
       scratch_off[c] = scratch;
-      scratch += state_bytes;
+      scratch += mpld::search_state_bytes(nc, ne2, k, nq);
       p->footprint[c] = mpld::search_footprint(nc, ne2, ns2, k, nq);
       p->inst_nq[c] = nq;
       mask_off[c] = p->comp_ptr[c];
@@ -506,7 +635,8 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     p->arena_bytes = (size_t)arena;
     p->scratch_bytes = (size_t)scratch;
     p->h_arena.assign((size_t)arena, 0);
-    for (int c = 0; c < C; ++c) {
+    // pass 2: the read-only blocks
+    parallel_for(C, 64, [&](int c) {
       const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
       const int nq = p->inst_nq[c];
       const mpld::RoLayout R = mpld::ro_layout(nc, p->inst_ne2[c], ns2v[c], nq * (k + 1));
@@ -526,15 +656,18 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       uint16_t *cn = (uint16_t *)(blk + R.cnbr);
       uint16_t *sn = (uint16_t *)(blk + R.snbr);
       int ci = 0, si = 0;
-      mark_instance(c);
       for (int t = a; t < b; ++t) {
         const int s = p->comp_seg[t];
         ptr[2 * (t - a)] = ci;
         ptr[2 * (t - a) + 1] = si;
-        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i)
-          if (stamp[p->cadj[i]] == c) cn[ci++] = (uint16_t)lid[p->cadj[i]];
-        for (int i = sptr[s]; i < sptr[s + 1]; ++i)
-          if (stamp[sadj[i]] == c) sn[si++] = (uint16_t)lid[sadj[i]];
+        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
+          const int l = local_of(c, p->cadj[i]);
+          if (l >= 0) cn[ci++] = (uint16_t)l;
+        }
+        for (int i = sptr[s]; i < sptr[s + 1]; ++i) {
+          const int l = local_of(c, sadj[i]);
+          if (l >= 0) sn[si++] = (uint16_t)l;
+        }
       }
       ptr[2 * nc] = ci;
       ptr[2 * nc + 1] = si;
@@ -570,7 +703,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
           }
         }
       }
-    }
+    });
     // largest first (ties: lower instance id first)
     p->h_order.resize((size_t)C);
     std::iota(p->h_order.begin(), p->h_order.end(), 0);
@@ -848,9 +981,20 @@ int mpld_internal_finish(mpld_problem *p, const InstResult *hres, const int8_t *
     if (c == p->k) return MPLD_E_STATE;
     for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) m[p->useg[t]] = (int8_t)c;
   }
-  int64_t nconf = 0, nst = 0;
-  for (size_t e = 0; e < p->cu.size(); ++e) nconf += m[p->cu[e]] == m[p->cv[e]];
-  for (size_t e = 0; e < p->su.size(); ++e) nst += m[p->su[e]] != m[p->sv[e]];
+  // monochromatic conflict edges and cut stitch edges, counted in chunks
+  std::atomic<int64_t> nconf_a{0}, nst_a{0};
+  const int64_t ne = (int64_t)p->cu.size(), ns = (int64_t)p->su.size();
+  constexpr int64_t CHUNK = 1 << 15;
+  const int nchunks = (int)((ne + ns + CHUNK - 1) / CHUNK);
+  parallel_for(nchunks, 1, [&](int q) {
+    int64_t a = 0, b = 0;
+    for (int64_t e = (int64_t)q * CHUNK, end = std::min<int64_t>(e + CHUNK, ne + ns); e < end; ++e)
+      if (e < ne) a += m[p->cu[e]] == m[p->cv[e]];
+      else b += m[p->su[e - ne]] != m[p->sv[e - ne]];
+    nconf_a += a;
+    nst_a += b;
+  });
+  const int64_t nconf = nconf_a.load(), nst = nst_a.load();
   const int64_t cost = p->Cc * nconf + p->Cs * nst;
   if (cost != csum) return MPLD_E_STATE;  // removed units must cost nothing
   if (mask_out && p->n_seg) std::memcpy(mask_out, m.data(), (size_t)p->n_seg);
