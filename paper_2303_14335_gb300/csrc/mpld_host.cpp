@@ -424,14 +424,22 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
   p->Cs = g->cost_stitch;
   p->flags = params ? params->flags : 0u;
   try {
-    if (!normalise(n, g->n_conf, g->conf_u, g->conf_v, p->cu, p->cv) ||
-        !normalise(n, g->n_stitch, g->st_u, g->st_v, p->su, p->sv)) {
+    // conflict and stitch edges are normalised and put in CSR form side by side
+    std::vector<int32_t> sptr, sadj;
+    bool ok[2] = {true, true};
+    parallel_for(2, 1, [&](int which) {
+      if (which == 0) {
+        ok[0] = normalise(n, g->n_conf, g->conf_u, g->conf_v, p->cu, p->cv);
+        if (ok[0]) csr(n, p->cu, p->cv, p->cptr, p->cadj);
+      } else {
+        ok[1] = normalise(n, g->n_stitch, g->st_u, g->st_v, p->su, p->sv);
+        if (ok[1]) csr(n, p->su, p->sv, sptr, sadj);
+      }
+    });
+    if (!ok[0] || !ok[1]) {
       delete p;
       return MPLD_E_INVALID;
     }
-    std::vector<int32_t> sptr, sadj;
-    csr(n, p->cu, p->cv, p->cptr, p->cadj);
-    csr(n, p->su, p->sv, sptr, sadj);
 
     // ---- units: polygons merged along stitch edges, id = lowest segment
     std::vector<int32_t> parent((size_t)n);

@@ -485,7 +485,7 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
   constexpr int P = 4 / (int)sizeof(FT);
   constexpr int RS = MK <= 4 ? 8 : 12;   // words per level record
-  constexpr int NC = MK <= 4 ? 4 : 8;    // count registers per kind
+  constexpr int NC = MK;                 // count registers per kind (one per mask)
   const int n = d.n, k = d.k;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
   const uint32_t kmask = (1u << k) - 1u;
@@ -652,12 +652,15 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       const uint32_t dd = deg[v];
       // v's neighbours per mask (Eq. 1 row costs): one byte per mask
       const uint32_t sel = (uint32_t)jv | ((uint32_t)(jv + 4) << 4);
-      uint32_t cw0 = pick_bytes(cc[0], cc[1], cc[2], cc[3], sel);
-      uint32_t sw0 = pick_bytes(sc[0], sc[1], sc[2], sc[3], sel);
+      // masks past NC have no register and count as zero
+      auto ccr = [&](int m) -> uint32_t { return m < NC ? cc[m < NC ? m : 0] : 0u; };
+      auto scr = [&](int m) -> uint32_t { return m < NC ? sc[m < NC ? m : 0] : 0u; };
+      uint32_t cw0 = pick_bytes(ccr(0), ccr(1), ccr(2), ccr(3), sel);
+      uint32_t sw0 = pick_bytes(scr(0), scr(1), scr(2), scr(3), sel);
       uint32_t cw1 = 0u, sw1 = 0u;
       if constexpr (NC == 8) {
-        cw1 = pick_bytes(cc[4], cc[5], cc[6], cc[7], sel);
-        sw1 = pick_bytes(sc[4], sc[5], sc[6], sc[7], sel);
+        cw1 = pick_bytes(ccr(4), ccr(5), ccr(6), ccr(7), sel);
+        sw1 = pick_bytes(scr(4), scr(5), scr(6), scr(7), sel);
       }
       cw0 = __shfl_sync(FULL, cw0, src);
       sw0 = __shfl_sync(FULL, sw0, src);
