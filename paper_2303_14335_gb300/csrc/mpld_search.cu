@@ -612,7 +612,7 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       }
       // column choice.  Rule 0 keys (count, v); rule 1 keys single-row
       // columns by v ahead of all others, which go by breadth-first rank.
-      uint32_t key = 0xFFFFFFFFu, z = 0;
+      uint32_t key = 0xFFFFFFFFu;
 #pragma unroll
       for (int j = 0; j < P; ++j) {
         const uint32_t f = (w >> (FB * j)) & FMASK;
@@ -623,7 +623,6 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
         else kv = cnt == 1 ? sg : (0x10000u | (((rk >> (8 * j)) & 0xFFu) << 8) | sg);
         kv = (f & FLAG) ? kv : 0xFFFFFFFFu;
         key = min(key, kv);
-        z += (f & FLAG) && cnt == 0;
       }
       key = __reduce_min_sync(FULL, key);
       if (key == 0xFFFFFFFFu) {
@@ -640,8 +639,16 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
       }
       if (best < INF32) {
         // uncovered columns with no active row; under rule 0 there is one
-        // only when the minimum count is 0
-        z = (RULE != 0 || key < 0x100u) ? __reduce_add_sync(FULL, z) : 0u;
+        // only when the minimum count is 0, so only then are they counted
+        uint32_t z = 0;
+        if (RULE != 0 || key < 0x100u) {
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const uint32_t f = (w >> (FB * j)) & FMASK;
+            z += (f & FLAG) && (f & kmask) == 0;
+          }
+          z = __reduce_add_sync(FULL, z);
+        }
         if ((int64_t)g + (int64_t)Cc * (z + (uint32_t)untouched) >= best) { enter = false; continue; }
       }
       const int v = (int)(key & 0xFFu);
