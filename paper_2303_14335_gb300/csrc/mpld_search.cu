@@ -305,32 +305,42 @@ struct Search {
         // which go by breadth-first rank.
         uint32_t key = 0xFFFFFFFFu, z = 0;
         if (rule == 0) {
-          for (int wi = lane; wi < nwords; wi += 32) {
-            const uint32_t w = rows32[wi];
+          // four words per lane in flight: an instance whose state is in
+          // global memory waits on one load latency per four words
+          for (int wb = lane; wb < nwords; wb += 128) {
+            uint32_t wv[4];
 #pragma unroll
-            for (int j = 0; j < PER_WORD; ++j) {
-              const uint32_t f = (w >> (FB * j)) & FMASK;
-              const uint32_t kv = (f & FLAG)
-                                      ? ((uint32_t)__popc(f & kmask) << 16) |
-                                            (uint32_t)(wi * PER_WORD + j)
-                                      : 0xFFFFFFFFu;
-              key = min(key, kv);
-              z += kv <= 0xFFFFu;  // uncovered column with no active row
-            }
+            for (int u = 0; u < 4; ++u) wv[u] = wb + 32 * u < nwords ? rows32[wb + 32 * u] : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int j = 0; j < PER_WORD; ++j) {
+                const uint32_t f = (wv[u] >> (FB * j)) & FMASK;
+                const uint32_t kv = (f & FLAG)
+                                        ? ((uint32_t)__popc(f & kmask) << 16) |
+                                              (uint32_t)((wb + 32 * u) * PER_WORD + j)
+                                        : 0xFFFFFFFFu;
+                key = min(key, kv);
+                z += kv <= 0xFFFFu;  // uncovered column with no active row
+              }
           }
         } else {
-          for (int wi = lane; wi < nwords; wi += 32) {
-            const uint32_t w = rows32[wi];
+          for (int wb = lane; wb < nwords; wb += 128) {
+            uint32_t wv[4];
 #pragma unroll
-            for (int j = 0; j < PER_WORD; ++j) {
-              const uint32_t f = (w >> (FB * j)) & FMASK;
-              const uint32_t seg = (uint32_t)(wi * PER_WORD + j);
-              const uint32_t cnt = (uint32_t)__popc(f & kmask);
-              uint32_t kv = 0xFFFFFFFFu;
-              if (f & FLAG) kv = cnt == 1 ? seg : 0x10000u | (uint32_t)ro_ld<SM>(rank + seg);
-              key = min(key, kv);
-              z += (f & FLAG) && cnt == 0;
-            }
+            for (int u = 0; u < 4; ++u) wv[u] = wb + 32 * u < nwords ? rows32[wb + 32 * u] : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int j = 0; j < PER_WORD; ++j) {
+                const uint32_t f = (wv[u] >> (FB * j)) & FMASK;
+                const uint32_t seg = (uint32_t)((wb + 32 * u) * PER_WORD + j);
+                const uint32_t cnt = (uint32_t)__popc(f & kmask);
+                uint32_t kv = 0xFFFFFFFFu;
+                if (f & FLAG) kv = cnt == 1 ? seg : 0x10000u | (uint32_t)ro_ld<SM>(rank + seg);
+                key = min(key, kv);
+                z += (f & FLAG) && cnt == 0;
+              }
           }
         }
         key = __reduce_min_sync(FULL, key);
