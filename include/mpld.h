@@ -131,7 +131,11 @@ typedef struct {
  *                  (used by mpld_build_matrix); MPLD_COLUMN_BFS (used by the
  *                  search calls);
  *   warps_per_cta, slot_bytes   launch shape of the batched kernel; 0 = the
- *                  tuned or default shape (see mpld_autotune).
+ *                  tuned or default shape (see mpld_autotune);
+ *   cta_segments   instances of at least this many segments are searched by
+ *                  all threads of a CTA together (at least 8 warps) instead
+ *                  of one warp; 0 = 4096, negative = never.  Same search and
+ *                  results; large instances go faster.
  */
 typedef struct {
   int64_t node_budget;
@@ -139,7 +143,7 @@ typedef struct {
   uint32_t flags;
   int32_t warps_per_cta;
   int32_t slot_bytes;
-  int32_t reserved;
+  int32_t cta_segments;
 } mpld_params;
 
 /* Layout-level result (Sec. 3: st# and cn# are n_stitches and n_conflicts). */

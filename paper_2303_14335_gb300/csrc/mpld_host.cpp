@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <limits>
 #include <memory>
 #include <deque>
 #include <condition_variable>
@@ -42,6 +43,8 @@ namespace {
 
 constexpr int MAX_COST = 10000;
 constexpr int64_t DEFAULT_TIME_LIMIT_MS = 60000;
+constexpr int DEFAULT_CTA_SEGMENTS = 4096;   // instances this large get a whole CTA
+constexpr int CTA_TEAM_WARPS = 8;            // least CTA size when some instance does
 
 using mpld::GraphKey;
 
@@ -825,6 +828,18 @@ int64_t time_limit_ns(const mpld_params *prm) {
 }
 int64_t budget_of(const mpld_params *prm) { return prm ? std::max<int64_t>(prm->node_budget, 0) : 0; }
 int rule_of(const mpld_params *prm) { return (prm && (prm->flags & MPLD_COLUMN_BFS)) ? 1 : 0; }
+int cta_min_of(const mpld_params *prm) {
+  if (prm && prm->cta_segments < 0) return std::numeric_limits<int>::max();
+  return (prm && prm->cta_segments > 0) ? prm->cta_segments : DEFAULT_CTA_SEGMENTS;
+}
+// Instances searched by a whole CTA: the leading entries of a largest-first
+// order whose instance has at least `min_segments` segments.
+template <typename SizeAt>
+int count_large(int total, SizeAt size_at, int min_segments) {
+  int nl = 0;
+  while (nl < total && size_at(nl) >= min_segments) ++nl;
+  return nl;
+}
 
 uint32_t max_footprint(mpld_problem *const *ps, int n) {
   uint32_t m = 0;
@@ -857,13 +872,24 @@ Shape pick_shape(mpld_problem *const *ps, int n, const mpld_params *prm) {
   return Shape{nw, slot, per_sm * sms};
 }
 
+// A shape with enough warps per CTA for the whole-CTA teams, when the launch
+// has large instances.
+Shape with_team(Shape sh, int n_large) {
+  if (n_large <= 0 || sh.nw >= CTA_TEAM_WARPS) return sh;
+  sh.nw = CTA_TEAM_WARPS;
+  sh.slot = std::max(16, std::min(sh.slot, mpld_internal_max_slot_bytes(sh.nw))) & ~15;
+  const int per_sm = std::max(1, mpld_internal_ctas_per_sm(sh.nw, sh.slot));
+  sh.ctas = per_sm * std::max(1, mpld_internal_num_sms());
+  return sh;
+}
+
 int launch_batch(const mpld::LaunchArgs &a, const Shape &sh, cudaStream_t st, uint32_t *queue,
                  int32_t *err) {
-  int rc = cuda_ok(cudaMemsetAsync(queue, 0, 4, st));
+  int rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));   // both work counters
   rc |= cuda_ok(cudaMemsetAsync(err, 0, 4, st));
   if (rc) return MPLD_E_CUDA;
   if (a.n_inst == 0) return MPLD_OK;
-  const int ctas = std::min(sh.ctas, (a.n_inst + sh.nw - 1) / sh.nw);
+  const int ctas = std::min(sh.ctas, a.n_large + (a.n_inst - a.n_large + sh.nw - 1) / sh.nw);
   return mpld_internal_launch(&a, std::max(ctas, 1), sh.nw, st);
 }
 
@@ -877,7 +903,9 @@ bool capturable(void *stream) {
 int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool copy_back) {
   cudaStream_t st = (cudaStream_t)stream;
   mpld_problem *ps[1] = {p};
-  const Shape sh = pick_shape(ps, 1, prm);
+  const int n_large =
+      count_large(p->n_comp, [&](int i) { return p->h_desc[p->h_order[i]].n; }, cta_min_of(prm));
+  const Shape sh = with_team(pick_shape(ps, 1, prm), n_large);
   mpld::LaunchArgs a;
   a.desc = p->d_desc;
   a.order = p->d_order;
@@ -888,7 +916,7 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   a.budget = budget_of(prm);
   a.time_limit_ns = time_limit_ns(prm);
   a.rule = rule_of(prm);
-  a.pad = 0;
+  a.n_large = n_large;
   auto body = [&]() -> int {
     int rc = cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
     if (rc) return rc;
@@ -906,7 +934,7 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     return rc;
   };
   if (!capturable(stream)) return body();
-  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns, a.rule};
+  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns, a.rule, a.n_large};
   key.ctas = copy_back ? sh.ctas : -sh.ctas;  // copy-back variant is a different graph
   if (!p->gexec || !(p->gkey == key) || p->gstream != stream) {
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
@@ -1043,16 +1071,15 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
     a.order = nullptr;
     a.n_inst = 1;
     const int fp = (int)mpld::align16(p->footprint[c]);
-    a.slot_bytes = fp <= maxslot ? fp : 0;  // too large: state in global memory
+    const bool large = p->h_desc[c].n >= cta_min_of(prm);   // searched by a whole CTA
+    a.slot_bytes = (!large && fp <= maxslot) ? fp : 0;  // else state in global memory
     a.queue = nullptr;
     a.err = p->d_err;
     a.budget = budget_of(prm);
     a.time_limit_ns = time_limit_ns(prm);
     a.rule = rule_of(prm);
-    a.pad = 0;
-  a.rule = rule_of(prm);
-  a.pad = 0;
-    rc = mpld_internal_launch(&a, 1, 1, st);
+    a.n_large = large ? 1 : 0;
+    rc = mpld_internal_launch(&a, 1, large ? CTA_TEAM_WARPS : 1, st);
   }
   p->searched = rc == MPLD_OK;
   p->results_copied = false;
@@ -1084,7 +1111,8 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   std::vector<int32_t> order((size_t)total);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sizes[x] > sizes[y]; });
-  const Shape sh = pick_shape(ps, n, prm);
+  const int n_large = count_large(total, [&](int i) { return sizes[order[i]]; }, cta_min_of(prm));
+  const Shape sh = with_team(pick_shape(ps, n, prm), n_large);
   void *buf = nullptr;
   const size_t dbytes = sizeof(InstDesc) * (size_t)std::max(total, 1);
   const size_t bytes = dbytes + sizeof(int32_t) * (size_t)std::max(total, 1) + 256;
@@ -1111,7 +1139,7 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   a.budget = budget_of(prm);
   a.time_limit_ns = time_limit_ns(prm);
   a.rule = rule_of(prm);
-  a.pad = 0;
+  a.n_large = n_large;
   for (int i = 0; i < n; ++i) {
     if (i) rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_err, 0, 4, st));
     rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_res, 0xFF,

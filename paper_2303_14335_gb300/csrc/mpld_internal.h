@@ -135,9 +135,13 @@ MPLD_HD RegLayout reg_layout(int n, int k, int nq = 0) {
 
 // Global scratch an instance needs when its state does not fit a slot, and
 // its shared-memory footprint when it does (nq: cliques of the second bound
-// mode, 0 without it).
+// mode, 0 without it).  The scratch holds either layout: an instance small
+// enough for the register search is still searched with the general layout
+// when a whole CTA takes it.
 MPLD_HD uint32_t search_state_bytes(int n, int ne2, int k, int nq = 0) {
-  return reg_fits(n, k) ? reg_layout(n, k, nq).bytes : state_layout(n, ne2, k, nq).bytes;
+  const uint32_t general = state_layout(n, ne2, k, nq).bytes;
+  const uint32_t reg = reg_fits(n, k) ? reg_layout(n, k, nq).bytes : 0u;
+  return general > reg ? general : reg;
 }
 MPLD_HD uint32_t search_footprint(int n, int ne2, int ns2, int k, int nq = 0) {
   return reg_fits(n, k) ? reg_layout(n, k, nq).bytes
@@ -178,12 +182,13 @@ struct LaunchArgs {
   const int32_t *order;    // instance indices, largest first
   int32_t n_inst;
   int32_t slot_bytes;      // shared memory per warp
-  uint32_t *queue;         // work counter; NULL = static assignment
+  uint32_t *queue;         // work counters [small, large]; NULL = static assignment
   int32_t *err;            // device status word (0 = fine)
   int64_t budget;
   int64_t time_limit_ns;
   int32_t rule;            // column rule: 0 fewest rows, 1 single row else BFS order
-  int32_t pad;
+  int32_t n_large;         // the first n_large instances of the order are searched by whole
+                           // CTAs (blocks 0..n_large-1 first; counter queue[1])
 };
 
 }  // namespace mpld

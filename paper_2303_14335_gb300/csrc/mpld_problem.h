@@ -17,10 +17,10 @@ namespace mpld {
 struct GraphKey {
   int nw = 0, slot = 0, ctas = 0;
   int64_t budget = 0, tl = 0;
-  int rule = 0;
+  int rule = 0, n_large = 0;
   bool operator==(const GraphKey &o) const {
     return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl &&
-           rule == o.rule;
+           rule == o.rule && n_large == o.n_large;
   }
 };
 

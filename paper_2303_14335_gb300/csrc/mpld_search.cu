@@ -54,6 +54,13 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int32_t INF32 = 0x7FFFFFFF;
 constexpr uint32_t TMA_MIN_BYTES = 1024;     // smaller blocks use vector loads
 constexpr uint32_t WAIT_LIMIT = 1u << 22;    // bounded mbarrier wait
+constexpr uint32_t TEAM_BYTES = 128;          // a CTA team's reduction words
+
+// Dynamic shared memory of the batched kernel: the CTA team's reduction
+// words, one mbarrier per warp, then one slot per warp.
+__host__ __device__ __forceinline__ uint32_t kernel_head_bytes(int warps_per_cta) {
+  return TEAM_BYTES + ((8u * (uint32_t)warps_per_cta + 15u) & ~15u);
+}
 
 __device__ __forceinline__ void cas_u32(uint32_t &a, uint32_t &b) {
   const uint32_t lo = min(a, b), hi = max(a, b);
@@ -130,6 +137,55 @@ __device__ __forceinline__ T ro_ld(const T *p) {
   else return __ldcg(p);
 }
 
+// The threads that search one instance together.  WarpTeam: one warp, with
+// warp-synchronous primitives.  CtaTeam: every thread of a CTA (instances
+// too large for one warp's pace), with reductions through a few words of
+// shared memory; every member calls every primitive (the search's control
+// flow depends only on reduced values).
+struct WarpTeam {
+  int rank;
+  __device__ __forceinline__ int size() const { return 32; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  __device__ __forceinline__ uint32_t min(uint32_t v) const { return __reduce_min_sync(FULL, v); }
+  __device__ __forceinline__ uint32_t sum(uint32_t v) const { return __reduce_add_sync(FULL, v); }
+  __device__ __forceinline__ uint64_t bcast0(uint64_t v) const { return __shfl_sync(FULL, v, 0); }
+};
+struct CtaTeam {
+  int rank, nthreads;
+  uint32_t *red;   // shared: one word per warp, then two for a broadcast
+  __device__ __forceinline__ int size() const { return nthreads; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ uint32_t min(uint32_t v) const {
+    v = __reduce_min_sync(FULL, v);
+    if ((rank & 31) == 0) red[rank >> 5] = v;
+    __syncthreads();
+    uint32_t r = red[0];
+    for (int w = 1; w < (nthreads >> 5); ++w) r = ::min(r, red[w]);
+    __syncthreads();
+    return r;
+  }
+  __device__ __forceinline__ uint32_t sum(uint32_t v) const {
+    v = __reduce_add_sync(FULL, v);
+    if ((rank & 31) == 0) red[rank >> 5] = v;
+    __syncthreads();
+    uint32_t r = 0;
+    for (int w = 0; w < (nthreads >> 5); ++w) r += red[w];
+    __syncthreads();
+    return r;
+  }
+  __device__ __forceinline__ uint64_t bcast0(uint64_t v) const {
+    const int w = nthreads >> 5;
+    if (rank == 0) {
+      red[w] = (uint32_t)v;
+      red[w + 1] = (uint32_t)(v >> 32);
+    }
+    __syncthreads();
+    const uint64_t r = (uint64_t)red[w] | ((uint64_t)red[w + 1] << 32);
+    __syncthreads();
+    return r;
+  }
+};
+
 // FT: field type of the activeRows bitset (uint8_t for k <= 7, uint16_t for
 // k = 8); MK: width of the row sort (k for k <= 4, else 8); SM: state and
 // read-only block in shared memory.  Each segment's field is written by one
@@ -140,7 +196,7 @@ __device__ __forceinline__ T ro_ld(const T *p) {
 // the same lanes, so the added cost of a segment's rows (Eq. 1) is read in
 // one load instead of gathered from its neighbours.
 // Instances of at most 32 words of fields go to reg_search below instead.
-template <typename FT, int MK, bool SM>
+template <typename FT, int MK, bool SM, typename Team>
 struct Search {
   static constexpr uint32_t FB = 8 * sizeof(FT);    // bits per field
   static constexpr uint32_t FLAG = 1u << (FB - 1);   // column P_v uncovered
@@ -172,10 +228,11 @@ struct Search {
   __device__ __forceinline__ static int lane16(uint64_t w, int c) {
     return (int)((w >> (16 * (c & 3))) & 0xFFFFull);
   }
-  // f(i) for i = lane, lane + 32, ... < d
+  Team team;          // the threads searching this instance together
+  // f(i) for i = rank, rank + team size, ... < d
   template <typename F>
-  __device__ __forceinline__ static void each(int d, int lane, F &&f) {
-    for (int i = lane; i < d; i += 32) f(i);
+  __device__ __forceinline__ void each(int d, int rank, F &&f) const {
+    for (int i = rank; i < d; i += team.size()) f(i);
   }
 
   // count word holding mask c of segment u
@@ -213,7 +270,7 @@ struct Search {
       move_count(ccnt, u, c, -1);
     });
     each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, -1); });
-    __syncwarp();
+    team.sync();
   }
 
   // Next row (v, c) of the same column, replacing row (v, c_old): every
@@ -228,7 +285,7 @@ struct Search {
       move_count(ccnt, u, c, c_old);
     });
     each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, c_old); });
-    __syncwarp();
+    team.sync();
   }
 
   // Every row of v's column tried (the last was c_last): put v's field and
@@ -245,7 +302,7 @@ struct Search {
       *cw_of(ccnt, u, c_last) -= one(c_last);
     });
     each(ds, lane, [&](int i) { *cw_of(scnt, ro_ld<SM>(snbr + sb + i), c_last) -= one(c_last); });
-    __syncwarp();
+    team.sync();
   }
 
   __device__ __forceinline__ int run(int lane, int64_t budget, int64_t time_limit_ns,
@@ -271,17 +328,17 @@ struct Search {
     // member counts of v's cliques move (the caller keeps `untouched`)
     auto clique_move = [&](int v, int dir) {
       const int q0 = ro_ld<SM>(qptr + v), q1 = ro_ld<SM>(qptr + v + 1);
-      for (int i = q0 + lane; i < q1; i += 32) {
+      for (int i = q0 + lane; i < q1; i += team.size()) {
         const int q = ro_ld<SM>(qlist + i);
         qcnt[q] = (uint8_t)(qcnt[q] + dir);
       }
-      __syncwarp();
+      team.sync();
     };
     auto untouched_after = [&](int v) -> int {
       const int q0 = ro_ld<SM>(qptr + v), q1 = ro_ld<SM>(qptr + v + 1);
       int left = untouched;
-      for (int i = q0 + lane; i - lane < q1; i += 32)
-        left -= __popc(__ballot_sync(FULL, i < q1 && qcnt[ro_ld<SM>(qlist + i)] == 0));
+      for (int i = q0 + lane; i - lane < q1; i += team.size())
+        left -= (int)team.sum(i < q1 && qcnt[ro_ld<SM>(qlist + i)] == 0);
       return left;
     };
     bool enter = true;
@@ -295,8 +352,7 @@ struct Search {
           next_check = nodes + 1024;
           work += work32;
           work32 = 0;
-          uint64_t now = lane == 0 ? globaltimer() : 0;
-          now = __shfl_sync(FULL, now, 0);
+          const uint64_t now = team.bcast0(lane == 0 ? globaltimer() : 0);
           if ((int64_t)(now - t0) > time_limit_ns) { status = MPLD_TIMEOUT; break; }
         }
         // column choice: min over uncovered P_v of popc(activeRows & colRows[P_v]),
@@ -305,12 +361,13 @@ struct Search {
         // which go by breadth-first rank.
         uint32_t key = 0xFFFFFFFFu, z = 0;
         if (rule == 0) {
-          // four words per lane in flight: an instance whose state is in
+          // four words per thread in flight: an instance whose state is in
           // global memory waits on one load latency per four words
-          for (int wb = lane; wb < nwords; wb += 128) {
+          const int ts = team.size();
+          for (int wb = lane; wb < nwords; wb += 4 * ts) {
             uint32_t wv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) wv[u] = wb + 32 * u < nwords ? rows32[wb + 32 * u] : 0u;
+            for (int u = 0; u < 4; ++u) wv[u] = wb + ts * u < nwords ? rows32[wb + ts * u] : 0u;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -318,23 +375,24 @@ struct Search {
                 const uint32_t f = (wv[u] >> (FB * j)) & FMASK;
                 const uint32_t kv = (f & FLAG)
                                         ? ((uint32_t)__popc(f & kmask) << 16) |
-                                              (uint32_t)((wb + 32 * u) * PER_WORD + j)
+                                              (uint32_t)((wb + ts * u) * PER_WORD + j)
                                         : 0xFFFFFFFFu;
                 key = min(key, kv);
                 z += kv <= 0xFFFFu;  // uncovered column with no active row
               }
           }
         } else {
-          for (int wb = lane; wb < nwords; wb += 128) {
+          const int ts = team.size();
+          for (int wb = lane; wb < nwords; wb += 4 * ts) {
             uint32_t wv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) wv[u] = wb + 32 * u < nwords ? rows32[wb + 32 * u] : 0u;
+            for (int u = 0; u < 4; ++u) wv[u] = wb + ts * u < nwords ? rows32[wb + ts * u] : 0u;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
               for (int j = 0; j < PER_WORD; ++j) {
                 const uint32_t f = (wv[u] >> (FB * j)) & FMASK;
-                const uint32_t seg = (uint32_t)((wb + 32 * u) * PER_WORD + j);
+                const uint32_t seg = (uint32_t)((wb + ts * u) * PER_WORD + j);
                 const uint32_t cnt = (uint32_t)__popc(f & kmask);
                 uint32_t kv = 0xFFFFFFFFu;
                 if (f & FLAG) kv = cnt == 1 ? seg : 0x10000u | (uint32_t)ro_ld<SM>(rank + seg);
@@ -343,12 +401,12 @@ struct Search {
               }
           }
         }
-        key = __reduce_min_sync(FULL, key);
+        key = team.min(key);
         if (key == 0xFFFFFFFFu) {
           // leaf: every primary column covered
           if (g < best) {
             best = g;
-            for (int i = lane; i < n; i += 32) best_mask[i] = x[i];
+            for (int i = lane; i < n; i += team.size()) best_mask[i] = x[i];
             if (best == 0) break;
           }
           enter = false;
@@ -357,7 +415,7 @@ struct Search {
         if (best < INF32) {
           // the bound needs the number of uncovered columns with no active
           // row; under rule 0 there is one only when the minimum count is 0
-          z = (rule != 0 || (key >> 16) == 0) ? __reduce_add_sync(FULL, z) : 0u;
+          z = (rule != 0 || (key >> 16) == 0) ? team.sum(z) : 0u;
           if ((int64_t)g + (int64_t)Cc * (z + (uint32_t)untouched) >= best) { enter = false; continue; }
         }
         const int v = (rule == 0 || key < 0x10000u) ? (int)(key & 0xFFFFu)
@@ -414,7 +472,7 @@ struct Search {
       if (level == 0) break;
       --level;
       const uint4 r0 = lv[2 * level], r1 = lv[2 * level + 1];
-      __syncwarp();   // read by every lane before lane 0 rewrites it below
+      team.sync();   // read by every thread before the first rewrites it below
       const int v = (int)(r0.y & 0xFFFFu);
       const int nxt = (int)(r0.y >> 16);
       const int cb = (int)r0.w, dc = (int)(r1.x & 0xFFFFu), sb = (int)r1.y, ds = (int)(r1.x >> 16);
@@ -817,14 +875,17 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
 
 // Initialise the state at `base` and search.  SM says at compile time
 // whether `base` and `ro` point into shared memory.
-template <typename FT, int MK, bool SM>
+template <typename FT, int MK, bool SM, typename Team>
 __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
-                                       const LaunchArgs &a, int lane) {
-  using S = Search<FT, MK, SM>;
+                                       const LaunchArgs &a, const Team &team) {
+  using S = Search<FT, MK, SM, Team>;
+  const int lane = team.rank;
+  const int ts = team.size();
   const int n = d.n;
   const StateLayout L = state_layout(n, d.ne2, d.k, d.nq);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2, d.nq * (d.k + 1));
   S s;
+  s.team = team;
   s.lv = (uint4 *)(base + L.lv);
   s.lvx = (int32_t *)(base + L.lvx);
   s.ccnt = (uint64_t *)(base + L.ccnt);
@@ -843,7 +904,7 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   s.qcnt = base + L.qcnt;
   s.qlev = (int32_t *)(base + L.qlev);
   s.nq = d.nq;
-  for (int i = lane; i < d.nq; i += 32) s.qcnt[i] = 0;
+  for (int i = lane; i < d.nq; i += ts) s.qcnt[i] = 0;
   s.rule = a.rule;
   s.n = n;
   s.k = d.k;
@@ -854,13 +915,13 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   // neighbour holds a mask; fields past n (word padding) stay zero
   const FT init = (FT)(s.kmask | S::FLAG);
   const int nfields = ((n + S::PER_WORD - 1) / S::PER_WORD) * S::PER_WORD;
-  for (int i = lane; i < nfields; i += 32) s.rows[i] = i < n ? init : (FT)0;
-  for (int i = lane; i < n; i += 32) s.x[i] = -1;
-  for (int i = lane; i < n * S::CW; i += 32) {
+  for (int i = lane; i < nfields; i += ts) s.rows[i] = i < n ? init : (FT)0;
+  for (int i = lane; i < n; i += ts) s.x[i] = -1;
+  for (int i = lane; i < n * S::CW; i += ts) {
     s.ccnt[i] = 0;
     s.scnt[i] = 0;
   }
-  __syncwarp();
+  team.sync();
   int32_t best = INF32;
   int64_t nodes = 0, work = 0;
   const int st = s.run(lane, a.budget, a.time_limit_ns, d.mask, best, nodes, work);
@@ -870,7 +931,7 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
     d.res->status = st;
     d.res->work = work;
   }
-  __syncwarp();
+  team.sync();
 }
 
 template <typename FT, int MK>
@@ -899,7 +960,7 @@ __device__ __noinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, 
   const StateLayout L = state_layout(d.n, d.ne2, d.k, d.nq);
   const RoLayout R = ro_layout(d.n, d.ne2, d.ns2, d.nq * (d.k + 1));
   if (slot_bytes <= 0 || (int)(L.bytes + R.bytes) > slot_bytes) {
-    run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
+    run_in<FT, MK, false>(d, d.scratch, d.ro, a, WarpTeam{lane});
     return true;
   }
   uint8_t *slot = g_smem + slot_off;
@@ -924,7 +985,7 @@ __device__ __noinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, 
       if (lane == 0) atomicExch(a.err, MPLD_E_TIMEOUT);
       for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
         if (mbar_try_wait(bar, phase ^ 1u)) break;
-      run_in<FT, MK, false>(d, d.scratch, d.ro, a, lane);
+      run_in<FT, MK, false>(d, d.scratch, d.ro, a, WarpTeam{lane});
       return false;
     }
   } else {
@@ -932,16 +993,25 @@ __device__ __noinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, 
     uint4 *d4 = (uint4 *)dst;
     for (uint32_t i = lane; i < ro_copy / 16; i += 32) d4[i] = __ldcg(src + i);
   }
-  run_in<FT, MK, true>(d, slot, dst, a, lane);
+  run_in<FT, MK, true>(d, slot, dst, a, WarpTeam{lane});
   return true;
+}
+
+// One large instance searched by the whole CTA; its state stays in its
+// global scratch region and its adjacency is read through L2.
+template <typename FT, int MK>
+__device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArgs &a,
+                                              const CtaTeam &team) {
+  run_in<FT, MK, false>(d, d.scratch, d.ro, a, team);
 }
 
 __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  uint64_t *bars = (uint64_t *)g_smem;
-  const uint32_t bar_bytes = align16(8u * (uint32_t)nw);
+  uint32_t *team_red = (uint32_t *)g_smem;
+  uint64_t *bars = (uint64_t *)(g_smem + TEAM_BYTES);
+  const uint32_t bar_bytes = kernel_head_bytes(nw);
   const uint32_t slot_off =
       bar_bytes + (uint32_t)warp * (uint32_t)(a.slot_bytes > 0 ? a.slot_bytes : 0);
   int slot_bytes = a.slot_bytes;
@@ -952,15 +1022,40 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
   __syncwarp();
   uint32_t phase = 0;
 
-  int idx = a.queue ? 0 : blockIdx.x * nw + warp;
+  // the first blocks search the large instances (the first n_large of the
+  // order) as whole-CTA teams, taking them from the second work counter;
+  // then they join the warps on the rest
+  if ((int)blockIdx.x < a.n_large) {
+    const CtaTeam team{(int)threadIdx.x, (int)blockDim.x, team_red};
+    for (int t = (int)blockIdx.x;;) {
+      if (a.queue) {
+        if (threadIdx.x == 0) team_red[18] = atomicAdd(a.queue + 1, 1u);
+        __syncthreads();
+        t = (int)team_red[18];
+        __syncthreads();
+      }
+      if (t >= a.n_large) break;
+      const InstDesc d = a.desc[a.order ? a.order[t] : t];
+      if (d.k == 3) run_instance_cta<uint8_t, 3>(d, a, team);
+      else if (d.k == 4) run_instance_cta<uint8_t, 4>(d, a, team);
+      else if (d.k == 2) run_instance_cta<uint8_t, 2>(d, a, team);
+      else if (d.k <= 7) run_instance_cta<uint8_t, 8>(d, a, team);
+      else run_instance_cta<uint16_t, 8>(d, a, team);
+      if (!a.queue) break;
+    }
+  }
+
+  const int n_small = a.n_inst - a.n_large;
+  int idx = a.queue ? 0 : blockIdx.x * nw + warp - a.n_large * nw;
   for (;;) {
     if (a.queue) {
       uint32_t t = 0;
       if (lane == 0) t = atomicAdd(a.queue, 1u);
       idx = (int)__shfl_sync(FULL, t, 0);
     }
-    if (idx >= a.n_inst) break;
-    const InstDesc d = a.desc[a.order ? a.order[idx] : idx];
+    if (idx < 0 || idx >= n_small) break;
+    const int pos = a.n_large + idx;
+    const InstDesc d = a.desc[a.order ? a.order[pos] : pos];
     bool ok;
     if (d.k == 3) ok = run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, a, lane);
     else if (d.k == 4) ok = run_instance<uint8_t, 4>(d, slot_off, slot_bytes, bar, phase, a, lane);
@@ -995,7 +1090,7 @@ using mpld::LaunchArgs;
 
 extern "C" int mpld_internal_launch(const LaunchArgs *a, int ctas, int warps_per_cta,
                                     void *stream) {
-  const size_t smem = mpld::align16(8u * (uint32_t)warps_per_cta) +
+  const size_t smem = mpld::kernel_head_bytes(warps_per_cta) +
                       (size_t)warps_per_cta * (size_t)(a->slot_bytes > 0 ? a->slot_bytes : 0);
   if (mpld::ensure_smem(smem) != MPLD_OK) return MPLD_E_CUDA;
   mpld::mpld_search_kernel<<<ctas, warps_per_cta * 32, smem, (cudaStream_t)stream>>>(*a);
@@ -1015,13 +1110,13 @@ extern "C" int mpld_internal_max_slot_bytes(int warps_per_cta) {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return 0;
-  const int avail = optin - (int)mpld::align16(8u * (uint32_t)warps_per_cta);
+  const int avail = optin - (int)mpld::kernel_head_bytes(warps_per_cta);
   return (avail / warps_per_cta) & ~15;
 }
 
 extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes) {
   const size_t smem =
-      mpld::align16(8u * (uint32_t)warps_per_cta) + (size_t)warps_per_cta * (size_t)slot_bytes;
+      mpld::kernel_head_bytes(warps_per_cta) + (size_t)warps_per_cta * (size_t)slot_bytes;
   if (mpld::ensure_smem(smem) != MPLD_OK) return 0;
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mpld::mpld_search_kernel,
@@ -1142,7 +1237,7 @@ __global__ void __launch_bounds__(32, 1)
   a.budget = budget;
   a.time_limit_ns = time_limit_ns;
   a.rule = 0;
-  a.pad = 0;
+  a.n_large = 0;
   uint32_t phase = 0;
   const uint32_t slot_off = align16(8u);
   if (d.k == 3) run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, a, lane);

@@ -147,6 +147,7 @@ struct mpld_server {
   mpld_server_config cfg{};
   int64_t budget = 0, tl_ns = 0;
   int rule = 0;
+  int cta_min = 4096;   // instances this large get a whole CTA
   int nsm = 1, max_slot = 0;
   std::vector<cudaStream_t> streams;
   uint64_t next_stream = 0;
@@ -270,10 +271,15 @@ int launch_request(mpld_server *s, Req &r) {
   rc |= cuda_ok(cudaMemsetAsync(base + S.ctrl, 0, ALIGN, st));
   rc |= cuda_ok(cudaMemsetAsync(d_res, 0xFF, sizeof(InstResult) * (size_t)C, st));
   if (rc) return MPLD_E_CUDA;
-  const int nw = s->cfg.warps_per_cta;
-  const int slot = (int)std::min<uint32_t>(mpld::align16(fmax), (uint32_t)s->max_slot) & ~15;
+  // instances of at least cta_min segments (the first of the largest-first
+  // order) are searched by whole CTAs of at least 8 warps
+  int n_large = 0;
+  while (n_large < C && p->h_desc[p->h_order[n_large]].n >= s->cta_min) ++n_large;
+  const int nw = n_large > 0 ? std::max(s->cfg.warps_per_cta, 8) : s->cfg.warps_per_cta;
+  const int max_slot = n_large > 0 ? mpld_internal_max_slot_bytes(nw) : s->max_slot;
+  const int slot = (int)std::min<uint32_t>(mpld::align16(fmax), (uint32_t)max_slot) & ~15;
   const int per_sm = std::max(1, mpld_internal_ctas_per_sm(nw, slot));
-  const int ctas = std::max(1, std::min(s->nsm * per_sm, (C + nw - 1) / nw));
+  const int ctas = std::max(1, std::min(s->nsm * per_sm, n_large + (C - n_large + nw - 1) / nw));
   mpld::LaunchArgs a;
   a.desc = d_desc;
   a.order = reinterpret_cast<const int32_t *>(base + S.order);
@@ -284,7 +290,7 @@ int launch_request(mpld_server *s, Req &r) {
   a.budget = s->budget;
   a.time_limit_ns = s->tl_ns;
   a.rule = s->rule;
-  a.pad = 0;
+  a.n_large = n_large;
   rc = mpld_internal_launch(&a, ctas, nw, st);
   if (rc) return rc;
   rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_res, d_res, sizeof(InstResult) * (size_t)C,
@@ -328,6 +334,8 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
   s->budget = search ? std::max<int64_t>(search->node_budget, 0) : 0;
   s->tl_ns = ((search && search->time_limit_ms > 0) ? search->time_limit_ms : 60000) * 1000000ll;
   s->rule = (search && (search->flags & MPLD_COLUMN_BFS)) ? 1 : 0;
+  if (search && search->cta_segments != 0)
+    s->cta_min = search->cta_segments > 0 ? search->cta_segments : INT32_MAX;
   s->nsm = std::max(1, mpld_internal_num_sms());
   s->max_slot = mpld_internal_max_slot_bytes(cfg.warps_per_cta);
   if (s->max_slot <= 0) {

@@ -48,7 +48,7 @@ class mpld_graph(ctypes.Structure):
 
 class mpld_params(ctypes.Structure):
     _fields_ = [("node_budget", _i64), ("time_limit_ms", _i64), ("flags", ctypes.c_uint32),
-                ("warps_per_cta", _i32), ("slot_bytes", _i32), ("reserved", _i32)]
+                ("warps_per_cta", _i32), ("slot_bytes", _i32), ("cta_segments", _i32)]
 
 
 class mpld_result(ctypes.Structure):
@@ -166,8 +166,8 @@ def _ptr(a: np.ndarray | None):
 
 
 def make_params(node_budget: int = 0, time_limit_ms: int = 0, flags: int = 0,
-                warps_per_cta: int = 0, slot_bytes: int = 0) -> mpld_params:
-    return mpld_params(node_budget, time_limit_ms, flags, warps_per_cta, slot_bytes, 0)
+                warps_per_cta: int = 0, slot_bytes: int = 0, cta_segments: int = 0) -> mpld_params:
+    return mpld_params(node_budget, time_limit_ms, flags, warps_per_cta, slot_bytes, cta_segments)
 
 
 # ------------------------------------------------------------------ ABI names

@@ -39,10 +39,10 @@ def edges(L):
 
 
 def gpu_run(L, flags=0, budget=0, path="batch", stream=0, warps=0, slot=0, time_limit_ms=0,
-            search_flags=0):
+            search_flags=0, cta=0):
     prob = mpld.mpld_build_matrix(L, mpld.make_params(flags=flags), stream)
     prm = mpld.make_params(node_budget=budget, warps_per_cta=warps, slot_bytes=slot,
-                           time_limit_ms=time_limit_ms, flags=search_flags)
+                           time_limit_ms=time_limit_ms, flags=search_flags, cta_segments=cta)
     if path == "plain":
         rc, mask, res = mpld.mpld_solve(prob, prm, stream)
     else:
@@ -308,6 +308,45 @@ def test_clique_bound_with_blocks_and_column_rule(stream):
         ref = oracle.decompose(L, flags=ofl, budget=2000, nthreads=NTHREADS)
         assert_same(gpu_run(L, flags=fl, budget=2000, stream=stream.cuda_stream, search_flags=sf),
                     ref, L)
+
+
+# ------------------------------------------- whole-CTA teams for large instances
+
+@pytest.mark.parametrize("n,k,seed,p", small_cases()[::4])
+def test_cta_teams_small_graphs(n, k, seed, p, stream):
+    # a low threshold sends every instance to a CTA team
+    L = synth.random_graph(n, k, seed=seed, p_edge=p, n_stitch=n // 4, identity_polygons=False)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=200000)
+    for path in ("batch", "plain"):
+        assert_same(gpu_run(L, flags=SINGLE, budget=200000, path=path, stream=stream.cuda_stream,
+                            cta=2), ref, L)
+
+
+@pytest.mark.parametrize("name", ["k3_n200k_p02_batched", "k4_n100k_p03_batched"])
+def test_cta_teams_with_warps_in_one_launch(name, stream):
+    # instances of 40+ segments go to CTA teams, the rest to warps
+    L, mode = synth.workload(name)
+    ref = oracle.decompose(L, budget=3000, nthreads=NTHREADS)
+    for warps in (0, 1, 16):
+        assert_same(gpu_run(L, budget=3000, stream=stream.cuda_stream, warps=warps, cta=40), ref, L)
+
+
+def test_cta_teams_with_options(stream):
+    L = synth.unit_disk_layout(6000, 3, seed=27, mean_deg=5.0, p_stitch=0.2)
+    for fl, ofl, sf in ((CQ, oracle.CLIQUE_BOUND, 0), (0, oracle.COLUMN_BFS, BFS),
+                        (BIC, oracle.BICONNECTED, 0)):
+        ref = oracle.decompose(L, flags=ofl, budget=2000, nthreads=NTHREADS)
+        assert_same(gpu_run(L, flags=fl, budget=2000, stream=stream.cuda_stream, search_flags=sf,
+                            cta=16), ref, L)
+
+
+def test_cta_team_large_instance_default_threshold(stream):
+    # one 5,000-segment instance: above the default threshold
+    L = synth.unit_disk_layout(5000, 3, seed=31, mean_deg=2.5)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=6000)
+    assert ref.max_component >= 4096
+    for cta in (0, -1):
+        assert_same(gpu_run(L, flags=SINGLE, budget=6000, stream=stream.cuda_stream, cta=cta), ref, L)
 
 
 # ---------------------------------------------------------------- launch forms

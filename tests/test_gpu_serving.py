@@ -155,3 +155,16 @@ def test_block_split_requests(torch_cuda):
         ref = oracle.decompose(L, flags=oracle.BICONNECTED, budget=BUDGET, nthreads=NTHREADS)
         rc, mask, res = got[t]
         assert np.array_equal(mask, ref.mask) and res.nodes == ref.nodes and res.cost == ref.cost
+
+
+def test_cta_team_threshold_reaches_served_searches(torch_cuda):
+    # a server whose instances of 30+ segments go to whole-CTA teams
+    Ls = requests(4, seed=85, n_max=8000)
+    prm = mpld.make_params(node_budget=BUDGET, cta_segments=30)
+    with mpld.mpld_server_create(None, prm) as srv:
+        tickets = [mpld.mpld_server_submit(srv, L) for L in Ls]
+        got = drain(srv, tickets)
+    for t, L in zip(tickets, Ls):
+        ref = oracle.decompose(L, budget=BUDGET, nthreads=NTHREADS)
+        rc, mask, res = got[t]
+        assert np.array_equal(mask, ref.mask) and res.nodes == ref.nodes and res.cost == ref.cost
