@@ -575,12 +575,30 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     // packed in parallel; a segment's local id in an instance is found by
     // binary search in the instance's ascending segment list (a segment may
     // sit in several blocks).
+    // when the instances are whole components each segment has one, and its
+    // local id is looked up directly
+    const bool blocks = !p->inst_attach.empty();
+    std::vector<int32_t> lid_of;
+    if (!blocks) {
+      lid_of.assign((size_t)n, -1);
+      for (int c = 0; c < C; ++c)
+        for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t)
+          lid_of[p->comp_seg[t]] = t - p->comp_ptr[c];
+    }
     auto local_of = [&](int c, int g) -> int {
+      if (!blocks) return p->comp_of[g] == c ? lid_of[g] : -1;
       const int32_t *first = p->comp_seg.data() + p->comp_ptr[c];
       const int32_t *last = p->comp_seg.data() + p->comp_ptr[c + 1];
       const int32_t *it = std::lower_bound(first, last, g);
       return (it != last && *it == g) ? (int)(it - first) : -1;
     };
+    // instances are packed largest first, one per task, so that the few
+    // large ones start at once on different threads
+    std::vector<int32_t> by_size((size_t)C);
+    std::iota(by_size.begin(), by_size.end(), 0);
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int x, int y) {
+      return p->comp_ptr[x + 1] - p->comp_ptr[x] > p->comp_ptr[y + 1] - p->comp_ptr[y];
+    });
     p->ro_off.resize((size_t)C);
     p->footprint.resize((size_t)C);
     p->inst_nq.assign((size_t)C, 0);
@@ -593,7 +611,8 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     const bool cliques = (p->flags & MPLD_CLIQUE_BOUND) != 0;
     std::vector<std::vector<uint16_t>> inst_q((size_t)(cliques ? C : 0));
     // pass 1: sizes, degrees, cliques
-    parallel_for(C, 64, [&](int c) {
+    parallel_for(C, 1, [&](int job) {
+      const int c = by_size[job];
       const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
       int ne2 = 0, ns2 = 0, mdc = 0, mds = 0;
       int64_t max_inc = 0;
@@ -647,7 +666,8 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     p->scratch_bytes = (size_t)scratch;
     p->h_arena.assign((size_t)arena, 0);
     // pass 2: the read-only blocks
-    parallel_for(C, 64, [&](int c) {
+    parallel_for(C, 1, [&](int job) {
+      const int c = by_size[job];
       const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
       const int nq = p->inst_nq[c];
       const mpld::RoLayout R = mpld::ro_layout(nc, p->inst_ne2[c], ns2v[c], nq * (k + 1));
