@@ -86,6 +86,18 @@ extern "C" {
                                     leaf is unchanged; fewer nodes.  Read by mpld_build_matrix
                                     (and mpld_server_submit); MPLD_E_TOO_LARGE above 65,535
                                     cliques in one instance. */
+#define MPLD_PARALLEL_EXACT 64u  /* exact search (node_budget must be 0, else MPLD_E_INVALID) with the
+                                    warps of one CTA splitting each instance of at least 16
+                                    segments that fits the register-resident form (at most 128
+                                    segments, 64 at k = 8): the tree is cut at the first depth D
+                                    with k^D >= 4 * warps, and the warps take its k^D subtrees
+                                    in depth-first order from a shared counter, sharing the
+                                    incumbent as (cost, subtree).  Cost and masks are those of
+                                    the one-warp search (the first minimum-cost leaf); node
+                                    counts depend on timing; the clique bound is not applied
+                                    inside split instances.  Read by the search calls except
+                                    mpld_search_instance_noalloc (MPLD_E_INVALID) and the
+                                    server (ignored). */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
                                     the solve calls then return MPLD_E_STATE */
@@ -127,11 +139,13 @@ typedef struct {
  *                  searching when it runs out stops with status MPLD_TIMEOUT
  *                  and keeps its incumbent (the layout status is then
  *                  MPLD_BUDGET);
- *   flags          MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_HOST_ONLY
- *                  (used by mpld_build_matrix); MPLD_COLUMN_BFS (used by the
- *                  search calls);
+ *   flags          MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_HOST_ONLY |
+ *                  MPLD_BICONNECTED | MPLD_CLIQUE_BOUND (used by
+ *                  mpld_build_matrix); MPLD_COLUMN_BFS | MPLD_PARALLEL_EXACT
+ *                  (used by the search calls);
  *   warps_per_cta, slot_bytes   launch shape of the batched kernel; 0 = the
- *                  tuned or default shape (see mpld_autotune);
+ *                  tuned or default shape (see mpld_autotune); at most 16
+ *                  warps (larger values are clamped);
  *   cta_segments   instances of at least this many segments are searched by
  *                  all threads of a CTA together (at least 8 warps) instead
  *                  of one warp; 0 = 4096, negative = never.  Same search and

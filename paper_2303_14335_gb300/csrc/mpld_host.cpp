@@ -848,7 +848,15 @@ int64_t time_limit_ns(const mpld_params *prm) {
 }
 int64_t budget_of(const mpld_params *prm) { return prm ? std::max<int64_t>(prm->node_budget, 0) : 0; }
 int rule_of(const mpld_params *prm) { return (prm && (prm->flags & MPLD_COLUMN_BFS)) ? 1 : 0; }
+// Parallel exact mode: instances of at least PAR_MIN_SEGMENTS segments are
+// searched by a CTA whose warps split the subtrees.
+constexpr int PAR_MIN_SEGMENTS = 16;
+int par_of(const mpld_params *prm) { return (prm && (prm->flags & MPLD_PARALLEL_EXACT)) ? 1 : 0; }
+// The split search is exact only: with a node budget the nodes a subtree
+// counts would depend on the order the warps finish.
+bool params_ok(const mpld_params *prm) { return !(par_of(prm) && budget_of(prm) != 0); }
 int cta_min_of(const mpld_params *prm) {
+  if (par_of(prm)) return PAR_MIN_SEGMENTS;
   if (prm && prm->cta_segments < 0) return std::numeric_limits<int>::max();
   return (prm && prm->cta_segments > 0) ? prm->cta_segments : DEFAULT_CTA_SEGMENTS;
 }
@@ -882,7 +890,7 @@ Shape pick_shape(mpld_problem *const *ps, int n, const mpld_params *prm) {
     }
   }
   if (!nw) nw = 4;
-  nw = std::max(1, std::min(nw, 32));
+  nw = std::max(1, std::min(nw, 16));   // the kernel's launch bound: 512 threads
   const int maxslot = mpld_internal_max_slot_bytes(nw);
   if (!slot) slot = (int)mpld::align16(std::max<uint32_t>(max_footprint(ps, n), 16));
   slot = std::max(16, std::min(slot, maxslot)) & ~15;
@@ -921,6 +929,7 @@ bool capturable(void *stream) {
 // Enqueue reset -> persistent search -> copy-back for one problem, as a
 // captured CUDA graph when the stream allows capture.
 int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool copy_back) {
+  if (!params_ok(prm)) return MPLD_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   mpld_problem *ps[1] = {p};
   const int n_large =
@@ -937,6 +946,8 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   a.time_limit_ns = time_limit_ns(prm);
   a.rule = rule_of(prm);
   a.n_large = n_large;
+  a.par = par_of(prm);
+  a.pad = 0;
   auto body = [&]() -> int {
     int rc = cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
     if (rc) return rc;
@@ -954,7 +965,7 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     return rc;
   };
   if (!capturable(stream)) return body();
-  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns, a.rule, a.n_large};
+  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns, a.rule, a.n_large * 2 + a.par};
   key.ctas = copy_back ? sh.ctas : -sh.ctas;  // copy-back variant is a different graph
   if (!p->gexec || !(p->gkey == key) || p->gstream != stream) {
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
@@ -1079,7 +1090,7 @@ int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
 }  // namespace
 
 extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, void *stream) {
-  if (!p) return MPLD_E_INVALID;
+  if (!p || !params_ok(prm)) return MPLD_E_INVALID;
   if (!p->d_base) return MPLD_E_STATE;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
@@ -1092,13 +1103,18 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
     a.n_inst = 1;
     const int fp = (int)mpld::align16(p->footprint[c]);
     const bool large = p->h_desc[c].n >= cta_min_of(prm);   // searched by a whole CTA
-    a.slot_bytes = (!large && fp <= maxslot) ? fp : 0;  // else state in global memory
+    // a whole CTA keeps the state in global memory, unless its warps split
+    // the instance (each then needs a slot)
+    const int team_slot = mpld_internal_max_slot_bytes(CTA_TEAM_WARPS);
+    a.slot_bytes = large ? (par_of(prm) && fp <= team_slot ? fp : 0) : (fp <= maxslot ? fp : 0);
     a.queue = nullptr;
     a.err = p->d_err;
     a.budget = budget_of(prm);
     a.time_limit_ns = time_limit_ns(prm);
     a.rule = rule_of(prm);
     a.n_large = large ? 1 : 0;
+    a.par = par_of(prm);
+    a.pad = 0;
     rc = mpld_internal_launch(&a, 1, large ? CTA_TEAM_WARPS : 1, st);
   }
   p->searched = rc == MPLD_OK;
@@ -1108,7 +1124,7 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
 
 extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const mpld_params *prm,
                                        void *stream) {
-  if (!ps || n < 1) return MPLD_E_INVALID;
+  if (!ps || n < 1 || !params_ok(prm)) return MPLD_E_INVALID;
   for (int i = 0; i < n; ++i) {
     if (!ps[i]) return MPLD_E_INVALID;
     if (!ps[i]->d_base) return MPLD_E_STATE;
@@ -1160,6 +1176,8 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   a.time_limit_ns = time_limit_ns(prm);
   a.rule = rule_of(prm);
   a.n_large = n_large;
+  a.par = par_of(prm);
+  a.pad = 0;
   for (int i = 0; i < n; ++i) {
     if (i) rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_err, 0, 4, st));
     rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_res, 0xFF,
@@ -1307,7 +1325,7 @@ extern "C" int mpld_export_matrix(const mpld_problem *p, int32_t comp, uint8_t *
 
 extern "C" int mpld_autotune(mpld_problem *const *ps, int32_t n, const mpld_params *prm,
                              void *stream, mpld_tune *best_out) {
-  if (!ps || n < 1) return MPLD_E_INVALID;
+  if (!ps || n < 1 || !params_ok(prm)) return MPLD_E_INVALID;
   for (int i = 0; i < n; ++i) {
     if (!ps[i]) return MPLD_E_INVALID;
     if (!ps[i]->d_base) return MPLD_E_STATE;

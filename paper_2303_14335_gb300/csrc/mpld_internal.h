@@ -113,8 +113,9 @@ MPLD_HD StateLayout state_layout(int n, int ne2, int k, int nq = 0) {
 //   qptr[n+1]    u16  (nq > 0 only) clique ranges, copied from the block
 //   qlist[nq*(k+1)] u16  cliques holding each segment
 //   qcnt[nq]     u8   members of each clique assigned
+//   bestx[n]     i8   parallel exact search: this warp's best masks
 struct RegLayout {
-  uint32_t adj, deg, rec, sav, qptr, qlist, qcnt, bytes;
+  uint32_t adj, deg, rec, sav, qptr, qlist, qcnt, bestx, bytes;
 };
 MPLD_HD bool reg_fits(int n, int k) { return n <= 32 * (4 / field_bytes_for(k)); }
 MPLD_HD RegLayout reg_layout(int n, int k, int nq = 0) {
@@ -129,6 +130,7 @@ MPLD_HD RegLayout reg_layout(int n, int k, int nq = 0) {
   L.qptr = o; o += nq > 0 ? align16(2u * (uint32_t)(n + 1)) : 0u;
   L.qlist = o; o += align16(2u * nqe);
   L.qcnt = o; o += align16((uint32_t)nq);
+  L.bestx = o; o += align16((uint32_t)n);
   L.bytes = o;
   return L;
 }
@@ -189,6 +191,8 @@ struct LaunchArgs {
   int32_t rule;            // column rule: 0 fewest rows, 1 single row else BFS order
   int32_t n_large;         // the first n_large instances of the order are searched by whole
                            // CTAs (blocks 0..n_large-1 first; counter queue[1])
+  int32_t par;             // 1: those CTAs search exactly, their warps splitting subtrees
+  int32_t pad;
 };
 
 }  // namespace mpld

@@ -54,7 +54,8 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int32_t INF32 = 0x7FFFFFFF;
 constexpr uint32_t TMA_MIN_BYTES = 1024;     // smaller blocks use vector loads
 constexpr uint32_t WAIT_LIMIT = 1u << 22;    // bounded mbarrier wait
-constexpr uint32_t TEAM_BYTES = 128;          // a CTA team's reduction words
+constexpr uint32_t TEAM_BYTES = 320;          // a CTA team's reduction words and
+                                              // the parallel exact search's context
 
 // Dynamic shared memory of the batched kernel: the CTA team's reduction
 // words, one mbarrier per warp, then one slot per warp.
@@ -873,6 +874,305 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   __syncwarp();
 }
 
+// ---- parallel exact search: the warps of a CTA split one instance --------
+//
+// For an exact search (no node budget) of an instance of at most 32 field
+// words.  The canonical tree is cut at depth D into k^D subtrees, numbered in
+// depth-first order: subtree s takes, at level i, the row whose place in the
+// ascending (cost, mask) order is digit i of s in base k.  Warps take
+// subtrees from a counter and search them as reg_search does.  They share the
+// incumbent as one 64-bit key (cost << 32 | subtree): a leaf of cost c in
+// subtree s improves it when (c, s) is smaller, so the answer is still the
+// first minimum-cost leaf of the whole tree, and a node is pruned when its
+// bound reaches cost* plus one if its subtree comes before the incumbent's.
+// Node counts depend on when each warp sees a better incumbent.
+struct ParCtx {
+  unsigned long long key;    // incumbent (cost << 32 | subtree); ~0 = none
+  unsigned long long nodes, work;
+  uint32_t next;             // next subtree to take
+  uint32_t timed_out;
+  unsigned long long wkey[16];   // each warp's own best
+};
+
+template <typename FT, int MK, int RULE>
+__device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
+                                        int lane, int warp, int nwarps, ParCtx *ctx) {
+  constexpr uint32_t FB = 8 * sizeof(FT);
+  constexpr uint32_t FLAG = 1u << (FB - 1);
+  constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
+  constexpr int P = 4 / (int)sizeof(FT);
+  constexpr int RS = MK <= 4 ? 8 : 12;
+  constexpr int NC = MK;
+  const int n = d.n, k = d.k;
+  const int Cc = d.cost_conflict, Cs = d.cost_stitch;
+  const uint32_t kmask = (1u << k) - 1u;
+  const RegLayout R = reg_layout(n, k, 0);
+  uint8_t *adj = base + R.adj;
+  uint32_t *deg = (uint32_t *)(base + R.deg);
+  uint32_t *rec = (uint32_t *)(base + R.rec);
+  uint16_t *sav = (uint16_t *)(base + R.sav);
+  int8_t *bestx = (int8_t *)(base + R.bestx);
+  uint32_t rk = 0u;
+  {
+    const RoLayout Q = ro_layout(n, d.ne2, d.ns2);
+    const int2 *ptr = (const int2 *)(d.ro + Q.ptr);
+    const uint16_t *cnbr = (const uint16_t *)(d.ro + Q.cnbr);
+    const uint16_t *snbr = (const uint16_t *)(d.ro + Q.snbr);
+    const uint16_t *rank = (const uint16_t *)(d.ro + Q.rank);
+    uint32_t *adj32 = (uint32_t *)adj;
+    for (int i = lane; i < 8 * n; i += 32) adj32[i] = 0u;
+    __syncwarp();
+    for (int v = lane; v < n; v += 32) {
+      const int2 p0 = __ldcg(ptr + v), p1 = __ldcg(ptr + v + 1);
+      uint8_t *row = adj + v * 32;
+      for (int i = p0.x; i < p1.x; ++i) {
+        const int u = __ldcg(cnbr + i);
+        row[u / P] |= (uint8_t)(1u << (u % P));
+      }
+      for (int i = p0.y; i < p1.y; ++i) {
+        const int u = __ldcg(snbr + i);
+        row[u / P] |= (uint8_t)(1u << (4 + u % P));
+      }
+      deg[v] = (uint32_t)(p1.x - p0.x) | ((uint32_t)(p1.y - p0.y) << 16);
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      if (RULE && lane * P + j < n) rk |= (uint32_t)__ldcg(rank + lane * P + j) << (8 * j);
+  }
+  __syncwarp();
+  // depth of the cut: about four subtrees per warp, never below the leaves
+  int D = 0;
+  uint32_t ns = 1;
+  while (ns < 4u * (uint32_t)nwarps && D < n) { ns *= (uint32_t)k; ++D; }
+  int64_t nodes = 0, work = 0;
+  uint32_t work32 = 0;
+  bool timed_out = false;
+  unsigned long long my_key = ~0ull;
+  const uint64_t t0 = globaltimer();
+  int64_t next_check = 1024;
+  // the pruning threshold for subtree s: a leaf must cost less than it
+  auto threshold = [&](uint32_t s) -> int32_t {
+    const unsigned long long key = *(volatile unsigned long long *)&ctx->key;
+    if (key == ~0ull) return INF32;
+    const int32_t c = (int32_t)(key >> 32);
+    return c + (s < (uint32_t)(key & 0xFFFFFFFFull) ? 1 : 0);
+  };
+  for (;;) {
+    uint32_t s = 0;
+    if (lane == 0) s = atomicAdd(&ctx->next, 1u);
+    s = __shfl_sync(FULL, s, 0);
+    if (s >= ns || timed_out) break;
+    // fresh state for the subtree
+    uint32_t w = 0u, xw = 0xFFFFFFFFu;
+    uint32_t cc[NC], sc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cc[c] = sc[c] = 0u;
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      if (lane * P + j < n) w |= (kmask | FLAG) << (FB * j);
+    int32_t g = 0;
+    int level = 0;
+    auto move_counts = [&](int c, uint32_t cb8, uint32_t sb8, bool add) {
+      const uint32_t dcw = add ? cb8 : 0u - cb8, dsw = add ? sb8 : 0u - sb8;
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        const bool hit = m == c;
+        cc[m] += hit ? dcw : 0u;
+        sc[m] += hit ? dsw : 0u;
+      }
+    };
+    // a leaf of cost g in subtree s
+    auto take_leaf = [&]() {
+      const unsigned long long key = ((unsigned long long)(uint32_t)g << 32) | s;
+      if (lane == 0) atomicMin(&ctx->key, key);
+      my_key = key;
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+        if (lane * P + j < n) bestx[lane * P + j] = (int8_t)((xw >> (8 * j)) & 0xFFu);
+      __syncwarp();
+    };
+    uint32_t digits = s;   // the prefix, most significant digit first
+    uint32_t top = ns / (uint32_t)k;
+    bool skip = false, done = false;
+    bool enter = true;
+    int floor_level = D;
+    for (;;) {
+      if (enter) {
+        ++nodes;
+        work32 += 2u * (uint32_t)(n - level);
+        if (nodes >= next_check) {
+          next_check = nodes + 1024;
+          work += work32;
+          work32 = 0;
+          const uint64_t now = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
+          if ((int64_t)(now - t0) > a.time_limit_ns) { timed_out = true; break; }
+        }
+        const int32_t thr = threshold(s);
+        uint32_t key = 0xFFFFFFFFu;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const uint32_t f = (w >> (FB * j)) & FMASK;
+          const uint32_t cnt = (uint32_t)__popc(f & kmask);
+          const uint32_t sg = (uint32_t)(lane * P + j);
+          uint32_t kv;
+          if constexpr (RULE == 0) kv = (cnt << 8) | sg;
+          else kv = cnt == 1 ? sg : (0x10000u | (((rk >> (8 * j)) & 0xFFu) << 8) | sg);
+          kv = (f & FLAG) ? kv : 0xFFFFFFFFu;
+          key = min(key, kv);
+        }
+        key = __reduce_min_sync(FULL, key);
+        if (key == 0xFFFFFFFFu) {
+          // a leaf; inside the prefix it is a subtree only on digit 0 below
+          if (level < D && (digits % (top * (uint32_t)k)) != 0u) { skip = true; break; }
+          if (g < thr) {
+            take_leaf();
+            if (g == 0) { done = true; break; }
+          }
+          if (level <= floor_level) { done = true; break; }
+          enter = false;
+          continue;
+        }
+        if (thr < INF32) {
+          uint32_t z = 0;
+          if (RULE != 0 || key < 0x100u) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              const uint32_t f = (w >> (FB * j)) & FMASK;
+              z += (f & FLAG) && (f & kmask) == 0;
+            }
+            z = __reduce_add_sync(FULL, z);
+          }
+          if ((int64_t)g + (int64_t)Cc * z >= thr) {
+            if (level < D) { skip = true; break; }
+            enter = false;
+            continue;
+          }
+        }
+        const int v = (int)(key & 0xFFu);
+        const int jv = v % P, src = v / P;
+        const uint32_t ab = adj[v * 32 + lane];
+        const uint32_t dd = deg[v];
+        const uint32_t sel = (uint32_t)jv | ((uint32_t)(jv + 4) << 4);
+        auto ccr = [&](int m) -> uint32_t { return m < NC ? cc[m < NC ? m : 0] : 0u; };
+        auto scr = [&](int m) -> uint32_t { return m < NC ? sc[m < NC ? m : 0] : 0u; };
+        uint32_t cw0 = __shfl_sync(FULL, pick_bytes(ccr(0), ccr(1), ccr(2), ccr(3), sel), src);
+        uint32_t sw0 = __shfl_sync(FULL, pick_bytes(scr(0), scr(1), scr(2), scr(3), sel), src);
+        uint32_t cw1 = 0u, sw1 = 0u;
+        if constexpr (NC == 8) {
+          cw1 = __shfl_sync(FULL, pick_bytes(ccr(4), ccr(5), ccr(6), ccr(7), sel), src);
+          sw1 = __shfl_sync(FULL, pick_bytes(scr(4), scr(5), scr(6), scr(7), sel), src);
+        }
+        const int stot = (int)(((sw0 * 0x01010101u) >> 24) + ((sw1 * 0x01010101u) >> 24));
+        uint32_t keys[MK];
+        uint32_t oldf = FLAG;
+#pragma unroll
+        for (int c = 0; c < MK; ++c) {
+          const uint32_t cwd = c < 4 ? cw0 : cw1, swd = c < 4 ? sw0 : sw1;
+          const int sh = 8 * (c & 3);
+          const int ncf = (int)((cwd >> sh) & 0xFFu);
+          const int inc = Cc * ncf + Cs * (stot - (int)((swd >> sh) & 0xFFu));
+          keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
+          if (c < k && ncf == 0) oldf |= 1u << c;
+        }
+        sort_keys<MK>(keys);
+        work32 += (uint32_t)(k * (int)((dd & 0xFFFFu) + (dd >> 16)) + 5 * (1 + (int)(dd & 0xFFFFu)));
+        // the row to take: the prefix digit above the cut, the first below it
+        int first = 0;
+        if (level < D) {
+          first = (int)((digits / top) % (uint32_t)k);
+          top /= (uint32_t)k;
+        }
+        uint32_t kf = keys[0];
+#pragma unroll
+        for (int i = 1; i < MK; ++i) kf = i == first ? keys[i] : kf;
+        if (thr < INF32 && g + (int32_t)(kf >> 3) >= thr) {
+          // this row and the ones after it cannot improve
+          if (level < D) { skip = true; break; }
+          enter = false;
+          continue;
+        }
+        if (level >= n) break;   // unreachable: each level covers a column
+        if (level >= D && lane == 0) {
+          uint4 *r4 = (uint4 *)(rec + level * RS);
+          r4[0] = make_uint4((uint32_t)v | (1u << 8) | (oldf << 12), (uint32_t)g, dd, 0u);
+          r4[1] = make_uint4(keys[0], MK > 1 ? keys[MK > 1 ? 1 : 0] : 0u,
+                             MK > 2 ? keys[MK > 2 ? 2 : 0] : 0u, MK > 3 ? keys[MK > 3 ? 3 : 0] : 0u);
+          if constexpr (MK == 8) r4[2] = make_uint4(keys[4 % MK], keys[5 % MK], keys[6 % MK], keys[7 % MK]);
+        }
+        const int c = (int)(kf & 7u);
+        const uint32_t cb = ab & 0xFu, sb = ab >> 4;
+        const uint32_t spc = spread_bits<FB>(cb);
+        if (level >= D)
+          sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (cb << 4) | (sb << 8));
+        w &= ~(spc << c);
+        move_counts(c, spread_bits<8>(cb), spread_bits<8>(sb), true);
+        if (lane == src) {
+          w &= ~(FMASK << (FB * jv));
+          xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+        }
+        g += (int32_t)(kf >> 3);
+        ++level;
+        __syncwarp();
+        continue;
+      }
+      // backtrack, never above the cut
+      if (level <= floor_level) { done = true; break; }
+      --level;
+      const uint32_t *r = rec + level * RS;
+      const uint4 r0 = *(const uint4 *)r, r1 = *(const uint4 *)(r + 4);
+      uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
+      if constexpr (MK == 8) r2 = *(const uint4 *)(r + 8);
+      const uint32_t sv = sav[level * 32 + lane];
+      __syncwarp();
+      const int v = (int)(r0.x & 0xFFu);
+      const int nxt = (int)((r0.x >> 8) & 0xFu);
+      const int jv = v % P, src = v / P;
+      auto key_at = [&](int i) -> uint32_t {
+        const uint32_t lo = i == 0 ? r1.x : i == 1 ? r1.y : i == 2 ? r1.z : r1.w;
+        const uint32_t hi = i == 4 ? r2.x : i == 5 ? r2.y : i == 6 ? r2.z : r2.w;
+        return i < 4 ? lo : hi;
+      };
+      const uint32_t klast = key_at(nxt - 1), knext = key_at(nxt < MK ? nxt : MK - 1);
+      const int cl = (int)(klast & 7u);
+      const uint32_t cb = (sv >> 4) & 0xFu, sb = sv >> 8;
+      const uint32_t spc = spread_bits<FB>(cb);
+      const uint32_t cb8 = spread_bits<8>(cb), sb8 = spread_bits<8>(sb);
+      w |= spread_bits<FB>(sv & 0xFu) << cl;
+      move_counts(cl, cb8, sb8, false);
+      bool last = nxt >= k;
+      const int32_t thr = threshold(s);
+      if (!last && thr < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= thr) last = true;
+      if (last) {
+        if (lane == src) {
+          w |= (r0.x >> 12) << (FB * jv);
+          xw |= 0xFFu << (8 * jv);
+        }
+        continue;
+      }
+      const int c = (int)(knext & 7u);
+      g = (int32_t)r0.y + (int32_t)(knext >> 3);
+      work32 += 5u * (1u + (r0.z & 0xFFFFu));
+      sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (sv & 0xFF0u));
+      if (lane == 0) rec[level * RS] = (r0.x & ~0xF00u) | ((uint32_t)(nxt + 1) << 8);
+      w &= ~(spc << c);
+      move_counts(c, cb8, sb8, true);
+      if (lane == src) xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+      ++level;
+      enter = true;
+      __syncwarp();
+    }
+    (void)skip;
+    (void)done;
+  }
+  if (lane == 0) {
+    atomicAdd(&ctx->nodes, (unsigned long long)nodes);
+    atomicAdd(&ctx->work, (unsigned long long)(work + work32));
+    if (timed_out) atomicExch(&ctx->timed_out, 1u);
+    ctx->wkey[warp] = my_key;
+  }
+  __syncwarp();
+}
+
 // Initialise the state at `base` and search.  SM says at compile time
 // whether `base` and `ro` point into shared memory.
 template <typename FT, int MK, bool SM, typename Team>
@@ -1036,7 +1336,49 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
       }
       if (t >= a.n_large) break;
       const InstDesc d = a.desc[a.order ? a.order[t] : t];
-      if (d.k == 3) run_instance_cta<uint8_t, 3>(d, a, team);
+      if (a.par && reg_fits(d.n, d.k) && a.slot_bytes >= (int)reg_layout(d.n, d.k, 0).bytes) {
+        // exact search with the warps splitting the subtrees of one instance
+        ParCtx *ctx = (ParCtx *)(g_smem + 128);
+        if (threadIdx.x == 0) {
+          ctx->key = ~0ull;
+          ctx->nodes = 0;
+          ctx->work = 0;
+          ctx->next = 0;
+          ctx->timed_out = 0;
+        }
+        __syncthreads();
+        uint8_t *mine = g_smem + slot_off;
+        if (d.k == 3) {
+          if (a.rule) par_search<uint8_t, 3, 1>(d, mine, a, lane, warp, nw, ctx);
+          else par_search<uint8_t, 3, 0>(d, mine, a, lane, warp, nw, ctx);
+        } else if (d.k == 4) {
+          if (a.rule) par_search<uint8_t, 4, 1>(d, mine, a, lane, warp, nw, ctx);
+          else par_search<uint8_t, 4, 0>(d, mine, a, lane, warp, nw, ctx);
+        } else if (d.k == 2) {
+          if (a.rule) par_search<uint8_t, 2, 1>(d, mine, a, lane, warp, nw, ctx);
+          else par_search<uint8_t, 2, 0>(d, mine, a, lane, warp, nw, ctx);
+        } else if (d.k <= 7) {
+          if (a.rule) par_search<uint8_t, 8, 1>(d, mine, a, lane, warp, nw, ctx);
+          else par_search<uint8_t, 8, 0>(d, mine, a, lane, warp, nw, ctx);
+        } else {
+          if (a.rule) par_search<uint16_t, 8, 1>(d, mine, a, lane, warp, nw, ctx);
+          else par_search<uint16_t, 8, 0>(d, mine, a, lane, warp, nw, ctx);
+        }
+        __syncthreads();
+        // the warp holding the winning leaf writes its masks
+        const unsigned long long key = ctx->key;
+        if (ctx->wkey[warp] == key) {
+          const int8_t *bx = (const int8_t *)(mine + reg_layout(d.n, d.k, 0).bestx);
+          for (int i = lane; i < d.n; i += 32) d.mask[i] = bx[i];
+        }
+        if (threadIdx.x == 0) {
+          d.res->cost = key == ~0ull ? INT64_MAX : (int64_t)(key >> 32);
+          d.res->nodes = (int64_t)ctx->nodes;
+          d.res->status = ctx->timed_out ? MPLD_TIMEOUT : MPLD_OK;
+          d.res->work = (int64_t)ctx->work;
+        }
+        __syncthreads();
+      } else if (d.k == 3) run_instance_cta<uint8_t, 3>(d, a, team);
       else if (d.k == 4) run_instance_cta<uint8_t, 4>(d, a, team);
       else if (d.k == 2) run_instance_cta<uint8_t, 2>(d, a, team);
       else if (d.k <= 7) run_instance_cta<uint8_t, 8>(d, a, team);
@@ -1238,6 +1580,8 @@ __global__ void __launch_bounds__(32, 1)
   a.time_limit_ns = time_limit_ns;
   a.rule = 0;
   a.n_large = 0;
+  a.par = 0;
+  a.pad = 0;
   uint32_t phase = 0;
   const uint32_t slot_off = align16(8u);
   if (d.k == 3) run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, a, lane);
@@ -1266,6 +1610,7 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
   using namespace mpld;
   if (!inst || !mask_out || !result_out || !inst->conf_ptr || !inst->st_ptr) return MPLD_E_INVALID;
   if (prm && (prm->flags & MPLD_COLUMN_BFS)) return MPLD_E_INVALID;  // no breadth-first ranks here
+  if (prm && (prm->flags & MPLD_PARALLEL_EXACT)) return MPLD_E_INVALID;  // one warp per instance
   const int n = inst->n, k = inst->k, ne2 = inst->n_conf_entries, ns2 = inst->n_stitch_entries;
   if (n < 1 || k < 2 || k > 8 || ne2 < 0 || ns2 < 0) return MPLD_E_INVALID;
   if ((ne2 > 0 && !inst->conf_nbr) || (ns2 > 0 && !inst->st_nbr)) return MPLD_E_INVALID;

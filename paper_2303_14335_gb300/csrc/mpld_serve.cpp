@@ -291,6 +291,8 @@ int launch_request(mpld_server *s, Req &r) {
   a.time_limit_ns = s->tl_ns;
   a.rule = s->rule;
   a.n_large = n_large;
+  a.par = 0;
+  a.pad = 0;
   rc = mpld_internal_launch(&a, ctas, nw, st);
   if (rc) return rc;
   rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_res, d_res, sizeof(InstResult) * (size_t)C,

@@ -33,6 +33,7 @@ MPLD_HOST_ONLY = 4
 MPLD_COLUMN_BFS = 8
 MPLD_BICONNECTED = 16
 MPLD_CLIQUE_BOUND = 32
+MPLD_PARALLEL_EXACT = 64
 MPLD_MAX_INSTANCE_SEGMENTS = 65535
 
 _P = ctypes.c_void_p

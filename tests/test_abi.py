@@ -158,6 +158,29 @@ def test_noalloc_entry_rejects_the_column_rule_before_any_device_work():
     assert e.value.code == mpld.MPLD_E_INVALID
 
 
+def test_noalloc_entry_rejects_the_split_search():
+    prm = mpld.make_params(flags=mpld.MPLD_PARALLEL_EXACT)
+    with pytest.raises(mpld.MpldError) as e:
+        mpld.mpld_search_instance_noalloc(4, 3, 256, 512, 0, 768, 1024, 0, 1280, 1536, prm)
+    assert e.value.code == mpld.MPLD_E_INVALID
+
+
+def test_split_search_needs_exact_mode():
+    # the split search takes no node budget: an argument error before the
+    # handle's state is looked at; without a budget the host-only handle
+    # is the state error it always is
+    prob = host_only(synth.graph_from_edges(3, 3, [(0, 1), (1, 2), (0, 2)]))
+    for call in (lambda prm: mpld.mpld_solve(prob, prm),
+                 lambda prm: mpld.mpld_solve_batch([prob, prob], prm),
+                 lambda prm: mpld.mpld_search_batch_async([prob], prm)):
+        with pytest.raises(mpld.MpldError) as e:
+            call(mpld.make_params(node_budget=100, flags=mpld.MPLD_PARALLEL_EXACT))
+        assert e.value.code == mpld.MPLD_E_INVALID
+        with pytest.raises(mpld.MpldError) as e:
+            call(mpld.make_params(flags=mpld.MPLD_PARALLEL_EXACT))
+        assert e.value.code == mpld.MPLD_E_STATE
+
+
 def test_too_large_instance_rejected():
     n = 70000
     L = synth.graph_from_edges(n, 3, [(i, i + 1) for i in range(n - 1)])

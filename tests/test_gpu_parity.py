@@ -349,6 +349,109 @@ def test_cta_team_large_instance_default_threshold(stream):
         assert_same(gpu_run(L, flags=SINGLE, budget=6000, stream=stream.cuda_stream, cta=cta), ref, L)
 
 
+# ------------------------------ exact search with the warps of a CTA splitting an instance
+
+PAR = mpld.MPLD_PARALLEL_EXACT
+
+
+def assert_same_answer(g, ref, L):
+    """assert_same without the node counts: with the subtrees split over
+    warps, how many nodes are visited depends on when each warp sees a better
+    incumbent; the answer (first minimum-cost leaf) does not."""
+    assert np.array_equal(g["mask"], ref.mask), "masks differ"
+    assert g["res"].cost == ref.cost
+    assert g["res"].n_conflicts == ref.n_conflicts and g["res"].n_stitches == ref.n_stitches
+    assert g["res"].n_components == ref.n_components
+    assert np.array_equal(g["comp_of"], ref.comp_of)
+    assert np.array_equal(g["cost"], ref.comp_cost)
+    assert np.all(g["status"] == mpld.MPLD_OK) and g["rc"] == mpld.MPLD_OK
+    assert ref.status == oracle.OK
+    assert np.all(g["nodes"] >= 1)
+    conf, stt = edges(L)
+    x = g["mask"]
+    assert g["res"].cost == L.cost_conflict * sum(x[a] == x[b] for a, b in conf) + \
+        L.cost_stitch * sum(x[a] != x[b] for a, b in stt)
+
+
+SPLIT_CASES = [(k, n) for k in (2, 3, 4, 5, 6) for n in (16, 18, 20)] + \
+    [(8, 16), (8, 18), (2, 24), (3, 24), (5, 24), (6, 24)]
+
+
+@pytest.mark.parametrize("k,n", SPLIT_CASES)
+def test_split_search_single_instance(k, n, stream):
+    # every field width and row count of the register form; 8 and 16 warps
+    L = synth.random_graph(n, k, seed=900 + n + k, p_edge=0.5, n_stitch=n // 4, identity_polygons=False)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE)
+    assert_same_answer(gpu_run(L, flags=SINGLE, path="plain", stream=stream.cuda_stream,
+                               search_flags=PAR), ref, L)
+    for warps in (0, 16):
+        assert_same_answer(gpu_run(L, flags=SINGLE, stream=stream.cuda_stream, warps=warps,
+                                   search_flags=PAR), ref, L)
+
+
+@pytest.mark.parametrize("k,n", [(3, 20), (4, 18), (6, 18)])
+def test_split_search_column_rule(k, n, stream):
+    L = synth.random_graph(n, k, seed=900 + n + k, p_edge=0.5, n_stitch=n // 4, identity_polygons=False)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | oracle.COLUMN_BFS)
+    for path in ("batch", "plain"):
+        assert_same_answer(gpu_run(L, flags=SINGLE, path=path, stream=stream.cuda_stream,
+                                   search_flags=PAR | BFS), ref, L)
+
+
+def test_split_search_k3_n24_workload(stream):
+    L, mode = synth.workload("k3_n24_plain")
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE)
+    for path in ("batch", "plain"):
+        assert_same_answer(gpu_run(L, flags=SINGLE, path=path, stream=stream.cuda_stream,
+                                   search_flags=PAR), ref, L)
+
+
+@pytest.mark.parametrize("n,k,deg,ps,seed", [(1000, 3, 2.6, 0.2, 5), (600, 4, 4.0, 0.3, 7)])
+def test_split_search_layouts(n, k, deg, ps, seed, stream):
+    # simplified layouts: instances of 16+ segments split, the rest on warps,
+    # in one launch; with the build options too
+    L = synth.unit_disk_layout(n, k, seed=seed, mean_deg=deg, p_stitch=ps)
+    for fl, ofl, sf in ((0, 0, 0), (CQ, oracle.CLIQUE_BOUND, 0), (BIC, oracle.BICONNECTED, 0),
+                        (0, oracle.COLUMN_BFS, BFS)):
+        if k == 4 and sf:
+            continue      # the column rule's exact tree is 135M nodes here
+        ref = oracle.decompose(L, flags=ofl, budget=0, nthreads=NTHREADS)
+        for warps in (0, 16):
+            assert_same_answer(gpu_run(L, flags=fl, stream=stream.cuda_stream, warps=warps,
+                                       search_flags=PAR | sf), ref, L)
+
+
+def test_split_search_beside_unsplit_large_instances(stream):
+    # a 200-segment ring (k = 3) and a 70-segment ring at k = 8 do not fit the
+    # register form: whole-CTA search, while the 20-segment graph is split
+    conf = [(i, (i + 1) % 200) for i in range(200)]
+    R = synth.random_graph(20, 3, seed=77, p_edge=0.5, identity_polygons=False)
+    conf += [(200 + a, 200 + b) for a, b in zip(R.conf_u.tolist(), R.conf_v.tolist())]
+    L = synth.graph_from_edges(220, 3, conf)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY)
+    assert ref.max_component == 200
+    for path in ("batch", "plain"):
+        assert_same_answer(gpu_run(L, flags=mpld.MPLD_NO_SIMPLIFY, path=path, stream=stream.cuda_stream,
+                                   search_flags=PAR), ref, L)
+    L = synth.graph_from_edges(70, 8, [(i, (i + 1) % 70) for i in range(70)] + [(0, 35), (10, 50)])
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE)
+    assert_same_answer(gpu_run(L, flags=SINGLE, stream=stream.cuda_stream, search_flags=PAR), ref, L)
+
+
+def test_split_search_time_limit(stream):
+    # 5 ms against a tree of about 5e8 nodes: every warp stops by itself and
+    # the incumbent is a consistent layout
+    L = synth.random_graph(20, 8, seed=928, p_edge=0.5, n_stitch=5, identity_polygons=False)
+    g = gpu_run(L, flags=SINGLE, time_limit_ms=5, stream=stream.cuda_stream, search_flags=PAR)
+    assert g["rc"] == mpld.MPLD_BUDGET
+    assert g["status"][0] == mpld.MPLD_TIMEOUT
+    conf, st = edges(L)
+    x = g["mask"]
+    assert np.all((x >= 0) & (x < 8))
+    assert g["res"].cost == g["cost"][0] == 10 * sum(x[a] == x[b] for a, b in conf) + \
+        sum(x[a] != x[b] for a, b in st)
+
+
 # ---------------------------------------------------------------- launch forms
 
 def test_results_independent_of_launch_shape(stream):
