@@ -8,7 +8,10 @@ the persistent batched kernel (one launch, device work queue, replayed from a
 CUDA graph).  ``value`` = decomposed segments per second with the EC
 matrices already resident in HBM; ``e2e`` = the same metric through the C
 ABI from host graph arrays to host masks (build + upload + search + copy
-back + recovery + counts).  Every search instance has the same node budget
+back + recovery + counts), for K layouts submitted together to the serving
+API so that the host work of one overlaps the search of another
+(``e2e.serial``: one layout at a time through mpld_build_matrix and
+mpld_solve_batch).  Every search instance has the same node budget
 on the GPU and in the CPU oracle, so both compute the same answer.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -52,6 +55,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="k3_n200k_p02_batched")
     ap.add_argument("--budget", type=int, default=1 << 16)
+    ap.add_argument("--parallel-exact", action="store_true",
+                    help="exact search (node budget 0) with the warps of a CTA splitting each "
+                         "instance of 16+ segments (for single-instance workloads)")
     ap.add_argument("--biconnected", action="store_true",
                     help="search the biconnected blocks of each sub-graph and join them at cut "
                          "segments")
@@ -75,7 +81,10 @@ def parse_args():
     ap.add_argument("--plain-scale", type=int, default=20,
                     help="the plain one-launch-per-instance path runs on the same workload with "
                          "polygons / plain-scale (same density and degree)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.parallel_exact:
+        args.budget = 0      # the split search is exact only
+    return args
 
 
 class ClockSampler:
@@ -291,6 +300,8 @@ def main():
     prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
     info = mpld.mpld_problem_info(prob)
     rule_flag = mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0
+    if args.parallel_exact:
+        rule_flag |= mpld.MPLD_PARALLEL_EXACT
     prm = mpld.make_params(node_budget=args.budget, flags=rule_flag)
     tune = None
     if not args.no_tune:
@@ -341,6 +352,7 @@ def main():
                    "k": layout.k, "node_budget": args.budget, "column_rule": args.column_rule,
                    "biconnected": bool(flags & mpld.MPLD_BICONNECTED),
                    "clique_bound": bool(flags & mpld.MPLD_CLIQUE_BOUND),
+                   "parallel_exact": bool(args.parallel_exact),
                    "instances": info.n_components,
                    "max_instance": info.max_component,
                    "removed_segments": info.n_removed_segments,
@@ -381,6 +393,8 @@ def main():
                        "work_ops_per_launch": res.work}
 
     if not args.no_e2e:
+        if dist:
+            from paper_2303_14335_gb300 import shard
         # end to end through the C ABI: host arrays in, host masks out
         e2e_t = []
         for i in range(args.warmup + args.steps):
@@ -398,16 +412,57 @@ def main():
             assert np.array_equal(masks2[0], mask)
         e2e_total = sum(e2e_t)
         if dist:
-            from paper_2303_14335_gb300 import shard
             _, e2e_total = shard.aggregate(dist, layout.n_seg, e2e_total, "cuda")
         # bytes copied per step: read-only blocks + descriptors + order up;
         # instance results + instance masks + status word down
         h2d = inf2.arena_bytes + 80 * inf2.n_components + 4 * inf2.n_components
         d2h = 32 * inf2.n_components + inf2.instance_segments + 4
-        out["e2e"] = {"value": all_segments * len(e2e_t) / e2e_total, "unit": "segments/s",
+        serial = {"value": all_segments * len(e2e_t) / e2e_total,
+                  "ms_per_step": 1000 * e2e_total / len(e2e_t),
+                  "form": "one layout at a time: mpld_build_matrix then mpld_solve_batch"}
+
+        # the same decompositions as a stream of K layouts through the
+        # server: host build, upload, search, copy-back and recovery of
+        # different layouts overlap (the form a user decomposing many
+        # layouts takes); every layout is still built, uploaded, searched,
+        # copied back and recovered inside the timed region
+        req_flags = flags & (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE |
+                             mpld.MPLD_BICONNECTED | mpld.MPLD_CLIQUE_BOUND)
+        cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
+                                      max_in_flight=max(args.steps, args.warmup, 1), streams=8,
+                                      warps_per_cta=tune.warps_per_cta if tune else 0)
+        srv = mpld.mpld_server_create(cfg, prm)
+
+        def stream_run(n):
+            t0 = time.perf_counter()
+            pending = {mpld.mpld_server_submit(srv, layout, flags=req_flags) for _ in range(n)}
+            got = []
+            while pending:
+                done = mpld.mpld_server_poll(srv)
+                for t in done:
+                    got.append(mpld.mpld_server_result(srv, t))
+                    pending.discard(t)
+                if not done:
+                    time.sleep(0.0002)
+            return time.perf_counter() - t0, got
+
+        stream_run(args.warmup)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_stream, got = stream_run(args.steps)
+        srv.close()
+        for rc3, m3, r3 in got:
+            assert rc3 == rc and np.array_equal(m3, mask) and r3.cost == res.cost
+        if dist:
+            _, t_stream = shard.aggregate(dist, layout.n_seg, t_stream, "cuda")
+        out["e2e"] = {"value": all_segments * args.steps / t_stream, "unit": "segments/s",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "ms_per_step": 1000 * e2e_total / len(e2e_t),
-                      "gpu_launches_per_step": 1}
+                      "ms_per_step": 1000 * t_stream / args.steps,
+                      "gpu_launches_per_step": 1,
+                      "form": f"{args.steps} layouts submitted together to the server API "
+                              "(mpld_server_submit / poll / result)",
+                      "serial": serial}
 
     if rank == 0 and not args.no_plain:
         # plain one-launch-per-instance path vs the batched one on a smaller
@@ -457,8 +512,10 @@ def main():
                                "sample": f"whole layout ({layout.n_seg} segments, "
                                          f"{ref.n_components} instances), one decomposition",
                                "nodes_per_s": ref.nodes / dt,
+                               # with split subtrees the node count depends on timing
                                "matches_gpu": bool(np.array_equal(ref.mask, mask) and
-                                                   ref.nodes == res.nodes)}
+                                                   ref.cost == res.cost and
+                                                   (args.parallel_exact or ref.nodes == res.nodes))}
     prob.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -832,6 +832,7 @@ extern "C" void mpld_free(mpld_problem *p) {
   if (!p) return;
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->d_base) cudaFree(p->d_base);
+  if (p->d_par) cudaFree(p->d_par);
   if (p->h_res) cudaFreeHost(p->h_res);
   if (p->h_masks) cudaFreeHost(p->h_masks);
   if (p->h_err) cudaFreeHost(p->h_err);
@@ -911,6 +912,68 @@ Shape with_team(Shape sh, int n_large) {
   return sh;
 }
 
+// Grid-wide split search of one instance: every warp of a full grid of
+// 8-warp CTAs takes subtrees of it.  Used when a launch holds that instance
+// alone (the plain path, a one-instance problem) and it fits the register
+// form.
+struct GridSplit {
+  bool on = false;
+  int slot = 0, ctas = 0;
+  size_t bytes = 0;
+};
+GridSplit grid_split_of(const mpld_problem *p, int c, const mpld_params *prm) {
+  GridSplit g;
+  const InstDesc &d = p->h_desc[c];
+  if (!par_of(prm) || d.n < PAR_MIN_SEGMENTS || !mpld::reg_fits(d.n, d.k)) return g;
+  g.slot = (int)mpld::align16(mpld::reg_layout(d.n, d.k, 0).bytes);
+  if (g.slot > mpld_internal_max_slot_bytes(CTA_TEAM_WARPS)) return g;
+  const int per_sm = std::max(1, mpld_internal_ctas_per_sm(CTA_TEAM_WARPS, g.slot));
+  g.ctas = per_sm * std::max(1, mpld_internal_num_sms());
+  g.bytes = mpld::par_layout(g.ctas * CTA_TEAM_WARPS, d.n).bytes;
+  g.on = true;
+  return g;
+}
+// Grow the problem's split-context buffer (outside any stream capture).
+int ensure_par_buf(mpld_problem *p, size_t bytes) {
+  if (bytes <= p->par_bytes) return MPLD_OK;
+  if (p->d_par) {
+    cudaFree(p->d_par);
+    p->d_par = nullptr;
+    p->par_bytes = 0;
+  }
+  if (cudaMalloc((void **)&p->d_par, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_par = nullptr;
+    return MPLD_E_OOM;
+  }
+  p->par_bytes = bytes;
+  return MPLD_OK;
+}
+// Reset the context (no incumbent, every warp key ~0, totals 0) and launch.
+int launch_grid_split(mpld_problem *p, int c, const GridSplit &g, const mpld_params *prm,
+                      cudaStream_t st) {
+  const int G = g.ctas * CTA_TEAM_WARPS;
+  const mpld::ParLayout PL = mpld::par_layout(G, p->h_desc[c].n);
+  int rc = cuda_ok(cudaMemsetAsync(p->d_par, 0xFF, PL.ctx + 8, st));
+  rc |= cuda_ok(cudaMemsetAsync(p->d_par + PL.ctx + 8, 0, PL.bestx - PL.ctx - 8, st));
+  if (rc) return MPLD_E_CUDA;
+  mpld::LaunchArgs a;
+  a.desc = p->d_desc + c;
+  a.order = nullptr;
+  a.n_inst = 1;
+  a.slot_bytes = g.slot;
+  a.queue = nullptr;
+  a.err = p->d_err;
+  a.budget = 0;
+  a.time_limit_ns = time_limit_ns(prm);
+  a.rule = rule_of(prm);
+  a.n_large = 0;
+  a.par = 2;
+  a.pad = 0;
+  a.par_buf = p->d_par;
+  return mpld_internal_launch(&a, g.ctas, CTA_TEAM_WARPS, st);
+}
+
 int launch_batch(const mpld::LaunchArgs &a, const Shape &sh, cudaStream_t st, uint32_t *queue,
                  int32_t *err) {
   int rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));   // both work counters
@@ -932,6 +995,8 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   if (!params_ok(prm)) return MPLD_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   mpld_problem *ps[1] = {p};
+  const GridSplit gs = p->n_comp == 1 ? grid_split_of(p, 0, prm) : GridSplit{};
+  if (gs.on && ensure_par_buf(p, gs.bytes) != MPLD_OK) return MPLD_E_OOM;
   const int n_large =
       count_large(p->n_comp, [&](int i) { return p->h_desc[p->h_order[i]].n; }, cta_min_of(prm));
   const Shape sh = with_team(pick_shape(ps, 1, prm), n_large);
@@ -948,10 +1013,16 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   a.n_large = n_large;
   a.par = par_of(prm);
   a.pad = 0;
+  a.par_buf = nullptr;
   auto body = [&]() -> int {
     int rc = cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
     if (rc) return rc;
-    rc = launch_batch(a, sh, st, p->d_queue, p->d_err);
+    if (gs.on) {
+      rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
+      rc |= launch_grid_split(p, 0, gs, prm, st);
+    } else {
+      rc = launch_batch(a, sh, st, p->d_queue, p->d_err);
+    }
     if (rc) return rc;
     if (copy_back) {
       if (p->n_comp)
@@ -965,7 +1036,13 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     return rc;
   };
   if (!capturable(stream)) return body();
-  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns, a.rule, a.n_large * 2 + a.par};
+  GraphKey key{sh.nw, sh.slot, sh.ctas, a.budget, a.time_limit_ns, a.rule, a.n_large * 4 + a.par};
+  if (gs.on) {
+    key.nw = CTA_TEAM_WARPS;
+    key.slot = gs.slot;
+    key.ctas = gs.ctas;
+    key.n_large = 2;
+  }
   key.ctas = copy_back ? sh.ctas : -sh.ctas;  // copy-back variant is a different graph
   if (!p->gexec || !(p->gkey == key) || p->gstream != stream) {
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
@@ -1096,7 +1173,18 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
   int rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
   rc |= cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
   const int maxslot = mpld_internal_max_slot_bytes(1);
+  size_t par_need = 0;
+  for (int c = 0; c < p->n_comp; ++c) {
+    const GridSplit g = grid_split_of(p, c, prm);
+    if (g.on) par_need = std::max(par_need, g.bytes);
+  }
+  if (rc == MPLD_OK && par_need) rc = ensure_par_buf(p, par_need);
   for (int c = 0; c < p->n_comp && rc == MPLD_OK; ++c) {
+    const GridSplit g = grid_split_of(p, c, prm);
+    if (g.on) {
+      rc = launch_grid_split(p, c, g, prm, st);
+      continue;
+    }
     mpld::LaunchArgs a;
     a.desc = p->d_desc + c;
     a.order = nullptr;
@@ -1115,6 +1203,7 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
     a.n_large = large ? 1 : 0;
     a.par = par_of(prm);
     a.pad = 0;
+    a.par_buf = nullptr;
     rc = mpld_internal_launch(&a, 1, large ? CTA_TEAM_WARPS : 1, st);
   }
   p->searched = rc == MPLD_OK;
@@ -1178,6 +1267,7 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   a.n_large = n_large;
   a.par = par_of(prm);
   a.pad = 0;
+  a.par_buf = nullptr;
   for (int i = 0; i < n; ++i) {
     if (i) rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_err, 0, 4, st));
     rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_res, 0xFF,

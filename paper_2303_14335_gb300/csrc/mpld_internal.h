@@ -191,9 +191,38 @@ struct LaunchArgs {
   int32_t rule;            // column rule: 0 fewest rows, 1 single row else BFS order
   int32_t n_large;         // the first n_large instances of the order are searched by whole
                            // CTAs (blocks 0..n_large-1 first; counter queue[1])
-  int32_t par;             // 1: those CTAs search exactly, their warps splitting subtrees
+  int32_t par;             // 1: those CTAs search exactly, their warps splitting subtrees;
+                           // 2: every warp of the grid splits the one instance desc[0]
   int32_t pad;
+  uint8_t *par_buf;        // par == 2: the split context in global memory (ParLayout)
 };
+
+// Shared state of a split exact search: the incumbent as one 64-bit key
+// (cost << 32 | subtree; ~0 = none), the next subtree to hand out, and
+// totals.  In shared memory for a CTA's warps, in global memory for a grid.
+struct ParCtx {
+  unsigned long long key;
+  unsigned long long nodes, work;
+  uint32_t next;
+  uint32_t timed_out;
+  uint32_t done;           // warps finished (grid form: the last one writes the result)
+  uint32_t pad;
+};
+
+// Global-memory block of the grid form for G warps and an n-segment
+// instance: each warp's best key, the context, each warp's best masks.
+struct ParLayout {
+  uint32_t wkey, ctx, bestx, row, bytes;
+};
+MPLD_HD ParLayout par_layout(int G, int n) {
+  ParLayout L;
+  L.wkey = 0;
+  L.ctx = (uint32_t)align16(8u * (uint32_t)G);
+  L.bestx = L.ctx + (uint32_t)align16(sizeof(ParCtx));
+  L.row = (uint32_t)align16((uint32_t)n);
+  L.bytes = L.bestx + (uint32_t)G * L.row;
+  return L;
+}
 
 }  // namespace mpld
 

@@ -60,6 +60,8 @@ struct mpld_problem {
   mpld::InstResult *d_res = nullptr;
   int8_t *d_masks = nullptr;
   uint32_t *d_queue = nullptr;
+  uint8_t *d_par = nullptr;           // grid-wide split search context (grown on demand)
+  size_t par_bytes = 0;
   int32_t *d_err = nullptr;
   // pinned host mirrors of the results
   mpld::InstResult *h_res = nullptr;

@@ -55,7 +55,11 @@ constexpr int32_t INF32 = 0x7FFFFFFF;
 constexpr uint32_t TMA_MIN_BYTES = 1024;     // smaller blocks use vector loads
 constexpr uint32_t WAIT_LIMIT = 1u << 22;    // bounded mbarrier wait
 constexpr uint32_t TEAM_BYTES = 320;          // a CTA team's reduction words and
-                                              // the parallel exact search's context
+                                              // the split exact search's context
+constexpr uint32_t PAR_CTX_OFF = 128;         // ParCtx (40 bytes)
+constexpr uint32_t PAR_WKEY_OFF = 176;        // each warp's best key (16 warps)
+static_assert(PAR_CTX_OFF + sizeof(ParCtx) <= PAR_WKEY_OFF && PAR_WKEY_OFF + 16 * 8 <= TEAM_BYTES,
+              "split-search context must fit the shared-memory head");
 
 // Dynamic shared memory of the batched kernel: the CTA team's reduction
 // words, one mbarrier per warp, then one slot per warp.
@@ -885,18 +889,14 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
 // subtree s improves it when (c, s) is smaller, so the answer is still the
 // first minimum-cost leaf of the whole tree, and a node is pruned when its
 // bound reaches cost* plus one if its subtree comes before the incumbent's.
-// Node counts depend on when each warp sees a better incumbent.
-struct ParCtx {
-  unsigned long long key;    // incumbent (cost << 32 | subtree); ~0 = none
-  unsigned long long nodes, work;
-  uint32_t next;             // next subtree to take
-  uint32_t timed_out;
-  unsigned long long wkey[16];   // each warp's own best
-};
-
+// Node counts depend on when each warp sees a better incumbent.  The G
+// warps are those of one CTA (context in shared memory) or of the whole grid
+// (context in global memory); a warp re-reads the shared key every 16 nodes
+// and keeps its own best masks at `bestx` and its best key at wkey[gw].
 template <typename FT, int MK, int RULE>
 __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
-                                        int lane, int warp, int nwarps, ParCtx *ctx) {
+                                        int lane, int gw, int G, ParCtx *ctx,
+                                        unsigned long long *wkey, int8_t *bestx) {
   constexpr uint32_t FB = 8 * sizeof(FT);
   constexpr uint32_t FLAG = 1u << (FB - 1);
   constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
@@ -911,7 +911,6 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
   uint32_t *deg = (uint32_t *)(base + R.deg);
   uint32_t *rec = (uint32_t *)(base + R.rec);
   uint16_t *sav = (uint16_t *)(base + R.sav);
-  int8_t *bestx = (int8_t *)(base + R.bestx);
   uint32_t rk = 0u;
   {
     const RoLayout Q = ro_layout(n, d.ne2, d.ns2);
@@ -940,19 +939,20 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
       if (RULE && lane * P + j < n) rk |= (uint32_t)__ldcg(rank + lane * P + j) << (8 * j);
   }
   __syncwarp();
-  // depth of the cut: about four subtrees per warp, never below the leaves
+  // depth of the cut: at least 16 subtrees per warp (the trees are skewed),
+  // never below the leaves
   int D = 0;
   uint32_t ns = 1;
-  while (ns < 4u * (uint32_t)nwarps && D < n) { ns *= (uint32_t)k; ++D; }
+  while (ns < 16u * (uint32_t)G && D < n) { ns *= (uint32_t)k; ++D; }
   int64_t nodes = 0, work = 0;
   uint32_t work32 = 0;
   bool timed_out = false;
-  unsigned long long my_key = ~0ull;
+  unsigned long long my_key = ~0ull, cached = ~0ull;
   const uint64_t t0 = globaltimer();
   int64_t next_check = 1024;
   // the pruning threshold for subtree s: a leaf must cost less than it
   auto threshold = [&](uint32_t s) -> int32_t {
-    const unsigned long long key = *(volatile unsigned long long *)&ctx->key;
+    const unsigned long long key = cached;
     if (key == ~0ull) return INF32;
     const int32_t c = (int32_t)(key >> 32);
     return c + (s < (uint32_t)(key & 0xFFFFFFFFull) ? 1 : 0);
@@ -986,6 +986,7 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
       const unsigned long long key = ((unsigned long long)(uint32_t)g << 32) | s;
       if (lane == 0) atomicMin(&ctx->key, key);
       my_key = key;
+      cached = key < cached ? key : cached;
 #pragma unroll
       for (int j = 0; j < P; ++j)
         if (lane * P + j < n) bestx[lane * P + j] = (int8_t)((xw >> (8 * j)) & 0xFFu);
@@ -998,6 +999,10 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
     int floor_level = D;
     for (;;) {
       if (enter) {
+        if ((nodes & 15) == 0) {
+          const unsigned long long kk = *(volatile unsigned long long *)&ctx->key;
+          cached = kk < cached ? kk : cached;
+        }
         ++nodes;
         work32 += 2u * (uint32_t)(n - level);
         if (nodes >= next_check) {
@@ -1168,7 +1173,7 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
     atomicAdd(&ctx->nodes, (unsigned long long)nodes);
     atomicAdd(&ctx->work, (unsigned long long)(work + work32));
     if (timed_out) atomicExch(&ctx->timed_out, 1u);
-    ctx->wkey[warp] = my_key;
+    wkey[gw] = my_key;
   }
   __syncwarp();
 }
@@ -1305,6 +1310,64 @@ __device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArg
   run_in<FT, MK, false>(d, d.scratch, d.ro, a, team);
 }
 
+// Every warp of the grid splits the one instance desc[0]; the last warp to
+// finish writes the result.
+__device__ __noinline__ void run_grid_split(const LaunchArgs &a, int lane, int warp, int nw,
+                                            uint8_t *mine) {
+  const InstDesc d = a.desc[0];
+  const int G = (int)gridDim.x * nw;
+  const int gw = (int)blockIdx.x * nw + warp;
+  const ParLayout PL = par_layout(G, d.n);
+  ParCtx *ctx = (ParCtx *)(a.par_buf + PL.ctx);
+  unsigned long long *wkey = (unsigned long long *)(a.par_buf + PL.wkey);
+  int8_t *bx = (int8_t *)(a.par_buf + PL.bestx + (size_t)gw * PL.row);
+  if (!reg_fits(d.n, d.k) || a.slot_bytes < (int)reg_layout(d.n, d.k, 0).bytes) {
+    // the host launches this form only for register-resident instances
+    if (threadIdx.x == 0) atomicExch(a.err, MPLD_E_STATE);
+    return;
+  }
+  if (d.k == 3) {
+    if (a.rule) par_search<uint8_t, 3, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+    else par_search<uint8_t, 3, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+  } else if (d.k == 4) {
+    if (a.rule) par_search<uint8_t, 4, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+    else par_search<uint8_t, 4, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+  } else if (d.k == 2) {
+    if (a.rule) par_search<uint8_t, 2, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+    else par_search<uint8_t, 2, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+  } else if (d.k <= 7) {
+    if (a.rule) par_search<uint8_t, 8, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+    else par_search<uint8_t, 8, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+  } else {
+    if (a.rule) par_search<uint16_t, 8, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+    else par_search<uint16_t, 8, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
+  }
+  // publish this warp's masks, key and totals, then count it finished
+  __threadfence();
+  __syncwarp();
+  uint32_t last = 0;
+  if (lane == 0) last = atomicAdd(&ctx->done, 1u) == (uint32_t)(G - 1) ? 1u : 0u;
+  last = __shfl_sync(FULL, last, 0);
+  if (last) {
+    __threadfence();
+    const unsigned long long key = *(volatile unsigned long long *)&ctx->key;
+    int win = -1;
+    for (int i = lane; i < G; i += 32)
+      if (__ldcg(wkey + i) == key) win = i;
+    win = __reduce_max_sync(FULL, (uint32_t)(win + 1)) - 1;
+    if (win >= 0) {
+      const int8_t *wb = (const int8_t *)(a.par_buf + PL.bestx + (size_t)win * PL.row);
+      for (int i = lane; i < d.n; i += 32) d.mask[i] = __ldcg(wb + i);
+    }
+    if (lane == 0) {
+      d.res->cost = key == ~0ull ? INT64_MAX : (int64_t)(key >> 32);
+      d.res->nodes = (int64_t)*(volatile unsigned long long *)&ctx->nodes;
+      d.res->status = *(volatile uint32_t *)&ctx->timed_out ? MPLD_TIMEOUT : MPLD_OK;
+      d.res->work = (int64_t)*(volatile unsigned long long *)&ctx->work;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -1322,6 +1385,11 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
   __syncwarp();
   uint32_t phase = 0;
 
+  if (a.par == 2) {
+    run_grid_split(a, lane, warp, nw, g_smem + slot_off);
+    return;
+  }
+
   // the first blocks search the large instances (the first n_large of the
   // order) as whole-CTA teams, taking them from the second work counter;
   // then they join the warps on the rest
@@ -1338,39 +1406,40 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
       const InstDesc d = a.desc[a.order ? a.order[t] : t];
       if (a.par && reg_fits(d.n, d.k) && a.slot_bytes >= (int)reg_layout(d.n, d.k, 0).bytes) {
         // exact search with the warps splitting the subtrees of one instance
-        ParCtx *ctx = (ParCtx *)(g_smem + 128);
+        ParCtx *ctx = (ParCtx *)(g_smem + PAR_CTX_OFF);
+        unsigned long long *wkey = (unsigned long long *)(g_smem + PAR_WKEY_OFF);
         if (threadIdx.x == 0) {
           ctx->key = ~0ull;
           ctx->nodes = 0;
           ctx->work = 0;
           ctx->next = 0;
           ctx->timed_out = 0;
+          ctx->done = 0;
         }
         __syncthreads();
         uint8_t *mine = g_smem + slot_off;
+        int8_t *bx = (int8_t *)(mine + reg_layout(d.n, d.k, 0).bestx);
         if (d.k == 3) {
-          if (a.rule) par_search<uint8_t, 3, 1>(d, mine, a, lane, warp, nw, ctx);
-          else par_search<uint8_t, 3, 0>(d, mine, a, lane, warp, nw, ctx);
+          if (a.rule) par_search<uint8_t, 3, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
+          else par_search<uint8_t, 3, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
         } else if (d.k == 4) {
-          if (a.rule) par_search<uint8_t, 4, 1>(d, mine, a, lane, warp, nw, ctx);
-          else par_search<uint8_t, 4, 0>(d, mine, a, lane, warp, nw, ctx);
+          if (a.rule) par_search<uint8_t, 4, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
+          else par_search<uint8_t, 4, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
         } else if (d.k == 2) {
-          if (a.rule) par_search<uint8_t, 2, 1>(d, mine, a, lane, warp, nw, ctx);
-          else par_search<uint8_t, 2, 0>(d, mine, a, lane, warp, nw, ctx);
+          if (a.rule) par_search<uint8_t, 2, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
+          else par_search<uint8_t, 2, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
         } else if (d.k <= 7) {
-          if (a.rule) par_search<uint8_t, 8, 1>(d, mine, a, lane, warp, nw, ctx);
-          else par_search<uint8_t, 8, 0>(d, mine, a, lane, warp, nw, ctx);
+          if (a.rule) par_search<uint8_t, 8, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
+          else par_search<uint8_t, 8, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
         } else {
-          if (a.rule) par_search<uint16_t, 8, 1>(d, mine, a, lane, warp, nw, ctx);
-          else par_search<uint16_t, 8, 0>(d, mine, a, lane, warp, nw, ctx);
+          if (a.rule) par_search<uint16_t, 8, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
+          else par_search<uint16_t, 8, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
         }
         __syncthreads();
         // the warp holding the winning leaf writes its masks
         const unsigned long long key = ctx->key;
-        if (ctx->wkey[warp] == key) {
-          const int8_t *bx = (const int8_t *)(mine + reg_layout(d.n, d.k, 0).bestx);
+        if (wkey[warp] == key)
           for (int i = lane; i < d.n; i += 32) d.mask[i] = bx[i];
-        }
         if (threadIdx.x == 0) {
           d.res->cost = key == ~0ull ? INT64_MAX : (int64_t)(key >> 32);
           d.res->nodes = (int64_t)ctx->nodes;
@@ -1582,6 +1651,7 @@ __global__ void __launch_bounds__(32, 1)
   a.n_large = 0;
   a.par = 0;
   a.pad = 0;
+  a.par_buf = nullptr;
   uint32_t phase = 0;
   const uint32_t slot_off = align16(8u);
   if (d.k == 3) run_instance<uint8_t, 3>(d, slot_off, slot_bytes, bar, phase, a, lane);

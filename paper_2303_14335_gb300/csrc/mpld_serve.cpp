@@ -293,6 +293,7 @@ int launch_request(mpld_server *s, Req &r) {
   a.n_large = n_large;
   a.par = 0;
   a.pad = 0;
+  a.par_buf = nullptr;
   rc = mpld_internal_launch(&a, ctas, nw, st);
   if (rc) return rc;
   rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_res, d_res, sizeof(InstResult) * (size_t)C,

@@ -438,6 +438,24 @@ def test_split_search_beside_unsplit_large_instances(stream):
     assert_same_answer(gpu_run(L, flags=SINGLE, stream=stream.cuda_stream, search_flags=PAR), ref, L)
 
 
+def test_split_search_repeated_calls(stream):
+    # one handle, the grid-wide form replayed from its captured graph, with
+    # searches of the other forms in between
+    L = synth.random_graph(20, 3, seed=923, p_edge=0.5, n_stitch=5, identity_polygons=False)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE)
+    prob = mpld.mpld_build_matrix(L, mpld.make_params(flags=SINGLE), stream.cuda_stream)
+    try:
+        for sf in (PAR, PAR, 0, PAR, PAR | BFS, PAR):
+            rc, masks, ress = mpld.mpld_solve_batch([prob], mpld.make_params(flags=sf), stream.cuda_stream)
+            if sf & BFS:
+                continue
+            assert rc == mpld.MPLD_OK and np.array_equal(masks[0], ref.mask) and ress[0].cost == ref.cost
+            if not sf:
+                assert ress[0].nodes == ref.nodes
+    finally:
+        prob.close()
+
+
 def test_split_search_time_limit(stream):
     # 5 ms against a tree of about 5e8 nodes: every warp stops by itself and
     # the incumbent is a consistent layout
