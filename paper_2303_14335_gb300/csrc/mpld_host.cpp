@@ -936,6 +936,11 @@ GridSplit grid_split_of(const mpld_problem *p, int c, const mpld_params *prm) {
 // Grow the problem's split-context buffer (outside any stream capture).
 int ensure_par_buf(mpld_problem *p, size_t bytes) {
   if (bytes <= p->par_bytes) return MPLD_OK;
+  p->queue_ready = false;
+  if (p->gexec) {   // a captured graph may hold the old buffer's address
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
   if (p->d_par) {
     cudaFree(p->d_par);
     p->d_par = nullptr;
@@ -974,6 +979,80 @@ int launch_grid_split(mpld_problem *p, int c, const GridSplit &g, const mpld_par
   return mpld_internal_launch(&a, g.ctas, CTA_TEAM_WARPS, st);
 }
 
+// Split-search queue of a batched problem: the PAR_QUEUE_MAX largest
+// instances of at least PAR_MIN_SEGMENTS segments that fit the register form
+// are split by every warp of the grid, one after another, in a launch before
+// the batched one; the batched launch takes the rest (its own order, with the
+// other split instances on CTAs).  Device block: 64-byte contexts, the
+// queue's instance indices, the rest of the largest-first order.
+constexpr int PAR_QUEUE_MAX = 16;
+struct QueuePlan {
+  int nq = 0, slot = 0, ctas = 0;
+  std::vector<int32_t> idx, rest;
+  size_t o_idx = 0, o_rest = 0, bytes = 0;
+};
+QueuePlan queue_plan_of(const mpld_problem *p, const mpld_params *prm) {
+  QueuePlan q;
+  if (!par_of(prm) || p->n_comp < 2) return q;
+  const int maxslot = mpld_internal_max_slot_bytes(CTA_TEAM_WARPS);
+  for (int i = 0; i < p->n_comp; ++i) {
+    const int c = p->h_order[i];
+    const InstDesc &d = p->h_desc[c];
+    bool queued = false;
+    if ((int)q.idx.size() < PAR_QUEUE_MAX && d.n >= PAR_MIN_SEGMENTS && mpld::reg_fits(d.n, d.k)) {
+      const int sl = (int)mpld::align16(mpld::reg_layout(d.n, d.k, 0).bytes);
+      if (sl <= maxslot) {
+        q.idx.push_back(c);
+        q.slot = std::max(q.slot, sl);
+        queued = true;
+      }
+    }
+    if (!queued) q.rest.push_back(c);
+  }
+  q.nq = (int)q.idx.size();
+  if (!q.nq) return QueuePlan{};
+  const int per_sm = std::max(1, mpld_internal_ctas_per_sm(CTA_TEAM_WARPS, q.slot));
+  q.ctas = per_sm * std::max(1, mpld_internal_num_sms());
+  q.o_idx = (64u * (size_t)q.nq + 255) & ~(size_t)255;
+  q.o_rest = (q.o_idx + 4u * (size_t)q.nq + 255) & ~(size_t)255;
+  q.bytes = q.o_rest + 4u * std::max<size_t>(q.rest.size(), 1);
+  return q;
+}
+// Make the queue's device block ready (outside any stream capture).
+int ensure_queue(mpld_problem *p, const QueuePlan &q) {
+  if (ensure_par_buf(p, q.bytes) != MPLD_OK) return MPLD_E_OOM;
+  if (p->queue_ready) return MPLD_OK;
+  int rc = cuda_ok(cudaMemcpy(p->d_par + q.o_idx, q.idx.data(), 4u * q.idx.size(),
+                              cudaMemcpyHostToDevice));
+  if (!q.rest.empty())
+    rc |= cuda_ok(cudaMemcpy(p->d_par + q.o_rest, q.rest.data(), 4u * q.rest.size(),
+                             cudaMemcpyHostToDevice));
+  if (rc) return MPLD_E_CUDA;
+  p->queue_ready = true;
+  return MPLD_OK;
+}
+// Reset the queue's contexts (no incumbent, totals 0) and launch it.
+int launch_queue(mpld_problem *p, const QueuePlan &q, const mpld_params *prm, cudaStream_t st) {
+  int rc = cuda_ok(cudaMemsetAsync(p->d_par, 0, 64u * (size_t)q.nq, st));
+  rc |= cuda_ok(cudaMemset2DAsync(p->d_par, 64, 0xFF, 8, (size_t)q.nq, st));   // keys
+  if (rc) return MPLD_E_CUDA;
+  mpld::LaunchArgs a;
+  a.desc = p->d_desc;
+  a.order = (const int32_t *)(p->d_par + q.o_idx);
+  a.n_inst = q.nq;
+  a.slot_bytes = q.slot;
+  a.queue = nullptr;
+  a.err = p->d_err;
+  a.budget = 0;
+  a.time_limit_ns = time_limit_ns(prm);
+  a.rule = rule_of(prm);
+  a.n_large = 0;
+  a.par = 3;
+  a.pad = 0;
+  a.par_buf = p->d_par;
+  return mpld_internal_launch(&a, q.ctas, CTA_TEAM_WARPS, st);
+}
+
 int launch_batch(const mpld::LaunchArgs &a, const Shape &sh, cudaStream_t st, uint32_t *queue,
                  int32_t *err) {
   int rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));   // both work counters
@@ -997,13 +1076,22 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   mpld_problem *ps[1] = {p};
   const GridSplit gs = p->n_comp == 1 ? grid_split_of(p, 0, prm) : GridSplit{};
   if (gs.on && ensure_par_buf(p, gs.bytes) != MPLD_OK) return MPLD_E_OOM;
-  const int n_large =
-      count_large(p->n_comp, [&](int i) { return p->h_desc[p->h_order[i]].n; }, cta_min_of(prm));
+  // the largest split instances go to the queue launch; the batched launch
+  // then takes the rest in its own order
+  const QueuePlan qp = gs.on ? QueuePlan{} : queue_plan_of(p, prm);
+  if (qp.nq) {
+    const int qrc = ensure_queue(p, qp);
+    if (qrc) return qrc;
+  }
+  const int n_rest = qp.nq ? (int)qp.rest.size() : p->n_comp;
+  const int n_large = qp.nq
+      ? count_large(n_rest, [&](int i) { return p->h_desc[qp.rest[i]].n; }, cta_min_of(prm))
+      : count_large(p->n_comp, [&](int i) { return p->h_desc[p->h_order[i]].n; }, cta_min_of(prm));
   const Shape sh = with_team(pick_shape(ps, 1, prm), n_large);
   mpld::LaunchArgs a;
   a.desc = p->d_desc;
-  a.order = p->d_order;
-  a.n_inst = p->n_comp;
+  a.order = qp.nq ? (const int32_t *)(p->d_par + qp.o_rest) : p->d_order;
+  a.n_inst = n_rest;
   a.slot_bytes = sh.slot;
   a.queue = p->d_queue;
   a.err = p->d_err;
@@ -1020,6 +1108,14 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     if (gs.on) {
       rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
       rc |= launch_grid_split(p, 0, gs, prm, st);
+    } else if (qp.nq) {
+      rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
+      rc |= cuda_ok(cudaMemsetAsync(p->d_queue, 0, 8, st));
+      rc |= launch_queue(p, qp, prm, st);
+      if (rc == MPLD_OK && n_rest > 0) {
+        const int ctas = std::min(sh.ctas, n_large + (n_rest - n_large + sh.nw - 1) / sh.nw);
+        rc = mpld_internal_launch(&a, std::max(ctas, 1), sh.nw, st);
+      }
     } else {
       rc = launch_batch(a, sh, st, p->d_queue, p->d_err);
     }
@@ -1043,7 +1139,10 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     key.ctas = gs.ctas;
     key.n_large = 2;
   }
-  key.ctas = copy_back ? sh.ctas : -sh.ctas;  // copy-back variant is a different graph
+  key.queue_ctas = qp.ctas;
+  key.queue_slot = qp.slot;
+  const int kc = gs.on ? gs.ctas : sh.ctas;
+  key.ctas = copy_back ? kc : -kc;  // copy-back variant is a different graph
   if (!p->gexec || !(p->gkey == key) || p->gstream != stream) {
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
     cudaGraph_t graph = nullptr;

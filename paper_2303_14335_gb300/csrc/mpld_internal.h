@@ -205,9 +205,10 @@ struct ParCtx {
   unsigned long long nodes, work;
   uint32_t next;
   uint32_t timed_out;
-  uint32_t done;           // warps finished (grid form: the last one writes the result)
+  uint32_t done;           // warps (or, in the queue, subtrees) finished
   uint32_t pad;
 };
+static_assert(sizeof(ParCtx) <= 64, "queue contexts are 64 bytes apart");
 
 // Global-memory block of the grid form for G warps and an n-segment
 // instance: each warp's best key, the context, each warp's best masks.

@@ -18,9 +18,11 @@ struct GraphKey {
   int nw = 0, slot = 0, ctas = 0;
   int64_t budget = 0, tl = 0;
   int rule = 0, n_large = 0;
+  int queue_ctas = 0, queue_slot = 0;  // the split-search queue launch before it (0 = none)
   bool operator==(const GraphKey &o) const {
     return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl &&
-           rule == o.rule && n_large == o.n_large;
+           rule == o.rule && n_large == o.n_large && queue_ctas == o.queue_ctas &&
+           queue_slot == o.queue_slot;
   }
 };
 
@@ -62,6 +64,7 @@ struct mpld_problem {
   uint32_t *d_queue = nullptr;
   uint8_t *d_par = nullptr;           // grid-wide split search context (grown on demand)
   size_t par_bytes = 0;
+  bool queue_ready = false;           // the queue's index arrays are in d_par
   int32_t *d_err = nullptr;
   // pinned host mirrors of the results
   mpld::InstResult *h_res = nullptr;

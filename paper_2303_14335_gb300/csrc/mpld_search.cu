@@ -891,12 +891,32 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
 // bound reaches cost* plus one if its subtree comes before the incumbent's.
 // Node counts depend on when each warp sees a better incumbent.  The G
 // warps are those of one CTA (context in shared memory) or of the whole grid
-// (context in global memory); a warp re-reads the shared key every 16 nodes
-// and keeps its own best masks at `bestx` and its best key at wkey[gw].
+// (context in global memory); a warp re-reads the shared key every 16 nodes.
+// Modes:
+//   PAR_OWN    each warp keeps its best masks at `bestx` and, at the end, its
+//              best key at wkey[gw] and its totals in the context;
+//   PAR_QUEUE  totals are published after every subtree, then the subtree
+//              is counted done; returns true in the warp that completes the
+//              last one (it then recovers the masks by a replay);
+//   PAR_REPLAY searches subtree s* alone with the bound of `replay_key`
+//              (cost* << 32 | s* + 1, so leaves of cost <= cost* are taken)
+//              and writes the first leaf it takes to d.mask: the first leaf
+//              of cost cost* in s*, which is the split search's answer.
+constexpr int PAR_OWN = 0, PAR_QUEUE = 1, PAR_REPLAY = 2;
+
+// Subtrees of the split search for G warps: k^D for the first depth D with
+// k^D >= 16 G (the trees are skewed), never below the leaves.
+__device__ __forceinline__ void par_cut(int n, int k, int G, int &D, uint32_t &ns) {
+  D = 0;
+  ns = 1;
+  while (ns < 16u * (uint32_t)G && D < n) { ns *= (uint32_t)k; ++D; }
+}
+
 template <typename FT, int MK, int RULE>
-__device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
+__device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
                                         int lane, int gw, int G, ParCtx *ctx,
-                                        unsigned long long *wkey, int8_t *bestx) {
+                                        unsigned long long *wkey, int8_t *bestx, int mode,
+                                        unsigned long long replay_key) {
   constexpr uint32_t FB = 8 * sizeof(FT);
   constexpr uint32_t FLAG = 1u << (FB - 1);
   constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
@@ -939,15 +959,13 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
       if (RULE && lane * P + j < n) rk |= (uint32_t)__ldcg(rank + lane * P + j) << (8 * j);
   }
   __syncwarp();
-  // depth of the cut: at least 16 subtrees per warp (the trees are skewed),
-  // never below the leaves
-  int D = 0;
-  uint32_t ns = 1;
-  while (ns < 16u * (uint32_t)G && D < n) { ns *= (uint32_t)k; ++D; }
-  int64_t nodes = 0, work = 0;
+  int D;
+  uint32_t ns;
+  par_cut(n, k, G, D, ns);
+  int64_t nodes = 0, work = 0, nodes_pub = 0;
   uint32_t work32 = 0;
-  bool timed_out = false;
-  unsigned long long my_key = ~0ull, cached = ~0ull;
+  bool timed_out = false, last_item = false;
+  unsigned long long my_key = ~0ull, cached = mode == PAR_REPLAY ? replay_key : ~0ull;
   const uint64_t t0 = globaltimer();
   int64_t next_check = 1024;
   // the pruning threshold for subtree s: a leaf must cost less than it
@@ -957,11 +975,19 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
     const int32_t c = (int32_t)(key >> 32);
     return c + (s < (uint32_t)(key & 0xFFFFFFFFull) ? 1 : 0);
   };
-  for (;;) {
+  for (bool first_pass = true;; first_pass = false) {
     uint32_t s = 0;
-    if (lane == 0) s = atomicAdd(&ctx->next, 1u);
-    s = __shfl_sync(FULL, s, 0);
-    if (s >= ns || timed_out) break;
+    if (mode == PAR_REPLAY) {
+      if (!first_pass) break;
+      s = (uint32_t)(replay_key & 0xFFFFFFFFull) - 1u;
+    } else {
+      if (lane == 0) s = atomicAdd(&ctx->next, 1u);
+      s = __shfl_sync(FULL, s, 0);
+    }
+    if (s >= ns) break;
+    // a timed-out warp stops, except in the queue, where it still counts
+    // the subtrees it takes as done
+    if (timed_out && mode != PAR_QUEUE) break;
     // fresh state for the subtree
     uint32_t w = 0u, xw = 0xFFFFFFFFu;
     uint32_t cc[NC], sc[NC];
@@ -984,12 +1010,15 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
     // a leaf of cost g in subtree s
     auto take_leaf = [&]() {
       const unsigned long long key = ((unsigned long long)(uint32_t)g << 32) | s;
-      if (lane == 0) atomicMin(&ctx->key, key);
+      if (lane == 0 && mode != PAR_REPLAY) atomicMin(&ctx->key, key);
       my_key = key;
       cached = key < cached ? key : cached;
+      int8_t *dst = mode == PAR_REPLAY ? d.mask : bestx;
+      if (dst) {
 #pragma unroll
-      for (int j = 0; j < P; ++j)
-        if (lane * P + j < n) bestx[lane * P + j] = (int8_t)((xw >> (8 * j)) & 0xFFu);
+        for (int j = 0; j < P; ++j)
+          if (lane * P + j < n) dst[lane * P + j] = (int8_t)((xw >> (8 * j)) & 0xFFu);
+      }
       __syncwarp();
     };
     uint32_t digits = s;   // the prefix, most significant digit first
@@ -997,9 +1026,10 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
     bool skip = false, done = false;
     bool enter = true;
     int floor_level = D;
+    if (!timed_out)
     for (;;) {
       if (enter) {
-        if ((nodes & 15) == 0) {
+        if (mode != PAR_REPLAY && (nodes & 15) == 0) {
           const unsigned long long kk = *(volatile unsigned long long *)&ctx->key;
           cached = kk < cached ? kk : cached;
         }
@@ -1010,7 +1040,10 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
           work += work32;
           work32 = 0;
           const uint64_t now = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
-          if ((int64_t)(now - t0) > a.time_limit_ns) { timed_out = true; break; }
+          if (mode != PAR_REPLAY && (int64_t)(now - t0) > a.time_limit_ns) {
+            timed_out = true;
+            break;
+          }
         }
         const int32_t thr = threshold(s);
         uint32_t key = 0xFFFFFFFFu;
@@ -1031,7 +1064,7 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
           if (level < D && (digits % (top * (uint32_t)k)) != 0u) { skip = true; break; }
           if (g < thr) {
             take_leaf();
-            if (g == 0) { done = true; break; }
+            if (g == 0 || mode == PAR_REPLAY) { done = true; break; }
           }
           if (level <= floor_level) { done = true; break; }
           enter = false;
@@ -1168,14 +1201,49 @@ __device__ __noinline__ void par_search(const InstDesc &d, uint8_t *base, const 
     }
     (void)skip;
     (void)done;
+    if (mode == PAR_QUEUE) {
+      // publish this subtree's totals, then count it done
+      work += work32;
+      work32 = 0;
+      uint32_t fin = 0;
+      if (lane == 0) {
+        atomicAdd(&ctx->nodes, (unsigned long long)(nodes - nodes_pub));
+        atomicAdd(&ctx->work, (unsigned long long)work);
+        if (timed_out) atomicExch(&ctx->timed_out, 1u);
+        __threadfence();
+        fin = atomicAdd(&ctx->done, 1u) == ns - 1u ? 1u : 0u;
+      }
+      nodes_pub = nodes;
+      work = 0;
+      if (__shfl_sync(FULL, fin, 0)) last_item = true;
+    }
   }
-  if (lane == 0) {
-    atomicAdd(&ctx->nodes, (unsigned long long)nodes);
-    atomicAdd(&ctx->work, (unsigned long long)(work + work32));
-    if (timed_out) atomicExch(&ctx->timed_out, 1u);
-    wkey[gw] = my_key;
+  if (mode == PAR_OWN) {
+    if (lane == 0) {
+      atomicAdd(&ctx->nodes, (unsigned long long)nodes);
+      atomicAdd(&ctx->work, (unsigned long long)(work + work32));
+      if (timed_out) atomicExch(&ctx->timed_out, 1u);
+      wkey[gw] = my_key;
+    }
   }
   __syncwarp();
+  return last_item;
+}
+
+// par_search for the instance's field width, mask count and column rule.
+__device__ __noinline__ bool par_dispatch(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
+                                          int lane, int gw, int G, ParCtx *ctx,
+                                          unsigned long long *wkey, int8_t *bestx, int mode,
+                                          unsigned long long replay_key) {
+#define MPLD_PAR(FT, MK)                                                                        \
+  return a.rule ? par_search<FT, MK, 1>(d, base, a, lane, gw, G, ctx, wkey, bestx, mode, replay_key) \
+                : par_search<FT, MK, 0>(d, base, a, lane, gw, G, ctx, wkey, bestx, mode, replay_key)
+  if (d.k == 3) { MPLD_PAR(uint8_t, 3); }
+  if (d.k == 4) { MPLD_PAR(uint8_t, 4); }
+  if (d.k == 2) { MPLD_PAR(uint8_t, 2); }
+  if (d.k <= 7) { MPLD_PAR(uint8_t, 8); }
+  MPLD_PAR(uint16_t, 8);
+#undef MPLD_PAR
 }
 
 // Initialise the state at `base` and search.  SM says at compile time
@@ -1310,6 +1378,43 @@ __device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArg
   run_in<FT, MK, false>(d, d.scratch, d.ro, a, team);
 }
 
+// Every warp of the grid splits the instances desc[order[0..n_inst)] one
+// after another: a warp takes subtrees of the first instance that still has
+// some.  Contexts are 64 bytes apart in par_buf.  The warp that completes an
+// instance's last subtree replays the winning subtree to write its masks,
+// then writes its result.
+__device__ __noinline__ void run_grid_queue(const LaunchArgs &a, int lane, int warp, int nw,
+                                            uint8_t *mine) {
+  const int G = (int)gridDim.x * nw;
+  const int gw = (int)blockIdx.x * nw + warp;
+  for (int j = 0; j < a.n_inst; ++j) {
+    const InstDesc d = a.desc[a.order[j]];
+    ParCtx *ctx = (ParCtx *)(a.par_buf + (size_t)j * 64);
+    int D;
+    uint32_t ns;
+    par_cut(d.n, d.k, G, D, ns);
+    if (*(volatile uint32_t *)&ctx->next >= ns) continue;   // all handed out
+    if (!reg_fits(d.n, d.k) || a.slot_bytes < (int)reg_layout(d.n, d.k, 0).bytes) {
+      // the host queues only register-resident instances
+      if (lane == 0) atomicExch(a.err, MPLD_E_STATE);
+      return;
+    }
+    if (!par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_QUEUE, 0ull)) continue;
+    __threadfence();
+    const unsigned long long key = *(volatile unsigned long long *)&ctx->key;
+    if (key != ~0ull)
+      par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_REPLAY,
+                   (key & ~0xFFFFFFFFull) | ((key & 0xFFFFFFFFull) + 1ull));
+    if (lane == 0) {
+      d.res->cost = key == ~0ull ? INT64_MAX : (int64_t)(key >> 32);
+      d.res->nodes = (int64_t)*(volatile unsigned long long *)&ctx->nodes;
+      d.res->status = *(volatile uint32_t *)&ctx->timed_out ? MPLD_TIMEOUT : MPLD_OK;
+      d.res->work = (int64_t)*(volatile unsigned long long *)&ctx->work;
+    }
+    __syncwarp();
+  }
+}
+
 // Every warp of the grid splits the one instance desc[0]; the last warp to
 // finish writes the result.
 __device__ __noinline__ void run_grid_split(const LaunchArgs &a, int lane, int warp, int nw,
@@ -1326,22 +1431,7 @@ __device__ __noinline__ void run_grid_split(const LaunchArgs &a, int lane, int w
     if (threadIdx.x == 0) atomicExch(a.err, MPLD_E_STATE);
     return;
   }
-  if (d.k == 3) {
-    if (a.rule) par_search<uint8_t, 3, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-    else par_search<uint8_t, 3, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-  } else if (d.k == 4) {
-    if (a.rule) par_search<uint8_t, 4, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-    else par_search<uint8_t, 4, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-  } else if (d.k == 2) {
-    if (a.rule) par_search<uint8_t, 2, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-    else par_search<uint8_t, 2, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-  } else if (d.k <= 7) {
-    if (a.rule) par_search<uint8_t, 8, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-    else par_search<uint8_t, 8, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-  } else {
-    if (a.rule) par_search<uint16_t, 8, 1>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-    else par_search<uint16_t, 8, 0>(d, mine, a, lane, gw, G, ctx, wkey, bx);
-  }
+  par_dispatch(d, mine, a, lane, gw, G, ctx, wkey, bx, PAR_OWN, 0ull);
   // publish this warp's masks, key and totals, then count it finished
   __threadfence();
   __syncwarp();
@@ -1389,6 +1479,10 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
     run_grid_split(a, lane, warp, nw, g_smem + slot_off);
     return;
   }
+  if (a.par == 3) {
+    run_grid_queue(a, lane, warp, nw, g_smem + slot_off);
+    return;
+  }
 
   // the first blocks search the large instances (the first n_large of the
   // order) as whole-CTA teams, taking them from the second work counter;
@@ -1419,22 +1513,7 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
         __syncthreads();
         uint8_t *mine = g_smem + slot_off;
         int8_t *bx = (int8_t *)(mine + reg_layout(d.n, d.k, 0).bestx);
-        if (d.k == 3) {
-          if (a.rule) par_search<uint8_t, 3, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-          else par_search<uint8_t, 3, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-        } else if (d.k == 4) {
-          if (a.rule) par_search<uint8_t, 4, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-          else par_search<uint8_t, 4, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-        } else if (d.k == 2) {
-          if (a.rule) par_search<uint8_t, 2, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-          else par_search<uint8_t, 2, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-        } else if (d.k <= 7) {
-          if (a.rule) par_search<uint8_t, 8, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-          else par_search<uint8_t, 8, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-        } else {
-          if (a.rule) par_search<uint16_t, 8, 1>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-          else par_search<uint16_t, 8, 0>(d, mine, a, lane, warp, nw, ctx, wkey, bx);
-        }
+        par_dispatch(d, mine, a, lane, warp, nw, ctx, wkey, bx, PAR_OWN, 0ull);
         __syncthreads();
         // the warp holding the winning leaf writes its masks
         const unsigned long long key = ctx->key;

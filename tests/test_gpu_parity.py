@@ -421,6 +421,36 @@ def test_split_search_layouts(n, k, deg, ps, seed, stream):
                                        search_flags=PAR | sf), ref, L)
 
 
+def test_split_search_queue_and_cta_forms(stream):
+    # 19 instances of 16+ segments: the 16 largest go to the grid-wide queue
+    # (one after another, masks recovered by replaying the winning subtree),
+    # the other 3 to CTAs in the batched launch, the rest to warps
+    L = synth.unit_disk_layout(9000, 3, seed=16, mean_deg=2.35, p_stitch=0.2)
+    for fl, ofl, sf in ((0, 0, 0), (CQ, oracle.CLIQUE_BOUND, 0), (0, oracle.COLUMN_BFS, BFS)):
+        ref = oracle.decompose(L, flags=ofl, budget=0, nthreads=NTHREADS)
+        sizes = np.bincount(ref.comp_of[ref.comp_of >= 0], minlength=ref.n_components)
+        assert (sizes >= 16).sum() == 19
+        for warps in (0, 16):
+            assert_same_answer(gpu_run(L, flags=fl, stream=stream.cuda_stream, warps=warps,
+                                       search_flags=PAR | sf), ref, L)
+
+
+def test_split_search_several_problems(stream):
+    # a batch of several layouts: the split instances go to CTAs
+    Ls = [synth.unit_disk_layout(1000, 3, seed=5, mean_deg=2.6, p_stitch=0.2),
+          synth.unit_disk_layout(5000, 3, seed=12, mean_deg=2.4, p_stitch=0.2)]
+    probs = [mpld.mpld_build_matrix(L, None, stream.cuda_stream) for L in Ls]
+    try:
+        rc, masks, ress = mpld.mpld_solve_batch(probs, mpld.make_params(flags=PAR), stream.cuda_stream)
+        assert rc == mpld.MPLD_OK
+        for L, m, r in zip(Ls, masks, ress):
+            ref = oracle.decompose(L, budget=0, nthreads=NTHREADS)
+            assert np.array_equal(m, ref.mask) and r.cost == ref.cost
+    finally:
+        for p in probs:
+            p.close()
+
+
 def test_split_search_beside_unsplit_large_instances(stream):
     # a 200-segment ring (k = 3) and a 70-segment ring at k = 8 do not fit the
     # register form: whole-CTA search, while the 20-segment graph is split
