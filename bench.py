@@ -428,9 +428,10 @@ def main():
         # copied back and recovered inside the timed region
         req_flags = flags & (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE |
                              mpld.MPLD_BICONNECTED | mpld.MPLD_CLIQUE_BOUND)
+        # the server's own launch shape (small CTAs, so that launches of
+        # different layouts share the SMs)
         cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
-                                      max_in_flight=max(args.steps, args.warmup, 1), streams=8,
-                                      warps_per_cta=tune.warps_per_cta if tune else 0)
+                                      max_in_flight=max(args.steps, args.warmup, 1), streams=8)
         srv = mpld.mpld_server_create(cfg, prm)
 
         def stream_run(n):

@@ -78,6 +78,18 @@ void unite_min(std::vector<int32_t> &parent, int a, int b) {
 // then each (short) bucket is sorted and deduplicated.
 bool normalise(int n, int m, const int32_t *u, const int32_t *v, std::vector<int32_t> &ou,
                std::vector<int32_t> &ov) {
+  // input already in that form (u < v, strictly ascending pairs): copied as is
+  bool sorted = true;
+  for (int e = 0; e < m && sorted; ++e) {
+    const int a = u[e], b = v[e];
+    sorted = a >= 0 && a < b && b < n &&
+             (e == 0 || a > u[e - 1] || (a == u[e - 1] && b > v[e - 1]));
+  }
+  if (sorted) {
+    ou.assign(u, u + m);
+    ov.assign(v, v + m);
+    return true;
+  }
   std::vector<int32_t> start((size_t)n + 1, 0);
   for (int e = 0; e < m; ++e) {
     const int a = u[e], b = v[e];
@@ -476,21 +488,27 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       // the conflict adjacency with each neighbour replaced by its unit
       std::vector<int32_t> uadj(p->cadj.size());
       parallel_for((int)p->cadj.size(), 1 << 16, [&](int i) { uadj[i] = p->unit_of[p->cadj[i]]; });
+      // each unit's state from its own segments (units in parallel), and
+      // whether it starts in the queue
       std::vector<int32_t> st((size_t)n, CAN);
-      for (int s = 0; s < n; ++s) {
-        const int a = p->unit_of[s];
-        for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
-          if (uadj[i] == a) st[a] &= ~CAN;   // a conflict edge inside the unit
-          else st[a]++;
+      std::vector<uint8_t> first((size_t)n, 0);
+      parallel_for(n, 1 << 14, [&](int u) {
+        int32_t x = CAN;
+        for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) {
+          const int s = p->useg[t];
+          for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
+            if (uadj[i] == u) x &= ~CAN;   // a conflict edge inside the unit
+            else x++;
+          }
         }
-      }
+        const bool q = p->uptr[u + 1] > p->uptr[u] && (x & CAN) && (x & DEG) < k;
+        st[u] = q ? x & ~CAN : x;
+        first[u] = q ? 1 : 0;
+      });
       std::vector<int32_t> &queue = p->removed_order;
       queue.reserve((size_t)n);
       for (int u = 0; u < n; ++u)
-        if (p->unit_of[u] == u && (st[u] & CAN) && (st[u] & DEG) < k) {
-          queue.push_back(u);
-          st[u] &= ~CAN;
-        }
+        if (first[u]) queue.push_back(u);
       // the queue is the removal order; a removed unit's degree is never
       // read again, so its neighbours may still decrement it
       for (size_t h = 0; h < queue.size(); ++h) {

@@ -130,6 +130,38 @@ def test_packed_matrices_of_components():
         assert np.array_equal(mpld.mpld_export_matrix(prob, c), oracle.export_matrix(len(segs), 3, cc))
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_edge_order_and_duplicates_do_not_matter(seed):
+    # sorted input takes a copy-only path; shuffled, reversed and repeated
+    # edges go through the bucket sort: the built problems are the same
+    import dataclasses
+    L = synth.unit_disk_layout(3000, 3, seed=seed, mean_deg=3.5, p_stitch=0.3)
+    rng = np.random.default_rng(seed)
+
+    def scramble(u, v):
+        u, v = u.copy(), v.copy()
+        flip = rng.random(len(u)) < 0.5
+        u[flip], v[flip] = v[flip].copy(), u[flip].copy()
+        dup = rng.random(len(u)) < 0.1
+        u, v = np.concatenate([u, v[dup]]), np.concatenate([v, u[dup]])
+        perm = rng.permutation(len(u))
+        return u[perm].astype(np.int32), v[perm].astype(np.int32)
+
+    cu, cv = scramble(L.conf_u, L.conf_v)
+    su, sv = scramble(L.st_u, L.st_v)
+    M = dataclasses.replace(L, conf_u=cu, conf_v=cv, st_u=su, st_v=sv)
+    a, b = host_only(L), host_only(M)
+    ia, ib = mpld.mpld_problem_info(a), mpld.mpld_problem_info(b)
+    assert (ia.n_components, ia.arena_bytes, ia.instance_segments) == \
+        (ib.n_components, ib.arena_bytes, ib.instance_segments)
+    assert np.array_equal(mpld.mpld_component_results(a, results=False)[3],
+                          mpld.mpld_component_results(b, results=False)[3])
+    for c in range(0, ia.n_components, max(1, ia.n_components // 25)):
+        assert np.array_equal(mpld.mpld_export_matrix(a, c), mpld.mpld_export_matrix(b, c))
+    a.close()
+    b.close()
+
+
 def test_invalid_inputs_rejected():
     bad = [synth.graph_from_edges(3, 3, [(0, 1)]), synth.graph_from_edges(3, 3, [(0, 1)])]
     bad[0].conf_v = np.array([0], dtype=np.int32)          # self-loop
