@@ -371,11 +371,12 @@ def main():
     }
 
     # roofline of the dominant kernel (the persistent search kernel): integer
-    # ALU work per launch / launch duration vs the SM integer-lane peak
+    # ALU work per launch / launch duration vs the SMs' 32-bit integer issue
+    # rate (64 ops per SM per clock; the probe below measures it)
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak_gops = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9
+    alu_peak_gops = props.multi_processor_count * 64 * sm_mhz * 1e6 / 1e9
     achieved = res.work / (total_s / args.steps) / 1e9
     traffic = None
     tr = TRAFFIC.get(args.workload)
@@ -388,9 +389,23 @@ def main():
                        "unit": "Gop/s", "frac": achieved / alu_peak_gops, "traffic": traffic,
                        "traffic_source": ("ncu capture at 1/10 scale, scaled by segments"
                                           if traffic is not None else None),
-                       "peak_source": f"{props.multi_processor_count} SMs x 128 int32 lanes x "
-                                      f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json)",
+                       "peak_source": f"{props.multi_processor_count} SMs x 64 int32 ops per clock x "
+                                      f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json); "
+                                      "derived, see int_pipes_measured",
                        "work_ops_per_launch": res.work}
+    # the integer pipes' measured throughput for the same op mix (context for
+    # the derived peak above)
+    import ctypes
+    pk = (ctypes.c_double * 2)()
+    fn = mpld.library().mpld_internal_int_peak
+    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    fn.restype = ctypes.c_int
+    if fn(1 << 14, pk) == 0:
+        out["roofline"]["int_pipes_measured"] = {
+            "logic_add_gops": pk[0], "logic_popc_add_gops": pk[1],
+            "frac_of_logic_popc_add": achieved / pk[1],
+            "source": "mpld_internal_int_peak: 8 independent chains per thread, 2,048 threads "
+                      "per SM, every SM"}
 
     if not args.no_e2e:
         if dist:

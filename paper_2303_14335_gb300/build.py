@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpld.so")
-SOURCES = ["mpld_search.cu", "mpld_host.cpp", "mpld_serve.cpp"]
+SOURCES = ["mpld_search.cu", "mpld_host.cpp", "mpld_serve.cpp", "mpld_peak.cu"]
 HEADERS = ["mpld_internal.h", "mpld_problem.h", os.path.join("..", "..", "include", "mpld.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-Wall"]
