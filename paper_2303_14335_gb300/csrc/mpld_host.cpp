@@ -73,6 +73,31 @@ void unite_min(std::vector<int32_t> &parent, int a, int b) {
   else parent[ra] = rb;
 }
 
+// The same forest shared by threads: a link hangs the larger root under the
+// smaller with a compare-and-swap, so parent[x] <= x always and every root is
+// its set's lowest element whatever the order of the unions; finds halve
+// paths (a parent only ever moves to an ancestor).
+int pfind(int32_t *par, int x) {
+  for (;;) {
+    const int px = __atomic_load_n(par + x, __ATOMIC_RELAXED);
+    if (px == x) return x;
+    const int gx = __atomic_load_n(par + px, __ATOMIC_RELAXED);
+    if (gx != px) __atomic_store_n(par + x, gx, __ATOMIC_RELAXED);
+    x = gx;
+  }
+}
+void punite(int32_t *par, int a, int b) {
+  for (;;) {
+    a = pfind(par, a);
+    b = pfind(par, b);
+    if (a == b) return;
+    if (a > b) std::swap(a, b);
+    int expect = b;
+    if (__atomic_compare_exchange_n(par + b, &expect, a, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED))
+      return;
+  }
+}
+
 // (min,max)-normalised, sorted, unique edges; returns false on a bad edge.
 // The larger endpoints are bucketed by the smaller one (a counting sort),
 // then each (short) bucket is sorted and deduplicated.
@@ -460,16 +485,23 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     std::vector<int32_t> parent((size_t)n);
     std::iota(parent.begin(), parent.end(), 0);
     {
-      std::vector<int32_t> first_of((size_t)n, -1);
-      for (int s = 0; s < n; ++s) {
-        const int poly = g->polygon_of ? g->polygon_of[s] : s;
-        if (first_of[poly] < 0) first_of[poly] = s;
-        else unite_min(parent, first_of[poly], s);
+      int32_t *par = parent.data();
+      if (g->polygon_of) {
+        // one segment of each polygon (the first to claim it), then every
+        // segment joins it
+        std::vector<int32_t> rep((size_t)n, -1);
+        parallel_for(n, 1 << 15, [&](int x) {
+          int expect = -1;
+          __atomic_compare_exchange_n(rep.data() + g->polygon_of[x], &expect, x, false,
+                                      __ATOMIC_RELAXED, __ATOMIC_RELAXED);
+        });
+        parallel_for(n, 1 << 15, [&](int x) { punite(par, x, rep[g->polygon_of[x]]); });
       }
+      const int ms = (int)p->su.size();
+      parallel_for(ms, 1 << 14, [&](int e) { punite(par, p->su[e], p->sv[e]); });
+      p->unit_of.resize((size_t)n);
+      parallel_for(n, 1 << 15, [&](int x) { p->unit_of[x] = pfind(par, x); });
     }
-    for (size_t e = 0; e < p->su.size(); ++e) unite_min(parent, p->su[e], p->sv[e]);
-    p->unit_of.resize((size_t)n);
-    for (int s = 0; s < n; ++s) p->unit_of[s] = find_root(parent, s);
     p->uptr.assign((size_t)n + 1, 0);
     for (int s = 0; s < n; ++s) p->uptr[p->unit_of[s] + 1]++;
     for (int u = 0; u < n; ++u) p->uptr[u + 1] += p->uptr[u];
@@ -528,31 +560,43 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       }
     }
 
-    // ---- sub-graphs: connected components of what remains
+    // ---- sub-graphs: connected components of what remains.  Edges are
+    // united in parallel; a link always hangs the larger root under the
+    // smaller, so every root is its component's lowest segment whatever the
+    // order, and ids follow the lowest segments ascending.
     std::iota(parent.begin(), parent.end(), 0);
     const bool single = (p->flags & MPLD_SINGLE_INSTANCE) != 0;
+    std::vector<uint8_t> alive((size_t)n);
+    parallel_for(n, 1 << 15, [&](int s) { alive[s] = removed[p->unit_of[s]] ? 0 : 1; });
     if (!single) {
-      for (size_t e = 0; e < p->cu.size(); ++e)
-        if (!removed[p->unit_of[p->cu[e]]] && !removed[p->unit_of[p->cv[e]]])
-          unite_min(parent, p->cu[e], p->cv[e]);
-      for (size_t e = 0; e < p->su.size(); ++e)
-        if (!removed[p->unit_of[p->su[e]]]) unite_min(parent, p->su[e], p->sv[e]);
+      int32_t *par = parent.data();
+      const int mc = (int)p->cu.size(), ms = (int)p->su.size();
+      parallel_for(mc + ms, 1 << 14, [&](int e) {
+        if (e < mc) {
+          if (alive[p->cu[e]] && alive[p->cv[e]]) punite(par, p->cu[e], p->cv[e]);
+        } else if (alive[p->su[e - mc]]) {
+          punite(par, p->su[e - mc], p->sv[e - mc]);
+        }
+      });
+      // every entry its root
+      parallel_for(n, 1 << 15, [&](int x) { __atomic_store_n(par + x, pfind(par, x), __ATOMIC_RELAXED); });
     }
     p->comp_of.assign((size_t)n, -1);
     {
+      // ids: the roots (lowest alive segments) in ascending order
       std::vector<int32_t> id_of((size_t)n, -1);
       int single_id = -1;
       for (int s = 0; s < n; ++s) {
-        if (removed[p->unit_of[s]]) continue;
+        if (!alive[s]) continue;
         if (single) {
           if (single_id < 0) single_id = p->n_comp++;
-          p->comp_of[s] = single_id;
-        } else {
-          const int r = find_root(parent, s);
-          if (id_of[r] < 0) id_of[r] = p->n_comp++;
-          p->comp_of[s] = id_of[r];
+        } else if (parent[s] == s) {
+          id_of[s] = p->n_comp++;
         }
       }
+      parallel_for(n, 1 << 15, [&](int s) {
+        if (alive[s]) p->comp_of[s] = single ? single_id : id_of[parent[s]];
+      });
     }
     for (int u : p->removed_order) p->n_removed_segments += p->uptr[u + 1] - p->uptr[u];
     int C = p->n_comp;
