@@ -141,21 +141,6 @@ bool normalise(int n, int m, const int32_t *u, const int32_t *v, std::vector<int
   return true;
 }
 
-// Adjacency with neighbours ascending (edges come sorted by (min,max)).
-void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
-         std::vector<int32_t> &ptr, std::vector<int32_t> &adj) {
-  ptr.assign((size_t)n + 1, 0);
-  for (size_t e = 0; e < u.size(); ++e) { ptr[u[e] + 1]++; ptr[v[e] + 1]++; }
-  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-  adj.resize(2 * u.size());
-  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
-  // smaller neighbours of x arrive (as u of edges (u,x)) in ascending u, then
-  // larger ones (as v of edges (x,v)) in ascending v -- but interleaved in
-  // edge order; two passes keep each list sorted.
-  for (size_t e = 0; e < u.size(); ++e) adj[fill[v[e]]++] = u[e];
-  for (size_t e = 0; e < u.size(); ++e) adj[fill[u[e]]++] = v[e];
-}
-
 // Biconnected blocks of one component (MPLD_BICONNECTED), appended in the
 // canonical order: breadth-first over the block-cut tree, starting from the
 // lexicographically first block (ascending segment list) that holds the
@@ -412,6 +397,40 @@ void parallel_for(int count, int grain, F f) {
     st->cv.wait(lk, [&] { return st->done.load() == chunks; });
   }
   if (st->failed) throw std::bad_alloc();
+}
+
+// Adjacency lists of the normalised edges, neighbours ascending: degrees and
+// slots are claimed in parallel, then each list is sorted.
+void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
+         std::vector<int32_t> &ptr, std::vector<int32_t> &adj) {
+  const int m = (int)u.size();
+  ptr.assign((size_t)n + 1, 0);
+  int32_t *pp = ptr.data();
+  parallel_for(m, 1 << 15, [&](int e) {
+    __atomic_fetch_add(pp + u[e] + 1, 1, __ATOMIC_RELAXED);
+    __atomic_fetch_add(pp + v[e] + 1, 1, __ATOMIC_RELAXED);
+  });
+  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+  adj.resize(2 * (size_t)m);
+  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+  int32_t *fp = fill.data();
+  parallel_for(m, 1 << 15, [&](int e) {
+    adj[__atomic_fetch_add(fp + v[e], 1, __ATOMIC_RELAXED)] = u[e];
+    adj[__atomic_fetch_add(fp + u[e], 1, __ATOMIC_RELAXED)] = v[e];
+  });
+  parallel_for(n, 1 << 14, [&](int x) {
+    int32_t *a = adj.data() + ptr[x], *b = adj.data() + ptr[x + 1];
+    if (b - a > 32) {
+      std::sort(a, b);
+      return;
+    }
+    for (int32_t *i = a + 1; i < b; ++i) {
+      const int32_t t = *i;
+      int32_t *j = i;
+      for (; j > a && j[-1] > t; --j) *j = j[-1];
+      *j = t;
+    }
+  });
 }
 
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
@@ -1252,7 +1271,13 @@ int mpld_internal_finish(mpld_problem *p, const InstResult *hres, const int8_t *
   }
   p->have_results = true;
   std::vector<int8_t> m((size_t)p->n_seg, (int8_t)-1);
-  for (int c = 0; c < C; ++c) {
+  if (p->inst_attach.empty()) {
+    // whole components: each segment in one instance
+    parallel_for(C, 64, [&](int c) {
+      for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) m[p->comp_seg[t]] = hmasks[t];
+    });
+  }
+  for (int c = 0; c < C && !p->inst_attach.empty(); ++c) {
     // a block attached at a segment already coloured takes the transposition
     // of masks that keeps that segment's mask (cost does not depend on the
     // names of the masks); instances come in an order where the attach

@@ -966,7 +966,7 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
   uint32_t work32 = 0;
   bool timed_out = false, last_item = false;
   unsigned long long my_key = ~0ull, cached = mode == PAR_REPLAY ? replay_key : ~0ull;
-  const uint64_t t0 = globaltimer();
+  const uint64_t t0 = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
   int64_t next_check = 1024;
   // the pruning threshold for subtree s: a leaf must cost less than it
   auto threshold = [&](uint32_t s) -> int32_t {
@@ -1030,7 +1030,10 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
     for (;;) {
       if (enter) {
         if (mode != PAR_REPLAY && (nodes & 15) == 0) {
-          const unsigned long long kk = *(volatile unsigned long long *)&ctx->key;
+          // one read of the shared key for the whole warp
+          unsigned long long kk = 0ull;
+          if (lane == 0) kk = *(volatile unsigned long long *)&ctx->key;
+          kk = __shfl_sync(FULL, kk, 0);
           cached = kk < cached ? kk : cached;
         }
         ++nodes;
@@ -1040,7 +1043,7 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
           work += work32;
           work32 = 0;
           const uint64_t now = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
-          if (mode != PAR_REPLAY && (int64_t)(now - t0) > a.time_limit_ns) {
+          if ((int64_t)(now - t0) > a.time_limit_ns) {
             timed_out = true;
             break;
           }
@@ -1393,7 +1396,9 @@ __device__ __noinline__ void run_grid_queue(const LaunchArgs &a, int lane, int w
     int D;
     uint32_t ns;
     par_cut(d.n, d.k, G, D, ns);
-    if (*(volatile uint32_t *)&ctx->next >= ns) continue;   // all handed out
+    uint32_t taken = 0;
+    if (lane == 0) taken = *(volatile uint32_t *)&ctx->next;
+    if (__shfl_sync(FULL, taken, 0) >= ns) continue;   // all handed out
     if (!reg_fits(d.n, d.k) || a.slot_bytes < (int)reg_layout(d.n, d.k, 0).bytes) {
       // the host queues only register-resident instances
       if (lane == 0) atomicExch(a.err, MPLD_E_STATE);
@@ -1401,7 +1406,9 @@ __device__ __noinline__ void run_grid_queue(const LaunchArgs &a, int lane, int w
     }
     if (!par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_QUEUE, 0ull)) continue;
     __threadfence();
-    const unsigned long long key = *(volatile unsigned long long *)&ctx->key;
+    unsigned long long key = 0ull;
+    if (lane == 0) key = *(volatile unsigned long long *)&ctx->key;
+    key = __shfl_sync(FULL, key, 0);
     if (key != ~0ull)
       par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_REPLAY,
                    (key & ~0xFFFFFFFFull) | ((key & 0xFFFFFFFFull) + 1ull));
