@@ -141,6 +141,21 @@ bool normalise(int n, int m, const int32_t *u, const int32_t *v, std::vector<int
   return true;
 }
 
+// Adjacency with neighbours ascending (edges come sorted by (min,max)).
+void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
+         std::vector<int32_t> &ptr, std::vector<int32_t> &adj) {
+  ptr.assign((size_t)n + 1, 0);
+  for (size_t e = 0; e < u.size(); ++e) { ptr[u[e] + 1]++; ptr[v[e] + 1]++; }
+  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+  adj.resize(2 * u.size());
+  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+  // smaller neighbours of x arrive (as u of edges (u,x)) in ascending u, then
+  // larger ones (as v of edges (x,v)) in ascending v -- but interleaved in
+  // edge order; two passes keep each list sorted.
+  for (size_t e = 0; e < u.size(); ++e) adj[fill[v[e]]++] = u[e];
+  for (size_t e = 0; e < u.size(); ++e) adj[fill[u[e]]++] = v[e];
+}
+
 // Biconnected blocks of one component (MPLD_BICONNECTED), appended in the
 // canonical order: breadth-first over the block-cut tree, starting from the
 // lexicographically first block (ascending segment list) that holds the
@@ -316,9 +331,14 @@ class HostPool {
     {
       std::lock_guard<std::mutex> lk(mu_);
       q_.push_back(std::move(task));
+      pending_.fetch_add(1, std::memory_order_relaxed);
     }
     cv_.notify_one();
   }
+  // tasks posted and not yet started (another parallel loop is filling the
+  // pool), and whether the calling thread is one of the helpers
+  int pending() const { return pending_.load(std::memory_order_relaxed); }
+  static bool on_helper() { return helper_flag(); }
 
  private:
   HostPool() {
@@ -334,7 +354,12 @@ class HostPool {
     cv_.notify_all();
     for (auto &t : th_) t.join();
   }
+  static bool &helper_flag() {
+    static thread_local bool flag = false;
+    return flag;
+  }
   void loop() {
+    helper_flag() = true;
     for (;;) {
       std::function<void()> task;
       {
@@ -343,6 +368,7 @@ class HostPool {
         if (stop_ && q_.empty()) return;
         task = std::move(q_.front());
         q_.pop_front();
+        pending_.fetch_sub(1, std::memory_order_relaxed);
       }
       task();
     }
@@ -351,6 +377,7 @@ class HostPool {
   std::condition_variable cv_;
   std::deque<std::function<void()>> q_;
   std::vector<std::thread> th_;
+  std::atomic<int> pending_{0};
   bool stop_ = false;
 };
 
@@ -361,7 +388,10 @@ template <typename F>
 void parallel_for(int count, int grain, F f) {
   const int chunks = (count + grain - 1) / grain;
   HostPool &pool = HostPool::get();
-  const int nh = std::min(pool.helpers(), chunks - 1);
+  // inline when nested in a pool task or when other loops already fill the
+  // pool (concurrent layout builds): their threads are busy anyway
+  const bool busy = HostPool::on_helper() || pool.pending() > 0;
+  const int nh = busy ? 0 : std::min(pool.helpers(), chunks - 1);
   if (nh <= 0) {
     for (int i = 0; i < count; ++i) f(i);
     return;
@@ -397,40 +427,6 @@ void parallel_for(int count, int grain, F f) {
     st->cv.wait(lk, [&] { return st->done.load() == chunks; });
   }
   if (st->failed) throw std::bad_alloc();
-}
-
-// Adjacency lists of the normalised edges, neighbours ascending: degrees and
-// slots are claimed in parallel, then each list is sorted.
-void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
-         std::vector<int32_t> &ptr, std::vector<int32_t> &adj) {
-  const int m = (int)u.size();
-  ptr.assign((size_t)n + 1, 0);
-  int32_t *pp = ptr.data();
-  parallel_for(m, 1 << 15, [&](int e) {
-    __atomic_fetch_add(pp + u[e] + 1, 1, __ATOMIC_RELAXED);
-    __atomic_fetch_add(pp + v[e] + 1, 1, __ATOMIC_RELAXED);
-  });
-  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-  adj.resize(2 * (size_t)m);
-  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
-  int32_t *fp = fill.data();
-  parallel_for(m, 1 << 15, [&](int e) {
-    adj[__atomic_fetch_add(fp + v[e], 1, __ATOMIC_RELAXED)] = u[e];
-    adj[__atomic_fetch_add(fp + u[e], 1, __ATOMIC_RELAXED)] = v[e];
-  });
-  parallel_for(n, 1 << 14, [&](int x) {
-    int32_t *a = adj.data() + ptr[x], *b = adj.data() + ptr[x + 1];
-    if (b - a > 32) {
-      std::sort(a, b);
-      return;
-    }
-    for (int32_t *i = a + 1; i < b; ++i) {
-      const int32_t t = *i;
-      int32_t *j = i;
-      for (; j > a && j[-1] > t; --j) *j = j[-1];
-      *j = t;
-    }
-  });
 }
 
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
@@ -504,23 +500,16 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     std::vector<int32_t> parent((size_t)n);
     std::iota(parent.begin(), parent.end(), 0);
     {
-      int32_t *par = parent.data();
-      if (g->polygon_of) {
-        // one segment of each polygon (the first to claim it), then every
-        // segment joins it
-        std::vector<int32_t> rep((size_t)n, -1);
-        parallel_for(n, 1 << 15, [&](int x) {
-          int expect = -1;
-          __atomic_compare_exchange_n(rep.data() + g->polygon_of[x], &expect, x, false,
-                                      __ATOMIC_RELAXED, __ATOMIC_RELAXED);
-        });
-        parallel_for(n, 1 << 15, [&](int x) { punite(par, x, rep[g->polygon_of[x]]); });
+      std::vector<int32_t> first_of((size_t)n, -1);
+      for (int s = 0; s < n; ++s) {
+        const int poly = g->polygon_of ? g->polygon_of[s] : s;
+        if (first_of[poly] < 0) first_of[poly] = s;
+        else unite_min(parent, first_of[poly], s);
       }
-      const int ms = (int)p->su.size();
-      parallel_for(ms, 1 << 14, [&](int e) { punite(par, p->su[e], p->sv[e]); });
-      p->unit_of.resize((size_t)n);
-      parallel_for(n, 1 << 15, [&](int x) { p->unit_of[x] = pfind(par, x); });
     }
+    for (size_t e = 0; e < p->su.size(); ++e) unite_min(parent, p->su[e], p->sv[e]);
+    p->unit_of.resize((size_t)n);
+    for (int s = 0; s < n; ++s) p->unit_of[s] = find_root(parent, s);
     p->uptr.assign((size_t)n + 1, 0);
     for (int s = 0; s < n; ++s) p->uptr[p->unit_of[s] + 1]++;
     for (int u = 0; u < n; ++u) p->uptr[u + 1] += p->uptr[u];

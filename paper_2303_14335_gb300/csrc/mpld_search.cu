@@ -1021,189 +1021,186 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
       }
       __syncwarp();
     };
-    uint32_t digits = s;   // the prefix, most significant digit first
+    const uint32_t prefix = s;   // digit i, most significant first, is the row at level i
     uint32_t top = ns / (uint32_t)k;
-    bool skip = false, done = false;
     bool enter = true;
-    int floor_level = D;
-    if (!timed_out)
-    for (;;) {
-      if (enter) {
-        if (mode != PAR_REPLAY && (nodes & 15) == 0) {
-          // one read of the shared key for the whole warp
-          unsigned long long kk = 0ull;
-          if (lane == 0) kk = *(volatile unsigned long long *)&ctx->key;
-          kk = __shfl_sync(FULL, kk, 0);
-          cached = kk < cached ? kk : cached;
-        }
-        ++nodes;
-        work32 += 2u * (uint32_t)(n - level);
-        if (nodes >= next_check) {
-          next_check = nodes + 1024;
-          work += work32;
-          work32 = 0;
-          const uint64_t now = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
-          if ((int64_t)(now - t0) > a.time_limit_ns) {
-            timed_out = true;
-            break;
+    const int floor_level = D;
+    if (!timed_out) {
+      for (;;) {
+        if (enter) {
+          if (mode != PAR_REPLAY && (nodes & 15) == 0) {
+            // one read of the shared key for the whole warp
+            unsigned long long kk = 0ull;
+            if (lane == 0) kk = *(volatile unsigned long long *)&ctx->key;
+            kk = __shfl_sync(FULL, kk, 0);
+            cached = kk < cached ? kk : cached;
           }
-        }
-        const int32_t thr = threshold(s);
-        uint32_t key = 0xFFFFFFFFu;
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-          const uint32_t f = (w >> (FB * j)) & FMASK;
-          const uint32_t cnt = (uint32_t)__popc(f & kmask);
-          const uint32_t sg = (uint32_t)(lane * P + j);
-          uint32_t kv;
-          if constexpr (RULE == 0) kv = (cnt << 8) | sg;
-          else kv = cnt == 1 ? sg : (0x10000u | (((rk >> (8 * j)) & 0xFFu) << 8) | sg);
-          kv = (f & FLAG) ? kv : 0xFFFFFFFFu;
-          key = min(key, kv);
-        }
-        key = __reduce_min_sync(FULL, key);
-        if (key == 0xFFFFFFFFu) {
-          // a leaf; inside the prefix it is a subtree only on digit 0 below
-          if (level < D && (digits % (top * (uint32_t)k)) != 0u) { skip = true; break; }
-          if (g < thr) {
-            take_leaf();
-            if (g == 0 || mode == PAR_REPLAY) { done = true; break; }
-          }
-          if (level <= floor_level) { done = true; break; }
-          enter = false;
-          continue;
-        }
-        if (thr < INF32) {
-          uint32_t z = 0;
-          if (RULE != 0 || key < 0x100u) {
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-              const uint32_t f = (w >> (FB * j)) & FMASK;
-              z += (f & FLAG) && (f & kmask) == 0;
+          ++nodes;
+          work32 += 2u * (uint32_t)(n - level);
+          if (nodes >= next_check) {
+            next_check = nodes + 1024;
+            work += work32;
+            work32 = 0;
+            const uint64_t now = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
+            if ((int64_t)(now - t0) > a.time_limit_ns) {
+              timed_out = true;
+              break;
             }
-            z = __reduce_add_sync(FULL, z);
           }
-          if ((int64_t)g + (int64_t)Cc * z >= thr) {
-            if (level < D) { skip = true; break; }
+          const int32_t thr = threshold(s);
+          uint32_t key = 0xFFFFFFFFu;
+  #pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const uint32_t f = (w >> (FB * j)) & FMASK;
+            const uint32_t cnt = (uint32_t)__popc(f & kmask);
+            const uint32_t sg = (uint32_t)(lane * P + j);
+            uint32_t kv;
+            if constexpr (RULE == 0) kv = (cnt << 8) | sg;
+            else kv = cnt == 1 ? sg : (0x10000u | (((rk >> (8 * j)) & 0xFFu) << 8) | sg);
+            kv = (f & FLAG) ? kv : 0xFFFFFFFFu;
+            key = min(key, kv);
+          }
+          key = __reduce_min_sync(FULL, key);
+          if (key == 0xFFFFFFFFu) {
+            // a leaf (always at level n >= D, so below the prefix)
+            if (g < thr) {
+              take_leaf();
+              if (g == 0 || mode == PAR_REPLAY) break;
+            }
+            if (level <= floor_level) break;
             enter = false;
             continue;
           }
-        }
-        const int v = (int)(key & 0xFFu);
-        const int jv = v % P, src = v / P;
-        const uint32_t ab = adj[v * 32 + lane];
-        const uint32_t dd = deg[v];
-        const uint32_t sel = (uint32_t)jv | ((uint32_t)(jv + 4) << 4);
-        auto ccr = [&](int m) -> uint32_t { return m < NC ? cc[m < NC ? m : 0] : 0u; };
-        auto scr = [&](int m) -> uint32_t { return m < NC ? sc[m < NC ? m : 0] : 0u; };
-        uint32_t cw0 = __shfl_sync(FULL, pick_bytes(ccr(0), ccr(1), ccr(2), ccr(3), sel), src);
-        uint32_t sw0 = __shfl_sync(FULL, pick_bytes(scr(0), scr(1), scr(2), scr(3), sel), src);
-        uint32_t cw1 = 0u, sw1 = 0u;
-        if constexpr (NC == 8) {
-          cw1 = __shfl_sync(FULL, pick_bytes(ccr(4), ccr(5), ccr(6), ccr(7), sel), src);
-          sw1 = __shfl_sync(FULL, pick_bytes(scr(4), scr(5), scr(6), scr(7), sel), src);
-        }
-        const int stot = (int)(((sw0 * 0x01010101u) >> 24) + ((sw1 * 0x01010101u) >> 24));
-        uint32_t keys[MK];
-        uint32_t oldf = FLAG;
-#pragma unroll
-        for (int c = 0; c < MK; ++c) {
-          const uint32_t cwd = c < 4 ? cw0 : cw1, swd = c < 4 ? sw0 : sw1;
-          const int sh = 8 * (c & 3);
-          const int ncf = (int)((cwd >> sh) & 0xFFu);
-          const int inc = Cc * ncf + Cs * (stot - (int)((swd >> sh) & 0xFFu));
-          keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
-          if (c < k && ncf == 0) oldf |= 1u << c;
-        }
-        sort_keys<MK>(keys);
-        work32 += (uint32_t)(k * (int)((dd & 0xFFFFu) + (dd >> 16)) + 5 * (1 + (int)(dd & 0xFFFFu)));
-        // the row to take: the prefix digit above the cut, the first below it
-        int first = 0;
-        if (level < D) {
-          first = (int)((digits / top) % (uint32_t)k);
-          top /= (uint32_t)k;
-        }
-        uint32_t kf = keys[0];
-#pragma unroll
-        for (int i = 1; i < MK; ++i) kf = i == first ? keys[i] : kf;
-        if (thr < INF32 && g + (int32_t)(kf >> 3) >= thr) {
-          // this row and the ones after it cannot improve
-          if (level < D) { skip = true; break; }
-          enter = false;
+          if (thr < INF32) {
+            uint32_t z = 0;
+            if (RULE != 0 || key < 0x100u) {
+  #pragma unroll
+              for (int j = 0; j < P; ++j) {
+                const uint32_t f = (w >> (FB * j)) & FMASK;
+                z += (f & FLAG) && (f & kmask) == 0;
+              }
+              z = __reduce_add_sync(FULL, z);
+            }
+            if ((int64_t)g + (int64_t)Cc * z >= thr) {
+              if (level < D) break;
+              enter = false;
+              continue;
+            }
+          }
+          const int v = (int)(key & 0xFFu);
+          const int jv = v % P, src = v / P;
+          const uint32_t ab = adj[v * 32 + lane];
+          const uint32_t dd = deg[v];
+          const uint32_t sel = (uint32_t)jv | ((uint32_t)(jv + 4) << 4);
+          auto ccr = [&](int m) -> uint32_t { return m < NC ? cc[m < NC ? m : 0] : 0u; };
+          auto scr = [&](int m) -> uint32_t { return m < NC ? sc[m < NC ? m : 0] : 0u; };
+          uint32_t cw0 = __shfl_sync(FULL, pick_bytes(ccr(0), ccr(1), ccr(2), ccr(3), sel), src);
+          uint32_t sw0 = __shfl_sync(FULL, pick_bytes(scr(0), scr(1), scr(2), scr(3), sel), src);
+          uint32_t cw1 = 0u, sw1 = 0u;
+          if constexpr (NC == 8) {
+            cw1 = __shfl_sync(FULL, pick_bytes(ccr(4), ccr(5), ccr(6), ccr(7), sel), src);
+            sw1 = __shfl_sync(FULL, pick_bytes(scr(4), scr(5), scr(6), scr(7), sel), src);
+          }
+          const int stot = (int)(((sw0 * 0x01010101u) >> 24) + ((sw1 * 0x01010101u) >> 24));
+          uint32_t keys[MK];
+          uint32_t oldf = FLAG;
+  #pragma unroll
+          for (int c = 0; c < MK; ++c) {
+            const uint32_t cwd = c < 4 ? cw0 : cw1, swd = c < 4 ? sw0 : sw1;
+            const int sh = 8 * (c & 3);
+            const int ncf = (int)((cwd >> sh) & 0xFFu);
+            const int inc = Cc * ncf + Cs * (stot - (int)((swd >> sh) & 0xFFu));
+            keys[c] = (MK == 8 && c >= k) ? 0xFFFFFFFFu : (((uint32_t)inc << 3) | (uint32_t)c);
+            if (c < k && ncf == 0) oldf |= 1u << c;
+          }
+          sort_keys<MK>(keys);
+          work32 += (uint32_t)(k * (int)((dd & 0xFFFFu) + (dd >> 16)) + 5 * (1 + (int)(dd & 0xFFFFu)));
+          // the row to take: the prefix digit above the cut, the first below it
+          int first = 0;
+          if (level < D) {
+            first = (int)((prefix / top) % (uint32_t)k);
+            top /= (uint32_t)k;
+          }
+          uint32_t kf = keys[0];
+  #pragma unroll
+          for (int i = 1; i < MK; ++i) kf = i == first ? keys[i] : kf;
+          if (thr < INF32 && g + (int32_t)(kf >> 3) >= thr) {
+            // this row and the ones after it cannot improve
+            if (level < D) break;
+            enter = false;
+            continue;
+          }
+          if (level >= n) break;   // unreachable: each level covers a column
+          if (level >= D && lane == 0) {
+            uint4 *r4 = (uint4 *)(rec + level * RS);
+            r4[0] = make_uint4((uint32_t)v | (1u << 8) | (oldf << 12), (uint32_t)g, dd, 0u);
+            r4[1] = make_uint4(keys[0], MK > 1 ? keys[MK > 1 ? 1 : 0] : 0u,
+                               MK > 2 ? keys[MK > 2 ? 2 : 0] : 0u, MK > 3 ? keys[MK > 3 ? 3 : 0] : 0u);
+            if constexpr (MK == 8) r4[2] = make_uint4(keys[4 % MK], keys[5 % MK], keys[6 % MK], keys[7 % MK]);
+          }
+          const int c = (int)(kf & 7u);
+          const uint32_t cb = ab & 0xFu, sb = ab >> 4;
+          const uint32_t spc = spread_bits<FB>(cb);
+          if (level >= D)
+            sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (cb << 4) | (sb << 8));
+          w &= ~(spc << c);
+          move_counts(c, spread_bits<8>(cb), spread_bits<8>(sb), true);
+          if (lane == src) {
+            w &= ~(FMASK << (FB * jv));
+            xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+          }
+          g += (int32_t)(kf >> 3);
+          ++level;
+          __syncwarp();
           continue;
         }
-        if (level >= n) break;   // unreachable: each level covers a column
-        if (level >= D && lane == 0) {
-          uint4 *r4 = (uint4 *)(rec + level * RS);
-          r4[0] = make_uint4((uint32_t)v | (1u << 8) | (oldf << 12), (uint32_t)g, dd, 0u);
-          r4[1] = make_uint4(keys[0], MK > 1 ? keys[MK > 1 ? 1 : 0] : 0u,
-                             MK > 2 ? keys[MK > 2 ? 2 : 0] : 0u, MK > 3 ? keys[MK > 3 ? 3 : 0] : 0u);
-          if constexpr (MK == 8) r4[2] = make_uint4(keys[4 % MK], keys[5 % MK], keys[6 % MK], keys[7 % MK]);
-        }
-        const int c = (int)(kf & 7u);
-        const uint32_t cb = ab & 0xFu, sb = ab >> 4;
-        const uint32_t spc = spread_bits<FB>(cb);
-        if (level >= D)
-          sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (cb << 4) | (sb << 8));
-        w &= ~(spc << c);
-        move_counts(c, spread_bits<8>(cb), spread_bits<8>(sb), true);
-        if (lane == src) {
-          w &= ~(FMASK << (FB * jv));
-          xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
-        }
-        g += (int32_t)(kf >> 3);
-        ++level;
+        // backtrack, never above the cut
+        if (level <= floor_level) break;
+        --level;
+        const uint32_t *r = rec + level * RS;
+        const uint4 r0 = *(const uint4 *)r, r1 = *(const uint4 *)(r + 4);
+        uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
+        if constexpr (MK == 8) r2 = *(const uint4 *)(r + 8);
+        const uint32_t sv = sav[level * 32 + lane];
         __syncwarp();
-        continue;
-      }
-      // backtrack, never above the cut
-      if (level <= floor_level) { done = true; break; }
-      --level;
-      const uint32_t *r = rec + level * RS;
-      const uint4 r0 = *(const uint4 *)r, r1 = *(const uint4 *)(r + 4);
-      uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
-      if constexpr (MK == 8) r2 = *(const uint4 *)(r + 8);
-      const uint32_t sv = sav[level * 32 + lane];
-      __syncwarp();
-      const int v = (int)(r0.x & 0xFFu);
-      const int nxt = (int)((r0.x >> 8) & 0xFu);
-      const int jv = v % P, src = v / P;
-      auto key_at = [&](int i) -> uint32_t {
-        const uint32_t lo = i == 0 ? r1.x : i == 1 ? r1.y : i == 2 ? r1.z : r1.w;
-        const uint32_t hi = i == 4 ? r2.x : i == 5 ? r2.y : i == 6 ? r2.z : r2.w;
-        return i < 4 ? lo : hi;
-      };
-      const uint32_t klast = key_at(nxt - 1), knext = key_at(nxt < MK ? nxt : MK - 1);
-      const int cl = (int)(klast & 7u);
-      const uint32_t cb = (sv >> 4) & 0xFu, sb = sv >> 8;
-      const uint32_t spc = spread_bits<FB>(cb);
-      const uint32_t cb8 = spread_bits<8>(cb), sb8 = spread_bits<8>(sb);
-      w |= spread_bits<FB>(sv & 0xFu) << cl;
-      move_counts(cl, cb8, sb8, false);
-      bool last = nxt >= k;
-      const int32_t thr = threshold(s);
-      if (!last && thr < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= thr) last = true;
-      if (last) {
-        if (lane == src) {
-          w |= (r0.x >> 12) << (FB * jv);
-          xw |= 0xFFu << (8 * jv);
+        const int v = (int)(r0.x & 0xFFu);
+        const int nxt = (int)((r0.x >> 8) & 0xFu);
+        const int jv = v % P, src = v / P;
+        auto key_at = [&](int i) -> uint32_t {
+          const uint32_t lo = i == 0 ? r1.x : i == 1 ? r1.y : i == 2 ? r1.z : r1.w;
+          const uint32_t hi = i == 4 ? r2.x : i == 5 ? r2.y : i == 6 ? r2.z : r2.w;
+          return i < 4 ? lo : hi;
+        };
+        const uint32_t klast = key_at(nxt - 1), knext = key_at(nxt < MK ? nxt : MK - 1);
+        const int cl = (int)(klast & 7u);
+        const uint32_t cb = (sv >> 4) & 0xFu, sb = sv >> 8;
+        const uint32_t spc = spread_bits<FB>(cb);
+        const uint32_t cb8 = spread_bits<8>(cb), sb8 = spread_bits<8>(sb);
+        w |= spread_bits<FB>(sv & 0xFu) << cl;
+        move_counts(cl, cb8, sb8, false);
+        bool last = nxt >= k;
+        const int32_t thr = threshold(s);
+        if (!last && thr < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= thr) last = true;
+        if (last) {
+          if (lane == src) {
+            w |= (r0.x >> 12) << (FB * jv);
+            xw |= 0xFFu << (8 * jv);
+          }
+          continue;
         }
-        continue;
+        const int c = (int)(knext & 7u);
+        g = (int32_t)r0.y + (int32_t)(knext >> 3);
+        work32 += 5u * (1u + (r0.z & 0xFFFFu));
+        sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (sv & 0xFF0u));
+        if (lane == 0) rec[level * RS] = (r0.x & ~0xF00u) | ((uint32_t)(nxt + 1) << 8);
+        w &= ~(spc << c);
+        move_counts(c, cb8, sb8, true);
+        if (lane == src) xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
+        ++level;
+        enter = true;
+        __syncwarp();
       }
-      const int c = (int)(knext & 7u);
-      g = (int32_t)r0.y + (int32_t)(knext >> 3);
-      work32 += 5u * (1u + (r0.z & 0xFFFFu));
-      sav[level * 32 + lane] = (uint16_t)(gather_bits<FB>((w >> c) & spc) | (sv & 0xFF0u));
-      if (lane == 0) rec[level * RS] = (r0.x & ~0xF00u) | ((uint32_t)(nxt + 1) << 8);
-      w &= ~(spc << c);
-      move_counts(c, cb8, sb8, true);
-      if (lane == src) xw = (xw & ~(0xFFu << (8 * jv))) | ((uint32_t)c << (8 * jv));
-      ++level;
-      enter = true;
-      __syncwarp();
     }
-    (void)skip;
-    (void)done;
     if (mode == PAR_QUEUE) {
       // publish this subtree's totals, then count it done
       work += work32;
