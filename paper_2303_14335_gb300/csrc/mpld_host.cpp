@@ -1411,28 +1411,63 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   std::vector<int32_t> order((size_t)total);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sizes[x] > sizes[y]; });
-  const int n_large = count_large(total, [&](int i) { return sizes[order[i]]; }, cta_min_of(prm));
+  // under the split search the largest split instances of all the layouts
+  // go to the queue launch first (as for one layout); the batched launch
+  // takes the rest of the order
+  std::vector<int32_t> qidx;
+  int qslot = 0, qctas = 0;
+  if (par_of(prm)) {
+    const int maxslot = mpld_internal_max_slot_bytes(CTA_TEAM_WARPS);
+    std::vector<int32_t> rest;
+    for (int i = 0; i < total; ++i) {
+      const InstDesc &d = desc[order[i]];
+      bool queued = false;
+      if ((int)qidx.size() < PAR_QUEUE_MAX && d.n >= PAR_MIN_SEGMENTS && mpld::reg_fits(d.n, d.k)) {
+        const int sl = (int)mpld::align16(mpld::reg_layout(d.n, d.k, 0).bytes);
+        if (sl <= maxslot) {
+          qidx.push_back(order[i]);
+          qslot = std::max(qslot, sl);
+          queued = true;
+        }
+      }
+      if (!queued) rest.push_back(order[i]);
+    }
+    if (!qidx.empty()) {
+      order = std::move(rest);
+      qctas = std::max(1, mpld_internal_ctas_per_sm(CTA_TEAM_WARPS, qslot)) *
+              std::max(1, mpld_internal_num_sms());
+    }
+  }
+  const int nq = (int)qidx.size(), n_rest = (int)order.size();
+  const int n_large = count_large(n_rest, [&](int i) { return sizes[order[i]]; }, cta_min_of(prm));
   const Shape sh = with_team(pick_shape(ps, n, prm), n_large);
   void *buf = nullptr;
   const size_t dbytes = sizeof(InstDesc) * (size_t)std::max(total, 1);
-  const size_t bytes = dbytes + sizeof(int32_t) * (size_t)std::max(total, 1) + 256;
+  const size_t obytes = (sizeof(int32_t) * (size_t)std::max(total, 1) + 255) & ~(size_t)255;
+  const size_t o_ctx = dbytes + obytes + 256;          // after desc, order, work counters
+  const size_t o_qidx = o_ctx + 64u * (size_t)nq;
+  const size_t bytes = o_qidx + sizeof(int32_t) * (size_t)std::max(nq, 1);
   if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess) { cudaGetLastError(); return MPLD_E_OOM; }
   uint8_t *b = (uint8_t *)buf;
   int rc = MPLD_OK;
   if (total) {
     rc |= cuda_ok(cudaMemcpyAsync(b, desc.data(), sizeof(InstDesc) * (size_t)total,
                                   cudaMemcpyHostToDevice, st));
-    rc |= cuda_ok(cudaMemcpyAsync(b + dbytes, order.data(), sizeof(int32_t) * (size_t)total,
-                                  cudaMemcpyHostToDevice, st));
+    if (n_rest)
+      rc |= cuda_ok(cudaMemcpyAsync(b + dbytes, order.data(), sizeof(int32_t) * (size_t)n_rest,
+                                    cudaMemcpyHostToDevice, st));
   }
+  if (nq)
+    rc |= cuda_ok(cudaMemcpyAsync(b + o_qidx, qidx.data(), sizeof(int32_t) * (size_t)nq,
+                                  cudaMemcpyHostToDevice, st));
   // the sources are pageable vectors local to this call: wait for the copies
   // before they go out of scope (they may be read by the GPU directly)
   rc |= cuda_ok(cudaStreamSynchronize(st));
-  uint32_t *queue = (uint32_t *)(b + dbytes + sizeof(int32_t) * (size_t)std::max(total, 1));
+  uint32_t *queue = (uint32_t *)(b + dbytes + obytes);
   mpld::LaunchArgs a;
   a.desc = (const InstDesc *)b;
   a.order = (const int32_t *)(b + dbytes);
-  a.n_inst = total;
+  a.n_inst = n_rest;
   a.slot_bytes = sh.slot;
   a.queue = queue;
   a.err = ps[0]->d_err;
@@ -1448,7 +1483,29 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
     rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_res, 0xFF,
                                   sizeof(InstResult) * (size_t)std::max(ps[i]->n_comp, 1), st));
   }
-  if (!rc) rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
+  if (!rc && nq) {
+    // the queue launch: contexts reset (no incumbent, totals 0), then split
+    rc |= cuda_ok(cudaMemsetAsync(ps[0]->d_err, 0, 4, st));
+    rc |= cuda_ok(cudaMemsetAsync(b + o_ctx, 0, 64u * (size_t)nq, st));
+    rc |= cuda_ok(cudaMemset2DAsync(b + o_ctx, 64, 0xFF, 8, (size_t)nq, st));
+    mpld::LaunchArgs qa = a;
+    qa.order = (const int32_t *)(b + o_qidx);
+    qa.n_inst = nq;
+    qa.slot_bytes = qslot;
+    qa.queue = nullptr;
+    qa.budget = 0;
+    qa.n_large = 0;
+    qa.par = 3;
+    qa.par_buf = b + o_ctx;
+    if (!rc) rc = mpld_internal_launch(&qa, qctas, CTA_TEAM_WARPS, st);
+    if (!rc) rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));
+    if (!rc && n_rest) {
+      const int ctas = std::min(sh.ctas, n_large + (n_rest - n_large + sh.nw - 1) / sh.nw);
+      rc = mpld_internal_launch(&a, std::max(ctas, 1), sh.nw, st);
+    }
+  } else if (!rc) {
+    rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
+  }
   rc |= cuda_ok(cudaFreeAsync(buf, st));
   for (int i = 0; i < n; ++i) {
     ps[i]->searched = rc == MPLD_OK;
