@@ -436,8 +436,8 @@ def test_split_search_queue_and_cta_forms(stream):
 
 
 def test_split_search_several_problems(stream):
-    # a batch of several layouts: 21 split instances, the 16 largest to the
-    # queue launch, the other 5 to CTAs in the batched launch
+    # a batch of several layouts: 17 split instances (1 + 16), the 16 largest
+    # to the queue launch, the smallest to a CTA in the batched launch
     Ls = [synth.unit_disk_layout(1000, 3, seed=5, mean_deg=2.6, p_stitch=0.2),
           synth.unit_disk_layout(5000, 3, seed=12, mean_deg=2.4, p_stitch=0.2)]
     probs = [mpld.mpld_build_matrix(L, None, stream.cuda_stream) for L in Ls]
