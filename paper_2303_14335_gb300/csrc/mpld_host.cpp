@@ -429,6 +429,18 @@ void parallel_for(int count, int grain, F f) {
   if (st->failed) throw std::bad_alloc();
 }
 
+// f(j) for j in [0, count) over `lanes` tasks, task q taking j = q, q + lanes,
+// ...: the first `lanes` jobs (the largest instances, in a largest-first
+// order) start at once on different threads, and the many small ones share
+// few claims of the work counter.
+template <typename F>
+void parallel_strided(int count, int lanes, F f) {
+  lanes = std::max(1, std::min(lanes, count));
+  parallel_for(lanes, 1, [&](int q) {
+    for (int j = q; j < count; j += lanes) f(j);
+  });
+}
+
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
 
 std::mutex g_tune_mu;
@@ -681,7 +693,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     const bool cliques = (p->flags & MPLD_CLIQUE_BOUND) != 0;
     std::vector<std::vector<uint16_t>> inst_q((size_t)(cliques ? C : 0));
     // pass 1: sizes, degrees, cliques
-    parallel_for(C, 1, [&](int job) {
+    parallel_strided(C, 256, [&](int job) {
       const int c = by_size[job];
       const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
       int ne2 = 0, ns2 = 0, mdc = 0, mds = 0;
@@ -736,7 +748,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     p->scratch_bytes = (size_t)scratch;
     p->h_arena.assign((size_t)arena, 0);
     // pass 2: the read-only blocks
-    parallel_for(C, 1, [&](int job) {
+    parallel_strided(C, 256, [&](int job) {
       const int c = by_size[job];
       const int a = p->comp_ptr[c], b = p->comp_ptr[c + 1], nc = b - a;
       const int nq = p->inst_nq[c];
