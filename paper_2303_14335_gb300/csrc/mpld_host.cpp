@@ -563,7 +563,20 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
         if (first[u]) queue.push_back(u);
       // the queue is the removal order; a removed unit's degree is never
       // read again, so its neighbours may still decrement it
+      // the walk is bound by memory latency: the units a few places ahead in
+      // the queue have their ranges, segments and neighbour states fetched
+      // early, one level per distance
+      const int32_t *uptr = p->uptr.data(), *useg = p->useg.data(), *cptr = p->cptr.data();
       for (size_t h = 0; h < queue.size(); ++h) {
+        const size_t qn = queue.size();
+        if (h + 12 < qn) __builtin_prefetch(uptr + queue[h + 12]);
+        if (h + 8 < qn) __builtin_prefetch(useg + uptr[queue[h + 8]]);
+        if (h + 4 < qn) __builtin_prefetch(cptr + useg[uptr[queue[h + 4]]]);
+        if (h + 2 < qn) {
+          const int s2 = useg[uptr[queue[h + 2]]];
+          for (int i = cptr[s2], e = std::min(cptr[s2 + 1], cptr[s2] + 8); i < e; ++i)
+            __builtin_prefetch(st.data() + uadj[i]);
+        }
         const int u = queue[h];
         removed[u] = 1;
         for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) {
@@ -618,7 +631,9 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
         if (alive[s]) p->comp_of[s] = single ? single_id : id_of[parent[s]];
       });
     }
-    for (int u : p->removed_order) p->n_removed_segments += p->uptr[u + 1] - p->uptr[u];
+    // every segment is either in a removed unit or in an instance
+    p->n_removed_segments = n;
+    for (int s = 0; s < n; ++s) p->n_removed_segments -= alive[s];
     int C = p->n_comp;
     p->comp_ptr.assign((size_t)C + 1, 0);
     for (int s = 0; s < n; ++s)
