@@ -42,6 +42,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "mpld_internal.h"
 #include "../../include/mpld.h"
 
@@ -1563,10 +1565,14 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
 
 // Largest dynamic shared memory size already granted to the kernel; the
 // attribute is only raised, and only outside stream capture (the shape is
-// chosen, and the attribute set, before any capture begins).
+// chosen, and the attribute set, before any capture begins).  Callers on
+// several threads (the server's, the user's) raise it under one lock, so it
+// never goes down.
 int g_smem_granted = 48 * 1024;
+std::mutex g_smem_mu;
 
 int ensure_smem(size_t smem) {
+  std::lock_guard<std::mutex> lk(g_smem_mu);
   if ((int)smem <= g_smem_granted) return MPLD_OK;
   if (cudaFuncSetAttribute(mpld_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess) {
@@ -1628,7 +1634,6 @@ extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes) {
 // Layout of the array: [0, 256) status word; then the read-only block of
 // the instance; then its mutable search state.
 
-#include <mutex>
 #include <stddef.h>
 
 namespace mpld {
