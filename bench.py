@@ -38,11 +38,11 @@ METRIC = "EC search nodes/s & segments/s (batched vs plain GPU vs CPU DLX); p99 
 
 # DRAM bytes per launch of the search kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the workload scaled down
-# by 10 (23,960 segments: 761,088 B read, 0 written), per segment; traffic
+# by 10 (23,960 segments: 704,000 B read, 0 written), per segment; traffic
 # grows with the packed matrices, i.e. with the segments.  Valid only for the
 # kernel source it was measured on.
-TRAFFIC = {"k3_n200k_p02_batched": {"bytes_per_segment": 761088 / 23960,
-                                    "kernel_sha256_16": "ebfbaccfe542ad1b",
+TRAFFIC = {"k3_n200k_p02_batched": {"bytes_per_segment": 704000 / 23960,
+                                    "kernel_sha256_16": "5c297bd97727abad",
                                     "profile": "profiles/mpld_search_kernel_k3_n20k_budget64k.md"}}
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 
