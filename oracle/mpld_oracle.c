@@ -25,7 +25,7 @@
  * which makes the search exact.  Stitch edges carry cost only; they have no
  * columns.
  *
- * Canonical order (the reading this build fixes where the paper is silent):
+ * Canonical order (the reading fixed here where the paper is silent):
  *   - node = one call of search(); the root counts;
  *   - leaf: every primary column covered; a leaf with cost g < best becomes
  *     the incumbent; best == 0 ends the search;
