@@ -1311,21 +1311,35 @@ int mpld_internal_finish(mpld_problem *p, const InstResult *hres, const int8_t *
       m[p->comp_seg[t]] = (int8_t)x;
     }
   }
-  // recovery: reverse removal order, lowest mask unused by coloured neighbours
-  for (auto it = p->removed_order.rbegin(); it != p->removed_order.rend(); ++it) {
-    const int u = *it;
-    unsigned used = 0;
-    for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) {
-      const int s = p->useg[t];
-      for (int i = p->cptr[s]; i < p->cptr[s + 1]; ++i) {
-        const int x = m[p->cadj[i]];
-        if (x >= 0) used |= 1u << x;
+  // recovery: reverse removal order, lowest mask unused by coloured neighbours.
+  // Units a few places ahead in that order have their ranges, segments,
+  // adjacency and neighbour masks fetched early, as in the peel.
+  {
+    const int32_t *ro = p->removed_order.data(), *uptr = p->uptr.data(), *useg = p->useg.data(),
+                  *cptr = p->cptr.data(), *cadj = p->cadj.data();
+    for (int h = (int)p->removed_order.size() - 1; h >= 0; --h) {
+      if (h >= 12) __builtin_prefetch(uptr + ro[h - 12]);
+      if (h >= 8) __builtin_prefetch(useg + uptr[ro[h - 8]]);
+      if (h >= 4) __builtin_prefetch(cadj + cptr[useg[uptr[ro[h - 4]]]]);
+      if (h >= 2) {
+        const int s2 = useg[uptr[ro[h - 2]]];
+        for (int i = cptr[s2], e = std::min(cptr[s2 + 1], cptr[s2] + 8); i < e; ++i)
+          __builtin_prefetch(m.data() + cadj[i]);
       }
+      const int u = ro[h];
+      unsigned used = 0;
+      for (int t = uptr[u]; t < uptr[u + 1]; ++t) {
+        const int s = useg[t];
+        for (int i = cptr[s]; i < cptr[s + 1]; ++i) {
+          const int x = m[cadj[i]];
+          if (x >= 0) used |= 1u << x;
+        }
+      }
+      int c = 0;
+      while (c < p->k && ((used >> c) & 1u)) ++c;
+      if (c == p->k) return MPLD_E_STATE;
+      for (int t = uptr[u]; t < uptr[u + 1]; ++t) m[useg[t]] = (int8_t)c;
     }
-    int c = 0;
-    while (c < p->k && ((used >> c) & 1u)) ++c;
-    if (c == p->k) return MPLD_E_STATE;
-    for (int t = p->uptr[u]; t < p->uptr[u + 1]; ++t) m[p->useg[t]] = (int8_t)c;
   }
   // monochromatic conflict edges and cut stitch edges, counted in chunks
   std::atomic<int64_t> nconf_a{0}, nst_a{0};
