@@ -365,7 +365,8 @@ def main():
         "nodes_per_s": nodes_per_s,
         "search": {"nodes": res.nodes, "cost": res.cost, "conflicts": res.n_conflicts,
                    "stitches": res.n_stitches, "budget_instances": res.n_budget_components,
-                   "status": rc, "step_ms": step_ms},
+                   "status": rc, "step_ms": step_ms,
+                   "median_step_ms": statistics.median(step_ms) if step_ms else None},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
