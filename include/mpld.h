@@ -86,17 +86,21 @@ extern "C" {
                                     leaf is unchanged; fewer nodes.  Read by mpld_build_matrix
                                     (and mpld_server_submit); MPLD_E_TOO_LARGE above 65,535
                                     cliques in one instance. */
-#define MPLD_PARALLEL_EXACT 64u  /* exact search (node_budget must be 0, else MPLD_E_INVALID) with the
-                                    warps of one CTA splitting each instance of at least 16
-                                    segments that fits the register-resident form (at most 128
-                                    segments, 64 at k = 8): the tree is cut at the first depth D
-                                    with k^D >= 4 * warps, and the warps take its k^D subtrees
-                                    in depth-first order from a shared counter, sharing the
-                                    incumbent as (cost, subtree).  Cost and masks are those of
-                                    the one-warp search (the first minimum-cost leaf); node
-                                    counts depend on timing; the clique bound is not applied
-                                    inside split instances.  Read by the search calls except
-                                    mpld_search_instance_noalloc (MPLD_E_INVALID) and the
+#define MPLD_PARALLEL_EXACT 64u  /* exact search (node_budget must be 0, else MPLD_E_INVALID) with
+                                    many warps splitting each instance of at least 16 segments
+                                    that fits the register-resident form (at most 128 segments,
+                                    64 at k = 8): the tree is cut at the first depth D with
+                                    k^D >= 16 * warps, and the warps take its k^D subtrees in
+                                    depth-first order from a shared counter, sharing the
+                                    incumbent as (cost, subtree).  An instance searched alone
+                                    (mpld_solve, a one-instance problem) is split by every warp
+                                    of the grid; in a batched call the 16 largest such instances
+                                    are split by the whole grid one after another, then the
+                                    others by the warps of one CTA each.  Cost and masks are
+                                    those of the one-warp search (the first minimum-cost leaf);
+                                    node counts depend on timing; the clique bound is not
+                                    applied inside split instances.  Read by the search calls
+                                    except mpld_search_instance_noalloc (MPLD_E_INVALID) and the
                                     server (ignored). */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
