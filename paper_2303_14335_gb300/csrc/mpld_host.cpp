@@ -491,44 +491,44 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
   p->Cs = g->cost_stitch;
   p->flags = params ? params->flags : 0u;
   try {
-    // conflict and stitch edges are normalised and put in CSR form side by side
+    // conflict edges are normalised and put in CSR form on one thread while
+    // another does the same for the stitch edges and then builds the units
+    // (polygons merged along stitch edges, id = lowest segment), which need
+    // nothing else
     std::vector<int32_t> sptr, sadj;
+    std::vector<int32_t> parent((size_t)n);
     bool ok[2] = {true, true};
     parallel_for(2, 1, [&](int which) {
       if (which == 0) {
         ok[0] = normalise(n, g->n_conf, g->conf_u, g->conf_v, p->cu, p->cv);
         if (ok[0]) csr(n, p->cu, p->cv, p->cptr, p->cadj);
-      } else {
-        ok[1] = normalise(n, g->n_stitch, g->st_u, g->st_v, p->su, p->sv);
-        if (ok[1]) csr(n, p->su, p->sv, sptr, sadj);
+        return;
       }
+      ok[1] = normalise(n, g->n_stitch, g->st_u, g->st_v, p->su, p->sv);
+      if (!ok[1]) return;
+      csr(n, p->su, p->sv, sptr, sadj);
+      std::iota(parent.begin(), parent.end(), 0);
+      {
+        std::vector<int32_t> first_of((size_t)n, -1);
+        for (int s = 0; s < n; ++s) {
+          const int poly = g->polygon_of ? g->polygon_of[s] : s;
+          if (first_of[poly] < 0) first_of[poly] = s;
+          else unite_min(parent, first_of[poly], s);
+        }
+      }
+      for (size_t e = 0; e < p->su.size(); ++e) unite_min(parent, p->su[e], p->sv[e]);
+      p->unit_of.resize((size_t)n);
+      for (int s = 0; s < n; ++s) p->unit_of[s] = find_root(parent, s);
+      p->uptr.assign((size_t)n + 1, 0);
+      for (int s = 0; s < n; ++s) p->uptr[p->unit_of[s] + 1]++;
+      for (int u = 0; u < n; ++u) p->uptr[u + 1] += p->uptr[u];
+      p->useg.resize((size_t)n);
+      std::vector<int32_t> fill(p->uptr.begin(), p->uptr.end() - 1);
+      for (int s = 0; s < n; ++s) p->useg[fill[p->unit_of[s]]++] = s;
     });
     if (!ok[0] || !ok[1]) {
       delete p;
       return MPLD_E_INVALID;
-    }
-
-    // ---- units: polygons merged along stitch edges, id = lowest segment
-    std::vector<int32_t> parent((size_t)n);
-    std::iota(parent.begin(), parent.end(), 0);
-    {
-      std::vector<int32_t> first_of((size_t)n, -1);
-      for (int s = 0; s < n; ++s) {
-        const int poly = g->polygon_of ? g->polygon_of[s] : s;
-        if (first_of[poly] < 0) first_of[poly] = s;
-        else unite_min(parent, first_of[poly], s);
-      }
-    }
-    for (size_t e = 0; e < p->su.size(); ++e) unite_min(parent, p->su[e], p->sv[e]);
-    p->unit_of.resize((size_t)n);
-    for (int s = 0; s < n; ++s) p->unit_of[s] = find_root(parent, s);
-    p->uptr.assign((size_t)n + 1, 0);
-    for (int s = 0; s < n; ++s) p->uptr[p->unit_of[s] + 1]++;
-    for (int u = 0; u < n; ++u) p->uptr[u + 1] += p->uptr[u];
-    p->useg.resize((size_t)n);
-    {
-      std::vector<int32_t> fill(p->uptr.begin(), p->uptr.end() - 1);
-      for (int s = 0; s < n; ++s) p->useg[fill[p->unit_of[s]]++] = s;
     }
 
     // ---- simplification: FIFO peel of units with < k external conflict edges
