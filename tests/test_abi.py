@@ -234,3 +234,44 @@ def test_solve_on_host_only_handle_is_a_state_error():
 def test_empty_layout():
     prob = host_only(synth.graph_from_edges(0, 3, []))
     assert mpld.mpld_problem_info(prob).n_components == 0
+
+
+def test_builds_are_identical_alone_and_concurrent():
+    # the host build uses a shared thread pool (parallel union-find, packing);
+    # builds on several threads at once take the inline path: every build
+    # must give the same instances, ids and packed matrices
+    import threading
+    L = synth.unit_disk_layout(20000, 3, seed=8, mean_deg=3.0, p_stitch=0.2)
+
+    def digest(prob):
+        info = mpld.mpld_problem_info(prob)
+        comp_of = mpld.mpld_component_results(prob, results=False)[3]
+        mats = [mpld.mpld_export_matrix(prob, c).tobytes()
+                for c in range(0, info.n_components, max(1, info.n_components // 20))]
+        return (info.n_components, info.arena_bytes, info.instance_segments,
+                comp_of.tobytes(), tuple(mats))
+
+    first = host_only(L)
+    ref = digest(first)
+    first.close()
+    for _ in range(2):
+        p = host_only(L)
+        assert digest(p) == ref
+        p.close()
+    out, errs = [None] * 4, []
+
+    def worker(i):
+        try:
+            p = host_only(L)
+            out[i] = digest(p)
+            p.close()
+        except Exception as e:  # surfaced below
+            errs.append(e)
+
+    ts = [threading.Thread(target=worker, args=(i,)) for i in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs
+    assert all(o == ref for o in out)
