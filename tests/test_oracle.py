@@ -54,6 +54,9 @@ def test_golden_hand_traces():
     for c in g["cases"]:
         r = oracle.solve_instance(c["n"], c["k"], c["conf"], c["stitch"])
         assert (r.cost, r.x.tolist(), r.nodes) == (c["cost"], c["x"], c["nodes"]), c["name"]
+        # the same numbers from the recursion over the partial assignment
+        cost, x, nodes, hit = bounded_search(c["n"], c["k"], c["conf"], c["stitch"])
+        assert (cost, x, nodes, hit) == (c["cost"], c["x"], c["nodes"], False), c["name"]
 
 
 @pytest.mark.parametrize("n,k,conf,cost,n_opt", [
