@@ -5,14 +5,24 @@ One step = the whole search path over one synthetic layout (unit-disk
 conflict graph, 200,000 polygons, mean degree 3, stitch p = 0.2, k = 3,
 seed 2): every connected sub-graph left after simplification is searched by
 the persistent batched kernel (one launch, device work queue, replayed from a
-CUDA graph).  ``value`` = decomposed segments per second with the EC
-matrices already resident in HBM; ``e2e`` = the same metric through the C
-ABI from host graph arrays to host masks (build + upload + search + copy
-back + recovery + counts), for K layouts submitted together to the serving
-API so that the host work of one overlaps the search of another
-(``e2e.serial``: one layout at a time through mpld_build_matrix and
-mpld_solve_batch).  Every search instance has the same node budget
-on the GPU and in the CPU oracle, so both compute the same answer.
+CUDA graph).  ``value`` = segments searched per second of kernel time, with
+the EC matrices already resident in HBM: the segments inside the search
+instances, not the ones simplification removed before the search (those are
+recovered on the host afterwards and counted in ``e2e``).  ``e2e`` = all
+segments of the layout per second through the C ABI from host graph arrays
+to host masks (build + upload + search + copy back + recovery + counts), for
+K layouts submitted together to the serving API so that the host work of one
+overlaps the search of another (``e2e.serial``: one layout at a time through
+mpld_build_matrix and mpld_solve_batch).  ``cpu_baseline`` is the oracle's
+search phase on the same instances, same metric; its whole decomposition is
+reported beside it.  Every search instance has the same node budget on the
+GPU and in the CPU oracle, so both compute the same answer.
+
+Also in the line: ``serving`` (Poisson streams of whole layouts at 10, 100
+and 1000 requests/s through the server, p50 / p99 latency) and ``configs``
+(the other workloads: 24-segment instance searched exactly, the 506-segment
+single instance, the k = 4 layout), each with its oracle time and whether
+the GPU result matches the oracle element by element.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank decomposes its own layout (seed + 1000 *
@@ -73,11 +83,15 @@ def parse_args():
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the workload's polygon count (same density and degree); "
                          "for small profiling cases")
-    ap.add_argument("--serve", action="store_true",
-                    help="also run the serving loop at 10, 100 and 1000 requests/s")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving loop (10, 100 and 1000 requests/s)")
+    ap.add_argument("--serve-seconds", type=float, nargs=3, default=[8.0, 4.0, 2.0],
+                    help="arrival span of the 10, 100 and 1000 requests/s streams")
     ap.add_argument("--serve-budget", type=int, default=1 << 12)
-    ap.add_argument("--serve-pool", type=int, default=48,
+    ap.add_argument("--serve-pool", type=int, default=24,
                     help="distinct pre-generated requests the Poisson streams cycle through")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the legs of the other workloads")
     ap.add_argument("--plain-scale", type=int, default=20,
                     help="the plain one-launch-per-instance path runs on the same workload with "
                          "polygons / plain-scale (same density and degree)")
@@ -174,7 +188,7 @@ def run_serving(args, mpld, synth):
     pool_segments = [L.n_seg for L in pool]
     out = {"budget": args.serve_budget, "pool_requests": len(pool),
            "pool_mean_segments": float(np.mean(pool_segments)), "loads": []}
-    for rate, duration in ((10, 12.0), (100, 6.0), (1000, 3.0)):
+    for rate, duration in zip((10, 100, 1000), args.serve_seconds):
         n = int(rate * duration)
         arrivals = synth.poisson_arrivals(777 + rate, n, rate)
         cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
@@ -226,12 +240,7 @@ def run_serving(args, mpld, synth):
     return out
 
 
-def run_reference(args, rank, world):
-    """The CPU oracle (Knuth dancing links on all host cores) on the same workload."""
-    if rank != 0:
-        return
-    import oracle
-    layout, mode = workload_layout(args.workload, 0)
+def oracle_flags(oracle, args, mode):
     flags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
     if args.column_rule == "bfs":
         flags |= oracle.COLUMN_BFS
@@ -239,35 +248,108 @@ def run_reference(args, rank, world):
         flags |= oracle.BICONNECTED
     if args.clique_bound:
         flags |= oracle.CLIQUE_BOUND
+    return flags
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle (Knuth dancing links on all host cores) on the same workload.
+
+    value = segments inside the search instances per second of the oracle's
+    search phase (the same metric as the GPU line's value); the whole
+    decomposition (simplify, split, search, recover, count) is reported
+    beside it."""
+    if rank != 0:
+        return
+    import oracle
+    layout, mode = workload_layout(args.workload, 0)
+    flags = oracle_flags(oracle, args, mode)
     cores = os.cpu_count() or 1
     oracle.build()
     for _ in range(args.warmup):
         oracle.decompose(layout, flags=flags, budget=args.budget, nthreads=cores)
-    times = []
+    search_s, whole_s = [], []
     res = None
     for _ in range(args.steps):
         t0 = time.perf_counter()
         res = oracle.decompose(layout, flags=flags, budget=args.budget, nthreads=cores)
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = layout.n_seg * args.steps / total
+        whole_s.append(time.perf_counter() - t0)
+        search_s.append(res.search_seconds)
+    total = sum(search_s)
+    value = res.instance_segments * args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "segments/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "segments": layout.n_seg, "k": layout.k,
+                   "instance_segments": res.instance_segments,
                    "node_budget": args.budget, "column_rule": args.column_rule,
                    "biconnected": bool(args.biconnected and mode != "single"),
                    "clique_bound": bool(args.clique_bound)},
         "nodes_per_s": res.nodes * args.steps / total,
+        "whole_decomposition": {"segments_per_s": layout.n_seg * args.steps / sum(whole_s),
+                                "ms_per_step": 1000 * sum(whole_s) / args.steps,
+                                "form": "simplify, split, search, recover, count"},
         "cpu_baseline": {"value": value, "unit": "segments/s", "cores": cores, "kind": "oracle",
-                         "sample": f"whole layout ({layout.n_seg} segments, "
-                                   f"{res.n_components} instances) per step"},
+                         "sample": f"search phase of the whole layout ({res.instance_segments} "
+                                   f"instance segments, {res.n_components} instances) per step"},
         "e2e": {"value": value, "unit": "segments/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def config_leg(name, budget, search_flags, label, mpld, oracle, torch, stream, flush, cores,
+               reps=3):
+    """One other workload: batched search timed with CUDA events (median of
+    ``reps`` after one warm-up, L2 flushed before each), then the oracle on
+    the same layout and budget (one thread for single-instance workloads,
+    every host core for layouts), compared element by element."""
+    import numpy as np
+    layout, mode = workload_layout(name, 0)
+    s = stream.cuda_stream
+    flags = (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE) if mode == "single" else 0
+    prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
+    try:
+        info = mpld.mpld_problem_info(prob)
+        prm = mpld.make_params(node_budget=budget, flags=search_flags)
+        if mode != "single":
+            mpld.mpld_autotune([prob], prm, s)
+        mpld.mpld_search_batch_async([prob], prm, s)
+        stream.synchronize()
+        ms = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mpld.mpld_search_batch_async([prob], prm, s)
+            e1.record(stream)
+            stream.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        rc, mask, res = mpld.mpld_fetch(prob, s)
+    finally:
+        prob.close()
+    med = statistics.median(ms) / 1000.0
+    oflags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
+    nthreads = 1 if mode == "single" else cores
+    ref = oracle.decompose(layout, flags=oflags, budget=budget, nthreads=nthreads)
+    split = bool(search_flags & mpld.MPLD_PARALLEL_EXACT)
+    return {
+        "workload": name, "search": label, "node_budget": budget, "segments": layout.n_seg,
+        "instances": info.n_components, "max_instance": info.max_component,
+        "instance_segments": info.instance_segments, "ms_per_step": 1000 * med,
+        "step_ms": ms, "value": info.instance_segments / med, "unit": "segments/s",
+        "nodes_per_s": res.nodes / med, "nodes": res.nodes, "cost": res.cost,
+        "budget_instances": res.n_budget_components, "status": rc,
+        "oracle": {"value": ref.instance_segments / ref.search_seconds, "unit": "segments/s",
+                   "search_ms": 1000 * ref.search_seconds, "threads": nthreads,
+                   "nodes_per_s": ref.nodes / ref.search_seconds, "nodes": ref.nodes},
+        "gpu_over_oracle": ref.search_seconds / med,
+        # split subtrees: node counts depend on timing, the answer does not
+        "matches_gpu": bool(np.array_equal(ref.mask, mask) and ref.cost == res.cost and
+                            (split or ref.nodes == res.nodes)),
+    }
 
 
 def main():
@@ -335,11 +417,15 @@ def main():
     total_s = sum(step_ms) / 1000.0
     if dist:
         from paper_2303_14335_gb300 import shard
-        all_segments, total_s = shard.aggregate(dist, layout.n_seg, total_s, "cuda")
+        all_segments, _ = shard.aggregate(dist, layout.n_seg, total_s, "cuda")
+        searched, total_s = shard.aggregate(dist, info.instance_segments, total_s, "cuda")
     else:
         all_segments = float(layout.n_seg)
+        searched = float(info.instance_segments)
     rc, mask, res = mpld.mpld_fetch(prob, s)
-    value = all_segments * args.steps / total_s
+    # segments the timed kernel searched (simplification removed the rest on
+    # the host before the search; they are recovered after it)
+    value = searched * args.steps / total_s
     nodes_per_s = res.nodes * world * args.steps / total_s
 
     out = {
@@ -354,8 +440,11 @@ def main():
                    "clique_bound": bool(flags & mpld.MPLD_CLIQUE_BOUND),
                    "parallel_exact": bool(args.parallel_exact),
                    "instances": info.n_components,
+                   "instance_segments": info.instance_segments,
                    "max_instance": info.max_component,
                    "removed_segments": info.n_removed_segments,
+                   "value_counts": "segments inside the search instances (removed segments "
+                                   "are recovered on the host and counted in e2e only)",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"weak: {world} independent layouts" if world > 1 else "1 GPU",
                    "launch": ({"warps_per_cta": tune.warps_per_cta, "slot_bytes": tune.slot_bytes,
@@ -398,14 +487,12 @@ def main():
     # the derived peak above)
     import ctypes
     pk = (ctypes.c_double * 2)()
-    fn = mpld.library().mpld_internal_int_peak
-    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
-    fn.restype = ctypes.c_int
+    fn = mpld.probe_library().mpld_probe_int_peak
     if fn(1 << 14, pk) == 0:
         out["roofline"]["int_pipes_measured"] = {
             "logic_add_gops": pk[0], "logic_popc_add_gops": pk[1],
             "frac_of_logic_popc_add": achieved / pk[1],
-            "source": "mpld_internal_int_peak: 8 independent chains per thread, 2,048 threads "
+            "source": "mpld_probe_int_peak (libmpld_probe.so): 8 independent chains per thread, 2,048 threads "
                       "per SM, every SM"}
 
     if not args.no_e2e:
@@ -501,38 +588,45 @@ def main():
             times[name] = e0.elapsed_time(e1) / 1000.0
         ps.close()
         out["plain"] = {"segments": small.n_seg, "instances": pinfo.n_components,
-                        "plain_segments_per_s": small.n_seg / times["plain"],
-                        "batched_segments_per_s": small.n_seg / times["batched"],
+                        "instance_segments": pinfo.instance_segments,
+                        "plain_segments_per_s": pinfo.instance_segments / times["plain"],
+                        "batched_segments_per_s": pinfo.instance_segments / times["batched"],
                         "batched_over_plain": times["plain"] / times["batched"],
                         "gpu_launches_plain": pinfo.n_components}
 
-    if rank == 0 and args.serve:
+    if rank == 0 and not args.no_serve:
         from paper_2303_14335_gb300 import synth
         out["serving"] = run_serving(args, mpld, synth)
 
+    cores = os.cpu_count() or 1
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
-        cores = os.cpu_count() or 1
         t0 = time.perf_counter()
-        oflags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
-        if args.column_rule == "bfs":
-            oflags |= oracle.COLUMN_BFS
-        if flags & mpld.MPLD_BICONNECTED:
-            oflags |= oracle.BICONNECTED
-        if flags & mpld.MPLD_CLIQUE_BOUND:
-            oflags |= oracle.CLIQUE_BOUND
-        ref = oracle.decompose(layout, flags=oflags, budget=args.budget, nthreads=cores)
+        ref = oracle.decompose(layout, flags=oracle_flags(oracle, args, mode), budget=args.budget,
+                               nthreads=cores)
         dt = time.perf_counter() - t0
-        out["cpu_baseline"] = {"value": layout.n_seg / dt, "unit": "segments/s", "cores": cores,
-                               "kind": "oracle",
-                               "sample": f"whole layout ({layout.n_seg} segments, "
-                                         f"{ref.n_components} instances), one decomposition",
-                               "nodes_per_s": ref.nodes / dt,
-                               # with split subtrees the node count depends on timing
-                               "matches_gpu": bool(np.array_equal(ref.mask, mask) and
-                                                   ref.cost == res.cost and
-                                                   (args.parallel_exact or ref.nodes == res.nodes))}
+        out["cpu_baseline"] = {
+            "value": ref.instance_segments / ref.search_seconds, "unit": "segments/s",
+            "cores": cores, "kind": "oracle",
+            "sample": f"search phase of the whole layout ({ref.instance_segments} instance "
+                      f"segments, {ref.n_components} instances), one decomposition",
+            "nodes_per_s": ref.nodes / ref.search_seconds,
+            "search_ms": 1000 * ref.search_seconds,
+            "whole_decomposition": {"segments_per_s": layout.n_seg / dt, "ms": 1000 * dt},
+            # with split subtrees the node count depends on timing
+            "matches_gpu": bool(np.array_equal(ref.mask, mask) and ref.cost == res.cost and
+                                (args.parallel_exact or ref.nodes == res.nodes))}
+
+    if rank == 0 and not args.no_configs:
+        import oracle
+        oracle.build()
+        legs = [("k3_n24_plain", 0, mpld.MPLD_PARALLEL_EXACT,
+                 "exact, subtrees split over every warp of the grid"),
+                ("k3_n400_p025_plain", args.budget, 0, "one warp, node budget"),
+                ("k4_n100k_p03_batched", args.budget, 0, "batched, node budget")]
+        out["configs"] = [config_leg(n, b, f, lab, mpld, oracle, torch, stream, flush, cores)
+                          for n, b, f, lab in legs if n != args.workload]
     prob.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -381,18 +381,26 @@ void mpld_server_destroy(mpld_server *s);
  * MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE.
  *
  *   inst        host struct holding sizes and DEVICE pointers: conflict and
- *               stitch adjacency in CSR form (ptr[n+1], nbr[ptr[n]]), both
- *               directions of every edge, no self-loops or duplicates;
+ *               stitch adjacency in CSR form (ptr[n+1], nbr[ptr[n]]), each
+ *               list in ascending order, both directions of every edge, no
+ *               self-loops or duplicates;
  *   params      node_budget and time_limit_ms are used; NULL = defaults;
  *   mask_out    DEVICE, n int8: best assignment found;
- *   result_out  DEVICE: cost, node count and status (status MPLD_E_INVALID
- *               if the kernel found a neighbour id out of range, a
- *               self-loop or a bad offset; the mask is then not written);
+ *   result_out  DEVICE: cost, node count and status.  The kernel checks the
+ *               CSR before searching: a neighbour id out of range, a
+ *               self-loop, a list out of order, a bad offset, or an edge
+ *               listed from one end only give status MPLD_E_INVALID, and
+ *               the mask is then not written.  device_error is 0, or
+ *               MPLD_E_TIMEOUT when the copy of the packed instance into
+ *               shared memory did not land in time (the search then ran
+ *               from the library's array and its result stands);
  *   stream      all work is enqueued on it; the call does not wait.
  * Returns MPLD_E_INVALID for bad sizes, k or costs, MPLD_E_TOO_LARGE when the
  * instance needs more than MPLD_NOALLOC_SCRATCH_BYTES bytes or has more than
  * MPLD_MAX_INSTANCE_SEGMENTS segments (nothing is launched then),
- * MPLD_E_CUDA on a failed launch.
+ * MPLD_E_CUDA on a failed launch, or when a CUDA error left by earlier work
+ * of the caller is still pending (nothing is launched, and that error is
+ * left pending for the caller).
  *
  * The first call on a device (the device current at the call) looks up the
  * array's device address and sets the kernel's shared-memory limit; make
@@ -417,7 +425,7 @@ typedef struct {
   int64_t cost;
   int64_t nodes;
   int32_t status;               /* MPLD_OK, MPLD_BUDGET, MPLD_TIMEOUT or MPLD_E_INVALID */
-  int32_t reserved;
+  int32_t device_error;         /* 0, or MPLD_E_TIMEOUT (see above) */
   int64_t work;                 /* as mpld_result.work */
 } mpld_instance_result;
 

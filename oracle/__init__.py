@@ -54,7 +54,8 @@ class _Totals(ctypes.Structure):
                 ("n_conflicts", ctypes.c_int64), ("n_stitches", ctypes.c_int64),
                 ("cost", ctypes.c_int64), ("nodes", ctypes.c_int64),
                 ("component_cost_sum", ctypes.c_int64), ("n_budget_components", ctypes.c_int64),
-                ("status", ctypes.c_int32), ("max_component", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("max_component", ctypes.c_int32),
+                ("search_seconds", ctypes.c_double), ("instance_segments", ctypes.c_int64)]
 
 
 _lib = None
@@ -204,6 +205,8 @@ class LayoutResult:
     component_cost_sum: int
     n_budget_components: int
     max_component: int
+    search_seconds: float = 0.0    # wall time of the search phase alone (timing, not a result)
+    instance_segments: int = 0     # segments inside search instances
 
 
 def decompose(layout, *, flags: int = 0, budget: int = 0, nthreads: int = 1) -> LayoutResult:
@@ -235,4 +238,6 @@ def decompose(layout, *, flags: int = 0, budget: int = 0, nthreads: int = 1) -> 
                         cost=int(tot.cost), nodes=int(tot.nodes),
                         component_cost_sum=int(tot.component_cost_sum),
                         n_budget_components=int(tot.n_budget_components),
-                        max_component=int(tot.max_component))
+                        max_component=int(tot.max_component),
+                        search_seconds=float(tot.search_seconds),
+                        instance_segments=int(tot.instance_segments))

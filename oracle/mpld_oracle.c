@@ -70,12 +70,14 @@
  * components (conflict + stitch edges), each searched on its own with
  * component-local ids in ascending global id.
  */
+#define _POSIX_C_SOURCE 199309L   /* clock_gettime under -std=c11 */
 #include <limits.h>
 #include <pthread.h>
 #include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #define OR_OK 0
 #define OR_BUDGET 1
@@ -592,7 +594,18 @@ typedef struct {
   int64_t n_conflicts, n_stitches, cost, nodes;
   int64_t component_cost_sum, n_budget_components;
   int32_t status, max_component;
+  /* timing of the search phase alone (the instances' matrices built and
+   * searched on the thread pool), for throughput figures; not part of the
+   * result */
+  double search_seconds;
+  int64_t instance_segments;   /* segments inside search instances */
 } oracle_totals;
+
+static double wall_seconds(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 typedef struct {
   /* shared, read-only */
@@ -1203,11 +1216,14 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
     pthread_attr_init(&attr);
     pthread_attr_setstacksize(&attr, (size_t)256 << 20);   /* deep recursion */
     int started = 0;
+    const double t_search = wall_seconds();
     for (int t = 0; t < nt; ++t)
       if (pthread_create(&th[t], &attr, pool_worker, &P) == 0) started++;
       else break;
     pthread_attr_destroy(&attr);
     for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    tot->search_seconds = wall_seconds() - t_search;
+    tot->instance_segments = len_seg;
     free(th);
     if (started == 0) goto done;
     if (atomic_load(&P.error)) { rc = atomic_load(&P.error); goto done; }

@@ -2,7 +2,9 @@
 
 The library is built with nvcc straight from ``csrc/`` into
 ``paper_2303_14335_gb300/_build/libmpld.so``; no torch extension machinery is
-involved, because the ABI is plain C.
+involved, because the ABI is plain C.  The integer-pipe throughput probe the
+benchmark reports beside its roofline (``csrc/probe/``) goes into a separate
+``_build/libmpld_probe.so``: measurement support, not part of the library.
 """
 from __future__ import annotations
 
@@ -15,7 +17,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpld.so")
-SOURCES = ["mpld_search.cu", "mpld_host.cpp", "mpld_serve.cpp", "mpld_peak.cu"]
+SOURCES = ["mpld_search.cu", "mpld_host.cpp", "mpld_serve.cpp"]
+PROBE_SOURCES = [os.path.join("probe", "int_peak.cu")]
+PROBE_LIB = os.path.join(OUT_DIR, "libmpld_probe.so")
 HEADERS = ["mpld_internal.h", "mpld_problem.h", os.path.join("..", "..", "include", "mpld.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-Wall"]
@@ -27,11 +31,14 @@ def _nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [__file__]
-    return any(os.path.getmtime(d) > t for d in deps)
+    for lib, srcs in ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES)):
+        if not os.path.exists(lib):
+            return True
+        t = os.path.getmtime(lib)
+        deps = [os.path.join(CSRC, s) for s in srcs + HEADERS] + [__file__]
+        if any(os.path.getmtime(d) > t for d in deps):
+            return True
+    return False
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -43,18 +50,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [nvcc, *ARCH, *COMMON, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v") if verbose else None
         subprocess.run(cmd, check=True, capture_output=not verbose)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], check=True)
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + len(PROBE_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES + PROBE_SOURCES))
+    for lib, o in ((LIB, objs[:len(SOURCES)]), (PROBE_LIB, objs[len(SOURCES):])):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *o, "-lpthread"], check=True)
+        os.replace(tmp, lib)
     return LIB
 
 

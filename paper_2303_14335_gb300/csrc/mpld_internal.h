@@ -207,6 +207,9 @@ struct ParCtx {
   uint32_t timed_out;
   uint32_t done;           // warps (or, in the queue, subtrees) finished
   uint32_t pad;
+  unsigned long long t0;   // %globaltimer when the first warp started on the
+                           // instance (0 = not yet): the time limit runs from
+                           // there for every warp, however late it joins
 };
 static_assert(sizeof(ParCtx) <= 64, "queue contexts are 64 bytes apart");
 

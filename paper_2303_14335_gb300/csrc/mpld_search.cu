@@ -58,7 +58,7 @@ constexpr uint32_t TMA_MIN_BYTES = 1024;     // smaller blocks use vector loads
 constexpr uint32_t WAIT_LIMIT = 1u << 22;    // bounded mbarrier wait
 constexpr uint32_t TEAM_BYTES = 320;          // a CTA team's reduction words and
                                               // the split exact search's context
-constexpr uint32_t PAR_CTX_OFF = 128;         // ParCtx (40 bytes)
+constexpr uint32_t PAR_CTX_OFF = 128;         // ParCtx (48 bytes)
 constexpr uint32_t PAR_WKEY_OFF = 176;        // each warp's best key (16 warps)
 static_assert(PAR_CTX_OFF + sizeof(ParCtx) <= PAR_WKEY_OFF && PAR_WKEY_OFF + 16 * 8 <= TEAM_BYTES,
               "split-search context must fit the shared-memory head");
@@ -968,7 +968,21 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
   uint32_t work32 = 0;
   bool timed_out = false, last_item = false;
   unsigned long long my_key = ~0ull, cached = mode == PAR_REPLAY ? replay_key : ~0ull;
-  const uint64_t t0 = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
+  // the instance's start: the first warp to arrive sets it, and every warp
+  // measures the time limit from there, so the limit bounds the instance's
+  // wall time, not each warp's.  The replay, which runs once the instance
+  // is done, has a limit of its own.
+  uint64_t t0 = 0;
+  if (lane == 0) {
+    const uint64_t now = globaltimer();
+    if (mode == PAR_REPLAY) {
+      t0 = now;
+    } else {
+      const unsigned long long prev = atomicCAS(&ctx->t0, 0ull, (unsigned long long)now);
+      t0 = prev != 0ull ? (uint64_t)prev : now;
+    }
+  }
+  t0 = __shfl_sync(FULL, t0, 0);
   int64_t next_check = 1024;
   // the pruning threshold for subtree s: a leaf must cost less than it
   auto threshold = [&](uint32_t s) -> int32_t {
@@ -1515,6 +1529,7 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
           ctx->next = 0;
           ctx->timed_out = 0;
           ctx->done = 0;
+          ctx->t0 = 0;
         }
         __syncthreads();
         uint8_t *mine = g_smem + slot_off;
@@ -1649,6 +1664,7 @@ static_assert(sizeof(mpld_instance_result) == sizeof(InstResult), "result layout
 static_assert(offsetof(mpld_instance_result, cost) == offsetof(InstResult, cost), "result layout");
 static_assert(offsetof(mpld_instance_result, nodes) == offsetof(InstResult, nodes), "result layout");
 static_assert(offsetof(mpld_instance_result, status) == offsetof(InstResult, status), "result layout");
+static_assert(offsetof(mpld_instance_result, device_error) == offsetof(InstResult, pad0), "result layout");
 static_assert(offsetof(mpld_instance_result, work) == offsetof(InstResult, work), "result layout");
 
 // One warp: check and pack the caller's adjacency into the array, then run
@@ -1692,11 +1708,41 @@ __global__ void __launch_bounds__(32, 1)
       prev = u;
     }
   }
+  // every edge must be listed from both ends: each entry u of v's list
+  // needs v in u's list (binary search in the packed copies, whose ranges
+  // and order were checked above)
+  if (!__any_sync(FULL, bad)) {
+    __syncwarp();
+    for (int v = lane; v < n && !bad; v += 32) {
+      const int2 p0 = ptr[v], p1 = ptr[v + 1];
+      for (int i = p0.x; i < p1.x && !bad; ++i) {
+        const int u = cn[i];
+        int lo = ptr[u].x, hi = ptr[u + 1].x;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if ((int)cn[mid] < v) lo = mid + 1;
+          else hi = mid;
+        }
+        bad = lo >= ptr[u + 1].x || (int)cn[lo] != v;
+      }
+      for (int i = p0.y; i < p1.y && !bad; ++i) {
+        const int u = sn[i];
+        int lo = ptr[u].y, hi = ptr[u + 1].y;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if ((int)sn[mid] < v) lo = mid + 1;
+          else hi = mid;
+        }
+        bad = lo >= ptr[u + 1].y || (int)sn[lo] != v;
+      }
+    }
+  }
   if (__any_sync(FULL, bad)) {
     if (lane == 0) {
       res_out->cost = INT64_MAX;
       res_out->nodes = 0;
       res_out->status = MPLD_E_INVALID;
+      res_out->pad0 = 0;
       res_out->work = 0;
     }
     return;
@@ -1747,6 +1793,10 @@ __global__ void __launch_bounds__(32, 1)
   else if (d.k == 2) run_instance<uint8_t, 2>(d, slot_off, slot_bytes, bar, phase, a, lane);
   else if (d.k <= 7) run_instance<uint8_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
   else run_instance<uint16_t, 8>(d, slot_off, slot_bytes, bar, phase, a, lane);
+  // the status word (a bulk copy that did not land in time: the search then
+  // ran from the array instead, and its result stands)
+  __syncwarp();
+  if (lane == 0) res_out->pad0 = *(volatile int32_t *)err;
 }
 
 // Per-device set-up of the allocation-free path: the array's device address
@@ -1776,6 +1826,12 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
       inst->cost_stitch > 10000)
     return MPLD_E_INVALID;
   if (n > MPLD_MAX_INSTANCE_SEGMENTS) return MPLD_E_TOO_LARGE;
+  // every adjacency entry takes at least two bytes of the array: larger
+  // entry counts cannot fit, and below this bound the 32-bit layout sums
+  // further down cannot wrap
+  if ((int64_t)ne2 > (int64_t)(MPLD_NOALLOC_SCRATCH_BYTES / 2) ||
+      (int64_t)ns2 > (int64_t)(MPLD_NOALLOC_SCRATCH_BYTES / 2))
+    return MPLD_E_TOO_LARGE;
   // row keys and path costs are 32-bit in the kernel (bound without degrees)
   if ((int64_t)inst->cost_conflict * ne2 + (int64_t)inst->cost_stitch * ns2 >= ((int64_t)1 << 28))
     return MPLD_E_TOO_LARGE;
@@ -1813,6 +1869,9 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
   const int slot = (int)fp <= nd->max_slot ? (int)fp : 0;   // else state stays in the array
   const int64_t budget = prm ? (prm->node_budget > 0 ? prm->node_budget : 0) : 0;
   const int64_t tl = (prm && prm->time_limit_ms > 0 ? prm->time_limit_ms : 60000) * 1000000ll;
+  // an error left pending by earlier work of the caller stays the caller's:
+  // nothing is launched, and the error is not consumed here
+  if (cudaPeekAtLastError() != cudaSuccess) return MPLD_E_CUDA;
   mpld_noalloc_kernel<<<1, 32, align16(8u) + (size_t)slot, (cudaStream_t)stream>>>(
       *inst, nd->scratch, mask_out, reinterpret_cast<InstResult *>(result_out), budget, tl, slot);
   return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;

@@ -1,4 +1,4 @@
-// mpld_peak.cu -- measured throughput of the integer pipes the search uses.
+// int_peak.cu -- measured throughput of the integer pipes the search uses.
 //
 // The search kernel's work is plain 32-bit integer arithmetic: logic ops and
 // adds on bit fields, and population counts.  Its roofline denominator is
@@ -6,13 +6,14 @@
 // pipes actually sustain on this device, for the same mix:
 //   mode 0: acc = (acc ^ x) + i        -- logic + add, 2 ops per step
 //   mode 1: acc += popc(x ^ acc)        -- logic + popcount + add, 3 ops
-// Each thread runs 8 independent chains; the grid fills every SM.  Test and
-// benchmark support, not part of the search path.
+// Each thread runs 8 independent chains; the grid fills every SM.  Built
+// into a library of its own (libmpld_probe.so) for the benchmark's roofline
+// context; libmpld.so does not contain it.
 #include <cuda_runtime.h>
 
 #include <stdint.h>
 
-#include "../../include/mpld.h"
+#include "../../../include/mpld.h"
 
 namespace {
 
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(256) int_pipe_kernel(uint32_t seed, int iters,
 
 // out[0]: logic + add throughput, out[1]: logic + popcount + add throughput,
 // both in 10^9 integer ops per second over every SM of the current device.
-extern "C" int mpld_internal_int_peak(int iters, double *out) {
+extern "C" int mpld_probe_int_peak(int iters, double *out) {
   if (!out || iters < 16) return MPLD_E_INVALID;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

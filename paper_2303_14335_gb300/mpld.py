@@ -146,6 +146,24 @@ def library(build_if_missing: bool = True) -> ctypes.CDLL:
     return _lib
 
 
+_probe = None
+
+
+def probe_library() -> ctypes.CDLL:
+    """Load libmpld_probe.so, the integer-pipe throughput probe the benchmark
+    reports beside its roofline (measurement support; not part of libmpld)."""
+    global _probe
+    if _probe is None:
+        library()   # builds both libraries when they are missing
+        if not os.path.exists(_build.PROBE_LIB):
+            raise ImportError(f"libmpld_probe.so not built ({_build.PROBE_LIB})")
+        lib = ctypes.CDLL(_build.PROBE_LIB)
+        lib.mpld_probe_int_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        lib.mpld_probe_int_peak.restype = ctypes.c_int
+        _probe = lib
+    return _probe
+
+
 class MpldError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {mpld_status_string(code)} ({code})")

@@ -431,8 +431,10 @@ def test_split_search_queue_and_cta_forms(stream):
         sizes = np.bincount(ref.comp_of[ref.comp_of >= 0], minlength=ref.n_components)
         assert (sizes >= 16).sum() == 19
         for warps in (0, 16):
+            # a 5 s limit per instance (these take milliseconds): a search
+            # that ran away would fail the test instead of holding the GPU
             assert_same_answer(gpu_run(L, flags=fl, stream=stream.cuda_stream, warps=warps,
-                                       search_flags=PAR | sf), ref, L)
+                                       search_flags=PAR | sf, time_limit_ms=5000), ref, L)
 
 
 def test_split_search_several_problems(stream):

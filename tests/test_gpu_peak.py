@@ -12,9 +12,7 @@ def test_int_pipe_probe_reports_positive_rates():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    fn = mpld.library().mpld_internal_int_peak
-    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
-    fn.restype = ctypes.c_int
+    fn = mpld.probe_library().mpld_probe_int_peak
     out = (ctypes.c_double * 2)()
     assert fn(1 << 12, out) == 0
     # more than one op per SM per clock, less than 1,024 per SM per clock
