@@ -34,6 +34,7 @@ SINGLE_INSTANCE = 2
 COLUMN_BFS = 8      # the paper's column rule (single-row column, else BFS order)
 BICONNECTED = 16    # search the biconnected blocks of each component, merge at cut segments
 CLIQUE_BOUND = 32   # second bound mode: dead columns plus untouched edge-disjoint (k+1)-cliques
+SPLIT_BUDGET = 64   # budgeted split search: the node budget spread over independent subtree searches
 INF = (1 << 63) - 1
 
 
@@ -104,13 +105,15 @@ class InstanceResult:
 
 
 def solve_instance(n, k, conf, stitch=(), cost_conflict=10, cost_stitch=1, budget=0,
-                   rule=0, clique_bound=False) -> InstanceResult:
+                   rule=0, clique_bound=False, split=False) -> InstanceResult:
     """Search one instance (the whole graph), Algorithm X with dancing links.
 
     rule 0: column with the fewest rows, lowest index on ties; rule 1: the
     paper's rule (a column with one row left, else breadth-first order).
     clique_bound: the second bound mode (dead columns plus untouched
-    edge-disjoint (k+1)-cliques).
+    edge-disjoint (k+1)-cliques).  split: the budgeted split search (the
+    node budget spent by a first search and then by independent searches of
+    the subtrees below a fixed depth).
     """
     lib = _load()
     conf = np.asarray(conf, dtype=np.int32).reshape(-1, 2)
@@ -122,7 +125,8 @@ def solve_instance(n, k, conf, stitch=(), cost_conflict=10, cost_stitch=1, budge
     nodes = ctypes.c_int64(0)
     rc = lib.oracle_solve_instance_rule(n, k, len(cu), _ptr(cu), _ptr(cv), len(su), _ptr(su),
                                         _ptr(sv), cost_conflict, cost_stitch, budget,
-                                        rule | (2 if clique_bound else 0), _ptr(x),
+                                        rule | (2 if clique_bound else 0) | (4 if split else 0),
+                                        _ptr(x),
                                         ctypes.byref(cost), ctypes.byref(nodes))
     if rc < 0:
         raise ValueError(f"oracle_solve_instance failed: {rc}")

@@ -89,8 +89,10 @@
 #define OR_COLUMN_BFS 8u
 #define OR_BICONNECTED 16u
 #define OR_CLIQUE_BOUND 32u
+#define OR_SPLIT_BUDGET 64u
 
 #define OR_INF INT64_MAX
+#define OR_SPLIT_MAX_DEPTH 8
 
 /* ------------------------------------------------------------------ */
 /* Dancing-links matrix for one instance                                */
@@ -117,6 +119,15 @@ typedef struct {
   int *bfs_rank;     /* rule 1: breadth-first rank of each segment */
   int nq;            /* clique bound: taken cliques, k + 1 members each */
   int *qv;
+  /* budgeted split search: the current call's level, the forced row places
+   * of the levels above the cut, and the row places on the path of the
+   * incumbent's leaf for the levels above `track` */
+  int depth;
+  int cut;
+  int prefix[OR_SPLIT_MAX_DEPTH];
+  int track;
+  int path_pos[OR_SPLIT_MAX_DEPTH], best_pos[OR_SPLIT_MAX_DEPTH];
+  int found;         /* a leaf became the incumbent in this search */
 } dlx_t;
 
 static void dlx_free(dlx_t *d) {
@@ -306,7 +317,9 @@ static void dlx_search(dlx_t *d, int64_t g) {
   if (d->R[0] == 0) {                      /* every primary column covered */
     if (g < d->best) {
       d->best = g;
+      d->found = 1;
       memcpy(d->bestx, d->x, (size_t)d->n);
+      memcpy(d->best_pos, d->path_pos, sizeof(int) * (size_t)d->track);
       if (g == 0) d->done = 1;
     }
     return;
@@ -343,6 +356,9 @@ static void dlx_search(dlx_t *d, int64_t g) {
 
   dlx_cover(d, cmin);
   for (int t = 0; t < k && !d->done; ++t) {
+    /* above the cut of a split search only the forced row is taken */
+    if (d->depth < d->cut && t != d->prefix[d->depth]) continue;
+    if (d->depth < d->track) d->path_pos[d->depth] = t;
     const int c = order[t];
     const int r = d->rownode[v * k + c];
     const int base = d->coltop;
@@ -355,7 +371,9 @@ static void dlx_search(dlx_t *d, int64_t g) {
       }
     }
     d->x[v] = (signed char)c;
+    d->depth++;
     dlx_search(d, g + inc[c]);
+    d->depth--;
     d->x[v] = -1;
     while (d->coltop > base) {
       int col = d->colstack[--d->coltop];
@@ -506,11 +524,98 @@ int oracle_cliques(int n, int k, int ne, const int *eu, const int *ev, int max_q
   return rc;
 }
 
+/* ------------------------------------------------------------------ */
+/* Budgeted split search                                                 */
+/* ------------------------------------------------------------------ */
+
+/* A node budget spent by one depth-first search is sequential: which nodes
+ * the first B are depends on every node before them.  The split search
+ * spends it on many independent searches instead (the paper's task
+ * parallelism, Sec. 1 and Sec. 2.3, applied inside one sub-graph):
+ *   - the canonical tree is cut at depth D, the first depth with
+ *     k^D >= OR_SPLIT_TARGET (at most n); subtree s (0 <= s < S = k^D) is
+ *     the set of nodes whose path takes, at level i < D, the row at place
+ *     digit i of s in base k (most significant first) of the ascending
+ *     (added cost, mask) order, so subtree numbers follow the depth-first
+ *     order of the whole tree;
+ *   - every search gets b = ceil(B / (S + 1)) nodes;
+ *   - phase 1 is the canonical search with budget b.  If it ends on its
+ *     own, its answer stands (the first minimum-cost leaf);
+ *   - otherwise its incumbent (c1, at subtree s1) seeds S subtree searches.
+ *     The search of subtree s is the canonical search restricted to s,
+ *     counting the nodes on its forced path, with budget b and an initial
+ *     bound of c1 + 1 if s < s1, else c1: a leaf of subtree s is taken
+ *     when it beats (c1, s1) in the order (cost, subtree);
+ *   - the answer is the smallest (cost, subtree) over (c1, s1) and the
+ *     subtrees' incumbents, with that leaf's masks; the nodes are phase 1's
+ *     plus every subtree's; the status is BUDGET if some subtree stopped on
+ *     its budget.  When none did, every subtree was searched to the end
+ *     and the answer is the first minimum-cost leaf of the whole tree, as
+ *     an exhaustive search gives.
+ * Each search depends on nothing but its own subtree and (c1, s1), so the
+ * result does not depend on the order the searches run in. */
+#ifndef OR_SPLIT_TARGET
+#define OR_SPLIT_TARGET 64
+#endif
+
+static void split_cut(int n, int k, int *D_out, int64_t *S_out) {
+  int D = 0;
+  int64_t S = 1;
+  while (S < OR_SPLIT_TARGET && D < n && D < OR_SPLIT_MAX_DEPTH) { S *= k; ++D; }
+  *D_out = D;
+  *S_out = S;
+}
+
+static int dlx_split_search(dlx_t *d, int64_t budget) {
+  const int n = d->n, k = d->k;
+  int D;
+  int64_t S;
+  split_cut(n, k, &D, &S);
+  const int64_t b = budget > 0 ? (budget + S) / (S + 1) : 0;   /* ceil(B / (S + 1)) */
+  /* phase 1 */
+  d->budget = b; d->cut = 0; d->track = D; d->depth = 0; d->found = 0;
+  dlx_search(d, 0);
+  int64_t nodes = d->nodes;
+  if (!d->budget_hit) return OR_OK;
+  const int64_t c1 = d->best;
+  int64_t s1 = 0;
+  for (int i = 0; i < D; ++i) s1 = s1 * k + d->best_pos[i];
+  int64_t cw = c1, sw = s1;
+  signed char *xw = malloc((size_t)n + 1);
+  if (!xw) return OR_E_OOM;
+  memcpy(xw, d->bestx, (size_t)n);
+  int any_budget = 0;
+  /* phase 2: the subtrees, each on its own */
+  for (int64_t s = 0; s < S; ++s) {
+    d->best = c1 + (s < s1 ? 1 : 0);
+    d->found = 0; d->nodes = 0; d->done = 0; d->budget_hit = 0;
+    d->budget = b; d->cut = D; d->track = 0; d->depth = 0;
+    int64_t t = s;
+    for (int i = D - 1; i >= 0; --i) { d->prefix[i] = (int)(t % k); t /= k; }
+    dlx_search(d, 0);
+    nodes += d->nodes;
+    any_budget |= d->budget_hit;
+    if (d->found && (d->best < cw || (d->best == cw && s < sw))) {
+      cw = d->best;
+      sw = s;
+      memcpy(xw, d->bestx, (size_t)n);
+    }
+  }
+  d->best = cw;
+  memcpy(d->bestx, xw, (size_t)n);
+  d->nodes = nodes;
+  d->budget_hit = any_budget;
+  d->cut = 0;
+  free(xw);
+  return any_budget ? OR_BUDGET : OR_OK;
+}
+
 int oracle_solve_instance_rule(int n, int k, int ne, const int *eu, const int *ev,
                                int ns, const int *su, const int *sv,
                                int64_t cost_conflict, int64_t cost_stitch, int64_t budget, int rule,
                                signed char *x_out, int64_t *cost_out, int64_t *nodes_out) {
-  if (rule < 0 || rule > 3) return OR_E_INVALID;   /* bit 0: column rule, bit 1: clique bound */
+  /* bit 0: column rule, bit 1: clique bound, bit 2: budgeted split search */
+  if (rule < 0 || rule > 7) return OR_E_INVALID;
   if (n < 0 || k < 2 || k > 8 || ne < 0 || ns < 0) return OR_E_INVALID;
   int *cu, *cv, *tu, *tv, mc, ms, rc;
   if ((rc = norm_edges(n, ne, eu, ev, &cu, &cv, &mc)) != OR_OK) return rc;
@@ -529,7 +634,12 @@ int oracle_solve_instance_rule(int n, int k, int ne, const int *eu, const int *e
     dlx_free(&d);
     return OR_E_OOM;
   }
-  dlx_search(&d, 0);
+  if (rule & 4) {
+    rc = dlx_split_search(&d, budget);
+    if (rc < 0) { dlx_free(&d); return rc; }
+  } else {
+    dlx_search(&d, 0);
+  }
   memcpy(x_out, d.bestx, (size_t)n);
   *cost_out = d.best;
   *nodes_out = d.nodes;
@@ -1203,7 +1313,8 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
     pool_t P;
     memset(&P, 0, sizeof(P));
     P.k = k; P.n_comp = n_inst; P.Cc = cost_conflict; P.Cs = cost_stitch; P.budget = budget;
-    P.rule = ((flags & OR_COLUMN_BFS) ? 1 : 0) | ((flags & OR_CLIQUE_BOUND) ? 2 : 0);
+    P.rule = ((flags & OR_COLUMN_BFS) ? 1 : 0) | ((flags & OR_CLIQUE_BOUND) ? 2 : 0) |
+             ((flags & OR_SPLIT_BUDGET) ? 4 : 0);
     P.comp_ptr = inst_ptr; P.comp_seg = inst_seg;
     P.cptr = cptr; P.cadj = cadj; P.sptr = sptr; P.sadj = sadj; P.work_order = order;
     P.imask = imask; P.comp_cost = ccost; P.comp_nodes = cnodes; P.comp_status = cstat;

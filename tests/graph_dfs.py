@@ -195,3 +195,95 @@ def bounded_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0, clique_bou
 
     rec(0)
     return st["best"], st["bestx"], st["nodes"], st["hit"]
+
+
+def _search_with_prefix(n, k, conf, stitch, cc, cs, budget, rule, prefix, init_best, track):
+    """bounded_search with three additions for the budgeted split search:
+    at level i < len(prefix) only the row at place prefix[i] of the row
+    order is taken; the incumbent starts at ``init_best`` (None = no bound;
+    a leaf must cost less than it to be taken); the row places of the
+    incumbent leaf's path are kept for its first ``track`` levels.
+    Returns (best, bestx, nodes, budget_hit, found, best_places)."""
+    S = _Search(n, k, conf, stitch, cc, cs, rule)
+    st = dict(best=init_best, bestx=None, nodes=0, done=False, hit=False, found=False,
+              places=None)
+    path = []
+
+    def rec(g):
+        if budget > 0 and st["best"] is not None and st["nodes"] >= budget:
+            st["hit"] = True
+            st["done"] = True
+            return
+        st["nodes"] += 1
+        v, z = S.pick()
+        if v < 0:
+            if st["best"] is None or g < st["best"]:
+                st["best"], st["bestx"], st["found"] = g, list(S.x), True
+                st["places"] = list(path[:track])
+                if g == 0:
+                    st["done"] = True
+            return
+        if st["best"] is not None and g + cc * z >= st["best"]:
+            return
+        order, inc = S.row_order(v)
+        level = len(path)
+        for place, c in enumerate(order):
+            if st["done"]:
+                break
+            if level < len(prefix) and place != prefix[level]:
+                continue
+            S.x[v] = c
+            path.append(place)
+            rec(g + inc[c])
+            path.pop()
+            S.x[v] = -1
+
+    rec(0)
+    return st["best"], st["bestx"], st["nodes"], st["hit"], st["found"], st["places"]
+
+
+def split_cut(n, k, target=64):
+    """Cut depth D (first depth with k^D >= target, at most n) and S = k^D."""
+    D, S = 0, 1
+    while S < target and D < n and D < 8:
+        S *= k
+        D += 1
+    return D, S
+
+
+def split_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0, target=64):
+    """The budgeted split search, restated over the partial assignment.
+
+    Every search gets b = ceil(budget / (S + 1)) nodes.  Phase 1 is the
+    canonical search; if it ends on its own its answer stands.  Otherwise
+    its incumbent (c1 in subtree s1, the number whose base-k digits are the
+    row places of its leaf's first D levels) seeds one search per subtree s
+    below the cut, each with the initial bound c1 + 1 if s < s1 else c1;
+    the answer is the smallest (cost, subtree) among (c1, s1) and the
+    subtrees' incumbents.  Returns (cost, x, nodes, budget_hit).
+    """
+    D, S = split_cut(n, k, target)
+    b = (budget + S) // (S + 1) if budget > 0 else 0
+    c1, x1, nodes, hit, _, places = _search_with_prefix(n, k, conf, stitch, cc, cs, b, rule, (),
+                                                        None, D)
+    if not hit:
+        return c1, x1, nodes, False
+    s1 = 0
+    for p in places:
+        s1 = s1 * k + p
+    win = (c1, s1, x1)
+    any_hit = False
+    for s in range(S):
+        digits = []
+        t = s
+        for _ in range(D):
+            digits.append(t % k)
+            t //= k
+        prefix = digits[::-1]
+        c, x, m, h, found, _ = _search_with_prefix(n, k, conf, stitch, cc, cs, b, rule, prefix,
+                                                   c1 + (1 if s < s1 else 0), 0)
+        nodes += m
+        any_hit = any_hit or h
+        if found and (c, s) < win[:2]:
+            win = (c, s, x)
+    return win[0], win[2], nodes, any_hit
