@@ -68,6 +68,9 @@ def parse_args():
     ap.add_argument("--parallel-exact", action="store_true",
                     help="exact search (node budget 0) with the warps of a CTA splitting each "
                          "instance of 16+ segments (for single-instance workloads)")
+    ap.add_argument("--split-budget", action="store_true",
+                    help="budgeted split search: each instance's node budget spent by a first "
+                         "search and then by independent subtree searches on every warp")
     ap.add_argument("--biconnected", action="store_true",
                     help="search the biconnected blocks of each sub-graph and join them at cut "
                          "segments")
@@ -248,6 +251,8 @@ def oracle_flags(oracle, args, mode):
         flags |= oracle.BICONNECTED
     if args.clique_bound:
         flags |= oracle.CLIQUE_BOUND
+    if args.split_budget:
+        flags |= oracle.SPLIT_BUDGET
     return flags
 
 
@@ -384,6 +389,8 @@ def main():
     rule_flag = mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0
     if args.parallel_exact:
         rule_flag |= mpld.MPLD_PARALLEL_EXACT
+    if args.split_budget:
+        rule_flag |= mpld.MPLD_SPLIT_BUDGET
     prm = mpld.make_params(node_budget=args.budget, flags=rule_flag)
     tune = None
     if not args.no_tune:
@@ -439,6 +446,7 @@ def main():
                    "biconnected": bool(flags & mpld.MPLD_BICONNECTED),
                    "clique_bound": bool(flags & mpld.MPLD_CLIQUE_BOUND),
                    "parallel_exact": bool(args.parallel_exact),
+                   "split_budget": bool(args.split_budget),
                    "instances": info.n_components,
                    "instance_segments": info.instance_segments,
                    "max_instance": info.max_component,
@@ -456,7 +464,7 @@ def main():
                    "stitches": res.n_stitches, "budget_instances": res.n_budget_components,
                    "status": rc, "step_ms": step_ms,
                    "median_step_ms": statistics.median(step_ms) if step_ms else None},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if args.split_budget else 1),
         "clocks": clk,
     }
 
@@ -524,49 +532,55 @@ def main():
                   "ms_per_step": 1000 * e2e_total / len(e2e_t),
                   "form": "one layout at a time: mpld_build_matrix then mpld_solve_batch"}
 
-        # the same decompositions as a stream of K layouts through the
-        # server: host build, upload, search, copy-back and recovery of
-        # different layouts overlap (the form a user decomposing many
-        # layouts takes); every layout is still built, uploaded, searched,
-        # copied back and recovered inside the timed region
-        req_flags = flags & (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE |
-                             mpld.MPLD_BICONNECTED | mpld.MPLD_CLIQUE_BOUND)
-        # the server's own launch shape (small CTAs, so that launches of
-        # different layouts share the SMs)
-        cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
-                                      max_in_flight=max(args.steps, args.warmup, 1), streams=8)
-        srv = mpld.mpld_server_create(cfg, prm)
+        if args.split_budget:
+            # the server has no budgeted split search: end to end is measured
+            # one layout at a time through mpld_build_matrix / mpld_solve_batch
+            out["e2e"] = dict(serial, unit="segments/s", h2d_bytes_per_step=int(h2d),
+                              d2h_bytes_per_step=int(d2h), gpu_launches_per_step=2)
+        else:
+            # the same decompositions as a stream of K layouts through the
+            # server: host build, upload, search, copy-back and recovery of
+            # different layouts overlap (the form a user decomposing many
+            # layouts takes); every layout is still built, uploaded, searched,
+            # copied back and recovered inside the timed region
+            req_flags = flags & (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE |
+                                 mpld.MPLD_BICONNECTED | mpld.MPLD_CLIQUE_BOUND)
+            # the server's own launch shape (small CTAs, so that launches of
+            # different layouts share the SMs)
+            cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
+                                          max_in_flight=max(args.steps, args.warmup, 1), streams=8)
+            srv = mpld.mpld_server_create(cfg, prm)
 
-        def stream_run(n):
-            t0 = time.perf_counter()
-            pending = {mpld.mpld_server_submit(srv, layout, flags=req_flags) for _ in range(n)}
-            got = []
-            while pending:
-                done = mpld.mpld_server_poll(srv)
-                for t in done:
-                    got.append(mpld.mpld_server_result(srv, t))
-                    pending.discard(t)
-                if not done:
-                    time.sleep(0.0002)
-            return time.perf_counter() - t0, got
+            def stream_run(n):
+                t0 = time.perf_counter()
+                pending = {mpld.mpld_server_submit(srv, layout, flags=req_flags) for _ in range(n)}
+                got = []
+                while pending:
+                    done = mpld.mpld_server_poll(srv)
+                    for t in done:
+                        got.append(mpld.mpld_server_result(srv, t))
+                        pending.discard(t)
+                    if not done:
+                        time.sleep(0.0002)
+                return time.perf_counter() - t0, got
 
-        stream_run(args.warmup)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t_stream, got = stream_run(args.steps)
-        srv.close()
-        for rc3, m3, r3 in got:
-            assert rc3 == rc and np.array_equal(m3, mask) and r3.cost == res.cost
-        if dist:
-            _, t_stream = shard.aggregate(dist, layout.n_seg, t_stream, "cuda")
-        out["e2e"] = {"value": all_segments * args.steps / t_stream, "unit": "segments/s",
-                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "ms_per_step": 1000 * t_stream / args.steps,
-                      "gpu_launches_per_step": 1,
-                      "form": f"{args.steps} layouts submitted together to the server API "
-                              "(mpld_server_submit / poll / result)",
-                      "serial": serial}
+            stream_run(args.warmup)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t_stream, got = stream_run(args.steps)
+            srv.close()
+            for rc3, m3, r3 in got:
+                assert rc3 == rc and np.array_equal(m3, mask) and r3.cost == res.cost
+            if dist:
+                _, t_stream = shard.aggregate(dist, layout.n_seg, t_stream, "cuda")
+            out["e2e"] = {"value": all_segments * args.steps / t_stream, "unit": "segments/s",
+                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                          "ms_per_step": 1000 * t_stream / args.steps,
+                          "gpu_launches_per_step": 1,
+                          "form": f"{args.steps} layouts submitted together to the server API "
+                                  "(mpld_server_submit / poll / result)",
+                          "serial": serial}
 
     if rank == 0 and not args.no_plain:
         # plain one-launch-per-instance path vs the batched one on a smaller

@@ -102,6 +102,29 @@ extern "C" {
                                     applied inside split instances.  Read by the search calls
                                     except mpld_search_instance_noalloc (MPLD_E_INVALID) and the
                                     server (ignored). */
+#define MPLD_SPLIT_BUDGET 128u   /* budgeted split search: the node budget B of each instance is
+                                    spent by many independent searches instead of one (the task
+                                    parallelism of Sec. 1 / Sec. 2.3 inside one sub-graph).  The
+                                    instance's tree is cut at depth D, the first depth with
+                                    k^D >= 64 (at most n and 8), into S = k^D subtrees numbered in
+                                    depth-first order (subtree s takes, at level i < D, the row
+                                    at place digit i of s in base k of the ascending (added cost,
+                                    mask) order).  Every search gets b = ceil(B / (S + 1)) nodes.
+                                    A first search of the whole tree runs with budget b; if it
+                                    ends on its own its answer stands.  Otherwise its incumbent
+                                    (cost c1 at subtree s1) seeds S subtree searches, each with
+                                    budget b, counting the nodes on its forced path, taking a
+                                    leaf only if it beats (c1, s1) in the order (cost, subtree);
+                                    these run on every warp of the GPU at once.  The result is
+                                    the smallest (cost, subtree) found, its masks, the nodes of
+                                    all searches, and status MPLD_BUDGET if a subtree search
+                                    stopped on its budget (else the answer is exact).  The result
+                                    does not depend on timing or launch shape.  node_budget 0:
+                                    the exhaustive search.  Read by the search calls; not with
+                                    MPLD_PARALLEL_EXACT, nor on problems built with
+                                    MPLD_CLIQUE_BOUND (MPLD_E_INVALID); not available to
+                                    mpld_search_instance_noalloc (MPLD_E_INVALID) or the server
+                                    (ignored). */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
                                     the solve calls then return MPLD_E_STATE */
@@ -145,8 +168,8 @@ typedef struct {
  *                  MPLD_BUDGET);
  *   flags          MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_HOST_ONLY |
  *                  MPLD_BICONNECTED | MPLD_CLIQUE_BOUND (used by
- *                  mpld_build_matrix); MPLD_COLUMN_BFS | MPLD_PARALLEL_EXACT
- *                  (used by the search calls);
+ *                  mpld_build_matrix); MPLD_COLUMN_BFS | MPLD_PARALLEL_EXACT |
+ *                  MPLD_SPLIT_BUDGET (used by the search calls);
  *   warps_per_cta, slot_bytes   launch shape of the batched kernel; 0 = the
  *                  tuned or default shape (see mpld_autotune); at most 16
  *                  warps (larger values are clamped);

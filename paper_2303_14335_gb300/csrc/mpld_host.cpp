@@ -855,6 +855,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       d.k = k;
       d.cost_conflict = (int32_t)p->Cc;
       d.cost_stitch = (int32_t)p->Cs;
+      d.idx = c;
     }
     if (p->flags & MPLD_HOST_ONLY) {
       *out = p;
@@ -930,6 +931,7 @@ extern "C" void mpld_free(mpld_problem *p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->d_base) cudaFree(p->d_base);
   if (p->d_par) cudaFree(p->d_par);
+  if (p->d_split) cudaFree(p->d_split);
   if (p->h_res) cudaFreeHost(p->h_res);
   if (p->h_masks) cudaFreeHost(p->h_masks);
   if (p->h_err) cudaFreeHost(p->h_err);
@@ -950,9 +952,20 @@ int rule_of(const mpld_params *prm) { return (prm && (prm->flags & MPLD_COLUMN_B
 // searched by a CTA whose warps split the subtrees.
 constexpr int PAR_MIN_SEGMENTS = 16;
 int par_of(const mpld_params *prm) { return (prm && (prm->flags & MPLD_PARALLEL_EXACT)) ? 1 : 0; }
-// The split search is exact only: with a node budget the nodes a subtree
-// counts would depend on the order the warps finish.
-bool params_ok(const mpld_params *prm) { return !(par_of(prm) && budget_of(prm) != 0); }
+int split_of(const mpld_params *prm) { return (prm && (prm->flags & MPLD_SPLIT_BUDGET)) ? 1 : 0; }
+// The split exact search is exact only: with a node budget the nodes a
+// subtree counts would depend on the order the warps finish.  The budgeted
+// split search has its own per-search budgets and cannot be combined with it.
+bool params_ok(const mpld_params *prm) {
+  return !(par_of(prm) && budget_of(prm) != 0) && !(par_of(prm) && split_of(prm));
+}
+// The budgeted split search's subtree searches have no clique bound: a
+// problem built with it is refused.
+bool split_ok(const mpld_problem *p) {
+  for (int32_t q : p->inst_nq)
+    if (q > 0) return false;
+  return true;
+}
 int cta_min_of(const mpld_params *prm) {
   if (par_of(prm)) return PAR_MIN_SEGMENTS;
   if (prm && prm->cta_segments < 0) return std::numeric_limits<int>::max();
@@ -1071,7 +1084,7 @@ int launch_grid_split(mpld_problem *p, int c, const GridSplit &g, const mpld_par
   a.rule = rule_of(prm);
   a.n_large = 0;
   a.par = 2;
-  a.pad = 0;
+  a.split = 0;
   a.par_buf = p->d_par;
   return mpld_internal_launch(&a, g.ctas, CTA_TEAM_WARPS, st);
 }
@@ -1145,9 +1158,102 @@ int launch_queue(mpld_problem *p, const QueuePlan &q, const mpld_params *prm, cu
   a.rule = rule_of(prm);
   a.n_large = 0;
   a.par = 3;
-  a.pad = 0;
+  a.split = 0;
   a.par_buf = p->d_par;
   return mpld_internal_launch(&a, q.ctas, CTA_TEAM_WARPS, st);
+}
+
+// Budgeted split search (MPLD_SPLIT_BUDGET): the first phase is the batched
+// (or plain) launch with split = 1, which searches every instance with its
+// per-search budget and puts the ones that stop on it on the hard list; the
+// second launch (par = 4) searches their subtrees, one per warp at a time.
+// Device block: hard list (count, then descriptor indices), one 64-byte
+// context per instance, then each warp's state for instances beyond the
+// register form.
+struct SplitPlan {
+  bool on = false;
+  int nw = 0, slot = 0, ctas = 0;   // second launch
+  int smax = 1;                     // item numbers per hard-list entry
+  int state_bytes = 0;              // per warp, general form (0: no such instance)
+  size_t o_hard = 0, o_ctx = 0, o_state = 0, bytes = 0;
+};
+SplitPlan split_plan_of(const InstDesc *desc, int n_inst, const mpld_params *prm) {
+  SplitPlan q;
+  if (!split_of(prm) || n_inst < 1) return q;
+  q.on = true;
+  int reg_slot = 16;
+  size_t gen = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    const InstDesc &d = desc[i];
+    int D;
+    uint32_t S;
+    mpld::split_cut(d.n, d.k, D, S);
+    q.smax = std::max(q.smax, (int)S);
+    if (mpld::reg_fits(d.n, d.k))
+      reg_slot = std::max(reg_slot, (int)mpld::align16(mpld::reg_layout(d.n, d.k, 0).bytes));
+    else
+      gen = std::max(gen, (size_t)d.state_bytes);
+  }
+  // as many warps per CTA as the slots allow (the launch bound is 16)
+  q.nw = 1;
+  for (int nw = 16; nw >= 1; --nw)
+    if (mpld_internal_max_slot_bytes(nw) >= reg_slot) { q.nw = nw; break; }
+  q.slot = reg_slot;
+  const int per_sm = std::max(1, mpld_internal_ctas_per_sm(q.nw, q.slot));
+  q.ctas = per_sm * std::max(1, mpld_internal_num_sms());
+  q.state_bytes = gen ? (int)((gen + 255) & ~(size_t)255) : 0;
+  q.o_hard = 0;
+  q.o_ctx = (4u * (size_t)(n_inst + 1) + 255) & ~(size_t)255;
+  q.o_state = q.o_ctx + 64u * (size_t)n_inst;
+  q.bytes = q.o_state + (size_t)q.ctas * (size_t)q.nw * (size_t)q.state_bytes;
+  return q;
+}
+// Grow the problem's split-search block (outside any stream capture).
+int ensure_split_buf(mpld_problem *p, size_t bytes) {
+  if (bytes <= p->split_bytes) return MPLD_OK;
+  if (p->gexec) {   // a captured graph may hold the old block's address
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  if (p->d_split) {
+    cudaFree(p->d_split);
+    p->d_split = nullptr;
+    p->split_bytes = 0;
+  }
+  if (cudaMalloc((void **)&p->d_split, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_split = nullptr;
+    return MPLD_E_OOM;
+  }
+  p->split_bytes = bytes;
+  return MPLD_OK;
+}
+// First-phase fields of a launch over `buf` (the plan's block).
+void split_phase1(mpld::LaunchArgs &a, const SplitPlan &q, uint8_t *buf) {
+  a.split = q.on ? 1 : 0;
+  a.hard = q.on ? (int32_t *)(buf + q.o_hard) : nullptr;
+  a.par_buf = q.on ? buf + q.o_ctx : a.par_buf;
+}
+// The second launch, after the first on the same stream: its item counter
+// (queue[0]) is reset, then every warp of the grid takes subtrees.
+int launch_split_phase2(const mpld::LaunchArgs &a1, const InstDesc *desc, const SplitPlan &q,
+                        uint8_t *buf, uint32_t *queue, cudaStream_t st) {
+  int rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));
+  if (rc) return rc;
+  mpld::LaunchArgs a = a1;
+  a.desc = desc;   // the hard list holds indices into the whole descriptor array
+  a.order = nullptr;
+  a.slot_bytes = q.slot;
+  a.queue = queue;
+  a.n_large = 0;
+  a.par = 4;
+  a.split = 0;
+  a.hard = (int32_t *)(buf + q.o_hard);
+  a.par_buf = buf + q.o_ctx;
+  a.split_scratch = q.state_bytes ? buf + q.o_state : nullptr;
+  a.smax = q.smax;
+  a.split_state_bytes = q.state_bytes;
+  return mpld_internal_launch(&a, q.ctas, q.nw, st);
 }
 
 int launch_batch(const mpld::LaunchArgs &a, const Shape &sh, cudaStream_t st, uint32_t *queue,
@@ -1169,10 +1275,13 @@ bool capturable(void *stream) {
 // captured CUDA graph when the stream allows capture.
 int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool copy_back) {
   if (!params_ok(prm)) return MPLD_E_INVALID;
+  if (split_of(prm) && !split_ok(p)) return MPLD_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   mpld_problem *ps[1] = {p};
   const GridSplit gs = p->n_comp == 1 ? grid_split_of(p, 0, prm) : GridSplit{};
   if (gs.on && ensure_par_buf(p, gs.bytes) != MPLD_OK) return MPLD_E_OOM;
+  const SplitPlan sp = split_plan_of(p->h_desc.data(), p->n_comp, prm);
+  if (sp.on && ensure_split_buf(p, sp.bytes) != MPLD_OK) return MPLD_E_OOM;
   // the largest split instances go to the queue launch; the batched launch
   // then takes the rest in its own order
   const QueuePlan qp = gs.on ? QueuePlan{} : queue_plan_of(p, prm);
@@ -1197,12 +1306,18 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   a.rule = rule_of(prm);
   a.n_large = n_large;
   a.par = par_of(prm);
-  a.pad = 0;
+  a.split = 0;
   a.par_buf = nullptr;
+  split_phase1(a, sp, p->d_split);
   auto body = [&]() -> int {
     int rc = cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
     if (rc) return rc;
-    if (gs.on) {
+    if (sp.on) {
+      // the first phase over every instance, then the subtrees of the hard ones
+      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 4, st));
+      rc |= launch_batch(a, sh, st, p->d_queue, p->d_err);
+      if (rc == MPLD_OK) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
+    } else if (gs.on) {
       rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
       rc |= launch_grid_split(p, 0, gs, prm, st);
     } else if (qp.nq) {
@@ -1238,6 +1353,8 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
   }
   key.queue_ctas = qp.ctas;
   key.queue_slot = qp.slot;
+  key.split_nw = sp.on ? sp.nw : 0;
+  key.split_ctas = sp.on ? sp.ctas : 0;
   const int kc = gs.on ? gs.ctas : sh.ctas;
   key.ctas = copy_back ? kc : -kc;  // copy-back variant is a different graph
   if (!p->gexec || !(p->gkey == key) || p->gstream != stream) {
@@ -1385,6 +1502,9 @@ int finish(mpld_problem *p, int8_t *mask_out, mpld_result *res) {
 extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, void *stream) {
   if (!p || !params_ok(prm)) return MPLD_E_INVALID;
   if (!p->d_base) return MPLD_E_STATE;
+  if (split_of(prm) && !split_ok(p)) return MPLD_E_INVALID;
+  const SplitPlan sp = split_plan_of(p->h_desc.data(), p->n_comp, prm);
+  if (sp.on && ensure_split_buf(p, sp.bytes) != MPLD_OK) return MPLD_E_OOM;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
   rc |= cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
@@ -1418,8 +1538,17 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
     a.rule = rule_of(prm);
     a.n_large = large ? 1 : 0;
     a.par = par_of(prm);
-    a.pad = 0;
+    a.split = 0;
     a.par_buf = nullptr;
+    if (sp.on) {
+      // this instance's first search; if it stops on its budget, its
+      // subtrees in a second launch
+      split_phase1(a, sp, p->d_split);
+      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 4, st));
+      if (rc == MPLD_OK) rc = mpld_internal_launch(&a, 1, large ? CTA_TEAM_WARPS : 1, st);
+      if (rc == MPLD_OK) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
+      continue;
+    }
     rc = mpld_internal_launch(&a, 1, large ? CTA_TEAM_WARPS : 1, st);
   }
   p->searched = rc == MPLD_OK;
@@ -1433,6 +1562,7 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   for (int i = 0; i < n; ++i) {
     if (!ps[i]) return MPLD_E_INVALID;
     if (!ps[i]->d_base) return MPLD_E_STATE;
+    if (split_of(prm) && !split_ok(ps[i])) return MPLD_E_INVALID;
   }
   if (n == 1) {
     const int rc = enqueue_single(ps[0], prm, stream, false);
@@ -1449,6 +1579,7 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
     for (int c = 0; c < ps[i]->n_comp; ++c) sizes.push_back(ps[i]->h_desc[c].n);
   }
   const int total = (int)desc.size();
+  for (int i = 0; i < total; ++i) desc[i].idx = i;
   std::vector<int32_t> order((size_t)total);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sizes[x] > sizes[y]; });
@@ -1487,7 +1618,9 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   const size_t obytes = (sizeof(int32_t) * (size_t)std::max(total, 1) + 255) & ~(size_t)255;
   const size_t o_ctx = dbytes + obytes + 256;          // after desc, order, work counters
   const size_t o_qidx = o_ctx + 64u * (size_t)nq;
-  const size_t bytes = o_qidx + sizeof(int32_t) * (size_t)std::max(nq, 1);
+  const SplitPlan sp = split_plan_of(desc.data(), total, prm);
+  const size_t o_split = (o_qidx + sizeof(int32_t) * (size_t)std::max(nq, 1) + 255) & ~(size_t)255;
+  const size_t bytes = o_split + (sp.on ? sp.bytes : 0);
   if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess) { cudaGetLastError(); return MPLD_E_OOM; }
   uint8_t *b = (uint8_t *)buf;
   int rc = MPLD_OK;
@@ -1517,7 +1650,7 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   a.rule = rule_of(prm);
   a.n_large = n_large;
   a.par = par_of(prm);
-  a.pad = 0;
+  a.split = 0;
   a.par_buf = nullptr;
   for (int i = 0; i < n; ++i) {
     if (i) rc |= cuda_ok(cudaMemsetAsync(ps[i]->d_err, 0, 4, st));
@@ -1544,6 +1677,12 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
       const int ctas = std::min(sh.ctas, n_large + (n_rest - n_large + sh.nw - 1) / sh.nw);
       rc = mpld_internal_launch(&a, std::max(ctas, 1), sh.nw, st);
     }
+  } else if (!rc && sp.on) {
+    // the first phase over every instance, then the subtrees of the hard ones
+    split_phase1(a, sp, b + o_split);
+    rc = cuda_ok(cudaMemsetAsync(b + o_split + sp.o_hard, 0, 4, st));
+    if (!rc) rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
+    if (!rc) rc = launch_split_phase2(a, a.desc, sp, b + o_split, queue, st);
   } else if (!rc) {
     rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
   }

@@ -162,14 +162,15 @@ struct __align__(16) InstDesc {
   int32_t ro_bytes, state_bytes;
   int32_t k, cost_conflict;
   int32_t cost_stitch, nq;   // nq: cliques of the second bound mode (0: none)
-  int64_t pad1;
+  int32_t idx;               // position in the launch's descriptor array
+  int32_t pad1;
 };
 
 struct InstResult {
   int64_t cost;
   int64_t nodes;
   int32_t status;   // MPLD_OK / MPLD_BUDGET / MPLD_TIMEOUT, -1 = not run
-  int32_t pad0;
+  int32_t sub;      // budgeted split search: subtree of the incumbent's leaf
   // algorithmic integer operations of the search: 2 per uncovered column at
   // every node that scans the columns (AND + popcount of the column choice;
   // a node pruned by its path cost alone scans nothing), k per neighbour
@@ -192,10 +193,39 @@ struct LaunchArgs {
   int32_t n_large;         // the first n_large instances of the order are searched by whole
                            // CTAs (blocks 0..n_large-1 first; counter queue[1])
   int32_t par;             // 1: those CTAs search exactly, their warps splitting subtrees;
-                           // 2: every warp of the grid splits the one instance desc[0]
-  int32_t pad;
-  uint8_t *par_buf;        // par == 2: the split context in global memory (ParLayout)
+                           // 2: every warp of the grid splits the one instance desc[0];
+                           // 3: the grid splits desc[order[0..n_inst)] one after another;
+                           // 4: budgeted split search, second phase: the warps of the
+                           //    grid search the subtrees of the instances on the hard list
+  int32_t split = 0;       // 1: budgeted split search, first phase: each instance searched
+                           // with its per-search budget; one that stops on it goes on the
+                           // hard list with a fresh context
+  uint8_t *par_buf;        // par == 2: the split context in global memory (ParLayout);
+                           // par == 3: one 64-byte context per queued instance;
+                           // split / par == 4: one 64-byte context per hard-list entry
+  int32_t *hard = nullptr; // split / par == 4: [0] entries, then the descriptor index of each
+  uint8_t *split_scratch = nullptr;  // par == 4: per-warp global search state for instances beyond
+                           // the register form (split_state_bytes per warp)
+  int32_t smax = 0;        // par == 4: item numbers per hard-list entry (>= its subtrees)
+  int32_t split_state_bytes = 0;
 };
+
+// Budgeted split search (MPLD_SPLIT_BUDGET): an instance's search tree is cut
+// at depth D, the first depth with k^D >= SPLIT_TARGET (at most n and 8),
+// into S = k^D subtrees; the first search and every subtree search get
+// b = ceil(B / (S + 1)) nodes of the instance's budget B.
+constexpr int SPLIT_TARGET = 64;
+MPLD_HD void split_cut(int n, int k, int &D, uint32_t &S) {
+  D = 0;
+  S = 1;
+  while (S < (uint32_t)SPLIT_TARGET && D < n && D < 8) {
+    S *= (uint32_t)k;
+    ++D;
+  }
+}
+MPLD_HD int64_t split_search_budget(int64_t B, uint32_t S) {
+  return B > 0 ? (B + (int64_t)S) / ((int64_t)S + 1) : 0;
+}
 
 // Shared state of a split exact search: the incumbent as one 64-bit key
 // (cost << 32 | subtree; ~0 = none), the next subtree to hand out, and

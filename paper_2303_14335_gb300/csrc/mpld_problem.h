@@ -19,10 +19,11 @@ struct GraphKey {
   int64_t budget = 0, tl = 0;
   int rule = 0, n_large = 0;
   int queue_ctas = 0, queue_slot = 0;  // the split-search queue launch before it (0 = none)
+  int split_nw = 0, split_ctas = 0;    // the budgeted split search's second launch (0 = none)
   bool operator==(const GraphKey &o) const {
     return nw == o.nw && slot == o.slot && ctas == o.ctas && budget == o.budget && tl == o.tl &&
            rule == o.rule && n_large == o.n_large && queue_ctas == o.queue_ctas &&
-           queue_slot == o.queue_slot;
+           queue_slot == o.queue_slot && split_nw == o.split_nw && split_ctas == o.split_ctas;
   }
 };
 
@@ -65,6 +66,8 @@ struct mpld_problem {
   uint8_t *d_par = nullptr;           // grid-wide split search context (grown on demand)
   size_t par_bytes = 0;
   bool queue_ready = false;           // the queue's index arrays are in d_par
+  uint8_t *d_split = nullptr;         // budgeted split search: hard list, contexts and the
+  size_t split_bytes = 0;             // per-warp state of the second launch (grown on demand)
   int32_t *d_err = nullptr;
   // pinned host mirrors of the results
   mpld::InstResult *h_res = nullptr;

@@ -193,6 +193,24 @@ struct CtaTeam {
   }
 };
 
+// What a search does with the levels above the cut of the budgeted split
+// search.  Default: nothing (the canonical search of the whole tree).
+//   track:  first phase -- the subtree (row places of the first `cut`
+//           levels) of each leaf taken is kept in `sub_out`;
+//   forced: one subtree -- at level i < cut only the row at place digit i of
+//           `prefix` (base k, most significant first) is taken, the search
+//           never backtracks above the cut, and the incumbent starts at
+//           `init_best` (a leaf must cost less); `replay` stops at the first
+//           leaf taken.
+struct SplitSpec {
+  int cut = 0;
+  bool track = false, forced = false, replay = false;
+  uint32_t prefix = 0;
+  int32_t init_best = 0x7FFFFFFF;
+  uint32_t sub_out = 0;   // track: subtree of the incumbent's leaf
+  bool found = false;     // forced: a leaf was taken
+};
+
 // FT: field type of the activeRows bitset (uint8_t for k <= 7, uint16_t for
 // k = 8); MK: width of the row sort (k for k <= 4, else 8); SM: state and
 // read-only block in shared memory.  Each segment's field is written by one
@@ -314,13 +332,16 @@ struct Search {
 
   __device__ __forceinline__ int run(int lane, int64_t budget, int64_t time_limit_ns,
                                      int8_t *best_mask, int32_t &best_out, int64_t &nodes_out,
-                                     int64_t &work_out) const {
-    int32_t best = INF32, g = 0;
+                                     int64_t &work_out, SplitSpec &sp,
+                                     uint64_t t0 = 0) const {
+    int32_t best = sp.forced ? sp.init_best : INF32, g = 0;
     int64_t nodes = 0, work = 0;
     uint32_t work32 = 0;
     int level = 0;
     int status = MPLD_OK;
-    const uint64_t t0 = globaltimer();
+    // a forced subtree search never backtracks above the cut
+    const int floor_level = sp.forced ? sp.cut : 0;
+    if (t0 == 0) t0 = globaltimer();
     const uint32_t *rows32 = reinterpret_cast<const uint32_t *>(rows);
     const int nwords = (n + PER_WORD - 1) / PER_WORD;
     int64_t next_check = 1024;
@@ -413,8 +434,16 @@ struct Search {
           // leaf: every primary column covered
           if (g < best) {
             best = g;
-            for (int i = lane; i < n; i += team.size()) best_mask[i] = x[i];
-            if (best == 0) break;
+            sp.found = true;
+            if (best_mask)
+              for (int i = lane; i < n; i += team.size()) best_mask[i] = x[i];
+            if (sp.track) {
+              // the row place taken at each level above the cut (rows tried - 1)
+              uint32_t sub = 0;
+              for (int i = 0; i < sp.cut; ++i) sub = sub * (uint32_t)k + ((lv[2 * i].y >> 16) - 1u);
+              sp.sub_out = sub;
+            }
+            if (best == 0 || sp.replay) break;
           }
           enter = false;
           continue;
@@ -448,6 +477,32 @@ struct Search {
         // times the cliques untouched once v is assigned
         const int left = nq > 0 ? untouched_after(v) : 0;
         const int32_t floor_c = Cc * left;
+        if (level < floor_level) {
+          // above the cut of a forced subtree: only the row at the prefix's
+          // place is taken; if its child is pruned on entry the subtree ends
+          uint32_t pw = 1;
+          for (int i = level + 1; i < sp.cut; ++i) pw *= (uint32_t)k;
+          const int place = (int)((sp.prefix / pw) % (uint32_t)k);
+          uint32_t kp = keys[0];
+#pragma unroll
+          for (int i = 1; i < MK; ++i) kp = i == place ? keys[i] : kp;
+          if (best < INF32 && g + (int32_t)(kp >> 3) + floor_c >= best) {
+            if (count_pruned(1)) status = MPLD_BUDGET;
+            break;
+          }
+          uint32_t ord = 0;
+#pragma unroll
+          for (int i = 0; i < MK; ++i) ord |= (keys[i] & 7u) << (4 * i);
+          if (lane == 0) {
+            lv[2 * level] = make_uint4((uint32_t)g, (uint32_t)v | ((uint32_t)(place + 1) << 16), ord,
+                                       (uint32_t)cb);
+            lv[2 * level + 1] = make_uint4((uint32_t)dc | ((uint32_t)ds << 16), (uint32_t)sb, 0u, 0u);
+          }
+          cover_first(v, (int)(kp & 7u), cb, dc, sb, ds, lane);
+          g += (int32_t)(kp >> 3);
+          ++level;
+          continue;
+        }
         if (best < INF32 && g + (int32_t)(keys[0] >> 3) + floor_c >= best) {
           // rows are in ascending cost: every child is pruned on entry
           if (count_pruned(k)) { status = MPLD_BUDGET; break; }
@@ -476,7 +531,7 @@ struct Search {
         continue;
       }
       // ---- backtrack: next row of the level above, or undo its column ----
-      if (level == 0) break;
+      if (level <= floor_level) break;
       --level;
       const uint4 r0 = lv[2 * level], r1 = lv[2 * level + 1];
       team.sync();   // read by every thread before the first rewrites it below
@@ -516,6 +571,24 @@ struct Search {
     return status;
   }
 };
+
+// Budgeted split search, first phase: an instance that stopped on its
+// per-search budget goes on the hard list, with a fresh context whose key is
+// its incumbent (cost << 32 | subtree of the incumbent's leaf).  Lane 0 only.
+__device__ __forceinline__ void split_enlist(const LaunchArgs &a, const InstDesc &d, int32_t best,
+                                             uint32_t sub) {
+  const int j = atomicAdd(a.hard, 1);
+  a.hard[1 + j] = d.idx;
+  ParCtx *c = (ParCtx *)(a.par_buf + (size_t)j * 64);
+  c->key = ((unsigned long long)(uint32_t)best << 32) | sub;
+  c->nodes = 0;
+  c->work = 0;
+  c->next = 0;
+  c->timed_out = 0;
+  c->done = 0;
+  c->pad = 0;
+  c->t0 = 0;
+}
 
 // ---- register-resident search (n <= 32 words of fields) -------------------
 //
@@ -631,7 +704,16 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
   uint32_t work32 = 0;
   int level = 0;
   int status = MPLD_OK;
-  const int64_t budget = a.budget, time_limit_ns = a.time_limit_ns;
+  int64_t budget = a.budget;
+  const int64_t time_limit_ns = a.time_limit_ns;
+  // budgeted split search, first phase: this search's share of the budget,
+  // and the subtree (row places of the first cut_d levels) of each leaf taken
+  int cut_d = 0;
+  uint32_t cut_s = 1, best_sub = 0;
+  if (a.split) {
+    split_cut(n, k, cut_d, cut_s);
+    budget = split_search_budget(a.budget, cut_s);
+  }
   const uint64_t t0 = globaltimer();
   int64_t next_check = 1024;
   int untouched = nq;   // cliques with no member assigned
@@ -707,6 +789,12 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
 #pragma unroll
           for (int j = 0; j < P; ++j)
             if (lane * P + j < n) d.mask[lane * P + j] = (int8_t)((xw >> (8 * j)) & 0xFFu);
+          if (cut_d > 0) {
+            // the row place taken at each level above the cut (next row - 1)
+            uint32_t sub = 0;
+            for (int i = 0; i < cut_d; ++i) sub = sub * (uint32_t)k + (((rec[i * RS] >> 8) & 0xFu) - 1u);
+            best_sub = sub;
+          }
           if (best == 0) break;
         }
         enter = false;
@@ -875,7 +963,9 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
     d.res->cost = best == INF32 ? INT64_MAX : (int64_t)best;
     d.res->nodes = nodes;
     d.res->status = status;
+    d.res->sub = (int32_t)best_sub;
     d.res->work = work + work32;
+    if (a.split && status == MPLD_BUDGET) split_enlist(a, d, best, best_sub);
   }
   __syncwarp();
 }
@@ -904,7 +994,23 @@ __device__ __forceinline__ void reg_search(const InstDesc &d, uint8_t *base, con
 //              (cost* << 32 | s* + 1, so leaves of cost <= cost* are taken)
 //              and writes the first leaf it takes to d.mask: the first leaf
 //              of cost cost* in s*, which is the split search's answer.
-constexpr int PAR_OWN = 0, PAR_QUEUE = 1, PAR_REPLAY = 2;
+//   PAR_BUDGET budgeted split search, second phase: searches subtree
+//              `it.sub` alone with its own budget and the incumbent of
+//              `replay_key` (the first search's), keeps no masks, publishes
+//              its best key and totals to the context and counts the subtree
+//              done; returns true in the warp that completes the instance's
+//              last subtree.
+// Item of a call: PAR_BUDGET's subtree and budget; `build` = 0 when the
+// warp's slot already holds this instance's adjacency; `split_cut` = the cut
+// of the budgeted split search instead of the one for G warps (for
+// PAR_BUDGET and its replay).
+constexpr int PAR_OWN = 0, PAR_QUEUE = 1, PAR_REPLAY = 2, PAR_BUDGET = 3;
+struct ParItem {
+  uint32_t sub = 0;
+  int64_t budget = 0;
+  bool build = true;
+  bool split_cut = false;
+};
 
 // Subtrees of the split search for G warps: k^D for the first depth D with
 // k^D >= 16 G (the trees are skewed), never below the leaves.
@@ -918,7 +1024,7 @@ template <typename FT, int MK, int RULE>
 __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
                                         int lane, int gw, int G, ParCtx *ctx,
                                         unsigned long long *wkey, int8_t *bestx, int mode,
-                                        unsigned long long replay_key) {
+                                        unsigned long long replay_key, const ParItem &it) {
   constexpr uint32_t FB = 8 * sizeof(FT);
   constexpr uint32_t FLAG = 1u << (FB - 1);
   constexpr uint32_t FMASK = (FB == 8) ? 0xFFu : 0xFFFFu;
@@ -940,21 +1046,23 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
     const uint16_t *cnbr = (const uint16_t *)(d.ro + Q.cnbr);
     const uint16_t *snbr = (const uint16_t *)(d.ro + Q.snbr);
     const uint16_t *rank = (const uint16_t *)(d.ro + Q.rank);
-    uint32_t *adj32 = (uint32_t *)adj;
-    for (int i = lane; i < 8 * n; i += 32) adj32[i] = 0u;
-    __syncwarp();
-    for (int v = lane; v < n; v += 32) {
-      const int2 p0 = __ldcg(ptr + v), p1 = __ldcg(ptr + v + 1);
-      uint8_t *row = adj + v * 32;
-      for (int i = p0.x; i < p1.x; ++i) {
-        const int u = __ldcg(cnbr + i);
-        row[u / P] |= (uint8_t)(1u << (u % P));
+    if (it.build) {
+      uint32_t *adj32 = (uint32_t *)adj;
+      for (int i = lane; i < 8 * n; i += 32) adj32[i] = 0u;
+      __syncwarp();
+      for (int v = lane; v < n; v += 32) {
+        const int2 p0 = __ldcg(ptr + v), p1 = __ldcg(ptr + v + 1);
+        uint8_t *row = adj + v * 32;
+        for (int i = p0.x; i < p1.x; ++i) {
+          const int u = __ldcg(cnbr + i);
+          row[u / P] |= (uint8_t)(1u << (u % P));
+        }
+        for (int i = p0.y; i < p1.y; ++i) {
+          const int u = __ldcg(snbr + i);
+          row[u / P] |= (uint8_t)(1u << (4 + u % P));
+        }
+        deg[v] = (uint32_t)(p1.x - p0.x) | ((uint32_t)(p1.y - p0.y) << 16);
       }
-      for (int i = p0.y; i < p1.y; ++i) {
-        const int u = __ldcg(snbr + i);
-        row[u / P] |= (uint8_t)(1u << (4 + u % P));
-      }
-      deg[v] = (uint32_t)(p1.x - p0.x) | ((uint32_t)(p1.y - p0.y) << 16);
     }
 #pragma unroll
     for (int j = 0; j < P; ++j)
@@ -963,11 +1071,21 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
   __syncwarp();
   int D;
   uint32_t ns;
-  par_cut(n, k, G, D, ns);
+  if (it.split_cut) split_cut(n, k, D, ns);
+  else par_cut(n, k, G, D, ns);
   int64_t nodes = 0, work = 0, nodes_pub = 0;
   uint32_t work32 = 0;
-  bool timed_out = false, last_item = false;
-  unsigned long long my_key = ~0ull, cached = mode == PAR_REPLAY ? replay_key : ~0ull;
+  bool timed_out = false, last_item = false, budget_hit = false, found = false;
+  const int64_t budget = mode == PAR_BUDGET ? it.budget : 0;
+  unsigned long long my_key = ~0ull;
+  unsigned long long cached = (mode == PAR_REPLAY || mode == PAR_BUDGET) ? replay_key : ~0ull;
+  // m children pruned on entry by their path cost: counted as the recursive
+  // search counts them, stopping where the node budget does
+  auto count_pruned = [&](int m) -> bool {
+    const int64_t room = budget > 0 ? budget - nodes : (int64_t)m;
+    nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
+    return room < m;
+  };
   // the instance's start: the first warp to arrive sets it, and every warp
   // measures the time limit from there, so the limit bounds the instance's
   // wall time, not each warp's.  The replay, which runs once the instance
@@ -996,6 +1114,9 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
     if (mode == PAR_REPLAY) {
       if (!first_pass) break;
       s = (uint32_t)(replay_key & 0xFFFFFFFFull) - 1u;
+    } else if (mode == PAR_BUDGET) {
+      if (!first_pass) break;
+      s = it.sub;
     } else {
       if (lane == 0) s = atomicAdd(&ctx->next, 1u);
       s = __shfl_sync(FULL, s, 0);
@@ -1026,10 +1147,11 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
     // a leaf of cost g in subtree s
     auto take_leaf = [&]() {
       const unsigned long long key = ((unsigned long long)(uint32_t)g << 32) | s;
-      if (lane == 0 && mode != PAR_REPLAY) atomicMin(&ctx->key, key);
+      if (lane == 0 && mode != PAR_REPLAY && mode != PAR_BUDGET) atomicMin(&ctx->key, key);
       my_key = key;
+      found = true;
       cached = key < cached ? key : cached;
-      int8_t *dst = mode == PAR_REPLAY ? d.mask : bestx;
+      int8_t *dst = mode == PAR_REPLAY ? d.mask : mode == PAR_BUDGET ? nullptr : bestx;
       if (dst) {
 #pragma unroll
         for (int j = 0; j < P; ++j)
@@ -1044,12 +1166,18 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
     if (!timed_out) {
       for (;;) {
         if (enter) {
-          if (mode != PAR_REPLAY && (nodes & 15) == 0) {
+          if (mode != PAR_REPLAY && mode != PAR_BUDGET && (nodes & 15) == 0) {
             // one read of the shared key for the whole warp
             unsigned long long kk = 0ull;
             if (lane == 0) kk = *(volatile unsigned long long *)&ctx->key;
             kk = __shfl_sync(FULL, kk, 0);
             cached = kk < cached ? kk : cached;
+          }
+          // the node budget (an incumbent always exists here: the first
+          // search's)
+          if (budget > 0 && nodes >= budget) {
+            budget_hit = true;
+            break;
           }
           ++nodes;
           work32 += 2u * (uint32_t)(n - level);
@@ -1141,8 +1269,10 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
   #pragma unroll
           for (int i = 1; i < MK; ++i) kf = i == first ? keys[i] : kf;
           if (thr < INF32 && g + (int32_t)(kf >> 3) >= thr) {
-            // this row and the ones after it cannot improve
-            if (level < D) break;
+            // this row and the ones after it cannot improve: their nodes are
+            // pruned on entry (above the cut only the forced row is taken)
+            if (count_pruned(level < D ? 1 : k)) budget_hit = true;
+            if (level < D || budget_hit) break;
             enter = false;
             continue;
           }
@@ -1196,7 +1326,14 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
         move_counts(cl, cb8, sb8, false);
         bool last = nxt >= k;
         const int32_t thr = threshold(s);
-        if (!last && thr < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= thr) last = true;
+        if (!last && thr < INF32 && (int32_t)r0.y + (int32_t)(knext >> 3) >= thr) {
+          // this row and the ones after it: children pruned on entry
+          if (count_pruned(k - nxt)) {
+            budget_hit = true;
+            break;
+          }
+          last = true;
+        }
         if (last) {
           if (lane == src) {
             w |= (r0.x >> 12) << (FB * jv);
@@ -1216,6 +1353,20 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
         enter = true;
         __syncwarp();
       }
+    }
+    if (mode == PAR_BUDGET) {
+      // publish this subtree's incumbent and totals, then count it done
+      uint32_t fin = 0;
+      if (lane == 0) {
+        if (found) atomicMin(&ctx->key, my_key);
+        atomicAdd(&ctx->nodes, (unsigned long long)nodes);
+        atomicAdd(&ctx->work, (unsigned long long)(work + work32));
+        if (timed_out) atomicExch(&ctx->timed_out, 1u);
+        if (budget_hit) atomicExch(&ctx->pad, 1u);
+        __threadfence();
+        fin = atomicAdd(&ctx->done, 1u) == ns - 1u ? 1u : 0u;
+      }
+      if (__shfl_sync(FULL, fin, 0)) last_item = true;
     }
     if (mode == PAR_QUEUE) {
       // publish this subtree's totals, then count it done
@@ -1243,17 +1394,19 @@ __device__ __noinline__ bool par_search(const InstDesc &d, uint8_t *base, const 
     }
   }
   __syncwarp();
-  return last_item;
+  // the replay reports whether it took its leaf
+  return mode == PAR_REPLAY ? found : last_item;
 }
 
 // par_search for the instance's field width, mask count and column rule.
 __device__ __noinline__ bool par_dispatch(const InstDesc &d, uint8_t *base, const LaunchArgs &a,
                                           int lane, int gw, int G, ParCtx *ctx,
                                           unsigned long long *wkey, int8_t *bestx, int mode,
-                                          unsigned long long replay_key) {
+                                          unsigned long long replay_key,
+                                          const ParItem &it = ParItem{}) {
 #define MPLD_PAR(FT, MK)                                                                        \
-  return a.rule ? par_search<FT, MK, 1>(d, base, a, lane, gw, G, ctx, wkey, bestx, mode, replay_key) \
-                : par_search<FT, MK, 0>(d, base, a, lane, gw, G, ctx, wkey, bestx, mode, replay_key)
+  return a.rule ? par_search<FT, MK, 1>(d, base, a, lane, gw, G, ctx, wkey, bestx, mode, replay_key, it) \
+                : par_search<FT, MK, 0>(d, base, a, lane, gw, G, ctx, wkey, bestx, mode, replay_key, it)
   if (d.k == 3) { MPLD_PAR(uint8_t, 3); }
   if (d.k == 4) { MPLD_PAR(uint8_t, 4); }
   if (d.k == 2) { MPLD_PAR(uint8_t, 2); }
@@ -1313,12 +1466,23 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   team.sync();
   int32_t best = INF32;
   int64_t nodes = 0, work = 0;
-  const int st = s.run(lane, a.budget, a.time_limit_ns, d.mask, best, nodes, work);
+  SplitSpec sp;
+  int64_t budget = a.budget;
+  if (a.split) {
+    // budgeted split search, first phase: this search's share of the budget
+    uint32_t S;
+    split_cut(n, d.k, sp.cut, S);
+    sp.track = sp.cut > 0;
+    budget = split_search_budget(a.budget, S);
+  }
+  const int st = s.run(lane, budget, a.time_limit_ns, d.mask, best, nodes, work, sp);
   if (lane == 0) {
     d.res->cost = best == INF32 ? INT64_MAX : (int64_t)best;
     d.res->nodes = nodes;
     d.res->status = st;
+    d.res->sub = (int32_t)sp.sub_out;
     d.res->work = work;
+    if (a.split && st == MPLD_BUDGET) split_enlist(a, d, best, sp.sub_out);
   }
   team.sync();
 }
@@ -1392,6 +1556,195 @@ template <typename FT, int MK>
 __device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArgs &a,
                                               const CtaTeam &team) {
   run_in<FT, MK, false>(d, d.scratch, d.ro, a, team);
+}
+
+// Budgeted split search, second phase, for an instance beyond the register
+// form: one subtree searched by one warp with the general search, its state
+// in the warp's own global region (`state`), its adjacency read through L2.
+// search: subtree s with budget b and the incumbent key1 (the first
+// search's); publishes to the context as par_search's PAR_BUDGET does and
+// returns true in the warp that completes the last subtree.  replay: the
+// subtree and bound of `key1` (cost* << 32 | s* + 1), masks to d.mask;
+// returns whether it took its leaf.
+template <typename FT, int MK>
+__device__ __noinline__ bool split_general(const InstDesc &d, uint8_t *state, const LaunchArgs &a,
+                                           int lane, ParCtx *ctx, uint32_t s, int cut, uint32_t S,
+                                           int64_t b, unsigned long long key1, bool replay) {
+  using Srch = Search<FT, MK, false, WarpTeam>;
+  const int n = d.n;
+  const StateLayout L = state_layout(n, d.ne2, d.k, 0);
+  const RoLayout R = ro_layout(n, d.ne2, d.ns2, 0);
+  Srch sr;
+  sr.team = WarpTeam{lane};
+  sr.lv = (uint4 *)(state + L.lv);
+  sr.lvx = (int32_t *)(state + L.lvx);
+  sr.ccnt = (uint64_t *)(state + L.ccnt);
+  sr.scnt = (uint64_t *)(state + L.scnt);
+  sr.rows = (FT *)(state + L.rows);
+  sr.oldf = (FT *)(state + L.oldf);
+  sr.savf = (FT *)(state + L.savf);
+  sr.x = (int8_t *)(state + L.x);
+  sr.ptr = (const int2 *)(d.ro + R.ptr);
+  sr.cnbr = (const uint16_t *)(d.ro + R.cnbr);
+  sr.snbr = (const uint16_t *)(d.ro + R.snbr);
+  sr.rank = (const uint16_t *)(d.ro + R.rank);
+  sr.order = (const uint16_t *)(d.ro + R.order);
+  sr.qptr = nullptr;
+  sr.qlist = nullptr;
+  sr.qcnt = state + L.qcnt;
+  sr.qlev = (int32_t *)(state + L.qlev);
+  sr.nq = 0;
+  sr.rule = a.rule;
+  sr.n = n;
+  sr.k = d.k;
+  sr.Cc = d.cost_conflict;
+  sr.Cs = d.cost_stitch;
+  sr.kmask = (1u << d.k) - 1u;
+  const FT init = (FT)(sr.kmask | Srch::FLAG);
+  const int nfields = ((n + Srch::PER_WORD - 1) / Srch::PER_WORD) * Srch::PER_WORD;
+  for (int i = lane; i < nfields; i += 32) sr.rows[i] = i < n ? init : (FT)0;
+  for (int i = lane; i < n; i += 32) sr.x[i] = -1;
+  for (int i = lane; i < n * Srch::CW; i += 32) {
+    sr.ccnt[i] = 0;
+    sr.scnt[i] = 0;
+  }
+  __syncwarp();
+  SplitSpec sp;
+  sp.cut = cut;
+  sp.forced = true;
+  sp.replay = replay;
+  const int32_t kc = (int32_t)(key1 >> 32);
+  const uint32_t ks = (uint32_t)(key1 & 0xFFFFFFFFull);
+  sp.prefix = replay ? ks - 1u : s;
+  sp.init_best = replay ? kc + 1 : kc + (s < ks ? 1 : 0);
+  // the time limit runs from the instance's start (the replay's from its own)
+  uint64_t t0 = 0;
+  if (lane == 0) {
+    const uint64_t now = globaltimer();
+    if (replay) {
+      t0 = now;
+    } else {
+      const unsigned long long prev = atomicCAS(&ctx->t0, 0ull, (unsigned long long)now);
+      t0 = prev != 0ull ? (uint64_t)prev : now;
+    }
+  }
+  t0 = __shfl_sync(FULL, t0, 0);
+  int32_t best = INF32;
+  int64_t nodes = 0, work = 0;
+  const int st = sr.run(lane, replay ? 0 : b, a.time_limit_ns, replay ? d.mask : nullptr, best,
+                        nodes, work, sp, t0);
+  if (replay) return sp.found;
+  uint32_t fin = 0;
+  if (lane == 0) {
+    if (sp.found) atomicMin(&ctx->key, ((unsigned long long)(uint32_t)best << 32) | s);
+    atomicAdd(&ctx->nodes, (unsigned long long)nodes);
+    atomicAdd(&ctx->work, (unsigned long long)work);
+    if (st == MPLD_TIMEOUT) atomicExch(&ctx->timed_out, 1u);
+    if (st == MPLD_BUDGET) atomicExch(&ctx->pad, 1u);
+    __threadfence();
+    fin = atomicAdd(&ctx->done, 1u) == S - 1u ? 1u : 0u;
+  }
+  return __shfl_sync(FULL, fin, 0) != 0u;
+}
+
+__device__ __noinline__ bool split_general_dispatch(const InstDesc &d, uint8_t *state,
+                                                    const LaunchArgs &a, int lane, ParCtx *ctx,
+                                                    uint32_t s, int cut, uint32_t S, int64_t b,
+                                                    unsigned long long key1, bool replay) {
+  if (d.k == 3) return split_general<uint8_t, 3>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
+  if (d.k == 4) return split_general<uint8_t, 4>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
+  if (d.k == 2) return split_general<uint8_t, 2>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
+  if (d.k <= 7) return split_general<uint8_t, 8>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
+  return split_general<uint16_t, 8>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
+}
+
+// Budgeted split search, second phase (par == 4): the warps of the grid take
+// items t = j * smax + s from a global counter, for hard-list entry j and
+// subtree s (items past the entry's own subtree count are skipped).  Each
+// subtree is searched on its own with its share of the budget; the warp
+// that completes an entry's last subtree replays the winning subtree (unless
+// the first search's incumbent stands, whose masks are already written) and
+// writes the instance's result: the best (cost, subtree), nodes and work of
+// both phases, and status TIMEOUT / BUDGET / OK.
+__device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int warp, int nw,
+                                              uint8_t *mine) {
+  const int G = (int)gridDim.x * nw;
+  const int gw = (int)blockIdx.x * nw + warp;
+  uint8_t *wstate = a.split_scratch ? a.split_scratch + (size_t)gw * (size_t)a.split_state_bytes
+                                    : nullptr;
+  uint32_t H = 0;
+  if (lane == 0) H = (uint32_t)*(volatile int32_t *)a.hard;
+  H = __shfl_sync(FULL, H, 0);
+  const uint64_t total = (uint64_t)H * (uint64_t)a.smax;
+  int built = -1;   // instance whose adjacency the slot holds
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(a.queue, 1u);
+    t = __shfl_sync(FULL, t, 0);
+    if ((uint64_t)t >= total) break;
+    const uint32_t j = t / (uint32_t)a.smax, s = t % (uint32_t)a.smax;
+    const int di = __ldcg(a.hard + 1 + j);
+    const InstDesc d = a.desc[di];
+    int D;
+    uint32_t S;
+    split_cut(d.n, d.k, D, S);
+    if (s >= S) continue;
+    ParCtx *ctx = (ParCtx *)(a.par_buf + (size_t)j * 64);
+    const int64_t b = split_search_budget(a.budget, S);
+    const int64_t c1 = __ldcg(&d.res->cost);
+    const uint32_t s1 = (uint32_t)__ldcg(&d.res->sub);
+    const unsigned long long key1 = ((unsigned long long)(uint32_t)c1 << 32) | s1;
+    const bool reg = reg_fits(d.n, d.k) && a.slot_bytes >= (int)reg_layout(d.n, d.k, 0).bytes;
+    if (!reg && (!wstate || a.split_state_bytes < d.state_bytes)) {
+      // the host sizes the per-warp regions for every instance
+      if (lane == 0) atomicExch(a.err, MPLD_E_STATE);
+      return;
+    }
+    bool fin;
+    if (reg) {
+      ParItem it;
+      it.sub = s;
+      it.budget = b;
+      it.build = built != di;
+      it.split_cut = true;
+      fin = par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_BUDGET, key1, it);
+      built = di;
+    } else {
+      fin = split_general_dispatch(d, wstate, a, lane, ctx, s, D, S, b, key1, false);
+    }
+    if (!fin) continue;
+    // every subtree of the instance is done: its best key is final
+    __threadfence();
+    unsigned long long key = 0ull;
+    if (lane == 0) key = *(volatile unsigned long long *)&ctx->key;
+    key = __shfl_sync(FULL, key, 0);
+    bool ok = true;
+    if (key != key1) {
+      const unsigned long long rk = (key & ~0xFFFFFFFFull) | ((key & 0xFFFFFFFFull) + 1ull);
+      if (reg) {
+        ParItem it;
+        it.build = false;
+        it.split_cut = true;
+        ok = par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_REPLAY, rk, it);
+      } else {
+        ok = split_general_dispatch(d, wstate, a, lane, ctx, 0, D, S, 0, rk, true);
+      }
+      // a replay that ran out of time leaves the first search's masks, so
+      // its incumbent is the result
+      if (!ok) key = key1;
+    }
+    if (lane == 0) {
+      const int64_t nodes1 = d.res->nodes, work1 = d.res->work;
+      const uint32_t to = *(volatile uint32_t *)&ctx->timed_out;
+      const uint32_t bh = *(volatile uint32_t *)&ctx->pad;
+      d.res->cost = (int64_t)(key >> 32);
+      d.res->nodes = nodes1 + (int64_t)*(volatile unsigned long long *)&ctx->nodes;
+      d.res->work = work1 + (int64_t)*(volatile unsigned long long *)&ctx->work;
+      d.res->sub = (int32_t)(key & 0xFFFFFFFFull);
+      d.res->status = (to || !ok) ? MPLD_TIMEOUT : bh ? MPLD_BUDGET : MPLD_OK;
+    }
+    __syncwarp();
+  }
 }
 
 // Every warp of the grid splits the instances desc[order[0..n_inst)] one
@@ -1501,6 +1854,10 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
   }
   if (a.par == 3) {
     run_grid_queue(a, lane, warp, nw, g_smem + slot_off);
+    return;
+  }
+  if (a.par == 4) {
+    run_split_phase2(a, lane, warp, nw, g_smem + slot_off);
     return;
   }
 
@@ -1664,7 +2021,7 @@ static_assert(sizeof(mpld_instance_result) == sizeof(InstResult), "result layout
 static_assert(offsetof(mpld_instance_result, cost) == offsetof(InstResult, cost), "result layout");
 static_assert(offsetof(mpld_instance_result, nodes) == offsetof(InstResult, nodes), "result layout");
 static_assert(offsetof(mpld_instance_result, status) == offsetof(InstResult, status), "result layout");
-static_assert(offsetof(mpld_instance_result, device_error) == offsetof(InstResult, pad0), "result layout");
+static_assert(offsetof(mpld_instance_result, device_error) == offsetof(InstResult, sub), "result layout");
 static_assert(offsetof(mpld_instance_result, work) == offsetof(InstResult, work), "result layout");
 
 // One warp: check and pack the caller's adjacency into the array, then run
@@ -1742,7 +2099,7 @@ __global__ void __launch_bounds__(32, 1)
       res_out->cost = INT64_MAX;
       res_out->nodes = 0;
       res_out->status = MPLD_E_INVALID;
-      res_out->pad0 = 0;
+      res_out->sub = 0;
       res_out->work = 0;
     }
     return;
@@ -1771,6 +2128,7 @@ __global__ void __launch_bounds__(32, 1)
   d.cost_conflict = inst.cost_conflict;
   d.cost_stitch = inst.cost_stitch;
   d.nq = 0;
+  d.idx = 0;
   d.pad1 = 0;
   LaunchArgs a;
   a.desc = nullptr;
@@ -1784,7 +2142,7 @@ __global__ void __launch_bounds__(32, 1)
   a.rule = 0;
   a.n_large = 0;
   a.par = 0;
-  a.pad = 0;
+  a.split = 0;
   a.par_buf = nullptr;
   uint32_t phase = 0;
   const uint32_t slot_off = align16(8u);
@@ -1796,7 +2154,7 @@ __global__ void __launch_bounds__(32, 1)
   // the status word (a bulk copy that did not land in time: the search then
   // ran from the array instead, and its result stands)
   __syncwarp();
-  if (lane == 0) res_out->pad0 = *(volatile int32_t *)err;
+  if (lane == 0) res_out->sub = *(volatile int32_t *)err;
 }
 
 // Per-device set-up of the allocation-free path: the array's device address
@@ -1819,6 +2177,7 @@ extern "C" int mpld_search_instance_noalloc(const mpld_device_instance *inst,
   if (!inst || !mask_out || !result_out || !inst->conf_ptr || !inst->st_ptr) return MPLD_E_INVALID;
   if (prm && (prm->flags & MPLD_COLUMN_BFS)) return MPLD_E_INVALID;  // no breadth-first ranks here
   if (prm && (prm->flags & MPLD_PARALLEL_EXACT)) return MPLD_E_INVALID;  // one warp per instance
+  if (prm && (prm->flags & MPLD_SPLIT_BUDGET)) return MPLD_E_INVALID;    // no second launch here
   const int n = inst->n, k = inst->k, ne2 = inst->n_conf_entries, ns2 = inst->n_stitch_entries;
   if (n < 1 || k < 2 || k > 8 || ne2 < 0 || ns2 < 0) return MPLD_E_INVALID;
   if ((ne2 > 0 && !inst->conf_nbr) || (ns2 > 0 && !inst->st_nbr)) return MPLD_E_INVALID;

@@ -292,7 +292,7 @@ int launch_request(mpld_server *s, Req &r) {
   a.rule = s->rule;
   a.n_large = n_large;
   a.par = 0;
-  a.pad = 0;
+  a.split = 0;
   a.par_buf = nullptr;
   rc = mpld_internal_launch(&a, ctas, nw, st);
   if (rc) return rc;
