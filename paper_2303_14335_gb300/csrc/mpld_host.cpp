@@ -799,6 +799,17 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       }
       ptr[2 * nc] = ci;
       ptr[2 * nc + 1] = si;
+      if (nc <= mpld::LANE_MAX_N) {
+        // the neighbours of each segment as bit masks (the per-lane search)
+        uint32_t *bits = (uint32_t *)(blk + R.bits);
+        for (int v = 0; v < nc; ++v) {
+          uint32_t cm = 0, sm = 0;
+          for (int i = ptr[2 * v]; i < ptr[2 * v + 2]; ++i) cm |= 1u << cn[i];
+          for (int i = ptr[2 * v + 1]; i < ptr[2 * v + 3]; ++i) sm |= 1u << sn[i];
+          bits[v] = cm;
+          bits[nc + v] = sm;
+        }
+      }
       // breadth-first ranks over conflict and stitch edges (local ids):
       // roots ascending, each segment's neighbours ascending, once each
       uint16_t *rank = (uint16_t *)(blk + R.rank);
@@ -1167,14 +1178,15 @@ int launch_queue(mpld_problem *p, const QueuePlan &q, const mpld_params *prm, cu
 // (or plain) launch with split = 1, which searches every instance with its
 // per-search budget and puts the ones that stop on it on the hard list; the
 // second launch (par = 4) searches their subtrees, one per warp at a time.
-// Device block: hard list (count, then descriptor indices), one 64-byte
-// context per instance, then each warp's state for instances beyond the
-// register form.
+// Device block: the two hard lists (their counts, then descriptor indices:
+// instances the per-lane search takes, and the rest), one 64-byte context per
+// descriptor, then each warp's state for instances beyond the register form.
 struct SplitPlan {
   bool on = false;
   int nw = 0, slot = 0, ctas = 0;   // second launch
   int smax = 1;                     // item numbers per hard-list entry
   int state_bytes = 0;              // per warp, general form (0: no such instance)
+  int cap = 0;                      // entries of each hard list (the launch's descriptors)
   size_t o_hard = 0, o_ctx = 0, o_state = 0, bytes = 0;
 };
 SplitPlan split_plan_of(const InstDesc *desc, int n_inst, const mpld_params *prm) {
@@ -1189,6 +1201,7 @@ SplitPlan split_plan_of(const InstDesc *desc, int n_inst, const mpld_params *prm
     uint32_t S;
     mpld::split_cut(d.n, d.k, D, S);
     q.smax = std::max(q.smax, (int)S);
+    if (mpld::lane_fits(d.n, d.k)) reg_slot = std::max(reg_slot, (int)mpld::LANE_STACK_BYTES);
     if (mpld::reg_fits(d.n, d.k))
       reg_slot = std::max(reg_slot, (int)mpld::align16(mpld::reg_layout(d.n, d.k, 0).bytes));
     else
@@ -1203,7 +1216,8 @@ SplitPlan split_plan_of(const InstDesc *desc, int n_inst, const mpld_params *prm
   q.ctas = per_sm * std::max(1, mpld_internal_num_sms());
   q.state_bytes = gen ? (int)((gen + 255) & ~(size_t)255) : 0;
   q.o_hard = 0;
-  q.o_ctx = (4u * (size_t)(n_inst + 1) + 255) & ~(size_t)255;
+  q.cap = n_inst;
+  q.o_ctx = (4u * (size_t)(2 + 2 * n_inst) + 255) & ~(size_t)255;
   q.o_state = q.o_ctx + 64u * (size_t)n_inst;
   q.bytes = q.o_state + (size_t)q.ctas * (size_t)q.nw * (size_t)q.state_bytes;
   return q;
@@ -1232,6 +1246,7 @@ int ensure_split_buf(mpld_problem *p, size_t bytes) {
 void split_phase1(mpld::LaunchArgs &a, const SplitPlan &q, uint8_t *buf) {
   a.split = q.on ? 1 : 0;
   a.hard = q.on ? (int32_t *)(buf + q.o_hard) : nullptr;
+  a.hard_cap = q.cap;
   a.par_buf = q.on ? buf + q.o_ctx : a.par_buf;
 }
 // The second launch, after the first on the same stream: its item counter
@@ -1249,6 +1264,7 @@ int launch_split_phase2(const mpld::LaunchArgs &a1, const InstDesc *desc, const 
   a.par = 4;
   a.split = 0;
   a.hard = (int32_t *)(buf + q.o_hard);
+  a.hard_cap = q.cap;
   a.par_buf = buf + q.o_ctx;
   a.split_scratch = q.state_bytes ? buf + q.o_state : nullptr;
   a.smax = q.smax;
@@ -1314,7 +1330,7 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     if (rc) return rc;
     if (sp.on) {
       // the first phase over every instance, then the subtrees of the hard ones
-      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 4, st));
+      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 8, st));
       rc |= launch_batch(a, sh, st, p->d_queue, p->d_err);
       if (rc == MPLD_OK) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
     } else if (gs.on) {
@@ -1544,7 +1560,7 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
       // this instance's first search; if it stops on its budget, its
       // subtrees in a second launch
       split_phase1(a, sp, p->d_split);
-      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 4, st));
+      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 8, st));
       if (rc == MPLD_OK) rc = mpld_internal_launch(&a, 1, large ? CTA_TEAM_WARPS : 1, st);
       if (rc == MPLD_OK) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
       continue;
@@ -1680,7 +1696,7 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   } else if (!rc && sp.on) {
     // the first phase over every instance, then the subtrees of the hard ones
     split_phase1(a, sp, b + o_split);
-    rc = cuda_ok(cudaMemsetAsync(b + o_split + sp.o_hard, 0, 4, st));
+    rc = cuda_ok(cudaMemsetAsync(b + o_split + sp.o_hard, 0, 8, st));
     if (!rc) rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
     if (!rc) rc = launch_split_phase2(a, a.desc, sp, b + o_split, queue, st);
   } else if (!rc) {

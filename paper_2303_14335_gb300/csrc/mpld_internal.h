@@ -34,12 +34,15 @@ MPLD_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 //   order[n]  uint16  segment of each breadth-first rank
 //   qptr[n+1] int32   (nq > 0 only) each segment's range in qlist
 //   qlist[nq*(k+1)] uint16  the bound's cliques holding each segment
+//   bits[2n]  uint32  (n <= 32 only) each segment's conflict neighbours as a
+//                     bit mask, then its stitch neighbours (the per-lane search)
 // (rank / order serve the paper's column rule, Algorithm 1: a column with a
 // single row left, else the first uncovered column in BFS order of G; the
 // clique lists serve the second bound mode.)
 struct RoLayout {
-  uint32_t ptr, cnbr, snbr, rank, order, qptr, qlist, bytes;
+  uint32_t ptr, cnbr, snbr, rank, order, qptr, qlist, bits, bytes;
 };
+constexpr int LANE_MAX_N = 32;   // the per-lane search's largest instance
 MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
   RoLayout L;
   uint32_t o = 0;
@@ -50,9 +53,17 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
   L.order = o; o += align16(2u * (uint32_t)n);
   L.qptr = o; o += nqe > 0 ? align16(4u * (uint32_t)(n + 1)) : 0u;
   L.qlist = o; o += align16(2u * (uint32_t)nqe);
+  L.bits = o; o += n <= LANE_MAX_N ? align16(8u * (uint32_t)n) : 0u;
   L.bytes = o;
   return L;
 }
+// Instances the second phase of the budgeted split search gives to single
+// lanes (a subtree per lane, the whole state in registers as one bit per
+// segment); larger ones, or k > 4, to whole warps.
+MPLD_HD bool lane_fits(int n, int k) { return n <= LANE_MAX_N && k <= 4; }
+// Per-warp shared memory of the per-lane search: three 32-bit words per
+// (level, lane).
+constexpr uint32_t LANE_STACK_BYTES = 3u * 4u * 32u * (uint32_t)LANE_MAX_N;
 
 // Mutable search state of one instance (shared memory, or the instance's
 // global scratch region when it does not fit the warp's slot).  The DFS
@@ -202,10 +213,14 @@ struct LaunchArgs {
                            // hard list with a fresh context
   uint8_t *par_buf;        // par == 2: the split context in global memory (ParLayout);
                            // par == 3: one 64-byte context per queued instance;
-                           // split / par == 4: one 64-byte context per hard-list entry
-  int32_t *hard = nullptr; // split / par == 4: [0] entries, then the descriptor index of each
-  uint8_t *split_scratch = nullptr;  // par == 4: per-warp global search state for instances beyond
-                           // the register form (split_state_bytes per warp)
+                           // split / par == 4: one 64-byte context per descriptor index
+  int32_t *hard = nullptr; // split / par == 4: [0] entries for warps, [1] entries for lanes,
+                           // then hard_cap descriptor indices of each kind (instances that
+                           // stopped on their first-phase budget); contexts are per
+                           // descriptor index
+  int32_t hard_cap = 0;
+  uint8_t *split_scratch = nullptr;  // par == 4: per-warp global search state for instances
+                                     // beyond the register form (split_state_bytes per warp)
   int32_t smax = 0;        // par == 4: item numbers per hard-list entry (>= its subtrees)
   int32_t split_state_bytes = 0;
 };

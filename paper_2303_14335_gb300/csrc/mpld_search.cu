@@ -573,13 +573,15 @@ struct Search {
 };
 
 // Budgeted split search, first phase: an instance that stopped on its
-// per-search budget goes on the hard list, with a fresh context whose key is
+// per-search budget goes on a hard list (the lanes' for instances the
+// per-lane search takes, else the warps'), with a fresh context whose key is
 // its incumbent (cost << 32 | subtree of the incumbent's leaf).  Lane 0 only.
 __device__ __forceinline__ void split_enlist(const LaunchArgs &a, const InstDesc &d, int32_t best,
                                              uint32_t sub) {
-  const int j = atomicAdd(a.hard, 1);
-  a.hard[1 + j] = d.idx;
-  ParCtx *c = (ParCtx *)(a.par_buf + (size_t)j * 64);
+  const int kind = lane_fits(d.n, d.k) ? 1 : 0;
+  const int j = atomicAdd(a.hard + kind, 1);
+  a.hard[2 + kind * a.hard_cap + j] = d.idx;
+  ParCtx *c = (ParCtx *)(a.par_buf + (size_t)d.idx * 64);
   c->key = ((unsigned long long)(uint32_t)best << 32) | sub;
   c->nodes = 0;
   c->work = 0;
@@ -1658,38 +1660,288 @@ __device__ __noinline__ bool split_general_dispatch(const InstDesc &d, uint8_t *
   return split_general<uint16_t, 8>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
 }
 
-// Budgeted split search, second phase (par == 4): the warps of the grid take
-// items t = j * smax + s from a global counter, for hard-list entry j and
-// subtree s (items past the entry's own subtree count are skipped).  Each
-// subtree is searched on its own with its share of the budget; the warp
-// that completes an entry's last subtree replays the winning subtree (unless
-// the first search's incumbent stands, whose masks are already written) and
-// writes the instance's result: the best (cost, subtree), nodes and work of
-// both phases, and status TIMEOUT / BUDGET / OK.
+// ---- per-lane search (budgeted split search, second phase) ---------------
+//
+// For instances of at most 32 segments and k <= 4 every lane searches a
+// subtree of its own: the same canonical search as par_search's PAR_BUDGET
+// (same column and row order, bound, node count and budget), with the
+// instance's state in registers as one bit per segment:
+//   unc      bit v: primary column P_v uncovered;
+//   act[c]   bit v: row (v, c) still active (no conflict neighbour of v
+//            holds mask c);
+//   asg[c]   bit v: x_v = c;
+//   uncr     (column rule 1) bit r: the segment of breadth-first rank r is
+//            uncovered.
+// The column choice counts each segment's active rows with a bit-sliced
+// adder over act[], so the fewest-rows column is the lowest set bit of the
+// first non-empty count class; a row's added cost (Eq. 1) is
+// cost_conflict * popc(conflict nbrs & asg[c]) + cost_stitch *
+// (assigned stitch nbrs - popc(stitch nbrs & asg[c])); the cover of row
+// (v, c) is act[c] &= ~conflict nbrs(v) and the clearing of v's bits.  Each
+// level below the cut keeps three words in shared memory, laid out
+// [level][lane]: {v | row place << 8 | row order << 12}, the path cost, and
+// act[c] before the cover.
+struct LaneOut {
+  int32_t best;
+  bool found, hit, timed_out;
+  int64_t nodes, work;
+};
+
+// per segment, the number of active rows among act[0..K) is m, as a mask
+template <int K>
+__device__ __forceinline__ void row_count_classes(const uint32_t (&act)[K], uint32_t (&cls)[K + 1]) {
+  if constexpr (K == 2) {
+    const uint32_t s0 = act[0] ^ act[1], s1 = act[0] & act[1];
+    cls[0] = ~(s0 | s1); cls[1] = s0; cls[2] = s1;
+  } else if constexpr (K == 3) {
+    const uint32_t s0 = act[0] ^ act[1] ^ act[2];
+    const uint32_t s1 = (act[0] & act[1]) | (act[2] & (act[0] ^ act[1]));
+    cls[0] = ~(s0 | s1); cls[1] = s0 & ~s1; cls[2] = ~s0 & s1; cls[3] = s0 & s1;
+  } else {
+    const uint32_t t0 = act[0] ^ act[1], u0 = act[0] & act[1];
+    const uint32_t t1 = act[2] ^ act[3], u1 = act[2] & act[3];
+    const uint32_t s0 = t0 ^ t1, cy = t0 & t1;
+    const uint32_t s1 = u0 ^ u1 ^ cy, s2 = (u0 & u1) | (cy & (u0 ^ u1));
+    cls[0] = ~(s0 | s1 | s2); cls[1] = s0 & ~s1 & ~s2; cls[2] = ~s0 & s1 & ~s2;
+    cls[3] = s0 & s1 & ~s2; cls[4] = s2;   // four rows: s2 set, s0 = s1 = 0
+  }
+}
+
+template <int K, int RULE>
+__device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, int cut,
+                                         uint32_t prefix, int32_t thr0, int64_t budget, bool replay,
+                                         uint32_t *stk, int64_t time_limit_ns, uint64_t t0,
+                                         LaneOut &o) {
+  const int n = d.n;
+  const int Cc = d.cost_conflict, Cs = d.cost_stitch;
+  const RoLayout R = ro_layout(n, d.ne2, d.ns2, 0);
+  const uint32_t *cadj = (const uint32_t *)(ro + R.bits);
+  const uint32_t *sadj = cadj + n;
+  const uint16_t *rank = (const uint16_t *)(ro + R.rank);
+  const uint16_t *order = (const uint16_t *)(ro + R.order);
+  uint32_t *st_h = stk, *st_g = stk + 32 * LANE_MAX_N, *st_s = stk + 64 * LANE_MAX_N;
+  const uint32_t all = n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  uint32_t unc = all, uncr = all, act[K], asg[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    act[c] = all;
+    asg[c] = 0u;
+  }
+  int32_t thr = thr0, g = 0;
+  int level = 0;
+  int64_t nodes = 0, work = 0, next_check = 1024;
+  bool found = false, hit = false, tout = false;
+  auto count_pruned = [&](int m) -> bool {
+    const int64_t room = budget > 0 ? budget - nodes : (int64_t)m;
+    nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
+    return room < m;
+  };
+  // added cost of row (v, c) against the current assignment
+  auto row_cost = [&](uint32_t ca, uint32_t sa, int c) -> int32_t {
+    const int stot = __popc(sa & all & ~unc);
+    return Cc * __popc(ca & asg[c]) + Cs * (stot - __popc(sa & asg[c]));
+  };
+  bool enter = true;
+  for (;;) {
+    if (enter) {
+      // ---- a node ----
+      if (budget > 0 && nodes >= budget) { hit = true; break; }
+      ++nodes;
+      work += 2 * (n - level);
+      if (nodes >= next_check) {
+        next_check = nodes + 1024;
+        if ((int64_t)(globaltimer() - t0) > time_limit_ns) { tout = true; break; }
+      }
+      if (unc == 0u) {
+        // leaf: every primary column covered
+        if (g < thr) {
+          thr = g;
+          found = true;
+          if (replay) {
+            for (int v = 0; v < n; ++v) {
+              int m = 0;
+#pragma unroll
+              for (int c = 1; c < K; ++c) m = (asg[c] >> v) & 1u ? c : m;
+              d.mask[v] = (int8_t)m;
+            }
+            break;
+          }
+          if (g == 0) break;
+        }
+        if (level <= cut) break;
+        enter = false;
+        continue;
+      }
+      uint32_t cls[K + 1];
+      row_count_classes<K>(act, cls);
+      const uint32_t dead = unc & cls[0];
+      int v;
+      if constexpr (RULE == 0) {
+        uint32_t cand = dead;
+#pragma unroll
+        for (int m = 1; m <= K; ++m) cand = cand ? cand : (unc & cls[m]);
+        v = __ffs(cand) - 1;
+      } else {
+        const uint32_t single = unc & cls[1];
+        v = single ? __ffs(single) - 1 : (int)order[__ffs(uncr) - 1];
+      }
+      if (thr < INF32 && g + Cc * __popc(dead) >= thr) {
+        if (level < cut) break;
+        enter = false;
+        continue;
+      }
+      const uint32_t ca = cadj[v], sa = sadj[v];
+      uint32_t keys[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) keys[c] = ((uint32_t)row_cost(ca, sa, c) << 3) | (uint32_t)c;
+      sort_keys<K>(keys);
+      work += K * (__popc(ca) + __popc(sa)) + 5 * (1 + __popc(ca));
+      int place = 0;
+      if (level < cut) {
+        uint32_t pw = 1;
+        for (int i = level + 1; i < cut; ++i) pw *= (uint32_t)K;
+        place = (int)((prefix / pw) % (uint32_t)K);
+      }
+      uint32_t kp = keys[0];
+#pragma unroll
+      for (int i = 1; i < K; ++i) kp = i == place ? keys[i] : kp;
+      if (thr < INF32 && g + (int32_t)(kp >> 3) >= thr) {
+        // this row and the ones after it: their children are pruned on entry
+        if (count_pruned(level < cut ? 1 : K)) { hit = true; break; }
+        if (level < cut) break;
+        enter = false;
+        continue;
+      }
+      const int c = (int)(kp & 7u);
+      if (level >= cut) {
+        uint32_t ord = 0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) ord |= (keys[i] & 3u) << (2 * i);
+        st_h[level * 32] = (uint32_t)v | ((uint32_t)place << 8) | (ord << 12);
+        st_g[level * 32] = (uint32_t)g;
+        st_s[level * 32] = act[c];
+      }
+      const uint32_t bit = 1u << v;
+      act[c] &= ~ca;
+      unc &= ~bit;
+      asg[c] |= bit;
+      if (RULE) uncr &= ~(1u << rank[v]);
+      g += (int32_t)(kp >> 3);
+      ++level;
+      continue;
+    }
+    // ---- backtrack: next row of the level above, or undo its column ----
+    if (level <= cut) break;
+    --level;
+    const uint32_t h = st_h[level * 32];
+    const int32_t gl = (int32_t)st_g[level * 32];
+    const int v = (int)(h & 0xFFu), place = (int)((h >> 8) & 0xFu);
+    const uint32_t ord = h >> 12, bit = 1u << v;
+    const int cl = (int)((ord >> (2 * place)) & 3u);
+    act[cl] = st_s[level * 32];
+    asg[cl] &= ~bit;
+    unc |= bit;
+    if (RULE) uncr |= 1u << rank[v];
+    const int np = place + 1;
+    if (np >= K) continue;
+    const int c = (int)((ord >> (2 * np)) & 3u);
+    const uint32_t ca = cadj[v], sa = sadj[v];
+    const int32_t inc = row_cost(ca, sa, c);
+    if (thr < INF32 && gl + inc >= thr) {
+      // this row and the ones after it: children pruned on entry
+      if (count_pruned(K - np)) { hit = true; break; }
+      continue;
+    }
+    work += 5 * (1 + __popc(ca));
+    st_h[level * 32] = (h & ~0xF00u) | ((uint32_t)np << 8);
+    st_s[level * 32] = act[c];
+    act[c] &= ~ca;
+    unc &= ~bit;
+    asg[c] |= bit;
+    if (RULE) uncr &= ~(1u << rank[v]);
+    g = gl + inc;
+    ++level;
+    enter = true;
+  }
+  o.best = thr;
+  o.found = found;
+  o.hit = hit;
+  o.timed_out = tout;
+  o.nodes = nodes;
+  o.work = work;
+}
+
+__device__ __noinline__ void lane_dispatch(const InstDesc &d, int rule, int cut, uint32_t prefix,
+                                           int32_t thr0, int64_t budget, bool replay,
+                                           uint32_t *stk, int64_t tl, uint64_t t0, LaneOut &o) {
+  const uint8_t *ro = d.ro;
+  if (d.k == 3) {
+    if (rule) lane_search<3, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    else lane_search<3, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+  } else if (d.k == 4) {
+    if (rule) lane_search<4, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    else lane_search<4, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+  } else {
+    if (rule) lane_search<2, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    else lane_search<2, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+  }
+}
+
+// The instance's result once its last subtree is done (one thread): the
+// best (cost, subtree) with `ok` (false: its replay ran out of time, so the
+// first search's incumbent and masks stand), nodes and work of both phases.
+__device__ __forceinline__ void split_write_result(const InstDesc &d, ParCtx *ctx,
+                                                   unsigned long long key, bool ok) {
+  const int64_t nodes1 = d.res->nodes, work1 = d.res->work;
+  const uint32_t to = *(volatile uint32_t *)&ctx->timed_out;
+  const uint32_t bh = *(volatile uint32_t *)&ctx->pad;
+  d.res->cost = (int64_t)(key >> 32);
+  d.res->nodes = nodes1 + (int64_t)*(volatile unsigned long long *)&ctx->nodes;
+  d.res->work = work1 + (int64_t)*(volatile unsigned long long *)&ctx->work;
+  d.res->sub = (int32_t)(key & 0xFFFFFFFFull);
+  d.res->status = (to || !ok) ? MPLD_TIMEOUT : bh ? MPLD_BUDGET : MPLD_OK;
+}
+
+// Budgeted split search, second phase (par == 4).  Items t = j * smax + s
+// stand for hard-list entry j and subtree s (items past the entry's own
+// subtree count are skipped).  First every warp takes items of the warps'
+// list (instances beyond the per-lane search) from counter queue[0] and
+// searches each subtree with the whole warp; then every lane takes items of
+// the lanes' list from counter queue[1] on its own.  Each subtree has its own
+// share of the budget and the first search's incumbent as its bound; the
+// thread or warp that completes an instance's last subtree replays the
+// winning subtree to write its masks (unless the first search's incumbent
+// stands, whose masks are already written) and writes the result: the best
+// (cost, subtree), nodes and work of both phases, status TIMEOUT / BUDGET /
+// OK.
 __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int warp, int nw,
                                               uint8_t *mine) {
   const int G = (int)gridDim.x * nw;
   const int gw = (int)blockIdx.x * nw + warp;
   uint8_t *wstate = a.split_scratch ? a.split_scratch + (size_t)gw * (size_t)a.split_state_bytes
                                     : nullptr;
-  uint32_t H = 0;
-  if (lane == 0) H = (uint32_t)*(volatile int32_t *)a.hard;
-  H = __shfl_sync(FULL, H, 0);
-  const uint64_t total = (uint64_t)H * (uint64_t)a.smax;
+  uint32_t HW = 0, HL = 0;
+  if (lane == 0) {
+    HW = (uint32_t)*(volatile int32_t *)a.hard;
+    HL = (uint32_t)*(volatile int32_t *)(a.hard + 1);
+  }
+  HW = __shfl_sync(FULL, HW, 0);
+  HL = __shfl_sync(FULL, HL, 0);
+  const int32_t *list_w = a.hard + 2, *list_l = a.hard + 2 + a.hard_cap;
   int built = -1;   // instance whose adjacency the slot holds
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(a.queue, 1u);
     t = __shfl_sync(FULL, t, 0);
-    if ((uint64_t)t >= total) break;
+    if ((uint64_t)t >= (uint64_t)HW * (uint64_t)a.smax) break;
     const uint32_t j = t / (uint32_t)a.smax, s = t % (uint32_t)a.smax;
-    const int di = __ldcg(a.hard + 1 + j);
+    const int di = __ldcg(list_w + j);
     const InstDesc d = a.desc[di];
     int D;
     uint32_t S;
     split_cut(d.n, d.k, D, S);
     if (s >= S) continue;
-    ParCtx *ctx = (ParCtx *)(a.par_buf + (size_t)j * 64);
+    ParCtx *ctx = (ParCtx *)(a.par_buf + (size_t)di * 64);
     const int64_t b = split_search_budget(a.budget, S);
     const int64_t c1 = __ldcg(&d.res->cost);
     const uint32_t s1 = (uint32_t)__ldcg(&d.res->sub);
@@ -1729,21 +1981,59 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
       } else {
         ok = split_general_dispatch(d, wstate, a, lane, ctx, 0, D, S, 0, rk, true);
       }
-      // a replay that ran out of time leaves the first search's masks, so
-      // its incumbent is the result
       if (!ok) key = key1;
     }
-    if (lane == 0) {
-      const int64_t nodes1 = d.res->nodes, work1 = d.res->work;
-      const uint32_t to = *(volatile uint32_t *)&ctx->timed_out;
-      const uint32_t bh = *(volatile uint32_t *)&ctx->pad;
-      d.res->cost = (int64_t)(key >> 32);
-      d.res->nodes = nodes1 + (int64_t)*(volatile unsigned long long *)&ctx->nodes;
-      d.res->work = work1 + (int64_t)*(volatile unsigned long long *)&ctx->work;
-      d.res->sub = (int32_t)(key & 0xFFFFFFFFull);
-      d.res->status = (to || !ok) ? MPLD_TIMEOUT : bh ? MPLD_BUDGET : MPLD_OK;
-    }
+    if (lane == 0) split_write_result(d, ctx, key, ok);
     __syncwarp();
+  }
+  // the lanes' list: a subtree per lane
+  if (HL == 0 || a.slot_bytes < (int)LANE_STACK_BYTES) {
+    if (HL != 0 && lane == 0) atomicExch(a.err, MPLD_E_STATE);   // the host sizes the slot
+    return;
+  }
+  uint32_t *stk = (uint32_t *)mine + lane;
+  const uint64_t total = (uint64_t)HL * (uint64_t)a.smax;
+  for (;;) {
+    const uint32_t t = atomicAdd(a.queue + 1, 1u);
+    if ((uint64_t)t >= total) break;
+    const uint32_t j = t / (uint32_t)a.smax, s = t % (uint32_t)a.smax;
+    const int di = __ldcg(list_l + j);
+    const InstDesc d = a.desc[di];
+    int D;
+    uint32_t S;
+    split_cut(d.n, d.k, D, S);
+    if (s >= S) continue;
+    ParCtx *ctx = (ParCtx *)(a.par_buf + (size_t)di * 64);
+    const int64_t b = split_search_budget(a.budget, S);
+    const int64_t c1 = __ldcg(&d.res->cost);
+    const uint32_t s1 = (uint32_t)__ldcg(&d.res->sub);
+    const unsigned long long key1 = ((unsigned long long)(uint32_t)c1 << 32) | s1;
+    // the time limit runs from the instance's start
+    const uint64_t now = globaltimer();
+    const unsigned long long prev = atomicCAS(&ctx->t0, 0ull, (unsigned long long)now);
+    const uint64_t t0 = prev != 0ull ? (uint64_t)prev : now;
+    LaneOut o;
+    lane_dispatch(d, a.rule, D, s, (int32_t)c1 + (s < s1 ? 1 : 0), b, false, stk,
+                  a.time_limit_ns, t0, o);
+    if (o.found) atomicMin(&ctx->key, ((unsigned long long)(uint32_t)o.best << 32) | s);
+    atomicAdd(&ctx->nodes, (unsigned long long)o.nodes);
+    atomicAdd(&ctx->work, (unsigned long long)o.work);
+    if (o.timed_out) atomicExch(&ctx->timed_out, 1u);
+    if (o.hit) atomicExch(&ctx->pad, 1u);
+    __threadfence();
+    if (atomicAdd(&ctx->done, 1u) != S - 1u) continue;
+    // this lane completed the instance's last subtree
+    __threadfence();
+    unsigned long long key = *(volatile unsigned long long *)&ctx->key;
+    bool ok = true;
+    if (key != key1) {
+      LaneOut r;
+      lane_dispatch(d, a.rule, D, (uint32_t)(key & 0xFFFFFFFFull), (int32_t)(key >> 32) + 1, 0,
+                    true, stk, a.time_limit_ns, globaltimer(), r);
+      ok = r.found;
+      if (!ok) key = key1;
+    }
+    split_write_result(d, ctx, key, ok);
   }
 }
 
