@@ -801,11 +801,11 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
       ptr[2 * nc + 1] = si;
       if (nc <= mpld::LANE_MAX_N) {
         // the neighbours of each segment as bit masks (the per-lane search)
-        uint32_t *bits = (uint32_t *)(blk + R.bits);
+        uint64_t *bits = (uint64_t *)(blk + R.bits);
         for (int v = 0; v < nc; ++v) {
-          uint32_t cm = 0, sm = 0;
-          for (int i = ptr[2 * v]; i < ptr[2 * v + 2]; ++i) cm |= 1u << cn[i];
-          for (int i = ptr[2 * v + 1]; i < ptr[2 * v + 3]; ++i) sm |= 1u << sn[i];
+          uint64_t cm = 0, sm = 0;
+          for (int i = ptr[2 * v]; i < ptr[2 * v + 2]; ++i) cm |= 1ull << cn[i];
+          for (int i = ptr[2 * v + 1]; i < ptr[2 * v + 3]; ++i) sm |= 1ull << sn[i];
           bits[v] = cm;
           bits[nc + v] = sm;
         }

@@ -34,7 +34,7 @@ MPLD_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 //   order[n]  uint16  segment of each breadth-first rank
 //   qptr[n+1] int32   (nq > 0 only) each segment's range in qlist
 //   qlist[nq*(k+1)] uint16  the bound's cliques holding each segment
-//   bits[2n]  uint32  (n <= 32 only) each segment's conflict neighbours as a
+//   bits[2n]  uint64  (n <= 64 only) each segment's conflict neighbours as a
 //                     bit mask, then its stitch neighbours (the per-lane search)
 // (rank / order serve the paper's column rule, Algorithm 1: a column with a
 // single row left, else the first uncovered column in BFS order of G; the
@@ -42,7 +42,7 @@ MPLD_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 struct RoLayout {
   uint32_t ptr, cnbr, snbr, rank, order, qptr, qlist, bits, bytes;
 };
-constexpr int LANE_MAX_N = 32;   // the per-lane search's largest instance
+constexpr int LANE_MAX_N = 64;   // the per-lane search's largest instance
 MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
   RoLayout L;
   uint32_t o = 0;
@@ -53,7 +53,7 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
   L.order = o; o += align16(2u * (uint32_t)n);
   L.qptr = o; o += nqe > 0 ? align16(4u * (uint32_t)(n + 1)) : 0u;
   L.qlist = o; o += align16(2u * (uint32_t)nqe);
-  L.bits = o; o += n <= LANE_MAX_N ? align16(8u * (uint32_t)n) : 0u;
+  L.bits = o; o += n <= LANE_MAX_N ? align16(16u * (uint32_t)n) : 0u;
   L.bytes = o;
   return L;
 }
@@ -61,9 +61,11 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
 // lanes (a subtree per lane, the whole state in registers as one bit per
 // segment); larger ones, or k > 4, to whole warps.
 MPLD_HD bool lane_fits(int n, int k) { return n <= LANE_MAX_N && k <= 4; }
-// Per-warp shared memory of the per-lane search: three 32-bit words per
-// (level, lane).
-constexpr uint32_t LANE_STACK_BYTES = 3u * 4u * 32u * (uint32_t)LANE_MAX_N;
+// Per-warp shared memory of the per-lane search of instances up to 32
+// segments: three 32-bit words per (level, lane).  (Larger ones keep their
+// levels in each thread's local memory.)
+constexpr int LANE_SMEM_N = 32;
+constexpr uint32_t LANE_STACK_BYTES = 3u * 4u * 32u * (uint32_t)LANE_SMEM_N;
 
 // Mutable search state of one instance (shared memory, or the instance's
 // global scratch region when it does not fit the warp's slot).  The DFS

@@ -1662,10 +1662,11 @@ __device__ __noinline__ bool split_general_dispatch(const InstDesc &d, uint8_t *
 
 // ---- per-lane search (budgeted split search, second phase) ---------------
 //
-// For instances of at most 32 segments and k <= 4 every lane searches a
+// For instances of at most 64 segments and k <= 4 every lane searches a
 // subtree of its own: the same canonical search as par_search's PAR_BUDGET
 // (same column and row order, bound, node count and budget), with the
-// instance's state in registers as one bit per segment:
+// instance's state in registers as one bit per segment (W: a 32- or 64-bit
+// word):
 //   unc      bit v: primary column P_v uncovered;
 //   act[c]   bit v: row (v, c) still active (no conflict neighbour of v
 //            holds mask c);
@@ -1678,54 +1679,81 @@ __device__ __noinline__ bool split_general_dispatch(const InstDesc &d, uint8_t *
 // cost_conflict * popc(conflict nbrs & asg[c]) + cost_stitch *
 // (assigned stitch nbrs - popc(stitch nbrs & asg[c])); the cover of row
 // (v, c) is act[c] &= ~conflict nbrs(v) and the clearing of v's bits.  Each
-// level below the cut keeps three words in shared memory, laid out
-// [level][lane]: {v | row place << 8 | row order << 12}, the path cost, and
-// act[c] before the cover.
+// level below the cut keeps {v | row place << 8 | row order << 12}, the path
+// cost and act[c] before the cover: for up to 32 segments in shared memory
+// laid out [word][level][lane], for more in the thread's local memory.
 struct LaneOut {
   int32_t best;
   bool found, hit, timed_out;
   int64_t nodes, work;
 };
 
-// per segment, the number of active rows among act[0..K) is m, as a mask
-template <int K>
-__device__ __forceinline__ void row_count_classes(const uint32_t (&act)[K], uint32_t (&cls)[K + 1]) {
+template <typename W> __device__ __forceinline__ int popcw(W x) {
+  if constexpr (sizeof(W) == 4) return __popc(x);
+  else return __popcll(x);
+}
+template <typename W> __device__ __forceinline__ int lowbit(W x) {
+  if constexpr (sizeof(W) == 4) return __ffs(x) - 1;
+  else return __ffsll((long long)x) - 1;
+}
+
+// per segment, whether its number of active rows among act[0..K) is m
+template <int K, typename W>
+__device__ __forceinline__ void row_count_classes(const W (&act)[K], W (&cls)[K + 1]) {
   if constexpr (K == 2) {
-    const uint32_t s0 = act[0] ^ act[1], s1 = act[0] & act[1];
+    const W s0 = act[0] ^ act[1], s1 = act[0] & act[1];
     cls[0] = ~(s0 | s1); cls[1] = s0; cls[2] = s1;
   } else if constexpr (K == 3) {
-    const uint32_t s0 = act[0] ^ act[1] ^ act[2];
-    const uint32_t s1 = (act[0] & act[1]) | (act[2] & (act[0] ^ act[1]));
+    const W s0 = act[0] ^ act[1] ^ act[2];
+    const W s1 = (act[0] & act[1]) | (act[2] & (act[0] ^ act[1]));
     cls[0] = ~(s0 | s1); cls[1] = s0 & ~s1; cls[2] = ~s0 & s1; cls[3] = s0 & s1;
   } else {
-    const uint32_t t0 = act[0] ^ act[1], u0 = act[0] & act[1];
-    const uint32_t t1 = act[2] ^ act[3], u1 = act[2] & act[3];
-    const uint32_t s0 = t0 ^ t1, cy = t0 & t1;
-    const uint32_t s1 = u0 ^ u1 ^ cy, s2 = (u0 & u1) | (cy & (u0 ^ u1));
+    const W t0 = act[0] ^ act[1], u0 = act[0] & act[1];
+    const W t1 = act[2] ^ act[3], u1 = act[2] & act[3];
+    const W s0 = t0 ^ t1, cy = t0 & t1;
+    const W s1 = u0 ^ u1 ^ cy, s2 = (u0 & u1) | (cy & (u0 ^ u1));
     cls[0] = ~(s0 | s1 | s2); cls[1] = s0 & ~s1 & ~s2; cls[2] = ~s0 & s1 & ~s2;
     cls[3] = s0 & s1 & ~s2; cls[4] = s2;   // four rows: s2 set, s0 = s1 = 0
   }
 }
 
-template <int K, int RULE>
+// The level records: shared memory for 32-bit words, local memory for 64.
+template <typename W> struct LaneStack;
+template <> struct LaneStack<uint32_t> {
+  uint32_t *p;   // this lane's column of the warp's [3][LANE_SMEM_N][32] words
+  __device__ __forceinline__ uint32_t &h(int l) { return p[l * 32]; }
+  __device__ __forceinline__ uint32_t &g(int l) { return p[32 * LANE_SMEM_N + l * 32]; }
+  __device__ __forceinline__ uint32_t &s(int l) { return p[64 * LANE_SMEM_N + l * 32]; }
+};
+template <> struct LaneStack<unsigned long long> {
+  uint32_t hh[LANE_MAX_N], gg[LANE_MAX_N];
+  unsigned long long ss[LANE_MAX_N];
+  __device__ __forceinline__ uint32_t &h(int l) { return hh[l]; }
+  __device__ __forceinline__ uint32_t &g(int l) { return gg[l]; }
+  __device__ __forceinline__ unsigned long long &s(int l) { return ss[l]; }
+};
+
+template <typename W, int K, int RULE>
 __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, int cut,
                                          uint32_t prefix, int32_t thr0, int64_t budget, bool replay,
-                                         uint32_t *stk, int64_t time_limit_ns, uint64_t t0,
+                                         uint32_t *smem_stack, int64_t time_limit_ns, uint64_t t0,
                                          LaneOut &o) {
   const int n = d.n;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
   const RoLayout R = ro_layout(n, d.ne2, d.ns2, 0);
-  const uint32_t *cadj = (const uint32_t *)(ro + R.bits);
-  const uint32_t *sadj = cadj + n;
+  const unsigned long long *cadj = (const unsigned long long *)(ro + R.bits);
+  const unsigned long long *sadj = cadj + n;
   const uint16_t *rank = (const uint16_t *)(ro + R.rank);
   const uint16_t *order = (const uint16_t *)(ro + R.order);
-  uint32_t *st_h = stk, *st_g = stk + 32 * LANE_MAX_N, *st_s = stk + 64 * LANE_MAX_N;
-  const uint32_t all = n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-  uint32_t unc = all, uncr = all, act[K], asg[K];
+  LaneStack<W> st;
+  if constexpr (sizeof(W) == 4) st.p = smem_stack;
+  const W one = 1;
+  const W all = n >= (int)(8 * sizeof(W)) ? ~(W)0 : ((one << n) - one);
+  W unc = all, uncr = all, act[K], asg[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) {
     act[c] = all;
-    asg[c] = 0u;
+    asg[c] = 0;
   }
   int32_t thr = thr0, g = 0;
   int level = 0;
@@ -1737,9 +1765,9 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
     return room < m;
   };
   // added cost of row (v, c) against the current assignment
-  auto row_cost = [&](uint32_t ca, uint32_t sa, int c) -> int32_t {
-    const int stot = __popc(sa & all & ~unc);
-    return Cc * __popc(ca & asg[c]) + Cs * (stot - __popc(sa & asg[c]));
+  auto row_cost = [&](W ca, W sa, int c) -> int32_t {
+    const int stot = popcw<W>(sa & all & ~unc);
+    return Cc * popcw<W>(ca & asg[c]) + Cs * (stot - popcw<W>(sa & asg[c]));
   };
   bool enter = true;
   for (;;) {
@@ -1752,7 +1780,7 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
         next_check = nodes + 1024;
         if ((int64_t)(globaltimer() - t0) > time_limit_ns) { tout = true; break; }
       }
-      if (unc == 0u) {
+      if (unc == 0) {
         // leaf: every primary column covered
         if (g < thr) {
           thr = g;
@@ -1761,7 +1789,7 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
             for (int v = 0; v < n; ++v) {
               int m = 0;
 #pragma unroll
-              for (int c = 1; c < K; ++c) m = (asg[c] >> v) & 1u ? c : m;
+              for (int c = 1; c < K; ++c) m = (asg[c] >> v) & one ? c : m;
               d.mask[v] = (int8_t)m;
             }
             break;
@@ -1772,30 +1800,30 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
         enter = false;
         continue;
       }
-      uint32_t cls[K + 1];
-      row_count_classes<K>(act, cls);
-      const uint32_t dead = unc & cls[0];
+      W cls[K + 1];
+      row_count_classes<K, W>(act, cls);
+      const W dead = unc & cls[0];
       int v;
       if constexpr (RULE == 0) {
-        uint32_t cand = dead;
+        W cand = dead;
 #pragma unroll
         for (int m = 1; m <= K; ++m) cand = cand ? cand : (unc & cls[m]);
-        v = __ffs(cand) - 1;
+        v = lowbit<W>(cand);
       } else {
-        const uint32_t single = unc & cls[1];
-        v = single ? __ffs(single) - 1 : (int)order[__ffs(uncr) - 1];
+        const W single = unc & cls[1];
+        v = single ? lowbit<W>(single) : (int)order[lowbit<W>(uncr)];
       }
-      if (thr < INF32 && g + Cc * __popc(dead) >= thr) {
+      if (thr < INF32 && g + Cc * popcw<W>(dead) >= thr) {
         if (level < cut) break;
         enter = false;
         continue;
       }
-      const uint32_t ca = cadj[v], sa = sadj[v];
+      const W ca = (W)cadj[v], sa = (W)sadj[v];
       uint32_t keys[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) keys[c] = ((uint32_t)row_cost(ca, sa, c) << 3) | (uint32_t)c;
       sort_keys<K>(keys);
-      work += K * (__popc(ca) + __popc(sa)) + 5 * (1 + __popc(ca));
+      work += K * (popcw<W>(ca) + popcw<W>(sa)) + 5 * (1 + popcw<W>(ca));
       int place = 0;
       if (level < cut) {
         uint32_t pw = 1;
@@ -1817,15 +1845,15 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
         uint32_t ord = 0;
 #pragma unroll
         for (int i = 0; i < K; ++i) ord |= (keys[i] & 3u) << (2 * i);
-        st_h[level * 32] = (uint32_t)v | ((uint32_t)place << 8) | (ord << 12);
-        st_g[level * 32] = (uint32_t)g;
-        st_s[level * 32] = act[c];
+        st.h(level) = (uint32_t)v | ((uint32_t)place << 8) | (ord << 12);
+        st.g(level) = (uint32_t)g;
+        st.s(level) = act[c];
       }
-      const uint32_t bit = 1u << v;
+      const W bit = one << v;
       act[c] &= ~ca;
       unc &= ~bit;
       asg[c] |= bit;
-      if (RULE) uncr &= ~(1u << rank[v]);
+      if (RULE) uncr &= ~(one << rank[v]);
       g += (int32_t)(kp >> 3);
       ++level;
       continue;
@@ -1833,32 +1861,33 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
     // ---- backtrack: next row of the level above, or undo its column ----
     if (level <= cut) break;
     --level;
-    const uint32_t h = st_h[level * 32];
-    const int32_t gl = (int32_t)st_g[level * 32];
+    const uint32_t h = st.h(level);
+    const int32_t gl = (int32_t)st.g(level);
     const int v = (int)(h & 0xFFu), place = (int)((h >> 8) & 0xFu);
-    const uint32_t ord = h >> 12, bit = 1u << v;
+    const uint32_t ord = h >> 12;
+    const W bit = one << v;
     const int cl = (int)((ord >> (2 * place)) & 3u);
-    act[cl] = st_s[level * 32];
+    act[cl] = st.s(level);
     asg[cl] &= ~bit;
     unc |= bit;
-    if (RULE) uncr |= 1u << rank[v];
+    if (RULE) uncr |= one << rank[v];
     const int np = place + 1;
     if (np >= K) continue;
     const int c = (int)((ord >> (2 * np)) & 3u);
-    const uint32_t ca = cadj[v], sa = sadj[v];
+    const W ca = (W)cadj[v], sa = (W)sadj[v];
     const int32_t inc = row_cost(ca, sa, c);
     if (thr < INF32 && gl + inc >= thr) {
       // this row and the ones after it: children pruned on entry
       if (count_pruned(K - np)) { hit = true; break; }
       continue;
     }
-    work += 5 * (1 + __popc(ca));
-    st_h[level * 32] = (h & ~0xF00u) | ((uint32_t)np << 8);
-    st_s[level * 32] = act[c];
+    work += 5 * (1 + popcw<W>(ca));
+    st.h(level) = (h & ~0xF00u) | ((uint32_t)np << 8);
+    st.s(level) = act[c];
     act[c] &= ~ca;
     unc &= ~bit;
     asg[c] |= bit;
-    if (RULE) uncr &= ~(1u << rank[v]);
+    if (RULE) uncr &= ~(one << rank[v]);
     g = gl + inc;
     ++level;
     enter = true;
@@ -1871,20 +1900,31 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
   o.work = work;
 }
 
+template <typename W>
+__device__ __forceinline__ void lane_dispatch_w(const InstDesc &d, int rule, int cut,
+                                                uint32_t prefix, int32_t thr0, int64_t budget,
+                                                bool replay, uint32_t *stk, int64_t tl,
+                                                uint64_t t0, LaneOut &o) {
+  const uint8_t *ro = d.ro;
+  if (d.k == 3) {
+    if (rule) lane_search<W, 3, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    else lane_search<W, 3, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+  } else if (d.k == 4) {
+    if (rule) lane_search<W, 4, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    else lane_search<W, 4, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+  } else {
+    if (rule) lane_search<W, 2, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    else lane_search<W, 2, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+  }
+}
+
 __device__ __noinline__ void lane_dispatch(const InstDesc &d, int rule, int cut, uint32_t prefix,
                                            int32_t thr0, int64_t budget, bool replay,
                                            uint32_t *stk, int64_t tl, uint64_t t0, LaneOut &o) {
-  const uint8_t *ro = d.ro;
-  if (d.k == 3) {
-    if (rule) lane_search<3, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-    else lane_search<3, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-  } else if (d.k == 4) {
-    if (rule) lane_search<4, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-    else lane_search<4, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-  } else {
-    if (rule) lane_search<2, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-    else lane_search<2, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-  }
+  if (d.n <= LANE_SMEM_N)
+    lane_dispatch_w<uint32_t>(d, rule, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+  else
+    lane_dispatch_w<unsigned long long>(d, rule, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
 }
 
 // The instance's result once its last subtree is done (one thread): the
