@@ -551,12 +551,16 @@ int oracle_cliques(int n, int k, int ne, const int *eu, const int *ev, int max_q
  *     plus every subtree's; the status is BUDGET if some subtree stopped on
  *     its budget.  When none did, every subtree was searched to the end
  *     and the answer is the first minimum-cost leaf of the whole tree, as
- *     an exhaustive search gives.
+ *     an exhaustive search gives;
+ *   - an instance of more than OR_SPLIT_MAX_N segments is not split: every
+ *     subtree search would first descend through all its levels, so it is
+ *     searched once with the whole budget B.
  * Each search depends on nothing but its own subtree and (c1, s1), so the
  * result does not depend on the order the searches run in. */
 #ifndef OR_SPLIT_TARGET
 #define OR_SPLIT_TARGET 64
 #endif
+#define OR_SPLIT_MAX_N 4096
 
 static void split_cut(int n, int k, int *D_out, int64_t *S_out) {
   int D = 0;
@@ -568,6 +572,11 @@ static void split_cut(int n, int k, int *D_out, int64_t *S_out) {
 
 static int dlx_split_search(dlx_t *d, int64_t budget) {
   const int n = d->n, k = d->k;
+  if (n > OR_SPLIT_MAX_N) {
+    d->budget = budget;
+    dlx_search(d, 0);
+    return d->budget_hit ? OR_BUDGET : OR_OK;
+  }
   int D;
   int64_t S;
   split_cut(n, k, &D, &S);

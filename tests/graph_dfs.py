@@ -242,6 +242,9 @@ def _search_with_prefix(n, k, conf, stitch, cc, cs, budget, rule, prefix, init_b
     return st["best"], st["bestx"], st["nodes"], st["hit"], st["found"], st["places"]
 
 
+SPLIT_MAX_N = 4096   # larger instances are searched once with the whole budget
+
+
 def split_cut(n, k, target=64):
     """Cut depth D (first depth with k^D >= target, at most n) and S = k^D."""
     D, S = 0, 1
@@ -260,8 +263,14 @@ def split_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0, target=64):
     row places of its leaf's first D levels) seeds one search per subtree s
     below the cut, each with the initial bound c1 + 1 if s < s1 else c1;
     the answer is the smallest (cost, subtree) among (c1, s1) and the
-    subtrees' incumbents.  Returns (cost, x, nodes, budget_hit).
+    subtrees' incumbents.  An instance of more than SPLIT_MAX_N segments is
+    searched once with the whole budget.  Returns (cost, x, nodes,
+    budget_hit).
     """
+    if n > SPLIT_MAX_N:
+        # not split: one search with the whole budget
+        c, x, m, h = bounded_search(n, k, conf, stitch, cc, cs, budget=budget, rule=rule)
+        return c, x, m, h
     D, S = split_cut(n, k, target)
     b = (budget + S) // (S + 1) if budget > 0 else 0
     c1, x1, nodes, hit, _, places = _search_with_prefix(n, k, conf, stitch, cc, cs, b, rule, (),

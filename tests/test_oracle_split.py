@@ -14,7 +14,9 @@ against things other than the oracle's dancing links:
   tests/graph_dfs.py), and its cost is the brute-force minimum of Eq. 1;
 * with no budget it is the exhaustive search, node for node;
 * on a layout, the flow (simplify, split, search, recover) gives each
-  instance the mode's own answer for that instance.
+  instance the mode's own answer for that instance;
+* an instance above the size limit is searched once with the whole budget
+  (the plain search's answer and node count).
 """
 import numpy as np
 import pytest
@@ -128,3 +130,22 @@ def test_layout_instances_take_the_modes_answer(k, deg):
     conf_n = sum(1 for a, b in conf if r.mask[a] == r.mask[b])
     st_n = sum(1 for a, b in st if r.mask[a] != r.mask[b])
     assert r.cost == 10 * conf_n + st_n
+
+
+@pytest.mark.parametrize("n", [4096, 4097, 6000])
+def test_instances_above_the_limit_are_not_split(n):
+    # a ring at k = 2 with triangle chords (each forces a conflict), big
+    # enough that the budget stops the search
+    conf = [(i, (i + 1) % n) for i in range(n)] + [(i, i + 2) for i in range(0, n - 2, 97)]
+    B = 3 * n
+    split = oracle.solve_instance(n, 2, conf, budget=B, split=True)
+    plain = oracle.solve_instance(n, 2, conf, budget=B)
+    if n > 4096:
+        assert (split.cost, split.nodes, split.x.tolist()) == (plain.cost, plain.nodes,
+                                                               plain.x.tolist())
+    else:
+        # at the limit the instance is still split: the first search has a
+        # share of the budget only
+        D, S = split_cut(n, 2)
+        first = oracle.solve_instance(n, 2, conf, budget=(B + S) // (S + 1))
+        assert first.status == oracle.BUDGET and split.nodes > first.nodes
