@@ -68,9 +68,10 @@ def parse_args():
     ap.add_argument("--parallel-exact", action="store_true",
                     help="exact search (node budget 0) with the warps of a CTA splitting each "
                          "instance of 16+ segments (for single-instance workloads)")
-    ap.add_argument("--split-budget", action="store_true",
-                    help="budgeted split search: each instance's node budget spent by a first "
-                         "search and then by independent subtree searches on every warp")
+    ap.add_argument("--sequential-budget", action="store_true",
+                    help="spend each instance's node budget in one depth-first search instead "
+                         "of the budgeted split search (a first search, then independent "
+                         "subtree searches on every lane and warp)")
     ap.add_argument("--biconnected", action="store_true",
                     help="search the biconnected blocks of each sub-graph and join them at cut "
                          "segments")
@@ -100,7 +101,8 @@ def parse_args():
                          "polygons / plain-scale (same density and degree)")
     args = ap.parse_args()
     if args.parallel_exact:
-        args.budget = 0      # the split search is exact only
+        args.budget = 0      # the split exact search is exact only
+    args.split_budget = not (args.sequential_budget or args.parallel_exact or args.clique_bound)
     return args
 
 
@@ -198,7 +200,8 @@ def run_serving(args, mpld, synth):
                                       max_in_flight=256, streams=16)
         srv = mpld.mpld_server_create(cfg, mpld.make_params(
             node_budget=args.serve_budget,
-            flags=mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0))
+            flags=(mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0) |
+            (mpld.MPLD_SPLIT_BUDGET if args.split_budget else 0)))
         arrival_of, lat, segs = {}, [], 0
         t0 = time.perf_counter()
         i = 0
@@ -337,6 +340,8 @@ def config_leg(name, budget, search_flags, label, mpld, oracle, torch, stream, f
         prob.close()
     med = statistics.median(ms) / 1000.0
     oflags = (oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE) if mode == "single" else 0
+    if search_flags & mpld.MPLD_SPLIT_BUDGET:
+        oflags |= oracle.SPLIT_BUDGET
     nthreads = 1 if mode == "single" else cores
     ref = oracle.decompose(layout, flags=oflags, budget=budget, nthreads=nthreads)
     split = bool(search_flags & mpld.MPLD_PARALLEL_EXACT)
@@ -430,6 +435,34 @@ def main():
         all_segments = float(layout.n_seg)
         searched = float(info.instance_segments)
     rc, mask, res = mpld.mpld_fetch(prob, s)
+    seq = None
+    if args.split_budget and not args.no_plain:
+        # the same budget spent by one depth-first search per instance, on the
+        # same matrices (L2 flushed before each run)
+        prm_seq = mpld.make_params(node_budget=args.budget, flags=rule_flag & ~mpld.MPLD_SPLIT_BUDGET)
+        if not args.no_tune:
+            mpld.mpld_autotune([prob], prm_seq, s)
+        mpld.mpld_search_batch_async([prob], prm_seq, s)
+        stream.synchronize()
+        seq_ms = []
+        for _ in range(3):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mpld.mpld_search_batch_async([prob], prm_seq, s)
+            e1.record(stream)
+            stream.synchronize()
+            seq_ms.append(e0.elapsed_time(e1))
+        _, _, sres = mpld.mpld_fetch(prob, s)
+        med = statistics.median(seq_ms) / 1000.0
+        seq = {"ms_per_step": 1000 * med, "value": info.instance_segments / med,
+               "nodes_per_s": sres.nodes / med, "cost": sres.cost, "nodes": sres.nodes,
+               "budget_instances": sres.n_budget_components,
+               "form": "the same node budget spent by one depth-first search per instance"}
+        # the split search's results again for what follows (e2e checks)
+        mpld.mpld_search_batch_async([prob], prm, s)
+        rc, mask, res = mpld.mpld_fetch(prob, s)
     # segments the timed kernel searched (simplification removed the rest on
     # the host before the search; they are recovered after it)
     value = searched * args.steps / total_s
@@ -465,6 +498,7 @@ def main():
                    "status": rc, "step_ms": step_ms,
                    "median_step_ms": statistics.median(step_ms) if step_ms else None},
         "gpu_launches": args.steps * (2 if args.split_budget else 1),
+        "sequential_budget": seq,
         "clocks": clk,
     }
 
@@ -532,55 +566,49 @@ def main():
                   "ms_per_step": 1000 * e2e_total / len(e2e_t),
                   "form": "one layout at a time: mpld_build_matrix then mpld_solve_batch"}
 
-        if args.split_budget:
-            # the server has no budgeted split search: end to end is measured
-            # one layout at a time through mpld_build_matrix / mpld_solve_batch
-            out["e2e"] = dict(serial, unit="segments/s", h2d_bytes_per_step=int(h2d),
-                              d2h_bytes_per_step=int(d2h), gpu_launches_per_step=2)
-        else:
-            # the same decompositions as a stream of K layouts through the
-            # server: host build, upload, search, copy-back and recovery of
-            # different layouts overlap (the form a user decomposing many
-            # layouts takes); every layout is still built, uploaded, searched,
-            # copied back and recovered inside the timed region
-            req_flags = flags & (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE |
-                                 mpld.MPLD_BICONNECTED | mpld.MPLD_CLIQUE_BOUND)
-            # the server's own launch shape (small CTAs, so that launches of
-            # different layouts share the SMs)
-            cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
-                                          max_in_flight=max(args.steps, args.warmup, 1), streams=8)
-            srv = mpld.mpld_server_create(cfg, prm)
+        # the same decompositions as a stream of K layouts through the
+        # server: host build, upload, search, copy-back and recovery of
+        # different layouts overlap (the form a user decomposing many
+        # layouts takes); every layout is still built, uploaded, searched,
+        # copied back and recovered inside the timed region
+        req_flags = flags & (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE |
+                             mpld.MPLD_BICONNECTED | mpld.MPLD_CLIQUE_BOUND)
+        # the server's own launch shape (small CTAs, so that launches of
+        # different layouts share the SMs)
+        cfg = mpld.mpld_server_config(arena_bytes=8 << 30, result_pool_bytes=1 << 30,
+                                      max_in_flight=max(args.steps, args.warmup, 1), streams=8)
+        srv = mpld.mpld_server_create(cfg, prm)
 
-            def stream_run(n):
-                t0 = time.perf_counter()
-                pending = {mpld.mpld_server_submit(srv, layout, flags=req_flags) for _ in range(n)}
-                got = []
-                while pending:
-                    done = mpld.mpld_server_poll(srv)
-                    for t in done:
-                        got.append(mpld.mpld_server_result(srv, t))
-                        pending.discard(t)
-                    if not done:
-                        time.sleep(0.0002)
-                return time.perf_counter() - t0, got
+        def stream_run(n):
+            t0 = time.perf_counter()
+            pending = {mpld.mpld_server_submit(srv, layout, flags=req_flags) for _ in range(n)}
+            got = []
+            while pending:
+                done = mpld.mpld_server_poll(srv)
+                for t in done:
+                    got.append(mpld.mpld_server_result(srv, t))
+                    pending.discard(t)
+                if not done:
+                    time.sleep(0.0002)
+            return time.perf_counter() - t0, got
 
-            stream_run(args.warmup)
-            if dist:
-                dist.barrier()
-            torch.cuda.synchronize()
-            t_stream, got = stream_run(args.steps)
-            srv.close()
-            for rc3, m3, r3 in got:
-                assert rc3 == rc and np.array_equal(m3, mask) and r3.cost == res.cost
-            if dist:
-                _, t_stream = shard.aggregate(dist, layout.n_seg, t_stream, "cuda")
-            out["e2e"] = {"value": all_segments * args.steps / t_stream, "unit": "segments/s",
-                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                          "ms_per_step": 1000 * t_stream / args.steps,
-                          "gpu_launches_per_step": 1,
-                          "form": f"{args.steps} layouts submitted together to the server API "
-                                  "(mpld_server_submit / poll / result)",
-                          "serial": serial}
+        stream_run(args.warmup)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_stream, got = stream_run(args.steps)
+        srv.close()
+        for rc3, m3, r3 in got:
+            assert rc3 == rc and np.array_equal(m3, mask) and r3.cost == res.cost
+        if dist:
+            _, t_stream = shard.aggregate(dist, layout.n_seg, t_stream, "cuda")
+        out["e2e"] = {"value": all_segments * args.steps / t_stream, "unit": "segments/s",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": 1000 * t_stream / args.steps,
+                      "gpu_launches_per_step": 2 if args.split_budget else 1,
+                      "form": f"{args.steps} layouts submitted together to the server API "
+                              "(mpld_server_submit / poll / result)",
+                      "serial": serial}
 
     if rank == 0 and not args.no_plain:
         # plain one-launch-per-instance path vs the batched one on a smaller
@@ -635,10 +663,12 @@ def main():
     if rank == 0 and not args.no_configs:
         import oracle
         oracle.build()
+        sb = mpld.MPLD_SPLIT_BUDGET if args.split_budget else 0
+        mode = "budgeted split search" if args.split_budget else "one search per instance"
         legs = [("k3_n24_plain", 0, mpld.MPLD_PARALLEL_EXACT,
                  "exact, subtrees split over every warp of the grid"),
-                ("k3_n400_p025_plain", args.budget, 0, "one warp, node budget"),
-                ("k4_n100k_p03_batched", args.budget, 0, "batched, node budget")]
+                ("k3_n400_p025_plain", args.budget, sb, f"one instance, node budget, {mode}"),
+                ("k4_n100k_p03_batched", args.budget, sb, f"batched, node budget, {mode}")]
         out["configs"] = [config_leg(n, b, f, lab, mpld, oracle, torch, stream, flush, cores)
                           for n, b, f, lab in legs if n != args.workload]
     prob.close()

@@ -119,12 +119,14 @@ extern "C" {
                                     the smallest (cost, subtree) found, its masks, the nodes of
                                     all searches, and status MPLD_BUDGET if a subtree search
                                     stopped on its budget (else the answer is exact).  The result
-                                    does not depend on timing or launch shape.  node_budget 0:
-                                    the exhaustive search.  Read by the search calls; not with
-                                    MPLD_PARALLEL_EXACT, nor on problems built with
-                                    MPLD_CLIQUE_BOUND (MPLD_E_INVALID); not available to
-                                    mpld_search_instance_noalloc (MPLD_E_INVALID) or the server
-                                    (ignored). */
+                                    does not depend on timing or launch shape.  An instance of
+                                    more than 4096 segments is not split: one search with the
+                                    whole budget.  node_budget 0: the exhaustive search.  Read
+                                    by the search calls and by mpld_server_create; not with
+                                    MPLD_PARALLEL_EXACT, nor on problems built (or layouts
+                                    submitted) with MPLD_CLIQUE_BOUND (MPLD_E_INVALID); not
+                                    available to mpld_search_instance_noalloc
+                                    (MPLD_E_INVALID). */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
                                     the solve calls then return MPLD_E_STATE */
@@ -357,15 +359,18 @@ typedef struct {
 } mpld_server_stats;
 
 /* Create a server on the current device: allocates the device arena, the pinned result pool
- * and the streams, starts the worker threads.  search: node_budget and time_limit_ms for every
- * instance (NULL = defaults).  Errors: MPLD_E_INVALID, MPLD_E_OOM, MPLD_E_CUDA. */
+ * and the streams, starts the worker threads.  search: node_budget, time_limit_ms and the
+ * flags MPLD_COLUMN_BFS and MPLD_SPLIT_BUDGET for every layout (NULL = defaults; with
+ * MPLD_SPLIT_BUDGET each layout's device bytes include the split search's lists, contexts and
+ * up to 64 MiB of per-warp state).  Errors: MPLD_E_INVALID, MPLD_E_OOM, MPLD_E_CUDA. */
 int mpld_server_create(const mpld_server_config *cfg, const mpld_params *search,
                        mpld_server **out);
 
 /* Queue a layout (copied; `graph` may be reused at once).  flags as mpld_params.flags for
  * mpld_build_matrix (MPLD_NO_SIMPLIFY, MPLD_SINGLE_INSTANCE, MPLD_BICONNECTED,
- * MPLD_CLIQUE_BOUND; other bits are ignored).  Returns MPLD_OK and a ticket.  Input errors surface later as the ticket's result
- * code. */
+ * MPLD_CLIQUE_BOUND; other bits are ignored).  Returns MPLD_OK and a ticket, or
+ * MPLD_E_INVALID for MPLD_CLIQUE_BOUND on a server with MPLD_SPLIT_BUDGET.  Input errors
+ * surface later as the ticket's result code. */
 int mpld_server_submit(mpld_server *s, const mpld_graph *graph, uint32_t flags, int64_t *ticket);
 
 /* Non-blocking progress: admit, upload, launch, detect finished layouts.  Writes up to

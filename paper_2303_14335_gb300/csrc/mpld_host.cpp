@@ -444,10 +444,13 @@ void parallel_strided(int count, int lanes, F f) {
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, mpld_tune> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int>, mpld_tune> g_tune_cache;
 
 // Process-wide cache key of a problem set: k and a coarse size histogram.
-std::tuple<int, int, int, int> tune_key(mpld_problem *const *ps, int n) {
+// Tuned launch shapes are kept per (k, size histogram, search mode): the
+// budgeted split search's first launch is much shorter than a whole search.
+std::tuple<int, int, int, int, int> tune_key(mpld_problem *const *ps, int n,
+                                             const mpld_params *prm) {
   int kmax = 0;
   int64_t inst = 0;
   uint32_t fmax = 0;
@@ -458,7 +461,8 @@ std::tuple<int, int, int, int> tune_key(mpld_problem *const *ps, int n) {
     for (uint32_t f : ps[i]->footprint) { fmax = std::max(fmax, f); fsum += f; }
   }
   auto lg = [](int64_t x) { int b = 0; while (x > 1) { x >>= 1; ++b; } return b; };
-  return {kmax, lg(inst), lg(fmax), lg(inst ? fsum / inst : 0)};
+  const int mode = (prm && (prm->flags & MPLD_SPLIT_BUDGET)) ? 1 : 0;
+  return {kmax, lg(inst), lg(fmax), lg(inst ? fsum / inst : 0), mode};
 }
 
 }  // namespace
@@ -1005,7 +1009,7 @@ Shape pick_shape(mpld_problem *const *ps, int n, const mpld_params *prm) {
   int slot = prm && prm->slot_bytes > 0 ? prm->slot_bytes : 0;
   if (!nw || !slot) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune_cache.find(tune_key(ps, n));
+    auto it = g_tune_cache.find(tune_key(ps, n, prm));
     if (it != g_tune_cache.end()) {
       if (!nw) nw = it->second.warps_per_cta;
       if (!slot) slot = it->second.slot_bytes;
@@ -1174,38 +1178,34 @@ int launch_queue(mpld_problem *p, const QueuePlan &q, const mpld_params *prm, cu
   return mpld_internal_launch(&a, q.ctas, CTA_TEAM_WARPS, st);
 }
 
+}  // namespace
+
 // Budgeted split search (MPLD_SPLIT_BUDGET): the first phase is the batched
 // (or plain) launch with split = 1, which searches every instance with its
-// per-search budget and puts the ones that stop on it on the hard list; the
-// second launch (par = 4) searches their subtrees, one per warp at a time.
-// Device block: the two hard lists (their counts, then descriptor indices:
-// instances the per-lane search takes, and the rest), one 64-byte context per
-// descriptor, then each warp's state for instances beyond the register form.
-struct SplitPlan {
-  bool on = false;
-  int nw = 0, slot = 0, ctas = 0;   // second launch
-  int smax = 1;                     // item numbers per hard-list entry
-  int state_bytes = 0;              // per warp, general form (0: no such instance)
-  int cap = 0;                      // entries of each hard list (the launch's descriptors)
-  size_t o_hard = 0, o_ctx = 0, o_state = 0, bytes = 0;
-};
-SplitPlan split_plan_of(const InstDesc *desc, int n_inst, const mpld_params *prm) {
+// per-search budget and puts the ones that stop on it on a hard list; the
+// second launch (par = 4) searches their subtrees, a lane or a warp per
+// subtree.  Device block: the three hard lists (counts, then descriptor
+// indices), one 64-byte context per descriptor, then the general-state
+// region of each of the first gen_warps warps.
+mpld::SplitPlan mpld::split_plan(const InstDesc *desc, int n_inst, const mpld_params *prm,
+                                 size_t gen_cap_bytes) {
   SplitPlan q;
-  if (!split_of(prm) || n_inst < 1) return q;
+  if (!prm || !(prm->flags & MPLD_SPLIT_BUDGET) || n_inst < 1) return q;
   q.on = true;
   int reg_slot = 16;
   size_t gen = 0;
   for (int i = 0; i < n_inst; ++i) {
     const InstDesc &d = desc[i];
+    if (d.n > SPLIT_MAX_N) continue;   // never split
     int D;
     uint32_t S;
-    mpld::split_cut(d.n, d.k, D, S);
+    split_cut(d.n, d.k, D, S);
     q.smax = std::max(q.smax, (int)S);
-    if (mpld::lane_fits(d.n, d.k)) reg_slot = std::max(reg_slot, (int)mpld::LANE_STACK_BYTES);
-    if (mpld::reg_fits(d.n, d.k))
-      reg_slot = std::max(reg_slot, (int)mpld::align16(mpld::reg_layout(d.n, d.k, 0).bytes));
-    else
-      gen = std::max(gen, (size_t)d.state_bytes);
+    const int list = split_list_of(d.n, d.k);
+    if (list == 1) reg_slot = std::max(reg_slot, (int)LANE_STACK_BYTES);
+    if (list == 0)
+      reg_slot = std::max(reg_slot, (int)align16(reg_layout(d.n, d.k, 0).bytes));
+    if (list == 2) gen = std::max(gen, (size_t)d.state_bytes);
   }
   // as many warps per CTA as the slots allow (the launch bound is 16)
   q.nw = 1;
@@ -1215,13 +1215,67 @@ SplitPlan split_plan_of(const InstDesc *desc, int n_inst, const mpld_params *prm
   const int per_sm = std::max(1, mpld_internal_ctas_per_sm(q.nw, q.slot));
   q.ctas = per_sm * std::max(1, mpld_internal_num_sms());
   q.state_bytes = gen ? (int)((gen + 255) & ~(size_t)255) : 0;
-  q.o_hard = 0;
+  const int G = q.ctas * q.nw;
+  q.gen_warps = q.state_bytes
+      ? (int)std::max<size_t>(1, std::min<size_t>((size_t)G, gen_cap_bytes / (size_t)q.state_bytes))
+      : 0;
   q.cap = n_inst;
-  q.o_ctx = (4u * (size_t)(2 + 2 * n_inst) + 255) & ~(size_t)255;
+  q.o_hard = 0;
+  q.o_ctx = (4u * (size_t)(4 + 3 * n_inst) + 255) & ~(size_t)255;
   q.o_state = q.o_ctx + 64u * (size_t)n_inst;
-  q.bytes = q.o_state + (size_t)q.ctas * (size_t)q.nw * (size_t)q.state_bytes;
+  q.bytes = q.o_state + (size_t)q.gen_warps * (size_t)q.state_bytes;
   return q;
 }
+// First-phase fields of a launch over `buf` (the plan's block).
+void mpld::split_phase1_args(LaunchArgs &a, const SplitPlan &q, uint8_t *buf) {
+  a.split = q.on ? 1 : 0;
+  a.hard = q.on ? (int32_t *)(buf + q.o_hard) : nullptr;
+  a.hard_cap = q.cap;
+  a.par_buf = q.on ? buf + q.o_ctx : a.par_buf;
+}
+// Reset the hard lists before the first phase.
+int mpld::split_reset(const SplitPlan &q, uint8_t *buf, cudaStream_t st) {
+  return cudaMemsetAsync(buf + q.o_hard, 0, 16, st) == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
+}
+// The second launch, after the first on the same stream: its item counters
+// (queue[0..2]) are reset, then every warp of the grid takes subtrees.
+int mpld::split_phase2_launch(const LaunchArgs &a1, const InstDesc *desc, const SplitPlan &q,
+                              uint8_t *buf, uint32_t *queue, cudaStream_t st) {
+  if (cudaMemsetAsync(queue, 0, 16, st) != cudaSuccess) return MPLD_E_CUDA;
+  LaunchArgs a = a1;
+  a.desc = desc;   // the hard lists hold indices into the whole descriptor array
+  a.order = nullptr;
+  a.slot_bytes = q.slot;
+  a.queue = queue;
+  a.n_large = 0;
+  a.par = 4;
+  a.split = 0;
+  a.hard = (int32_t *)(buf + q.o_hard);
+  a.hard_cap = q.cap;
+  a.par_buf = buf + q.o_ctx;
+  a.split_scratch = q.state_bytes ? buf + q.o_state : nullptr;
+  a.split_gen_warps = q.gen_warps;
+  a.smax = q.smax;
+  a.split_state_bytes = q.state_bytes;
+  return mpld_internal_launch(&a, q.ctas, q.nw, st);
+}
+
+namespace {
+
+using mpld::SplitPlan;
+// general-state regions of a batched call: at most this many bytes
+constexpr size_t SPLIT_GEN_BYTES = (size_t)1 << 30;
+SplitPlan split_plan_of(const InstDesc *desc, int n_inst, const mpld_params *prm) {
+  return mpld::split_plan(desc, n_inst, prm, SPLIT_GEN_BYTES);
+}
+void split_phase1(mpld::LaunchArgs &a, const SplitPlan &q, uint8_t *buf) {
+  mpld::split_phase1_args(a, q, buf);
+}
+int launch_split_phase2(const mpld::LaunchArgs &a1, const InstDesc *desc, const SplitPlan &q,
+                        uint8_t *buf, uint32_t *queue, cudaStream_t st) {
+  return mpld::split_phase2_launch(a1, desc, q, buf, queue, st);
+}
+
 // Grow the problem's split-search block (outside any stream capture).
 int ensure_split_buf(mpld_problem *p, size_t bytes) {
   if (bytes <= p->split_bytes) return MPLD_OK;
@@ -1242,36 +1296,6 @@ int ensure_split_buf(mpld_problem *p, size_t bytes) {
   p->split_bytes = bytes;
   return MPLD_OK;
 }
-// First-phase fields of a launch over `buf` (the plan's block).
-void split_phase1(mpld::LaunchArgs &a, const SplitPlan &q, uint8_t *buf) {
-  a.split = q.on ? 1 : 0;
-  a.hard = q.on ? (int32_t *)(buf + q.o_hard) : nullptr;
-  a.hard_cap = q.cap;
-  a.par_buf = q.on ? buf + q.o_ctx : a.par_buf;
-}
-// The second launch, after the first on the same stream: its item counter
-// (queue[0]) is reset, then every warp of the grid takes subtrees.
-int launch_split_phase2(const mpld::LaunchArgs &a1, const InstDesc *desc, const SplitPlan &q,
-                        uint8_t *buf, uint32_t *queue, cudaStream_t st) {
-  int rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));
-  if (rc) return rc;
-  mpld::LaunchArgs a = a1;
-  a.desc = desc;   // the hard list holds indices into the whole descriptor array
-  a.order = nullptr;
-  a.slot_bytes = q.slot;
-  a.queue = queue;
-  a.n_large = 0;
-  a.par = 4;
-  a.split = 0;
-  a.hard = (int32_t *)(buf + q.o_hard);
-  a.hard_cap = q.cap;
-  a.par_buf = buf + q.o_ctx;
-  a.split_scratch = q.state_bytes ? buf + q.o_state : nullptr;
-  a.smax = q.smax;
-  a.split_state_bytes = q.state_bytes;
-  return mpld_internal_launch(&a, q.ctas, q.nw, st);
-}
-
 int launch_batch(const mpld::LaunchArgs &a, const Shape &sh, cudaStream_t st, uint32_t *queue,
                  int32_t *err) {
   int rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));   // both work counters
@@ -1330,7 +1354,7 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     if (rc) return rc;
     if (sp.on) {
       // the first phase over every instance, then the subtrees of the hard ones
-      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 8, st));
+      rc = mpld::split_reset(sp, p->d_split, st);
       rc |= launch_batch(a, sh, st, p->d_queue, p->d_err);
       if (rc == MPLD_OK) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
     } else if (gs.on) {
@@ -1560,7 +1584,7 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
       // this instance's first search; if it stops on its budget, its
       // subtrees in a second launch
       split_phase1(a, sp, p->d_split);
-      rc = cuda_ok(cudaMemsetAsync(p->d_split + sp.o_hard, 0, 8, st));
+      rc = mpld::split_reset(sp, p->d_split, st);
       if (rc == MPLD_OK) rc = mpld_internal_launch(&a, 1, large ? CTA_TEAM_WARPS : 1, st);
       if (rc == MPLD_OK) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
       continue;
@@ -1696,7 +1720,7 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
   } else if (!rc && sp.on) {
     // the first phase over every instance, then the subtrees of the hard ones
     split_phase1(a, sp, b + o_split);
-    rc = cuda_ok(cudaMemsetAsync(b + o_split + sp.o_hard, 0, 8, st));
+    rc = mpld::split_reset(sp, b + o_split, st);
     if (!rc) rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
     if (!rc) rc = launch_split_phase2(a, a.desc, sp, b + o_split, queue, st);
   } else if (!rc) {
@@ -1898,7 +1922,7 @@ extern "C" int mpld_autotune(mpld_problem *const *ps, int32_t n, const mpld_para
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[tune_key(ps, n)] = best;
+    g_tune_cache[tune_key(ps, n, prm)] = best;
   }
   if (best_out) *best_out = best;
   return MPLD_OK;

@@ -216,11 +216,13 @@ struct LaunchArgs {
   uint8_t *par_buf;        // par == 2: the split context in global memory (ParLayout);
                            // par == 3: one 64-byte context per queued instance;
                            // split / par == 4: one 64-byte context per descriptor index
-  int32_t *hard = nullptr; // split / par == 4: [0] entries for warps, [1] entries for lanes,
-                           // then hard_cap descriptor indices of each kind (instances that
+  int32_t *hard = nullptr; // split / par == 4: entry counts of the three hard lists (warps,
+                           // lanes, warps with general state) at [0..2], then hard_cap
+                           // descriptor indices of each list from [4] on (instances that
                            // stopped on their first-phase budget); contexts are per
                            // descriptor index
   int32_t hard_cap = 0;
+  int32_t split_gen_warps = 0;   // par == 4: warps with a general-state region (the first)
   uint8_t *split_scratch = nullptr;  // par == 4: per-warp global search state for instances
                                      // beyond the register form (split_state_bytes per warp)
   int32_t smax = 0;        // par == 4: item numbers per hard-list entry (>= its subtrees)
@@ -232,6 +234,13 @@ struct LaunchArgs {
 // into S = k^D subtrees; the first search and every subtree search get
 // b = ceil(B / (S + 1)) nodes of the instance's budget B.
 constexpr int SPLIT_TARGET = 64;
+// Instances of more than SPLIT_MAX_N segments are not split: one search with
+// the whole budget (every subtree search would first descend through all
+// their levels).
+constexpr int SPLIT_MAX_N = 4096;
+// Hard list of an instance: 1 = a lane per subtree, 0 = a warp per subtree
+// with the register form, 2 = a warp with a general-state region.
+MPLD_HD int split_list_of(int n, int k) { return lane_fits(n, k) ? 1 : reg_fits(n, k) ? 0 : 2; }
 MPLD_HD void split_cut(int n, int k, int &D, uint32_t &S) {
   D = 0;
   S = 1;

@@ -27,6 +27,27 @@ struct GraphKey {
   }
 };
 
+// Budgeted split search (MPLD_SPLIT_BUDGET): the device block and the second
+// launch of a batched call (mpld_host.cpp; used by the server too).
+struct SplitPlan {
+  bool on = false;
+  int nw = 0, slot = 0, ctas = 0;   // second launch
+  int smax = 1;                     // item numbers per hard-list entry
+  int state_bytes = 0;              // general-state region per warp (0: no such instance)
+  int gen_warps = 0;                // warps with such a region
+  int cap = 0;                      // entries of each hard list (the launch's descriptors)
+  size_t o_hard = 0, o_ctx = 0, o_state = 0, bytes = 0;
+};
+// Plan for the descriptors of one launch; the general-state regions take at
+// most gen_cap_bytes (fewer warps get one).  on = false unless prm asks for
+// the split search.
+SplitPlan split_plan(const InstDesc *desc, int n_inst, const mpld_params *prm,
+                     size_t gen_cap_bytes);
+void split_phase1_args(LaunchArgs &a, const SplitPlan &q, uint8_t *buf);
+int split_reset(const SplitPlan &q, uint8_t *buf, cudaStream_t st);
+int split_phase2_launch(const LaunchArgs &a1, const InstDesc *desc, const SplitPlan &q,
+                        uint8_t *buf, uint32_t *queue, cudaStream_t st);
+
 }  // namespace mpld
 
 struct mpld_problem {

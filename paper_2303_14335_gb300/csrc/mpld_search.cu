@@ -578,9 +578,9 @@ struct Search {
 // its incumbent (cost << 32 | subtree of the incumbent's leaf).  Lane 0 only.
 __device__ __forceinline__ void split_enlist(const LaunchArgs &a, const InstDesc &d, int32_t best,
                                              uint32_t sub) {
-  const int kind = lane_fits(d.n, d.k) ? 1 : 0;
+  const int kind = split_list_of(d.n, d.k);
   const int j = atomicAdd(a.hard + kind, 1);
-  a.hard[2 + kind * a.hard_cap + j] = d.idx;
+  a.hard[4 + kind * a.hard_cap + j] = d.idx;
   ParCtx *c = (ParCtx *)(a.par_buf + (size_t)d.idx * 64);
   c->key = ((unsigned long long)(uint32_t)best << 32) | sub;
   c->nodes = 0;
@@ -1470,7 +1470,8 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   int64_t nodes = 0, work = 0;
   SplitSpec sp;
   int64_t budget = a.budget;
-  if (a.split) {
+  const bool split = a.split && n <= SPLIT_MAX_N;   // larger: one search, the whole budget
+  if (split) {
     // budgeted split search, first phase: this search's share of the budget
     uint32_t S;
     split_cut(n, d.k, sp.cut, S);
@@ -1484,7 +1485,7 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
     d.res->status = st;
     d.res->sub = (int32_t)sp.sub_out;
     d.res->work = work;
-    if (a.split && st == MPLD_BUDGET) split_enlist(a, d, best, sp.sub_out);
+    if (split && st == MPLD_BUDGET) split_enlist(a, d, best, sp.sub_out);
   }
   team.sync();
 }
@@ -1960,22 +1961,36 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
   const int gw = (int)blockIdx.x * nw + warp;
   uint8_t *wstate = a.split_scratch ? a.split_scratch + (size_t)gw * (size_t)a.split_state_bytes
                                     : nullptr;
-  uint32_t HW = 0, HL = 0;
+  uint32_t HW = 0, HL = 0, HG = 0;
   if (lane == 0) {
     HW = (uint32_t)*(volatile int32_t *)a.hard;
     HL = (uint32_t)*(volatile int32_t *)(a.hard + 1);
+    HG = (uint32_t)*(volatile int32_t *)(a.hard + 2);
   }
   HW = __shfl_sync(FULL, HW, 0);
   HL = __shfl_sync(FULL, HL, 0);
-  const int32_t *list_w = a.hard + 2, *list_l = a.hard + 2 + a.hard_cap;
+  HG = __shfl_sync(FULL, HG, 0);
+  const int32_t *list_w = a.hard + 4, *list_l = a.hard + 4 + a.hard_cap;
+  const int32_t *list_g = a.hard + 4 + 2 * a.hard_cap;
+  // warps with a general-state region first take the subtrees of instances
+  // beyond the register form (counter queue[2]), then every warp those of
+  // the register form (queue[0])
+  const bool gen_warp = gw < a.split_gen_warps && wstate != nullptr;
+  bool gen_phase = gen_warp && HG > 0;
   int built = -1;   // instance whose adjacency the slot holds
   for (;;) {
     uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(a.queue, 1u);
+    if (lane == 0) t = atomicAdd(a.queue + (gen_phase ? 2 : 0), 1u);
     t = __shfl_sync(FULL, t, 0);
-    if ((uint64_t)t >= (uint64_t)HW * (uint64_t)a.smax) break;
+    if ((uint64_t)t >= (uint64_t)(gen_phase ? HG : HW) * (uint64_t)a.smax) {
+      if (gen_phase) {
+        gen_phase = false;
+        continue;
+      }
+      break;
+    }
     const uint32_t j = t / (uint32_t)a.smax, s = t % (uint32_t)a.smax;
-    const int di = __ldcg(list_w + j);
+    const int di = __ldcg((gen_phase ? list_g : list_w) + j);
     const InstDesc d = a.desc[di];
     int D;
     uint32_t S;

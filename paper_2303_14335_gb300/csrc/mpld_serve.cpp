@@ -89,11 +89,14 @@ enum class State { Building, Built, Admitted, Finishing, Done };
 // Byte layout of one admitted layout in the device arena and in the pinned
 // result pool (256-byte aligned sections).
 struct Sections {
-  uint64_t ro, state, desc, order, res, masks, ctrl, total;   // device
-  uint64_t h_res, h_masks, h_err, h_total;                    // pinned
+  uint64_t ro, state, desc, order, res, masks, ctrl, split, total;   // device
+  uint64_t h_res, h_masks, h_err, h_total;                           // pinned
 };
 
-Sections sections_of(const mpld_problem *p) {
+// general-state regions of the budgeted split search, per layout
+constexpr size_t SPLIT_GEN_BYTES = (size_t)64 << 20;
+
+Sections sections_of(const mpld_problem *p, const mpld::SplitPlan &sp) {
   const uint64_t C = (uint64_t)std::max(p->n_comp, 1);
   const uint64_t segs = (uint64_t)std::max<int64_t>(p->instance_segments, 1);
   Sections S;
@@ -104,7 +107,8 @@ Sections sections_of(const mpld_problem *p) {
   S.order = o; o += round_up(sizeof(int32_t) * C);
   S.res = o; o += round_up(sizeof(InstResult) * C);
   S.masks = o; o += round_up(segs);
-  S.ctrl = o; o += ALIGN;   // work counter at 0, status word at 16
+  S.ctrl = o; o += ALIGN;   // work counters at 0, status word at 16
+  S.split = o; o += sp.on ? round_up(sp.bytes) : 0;   // budgeted split search block
   S.total = o;
   o = 0;
   S.h_res = o; o += round_up(sizeof(InstResult) * C);
@@ -124,6 +128,7 @@ struct Req {
   int n_seg = 0;
   // admission
   Sections sec{};
+  mpld::SplitPlan split{};      // the budgeted split search's block and second launch
   uint64_t arena_off = 0, pool_off = 0;
   std::vector<InstDesc> desc;   // upload source, alive until the layout is finished
   cudaEvent_t done = nullptr;
@@ -147,6 +152,7 @@ struct mpld_server {
   mpld_server_config cfg{};
   int64_t budget = 0, tl_ns = 0;
   int rule = 0;
+  mpld_params search{};   // flags: the column rule and the budgeted split search
   int cta_min = 4096;   // instances this large get a whole CTA
   int nsm = 1, max_slot = 0;
   std::vector<cudaStream_t> streams;
@@ -294,7 +300,18 @@ int launch_request(mpld_server *s, Req &r) {
   a.par = 0;
   a.split = 0;
   a.par_buf = nullptr;
-  rc = mpld_internal_launch(&a, ctas, nw, st);
+  if (r.split.on) {
+    // budgeted split search: every instance with its share of the budget,
+    // then the subtrees of the ones that stop on it
+    uint8_t *sb = base + S.split;
+    mpld::split_phase1_args(a, r.split, sb);
+    rc = mpld::split_reset(r.split, sb, st);
+    if (!rc) rc = mpld_internal_launch(&a, ctas, nw, st);
+    if (!rc) rc = mpld::split_phase2_launch(a, d_desc, r.split, sb, d_queue, st);
+    s->st.kernel_launches++;
+  } else {
+    rc = mpld_internal_launch(&a, ctas, nw, st);
+  }
   if (rc) return rc;
   rc |= cuda_ok(cudaMemcpyAsync(hp + S.h_res, d_res, sizeof(InstResult) * (size_t)C,
                                 cudaMemcpyDeviceToHost, st));
@@ -337,6 +354,10 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
   s->budget = search ? std::max<int64_t>(search->node_budget, 0) : 0;
   s->tl_ns = ((search && search->time_limit_ms > 0) ? search->time_limit_ms : 60000) * 1000000ll;
   s->rule = (search && (search->flags & MPLD_COLUMN_BFS)) ? 1 : 0;
+  if (search) {
+    s->search = *search;
+    s->search.flags &= MPLD_COLUMN_BFS | MPLD_SPLIT_BUDGET;
+  }
   if (search && search->cta_segments != 0)
     s->cta_min = search->cta_segments > 0 ? search->cta_segments : INT32_MAX;
   s->nsm = std::max(1, mpld_internal_num_sms());
@@ -370,6 +391,8 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
 extern "C" int mpld_server_submit(mpld_server *s, const mpld_graph *g, uint32_t flags,
                                   int64_t *ticket) {
   if (!s || !g || !ticket) return MPLD_E_INVALID;
+  // the budgeted split search has no clique bound
+  if ((s->search.flags & MPLD_SPLIT_BUDGET) && (flags & MPLD_CLIQUE_BOUND)) return MPLD_E_INVALID;
   auto r = std::make_shared<Req>();
   const int n = std::max(g->n_seg, 0);
   try {
@@ -445,7 +468,8 @@ extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
       if (r->state != State::Built) break;
       if ((int)s->inflight.size() >= s->cfg.max_in_flight) break;
       mpld_problem *p = r->p;
-      r->sec = sections_of(p);
+      r->split = mpld::split_plan(p->h_desc.data(), p->n_comp, &s->search, SPLIT_GEN_BYTES);
+      r->sec = sections_of(p, r->split);
       if (r->sec.total > s->arena.size() || r->sec.h_total > s->pool.size()) {
         // can never fit: fail the ticket
         mpld_free(p);

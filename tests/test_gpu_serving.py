@@ -168,3 +168,27 @@ def test_cta_team_threshold_reaches_served_searches(torch_cuda):
         ref = oracle.decompose(L, budget=BUDGET, nthreads=NTHREADS)
         rc, mask, res = got[t]
         assert np.array_equal(mask, ref.mask) and res.nodes == ref.nodes and res.cost == ref.cost
+
+
+def test_split_budget_served(torch_cuda):
+    # a server with the budgeted split search: each layout's result equals
+    # mpld_solve_batch's with the same flag and the oracle's split mode, in a
+    # mix with a small arena (layouts wait for device bytes)
+    stream = torch_cuda.cuda.Stream().cuda_stream
+    Ls = requests(10, seed=91)
+    prm = mpld.make_params(node_budget=BUDGET, flags=mpld.MPLD_SPLIT_BUDGET)
+    cfg = mpld.mpld_server_config(arena_bytes=96 << 20)
+    with mpld.mpld_server_create(cfg, prm) as srv:
+        tickets = [mpld.mpld_server_submit(srv, L) for L in Ls]
+        got = drain(srv, tickets)
+        with pytest.raises(mpld.MpldError) as e:
+            mpld.mpld_server_submit(srv, Ls[0], flags=mpld.MPLD_CLIQUE_BOUND)
+        assert e.value.code == mpld.MPLD_E_INVALID
+    for t, L in zip(tickets, Ls):
+        rc, mask, res = got[t]
+        prob = mpld.mpld_build_matrix(L, None, stream)
+        rc2, masks2, res2 = mpld.mpld_solve_batch([prob], prm, stream)
+        prob.close()
+        ref = oracle.decompose(L, flags=oracle.SPLIT_BUDGET, budget=BUDGET, nthreads=NTHREADS)
+        assert rc == rc2 and np.array_equal(mask, masks2[0]) and np.array_equal(mask, ref.mask)
+        assert res.cost == res2[0].cost == ref.cost and res.nodes == res2[0].nodes == ref.nodes
