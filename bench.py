@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="k3_n200k_p02_batched")
     ap.add_argument("--budget", type=int, default=1 << 16)
+    ap.add_argument("--time-limit-ms", type=int, default=0,
+                    help="per-instance search time limit (0 = the library's 60 s)")
     ap.add_argument("--parallel-exact", action="store_true",
                     help="exact search (node budget 0) with the warps of a CTA splitting each "
                          "instance of 16+ segments (for single-instance workloads)")
@@ -396,7 +398,8 @@ def main():
         rule_flag |= mpld.MPLD_PARALLEL_EXACT
     if args.split_budget:
         rule_flag |= mpld.MPLD_SPLIT_BUDGET
-    prm = mpld.make_params(node_budget=args.budget, flags=rule_flag)
+    prm = mpld.make_params(node_budget=args.budget, flags=rule_flag,
+                           time_limit_ms=args.time_limit_ms)
     tune = None
     if not args.no_tune:
         tune = mpld.mpld_autotune([prob], prm, s)
@@ -463,6 +466,15 @@ def main():
         # the split search's results again for what follows (e2e checks)
         mpld.mpld_search_batch_async([prob], prm, s)
         rc, mask, res = mpld.mpld_fetch(prob, s)
+    inst_status = None
+    if args.parallel_exact:
+        # which instances the exact search finished, and the sizes of the ones
+        # it did not (time limit)
+        _, icost, istat, icomp = mpld.mpld_component_results(prob)
+        isize = np.bincount(icomp[icomp >= 0], minlength=len(istat))
+        late = np.flatnonzero(istat != mpld.MPLD_OK)
+        inst_status = {"finished": int((istat == mpld.MPLD_OK).sum()), "timed_out": int(len(late)),
+                       "timed_out_sizes": sorted(isize[late].tolist(), reverse=True)[:50]}
     # segments the timed kernel searched (simplification removed the rest on
     # the host before the search; they are recovered after it)
     value = searched * args.steps / total_s
@@ -480,6 +492,7 @@ def main():
                    "clique_bound": bool(flags & mpld.MPLD_CLIQUE_BOUND),
                    "parallel_exact": bool(args.parallel_exact),
                    "split_budget": bool(args.split_budget),
+                   "time_limit_ms": args.time_limit_ms or 60000,
                    "instances": info.n_components,
                    "instance_segments": info.instance_segments,
                    "max_instance": info.max_component,
@@ -496,8 +509,13 @@ def main():
         "search": {"nodes": res.nodes, "cost": res.cost, "conflicts": res.n_conflicts,
                    "stitches": res.n_stitches, "budget_instances": res.n_budget_components,
                    "status": rc, "step_ms": step_ms,
-                   "median_step_ms": statistics.median(step_ms) if step_ms else None},
-        "gpu_launches": args.steps * (2 if args.split_budget else 1),
+                   "median_step_ms": statistics.median(step_ms) if step_ms else None,
+                   "instances_exact": inst_status},
+        # launches per step: the split search's two; the exact split search's
+        # queue launch before the batched one when the layout has several
+        # instances, one grid launch for a single instance
+        "gpu_launches": args.steps * (2 if args.split_budget or
+                                      (args.parallel_exact and info.n_components > 1) else 1),
         "sequential_budget": seq,
         "clocks": clk,
     }
