@@ -98,6 +98,10 @@ def parse_args():
                     help="distinct pre-generated requests the Poisson streams cycle through")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the legs of the other workloads")
+    ap.add_argument("--shard", choices=["layouts", "instances"], default="layouts",
+                    help="several GPUs: every rank decomposes its own layout (weak scaling), or "
+                         "one layout's instances are shared over the ranks, longest processing "
+                         "time first, and their results gathered (strong scaling)")
     ap.add_argument("--plain-scale", type=int, default=20,
                     help="the plain one-launch-per-instance path runs on the same workload with "
                          "polygons / plain-scale (same density and degree)")
@@ -364,6 +368,134 @@ def config_leg(name, budget, search_flags, label, mpld, oracle, torch, stream, f
     }
 
 
+def run_shards(args, rank, world, local_rank):
+    """One layout over all ranks: every rank builds the same problem, searches
+    its longest-processing-time-first share of the instances (timed on the
+    device, max over ranks), the per-instance results are all-gathered and
+    every rank finishes (recovery and counts) from the merged results."""
+    import numpy as np
+    import torch
+
+    from paper_2303_14335_gb300 import mpld, synth
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    layout, mode = synth.workload(args.workload)      # the same layout on every rank
+    flags = (mpld.MPLD_NO_SIMPLIFY | mpld.MPLD_SINGLE_INSTANCE) if mode == "single" else 0
+    sflags = (mpld.MPLD_COLUMN_BFS if args.column_rule == "bfs" else 0) | \
+        (mpld.MPLD_SPLIT_BUDGET if args.split_budget else 0)
+    prm = mpld.make_params(node_budget=args.budget, flags=sflags, time_limit_ms=args.time_limit_ms)
+    prob = mpld.mpld_build_matrix(layout, mpld.make_params(flags=flags), s)
+    info = mpld.mpld_problem_info(prob)
+    owner = mpld.mpld_shard_instances(prob, world)
+    mine = np.flatnonzero(owner == rank).astype(np.int32)
+    sizes = mpld.mpld_instance_sizes(prob)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        mpld.mpld_search_subset_async(prob, mine, prm, s)
+        stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        mpld.mpld_search_subset_async(prob, mine, prm, s)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+
+    def gather_and_finish():
+        nd, co, stt, ms = mpld.mpld_fetch_instances(prob, s)
+        part = (mine.tolist(), nd[mine].tolist(), co[mine].tolist(), stt[mine].tolist(),
+                [ms[off[c]:off[c + 1]].tobytes() for c in mine])
+        parts = [part]
+        if dist:
+            parts = [None] * world
+            dist.all_gather_object(parts, part)
+        C = len(sizes)
+        nodes, cost = np.zeros(C, np.int64), np.zeros(C, np.int64)
+        status, masks = -np.ones(C, np.int32), np.zeros(int(off[-1]), np.int8)
+        for ids, nds, cos, sts, mss in parts:
+            for c, a, b, st_, m in zip(ids, nds, cos, sts, mss):
+                nodes[c], cost[c], status[c] = a, b, st_
+                masks[off[c]:off[c + 1]] = np.frombuffer(m, dtype=np.int8)
+        return mpld.mpld_finish_from(prob, nodes, cost, status, masks)
+
+    rc, mask, res = gather_and_finish()
+    # end to end: this rank's share searched, results gathered, finished
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mpld.mpld_search_subset_async(prob, mine, prm, s)
+        rc2, mask2, _ = gather_and_finish()
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+        assert np.array_equal(mask2, mask)
+    e2e_s = sum(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    matches = None
+    if rank == 0:
+        # the same layout searched whole on this GPU
+        rc1, masks1, res1 = mpld.mpld_solve_batch([prob], prm, s)
+        matches = bool(np.array_equal(masks1[0], mask) and res1[0].cost == res.cost and
+                       res1[0].nodes == res.nodes)
+    prob.close()
+    if rank == 0:
+        searched = float(info.instance_segments)
+        out = {
+            "metric": METRIC, "value": searched * args.steps / total_s, "unit": "segments/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "segments": layout.n_seg,
+                       "instance_segments": info.instance_segments, "k": layout.k,
+                       "node_budget": args.budget, "split_budget": bool(args.split_budget),
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"one layout's instances shared over {world} GPUs "
+                                      "(longest processing time first), results all-gathered"},
+            "nodes_per_s": res.nodes * args.steps / total_s,
+            "search": {"nodes": res.nodes, "cost": res.cost, "status": rc,
+                       "instances_rank0": int(len(mine)), "instances": int(len(sizes))},
+            "gpu_launches": args.steps * (2 if args.split_budget else 1),
+            "clocks": clk,
+            "e2e": {"value": layout.n_seg * len(e2e_t) / e2e_s, "unit": "segments/s",
+                    "h2d_bytes_per_step": 4 * int(len(mine)),
+                    "d2h_bytes_per_step": 32 * int(len(sizes)) + int(info.instance_segments) + 4,
+                    "ms_per_step": 1000 * e2e_s / len(e2e_t),
+                    "form": "share searched, per-instance results copied back, all-gathered, "
+                            "recovery and counts on every rank"},
+            "matches_one_gpu": matches,
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -371,6 +503,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.shard == "instances":
+        run_shards(args, rank, world, local_rank)
         return
 
     import numpy as np

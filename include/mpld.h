@@ -315,6 +315,45 @@ int mpld_autotune(mpld_problem *const *ps, int32_t n, const mpld_params *params,
                   mpld_tune *best);
 
 /*
+ * One layout over several GPUs (one process per GPU).  The layout's search
+ * instances are independent (Sec. 1, task parallelism over sub-graphs), so
+ * every rank builds the same problem, searches its share of the instances,
+ * and the ranks' per-instance results are gathered (by the caller, e.g. with
+ * an all-gather) before the recovery of the removed segments and the counts.
+ *
+ * mpld_shard_instances: the share of each instance, longest processing time
+ *   first: instances by decreasing estimated work (segments + adjacency
+ *   entries, ties to the lower index), each to the rank with the least work
+ *   so far (ties to the lower rank).  owner_out: n_components entries in
+ *   [0, world).  Deterministic: every rank computes the same shares.
+ * mpld_instance_sizes: segments of each instance (n_components entries); the
+ *   masks of instance c start at the sum of the sizes of the instances
+ *   before it in the arrays below.
+ * mpld_search_subset_async: the batched search (mpld_search_batch_async's
+ *   kernel and launch shape) of the listed distinct instances only; the
+ *   others are not searched.  MPLD_PARALLEL_EXACT is refused (MPLD_E_INVALID).
+ * mpld_fetch_instances: the last search's per-instance results, copied back
+ *   (synchronises `stream`): nodes, cost, status (-1 for an instance that
+ *   was not searched) and the masks of every instance (instance_segments
+ *   bytes, instance after instance, each in ascending segment id); any
+ *   pointer may be NULL.  MPLD_E_STATE before a search.
+ * mpld_finish_from: scatter per-instance results given by the caller (the
+ *   arrays of mpld_fetch_instances, merged over the ranks), recover the
+ *   removed segments and count, as mpld_fetch does; every status must be
+ *   MPLD_OK, MPLD_BUDGET or MPLD_TIMEOUT (else MPLD_E_STATE).  Works on
+ *   MPLD_HOST_ONLY handles.
+ */
+int mpld_shard_instances(const mpld_problem *p, int32_t world, int32_t *owner_out);
+int mpld_instance_sizes(const mpld_problem *p, int32_t *sizes);
+int mpld_search_subset_async(mpld_problem *p, const mpld_params *params, const int32_t *inst,
+                             int32_t n, void *stream);
+int mpld_fetch_instances(mpld_problem *p, int64_t *nodes, int64_t *cost, int32_t *status,
+                         int8_t *inst_masks, void *stream);
+int mpld_finish_from(mpld_problem *p, const int64_t *nodes, const int64_t *cost,
+                     const int32_t *status, const int8_t *inst_masks, int8_t *mask_out,
+                     mpld_result *result);
+
+/*
  * Serving: continuous batching of whole layouts on one GPU.
  *
  * The paper runs the sub-graphs of one layout in parallel (Sec. 1, "task

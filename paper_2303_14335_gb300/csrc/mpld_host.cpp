@@ -1754,6 +1754,150 @@ extern "C" int mpld_fetch(mpld_problem *p, int8_t *mask_out, mpld_result *res, v
   return finish(p, mask_out, res);
 }
 
+// ================================================================= shards
+
+// One layout over several GPUs: its instances are independent (Sec. 1, task
+// parallelism), so each rank searches a share of them and the ranks'
+// per-instance results are gathered before the recovery.  Shares are longest
+// processing time first: instances by decreasing estimated work (segments +
+// adjacency entries; ties to the lower index), each to the rank with the
+// least work so far (ties to the lower rank).
+extern "C" int mpld_shard_instances(const mpld_problem *p, int32_t world, int32_t *owner_out) {
+  if (!p || world < 1 || (!owner_out && p->n_comp > 0)) return MPLD_E_INVALID;
+  const int C = p->n_comp;
+  std::vector<int64_t> w((size_t)C);
+  for (int c = 0; c < C; ++c) w[c] = (int64_t)p->h_desc[c].n + p->h_desc[c].ne2 + p->h_desc[c].ns2;
+  std::vector<int32_t> ord((size_t)C);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return w[x] > w[y]; });
+  std::vector<int64_t> load((size_t)world, 0);
+  for (int c : ord) {
+    int r = 0;
+    for (int q = 1; q < world; ++q)
+      if (load[q] < load[r]) r = q;
+    owner_out[c] = r;
+    load[r] += w[c];
+  }
+  return MPLD_OK;
+}
+
+extern "C" int mpld_instance_sizes(const mpld_problem *p, int32_t *sizes) {
+  if (!p || (!sizes && p->n_comp > 0)) return MPLD_E_INVALID;
+  for (int c = 0; c < p->n_comp; ++c) sizes[c] = p->comp_ptr[c + 1] - p->comp_ptr[c];
+  return MPLD_OK;
+}
+
+// The batched search of the listed instances only, in one launch (two with
+// the budgeted split search), largest first; the others are not searched.
+extern "C" int mpld_search_subset_async(mpld_problem *p, const mpld_params *prm,
+                                        const int32_t *inst, int32_t n, void *stream) {
+  if (!p || n < 0 || (n > 0 && !inst) || !params_ok(prm) || par_of(prm)) return MPLD_E_INVALID;
+  if (!p->d_base) return MPLD_E_STATE;
+  if (split_of(prm) && !split_ok(p)) return MPLD_E_INVALID;
+  std::vector<int32_t> order(inst, inst + n);
+  std::vector<uint8_t> seen((size_t)p->n_comp, 0);
+  for (int32_t c : order) {
+    if (c < 0 || c >= p->n_comp || seen[c]) return MPLD_E_INVALID;
+    seen[c] = 1;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return p->h_desc[x].n > p->h_desc[y].n || (p->h_desc[x].n == p->h_desc[y].n && x < y);
+  });
+  const SplitPlan sp = split_plan_of(p->h_desc.data(), p->n_comp, prm);
+  if (sp.on && ensure_split_buf(p, sp.bytes) != MPLD_OK) return MPLD_E_OOM;
+  cudaStream_t st = (cudaStream_t)stream;
+  mpld_problem *ps[1] = {p};
+  const int n_large = count_large(n, [&](int i) { return p->h_desc[order[i]].n; }, cta_min_of(prm));
+  const Shape sh = with_team(pick_shape(ps, 1, prm), n_large);
+  void *buf = nullptr;
+  if (cudaMallocAsync(&buf, 4u * (size_t)std::max(n, 1), st) != cudaSuccess) {
+    cudaGetLastError();
+    return MPLD_E_OOM;
+  }
+  int rc = cuda_ok(cudaMemsetAsync(p->d_res, 0xFF, sizeof(InstResult) * (size_t)std::max(p->n_comp, 1), st));
+  if (n) rc |= cuda_ok(cudaMemcpyAsync(buf, order.data(), 4u * (size_t)n, cudaMemcpyHostToDevice, st));
+  // the source is a vector local to this call
+  rc |= cuda_ok(cudaStreamSynchronize(st));
+  mpld::LaunchArgs a;
+  a.desc = p->d_desc;
+  a.order = (const int32_t *)buf;
+  a.n_inst = n;
+  a.slot_bytes = sh.slot;
+  a.queue = p->d_queue;
+  a.err = p->d_err;
+  a.budget = budget_of(prm);
+  a.time_limit_ns = time_limit_ns(prm);
+  a.rule = rule_of(prm);
+  a.n_large = n_large;
+  a.par = 0;
+  a.split = 0;
+  a.par_buf = nullptr;
+  if (!rc && sp.on) {
+    split_phase1(a, sp, p->d_split);
+    rc = mpld::split_reset(sp, p->d_split, st);
+    if (!rc) rc = launch_batch(a, sh, st, p->d_queue, p->d_err);
+    if (!rc) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
+  } else if (!rc) {
+    rc = launch_batch(a, sh, st, p->d_queue, p->d_err);
+  }
+  rc |= cuda_ok(cudaFreeAsync(buf, st));
+  p->searched = rc == MPLD_OK;
+  p->results_copied = false;
+  return rc ? MPLD_E_CUDA : MPLD_OK;
+}
+
+// Per-instance results of the last search, copied back: nodes, cost and
+// status per instance (status -1: not searched), and the instances' masks,
+// instance after instance, each in ascending segment id.
+extern "C" int mpld_fetch_instances(mpld_problem *p, int64_t *nodes, int64_t *cost,
+                                    int32_t *status, int8_t *inst_masks, void *stream) {
+  if (!p) return MPLD_E_INVALID;
+  if (!p->searched) return MPLD_E_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = MPLD_OK;
+  if (!p->results_copied) {
+    if (p->n_comp)
+      rc |= cuda_ok(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(InstResult) * (size_t)p->n_comp,
+                                    cudaMemcpyDeviceToHost, st));
+    if (p->instance_segments)
+      rc |= cuda_ok(cudaMemcpyAsync(p->h_masks, p->d_masks, (size_t)p->instance_segments,
+                                    cudaMemcpyDeviceToHost, st));
+    rc |= cuda_ok(cudaMemcpyAsync(p->h_err, p->d_err, 4, cudaMemcpyDeviceToHost, st));
+  }
+  rc |= cuda_ok(cudaStreamSynchronize(st));
+  if (rc) return MPLD_E_CUDA;
+  if (*p->h_err) return *p->h_err < 0 ? *p->h_err : MPLD_E_STATE;
+  p->results_copied = true;
+  for (int c = 0; c < p->n_comp; ++c) {
+    if (nodes) nodes[c] = p->h_res[c].nodes;
+    if (cost) cost[c] = p->h_res[c].cost;
+    if (status) status[c] = p->h_res[c].status;
+  }
+  if (inst_masks && p->instance_segments) std::memcpy(inst_masks, p->h_masks, (size_t)p->instance_segments);
+  return MPLD_OK;
+}
+
+// Scatter per-instance results given by the caller (for instance gathered
+// from the ranks that searched them), recover the removed segments and count
+// (as mpld_fetch does after a search on this handle).  Works on host-only
+// handles too.
+extern "C" int mpld_finish_from(mpld_problem *p, const int64_t *nodes, const int64_t *cost,
+                                const int32_t *status, const int8_t *inst_masks, int8_t *mask_out,
+                                mpld_result *res) {
+  if (!p || (p->n_comp > 0 && (!nodes || !cost || !status)) ||
+      (p->instance_segments > 0 && !inst_masks))
+    return MPLD_E_INVALID;
+  std::vector<InstResult> r((size_t)std::max(p->n_comp, 1));
+  for (int c = 0; c < p->n_comp; ++c) {
+    r[c].cost = cost[c];
+    r[c].nodes = nodes[c];
+    r[c].status = status[c];
+    r[c].sub = 0;
+    r[c].work = 0;
+  }
+  return mpld_internal_finish(p, r.data(), inst_masks, 0, mask_out, res);
+}
+
 extern "C" int mpld_solve(mpld_problem *p, const mpld_params *prm, int8_t *mask_out,
                           mpld_result *res, void *stream) {
   const int rc = mpld_search_plain_async(p, prm, stream);

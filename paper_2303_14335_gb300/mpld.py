@@ -105,6 +105,11 @@ _SIGS = {
     "mpld_search_batch_async": ([ctypes.POINTER(_P), _i32, ctypes.POINTER(mpld_params), _P], _i32),
     "mpld_fetch": ([_P, _P, ctypes.POINTER(mpld_result), _P], _i32),
     "mpld_search_plain_async": ([_P, ctypes.POINTER(mpld_params), _P], _i32),
+    "mpld_shard_instances": ([_P, _i32, _P], _i32),
+    "mpld_instance_sizes": ([_P, _P], _i32),
+    "mpld_search_subset_async": ([_P, ctypes.POINTER(mpld_params), _P, _i32, _P], _i32),
+    "mpld_fetch_instances": ([_P, _P, _P, _P, _P, _P], _i32),
+    "mpld_finish_from": ([_P, _P, _P, _P, _P, _P, ctypes.POINTER(mpld_result)], _i32),
     "mpld_free": ([_P], None),
     "mpld_status_string": ([_i32], ctypes.c_char_p),
     "mpld_problem_info": ([_P, ctypes.POINTER(mpld_info)], _i32),
@@ -286,6 +291,55 @@ def mpld_component_results(p: "Problem", results: bool = True):
     _check(library().mpld_component_results(p.handle, _ptr(nodes), _ptr(cost), _ptr(status),
                                             _ptr(comp_of)), "mpld_component_results")
     return nodes[:C], cost[:C], status[:C], comp_of[:p.n_seg]
+
+
+def mpld_shard_instances(p: "Problem", world: int) -> np.ndarray:
+    """Rank of every search instance (longest processing time first)."""
+    C = mpld_problem_info(p).n_components
+    owner = np.zeros(max(C, 1), dtype=np.int32)
+    _check(library().mpld_shard_instances(p.handle, world, _ptr(owner)), "mpld_shard_instances")
+    return owner[:C]
+
+
+def mpld_instance_sizes(p: "Problem") -> np.ndarray:
+    C = mpld_problem_info(p).n_components
+    sizes = np.zeros(max(C, 1), dtype=np.int32)
+    _check(library().mpld_instance_sizes(p.handle, _ptr(sizes)), "mpld_instance_sizes")
+    return sizes[:C]
+
+
+def mpld_search_subset_async(p: "Problem", instances, params: mpld_params | None = None,
+                             stream: int = 0) -> int:
+    inst = _arr(instances)
+    prm = params or make_params()
+    return _check(library().mpld_search_subset_async(p.handle, ctypes.byref(prm), _ptr(inst),
+                                                     len(inst), _P(stream)),
+                  "mpld_search_subset_async")
+
+
+def mpld_fetch_instances(p: "Problem", stream: int = 0):
+    """(nodes, cost, status, instance masks) of the last search, per instance."""
+    info = mpld_problem_info(p)
+    C = info.n_components
+    nodes = np.zeros(max(C, 1), dtype=np.int64)
+    cost = np.zeros(max(C, 1), dtype=np.int64)
+    status = np.zeros(max(C, 1), dtype=np.int32)
+    masks = np.zeros(max(info.instance_segments, 1), dtype=np.int8)
+    _check(library().mpld_fetch_instances(p.handle, _ptr(nodes), _ptr(cost), _ptr(status),
+                                          _ptr(masks), _P(stream)), "mpld_fetch_instances")
+    return nodes[:C], cost[:C], status[:C], masks[:info.instance_segments]
+
+
+def mpld_finish_from(p: "Problem", nodes, cost, status, inst_masks):
+    """Recovery and counts from per-instance results (e.g. gathered from several ranks)."""
+    nodes, cost = _arr(nodes, np.int64), _arr(cost, np.int64)
+    status, inst_masks = _arr(status, np.int32), _arr(inst_masks, np.int8)
+    mask = np.empty(max(p.n_seg, 1), dtype=np.int8)
+    res = mpld_result()
+    rc = _check(library().mpld_finish_from(p.handle, _ptr(nodes), _ptr(cost), _ptr(status),
+                                           _ptr(inst_masks), _ptr(mask), ctypes.byref(res)),
+                "mpld_finish_from")
+    return rc, mask[:p.n_seg], res
 
 
 def mpld_export_matrix(p: "Problem", comp: int) -> np.ndarray:
