@@ -1202,7 +1202,6 @@ mpld::SplitPlan mpld::split_plan(const InstDesc *desc, int n_inst, const mpld_pa
     split_cut(d.n, d.k, D, S);
     q.smax = std::max(q.smax, (int)S);
     const int list = split_list_of(d.n, d.k);
-    if (list == 1) reg_slot = std::max(reg_slot, (int)LANE_STACK_BYTES);
     if (list == 0)
       reg_slot = std::max(reg_slot, (int)align16(reg_layout(d.n, d.k, 0).bytes));
     if (list == 2) gen = std::max(gen, (size_t)d.state_bytes);
@@ -1257,6 +1256,9 @@ int mpld::split_phase2_launch(const LaunchArgs &a1, const InstDesc *desc, const 
   a.split_gen_warps = q.gen_warps;
   a.smax = q.smax;
   a.split_state_bytes = q.state_bytes;
+  // the lanes' subtrees in a kernel of their own, then the warps'
+  const int rc = mpld_internal_launch_lanes(&a, st);
+  if (rc) return rc;
   return mpld_internal_launch(&a, q.ctas, q.nw, st);
 }
 

@@ -61,11 +61,7 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
 // lanes (a subtree per lane, the whole state in registers as one bit per
 // segment); larger ones, or k > 4, to whole warps.
 MPLD_HD bool lane_fits(int n, int k) { return n <= LANE_MAX_N && k <= 4; }
-// Per-warp shared memory of the per-lane search of instances up to 32
-// segments: three 32-bit words per (level, lane).  (Larger ones keep their
-// levels in each thread's local memory.)
-constexpr int LANE_SMEM_N = 32;
-constexpr uint32_t LANE_STACK_BYTES = 3u * 4u * 32u * (uint32_t)LANE_SMEM_N;
+
 
 // Mutable search state of one instance (shared memory, or the instance's
 // global scratch region when it does not fit the warp's slot).  The DFS
@@ -292,3 +288,5 @@ extern "C" int mpld_internal_launch(const mpld::LaunchArgs *a, int ctas, int war
 extern "C" int mpld_internal_max_slot_bytes(int warps_per_cta);
 extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes);
 extern "C" int mpld_internal_num_sms(void);
+// The budgeted split search's per-lane subtree searches (the lanes' hard list).
+extern "C" int mpld_internal_launch_lanes(const mpld::LaunchArgs *a, void *stream);

@@ -42,6 +42,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "mpld_internal.h"
@@ -1718,27 +1719,20 @@ __device__ __forceinline__ void row_count_classes(const W (&act)[K], W (&cls)[K 
   }
 }
 
-// The level records: shared memory for 32-bit words, local memory for 64.
-template <typename W> struct LaneStack;
-template <> struct LaneStack<uint32_t> {
-  uint32_t *p;   // this lane's column of the warp's [3][LANE_SMEM_N][32] words
-  __device__ __forceinline__ uint32_t &h(int l) { return p[l * 32]; }
-  __device__ __forceinline__ uint32_t &g(int l) { return p[32 * LANE_SMEM_N + l * 32]; }
-  __device__ __forceinline__ uint32_t &s(int l) { return p[64 * LANE_SMEM_N + l * 32]; }
-};
-template <> struct LaneStack<unsigned long long> {
-  uint32_t hh[LANE_MAX_N], gg[LANE_MAX_N];
-  unsigned long long ss[LANE_MAX_N];
+// The level records, in the thread's local memory.
+template <typename W> struct LaneStack {
+  static constexpr int N = 8 * (int)sizeof(W);
+  uint32_t hh[N], gg[N];
+  W ss[N];
   __device__ __forceinline__ uint32_t &h(int l) { return hh[l]; }
   __device__ __forceinline__ uint32_t &g(int l) { return gg[l]; }
-  __device__ __forceinline__ unsigned long long &s(int l) { return ss[l]; }
+  __device__ __forceinline__ W &s(int l) { return ss[l]; }
 };
 
 template <typename W, int K, int RULE>
 __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, int cut,
                                          uint32_t prefix, int32_t thr0, int64_t budget, bool replay,
-                                         uint32_t *smem_stack, int64_t time_limit_ns, uint64_t t0,
-                                         LaneOut &o) {
+                                         int64_t time_limit_ns, uint64_t t0, LaneOut &o) {
   const int n = d.n;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
   const RoLayout R = ro_layout(n, d.ne2, d.ns2, 0);
@@ -1747,7 +1741,6 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
   const uint16_t *rank = (const uint16_t *)(ro + R.rank);
   const uint16_t *order = (const uint16_t *)(ro + R.order);
   LaneStack<W> st;
-  if constexpr (sizeof(W) == 4) st.p = smem_stack;
   const W one = 1;
   const W all = n >= (int)(8 * sizeof(W)) ? ~(W)0 : ((one << n) - one);
   W unc = all, uncr = all, act[K], asg[K];
@@ -1904,28 +1897,25 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
 template <typename W>
 __device__ __forceinline__ void lane_dispatch_w(const InstDesc &d, int rule, int cut,
                                                 uint32_t prefix, int32_t thr0, int64_t budget,
-                                                bool replay, uint32_t *stk, int64_t tl,
-                                                uint64_t t0, LaneOut &o) {
+                                                bool replay, int64_t tl, uint64_t t0, LaneOut &o) {
   const uint8_t *ro = d.ro;
   if (d.k == 3) {
-    if (rule) lane_search<W, 3, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-    else lane_search<W, 3, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    if (rule) lane_search<W, 3, 1>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
+    else lane_search<W, 3, 0>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
   } else if (d.k == 4) {
-    if (rule) lane_search<W, 4, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-    else lane_search<W, 4, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    if (rule) lane_search<W, 4, 1>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
+    else lane_search<W, 4, 0>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
   } else {
-    if (rule) lane_search<W, 2, 1>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-    else lane_search<W, 2, 0>(d, ro, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+    if (rule) lane_search<W, 2, 1>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
+    else lane_search<W, 2, 0>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
   }
 }
 
 __device__ __noinline__ void lane_dispatch(const InstDesc &d, int rule, int cut, uint32_t prefix,
-                                           int32_t thr0, int64_t budget, bool replay,
-                                           uint32_t *stk, int64_t tl, uint64_t t0, LaneOut &o) {
-  if (d.n <= LANE_SMEM_N)
-    lane_dispatch_w<uint32_t>(d, rule, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
-  else
-    lane_dispatch_w<unsigned long long>(d, rule, cut, prefix, thr0, budget, replay, stk, tl, t0, o);
+                                           int32_t thr0, int64_t budget, bool replay, int64_t tl,
+                                           uint64_t t0, LaneOut &o) {
+  if (d.n <= 32) lane_dispatch_w<uint32_t>(d, rule, cut, prefix, thr0, budget, replay, tl, t0, o);
+  else lane_dispatch_w<unsigned long long>(d, rule, cut, prefix, thr0, budget, replay, tl, t0, o);
 }
 
 // The instance's result once its last subtree is done (one thread): the
@@ -2040,55 +2030,6 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
     }
     if (lane == 0) split_write_result(d, ctx, key, ok);
     __syncwarp();
-  }
-  // the lanes' list: a subtree per lane
-  if (HL == 0 || a.slot_bytes < (int)LANE_STACK_BYTES) {
-    if (HL != 0 && lane == 0) atomicExch(a.err, MPLD_E_STATE);   // the host sizes the slot
-    return;
-  }
-  uint32_t *stk = (uint32_t *)mine + lane;
-  const uint64_t total = (uint64_t)HL * (uint64_t)a.smax;
-  for (;;) {
-    const uint32_t t = atomicAdd(a.queue + 1, 1u);
-    if ((uint64_t)t >= total) break;
-    const uint32_t j = t / (uint32_t)a.smax, s = t % (uint32_t)a.smax;
-    const int di = __ldcg(list_l + j);
-    const InstDesc d = a.desc[di];
-    int D;
-    uint32_t S;
-    split_cut(d.n, d.k, D, S);
-    if (s >= S) continue;
-    ParCtx *ctx = (ParCtx *)(a.par_buf + (size_t)di * 64);
-    const int64_t b = split_search_budget(a.budget, S);
-    const int64_t c1 = __ldcg(&d.res->cost);
-    const uint32_t s1 = (uint32_t)__ldcg(&d.res->sub);
-    const unsigned long long key1 = ((unsigned long long)(uint32_t)c1 << 32) | s1;
-    // the time limit runs from the instance's start
-    const uint64_t now = globaltimer();
-    const unsigned long long prev = atomicCAS(&ctx->t0, 0ull, (unsigned long long)now);
-    const uint64_t t0 = prev != 0ull ? (uint64_t)prev : now;
-    LaneOut o;
-    lane_dispatch(d, a.rule, D, s, (int32_t)c1 + (s < s1 ? 1 : 0), b, false, stk,
-                  a.time_limit_ns, t0, o);
-    if (o.found) atomicMin(&ctx->key, ((unsigned long long)(uint32_t)o.best << 32) | s);
-    atomicAdd(&ctx->nodes, (unsigned long long)o.nodes);
-    atomicAdd(&ctx->work, (unsigned long long)o.work);
-    if (o.timed_out) atomicExch(&ctx->timed_out, 1u);
-    if (o.hit) atomicExch(&ctx->pad, 1u);
-    __threadfence();
-    if (atomicAdd(&ctx->done, 1u) != S - 1u) continue;
-    // this lane completed the instance's last subtree
-    __threadfence();
-    unsigned long long key = *(volatile unsigned long long *)&ctx->key;
-    bool ok = true;
-    if (key != key1) {
-      LaneOut r;
-      lane_dispatch(d, a.rule, D, (uint32_t)(key & 0xFFFFFFFFull), (int32_t)(key >> 32) + 1, 0,
-                    true, stk, a.time_limit_ns, globaltimer(), r);
-      ok = r.found;
-      if (!ok) key = key1;
-    }
-    split_write_result(d, ctx, key, ok);
   }
 }
 
@@ -2340,6 +2281,85 @@ extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes) {
                                                     warps_per_cta * 32, smem) != cudaSuccess)
     return 0;
   return blocks;
+}
+
+// ---- budgeted split search: the lanes' subtrees ---------------------------
+//
+// A kernel of its own, so that its threads can have fewer registers than the
+// warp searches need and twice as many warps fit an SM: every thread takes
+// (hard-list entry, subtree) items of the lanes' list from counter queue[1]
+// and searches each subtree alone (lane_search); the thread that completes an
+// instance's last subtree replays the winning subtree and writes the result.
+
+namespace mpld {
+namespace {
+
+__global__ void __launch_bounds__(1024, 1) mpld_lane_kernel(const LaunchArgs a) {
+  uint32_t HL = (uint32_t)*(volatile int32_t *)(a.hard + 1);
+  if (HL == 0) return;
+  const int32_t *list_l = a.hard + 4 + a.hard_cap;
+  const uint64_t total = (uint64_t)HL * (uint64_t)a.smax;
+  for (;;) {
+    const uint32_t t = atomicAdd(a.queue + 1, 1u);
+    if ((uint64_t)t >= total) break;
+    const uint32_t j = t / (uint32_t)a.smax, s = t % (uint32_t)a.smax;
+    const int di = __ldcg(list_l + j);
+    const InstDesc d = a.desc[di];
+    int D;
+    uint32_t S;
+    split_cut(d.n, d.k, D, S);
+    if (s >= S) continue;
+    ParCtx *ctx = (ParCtx *)(a.par_buf + (size_t)di * 64);
+    const int64_t b = split_search_budget(a.budget, S);
+    const int64_t c1 = __ldcg(&d.res->cost);
+    const uint32_t s1 = (uint32_t)__ldcg(&d.res->sub);
+    const unsigned long long key1 = ((unsigned long long)(uint32_t)c1 << 32) | s1;
+    // the time limit runs from the instance's start
+    const uint64_t now = globaltimer();
+    const unsigned long long prev = atomicCAS(&ctx->t0, 0ull, (unsigned long long)now);
+    const uint64_t t0 = prev != 0ull ? (uint64_t)prev : now;
+    LaneOut o;
+    lane_dispatch(d, a.rule, D, s, (int32_t)c1 + (s < s1 ? 1 : 0), b, false, a.time_limit_ns,
+                  t0, o);
+    if (o.found) atomicMin(&ctx->key, ((unsigned long long)(uint32_t)o.best << 32) | s);
+    atomicAdd(&ctx->nodes, (unsigned long long)o.nodes);
+    atomicAdd(&ctx->work, (unsigned long long)o.work);
+    if (o.timed_out) atomicExch(&ctx->timed_out, 1u);
+    if (o.hit) atomicExch(&ctx->pad, 1u);
+    __threadfence();
+    if (atomicAdd(&ctx->done, 1u) != S - 1u) continue;
+    // this thread completed the instance's last subtree
+    __threadfence();
+    unsigned long long key = *(volatile unsigned long long *)&ctx->key;
+    bool ok = true;
+    if (key != key1) {
+      LaneOut r;
+      lane_dispatch(d, a.rule, D, (uint32_t)(key & 0xFFFFFFFFull), (int32_t)(key >> 32) + 1, 0,
+                    true, a.time_limit_ns, globaltimer(), r);
+      ok = r.found;
+      if (!ok) key = key1;
+    }
+    split_write_result(d, ctx, key, ok);
+  }
+}
+
+}  // namespace
+}  // namespace mpld
+
+extern "C" int mpld_internal_launch_lanes(const LaunchArgs *a, void *stream) {
+  static int blocks = 0;   // resident blocks of the lane kernel (one query per process)
+  if (blocks == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpld::mpld_lane_kernel, 1024, 0) !=
+            cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    blocks = per_sm * std::max(1, mpld_internal_num_sms());
+  }
+  mpld::mpld_lane_kernel<<<blocks, 1024, 0, (cudaStream_t)stream>>>(*a);
+  return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
 }
 
 // ---- search of one instance without allocating --------------------------
