@@ -35,6 +35,7 @@ COLUMN_BFS = 8      # the paper's column rule (single-row column, else BFS order
 BICONNECTED = 16    # search the biconnected blocks of each component, merge at cut segments
 CLIQUE_BOUND = 32   # second bound mode: dead columns plus untouched edge-disjoint (k+1)-cliques
 SPLIT_BUDGET = 64   # budgeted split search: the node budget spread over independent subtree searches
+DENSITY_BALANCE = 128  # per-component mask permutations and recovery that balance mask usage
 INF = (1 << 63) - 1
 
 

@@ -90,6 +90,7 @@
 #define OR_BICONNECTED 16u
 #define OR_CLIQUE_BOUND 32u
 #define OR_SPLIT_BUDGET 64u
+#define OR_DENSITY_BALANCE 128u
 
 #define OR_INF INT64_MAX
 #define OR_SPLIT_MAX_DEPTH 8
@@ -1130,6 +1131,7 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
                      oracle_totals *tot) {
   if (n_seg < 0 || k < 2 || k > 8 || n_conf < 0 || n_st < 0 || nthreads < 1) return OR_E_INVALID;
   if ((flags & OR_BICONNECTED) && (flags & OR_SINGLE_INSTANCE)) return OR_E_INVALID;
+  if ((flags & OR_BICONNECTED) && (flags & OR_DENSITY_BALANCE)) return OR_E_INVALID;
   if (polygon_of)
     for (int s = 0; s < n_seg; ++s)
       if (polygon_of[s] < 0 || polygon_of[s] >= n_seg) return OR_E_INVALID;
@@ -1365,6 +1367,35 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
       mask_out[inst_seg[t]] = (signed char)m;
     }
   }
+  /* density balance (a reading; the paper names the rule only in passing):
+   * permuting the masks of one component keeps its cost, so each instance in
+   * instance order gets the permutation that pairs its masks, by decreasing
+   * segment count (lower mask first on ties), with the masks of the layout so
+   * far by increasing segment count (lower mask first); recovery below then
+   * gives a removed unit the least used of the masks its coloured conflict
+   * neighbours leave free (lowest on ties) */
+  int64_t tot_mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (flags & OR_DENSITY_BALANCE) {
+    for (int c = 0; c < n_inst; ++c) {
+      int64_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int t = inst_ptr[c]; t < inst_ptr[c + 1]; ++t) x[mask_out[inst_seg[t]]]++;
+      int src[8], dst[8], perm[8];
+      for (int m = 0; m < k; ++m) { src[m] = m; dst[m] = m; }
+      /* insertion sorts: src by (x desc, m asc), dst by (tot asc, m asc) */
+      for (int i = 1; i < k; ++i)
+        for (int j = i; j > 0 && x[src[j]] > x[src[j - 1]]; --j) {
+          int t = src[j]; src[j] = src[j - 1]; src[j - 1] = t;
+        }
+      for (int i = 1; i < k; ++i)
+        for (int j = i; j > 0 && tot_mask[dst[j]] < tot_mask[dst[j - 1]]; --j) {
+          int t = dst[j]; dst[j] = dst[j - 1]; dst[j - 1] = t;
+        }
+      for (int i = 0; i < k; ++i) perm[src[i]] = dst[i];
+      for (int t = inst_ptr[c]; t < inst_ptr[c + 1]; ++t)
+        mask_out[inst_seg[t]] = (signed char)perm[mask_out[inst_seg[t]]];
+      for (int m = 0; m < k; ++m) tot_mask[perm[m]] += x[m];
+    }
+  }
   /* instance of each segment: the first one holding it */
   for (int s = 0; s < n_seg; ++s) comp_of[s] = -1;
   for (int c = n_inst - 1; c >= 0; --c)
@@ -1382,9 +1413,17 @@ int oracle_decompose(int n_seg, int k, int n_conf, const int *conf_u, const int 
       }
     }
     int c = 0;
-    while (c < k && (used >> c) & 1u) ++c;
+    if (flags & OR_DENSITY_BALANCE) {
+      c = -1;
+      for (int m = 0; m < k; ++m)
+        if (!((used >> m) & 1u) && (c < 0 || tot_mask[m] < tot_mask[c])) c = m;
+      if (c < 0) c = k;
+    } else {
+      while (c < k && (used >> c) & 1u) ++c;
+    }
     if (c == k) { rc = OR_E_INVALID; goto done; }   /* cannot happen for a k-core peel */
     for (int q = uptr[u]; q < uptr[u + 1]; ++q) mask_out[useg[q]] = (signed char)c;
+    tot_mask[c] += uptr[u + 1] - uptr[u];
     tot->n_removed_segments += uptr[u + 1] - uptr[u];
   }
 

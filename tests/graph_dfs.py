@@ -296,3 +296,114 @@ def split_search(n, k, conf, stitch, cc=10, cs=1, budget=0, rule=0, target=64):
         if found and (c, s) < win[:2]:
             win = (c, s, x)
     return win[0], win[2], nodes, any_hit
+
+
+def units_of(n, polygon_of, stitch):
+    """Unit of each segment: a polygon together with everything joined to it
+    by stitch edges; a unit's id is its lowest segment."""
+    parent = list(range(n))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    def unite(a, b):
+        ra, rb = find(a), find(b)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+
+    first = {}
+    for s in range(n):
+        p = polygon_of[s] if polygon_of is not None else s
+        if p in first:
+            unite(first[p], s)
+        else:
+            first[p] = s
+    for a, b in stitch:
+        unite(a, b)
+    return [find(s) for s in range(n)]
+
+
+def peel_order(n, k, conf, unit):
+    """Removal order of the polygon-level k-core peel: FIFO queue seeded in
+    ascending unit id; a unit with fewer than k conflict edges to remaining
+    units is removed (its neighbours' counts drop and they join the queue when
+    below k); a unit with a conflict edge inside itself is never removed."""
+    edges = sorted({(min(a, b), max(a, b)) for a, b in conf if a != b})
+    units = sorted(set(unit))
+    deg = {u: 0 for u in units}
+    selfc = set()
+    for a, b in edges:
+        ua, ub = unit[a], unit[b]
+        if ua == ub:
+            selfc.add(ua)
+        else:
+            deg[ua] += 1
+            deg[ub] += 1
+    cadj = adjacency(len(unit), edges)
+    segs = {}
+    for s_ in range(len(unit)):
+        segs.setdefault(unit[s_], []).append(s_)
+    queue = [u for u in units if u not in selfc and deg[u] < k]
+    queued = set(queue)
+    removed, order = set(), []
+    h = 0
+    while h < len(queue):
+        u = queue[h]
+        h += 1
+        removed.add(u)
+        order.append(u)
+        # the unit's segments in ascending id, each one's neighbours ascending
+        for s_ in segs[u]:
+            for v in cadj[s_]:
+                w = unit[v]
+                if w == u or w in removed:
+                    continue
+                deg[w] -= 1
+                if w not in queued and w not in selfc and deg[w] < k:
+                    queue.append(w)
+                    queued.add(w)
+    return order
+
+
+def density_balanced(n, k, conf, stitch, polygon_of, comp_of, inst_masks):
+    """The density-balance rule written out: instances in order (ascending
+    lowest segment) each take the mask permutation pairing their masks by
+    decreasing segment count (lower mask first on ties) with the layout's
+    masks so far by increasing count (lower first); then the removed units,
+    in reverse removal order, take the least used of the masks their coloured
+    conflict neighbours leave free (lowest on ties).  `inst_masks`: the
+    search's masks on instance segments (-1 elsewhere)."""
+    x = [-1] * n
+    tot = [0] * k
+    n_inst = max(comp_of) + 1 if len(comp_of) and max(comp_of) >= 0 else 0
+    members = [[] for _ in range(n_inst)]
+    for s in range(n):
+        if comp_of[s] >= 0:
+            members[comp_of[s]].append(s)
+    for c in range(n_inst):
+        cnt = [0] * k
+        for s in members[c]:
+            cnt[inst_masks[s]] += 1
+        src = sorted(range(k), key=lambda m: (-cnt[m], m))
+        dst = sorted(range(k), key=lambda m: (tot[m], m))
+        perm = {src[i]: dst[i] for i in range(k)}
+        for s in members[c]:
+            x[s] = perm[inst_masks[s]]
+        for m in range(k):
+            tot[perm[m]] += cnt[m]
+    unit = units_of(n, polygon_of, stitch)
+    segs = {}
+    for s in range(n):
+        segs.setdefault(unit[s], []).append(s)
+    cadj = adjacency(n, conf)
+    for u in reversed(peel_order(n, k, conf, unit)):
+        used = {x[w] for s in segs[u] for w in cadj[s] if x[w] >= 0}
+        free = [m for m in range(k) if m not in used]
+        c = min(free, key=lambda m: (tot[m], m))
+        for s in segs[u]:
+            x[s] = c
+        tot[c] += len(segs[u])
+    return x
