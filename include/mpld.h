@@ -127,6 +127,18 @@ extern "C" {
                                     submitted) with MPLD_CLIQUE_BOUND (MPLD_E_INVALID); not
                                     available to mpld_search_instance_noalloc
                                     (MPLD_E_INVALID). */
+#define MPLD_DENSITY_BALANCE 256u  /* balance mask usage over the layout (a reading of the density
+                                    balance the paper names only in passing): renaming the masks
+                                    of one component keeps its cost, so after the search each
+                                    instance in instance order takes the permutation that pairs
+                                    its masks by decreasing segment count (lower mask first on
+                                    ties) with the layout's masks so far by increasing count
+                                    (lower first), and the recovery gives a removed unit the least
+                                    used of the masks its coloured conflict neighbours leave free
+                                    (lowest on ties).  Cost, conflicts and stitches are those
+                                    without the flag.  Read by mpld_build_matrix (and
+                                    mpld_server_submit); not with MPLD_BICONNECTED
+                                    (MPLD_E_INVALID). */
 #define MPLD_HOST_ONLY 4u        /* build the host side only (no device memory): for inspection with
                                     mpld_problem_info / mpld_component_results / mpld_export_matrix;
                                     the solve calls then return MPLD_E_STATE */
@@ -169,7 +181,7 @@ typedef struct {
  *                  and keeps its incumbent (the layout status is then
  *                  MPLD_BUDGET);
  *   flags          MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_HOST_ONLY |
- *                  MPLD_BICONNECTED | MPLD_CLIQUE_BOUND (used by
+ *                  MPLD_BICONNECTED | MPLD_CLIQUE_BOUND | MPLD_DENSITY_BALANCE (used by
  *                  mpld_build_matrix); MPLD_COLUMN_BFS | MPLD_PARALLEL_EXACT |
  *                  MPLD_SPLIT_BUDGET (used by the search calls);
  *   warps_per_cta, slot_bytes   launch shape of the batched kernel; 0 = the
@@ -407,7 +419,7 @@ int mpld_server_create(const mpld_server_config *cfg, const mpld_params *search,
 
 /* Queue a layout (copied; `graph` may be reused at once).  flags as mpld_params.flags for
  * mpld_build_matrix (MPLD_NO_SIMPLIFY, MPLD_SINGLE_INSTANCE, MPLD_BICONNECTED,
- * MPLD_CLIQUE_BOUND; other bits are ignored).  Returns MPLD_OK and a ticket, or
+ * MPLD_CLIQUE_BOUND, MPLD_DENSITY_BALANCE; other bits are ignored).  Returns MPLD_OK and a ticket, or
  * MPLD_E_INVALID for MPLD_CLIQUE_BOUND on a server with MPLD_SPLIT_BUDGET.  Input errors
  * surface later as the ticket's result code. */
 int mpld_server_submit(mpld_server *s, const mpld_graph *graph, uint32_t flags, int64_t *ticket);

@@ -487,6 +487,9 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
 
   if (params && (params->flags & MPLD_BICONNECTED) && (params->flags & MPLD_SINGLE_INSTANCE))
     return MPLD_E_INVALID;
+  // a block's masks are tied to its attach segment: no renaming for balance
+  if (params && (params->flags & MPLD_BICONNECTED) && (params->flags & MPLD_DENSITY_BALANCE))
+    return MPLD_E_INVALID;
   mpld_problem *p = new (std::nothrow) mpld_problem();
   if (!p) return MPLD_E_OOM;
   p->n_seg = n;
@@ -1470,9 +1473,32 @@ int mpld_internal_finish(mpld_problem *p, const InstResult *hres, const int8_t *
       m[p->comp_seg[t]] = (int8_t)x;
     }
   }
-  // recovery: reverse removal order, lowest mask unused by coloured neighbours.
-  // Units a few places ahead in that order have their ranges, segments,
-  // adjacency and neighbour masks fetched early, as in the peel.
+  // density balance: renaming the masks of one component keeps its cost, so
+  // each instance in instance order takes the permutation that pairs its
+  // masks by decreasing segment count (lower mask first on ties) with the
+  // layout's masks so far by increasing count (lower first); recovery then
+  // gives a removed unit the least used of its free masks (lowest on ties)
+  const bool balance = (p->flags & MPLD_DENSITY_BALANCE) != 0;
+  int64_t tot_mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (balance) {
+    const int k = p->k;
+    for (int c = 0; c < C; ++c) {
+      int64_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t) x[m[p->comp_seg[t]]]++;
+      int src[8], dst[8], perm[8];
+      for (int q = 0; q < k; ++q) src[q] = dst[q] = q;
+      std::stable_sort(src, src + k, [&](int a, int b) { return x[a] > x[b]; });
+      std::stable_sort(dst, dst + k, [&](int a, int b) { return tot_mask[a] < tot_mask[b]; });
+      for (int q = 0; q < k; ++q) perm[src[q]] = dst[q];
+      for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t)
+        m[p->comp_seg[t]] = (int8_t)perm[m[p->comp_seg[t]]];
+      for (int q = 0; q < k; ++q) tot_mask[perm[q]] += x[q];
+    }
+  }
+  // recovery: reverse removal order, lowest mask unused by coloured neighbours
+  // (the least used one under density balance).  Units a few places ahead in
+  // that order have their ranges, segments, adjacency and neighbour masks
+  // fetched early, as in the peel.
   {
     const int32_t *ro = p->removed_order.data(), *uptr = p->uptr.data(), *useg = p->useg.data(),
                   *cptr = p->cptr.data(), *cadj = p->cadj.data();
@@ -1495,9 +1521,17 @@ int mpld_internal_finish(mpld_problem *p, const InstResult *hres, const int8_t *
         }
       }
       int c = 0;
-      while (c < p->k && ((used >> c) & 1u)) ++c;
+      if (balance) {
+        c = -1;
+        for (int q = 0; q < p->k; ++q)
+          if (!((used >> q) & 1u) && (c < 0 || tot_mask[q] < tot_mask[c])) c = q;
+        if (c < 0) c = p->k;
+      } else {
+        while (c < p->k && ((used >> c) & 1u)) ++c;
+      }
       if (c == p->k) return MPLD_E_STATE;
       for (int t = uptr[u]; t < uptr[u + 1]; ++t) m[useg[t]] = (int8_t)c;
+      if (balance) tot_mask[c] += uptr[u + 1] - uptr[u];
     }
   }
   // monochromatic conflict edges and cut stitch edges, counted in chunks

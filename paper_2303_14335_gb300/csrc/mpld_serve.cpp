@@ -414,7 +414,8 @@ extern "C" int mpld_server_submit(mpld_server *s, const mpld_graph *g, uint32_t 
   r->g.st_u = r->su.empty() ? nullptr : r->su.data();
   r->g.st_v = r->sv.empty() ? nullptr : r->sv.data();
   r->g.polygon_of = r->poly.empty() ? nullptr : r->poly.data();
-  r->flags = flags & (MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_BICONNECTED | MPLD_CLIQUE_BOUND);
+  r->flags = flags & (MPLD_NO_SIMPLIFY | MPLD_SINGLE_INSTANCE | MPLD_BICONNECTED | MPLD_CLIQUE_BOUND |
+                      MPLD_DENSITY_BALANCE);
   r->n_seg = n;
   std::lock_guard<std::mutex> lk(s->mu);
   r->ticket = s->next_ticket++;

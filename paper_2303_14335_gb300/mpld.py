@@ -35,6 +35,7 @@ MPLD_BICONNECTED = 16
 MPLD_CLIQUE_BOUND = 32
 MPLD_PARALLEL_EXACT = 64
 MPLD_SPLIT_BUDGET = 128
+MPLD_DENSITY_BALANCE = 256
 MPLD_MAX_INSTANCE_SEGMENTS = 65535
 
 _P = ctypes.c_void_p

@@ -275,3 +275,37 @@ def test_builds_are_identical_alone_and_concurrent():
         t.join()
     assert not errs
     assert all(o == ref for o in out)
+
+
+def test_density_balance_finish_on_the_host_matches_the_oracle():
+    # host-only handle: the oracle's per-instance results go through the
+    # library's own finish (scatter, balance, recovery, counts)
+    import oracle
+    for n, k, deg, ps, seed in ((3000, 3, 3.0, 0.2, 2), (1500, 4, 5.0, 0.3, 3), (1200, 5, 6.0, 0.2, 9)):
+        L = synth.unit_disk_layout(n, k, seed=seed, mean_deg=deg, p_stitch=ps)
+        plain = oracle.decompose(L, budget=3000, nthreads=4)
+        want = oracle.decompose(L, flags=oracle.DENSITY_BALANCE, budget=3000, nthreads=4)
+        prob = mpld.mpld_build_matrix(L, mpld.make_params(flags=mpld.MPLD_HOST_ONLY |
+                                                          mpld.MPLD_DENSITY_BALANCE))
+        try:
+            _, _, _, comp_of = mpld.mpld_component_results(prob, results=False)
+            assert np.array_equal(comp_of, plain.comp_of)
+            sizes = mpld.mpld_instance_sizes(prob)
+            masks = np.concatenate([plain.mask[comp_of == c] for c in range(len(sizes))] or
+                                   [np.zeros(0, np.int8)])
+            status = np.where(plain.comp_status == oracle.BUDGET, mpld.MPLD_BUDGET, mpld.MPLD_OK)
+            rc, mask, res = mpld.mpld_finish_from(prob, plain.comp_nodes, plain.comp_cost, status,
+                                                  masks)
+        finally:
+            prob.close()
+        assert np.array_equal(mask, want.mask)
+        assert (res.cost, res.n_conflicts, res.n_stitches) == (want.cost, want.n_conflicts,
+                                                               want.n_stitches)
+
+
+def test_density_balance_refused_with_blocks():
+    L = synth.unit_disk_layout(500, 3, seed=2, mean_deg=3.0, p_stitch=0.2)
+    with pytest.raises(mpld.MpldError) as e:
+        mpld.mpld_build_matrix(L, mpld.make_params(flags=mpld.MPLD_HOST_ONLY | mpld.MPLD_BICONNECTED |
+                                                   mpld.MPLD_DENSITY_BALANCE))
+    assert e.value.code == mpld.MPLD_E_INVALID

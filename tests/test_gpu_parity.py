@@ -586,3 +586,20 @@ def test_edge_cases(stream):
     L = synth.unit_disk_layout(700, 8, seed=3, mean_deg=9.0)
     ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=20000)
     assert_same(gpu_run(L, flags=SINGLE, budget=20000, stream=s), ref, L)
+
+
+# ------------------------------ density balance (a mask renaming after the search)
+
+@pytest.mark.parametrize("n,k,deg,ps,seed", [(20000, 3, 3.0, 0.2, 2), (8000, 4, 5.0, 0.3, 3),
+                                             (4000, 6, 7.0, 0.2, 9)])
+def test_density_balance(n, k, deg, ps, seed, stream):
+    L = synth.unit_disk_layout(n, k, seed=seed, mean_deg=deg, p_stitch=ps)
+    DB = mpld.MPLD_DENSITY_BALANCE
+    for sf, of in ((0, 0), (mpld.MPLD_SPLIT_BUDGET, oracle.SPLIT_BUDGET)):
+        ref = oracle.decompose(L, flags=oracle.DENSITY_BALANCE | of, budget=4000, nthreads=NTHREADS)
+        g = gpu_run(L, flags=DB, budget=4000, stream=stream.cuda_stream, search_flags=sf)
+        assert_same(g, ref, L)
+        counts = np.bincount(g["mask"], minlength=k)
+        plain = oracle.decompose(L, flags=of, budget=4000, nthreads=NTHREADS)
+        pc = np.bincount(plain.mask, minlength=k)
+        assert counts.max() - counts.min() <= pc.max() - pc.min()

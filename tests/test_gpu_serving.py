@@ -192,3 +192,14 @@ def test_split_budget_served(torch_cuda):
         ref = oracle.decompose(L, flags=oracle.SPLIT_BUDGET, budget=BUDGET, nthreads=NTHREADS)
         assert rc == rc2 and np.array_equal(mask, masks2[0]) and np.array_equal(mask, ref.mask)
         assert res.cost == res2[0].cost == ref.cost and res.nodes == res2[0].nodes == ref.nodes
+
+
+def test_density_balance_served(torch_cuda):
+    Ls = requests(6, seed=93)
+    with mpld.mpld_server_create(None, mpld.make_params(node_budget=BUDGET)) as srv:
+        tickets = [mpld.mpld_server_submit(srv, L, flags=mpld.MPLD_DENSITY_BALANCE) for L in Ls]
+        got = drain(srv, tickets)
+    for t, L in zip(tickets, Ls):
+        rc, mask, res = got[t]
+        ref = oracle.decompose(L, flags=oracle.DENSITY_BALANCE, budget=BUDGET, nthreads=NTHREADS)
+        assert np.array_equal(mask, ref.mask) and res.cost == ref.cost and res.nodes == ref.nodes
