@@ -57,6 +57,14 @@ MPLD_HD RoLayout ro_layout(int n, int ne2, int ns2, int nqe = 0) {
   L.bytes = o;
   return L;
 }
+// Shared memory of the column classes a giant instance is searched with
+// (one warp): per count class a bit per segment, its summary and its size,
+// and the breadth-first rank map with its summary.
+MPLD_HD uint32_t bucket_bytes(int n, int k) {
+  const uint32_t w = (uint32_t)(n + 31) / 32u, sw = (w + 31u) / 32u;
+  return 4u * ((uint32_t)(k + 1) * (w + sw + 1u) + w + sw);
+}
+
 // Instances the second phase of the budgeted split search gives to single
 // lanes (a subtree per lane, the whole state in registers as one bit per
 // segment); larger ones, or k > 4, to whole warps.

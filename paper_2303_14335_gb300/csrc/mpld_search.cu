@@ -194,6 +194,104 @@ struct CtaTeam {
   }
 };
 
+// Column classes of a giant instance, for a column choice that does not scan
+// every segment: per count class m (0..k), a bit per segment that is
+// uncovered with exactly m active rows, a summary bit per non-empty 32-bit
+// word of it, and the class size; under column rule 1 also a bit per
+// breadth-first rank that is uncovered, with its summary.  The fewest-rows
+// column is then the lowest set bit of the first non-empty class (lowest
+// index on ties, as the scan gives), found through the summary; covers and
+// undos move only the segment and its neighbours between classes.  One warp
+// keeps them in shared memory.
+struct Buckets {
+  uint32_t *cls;   // [k+1][w32]
+  uint32_t *sum;   // [k+1][s32]
+  int32_t *cnt;    // [k+1]
+  uint32_t *ur;    // [w32] rank space (rule 1)
+  uint32_t *urs;   // [s32]
+  int w32, s32, k;   // layout: bucket_bytes(n, k) bytes
+  __device__ void carve(uint8_t *base, int n, int kk) {
+    k = kk;
+    w32 = (n + 31) / 32;
+    s32 = (w32 + 31) / 32;
+    uint32_t *p = (uint32_t *)base;
+    cls = p; p += (k + 1) * w32;
+    sum = p; p += (k + 1) * s32;
+    cnt = (int32_t *)p; p += k + 1;
+    ur = p; p += w32;
+    urs = p;
+  }
+  // every segment uncovered with k active rows (one warp)
+  __device__ void init(int n, int lane) const {
+    // classes below k and every summary start empty; class k and the rank
+    // map hold every segment
+    for (int i = lane; i < k * w32; i += 32) cls[i] = 0u;
+    for (int i = lane; i < (k + 1) * s32; i += 32) sum[i] = 0u;
+    for (int i = lane; i < s32; i += 32) urs[i] = 0u;
+    for (int w = lane; w < w32; w += 32) {
+      const int lo = 32 * w;
+      const uint32_t bits = n - lo >= 32 ? 0xFFFFFFFFu : ((1u << (n - lo)) - 1u);
+      cls[k * w32 + w] = bits;
+      ur[w] = bits;
+    }
+    for (int i = lane; i <= k; i += 32) cnt[i] = i == k ? n : 0;
+    __syncwarp();
+    for (int w = lane; w < w32; w += 32) {
+      atomicOr(&sum[k * s32 + (w >> 5)], 1u << (w & 31));
+      atomicOr(&urs[w >> 5], 1u << (w & 31));
+    }
+    __syncwarp();
+  }
+  // segment v leaves class a (a < 0: none) and joins class b (b < 0: none)
+  __device__ __forceinline__ void move(int v, int a, int b) const {
+    if (a == b) return;
+    const uint32_t bit = 1u << (v & 31);
+    const int w = v >> 5;
+    if (a >= 0) {
+      atomicAnd(&cls[a * w32 + w], ~bit);
+      atomicSub(&cnt[a], 1);
+    }
+    if (b >= 0) {
+      atomicOr(&cls[b * w32 + w], bit);
+      atomicAdd(&cnt[b], 1);
+    }
+  }
+  // after the moves (and a __syncwarp): the summary bit of v's word in class m
+  __device__ __forceinline__ void fix(int v, int m) const {
+    if (m < 0) return;
+    const int w = v >> 5;
+    const uint32_t sb = 1u << (w & 31);
+    if (cls[m * w32 + w]) atomicOr(&sum[m * s32 + (w >> 5)], sb);
+    else atomicAnd(&sum[m * s32 + (w >> 5)], ~sb);
+  }
+  __device__ __forceinline__ void rank_set(int r, bool on) const {
+    const uint32_t bit = 1u << (r & 31);
+    const int w = r >> 5;
+    if (on) {
+      atomicOr(&ur[w], bit);
+      atomicOr(&urs[w >> 5], 1u << (w & 31));
+    } else {
+      const uint32_t old = atomicAnd(&ur[w], ~bit);
+      if ((old & ~bit) == 0u) atomicAnd(&urs[w >> 5], ~(1u << (w & 31)));
+    }
+  }
+  // lowest set bit of a bit map with summary `sm` (s32 words), -1 if none;
+  // every lane gets the answer
+  __device__ __forceinline__ int lowest(const uint32_t *bm, const uint32_t *sm, int lane) const {
+    for (int base = 0; base < s32; base += 32) {
+      const uint32_t sv = base + lane < s32 ? sm[base + lane] : 0u;
+      const uint32_t nz = __ballot_sync(FULL, sv != 0u);
+      if (nz) {
+        const int l = __ffs(nz) - 1;
+        const uint32_t s0 = __shfl_sync(FULL, sv, l);
+        const int w = (base + l) * 32 + __ffs(s0) - 1;
+        return w * 32 + __ffs(bm[w]) - 1;
+      }
+    }
+    return -1;
+  }
+};
+
 // What a search does with the levels above the cut of the budgeted split
 // search.  Default: nothing (the canonical search of the whole tree).
 //   track:  first phase -- the subtree (row places of the first `cut`
@@ -222,7 +320,7 @@ struct SplitSpec {
 // the same lanes, so the added cost of a segment's rows (Eq. 1) is read in
 // one load instead of gathered from its neighbours.
 // Instances of at most 32 words of fields go to reg_search below instead.
-template <typename FT, int MK, bool SM, typename Team>
+template <typename FT, int MK, bool SM, typename Team, bool BK = false>
 struct Search {
   static constexpr uint32_t FB = 8 * sizeof(FT);    // bits per field
   static constexpr uint32_t FLAG = 1u << (FB - 1);   // column P_v uncovered
@@ -255,6 +353,10 @@ struct Search {
     return (int)((w >> (16 * (c & 3))) & 0xFFFFull);
   }
   Team team;          // the threads searching this instance together
+  Buckets bk;         // BK: the column classes (one warp, shared memory)
+  __device__ __forceinline__ int cls_of(uint32_t f) const {
+    return (f & FLAG) ? __popc(f & kmask) : -1;
+  }
   // f(i) for i = rank, rank + team size, ... < d
   template <typename F>
   __device__ __forceinline__ void each(int d, int rank, F &&f) const {
@@ -283,9 +385,14 @@ struct Search {
   __device__ __forceinline__ void cover_first(int v, int c, int cb, int dc, int sb, int ds,
                                               int lane) const {
     if (lane == 0) {
-      oldf[v] = rows[v];
+      const FT fv = rows[v];
+      oldf[v] = fv;
       rows[v] = 0;
       x[v] = (int8_t)c;
+      if constexpr (BK) {
+        bk.move(v, cls_of(fv), -1);
+        if (rule) bk.rank_set(ro_ld<SM>(rank + v), false);
+      }
     }
     const uint32_t clr = ~(1u << c);
     each(dc, lane, [&](int i) {
@@ -294,9 +401,20 @@ struct Search {
       savf[cb + i] = f;
       rows[u] = (FT)(f & clr);
       move_count(ccnt, u, c, -1);
+      if constexpr (BK) bk.move(u, cls_of(f), cls_of(f & clr));
     });
     each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, -1); });
     team.sync();
+    if constexpr (BK) {
+      if (lane == 0) bk.fix(v, cls_of(oldf[v]));
+      each(dc, lane, [&](int i) {
+        const int u = ro_ld<SM>(cnbr + cb + i);
+        const FT f = savf[cb + i];
+        bk.fix(u, cls_of(f));
+        bk.fix(u, cls_of(f & clr));
+      });
+      team.sync();
+    }
   }
 
   // Next row (v, c) of the same column, replacing row (v, c_old): every
@@ -304,14 +422,25 @@ struct Search {
   __device__ __forceinline__ void switch_row(int v, int c_old, int c, int cb, int dc, int sb,
                                              int ds, int lane) const {
     if (lane == 0) x[v] = (int8_t)c;
-    const uint32_t clr = ~(1u << c);
+    const uint32_t clr = ~(1u << c), clr_old = ~(1u << c_old);
     each(dc, lane, [&](int i) {
       const int u = ro_ld<SM>(cnbr + cb + i);
-      rows[u] = (FT)(savf[cb + i] & clr);
+      const FT f = savf[cb + i];
+      rows[u] = (FT)(f & clr);
       move_count(ccnt, u, c, c_old);
+      if constexpr (BK) bk.move(u, cls_of(f & clr_old), cls_of(f & clr));
     });
     each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, c_old); });
     team.sync();
+    if constexpr (BK) {
+      each(dc, lane, [&](int i) {
+        const int u = ro_ld<SM>(cnbr + cb + i);
+        const FT f = savf[cb + i];
+        bk.fix(u, cls_of(f & clr_old));
+        bk.fix(u, cls_of(f & clr));
+      });
+      team.sync();
+    }
   }
 
   // Every row of v's column tried (the last was c_last): put v's field and
@@ -319,16 +448,34 @@ struct Search {
   __device__ __forceinline__ void restore(int v, int c_last, int cb, int dc, int sb, int ds,
                                           int lane) const {
     if (lane == 0) {
-      rows[v] = oldf[v];
+      const FT fv = oldf[v];
+      rows[v] = fv;
       x[v] = -1;
+      if constexpr (BK) {
+        bk.move(v, -1, cls_of(fv));
+        if (rule) bk.rank_set(ro_ld<SM>(rank + v), true);
+      }
     }
+    const uint32_t clr_last = ~(1u << c_last);
     each(dc, lane, [&](int i) {
       const int u = ro_ld<SM>(cnbr + cb + i);
-      rows[u] = savf[cb + i];
+      const FT f = savf[cb + i];
+      rows[u] = f;
       *cw_of(ccnt, u, c_last) -= one(c_last);
+      if constexpr (BK) bk.move(u, cls_of(f & clr_last), cls_of(f));
     });
     each(ds, lane, [&](int i) { *cw_of(scnt, ro_ld<SM>(snbr + sb + i), c_last) -= one(c_last); });
     team.sync();
+    if constexpr (BK) {
+      if (lane == 0) bk.fix(v, cls_of(oldf[v]));
+      each(dc, lane, [&](int i) {
+        const int u = ro_ld<SM>(cnbr + cb + i);
+        const FT f = savf[cb + i];
+        bk.fix(u, cls_of(f & clr_last));
+        bk.fix(u, cls_of(f));
+      });
+      team.sync();
+    }
   }
 
   __device__ __forceinline__ int run(int lane, int64_t budget, int64_t time_limit_ns,
@@ -389,7 +536,25 @@ struct Search {
         // (the paper's) keys single-row columns by v ahead of all others,
         // which go by breadth-first rank.
         uint32_t key = 0xFFFFFFFFu, z = 0;
-        if (rule == 0) {
+        if (BK) {
+          // the column classes: the first non-empty one's lowest segment
+          // (rule 0), or a single-row column, else the lowest uncovered
+          // breadth-first rank (rule 1); z = the dead columns
+          int m0 = -1;
+          for (int m = 0; m <= k; ++m)
+            if (m0 < 0 && *(volatile int32_t *)&bk.cnt[m] > 0) m0 = m;
+          if (m0 >= 0) {
+            if (rule == 0) {
+              key = ((uint32_t)m0 << 16) | (uint32_t)bk.lowest(bk.cls + m0 * bk.w32,
+                                                             bk.sum + m0 * bk.s32, lane);
+            } else if (*(volatile int32_t *)&bk.cnt[1] > 0) {
+              key = (uint32_t)bk.lowest(bk.cls + bk.w32, bk.sum + bk.s32, lane);
+            } else {
+              key = 0x10000u | (uint32_t)bk.lowest(bk.ur, bk.urs, lane);
+            }
+          }
+          z = (uint32_t)*(volatile int32_t *)&bk.cnt[0];
+        } else if (rule == 0) {
           // four words per thread in flight: an instance whose state is in
           // global memory waits on one load latency per four words
           const int ts = team.size();
@@ -430,7 +595,7 @@ struct Search {
               }
           }
         }
-        key = team.min(key);
+        if (!BK) key = team.min(key);
         if (key == 0xFFFFFFFFu) {
           // leaf: every primary column covered
           if (g < best) {
@@ -452,7 +617,7 @@ struct Search {
         if (best < INF32) {
           // the bound needs the number of uncovered columns with no active
           // row; under rule 0 there is one only when the minimum count is 0
-          z = (rule != 0 || (key >> 16) == 0) ? team.sum(z) : 0u;
+          if (!BK) z = (rule != 0 || (key >> 16) == 0) ? team.sum(z) : 0u;
           if ((int64_t)g + (int64_t)Cc * (z + (uint32_t)untouched) >= best) { enter = false; continue; }
         }
         const int v = (rule == 0 || key < 0x10000u) ? (int)(key & 0xFFFFu)
@@ -1420,10 +1585,11 @@ __device__ __noinline__ bool par_dispatch(const InstDesc &d, uint8_t *base, cons
 
 // Initialise the state at `base` and search.  SM says at compile time
 // whether `base` and `ro` point into shared memory.
-template <typename FT, int MK, bool SM, typename Team>
+template <typename FT, int MK, bool SM, typename Team, bool BK = false>
 __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
-                                       const LaunchArgs &a, const Team &team) {
-  using S = Search<FT, MK, SM, Team>;
+                                       const LaunchArgs &a, const Team &team,
+                                       uint8_t *bk_mem = nullptr) {
+  using S = Search<FT, MK, SM, Team, BK>;
   const int lane = team.rank;
   const int ts = team.size();
   const int n = d.n;
@@ -1465,6 +1631,10 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   for (int i = lane; i < n * S::CW; i += ts) {
     s.ccnt[i] = 0;
     s.scnt[i] = 0;
+  }
+  if constexpr (BK) {
+    s.bk.carve(bk_mem, n, d.k);
+    s.bk.init(n, lane);
   }
   team.sync();
   int32_t best = INF32;
@@ -1554,11 +1724,21 @@ __device__ __noinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, 
   return true;
 }
 
-// One large instance searched by the whole CTA; its state stays in its
-// global scratch region and its adjacency is read through L2.
+// One large instance searched by the CTA; its state stays in its global
+// scratch region and its adjacency is read through L2.  When the CTA's
+// slots hold its column classes (`bk_mem`, `bk_room` bytes), warp 0 searches
+// it alone with them, so that a node costs its neighbours' updates rather
+// than a scan of every segment; otherwise every thread of the CTA scans.
 template <typename FT, int MK>
 __device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArgs &a,
-                                              const CtaTeam &team) {
+                                              const CtaTeam &team, uint8_t *bk_mem,
+                                              uint32_t bk_room) {
+  if (bucket_bytes(d.n, d.k) <= bk_room) {
+    if ((team.rank >> 5) == 0)
+      run_in<FT, MK, false, WarpTeam, true>(d, d.scratch, d.ro, a, WarpTeam{team.rank}, bk_mem);
+    __syncthreads();
+    return;
+  }
   run_in<FT, MK, false>(d, d.scratch, d.ro, a, team);
 }
 
@@ -1960,7 +2140,7 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
   HW = __shfl_sync(FULL, HW, 0);
   HL = __shfl_sync(FULL, HL, 0);
   HG = __shfl_sync(FULL, HG, 0);
-  const int32_t *list_w = a.hard + 4, *list_l = a.hard + 4 + a.hard_cap;
+  const int32_t *list_w = a.hard + 4;
   const int32_t *list_g = a.hard + 4 + 2 * a.hard_cap;
   // warps with a general-state region first take the subtrees of instances
   // beyond the register form (counter queue[2]), then every warp those of
@@ -2190,11 +2370,16 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
           d.res->work = (int64_t)ctx->work;
         }
         __syncthreads();
-      } else if (d.k == 3) run_instance_cta<uint8_t, 3>(d, a, team);
-      else if (d.k == 4) run_instance_cta<uint8_t, 4>(d, a, team);
-      else if (d.k == 2) run_instance_cta<uint8_t, 2>(d, a, team);
-      else if (d.k <= 7) run_instance_cta<uint8_t, 8>(d, a, team);
-      else run_instance_cta<uint16_t, 8>(d, a, team);
+      } else {
+        // the CTA's slots, free while it searches this instance
+        uint8_t *bkm = g_smem + bar_bytes;
+        const uint32_t room = (uint32_t)nw * (uint32_t)(a.slot_bytes > 0 ? a.slot_bytes : 0);
+        if (d.k == 3) run_instance_cta<uint8_t, 3>(d, a, team, bkm, room);
+        else if (d.k == 4) run_instance_cta<uint8_t, 4>(d, a, team, bkm, room);
+        else if (d.k == 2) run_instance_cta<uint8_t, 2>(d, a, team, bkm, room);
+        else if (d.k <= 7) run_instance_cta<uint8_t, 8>(d, a, team, bkm, room);
+        else run_instance_cta<uint16_t, 8>(d, a, team, bkm, room);
+      }
       if (!a.queue) break;
     }
   }

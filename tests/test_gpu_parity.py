@@ -347,6 +347,29 @@ def test_cta_team_large_instance_default_threshold(stream):
     assert ref.max_component >= 4096
     for cta in (0, -1):
         assert_same(gpu_run(L, flags=SINGLE, budget=6000, stream=stream.cuda_stream, cta=cta), ref, L)
+    # 16-byte slots leave no room for the column classes: every thread of the
+    # CTA scans instead
+    assert_same(gpu_run(L, flags=SINGLE, budget=6000, stream=stream.cuda_stream, slot=16), ref, L)
+    for path in ("batch", "plain"):
+        assert_same(gpu_run(L, flags=SINGLE, budget=6000, path=path, stream=stream.cuda_stream),
+                    ref, L)
+
+
+@pytest.mark.parametrize("k,rule", [(3, 0), (3, 1), (4, 0), (8, 0), (2, 1)])
+def test_giant_instance_column_classes(k, rule, stream):
+    # about 11,000 segments in one instance, searched by warp 0 of a CTA with
+    # its column classes in shared memory, under both column rules
+    L = synth.unit_disk_layout(9000 if k < 8 else 6000, k, seed=41 + k,
+                               mean_deg=4.5 if k < 8 else 9.0, p_stitch=0.2)
+    of = oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | (oracle.COLUMN_BFS if rule else 0)
+    ref = oracle.decompose(L, flags=of, budget=3000)
+    assert ref.max_component >= 4096
+    for cta in (0, 2000):
+        assert_same(gpu_run(L, flags=SINGLE, budget=3000, stream=stream.cuda_stream, cta=cta,
+                            search_flags=BFS if rule else 0), ref, L)
+    # and with no room for the classes: the scan by every thread of the CTA
+    assert_same(gpu_run(L, flags=SINGLE, budget=3000, stream=stream.cuda_stream, slot=16,
+                        search_flags=BFS if rule else 0), ref, L)
 
 
 # ------------------------------ exact search with the warps of a CTA splitting an instance
