@@ -1588,7 +1588,7 @@ __device__ __noinline__ bool par_dispatch(const InstDesc &d, uint8_t *base, cons
 template <typename FT, int MK, bool SM, typename Team, bool BK = false>
 __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const uint8_t *ro,
                                        const LaunchArgs &a, const Team &team,
-                                       uint8_t *bk_mem = nullptr) {
+                                       uint8_t *bk_mem = nullptr, uint32_t bk_room = 0) {
   using S = Search<FT, MK, SM, Team, BK>;
   const int lane = team.rank;
   const int ts = team.size();
@@ -1635,6 +1635,17 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
   if constexpr (BK) {
     s.bk.carve(bk_mem, n, d.k);
     s.bk.init(n, lane);
+    // the fields and masks too, when the room allows: the column choice and
+    // the covers then touch no global memory for them
+    const uint32_t fb = align16((uint32_t)sizeof(FT) * (uint32_t)nfields);
+    const uint32_t at = align16(bucket_bytes(n, d.k));
+    if (at + 2u * fb + align16((uint32_t)n) <= bk_room) {
+      s.rows = (FT *)(bk_mem + at);
+      s.oldf = (FT *)(bk_mem + at + fb);
+      s.x = (int8_t *)(bk_mem + at + 2u * fb);
+      for (int i = lane; i < nfields; i += ts) s.rows[i] = i < n ? init : (FT)0;
+      for (int i = lane; i < n; i += ts) s.x[i] = -1;
+    }
   }
   team.sync();
   int32_t best = INF32;
@@ -1735,7 +1746,8 @@ __device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArg
                                               uint32_t bk_room) {
   if (bucket_bytes(d.n, d.k) <= bk_room) {
     if ((team.rank >> 5) == 0)
-      run_in<FT, MK, false, WarpTeam, true>(d, d.scratch, d.ro, a, WarpTeam{team.rank}, bk_mem);
+      run_in<FT, MK, false, WarpTeam, true>(d, d.scratch, d.ro, a, WarpTeam{team.rank}, bk_mem,
+                                            bk_room);
     __syncthreads();
     return;
   }
