@@ -1606,11 +1606,12 @@ extern "C" int mpld_search_plain_async(mpld_problem *p, const mpld_params *prm, 
     // a whole CTA keeps the state in global memory, unless its warps split
     // the instance (each then needs a slot)
     const int team_slot = mpld_internal_max_slot_bytes(CTA_TEAM_WARPS);
-    // ... or, not split, its column classes in the CTA's slots (warp 0 then
-    // searches it alone; without room every thread of the CTA scans)
+    // ... or, not split, its column classes in the CTA's slots, with as much
+    // of its state beside them as fits (warp 0 then searches it alone;
+    // without room for the classes every thread of the CTA scans)
     const int bk_slot = (int)mpld::align16((mpld::bucket_bytes(p->h_desc[c].n, p->h_desc[c].k) +
                                             CTA_TEAM_WARPS - 1) / CTA_TEAM_WARPS);
-    a.slot_bytes = large ? (par_of(prm) ? (fp <= team_slot ? fp : 0) : (bk_slot <= team_slot ? bk_slot : 0))
+    a.slot_bytes = large ? (par_of(prm) ? (fp <= team_slot ? fp : 0) : (bk_slot <= team_slot ? team_slot : 0))
                          : (fp <= maxslot ? fp : 0);
     a.queue = nullptr;
     a.err = p->d_err;

@@ -354,6 +354,18 @@ struct Search {
   }
   Team team;          // the threads searching this instance together
   Buckets bk;         // BK: the column classes (one warp, shared memory)
+  // BK, when the room allows (k <= 4 and every degree below 256): the
+  // per-mask neighbour counts as 8-bit lanes of one word per segment, and
+  // the adjacency offsets as 16-bit offsets from the first segment of each
+  // block of 64 (`cob`, `sob`: the blocks' own offsets), in shared memory;
+  // a node then reads only its neighbour lists from global memory
+  uint32_t *bcc = nullptr, *bsc = nullptr;
+  uint16_t *co16 = nullptr, *so16 = nullptr;
+  int32_t *cob = nullptr, *sob = nullptr;
+  // 8-bit lanes 0..3 of w as the 16-bit lanes of the global count words
+  __device__ __forceinline__ static uint64_t widen8(uint32_t w) {
+    return (uint64_t)__byte_perm(w, 0u, 0x4140u) | ((uint64_t)__byte_perm(w, 0u, 0x4342u) << 32);
+  }
   __device__ __forceinline__ int cls_of(uint32_t f) const {
     return (f & FLAG) ? __popc(f & kmask) : -1;
   }
@@ -395,24 +407,47 @@ struct Search {
       }
     }
     const uint32_t clr = ~(1u << c);
-    each(dc, lane, [&](int i) {
-      const int u = ro_ld<SM>(cnbr + cb + i);
-      const FT f = rows[u];
-      savf[cb + i] = f;
-      rows[u] = (FT)(f & clr);
-      move_count(ccnt, u, c, -1);
-      if constexpr (BK) bk.move(u, cls_of(f), cls_of(f & clr));
-    });
-    each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, -1); });
-    team.sync();
     if constexpr (BK) {
-      if (lane == 0) bk.fix(v, cls_of(oldf[v]));
+      // each lane keeps its first neighbour and that neighbour's saved
+      // field for the summary fix below (no second read of either)
+      int u0 = 0;
+      FT f0 = 0;
       each(dc, lane, [&](int i) {
         const int u = ro_ld<SM>(cnbr + cb + i);
-        const FT f = savf[cb + i];
+        const FT f = rows[u];
+        savf[cb + i] = f;
+        rows[u] = (FT)(f & clr);
+        if (bcc) bcc[u] += 1u << (8 * c);
+        else move_count(ccnt, u, c, -1);
+        bk.move(u, cls_of(f), cls_of(f & clr));
+        if (i == lane) {
+          u0 = u;
+          f0 = f;
+        }
+      });
+      each(ds, lane, [&](int i) {
+        const int u = ro_ld<SM>(snbr + sb + i);
+        if (bsc) bsc[u] += 1u << (8 * c);
+        else move_count(scnt, u, c, -1);
+      });
+      team.sync();
+      if (lane == 0) bk.fix(v, cls_of(oldf[v]));
+      each(dc, lane, [&](int i) {
+        const int u = i == lane ? u0 : (int)ro_ld<SM>(cnbr + cb + i);
+        const FT f = i == lane ? f0 : savf[cb + i];
         bk.fix(u, cls_of(f));
         bk.fix(u, cls_of(f & clr));
       });
+      team.sync();
+    } else {
+      each(dc, lane, [&](int i) {
+        const int u = ro_ld<SM>(cnbr + cb + i);
+        const FT f = rows[u];
+        savf[cb + i] = f;
+        rows[u] = (FT)(f & clr);
+        move_count(ccnt, u, c, -1);
+      });
+      each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, -1); });
       team.sync();
     }
   }
@@ -427,10 +462,15 @@ struct Search {
       const int u = ro_ld<SM>(cnbr + cb + i);
       const FT f = savf[cb + i];
       rows[u] = (FT)(f & clr);
-      move_count(ccnt, u, c, c_old);
+      if (BK && bcc) bcc[u] += (1u << (8 * c)) - (1u << (8 * c_old));
+      else move_count(ccnt, u, c, c_old);
       if constexpr (BK) bk.move(u, cls_of(f & clr_old), cls_of(f & clr));
     });
-    each(ds, lane, [&](int i) { move_count(scnt, ro_ld<SM>(snbr + sb + i), c, c_old); });
+    each(ds, lane, [&](int i) {
+      const int u = ro_ld<SM>(snbr + sb + i);
+      if (BK && bsc) bsc[u] += (1u << (8 * c)) - (1u << (8 * c_old));
+      else move_count(scnt, u, c, c_old);
+    });
     team.sync();
     if constexpr (BK) {
       each(dc, lane, [&](int i) {
@@ -461,10 +501,15 @@ struct Search {
       const int u = ro_ld<SM>(cnbr + cb + i);
       const FT f = savf[cb + i];
       rows[u] = f;
-      *cw_of(ccnt, u, c_last) -= one(c_last);
+      if (BK && bcc) bcc[u] -= 1u << (8 * c_last);
+      else *cw_of(ccnt, u, c_last) -= one(c_last);
       if constexpr (BK) bk.move(u, cls_of(f & clr_last), cls_of(f));
     });
-    each(ds, lane, [&](int i) { *cw_of(scnt, ro_ld<SM>(snbr + sb + i), c_last) -= one(c_last); });
+    each(ds, lane, [&](int i) {
+      const int u = ro_ld<SM>(snbr + sb + i);
+      if (BK && bsc) bsc[u] -= 1u << (8 * c_last);
+      else *cw_of(scnt, u, c_last) -= one(c_last);
+    });
     team.sync();
     if constexpr (BK) {
       if (lane == 0) bk.fix(v, cls_of(oldf[v]));
@@ -541,8 +586,8 @@ struct Search {
           // (rule 0), or a single-row column, else the lowest uncovered
           // breadth-first rank (rule 1); z = the dead columns
           int m0 = -1;
-          for (int m = 0; m <= k; ++m)
-            if (m0 < 0 && *(volatile int32_t *)&bk.cnt[m] > 0) m0 = m;
+          for (int m = k; m >= 0; --m)
+            if (*(volatile int32_t *)&bk.cnt[m] > 0) m0 = m;
           if (m0 >= 0) {
             if (rule == 0) {
               key = ((uint32_t)m0 << 16) | (uint32_t)bk.lowest(bk.cls + m0 * bk.w32,
@@ -623,11 +668,26 @@ struct Search {
         const int v = (rule == 0 || key < 0x10000u) ? (int)(key & 0xFFFFu)
                                                      : (int)ro_ld<SM>(order + (key & 0xFFFFu));
         // added cost of each row (v, c) against the current assignment (Eq. 1)
-        const int2 p0 = ro_ld<SM>(ptr + v), p1 = ro_ld<SM>(ptr + v + 1);
-        const uint64_t cc0 = ccnt[(size_t)v * CW], sc0 = scnt[(size_t)v * CW];
-        const uint64_t cc1 = CW == 2 ? ccnt[(size_t)v * CW + 1] : 0ull;
-        const uint64_t sc1 = CW == 2 ? scnt[(size_t)v * CW + 1] : 0ull;
-        const int cb = p0.x, dc = p1.x - p0.x, sb = p0.y, ds = p1.y - p0.y;
+        int cb, dc, sb, ds;
+        uint64_t cc0, sc0, cc1 = 0ull, sc1 = 0ull;
+        if (BK && bcc) {
+          const int v1 = v + 1;
+          cb = cob[v >> 6] + (int)co16[v];
+          dc = cob[v1 >> 6] + (int)co16[v1] - cb;
+          sb = sob[v >> 6] + (int)so16[v];
+          ds = sob[v1 >> 6] + (int)so16[v1] - sb;
+          cc0 = widen8(bcc[v]);
+          sc0 = widen8(bsc[v]);
+        } else {
+          const int2 p0 = ro_ld<SM>(ptr + v), p1 = ro_ld<SM>(ptr + v + 1);
+          cc0 = ccnt[(size_t)v * CW];
+          sc0 = scnt[(size_t)v * CW];
+          if (CW == 2) {
+            cc1 = ccnt[(size_t)v * CW + 1];
+            sc1 = scnt[(size_t)v * CW + 1];
+          }
+          cb = p0.x, dc = p1.x - p0.x, sb = p0.y, ds = p1.y - p0.y;
+        }
         work32 += (uint32_t)(k * (dc + ds) + 5 * (1 + dc));
         int stot = 0;
 #pragma unroll
@@ -1639,12 +1699,47 @@ __device__ __forceinline__ void run_in(const InstDesc &d, uint8_t *base, const u
     // the covers then touch no global memory for them
     const uint32_t fb = align16((uint32_t)sizeof(FT) * (uint32_t)nfields);
     const uint32_t at = align16(bucket_bytes(n, d.k));
-    if (at + 2u * fb + align16((uint32_t)n) <= bk_room) {
+    uint32_t off = at + 2u * fb + align16((uint32_t)n);
+    if (off <= bk_room) {
       s.rows = (FT *)(bk_mem + at);
       s.oldf = (FT *)(bk_mem + at + fb);
       s.x = (int8_t *)(bk_mem + at + 2u * fb);
       for (int i = lane; i < nfields; i += ts) s.rows[i] = i < n ? init : (FT)0;
       for (int i = lane; i < n; i += ts) s.x[i] = -1;
+      // then the counts and offsets, for k <= 4 when every degree is below
+      // 256 (no 8-bit count can overflow, and a block of 64 segments spans
+      // fewer than 65,536 list entries)
+      const uint32_t cw = align16(4u * (uint32_t)n), ow = align16(2u * (uint32_t)(n + 1));
+      const uint32_t bw = align16(4u * (uint32_t)((n >> 6) + 1));
+      if (MK <= 4 && off + 2u * (cw + ow + bw) <= bk_room) {
+        int dmax = 0;
+        for (int i = lane; i < n; i += ts) {
+          const int2 a0 = s.ptr[i], a1 = s.ptr[i + 1];
+          dmax = max(dmax, max(a1.x - a0.x, a1.y - a0.y));
+        }
+        dmax = (int)__reduce_max_sync(FULL, (uint32_t)dmax);   // one warp
+        if (dmax < 256) {
+          s.bcc = (uint32_t *)(bk_mem + off);
+          s.bsc = (uint32_t *)(bk_mem + off + cw);
+          s.co16 = (uint16_t *)(bk_mem + off + 2u * cw);
+          s.so16 = (uint16_t *)(bk_mem + off + 2u * cw + ow);
+          s.cob = (int32_t *)(bk_mem + off + 2u * (cw + ow));
+          s.sob = (int32_t *)(bk_mem + off + 2u * (cw + ow) + bw);
+          for (int i = lane; i < n; i += ts) {
+            s.bcc[i] = 0u;
+            s.bsc[i] = 0u;
+          }
+          for (int i = lane; i <= n; i += ts) {
+            const int2 q = s.ptr[i], b = s.ptr[i & ~63];
+            s.co16[i] = (uint16_t)(q.x - b.x);
+            s.so16[i] = (uint16_t)(q.y - b.y);
+            if ((i & 63) == 0) {
+              s.cob[i >> 6] = q.x;
+              s.sob[i >> 6] = q.y;
+            }
+          }
+        }
+      }
     }
   }
   team.sync();

@@ -372,6 +372,28 @@ def test_giant_instance_column_classes(k, rule, stream):
                         search_flags=BFS if rule else 0), ref, L)
 
 
+def test_column_classes_backtracking_and_high_degree(stream):
+    # instances sent to the one-warp search with column classes (threshold
+    # 100): a budget well past the first leaf makes it backtrack, with the
+    # counts and offsets in shared memory; a hub of 300 neighbours leaves a
+    # degree above 255, and the counts then stay in global memory
+    L = synth.unit_disk_layout(700, 3, seed=61, mean_deg=4.5, p_stitch=0.2)
+    ref = oracle.decompose(L, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=30000)
+    for path in ("batch", "plain"):
+        assert_same(gpu_run(L, flags=SINGLE, budget=30000, path=path, stream=stream.cuda_stream,
+                            cta=100), ref, L)
+    conf = set(zip(L.conf_u.tolist(), L.conf_v.tolist()))
+    st = list(zip(L.st_u.tolist(), L.st_v.tolist()))
+    conf |= {(0, j) for j in range(1, 301)} - set(st)
+    H = synth.graph_from_edges(L.n_seg, 3, sorted(conf), st, polygon_of=L.polygon_of)
+    for k in (3, 4):
+        H.k = k
+        ref = oracle.decompose(H, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=30000)
+        for path in ("batch", "plain"):
+            assert_same(gpu_run(H, flags=SINGLE, budget=30000, path=path,
+                                stream=stream.cuda_stream, cta=100), ref, H)
+
+
 # ------------------------------ exact search with the warps of a CTA splitting an instance
 
 PAR = mpld.MPLD_PARALLEL_EXACT
