@@ -648,11 +648,13 @@ def main():
                    "status": rc, "step_ms": step_ms,
                    "median_step_ms": statistics.median(step_ms) if step_ms else None,
                    "instances_exact": inst_status},
-        # launches per step: the split search's two; the exact split search's
-        # queue launch before the batched one when the layout has several
-        # instances, one grid launch for a single instance
-        "gpu_launches": args.steps * (2 if args.split_budget or
-                                      (args.parallel_exact and info.n_components > 1) else 1),
+        # launches per step: the split search's three (the first search of
+        # every instance, then the subtrees of the per-lane list and of the
+        # warps' list); the exact split search's queue launch before the
+        # batched one when the layout has several instances, one grid launch
+        # for a single instance
+        "gpu_launches": args.steps * (3 if args.split_budget else
+                                      2 if (args.parallel_exact and info.n_components > 1) else 1),
         "sequential_budget": seq,
         "clocks": clk,
     }
@@ -680,8 +682,8 @@ def main():
                                       f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json); "
                                       "derived, see int_pipes_measured",
                        "work_ops_per_launch": res.work,
-                       "covers": ("both launches of a step (the second, the subtree searches, is "
-                                  "87 % of the device time in the launch list)"
+                       "covers": ("the three launches of a step (first searches; the per-lane "
+                                  "subtree searches; the warps' subtree searches), timed together"
                                   if args.split_budget else "the one launch of a step")}
     # the integer pipes' measured throughput for the same op mix (context for
     # the derived peak above)

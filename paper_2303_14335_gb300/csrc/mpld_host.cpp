@@ -1222,10 +1222,15 @@ mpld::SplitPlan mpld::split_plan(const InstDesc *desc, int n_inst, const mpld_pa
       ? (int)std::max<size_t>(1, std::min<size_t>((size_t)G, gen_cap_bytes / (size_t)q.state_bytes))
       : 0;
   q.cap = n_inst;
+  // the lanes' list holds at most the instances the per-lane search takes
+  int lane_cap = 0;
+  for (int i = 0; i < n_inst; ++i)
+    if (desc[i].n <= SPLIT_MAX_N && split_list_of(desc[i].n, desc[i].k) == 1) ++lane_cap;
   q.o_hard = 0;
   q.o_ctx = (4u * (size_t)(4 + 3 * n_inst) + 255) & ~(size_t)255;
   q.o_state = q.o_ctx + 64u * (size_t)n_inst;
-  q.bytes = q.o_state + (size_t)q.gen_warps * (size_t)q.state_bytes;
+  q.o_lmask = q.o_state + (size_t)q.gen_warps * (size_t)q.state_bytes;
+  q.bytes = q.o_lmask + 16u * (size_t)lane_cap * (size_t)q.smax;
   return q;
 }
 // First-phase fields of a launch over `buf` (the plan's block).
@@ -1256,6 +1261,7 @@ int mpld::split_phase2_launch(const LaunchArgs &a1, const InstDesc *desc, const 
   a.hard_cap = q.cap;
   a.par_buf = buf + q.o_ctx;
   a.split_scratch = q.state_bytes ? buf + q.o_state : nullptr;
+  a.lane_masks = (unsigned long long *)(buf + q.o_lmask);
   a.split_gen_warps = q.gen_warps;
   a.smax = q.smax;
   a.split_state_bytes = q.state_bytes;

@@ -230,6 +230,9 @@ struct LaunchArgs {
   uint8_t *split_scratch = nullptr;  // par == 4: per-warp global search state for instances
                                      // beyond the register form (split_state_bytes per warp)
   int32_t smax = 0;        // par == 4: item numbers per hard-list entry (>= its subtrees)
+  // par == 4: per item of the lanes' list (entry * smax + subtree), the masks
+  // of its best leaf, two bits per segment as two words (bit 0, bit 1)
+  unsigned long long *lane_masks = nullptr;
   int32_t split_state_bytes = 0;
 };
 

@@ -37,6 +37,7 @@ struct SplitPlan {
   int gen_warps = 0;                // warps with such a region
   int cap = 0;                      // entries of each hard list (the launch's descriptors)
   size_t o_hard = 0, o_ctx = 0, o_state = 0, bytes = 0;
+  size_t o_lmask = 0;               // best-leaf masks of the lanes' items (16 bytes each)
 };
 // Plan for the descriptors of one launch; the general-state regions take at
 // most gen_cap_bytes (fewer warps get one).  on = false unless prm asks for

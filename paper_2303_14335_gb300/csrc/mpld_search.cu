@@ -1975,6 +1975,7 @@ struct LaneOut {
   int32_t best;
   bool found, hit, timed_out;
   int64_t nodes, work;
+  unsigned long long m0, m1;   // found: the best leaf's masks, bit 0 and bit 1 per segment
 };
 
 template <typename W> __device__ __forceinline__ int popcw(W x) {
@@ -2018,7 +2019,7 @@ template <typename W> struct LaneStack {
 
 template <typename W, int K, int RULE>
 __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, int cut,
-                                         uint32_t prefix, int32_t thr0, int64_t budget, bool replay,
+                                         uint32_t prefix, int32_t thr0, int64_t budget,
                                          int64_t time_limit_ns, uint64_t t0, LaneOut &o) {
   const int n = d.n;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
@@ -2040,6 +2041,7 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
   int level = 0;
   int64_t nodes = 0, work = 0, next_check = 1024;
   bool found = false, hit = false, tout = false;
+  W m0 = 0, m1 = 0;
   auto count_pruned = [&](int m) -> bool {
     const int64_t room = budget > 0 ? budget - nodes : (int64_t)m;
     nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
@@ -2064,16 +2066,16 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
       if (unc == 0) {
         // leaf: every primary column covered
         if (g < thr) {
+          // this leaf's masks: the leaf that sets the final bound is the
+          // first one in depth-first order at that cost, the one a search of
+          // this subtree bounded by that cost plus one would take first
           thr = g;
           found = true;
-          if (replay) {
-            for (int v = 0; v < n; ++v) {
-              int m = 0;
-#pragma unroll
-              for (int c = 1; c < K; ++c) m = (asg[c] >> v) & one ? c : m;
-              d.mask[v] = (int8_t)m;
-            }
-            break;
+          m0 = asg[1];
+          m1 = K > 2 ? asg[K > 2 ? 2 : 1] : (W)0;
+          if constexpr (K == 4) {
+            m0 |= asg[3];
+            m1 |= asg[3];
           }
           if (g == 0) break;
         }
@@ -2179,30 +2181,32 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
   o.timed_out = tout;
   o.nodes = nodes;
   o.work = work;
+  o.m0 = (unsigned long long)m0;
+  o.m1 = (unsigned long long)m1;
 }
 
 template <typename W>
 __device__ __forceinline__ void lane_dispatch_w(const InstDesc &d, int rule, int cut,
                                                 uint32_t prefix, int32_t thr0, int64_t budget,
-                                                bool replay, int64_t tl, uint64_t t0, LaneOut &o) {
+                                                int64_t tl, uint64_t t0, LaneOut &o) {
   const uint8_t *ro = d.ro;
   if (d.k == 3) {
-    if (rule) lane_search<W, 3, 1>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
-    else lane_search<W, 3, 0>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
+    if (rule) lane_search<W, 3, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
+    else lane_search<W, 3, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
   } else if (d.k == 4) {
-    if (rule) lane_search<W, 4, 1>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
-    else lane_search<W, 4, 0>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
+    if (rule) lane_search<W, 4, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
+    else lane_search<W, 4, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
   } else {
-    if (rule) lane_search<W, 2, 1>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
-    else lane_search<W, 2, 0>(d, ro, cut, prefix, thr0, budget, replay, tl, t0, o);
+    if (rule) lane_search<W, 2, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
+    else lane_search<W, 2, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
   }
 }
 
 __device__ __noinline__ void lane_dispatch(const InstDesc &d, int rule, int cut, uint32_t prefix,
-                                           int32_t thr0, int64_t budget, bool replay, int64_t tl,
-                                           uint64_t t0, LaneOut &o) {
-  if (d.n <= 32) lane_dispatch_w<uint32_t>(d, rule, cut, prefix, thr0, budget, replay, tl, t0, o);
-  else lane_dispatch_w<unsigned long long>(d, rule, cut, prefix, thr0, budget, replay, tl, t0, o);
+                                           int32_t thr0, int64_t budget, int64_t tl, uint64_t t0,
+                                           LaneOut &o) {
+  if (d.n <= 32) lane_dispatch_w<uint32_t>(d, rule, cut, prefix, thr0, budget, tl, t0, o);
+  else lane_dispatch_w<unsigned long long>(d, rule, cut, prefix, thr0, budget, tl, t0, o);
 }
 
 // The instance's result once its last subtree is done (one thread): the
@@ -2611,9 +2615,13 @@ __global__ void __launch_bounds__(1024, 1) mpld_lane_kernel(const LaunchArgs a) 
     const unsigned long long prev = atomicCAS(&ctx->t0, 0ull, (unsigned long long)now);
     const uint64_t t0 = prev != 0ull ? (uint64_t)prev : now;
     LaneOut o;
-    lane_dispatch(d, a.rule, D, s, (int32_t)c1 + (s < s1 ? 1 : 0), b, false, a.time_limit_ns,
-                  t0, o);
-    if (o.found) atomicMin(&ctx->key, ((unsigned long long)(uint32_t)o.best << 32) | s);
+    lane_dispatch(d, a.rule, D, s, (int32_t)c1 + (s < s1 ? 1 : 0), b, a.time_limit_ns, t0, o);
+    unsigned long long *slot = a.lane_masks + 2u * ((size_t)j * (size_t)a.smax + s);
+    if (o.found) {
+      slot[0] = o.m0;
+      slot[1] = o.m1;
+      atomicMin(&ctx->key, ((unsigned long long)(uint32_t)o.best << 32) | s);
+    }
     atomicAdd(&ctx->nodes, (unsigned long long)o.nodes);
     atomicAdd(&ctx->work, (unsigned long long)o.work);
     if (o.timed_out) atomicExch(&ctx->timed_out, 1u);
@@ -2622,16 +2630,17 @@ __global__ void __launch_bounds__(1024, 1) mpld_lane_kernel(const LaunchArgs a) 
     if (atomicAdd(&ctx->done, 1u) != S - 1u) continue;
     // this thread completed the instance's last subtree
     __threadfence();
-    unsigned long long key = *(volatile unsigned long long *)&ctx->key;
-    bool ok = true;
+    const unsigned long long key = *(volatile unsigned long long *)&ctx->key;
     if (key != key1) {
-      LaneOut r;
-      lane_dispatch(d, a.rule, D, (uint32_t)(key & 0xFFFFFFFFull), (int32_t)(key >> 32) + 1, 0,
-                    true, a.time_limit_ns, globaltimer(), r);
-      ok = r.found;
-      if (!ok) key = key1;
+      // the winning subtree's leaf (its item wrote the slot before counting
+      // itself done): mask of segment v = bit v of word 0 + 2 * bit v of word 1
+      const unsigned long long *w =
+          a.lane_masks + 2u * ((size_t)j * (size_t)a.smax + (size_t)(key & 0xFFFFFFFFull));
+      const unsigned long long w0 = __ldcg(w), w1 = __ldcg(w + 1);
+      for (int v = 0; v < d.n; ++v)
+        d.mask[v] = (int8_t)(((w0 >> v) & 1ull) | (((w1 >> v) & 1ull) << 1));
     }
-    split_write_result(d, ctx, key, ok);
+    split_write_result(d, ctx, key, true);
   }
 }
 
