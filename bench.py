@@ -46,16 +46,17 @@ if HERE not in sys.path:
 
 METRIC = "EC search nodes/s & segments/s (batched vs plain GPU vs CPU DLX); p99 latency"
 
-# DRAM bytes per launch of the dominant kernel (the budgeted split search's
-# second launch) from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the workload scaled down by 10 (23,960 segments:
-# 3,635,456 B read, 539,392 B written), per segment; traffic grows with the
-# instances, i.e. with the segments.  Valid only for the kernel source and
-# search mode it was measured on.
-TRAFFIC = {"k3_n200k_p02_batched": {"bytes_per_segment": (3635456 + 539392) / 23960,
-                                    "kernel_sha256_16": "13bdaf91994664c0",
+# DRAM bytes of one step (the budgeted split search's three launches: first
+# searches, the lanes' subtrees, the warps' subtrees) from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum per launch) on the workload
+# scaled down by 10 (23,960 segments: 439,296 + 256, 597,504 + 59,648 and
+# 68,352 + 0 bytes), per segment; traffic grows with the instances, i.e. with
+# the segments.  Valid only for the kernel source and search mode it was
+# measured on.
+TRAFFIC = {"k3_n200k_p02_batched": {"bytes_per_segment": (439296 + 256 + 597504 + 59648 + 68352) / 23960,
+                                    "kernel_sha256_16": "43b80edfd9659a06",
                                     "split_budget": True,
-                                    "profile": "profiles/mpld_search_kernel_split_k3_n20k_budget64k.md"}}
+                                    "profile": "profiles/split_step_traffic_k3_n20k_budget64k.md"}}
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 
 
@@ -676,8 +677,8 @@ def main():
             traffic = tr["bytes_per_segment"] * layout.n_seg
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak_gops,
                        "unit": "Gop/s", "frac": achieved / alu_peak_gops, "traffic": traffic,
-                       "traffic_source": ("ncu capture at 1/10 scale, scaled by segments"
-                                          if traffic is not None else None),
+                       "traffic_source": ("ncu capture of the step's three launches at 1/10 scale, "
+                                          "scaled by segments" if traffic is not None else None),
                        "peak_source": f"{props.multi_processor_count} SMs x 64 int32 ops per clock x "
                                       f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json); "
                                       "derived, see int_pipes_measured",

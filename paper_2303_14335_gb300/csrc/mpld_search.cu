@@ -196,13 +196,15 @@ struct CtaTeam {
 
 // Column classes of a giant instance, for a column choice that does not scan
 // every segment: per count class m (0..k), a bit per segment that is
-// uncovered with exactly m active rows, a summary bit per non-empty 32-bit
-// word of it, and the class size; under column rule 1 also a bit per
-// breadth-first rank that is uncovered, with its summary.  The fewest-rows
-// column is then the lowest set bit of the first non-empty class (lowest
-// index on ties, as the scan gives), found through the summary; covers and
-// undos move only the segment and its neighbours between classes.  One warp
-// keeps them in shared memory.
+// uncovered with exactly m active rows, a summary bit per 32-bit word of it
+// that may be non-zero (set when a segment joins the word; a bit whose word
+// has emptied is cleared when the column choice meets it), and the class
+// size; under column rule 1 also a bit per breadth-first rank that is
+// uncovered, with an exact summary.  The fewest-rows column is then the
+// lowest set bit of the first non-empty class (lowest index on ties, as the
+// scan gives), found through the summary; covers and undos move only the
+// segment and its neighbours between classes, with atomics whose results
+// nothing waits for.  One warp keeps them in shared memory.
 struct Buckets {
   uint32_t *cls;   // [k+1][w32]
   uint32_t *sum;   // [k+1][s32]
@@ -254,15 +256,40 @@ struct Buckets {
     if (b >= 0) {
       atomicOr(&cls[b * w32 + w], bit);
       atomicAdd(&cnt[b], 1);
+      atomicOr(&sum[b * s32 + (w >> 5)], 1u << (w & 31));
     }
   }
-  // after the moves (and a __syncwarp): the summary bit of v's word in class m
-  __device__ __forceinline__ void fix(int v, int m) const {
-    if (m < 0) return;
-    const int w = v >> 5;
-    const uint32_t sb = 1u << (w & 31);
-    if (cls[m * w32 + w]) atomicOr(&sum[m * s32 + (w >> 5)], sb);
-    else atomicAnd(&sum[m * s32 + (w >> 5)], ~sb);
+  // lowest segment of class m, which is not empty (every lane gets it);
+  // summary bits met on the way whose word has emptied are cleared
+  __device__ __forceinline__ int lowest_in(int m, int lane) const {
+    uint32_t *sm = sum + m * s32;
+    const uint32_t *bm = cls + m * w32;
+    for (int base = 0; base < s32;) {
+      const uint32_t sv = base + lane < s32 ? sm[base + lane] : 0u;
+      const uint32_t nz = __ballot_sync(FULL, sv != 0u);
+      if (!nz) {
+        base += 32;
+        continue;
+      }
+      const int l = __ffs(nz) - 1;
+      uint32_t s0 = __shfl_sync(FULL, sv, l);
+      bool stale = false;
+      while (s0) {
+        const int j = __ffs(s0) - 1;
+        const int w = (base + l) * 32 + j;
+        const uint32_t wv = bm[w];
+        if (wv) {
+          // a cleared bit is ordered before the moves of the next cover
+          if (stale) __syncwarp();
+          return w * 32 + __ffs(wv) - 1;
+        }
+        if (lane == 0) atomicAnd(&sm[base + l], ~(1u << j));
+        stale = true;
+        s0 &= s0 - 1u;
+      }
+      __syncwarp();   // every bit of this summary word was stale: read it again
+    }
+    return -1;
   }
   __device__ __forceinline__ void rank_set(int r, bool on) const {
     const uint32_t bit = 1u << (r & 31);
@@ -394,8 +421,10 @@ struct Search {
   // First row (v, c) of v's column: save and clear v's field (column P_v
   // and all its rows), clear bit c of every conflict neighbour (column
   // S_{(v,u),c}) saving its field, and count mask c at every neighbour.
+  // upre / spre: this lane's first conflict / stitch neighbour when the
+  // caller has loaded it already (BK), else -1.
   __device__ __forceinline__ void cover_first(int v, int c, int cb, int dc, int sb, int ds,
-                                              int lane) const {
+                                              int lane, int upre = -1, int spre = -1) const {
     if (lane == 0) {
       const FT fv = rows[v];
       oldf[v] = fv;
@@ -408,35 +437,19 @@ struct Search {
     }
     const uint32_t clr = ~(1u << c);
     if constexpr (BK) {
-      // each lane keeps its first neighbour and that neighbour's saved
-      // field for the summary fix below (no second read of either)
-      int u0 = 0;
-      FT f0 = 0;
       each(dc, lane, [&](int i) {
-        const int u = ro_ld<SM>(cnbr + cb + i);
+        const int u = (i == lane && upre >= 0) ? upre : (int)ro_ld<SM>(cnbr + cb + i);
         const FT f = rows[u];
         savf[cb + i] = f;
         rows[u] = (FT)(f & clr);
         if (bcc) bcc[u] += 1u << (8 * c);
         else move_count(ccnt, u, c, -1);
         bk.move(u, cls_of(f), cls_of(f & clr));
-        if (i == lane) {
-          u0 = u;
-          f0 = f;
-        }
       });
       each(ds, lane, [&](int i) {
-        const int u = ro_ld<SM>(snbr + sb + i);
+        const int u = (i == lane && spre >= 0) ? spre : (int)ro_ld<SM>(snbr + sb + i);
         if (bsc) bsc[u] += 1u << (8 * c);
         else move_count(scnt, u, c, -1);
-      });
-      team.sync();
-      if (lane == 0) bk.fix(v, cls_of(oldf[v]));
-      each(dc, lane, [&](int i) {
-        const int u = i == lane ? u0 : (int)ro_ld<SM>(cnbr + cb + i);
-        const FT f = i == lane ? f0 : savf[cb + i];
-        bk.fix(u, cls_of(f));
-        bk.fix(u, cls_of(f & clr));
       });
       team.sync();
     } else {
@@ -472,15 +485,6 @@ struct Search {
       else move_count(scnt, u, c, c_old);
     });
     team.sync();
-    if constexpr (BK) {
-      each(dc, lane, [&](int i) {
-        const int u = ro_ld<SM>(cnbr + cb + i);
-        const FT f = savf[cb + i];
-        bk.fix(u, cls_of(f & clr_old));
-        bk.fix(u, cls_of(f & clr));
-      });
-      team.sync();
-    }
   }
 
   // Every row of v's column tried (the last was c_last): put v's field and
@@ -511,16 +515,6 @@ struct Search {
       else *cw_of(scnt, u, c_last) -= one(c_last);
     });
     team.sync();
-    if constexpr (BK) {
-      if (lane == 0) bk.fix(v, cls_of(oldf[v]));
-      each(dc, lane, [&](int i) {
-        const int u = ro_ld<SM>(cnbr + cb + i);
-        const FT f = savf[cb + i];
-        bk.fix(u, cls_of(f & clr_last));
-        bk.fix(u, cls_of(f));
-      });
-      team.sync();
-    }
   }
 
   __device__ __forceinline__ int run(int lane, int64_t budget, int64_t time_limit_ns,
@@ -590,10 +584,9 @@ struct Search {
             if (*(volatile int32_t *)&bk.cnt[m] > 0) m0 = m;
           if (m0 >= 0) {
             if (rule == 0) {
-              key = ((uint32_t)m0 << 16) | (uint32_t)bk.lowest(bk.cls + m0 * bk.w32,
-                                                             bk.sum + m0 * bk.s32, lane);
+              key = ((uint32_t)m0 << 16) | (uint32_t)bk.lowest_in(m0, lane);
             } else if (*(volatile int32_t *)&bk.cnt[1] > 0) {
-              key = (uint32_t)bk.lowest(bk.cls + bk.w32, bk.sum + bk.s32, lane);
+              key = (uint32_t)bk.lowest_in(1, lane);
             } else {
               key = 0x10000u | (uint32_t)bk.lowest(bk.ur, bk.urs, lane);
             }
@@ -669,6 +662,7 @@ struct Search {
                                                      : (int)ro_ld<SM>(order + (key & 0xFFFFu));
         // added cost of each row (v, c) against the current assignment (Eq. 1)
         int cb, dc, sb, ds;
+        int upre = -1, spre = -1;
         uint64_t cc0, sc0, cc1 = 0ull, sc1 = 0ull;
         if (BK && bcc) {
           const int v1 = v + 1;
@@ -678,6 +672,10 @@ struct Search {
           ds = sob[v1 >> 6] + (int)so16[v1] - sb;
           cc0 = widen8(bcc[v]);
           sc0 = widen8(bsc[v]);
+          // the cover below needs v's neighbour lists whichever row it takes:
+          // their loads overlap the row costs
+          if (lane < dc) upre = (int)ro_ld<SM>(cnbr + cb + lane);
+          if (lane < ds) spre = (int)ro_ld<SM>(snbr + sb + lane);
         } else {
           const int2 p0 = ro_ld<SM>(ptr + v), p1 = ro_ld<SM>(ptr + v + 1);
           cc0 = ccnt[(size_t)v * CW];
@@ -746,7 +744,7 @@ struct Search {
           for (int i = 3; i < MK; ++i)
             if (i < k) lvx[level * MK + i] = (int32_t)(keys[i] >> 3);
         }
-        cover_first(v, (int)(ord & 7u), cb, dc, sb, ds, lane);
+        cover_first(v, (int)(ord & 7u), cb, dc, sb, ds, lane, upre, spre);
         if (nq > 0) {
           if (lane == 0) qlev[level] = untouched - left;
           clique_move(v, 1);
@@ -2590,7 +2588,11 @@ extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes) {
 namespace mpld {
 namespace {
 
-__global__ void __launch_bounds__(1024, 1) mpld_lane_kernel(const LaunchArgs a) {
+// threads per block and resident blocks per SM the lane kernel is built for
+constexpr int LANE_BLOCK = 1024, LANE_BLOCKS_PER_SM = 1;
+
+__global__ void __launch_bounds__(LANE_BLOCK, LANE_BLOCKS_PER_SM)
+    mpld_lane_kernel(const LaunchArgs a) {
   uint32_t HL = (uint32_t)*(volatile int32_t *)(a.hard + 1);
   if (HL == 0) return;
   const int32_t *list_l = a.hard + 4 + a.hard_cap;
@@ -2651,7 +2653,8 @@ extern "C" int mpld_internal_launch_lanes(const LaunchArgs *a, void *stream) {
   static int blocks = 0;   // resident blocks of the lane kernel (one query per process)
   if (blocks == 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpld::mpld_lane_kernel, 1024, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpld::mpld_lane_kernel,
+                                                      mpld::LANE_BLOCK, 0) !=
             cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
@@ -2659,7 +2662,7 @@ extern "C" int mpld_internal_launch_lanes(const LaunchArgs *a, void *stream) {
     }
     blocks = per_sm * std::max(1, mpld_internal_num_sms());
   }
-  mpld::mpld_lane_kernel<<<blocks, 1024, 0, (cudaStream_t)stream>>>(*a);
+  mpld::mpld_lane_kernel<<<blocks, mpld::LANE_BLOCK, 0, (cudaStream_t)stream>>>(*a);
   return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
 }
 
