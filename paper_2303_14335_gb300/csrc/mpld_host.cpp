@@ -1265,10 +1265,12 @@ int mpld::split_phase2_launch(const LaunchArgs &a1, const InstDesc *desc, const 
   a.split_gen_warps = q.gen_warps;
   a.smax = q.smax;
   a.split_state_bytes = q.state_bytes;
-  // the lanes' subtrees in a kernel of their own, then the warps'
+  // the lanes' subtrees in a kernel of their own, then the warps' (other
+  // instances, other counters): that launch's blocks take SMs as the lanes'
+  // blocks finish, and it completes only after the lanes' kernel
   const int rc = mpld_internal_launch_lanes(&a, st);
   if (rc) return rc;
-  return mpld_internal_launch(&a, q.ctas, q.nw, st);
+  return mpld_internal_launch_overlapped(&a, q.ctas, q.nw, st);
 }
 
 namespace {

@@ -301,3 +301,5 @@ extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes);
 extern "C" int mpld_internal_num_sms(void);
 // The budgeted split search's per-lane subtree searches (the lanes' hard list).
 extern "C" int mpld_internal_launch_lanes(const mpld::LaunchArgs *a, void *stream);
+extern "C" int mpld_internal_launch_overlapped(const mpld::LaunchArgs *a, int ctas,
+                                              int warps_per_cta, void *stream);

@@ -94,6 +94,17 @@ template <> __device__ __forceinline__ void sort_keys<8>(uint32_t (&k)[8]) {
   cas_u32(k[1], k[2]); cas_u32(k[3], k[4]); cas_u32(k[5], k[6]);
 }
 
+// Programmatic dependent launch: let the grid launched after this one (with
+// programmatic stream serialization) start its blocks as SMs free up, and,
+// in that grid, wait until the grids before it have completed and their
+// memory is visible.  Both return at once when no such launch is involved.
+__device__ __forceinline__ void launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;");
+}
+__device__ __forceinline__ void wait_prerequisites() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -2433,6 +2444,10 @@ __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a)
   }
   if (a.par == 4) {
     run_split_phase2(a, lane, warp, nw, g_smem + slot_off);
+    // this launch may have started beside the lanes' kernel before it (its
+    // blocks take SMs as the lanes' blocks finish): it completes only after
+    // that kernel, so what follows on the stream sees both
+    wait_prerequisites();
     return;
   }
 
@@ -2549,6 +2564,30 @@ extern "C" int mpld_internal_launch(const LaunchArgs *a, int ctas, int warps_per
   return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
 }
 
+// The same launch, allowed to start before the kernel before it on the stream
+// completes (programmatic stream serialization): its blocks are scheduled as
+// that kernel's blocks leave SMs.  Only for a kernel that reads nothing the
+// previous one writes and waits for it before it exits (par == 4).
+extern "C" int mpld_internal_launch_overlapped(const LaunchArgs *a, int ctas, int warps_per_cta,
+                                              void *stream) {
+  const size_t smem = mpld::kernel_head_bytes(warps_per_cta) +
+                      (size_t)warps_per_cta * (size_t)(a->slot_bytes > 0 ? a->slot_bytes : 0);
+  if (mpld::ensure_smem(smem) != MPLD_OK) return MPLD_E_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3((unsigned)(warps_per_cta * 32));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const LaunchArgs args = *a;
+  return cudaLaunchKernelEx(&cfg, mpld::mpld_search_kernel, args) == cudaSuccess ? MPLD_OK
+                                                                                 : MPLD_E_CUDA;
+}
+
 extern "C" int mpld_internal_num_sms(void) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -2593,6 +2632,8 @@ constexpr int LANE_BLOCK = 1024, LANE_BLOCKS_PER_SM = 1;
 
 __global__ void __launch_bounds__(LANE_BLOCK, LANE_BLOCKS_PER_SM)
     mpld_lane_kernel(const LaunchArgs a) {
+  // the warps' subtree launch that follows may take SMs as these blocks finish
+  launch_dependents();
   uint32_t HL = (uint32_t)*(volatile int32_t *)(a.hard + 1);
   if (HL == 0) return;
   const int32_t *list_l = a.hard + 4 + a.hard_cap;
