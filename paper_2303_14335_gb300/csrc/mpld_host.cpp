@@ -1240,6 +1240,38 @@ void mpld::split_phase1_args(LaunchArgs &a, const SplitPlan &q, uint8_t *buf) {
   a.hard_cap = q.cap;
   a.par_buf = q.on ? buf + q.o_ctx : a.par_buf;
 }
+int mpld::split_warp_prefix(const InstDesc *h_desc, const int32_t *h_order, int n, int n_large) {
+  auto lane = [&](int i) {
+    const InstDesc &d = h_desc[h_order[i]];
+    return d.n <= SPLIT_MAX_N && split_list_of(d.n, d.k) == 1;
+  };
+  int p = 0;
+  while (p < n && !lane(p)) ++p;
+  for (int i = p; i < n; ++i)
+    if (!lane(i)) return n;
+  return std::max(p, std::min(n_large, n));
+}
+int mpld::split_phase1_launch(const LaunchArgs &a, int ctas, int nw, int n_w, cudaStream_t st) {
+  if (a.n_inst == 0) return MPLD_OK;
+  int rc = MPLD_OK, c = 0;
+  if (n_w > 0) {
+    LaunchArgs w = a;
+    w.n_inst = n_w;
+    c = std::max(1, std::min(ctas, a.n_large + (n_w - a.n_large + nw - 1) / nw));
+    rc = mpld_internal_launch(&w, c, nw, st);
+  }
+  if (rc || n_w >= a.n_inst) return rc;
+  LaunchArgs l = a;
+  l.order = a.order + n_w;
+  l.n_inst = a.n_inst - n_w;
+  l.n_large = 0;
+  l.lane_phase1 = 1;
+  if (n_w == 0) return mpld_internal_launch_lanes(&l, st);
+  // a lane block takes a whole SM: one per SM the warps' CTAs leave free, so
+  // that no block (and none of the instances it holds) waits for them
+  const int sms = std::max(1, mpld_internal_num_sms());
+  return mpld_internal_launch_lanes_overlapped(&l, c < sms ? sms - c : 0, st);
+}
 // Reset the hard lists before the first phase.
 int mpld::split_reset(const SplitPlan &q, uint8_t *buf, cudaStream_t st) {
   return cudaMemsetAsync(buf + q.o_hard, 0, 16, st) == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
@@ -1309,12 +1341,15 @@ int ensure_split_buf(mpld_problem *p, size_t bytes) {
   p->split_bytes = bytes;
   return MPLD_OK;
 }
+// n_w (budgeted split search): the first n_w entries of the order go to the
+// warps, the rest to the lane kernel beside them (n_w < 0: all to the warps)
 int launch_batch(const mpld::LaunchArgs &a, const Shape &sh, cudaStream_t st, uint32_t *queue,
-                 int32_t *err) {
+                 int32_t *err, int n_w = -1) {
   int rc = cuda_ok(cudaMemsetAsync(queue, 0, 8, st));   // both work counters
   rc |= cuda_ok(cudaMemsetAsync(err, 0, 4, st));
   if (rc) return MPLD_E_CUDA;
   if (a.n_inst == 0) return MPLD_OK;
+  if (a.split && n_w >= 0 && n_w < a.n_inst) return mpld::split_phase1_launch(a, sh.ctas, sh.nw, n_w, st);
   const int ctas = std::min(sh.ctas, a.n_large + (a.n_inst - a.n_large + sh.nw - 1) / sh.nw);
   return mpld_internal_launch(&a, std::max(ctas, 1), sh.nw, st);
 }
@@ -1368,7 +1403,9 @@ int enqueue_single(mpld_problem *p, const mpld_params *prm, void *stream, bool c
     if (sp.on) {
       // the first phase over every instance, then the subtrees of the hard ones
       rc = mpld::split_reset(sp, p->d_split, st);
-      rc |= launch_batch(a, sh, st, p->d_queue, p->d_err);
+      rc |= launch_batch(a, sh, st, p->d_queue, p->d_err,
+                         mpld::split_warp_prefix(p->h_desc.data(), p->h_order.data(), p->n_comp,
+                                                 n_large));
       if (rc == MPLD_OK) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
     } else if (gs.on) {
       rc = cuda_ok(cudaMemsetAsync(p->d_err, 0, 4, st));
@@ -1771,7 +1808,9 @@ extern "C" int mpld_search_batch_async(mpld_problem *const *ps, int32_t n, const
     // the first phase over every instance, then the subtrees of the hard ones
     split_phase1(a, sp, b + o_split);
     rc = mpld::split_reset(sp, b + o_split, st);
-    if (!rc) rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
+    if (!rc)
+      rc = launch_batch(a, sh, st, queue, ps[0]->d_err,
+                        mpld::split_warp_prefix(desc.data(), order.data(), n_rest, n_large));
     if (!rc) rc = launch_split_phase2(a, a.desc, sp, b + o_split, queue, st);
   } else if (!rc) {
     rc = launch_batch(a, sh, st, queue, ps[0]->d_err);
@@ -1885,7 +1924,9 @@ extern "C" int mpld_search_subset_async(mpld_problem *p, const mpld_params *prm,
   if (!rc && sp.on) {
     split_phase1(a, sp, p->d_split);
     rc = mpld::split_reset(sp, p->d_split, st);
-    if (!rc) rc = launch_batch(a, sh, st, p->d_queue, p->d_err);
+    if (!rc)
+      rc = launch_batch(a, sh, st, p->d_queue, p->d_err,
+                        mpld::split_warp_prefix(p->h_desc.data(), order.data(), n, n_large));
     if (!rc) rc = launch_split_phase2(a, p->d_desc, sp, p->d_split, p->d_queue, st);
   } else if (!rc) {
     rc = launch_batch(a, sh, st, p->d_queue, p->d_err);

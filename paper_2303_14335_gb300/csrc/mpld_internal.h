@@ -233,6 +233,9 @@ struct LaunchArgs {
   // par == 4: per item of the lanes' list (entry * smax + subtree), the masks
   // of its best leaf, two bits per segment as two words (bit 0, bit 1)
   unsigned long long *lane_masks = nullptr;
+  // lane kernel: 1 = the budgeted split search's first search of the
+  // per-lane instances desc[order[0..n_inst)] (0 = their subtrees)
+  int32_t lane_phase1 = 0;
   int32_t split_state_bytes = 0;
 };
 
@@ -301,5 +304,7 @@ extern "C" int mpld_internal_ctas_per_sm(int warps_per_cta, int slot_bytes);
 extern "C" int mpld_internal_num_sms(void);
 // The budgeted split search's per-lane subtree searches (the lanes' hard list).
 extern "C" int mpld_internal_launch_lanes(const mpld::LaunchArgs *a, void *stream);
+extern "C" int mpld_internal_launch_lanes_overlapped(const mpld::LaunchArgs *a, int blocks,
+                                                    void *stream);
 extern "C" int mpld_internal_launch_overlapped(const mpld::LaunchArgs *a, int ctas,
                                               int warps_per_cta, void *stream);

@@ -48,6 +48,15 @@ void split_phase1_args(LaunchArgs &a, const SplitPlan &q, uint8_t *buf);
 int split_reset(const SplitPlan &q, uint8_t *buf, cudaStream_t st);
 int split_phase2_launch(const LaunchArgs &a1, const InstDesc *desc, const SplitPlan &q,
                         uint8_t *buf, uint32_t *queue, cudaStream_t st);
+// First phase: how many leading entries of the largest-first order h_order
+// the warps' forms take (at least the n_large whole-CTA instances); every
+// later entry is an instance of the per-lane form.  n when the order does
+// not split that way (then the warps take every instance).
+int split_warp_prefix(const InstDesc *h_desc, const int32_t *h_order, int n, int n_large);
+// First phase over desc[order[0..a.n_inst)]: the warps' searches of the first
+// n_w entries (at most ctas CTAs of nw warps), and the lane kernel's of the
+// rest beside them.
+int split_phase1_launch(const LaunchArgs &a, int ctas, int nw, int n_w, cudaStream_t st);
 
 }  // namespace mpld
 

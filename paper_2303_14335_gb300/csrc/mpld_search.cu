@@ -1985,6 +1985,7 @@ struct LaneOut {
   bool found, hit, timed_out;
   int64_t nodes, work;
   unsigned long long m0, m1;   // found: the best leaf's masks, bit 0 and bit 1 per segment
+  uint32_t sub;                // track > 0: subtree of the best leaf (its first `track` row places)
 };
 
 template <typename W> __device__ __forceinline__ int popcw(W x) {
@@ -2026,10 +2027,14 @@ template <typename W> struct LaneStack {
   __device__ __forceinline__ W &s(int l) { return ss[l]; }
 };
 
+// cut / prefix: the forced levels of a subtree search (cut = 0: the whole
+// tree); track: the whole tree's first search of the budgeted split search,
+// whose best leaf's subtree (row places of the first `track` levels) is kept.
 template <typename W, int K, int RULE>
 __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, int cut,
                                          uint32_t prefix, int32_t thr0, int64_t budget,
-                                         int64_t time_limit_ns, uint64_t t0, LaneOut &o) {
+                                         int64_t time_limit_ns, uint64_t t0, int track,
+                                         LaneOut &o) {
   const int n = d.n;
   const int Cc = d.cost_conflict, Cs = d.cost_stitch;
   const RoLayout R = ro_layout(n, d.ne2, d.ns2, 0);
@@ -2051,6 +2056,7 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
   int64_t nodes = 0, work = 0, next_check = 1024;
   bool found = false, hit = false, tout = false;
   W m0 = 0, m1 = 0;
+  uint32_t sub = 0;
   auto count_pruned = [&](int m) -> bool {
     const int64_t room = budget > 0 ? budget - nodes : (int64_t)m;
     nodes += room < m ? (room > 0 ? room : 0) : (int64_t)m;
@@ -2065,7 +2071,8 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
   for (;;) {
     if (enter) {
       // ---- a node ----
-      if (budget > 0 && nodes >= budget) { hit = true; break; }
+      // the budget stops a search once it has an incumbent
+      if (budget > 0 && thr < INF32 && nodes >= budget) { hit = true; break; }
       ++nodes;
       work += 2 * (n - level);
       if (nodes >= next_check) {
@@ -2085,6 +2092,10 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
           if constexpr (K == 4) {
             m0 |= asg[3];
             m1 |= asg[3];
+          }
+          if (track > 0) {
+            sub = 0;
+            for (int i = 0; i < track; ++i) sub = sub * (uint32_t)K + ((st.h(i) >> 8) & 0xFu);
           }
           if (g == 0) break;
         }
@@ -2192,30 +2203,31 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
   o.work = work;
   o.m0 = (unsigned long long)m0;
   o.m1 = (unsigned long long)m1;
+  o.sub = sub;
 }
 
 template <typename W>
 __device__ __forceinline__ void lane_dispatch_w(const InstDesc &d, int rule, int cut,
                                                 uint32_t prefix, int32_t thr0, int64_t budget,
-                                                int64_t tl, uint64_t t0, LaneOut &o) {
+                                                int64_t tl, uint64_t t0, int track, LaneOut &o) {
   const uint8_t *ro = d.ro;
   if (d.k == 3) {
-    if (rule) lane_search<W, 3, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
-    else lane_search<W, 3, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
+    if (rule) lane_search<W, 3, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, track, o);
+    else lane_search<W, 3, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, track, o);
   } else if (d.k == 4) {
-    if (rule) lane_search<W, 4, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
-    else lane_search<W, 4, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
+    if (rule) lane_search<W, 4, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, track, o);
+    else lane_search<W, 4, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, track, o);
   } else {
-    if (rule) lane_search<W, 2, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
-    else lane_search<W, 2, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, o);
+    if (rule) lane_search<W, 2, 1>(d, ro, cut, prefix, thr0, budget, tl, t0, track, o);
+    else lane_search<W, 2, 0>(d, ro, cut, prefix, thr0, budget, tl, t0, track, o);
   }
 }
 
 __device__ __noinline__ void lane_dispatch(const InstDesc &d, int rule, int cut, uint32_t prefix,
                                            int32_t thr0, int64_t budget, int64_t tl, uint64_t t0,
-                                           LaneOut &o) {
-  if (d.n <= 32) lane_dispatch_w<uint32_t>(d, rule, cut, prefix, thr0, budget, tl, t0, o);
-  else lane_dispatch_w<unsigned long long>(d, rule, cut, prefix, thr0, budget, tl, t0, o);
+                                           int track, LaneOut &o) {
+  if (d.n <= 32) lane_dispatch_w<uint32_t>(d, rule, cut, prefix, thr0, budget, tl, t0, track, o);
+  else lane_dispatch_w<unsigned long long>(d, rule, cut, prefix, thr0, budget, tl, t0, track, o);
 }
 
 // The instance's result once its last subtree is done (one thread): the
@@ -2418,6 +2430,9 @@ __device__ __noinline__ void run_grid_split(const LaunchArgs &a, int lane, int w
 }
 
 __global__ void __launch_bounds__(512, 1) mpld_search_kernel(const LaunchArgs a) {
+  // a launch after this one that reads nothing it writes (the per-lane
+  // first searches) may take SMs as its blocks finish
+  launch_dependents();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
@@ -2632,6 +2647,37 @@ constexpr int LANE_BLOCK = 1024, LANE_BLOCKS_PER_SM = 1;
 
 __global__ void __launch_bounds__(LANE_BLOCK, LANE_BLOCKS_PER_SM)
     mpld_lane_kernel(const LaunchArgs a) {
+  if (a.lane_phase1) {
+    // the budgeted split search's first search of the per-lane instances
+    // desc[order[0..n_inst)], one per thread: instance l * W + w goes to lane
+    // l of warp w (W warps in the grid), so each warp holds about n_inst / W
+    // of them; written as the warps' first search writes them.  This launch
+    // may run beside the warps' first searches launched before it, and
+    // completes only after them.
+    const uint32_t W = gridDim.x * (blockDim.x >> 5);
+    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (uint32_t i = (threadIdx.x & 31u) * W + gw; i < (uint32_t)a.n_inst; i += 32u * W) {
+      const InstDesc d = a.desc[a.order[i]];
+      int D;
+      uint32_t S;
+      split_cut(d.n, d.k, D, S);
+      LaneOut o;
+      lane_dispatch(d, a.rule, 0, 0u, INF32, split_search_budget(a.budget, S), a.time_limit_ns,
+                    globaltimer(), D, o);
+      if (o.found)
+        for (int v = 0; v < d.n; ++v)
+          d.mask[v] = (int8_t)(((o.m0 >> v) & 1ull) | (((o.m1 >> v) & 1ull) << 1));
+      const int st = o.timed_out ? MPLD_TIMEOUT : o.hit ? MPLD_BUDGET : MPLD_OK;
+      d.res->cost = o.found ? (int64_t)o.best : INT64_MAX;
+      d.res->nodes = o.nodes;
+      d.res->status = st;
+      d.res->sub = (int32_t)o.sub;
+      d.res->work = o.work;
+      if (st == MPLD_BUDGET) split_enlist(a, d, o.best, o.sub);
+    }
+    wait_prerequisites();
+    return;
+  }
   // the warps' subtree launch that follows may take SMs as these blocks finish
   launch_dependents();
   uint32_t HL = (uint32_t)*(volatile int32_t *)(a.hard + 1);
@@ -2658,7 +2704,7 @@ __global__ void __launch_bounds__(LANE_BLOCK, LANE_BLOCKS_PER_SM)
     const unsigned long long prev = atomicCAS(&ctx->t0, 0ull, (unsigned long long)now);
     const uint64_t t0 = prev != 0ull ? (uint64_t)prev : now;
     LaneOut o;
-    lane_dispatch(d, a.rule, D, s, (int32_t)c1 + (s < s1 ? 1 : 0), b, a.time_limit_ns, t0, o);
+    lane_dispatch(d, a.rule, D, s, (int32_t)c1 + (s < s1 ? 1 : 0), b, a.time_limit_ns, t0, 0, o);
     unsigned long long *slot = a.lane_masks + 2u * ((size_t)j * (size_t)a.smax + s);
     if (o.found) {
       slot[0] = o.m0;
@@ -2690,21 +2736,47 @@ __global__ void __launch_bounds__(LANE_BLOCK, LANE_BLOCKS_PER_SM)
 }  // namespace
 }  // namespace mpld
 
-extern "C" int mpld_internal_launch_lanes(const LaunchArgs *a, void *stream) {
+namespace {
+int lane_blocks() {
   static int blocks = 0;   // resident blocks of the lane kernel (one query per process)
   if (blocks == 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpld::mpld_lane_kernel,
-                                                      mpld::LANE_BLOCK, 0) !=
-            cudaSuccess ||
+                                                      mpld::LANE_BLOCK, 0) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
     }
     blocks = per_sm * std::max(1, mpld_internal_num_sms());
   }
-  mpld::mpld_lane_kernel<<<blocks, mpld::LANE_BLOCK, 0, (cudaStream_t)stream>>>(*a);
+  return blocks;
+}
+}  // namespace
+
+extern "C" int mpld_internal_launch_lanes(const LaunchArgs *a, void *stream) {
+  mpld::mpld_lane_kernel<<<lane_blocks(), mpld::LANE_BLOCK, 0, (cudaStream_t)stream>>>(*a);
   return cudaGetLastError() == cudaSuccess ? MPLD_OK : MPLD_E_CUDA;
+}
+
+// The lane kernel allowed to start before the kernel before it completes
+// (programmatic stream serialization; the per-lane first searches beside
+// the warps' first searches, which read and write other instances), with
+// `blocks` blocks (0: one per resident place).
+extern "C" int mpld_internal_launch_lanes_overlapped(const LaunchArgs *a, int blocks,
+                                                    void *stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(blocks > 0 ? blocks : lane_blocks()));
+  cfg.blockDim = dim3((unsigned)mpld::LANE_BLOCK);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const LaunchArgs args = *a;
+  return cudaLaunchKernelEx(&cfg, mpld::mpld_lane_kernel, args) == cudaSuccess ? MPLD_OK
+                                                                               : MPLD_E_CUDA;
 }
 
 // ---- search of one instance without allocating --------------------------

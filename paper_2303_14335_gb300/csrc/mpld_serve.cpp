@@ -306,7 +306,9 @@ int launch_request(mpld_server *s, Req &r) {
     uint8_t *sb = base + S.split;
     mpld::split_phase1_args(a, r.split, sb);
     rc = mpld::split_reset(r.split, sb, st);
-    if (!rc) rc = mpld_internal_launch(&a, ctas, nw, st);
+    if (!rc)
+      rc = mpld::split_phase1_launch(
+          a, ctas, nw, mpld::split_warp_prefix(p->h_desc.data(), p->h_order.data(), C, n_large), st);
     if (!rc) rc = mpld::split_phase2_launch(a, d_desc, r.split, sb, d_queue, st);
     s->st.kernel_launches++;
   } else {
