@@ -189,6 +189,19 @@ def workload_layout(name: str, rank: int, scale: int = 1):
     return synth.unit_disk_layout(name=name, **cfg), mode
 
 
+def split_launches(mpld, prob, k, sizes=None):
+    """Kernel launches of one budgeted split search step over a problem: the
+    warps' first searches of the instances beyond the per-lane form and the
+    lane kernel's first searches of the others (each when there are some),
+    then the lanes' and the warps' subtree launches."""
+    import numpy as np
+    sizes = np.asarray(mpld.mpld_instance_sizes(prob) if sizes is None else sizes)
+    if len(sizes) == 0:
+        return 0
+    n_lane = int(np.sum(sizes <= 64)) if k <= 4 else 0
+    return (1 if n_lane < len(sizes) else 0) + (1 if n_lane > 0 else 0) + 2
+
+
 def run_serving(args, mpld, synth):
     """Poisson streams of whole layouts through the server (continuous batching).
 
@@ -483,7 +496,8 @@ def run_shards(args, rank, world, local_rank):
             "nodes_per_s": res.nodes * args.steps / total_s,
             "search": {"nodes": res.nodes, "cost": res.cost, "status": rc,
                        "instances_rank0": int(len(mine)), "instances": int(len(sizes))},
-            "gpu_launches": args.steps * (2 if args.split_budget else 1),
+            "gpu_launches": args.steps * (split_launches(mpld, prob, layout.k, sizes[mine])
+                                          if args.split_budget else 1),
             "clocks": clk,
             "e2e": {"value": layout.n_seg * len(e2e_t) / e2e_s, "unit": "segments/s",
                     "h2d_bytes_per_step": 4 * int(len(mine)),
@@ -649,12 +663,10 @@ def main():
                    "status": rc, "step_ms": step_ms,
                    "median_step_ms": statistics.median(step_ms) if step_ms else None,
                    "instances_exact": inst_status},
-        # launches per step: the split search's three (the first search of
-        # every instance, then the subtrees of the per-lane list and of the
-        # warps' list); the exact split search's queue launch before the
-        # batched one when the layout has several instances, one grid launch
-        # for a single instance
-        "gpu_launches": args.steps * (3 if args.split_budget else
+        # launches per step: the split search's (see split_launches); the
+        # exact split search's queue launch before the batched one when the
+        # layout has several instances, one grid launch for a single instance
+        "gpu_launches": args.steps * (split_launches(mpld, prob, layout.k) if args.split_budget else
                                       2 if (args.parallel_exact and info.n_components > 1) else 1),
         "sequential_budget": seq,
         "clocks": clk,
@@ -683,8 +695,9 @@ def main():
                                       f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json); "
                                       "derived, see int_pipes_measured",
                        "work_ops_per_launch": res.work,
-                       "covers": ("the three launches of a step (first searches; the per-lane "
-                                  "subtree searches; the warps' subtree searches), timed together"
+                       "covers": ("the launches of a step (the warps' and the lanes' first "
+                                  "searches, side by side; the lanes' subtree searches; the warps' "
+                                  "subtree searches, started beside the lanes'), timed together"
                                   if args.split_budget else "the one launch of a step")}
     # the integer pipes' measured throughput for the same op mix (context for
     # the derived peak above)
@@ -766,7 +779,8 @@ def main():
         out["e2e"] = {"value": all_segments * args.steps / t_stream, "unit": "segments/s",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                       "ms_per_step": 1000 * t_stream / args.steps,
-                      "gpu_launches_per_step": 2 if args.split_budget else 1,
+                      "gpu_launches_per_step": (split_launches(mpld, prob, layout.k)
+                                                if args.split_budget else 1),
                       "form": f"{args.steps} layouts submitted together to the server API "
                               "(mpld_server_submit / poll / result)",
                       "serial": serial}
