@@ -2067,133 +2067,150 @@ __device__ __noinline__ void lane_search(const InstDesc &d, const uint8_t *ro, i
     const int stot = popcw<W>(sa & all & ~unc);
     return Cc * popcw<W>(ca & asg[c]) + Cs * (stot - popcw<W>(sa & asg[c]));
   };
+  // Each pass: a lane that must backtrack pops levels until it covers the
+  // next row of one (or its search ends), then every lane that is entering
+  // a node expands it, so a warp's lanes meet in the node code whichever of
+  // them backtracked.  Each lane takes the same steps in the same order as
+  // a depth-first search of its own.
   bool enter = true;
   for (;;) {
-    if (enter) {
-      // ---- a node ----
-      // the budget stops a search once it has an incumbent
-      if (budget > 0 && thr < INF32 && nodes >= budget) { hit = true; break; }
-      ++nodes;
-      work += 2 * (n - level);
-      if (nodes >= next_check) {
-        next_check = nodes + 1024;
-        if ((int64_t)(globaltimer() - t0) > time_limit_ns) { tout = true; break; }
-      }
-      if (unc == 0) {
-        // leaf: every primary column covered
-        if (g < thr) {
-          // this leaf's masks: the leaf that sets the final bound is the
-          // first one in depth-first order at that cost, the one a search of
-          // this subtree bounded by that cost plus one would take first
-          thr = g;
-          found = true;
-          m0 = asg[1];
-          m1 = K > 2 ? asg[K > 2 ? 2 : 1] : (W)0;
-          if constexpr (K == 4) {
-            m0 |= asg[3];
-            m1 |= asg[3];
-          }
-          if (track > 0) {
-            sub = 0;
-            for (int i = 0; i < track; ++i) sub = sub * (uint32_t)K + ((st.h(i) >> 8) & 0xFu);
-          }
-          if (g == 0) break;
+    if (!enter) {
+      // ---- backtrack: next row of the level above, or undo its column ----
+      bool stop = false;
+      for (;;) {
+        if (level <= cut) {
+          stop = true;
+          break;
         }
-        if (level <= cut) break;
-        enter = false;
-        continue;
-      }
-      W cls[K + 1];
-      row_count_classes<K, W>(act, cls);
-      const W dead = unc & cls[0];
-      int v;
-      if constexpr (RULE == 0) {
-        W cand = dead;
-#pragma unroll
-        for (int m = 1; m <= K; ++m) cand = cand ? cand : (unc & cls[m]);
-        v = lowbit<W>(cand);
-      } else {
-        const W single = unc & cls[1];
-        v = single ? lowbit<W>(single) : (int)order[lowbit<W>(uncr)];
-      }
-      if (thr < INF32 && g + Cc * popcw<W>(dead) >= thr) {
-        if (level < cut) break;
-        enter = false;
-        continue;
-      }
-      const W ca = (W)cadj[v], sa = (W)sadj[v];
-      uint32_t keys[K];
-#pragma unroll
-      for (int c = 0; c < K; ++c) keys[c] = ((uint32_t)row_cost(ca, sa, c) << 3) | (uint32_t)c;
-      sort_keys<K>(keys);
-      work += K * (popcw<W>(ca) + popcw<W>(sa)) + 5 * (1 + popcw<W>(ca));
-      int place = 0;
-      if (level < cut) {
-        uint32_t pw = 1;
-        for (int i = level + 1; i < cut; ++i) pw *= (uint32_t)K;
-        place = (int)((prefix / pw) % (uint32_t)K);
-      }
-      uint32_t kp = keys[0];
-#pragma unroll
-      for (int i = 1; i < K; ++i) kp = i == place ? keys[i] : kp;
-      if (thr < INF32 && g + (int32_t)(kp >> 3) >= thr) {
-        // this row and the ones after it: their children are pruned on entry
-        if (count_pruned(level < cut ? 1 : K)) { hit = true; break; }
-        if (level < cut) break;
-        enter = false;
-        continue;
-      }
-      const int c = (int)(kp & 7u);
-      if (level >= cut) {
-        uint32_t ord = 0;
-#pragma unroll
-        for (int i = 0; i < K; ++i) ord |= (keys[i] & 3u) << (2 * i);
-        st.h(level) = (uint32_t)v | ((uint32_t)place << 8) | (ord << 12);
-        st.g(level) = (uint32_t)g;
+        --level;
+        const uint32_t h = st.h(level);
+        const int32_t gl = (int32_t)st.g(level);
+        const int v = (int)(h & 0xFFu), place = (int)((h >> 8) & 0xFu);
+        const uint32_t ord = h >> 12;
+        const W bit = one << v;
+        const int cl = (int)((ord >> (2 * place)) & 3u);
+        act[cl] = st.s(level);
+        asg[cl] &= ~bit;
+        unc |= bit;
+        if (RULE) uncr |= one << rank[v];
+        const int np = place + 1;
+        if (np >= K) continue;   // the column is exhausted: keep popping
+        const int c = (int)((ord >> (2 * np)) & 3u);
+        const W ca = (W)cadj[v], sa = (W)sadj[v];
+        const int32_t inc = row_cost(ca, sa, c);
+        if (thr < INF32 && gl + inc >= thr) {
+          // this row and the ones after it: children pruned on entry
+          if (count_pruned(K - np)) {
+            hit = true;
+            stop = true;
+            break;
+          }
+          continue;
+        }
+        work += 5 * (1 + popcw<W>(ca));
+        st.h(level) = (h & ~0xF00u) | ((uint32_t)np << 8);
         st.s(level) = act[c];
+        act[c] &= ~ca;
+        unc &= ~bit;
+        asg[c] |= bit;
+        if (RULE) uncr &= ~(one << rank[v]);
+        g = gl + inc;
+        ++level;
+        enter = true;
+        break;
       }
-      const W bit = one << v;
-      act[c] &= ~ca;
-      unc &= ~bit;
-      asg[c] |= bit;
-      if (RULE) uncr &= ~(one << rank[v]);
-      g += (int32_t)(kp >> 3);
-      ++level;
+      if (stop) break;
+    }
+    // ---- a node ----
+    // the budget stops a search once it has an incumbent
+    if (budget > 0 && thr < INF32 && nodes >= budget) { hit = true; break; }
+    ++nodes;
+    work += 2 * (n - level);
+    if (nodes >= next_check) {
+      next_check = nodes + 1024;
+      if ((int64_t)(globaltimer() - t0) > time_limit_ns) { tout = true; break; }
+    }
+    if (unc == 0) {
+      // leaf: every primary column covered
+      if (g < thr) {
+        // this leaf's masks: the leaf that sets the final bound is the
+        // first one in depth-first order at that cost, the one a search of
+        // this subtree bounded by that cost plus one would take first
+        thr = g;
+        found = true;
+        m0 = asg[1];
+        m1 = K > 2 ? asg[K > 2 ? 2 : 1] : (W)0;
+        if constexpr (K == 4) {
+          m0 |= asg[3];
+          m1 |= asg[3];
+        }
+        if (track > 0) {
+          sub = 0;
+          for (int i = 0; i < track; ++i) sub = sub * (uint32_t)K + ((st.h(i) >> 8) & 0xFu);
+        }
+        if (g == 0) break;
+      }
+      if (level <= cut) break;
+      enter = false;
       continue;
     }
-    // ---- backtrack: next row of the level above, or undo its column ----
-    if (level <= cut) break;
-    --level;
-    const uint32_t h = st.h(level);
-    const int32_t gl = (int32_t)st.g(level);
-    const int v = (int)(h & 0xFFu), place = (int)((h >> 8) & 0xFu);
-    const uint32_t ord = h >> 12;
-    const W bit = one << v;
-    const int cl = (int)((ord >> (2 * place)) & 3u);
-    act[cl] = st.s(level);
-    asg[cl] &= ~bit;
-    unc |= bit;
-    if (RULE) uncr |= one << rank[v];
-    const int np = place + 1;
-    if (np >= K) continue;
-    const int c = (int)((ord >> (2 * np)) & 3u);
+    W cls[K + 1];
+    row_count_classes<K, W>(act, cls);
+    const W dead = unc & cls[0];
+    int v;
+    if constexpr (RULE == 0) {
+      W cand = dead;
+#pragma unroll
+      for (int m = 1; m <= K; ++m) cand = cand ? cand : (unc & cls[m]);
+      v = lowbit<W>(cand);
+    } else {
+      const W single = unc & cls[1];
+      v = single ? lowbit<W>(single) : (int)order[lowbit<W>(uncr)];
+    }
+    if (thr < INF32 && g + Cc * popcw<W>(dead) >= thr) {
+      if (level < cut) break;
+      enter = false;
+      continue;
+    }
     const W ca = (W)cadj[v], sa = (W)sadj[v];
-    const int32_t inc = row_cost(ca, sa, c);
-    if (thr < INF32 && gl + inc >= thr) {
-      // this row and the ones after it: children pruned on entry
-      if (count_pruned(K - np)) { hit = true; break; }
+    uint32_t keys[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) keys[c] = ((uint32_t)row_cost(ca, sa, c) << 3) | (uint32_t)c;
+    sort_keys<K>(keys);
+    work += K * (popcw<W>(ca) + popcw<W>(sa)) + 5 * (1 + popcw<W>(ca));
+    int place = 0;
+    if (level < cut) {
+      uint32_t pw = 1;
+      for (int i = level + 1; i < cut; ++i) pw *= (uint32_t)K;
+      place = (int)((prefix / pw) % (uint32_t)K);
+    }
+    uint32_t kp = keys[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) kp = i == place ? keys[i] : kp;
+    if (thr < INF32 && g + (int32_t)(kp >> 3) >= thr) {
+      // this row and the ones after it: their children are pruned on entry
+      if (count_pruned(level < cut ? 1 : K)) { hit = true; break; }
+      if (level < cut) break;
+      enter = false;
       continue;
     }
-    work += 5 * (1 + popcw<W>(ca));
-    st.h(level) = (h & ~0xF00u) | ((uint32_t)np << 8);
-    st.s(level) = act[c];
+    const int c = (int)(kp & 7u);
+    if (level >= cut) {
+      uint32_t ord = 0;
+#pragma unroll
+      for (int i = 0; i < K; ++i) ord |= (keys[i] & 3u) << (2 * i);
+      st.h(level) = (uint32_t)v | ((uint32_t)place << 8) | (ord << 12);
+      st.g(level) = (uint32_t)g;
+      st.s(level) = act[c];
+    }
+    const W bit = one << v;
     act[c] &= ~ca;
     unc &= ~bit;
     asg[c] |= bit;
     if (RULE) uncr &= ~(one << rank[v]);
-    g = gl + inc;
+    g += (int32_t)(kp >> 3);
     ++level;
-    enter = true;
+    continue;
   }
   o.best = thr;
   o.found = found;
