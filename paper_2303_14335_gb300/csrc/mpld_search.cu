@@ -1839,6 +1839,351 @@ __device__ __noinline__ bool run_instance(const InstDesc &d, uint32_t slot_off, 
   return true;
 }
 
+// ---- a search that its node budget ends at the first leaf ----------------
+//
+// With no incumbent nothing is pruned, so a search's first descent takes the
+// first row of every column's order down to a leaf at node n + 1.  When the
+// node budget is at most n + 1 the budget stops the search right there (the
+// next row of the deepest level costs at least the leaf, so it is pruned and
+// its count finds the budget spent), unless the leaf costs 0, which ends the
+// search anyway.  The result is then that leaf, n + 1 nodes, status BUDGET
+// (OK at cost 0), and the work of the descent alone.  Such a search needs no
+// level record and no undo data: its state is the column classes (with
+// exact summaries, and no class sizes), the fields and the masks, with a copy
+// of the adjacency beside them as room allows, and a row's added cost comes
+// from the masks of v's neighbours (Eq. 1) summed by one warp reduction per
+// kind.  Giant instances under a
+// small budget (a served layout whose simplified graph keeps a component of
+// thousands of segments) take this form.
+
+// Shared-memory layout of the descent: the column classes, the fields, the
+// masks, then as room allows the adjacency offsets (16-bit, relative to the
+// first segment of each block of 64), the conflict and stitch neighbour
+// lists and the breadth-first ranks.
+struct DescentLayout {
+  uint32_t bk, rows, x, base;          // base: bytes of the part that must fit
+  uint32_t co16, so16, cob, sob, offs_end;
+  uint32_t cnbr, cnbr_end, snbr, snbr_end, rank, rank_end;
+};
+__device__ __forceinline__ DescentLayout descent_layout(int n, int k, int fb, int ne2, int ns2) {
+  DescentLayout L;
+  const int nfields = ((n + 3) / 4) * 4;
+  uint32_t o = 0;
+  L.bk = o; o += align16(bucket_bytes(n, k));
+  L.rows = o; o += align16((uint32_t)fb * (uint32_t)nfields);
+  L.x = o; o += align16((uint32_t)n);
+  L.base = o;
+  const uint32_t ow = align16(2u * (uint32_t)(n + 1)), bw = align16(4u * (uint32_t)((n >> 6) + 1));
+  L.co16 = o; L.so16 = o + ow; L.cob = o + 2u * ow; L.sob = o + 2u * ow + bw;
+  o += 2u * (ow + bw);
+  L.offs_end = o;
+  L.cnbr = o; o += align16(2u * (uint32_t)ne2);
+  L.cnbr_end = o;
+  L.snbr = o; o += align16(2u * (uint32_t)ns2);
+  L.snbr_end = o;
+  L.rank = o; o += align16(2u * (uint32_t)n);
+  L.rank_end = o;
+  return L;
+}
+
+// summary words per column class (two per lane of the column choice)
+__device__ __forceinline__ int bk_summary_words(int n) { return (((n + 31) / 32) + 31) / 32; }
+
+// 16-byte copy of `bytes` (a multiple of 16) from the read-only block in
+// global memory into shared memory, by every thread of the CTA
+__device__ __forceinline__ void cta_copy16(uint8_t *dst, const uint8_t *src, uint32_t bytes,
+                                           int rank, int nthreads) {
+  const uint4 *s = (const uint4 *)src;
+  uint4 *d = (uint4 *)dst;
+  for (uint32_t i = (uint32_t)rank; i < bytes / 16u; i += (uint32_t)nthreads) d[i] = __ldcg(s + i);
+}
+
+// The descent of instance d by warp 0 of the CTA (the other warps help set
+// the state up).  `budget` is the search's budget (0 < budget <= n + 1);
+// `split` / `sub`: the budgeted split search's first phase, whose leaf lies
+// in subtree 0 (every level takes its first row).  Returns false, having
+// done nothing, when the classes, fields and masks do not fit `room`.
+template <typename FT, int MK>
+__device__ __noinline__ bool run_descent(const InstDesc &d, const LaunchArgs &a,
+                                         const CtaTeam &team, uint8_t *mem, uint32_t room,
+                                         bool split) {
+  constexpr uint32_t FLAG = 1u << (8 * sizeof(FT) - 1);
+  const int n = d.n, k = d.k;
+  const DescentLayout L = descent_layout(n, k, (int)sizeof(FT), d.ne2, d.ns2);
+  if (L.base > room || n < 1 || bk_summary_words(n) > 64) return false;
+  const RoLayout R = ro_layout(n, d.ne2, d.ns2, d.nq * (k + 1));
+  const int2 *gptr = (const int2 *)(d.ro + R.ptr);
+  const int rk = team.rank, nt = team.size();
+  // the 16-bit offsets need every block of 64 segments to span fewer than
+  // 65,536 entries of each list
+  bool offs = L.offs_end <= room;
+  if (offs) {
+    bool wide = false;
+    for (int b = rk * 64; b < n; b += nt * 64) {
+      const int2 p0 = __ldcg(gptr + b), p1 = __ldcg(gptr + min(b + 64, n));
+      wide |= (p1.x - p0.x) >= 65536 || (p1.y - p0.y) >= 65536;
+    }
+    offs = !__syncthreads_or(wide);
+  }
+  const bool cl = offs && L.cnbr_end <= room;
+  const bool sl = cl && L.snbr_end <= room;
+  const bool rl = sl && a.rule && L.rank_end <= room;
+  Buckets bk;
+  bk.carve(mem + L.bk, n, k);
+  FT *rows = (FT *)(mem + L.rows);
+  int8_t *x = (int8_t *)(mem + L.x);
+  uint16_t *co16 = (uint16_t *)(mem + L.co16), *so16 = (uint16_t *)(mem + L.so16);
+  int32_t *cob = (int32_t *)(mem + L.cob), *sob = (int32_t *)(mem + L.sob);
+  const uint16_t *cnbr = cl ? (const uint16_t *)(mem + L.cnbr) : (const uint16_t *)(d.ro + R.cnbr);
+  const uint16_t *snbr = sl ? (const uint16_t *)(mem + L.snbr) : (const uint16_t *)(d.ro + R.snbr);
+  const uint16_t *rank = rl ? (const uint16_t *)(mem + L.rank) : (const uint16_t *)(d.ro + R.rank);
+  const uint16_t *order = (const uint16_t *)(d.ro + R.order);
+  // ---- state: every segment uncovered with k active rows, no mask ----
+  const uint32_t kmask = (1u << k) - 1u;
+  const int nfields = ((n + 3) / 4) * 4;
+  for (int i = rk; i < nfields; i += nt) rows[i] = i < n ? (FT)(kmask | FLAG) : (FT)0;
+  for (int i = rk; i < n; i += nt) x[i] = -1;
+  {
+    const int w32 = bk.w32, s32 = bk.s32;
+    for (int i = rk; i < k * w32; i += nt) bk.cls[i] = 0u;
+    for (int w = rk; w < w32; w += nt) {
+      const int lo = 32 * w;
+      const uint32_t bits = n - lo >= 32 ? 0xFFFFFFFFu : ((1u << (n - lo)) - 1u);
+      bk.cls[k * w32 + w] = bits;
+      bk.ur[w] = bits;
+    }
+    for (int j = rk; j < (k + 1) * s32; j += nt) {
+      const int m = j / s32, jj = j % s32, left = w32 - 32 * jj;
+      bk.sum[j] = m < k ? 0u : left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+    }
+    for (int jj = rk; jj < s32; jj += nt) {
+      const int left = w32 - 32 * jj;
+      bk.urs[jj] = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+    }
+  }
+  if (offs)
+    for (int i = rk; i <= n; i += nt) {
+      const int2 q = __ldcg(gptr + i), b = __ldcg(gptr + (i & ~63));
+      co16[i] = (uint16_t)(q.x - b.x);
+      so16[i] = (uint16_t)(q.y - b.y);
+      if ((i & 63) == 0) {
+        cob[i >> 6] = q.x;
+        sob[i >> 6] = q.y;
+      }
+    }
+  if (cl) cta_copy16(mem + L.cnbr, d.ro + R.cnbr, align16(2u * (uint32_t)d.ne2), rk, nt);
+  if (sl) cta_copy16(mem + L.snbr, d.ro + R.snbr, align16(2u * (uint32_t)d.ns2), rk, nt);
+  if (rl) cta_copy16(mem + L.rank, d.ro + R.rank, align16(2u * (uint32_t)n), rk, nt);
+  __syncthreads();
+  if ((rk >> 5) == 0) {
+    const int lane = rk;
+    const int Cc = d.cost_conflict, Cs = d.cost_stitch;
+    const int w32 = bk.w32, s32 = bk.s32;
+    // class membership moves.  Every summary here is exact (a bit per word of
+    // the class that holds a segment): a cover first takes segments out of
+    // their classes, clearing the summary bit of a word it empties, and only
+    // after a warp barrier puts them into their new ones, so no word refills
+    // while another lane judges it empty.
+    auto cls_remove = [&](int m, int u) {
+      const int w = u >> 5;
+      const uint32_t b = 1u << (u & 31);
+      const uint32_t old = atomicAnd(&bk.cls[m * w32 + w], ~b);
+      if ((old & ~b) == 0u) atomicAnd(&bk.sum[m * s32 + (w >> 5)], ~(1u << (w & 31)));
+    };
+    auto cls_add = [&](int m, int u) {
+      const int w = u >> 5;
+      atomicOr(&bk.cls[m * w32 + w], 1u << (u & 31));
+      atomicOr(&bk.sum[m * s32 + (w >> 5)], 1u << (w & 31));
+    };
+    int32_t g = 0, best = INF32;
+    int64_t nodes = 0, work = 0, next_check = 1024;
+    int status = MPLD_OK;
+    const uint64_t t0 = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
+    for (int level = 0;; ++level) {
+      // ---- a node ----
+      ++nodes;
+      work += 2 * (int64_t)(n - level);
+      if (nodes >= next_check) {
+        next_check = nodes + 1024;
+        const uint64_t now = __shfl_sync(FULL, lane == 0 ? globaltimer() : 0ull, 0);
+        if ((int64_t)(now - t0) > a.time_limit_ns) { status = MPLD_TIMEOUT; break; }
+      }
+      // column choice, as the column classes give it to the full search:
+      // the first class with a summary bit is the fewest-rows class, and
+      // its lowest summary bit leads to its lowest segment (summary words
+      // lane and lane + 32 of each class in this lane)
+      uint32_t slo[MK + 1], shi[MK + 1];
+      uint32_t have = 0u;
+#pragma unroll
+      for (int m = 0; m <= MK; ++m) {
+        slo[m] = 0u;
+        shi[m] = 0u;
+        if (m <= k) {
+          if (lane < s32) slo[m] = bk.sum[m * s32 + lane];
+          if (lane + 32 < s32) shi[m] = bk.sum[m * s32 + lane + 32];
+        }
+        have |= (slo[m] | shi[m]) != 0u ? 1u << m : 0u;
+      }
+      have = __reduce_or_sync(FULL, have);
+      if (have == 0u) {
+        // leaf: every primary column covered
+        best = g;
+        for (int i = lane; i < n; i += 32) d.mask[i] = x[i];
+        status = g == 0 ? MPLD_OK : MPLD_BUDGET;
+        break;
+      }
+      int v = -1;
+      const int m0 = a.rule == 0 ? __ffs(have) - 1 : ((have & 2u) ? 1 : -1);
+      if (m0 >= 0) {
+        uint32_t lo = slo[0], hi = shi[0];
+#pragma unroll
+        for (int m = 1; m <= MK; ++m)
+          if (m == m0) {
+            lo = slo[m];
+            hi = shi[m];
+          }
+        const uint32_t nzl = __ballot_sync(FULL, lo != 0u), nzh = __ballot_sync(FULL, hi != 0u);
+        const int l = nzl ? __ffs(nzl) - 1 : __ffs(nzh) - 1;
+        const uint32_t sw = __shfl_sync(FULL, nzl ? lo : hi, l & 31);
+        if (sw != 0u) {
+          const int w = (nzl ? l : 32 + l) * 32 + __ffs(sw) - 1;
+          v = w * 32 + __ffs(bk.cls[m0 * w32 + w]) - 1;
+        }
+      } else {
+        const int r = bk.lowest(bk.ur, bk.urs, lane);
+        if (r >= 0) v = (int)__ldcg(order + r);
+      }
+      // (never taken: every class and its summary agree after each cover)
+      if ((unsigned)v >= (unsigned)n) { status = MPLD_TIMEOUT; break; }
+      const uint32_t fv = (uint32_t)rows[v];
+      int cb, dc, sb, ds;
+      if (offs) {
+        const int v1 = v + 1;
+        cb = cob[v >> 6] + (int)co16[v];
+        dc = cob[v1 >> 6] + (int)co16[v1] - cb;
+        sb = sob[v >> 6] + (int)so16[v];
+        ds = sob[v1 >> 6] + (int)so16[v1] - sb;
+      } else {
+        const int2 p0 = __ldcg(gptr + v), p1 = __ldcg(gptr + v + 1);
+        cb = p0.x, dc = p1.x - p0.x, sb = p0.y, ds = p1.y - p0.y;
+      }
+      // masks held by v's neighbours: per mask, how many conflict / stitch
+      // neighbours hold it (one-hot 8-bit lanes, masks 0-3 and 4-7, summed
+      // over the warp)
+      int cc[MK], sc[MK];
+#pragma unroll
+      for (int c = 0; c < MK; ++c) cc[c] = sc[c] = 0;
+      auto onehot = [](int xu, uint32_t &lo, uint32_t &hi) {
+        if (xu >= 0) {
+          if (xu < 4) lo = 1u << (8 * xu);
+          else hi = 1u << (8 * (xu - 4));
+        }
+      };
+      auto tally = [&](int (&cnt)[MK], uint32_t lo, uint32_t hi) {
+        lo = __reduce_add_sync(FULL, lo);
+        if (MK > 4) hi = __reduce_add_sync(FULL, hi);
+#pragma unroll
+        for (int c = 0; c < MK; ++c) cnt[c] += (int)(((c < 4 ? lo : hi) >> (8 * (c & 3))) & 0xFFu);
+      };
+      int u0 = -1;   // this lane's conflict neighbour of the first pass and its field
+      uint32_t f0 = 0u;
+      if (dc + ds <= 32) {
+        // one pass: lanes [0, dc) take the conflict neighbours, lanes
+        // [dc, dc + ds) the stitch neighbours
+        uint32_t clo = 0u, chi = 0u, tlo = 0u, thi = 0u;
+        if (lane < dc) {
+          u0 = cl ? (int)cnbr[cb + lane] : (int)__ldcg(cnbr + cb + lane);
+          f0 = (uint32_t)rows[u0];
+          onehot(x[u0], clo, chi);
+        } else if (lane < dc + ds) {
+          const int u = sl ? (int)snbr[sb + lane - dc] : (int)__ldcg(snbr + sb + lane - dc);
+          onehot(x[u], tlo, thi);
+        }
+        tally(cc, clo, chi);
+        tally(sc, tlo, thi);
+      } else {
+        for (int i0 = 0; i0 < dc; i0 += 32) {
+          const int i = i0 + lane;
+          uint32_t lo = 0u, hi = 0u;
+          if (i < dc) {
+            const int u = cl ? (int)cnbr[cb + i] : (int)__ldcg(cnbr + cb + i);
+            if (i0 == 0) {
+              u0 = u;
+              f0 = (uint32_t)rows[u];
+            }
+            onehot(x[u], lo, hi);
+          }
+          tally(cc, lo, hi);
+        }
+        for (int i0 = 0; i0 < ds; i0 += 32) {
+          const int i = i0 + lane;
+          uint32_t lo = 0u, hi = 0u;
+          if (i < ds) onehot(x[sl ? (int)snbr[sb + i] : (int)__ldcg(snbr + sb + i)], lo, hi);
+          tally(sc, lo, hi);
+        }
+      }
+      int stot = 0;
+#pragma unroll
+      for (int c = 0; c < MK; ++c) stot += sc[c];
+      // the first row of v's order: the lowest added cost, lowest mask on ties
+      int cbest = 0;
+      int32_t ibest = INF32;
+#pragma unroll
+      for (int c = 0; c < MK; ++c) {
+        const int32_t inc = Cc * cc[c] + Cs * (stot - sc[c]);
+        if (c < k && inc < ibest) {
+          ibest = inc;
+          cbest = c;
+        }
+      }
+      work += (int64_t)(k * (dc + ds) + 5 * (1 + dc));
+      // ---- cover row (v, cbest), 32 conflict neighbours at a time ----
+      const uint32_t bit = 1u << cbest;
+      for (int i0 = 0; i0 == 0 || i0 < dc; i0 += 32) {
+        const int i = i0 + lane;
+        int u = -1;
+        uint32_t f = 0u;
+        if (i < dc) {
+          if (i0 == 0) {
+            u = u0;
+            f = f0;
+          } else {
+            u = cl ? (int)cnbr[cb + i] : (int)__ldcg(cnbr + cb + i);
+            f = (uint32_t)rows[u];
+          }
+        }
+        if (i0 == 0 && lane == 0) {
+          rows[v] = 0;
+          x[v] = (int8_t)cbest;
+          cls_remove(__popc(fv & kmask), v);
+          if (a.rule) bk.rank_set(rl ? (int)rank[v] : (int)__ldcg(rank + v), false);
+        }
+        int mv = 0;
+        if (u >= 0 && (f & FLAG) && (f & bit)) {
+          rows[u] = (FT)(f & ~bit);
+          mv = __popc(f & kmask);
+          cls_remove(mv, u);
+        }
+        __syncwarp();
+        if (mv > 0) cls_add(mv - 1, u);
+        __syncwarp();
+      }
+      g += ibest;
+    }
+    if (lane == 0) {
+      d.res->cost = best == INF32 ? INT64_MAX : (int64_t)best;
+      d.res->nodes = nodes;
+      d.res->status = status;
+      d.res->sub = 0;
+      d.res->work = work;
+      if (split && status == MPLD_BUDGET) split_enlist(a, d, best, 0u);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  return true;
+}
+
 // One large instance searched by the CTA; its state stays in its global
 // scratch region and its adjacency is read through L2.  When the CTA's
 // slots hold its column classes (`bk_mem`, `bk_room` bytes), warp 0 searches
@@ -1848,6 +2193,19 @@ template <typename FT, int MK>
 __device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArgs &a,
                                               const CtaTeam &team, uint8_t *bk_mem,
                                               uint32_t bk_room) {
+  {
+    // a search whose budget ends it at its first leaf: the descent alone
+    const bool split = a.split && d.n <= SPLIT_MAX_N;
+    int64_t b = a.budget;
+    if (split) {
+      int D;
+      uint32_t S;
+      split_cut(d.n, d.k, D, S);
+      b = split_search_budget(a.budget, S);
+    }
+    if (b > 0 && b <= (int64_t)d.n + 1 && run_descent<FT, MK>(d, a, team, bk_mem, bk_room, split))
+      return;
+  }
   if (bucket_bytes(d.n, d.k) <= bk_room) {
     if ((team.rank >> 5) == 0)
       run_in<FT, MK, false, WarpTeam, true>(d, d.scratch, d.ro, a, WarpTeam{team.rank}, bk_mem,

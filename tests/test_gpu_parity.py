@@ -394,6 +394,82 @@ def test_column_classes_backtracking_and_high_degree(stream):
                                 stream=stream.cuda_stream, cta=100), ref, H)
 
 
+# ------------------------- a budget that ends the search at its first leaf
+
+def descent_room(n, k, ne2, ns2):
+    """Shared-memory bytes the first-descent form needs for its state, then
+    with the adjacency offsets, the conflict lists and the stitch lists
+    beside it (the layout the kernel carves, restated)."""
+    a16 = lambda b: (b + 15) // 16 * 16
+    w = (n + 31) // 32
+    sw = (w + 31) // 32
+    classes = 4 * ((k + 1) * (w + sw + 1) + w + sw)
+    fb = 1 if k <= 7 else 2
+    base = a16(classes) + a16(fb * ((n + 3) // 4) * 4) + a16(n)
+    offs = base + 2 * (a16(2 * (n + 1)) + a16(4 * ((n >> 6) + 1)))
+    cn = offs + a16(2 * ne2)
+    return [base, offs, cn, cn + a16(2 * ns2)]
+
+
+def entries(L):
+    conf, st = edges(L)
+    return 2 * len({(min(a, b), max(a, b)) for a, b in conf}), \
+        2 * len({(min(a, b), max(a, b)) for a, b in st})
+
+
+@pytest.mark.parametrize("k,rule", [(3, 0), (3, 1), (4, 0), (2, 1), (5, 1), (8, 0)])
+def test_first_descent_of_a_giant_instance(k, rule, stream):
+    # node budgets of at most n + 1 end the search at its first leaf: the
+    # descent alone, by one warp, with the adjacency in shared memory as the
+    # room allows (every tier), and the full search's scan (16-byte slots)
+    L = synth.unit_disk_layout(4500 if k < 8 else 3000, k, seed=71 + k,
+                               mean_deg=4.5 if k < 8 else 3.0, p_stitch=0.2 if k < 8 else 0.0)
+    n = L.n_seg
+    ne2, ns2 = entries(L)
+    bounds = descent_room(n, k, ne2, ns2)
+    assert bounds[-1] < 200 * 1024
+    of = oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE | (oracle.COLUMN_BFS if rule else 0)
+    sf = BFS if rule else 0
+    for budget in (n + 1, 1000):
+        ref = oracle.decompose(L, flags=of, budget=budget)
+        assert ref.max_component == n and ref.nodes == n + 1
+        scan = gpu_run(L, flags=SINGLE, budget=budget, stream=stream.cuda_stream, slot=16,
+                       search_flags=sf, cta=2000)
+        assert_same(scan, ref, L)
+        rooms = [(lo + hi) // 2 for lo, hi in zip(bounds, bounds[1:])] + [bounds[-1] + 4096]
+        for room in rooms:
+            slot = (room // 8 + 15) // 16 * 16
+            g = gpu_run(L, flags=SINGLE, budget=budget, stream=stream.cuda_stream, warps=8,
+                        slot=slot, search_flags=sf, cta=2000)
+            assert_same(g, ref, L)
+            assert g["res"].work == scan["res"].work
+        if k == 8:
+            # few neighbours, eight masks, no stitches: the first leaf costs
+            # nothing, which ends the search before the budget does
+            assert ref.cost == 0 and ref.comp_status[0] == oracle.OK
+
+
+def test_first_descent_hub_and_split_first_phase(stream):
+    # a hub with 100 conflict neighbours (several passes of one warp over a
+    # neighbour list), and the budgeted split search's first phase on CTA
+    # teams, whose per-search share is below n + 1
+    L = synth.unit_disk_layout(4500, 3, seed=77, mean_deg=4.0, p_stitch=0.2)
+    conf, st = edges(L)
+    conf = set(conf) | ({(0, j) for j in range(1, 101)} - set(st))
+    for k in (3, 4):
+        H = synth.graph_from_edges(L.n_seg, k, sorted(conf), st, polygon_of=L.polygon_of)
+        ref = oracle.decompose(H, flags=oracle.NO_SIMPLIFY | oracle.SINGLE_INSTANCE, budget=2000)
+        assert ref.nodes == H.n_seg + 1
+        for path in ("batch", "plain"):
+            assert_same(gpu_run(H, flags=SINGLE, budget=2000, path=path, stream=stream.cuda_stream),
+                        ref, H)
+    M = synth.unit_disk_layout(30000, 3, seed=79, mean_deg=3.5, p_stitch=0.2)
+    ref = oracle.decompose(M, flags=oracle.SPLIT_BUDGET, budget=3000, nthreads=NTHREADS)
+    for cta in (40, 100):
+        assert_same(gpu_run(M, budget=3000, stream=stream.cuda_stream, cta=cta,
+                            search_flags=mpld.MPLD_SPLIT_BUDGET), ref, M)
+
+
 # ------------------------------ exact search with the warps of a CTA splitting an instance
 
 PAR = mpld.MPLD_PARALLEL_EXACT
