@@ -373,8 +373,9 @@ int mpld_finish_from(mpld_problem *p, const int64_t *nodes, const int64_t *cost,
  * to a stream of layouts:
  *   - mpld_server_submit copies the layout and queues it; host worker
  *     threads simplify, split and pack it (as mpld_build_matrix);
- *   - mpld_server_poll admits built layouts in submission order while their
- *     device bytes (packed matrices, search state, descriptors, results)
+ *   - mpld_server_poll admits built layouts in submission order (a layout
+ *     still being built holds back none behind it; one waiting for device
+ *     memory holds back the layouts after it) while their device bytes (packed matrices, search state, descriptors, results)
  *     fit the server's arena and fewer than max_in_flight layouts are on
  *     the device; each admitted layout is uploaded and searched by one
  *     persistent launch of the batched kernel on one of the server's

@@ -1197,6 +1197,11 @@ mpld::SplitPlan mpld::split_plan(const InstDesc *desc, int n_inst, const mpld_pa
   q.on = true;
   int reg_slot = 16;
   size_t gen = 0;
+  // slot bytes that hold the largest general-form state with the read-only
+  // block after it (the breadth-first tables only under column rule 1)
+  uint32_t gen_slot = 0;
+  const bool rule1 = (prm->flags & MPLD_COLUMN_BFS) != 0;
+  bool any_reg = false;
   for (int i = 0; i < n_inst; ++i) {
     const InstDesc &d = desc[i];
     if (d.n > SPLIT_MAX_N) continue;   // never split
@@ -1205,10 +1210,24 @@ mpld::SplitPlan mpld::split_plan(const InstDesc *desc, int n_inst, const mpld_pa
     split_cut(d.n, d.k, D, S);
     q.smax = std::max(q.smax, (int)S);
     const int list = split_list_of(d.n, d.k);
-    if (list == 0)
+    if (list == 0) {
       reg_slot = std::max(reg_slot, (int)align16(reg_layout(d.n, d.k, 0).bytes));
-    if (list == 2) gen = std::max(gen, (size_t)d.state_bytes);
+      any_reg = true;
+    }
+    if (list == 2) {
+      gen = std::max(gen, (size_t)d.state_bytes);
+      const RoLayout R = ro_layout(d.n, d.ne2, d.ns2, 0);
+      gen_slot = std::max(gen_slot, align16(state_layout(d.n, d.ne2, d.k, 0).bytes) +
+                                        (rule1 ? R.bytes : R.rank));
+    }
   }
+  // with no register-form subtrees to share the SMs with, the slots are
+  // sized for the general form's state and read-only block when they fit,
+  // and every warp takes general-form subtrees with no global region;
+  // otherwise the general form uses a warp's slot only when it fits there
+  const bool gen_in_slot =
+      !any_reg && gen_slot > 0 && (int)gen_slot <= mpld_internal_max_slot_bytes(1);
+  if (gen_in_slot) reg_slot = std::max(reg_slot, (int)gen_slot);
   // as many warps per CTA as the slots allow (the launch bound is 16)
   q.nw = 1;
   for (int nw = 16; nw >= 1; --nw)
@@ -1216,9 +1235,10 @@ mpld::SplitPlan mpld::split_plan(const InstDesc *desc, int n_inst, const mpld_pa
   q.slot = reg_slot;
   const int per_sm = std::max(1, mpld_internal_ctas_per_sm(q.nw, q.slot));
   q.ctas = per_sm * std::max(1, mpld_internal_num_sms());
-  q.state_bytes = gen ? (int)((gen + 255) & ~(size_t)255) : 0;
+  q.state_bytes = (gen && !gen_in_slot) ? (int)((gen + 255) & ~(size_t)255) : 0;
   const int G = q.ctas * q.nw;
-  q.gen_warps = q.state_bytes
+  q.gen_warps = gen_in_slot ? G
+      : q.state_bytes
       ? (int)std::max<size_t>(1, std::min<size_t>((size_t)G, gen_cap_bytes / (size_t)q.state_bytes))
       : 0;
   q.cap = n_inst;

@@ -34,7 +34,8 @@ struct SplitPlan {
   int nw = 0, slot = 0, ctas = 0;   // second launch
   int smax = 1;                     // item numbers per hard-list entry
   int state_bytes = 0;              // general-state region per warp (0: no such instance)
-  int gen_warps = 0;                // warps with such a region
+  int gen_warps = 0;                // warps with such a region (all warps when every
+                                    // general-form state fits the slot)
   int cap = 0;                      // entries of each hard list (the launch's descriptors)
   size_t o_hard = 0, o_ctx = 0, o_state = 0, bytes = 0;
   size_t o_lmask = 0;               // best-leaf masks of the lanes' items (16 bytes each)

@@ -2224,11 +2224,12 @@ __device__ __noinline__ void run_instance_cta(const InstDesc &d, const LaunchArg
 // returns true in the warp that completes the last subtree.  replay: the
 // subtree and bound of `key1` (cost* << 32 | s* + 1), masks to d.mask;
 // returns whether it took its leaf.
-template <typename FT, int MK>
-__device__ __noinline__ bool split_general(const InstDesc &d, uint8_t *state, const LaunchArgs &a,
-                                           int lane, ParCtx *ctx, uint32_t s, int cut, uint32_t S,
-                                           int64_t b, unsigned long long key1, bool replay) {
-  using Srch = Search<FT, MK, false, WarpTeam>;
+template <typename FT, int MK, bool SM>
+__device__ __noinline__ bool split_general(const InstDesc &d, uint8_t *state, const uint8_t *ro,
+                                           const LaunchArgs &a, int lane, ParCtx *ctx, uint32_t s,
+                                           int cut, uint32_t S, int64_t b, unsigned long long key1,
+                                           bool replay) {
+  using Srch = Search<FT, MK, SM, WarpTeam>;
   const int n = d.n;
   const StateLayout L = state_layout(n, d.ne2, d.k, 0);
   const RoLayout R = ro_layout(n, d.ne2, d.ns2, 0);
@@ -2242,11 +2243,11 @@ __device__ __noinline__ bool split_general(const InstDesc &d, uint8_t *state, co
   sr.oldf = (FT *)(state + L.oldf);
   sr.savf = (FT *)(state + L.savf);
   sr.x = (int8_t *)(state + L.x);
-  sr.ptr = (const int2 *)(d.ro + R.ptr);
-  sr.cnbr = (const uint16_t *)(d.ro + R.cnbr);
-  sr.snbr = (const uint16_t *)(d.ro + R.snbr);
-  sr.rank = (const uint16_t *)(d.ro + R.rank);
-  sr.order = (const uint16_t *)(d.ro + R.order);
+  sr.ptr = (const int2 *)(ro + R.ptr);
+  sr.cnbr = (const uint16_t *)(ro + R.cnbr);
+  sr.snbr = (const uint16_t *)(ro + R.snbr);
+  sr.rank = (const uint16_t *)(ro + R.rank);
+  sr.order = (const uint16_t *)(ro + R.order);
   sr.qptr = nullptr;
   sr.qlist = nullptr;
   sr.qcnt = state + L.qcnt;
@@ -2305,15 +2306,31 @@ __device__ __noinline__ bool split_general(const InstDesc &d, uint8_t *state, co
   return __shfl_sync(FULL, fin, 0) != 0u;
 }
 
+// state: the search state (the warp's slot or its global region); ro: the
+// instance's read-only block, copied into the slot after the state (ro_smem)
+// or in the arena
+template <bool SM>
+__device__ __forceinline__ bool split_general_k(const InstDesc &d, uint8_t *state,
+                                                const uint8_t *ro, const LaunchArgs &a, int lane,
+                                                ParCtx *ctx, uint32_t s, int cut, uint32_t S,
+                                                int64_t b, unsigned long long key1, bool replay) {
+  if (d.k == 3)
+    return split_general<uint8_t, 3, SM>(d, state, ro, a, lane, ctx, s, cut, S, b, key1, replay);
+  if (d.k == 4)
+    return split_general<uint8_t, 4, SM>(d, state, ro, a, lane, ctx, s, cut, S, b, key1, replay);
+  if (d.k == 2)
+    return split_general<uint8_t, 2, SM>(d, state, ro, a, lane, ctx, s, cut, S, b, key1, replay);
+  if (d.k <= 7)
+    return split_general<uint8_t, 8, SM>(d, state, ro, a, lane, ctx, s, cut, S, b, key1, replay);
+  return split_general<uint16_t, 8, SM>(d, state, ro, a, lane, ctx, s, cut, S, b, key1, replay);
+}
 __device__ __noinline__ bool split_general_dispatch(const InstDesc &d, uint8_t *state,
+                                                    const uint8_t *ro, bool ro_smem,
                                                     const LaunchArgs &a, int lane, ParCtx *ctx,
                                                     uint32_t s, int cut, uint32_t S, int64_t b,
                                                     unsigned long long key1, bool replay) {
-  if (d.k == 3) return split_general<uint8_t, 3>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
-  if (d.k == 4) return split_general<uint8_t, 4>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
-  if (d.k == 2) return split_general<uint8_t, 2>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
-  if (d.k <= 7) return split_general<uint8_t, 8>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
-  return split_general<uint16_t, 8>(d, state, a, lane, ctx, s, cut, S, b, key1, replay);
+  if (ro_smem) return split_general_k<true>(d, state, ro, a, lane, ctx, s, cut, S, b, key1, replay);
+  return split_general_k<false>(d, state, ro, a, lane, ctx, s, cut, S, b, key1, replay);
 }
 
 // ---- per-lane search (budgeted split search, second phase) ---------------
@@ -2652,9 +2669,10 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
   // warps with a general-state region first take the subtrees of instances
   // beyond the register form (counter queue[2]), then every warp those of
   // the register form (queue[0])
-  const bool gen_warp = gw < a.split_gen_warps && wstate != nullptr;
+  const bool gen_warp = gw < a.split_gen_warps;
   bool gen_phase = gen_warp && HG > 0;
-  int built = -1;   // instance whose adjacency the slot holds
+  int built = -1;   // instance whose adjacency the slot holds (register form)
+  int gro = -1;     // instance whose read-only block the slot holds (general form)
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(a.queue + (gen_phase ? 2 : 0), 1u);
@@ -2679,13 +2697,39 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
     const uint32_t s1 = (uint32_t)__ldcg(&d.res->sub);
     const unsigned long long key1 = ((unsigned long long)(uint32_t)c1 << 32) | s1;
     const bool reg = reg_fits(d.n, d.k) && a.slot_bytes >= (int)reg_layout(d.n, d.k, 0).bytes;
-    if (!reg && (!wstate || a.split_state_bytes < d.state_bytes)) {
-      // the host sizes the per-warp regions for every instance
-      if (lane == 0) atomicExch(a.err, MPLD_E_STATE);
-      return;
+    // the general form keeps its state in the warp's slot when it fits, and
+    // its read-only block after it when that fits too; else its state is in
+    // the warp's global region
+    uint8_t *gstate = wstate;
+    const uint8_t *gro_ptr = d.ro;
+    bool ro_smem = false;
+    if (!reg) {
+      const uint32_t sb = align16(state_layout(d.n, d.ne2, d.k, 0).bytes);
+      const RoLayout R = ro_layout(d.n, d.ne2, d.ns2, 0);
+      const uint32_t ro_copy = a.rule ? R.bytes : R.rank;
+      if ((uint32_t)a.slot_bytes >= sb) {
+        gstate = mine;
+        built = -1;
+        if ((uint32_t)a.slot_bytes >= sb + ro_copy) {
+          ro_smem = true;
+          gro_ptr = mine + sb;
+          if (gro != di) {
+            const uint4 *src = (const uint4 *)d.ro;
+            uint4 *dst = (uint4 *)(mine + sb);
+            for (uint32_t i = lane; i < ro_copy / 16u; i += 32u) dst[i] = __ldcg(src + i);
+            __syncwarp();
+            gro = di;
+          }
+        }
+      } else if (!wstate || a.split_state_bytes < d.state_bytes) {
+        // the host sizes the slots or the per-warp regions for every instance
+        if (lane == 0) atomicExch(a.err, MPLD_E_STATE);
+        return;
+      }
     }
     bool fin;
     if (reg) {
+      gro = -1;
       ParItem it;
       it.sub = s;
       it.budget = b;
@@ -2694,7 +2738,8 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
       fin = par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_BUDGET, key1, it);
       built = di;
     } else {
-      fin = split_general_dispatch(d, wstate, a, lane, ctx, s, D, S, b, key1, false);
+      fin = split_general_dispatch(d, gstate, gro_ptr, ro_smem, a, lane, ctx, s, D, S, b, key1,
+                                   false);
     }
     if (!fin) continue;
     // every subtree of the instance is done: its best key is final
@@ -2711,7 +2756,8 @@ __device__ __noinline__ void run_split_phase2(const LaunchArgs &a, int lane, int
         it.split_cut = true;
         ok = par_dispatch(d, mine, a, lane, gw, G, ctx, nullptr, nullptr, PAR_REPLAY, rk, it);
       } else {
-        ok = split_general_dispatch(d, wstate, a, lane, ctx, 0, D, S, 0, rk, true);
+        ok = split_general_dispatch(d, gstate, gro_ptr, ro_smem, a, lane, ctx, 0, D, S, 0, rk,
+                                    true);
       }
       if (!ok) key = key1;
     }

@@ -2,9 +2,10 @@
 // layouts on one GPU.
 //
 // Request life: submit (copy) -> a worker builds it host-side (simplify,
-// split, pack, as mpld_build_matrix) -> poll admits it in submission order
-// when its device bytes fit the arena and fewer than max_in_flight layouts
-// are on the device -> on one of the server's streams: upload, one
+// split, pack, as mpld_build_matrix) -> poll admits built layouts in
+// submission order (one still being built holds none back; one waiting for
+// device memory holds back those after it) when their device bytes fit the
+// arena and fewer than max_in_flight layouts are on the device -> on one of the server's streams: upload, one
 // persistent launch of the batched search kernel over its instances, copy of
 // the results into pinned memory, an event -> poll sees the event, returns
 // the device bytes (admitting waiting layouts) -> a worker recovers the
@@ -453,22 +454,27 @@ extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
     s->inflight[i] = s->inflight.back();
     s->inflight.pop_back();
   }
-  // admission in submission order
+  // admission of built layouts in submission order: one still being built
+  // does not hold back the built ones behind it, while one that waits for
+  // device memory does (so that a large layout is never passed over)
   for (;;) {
     ReqPtr r;
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      while (!s->admit_order.empty()) {
-        auto it = s->reqs.find(s->admit_order.front());
+      size_t pos = 0;
+      while (pos < s->admit_order.size()) {
+        auto it = s->reqs.find(s->admit_order[pos]);
         if (it == s->reqs.end() || it->second->state == State::Done) {
-          s->admit_order.pop_front();  // failed while building
+          s->admit_order.erase(s->admit_order.begin() + (ptrdiff_t)pos);  // failed while building
           continue;
         }
-        break;
+        if (it->second->state == State::Built) {
+          r = it->second;
+          break;
+        }
+        ++pos;   // still being built
       }
-      if (s->admit_order.empty()) break;
-      r = s->reqs[s->admit_order.front()];
-      if (r->state != State::Built) break;
+      if (!r) break;
       if ((int)s->inflight.size() >= s->cfg.max_in_flight) break;
       mpld_problem *p = r->p;
       r->split = mpld::split_plan(p->h_desc.data(), p->n_comp, &s->search, SPLIT_GEN_BYTES);
@@ -481,7 +487,7 @@ extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
         r->state = State::Done;
         s->done_tickets.push_back(r->ticket);
         s->st.failed++;
-        s->admit_order.pop_front();
+        s->admit_order.erase(s->admit_order.begin() + (ptrdiff_t)pos);
         continue;
       }
       if (!s->arena.alloc(r->sec.total, &r->arena_off)) break;
@@ -489,7 +495,7 @@ extern "C" int mpld_server_poll(mpld_server *s, int64_t *done, int32_t max_done,
         s->arena.release(r->arena_off, r->sec.total);
         break;
       }
-      s->admit_order.pop_front();
+      s->admit_order.erase(s->admit_order.begin() + (ptrdiff_t)pos);
       s->st.arena_used_bytes = (int64_t)s->arena.used();
       s->st.arena_peak_bytes = std::max(s->st.arena_peak_bytes, s->st.arena_used_bytes);
       s->st.admitted++;
