@@ -53,10 +53,11 @@ METRIC = "EC search nodes/s & segments/s (batched vs plain GPU vs CPU DLX); p99 
 # 68,352 + 0 bytes), per segment; traffic grows with the instances, i.e. with
 # the segments.  Valid only for the kernel source and search mode it was
 # measured on.
-TRAFFIC = {"k3_n200k_p02_batched": {"bytes_per_segment": (439296 + 256 + 597504 + 59648 + 68352) / 23960,
-                                    "kernel_sha256_16": "43b80edfd9659a06",
+TRAFFIC = {"k3_n200k_p02_batched": {"bytes_per_segment": (103680 + 0 + 5041920 + 1678080 + 1773568 +
+                                                          498944 + 113664 + 1536) / 59953,
+                                    "kernel_sha256_16": "a4d89a7b061515b5",
                                     "split_budget": True,
-                                    "profile": "profiles/split_step_traffic_k3_n20k_budget64k.md"}}
+                                    "profile": "profiles/split_step_traffic_k3_n50k_budget64k.md"}}
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 
 
@@ -689,7 +690,7 @@ def main():
             traffic = tr["bytes_per_segment"] * layout.n_seg
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak_gops,
                        "unit": "Gop/s", "frac": achieved / alu_peak_gops, "traffic": traffic,
-                       "traffic_source": ("ncu capture of the step's three launches at 1/10 scale, "
+                       "traffic_source": ("ncu capture of the step's four launches at 1/4 scale, "
                                           "scaled by segments" if traffic is not None else None),
                        "peak_source": f"{props.multi_processor_count} SMs x 64 int32 ops per clock x "
                                       f"{sm_mhz:.0f} MHz (max clock from MEASURED_PEAKS.json); "
