@@ -24,6 +24,7 @@
 #include <functional>
 #include <chrono>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -96,64 +97,6 @@ void punite(int32_t *par, int a, int b) {
     if (__atomic_compare_exchange_n(par + b, &expect, a, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED))
       return;
   }
-}
-
-// (min,max)-normalised, sorted, unique edges; returns false on a bad edge.
-// The larger endpoints are bucketed by the smaller one (a counting sort),
-// then each (short) bucket is sorted and deduplicated.
-bool normalise(int n, int m, const int32_t *u, const int32_t *v, std::vector<int32_t> &ou,
-               std::vector<int32_t> &ov) {
-  // input already in that form (u < v, strictly ascending pairs): copied as is
-  bool sorted = true;
-  for (int e = 0; e < m && sorted; ++e) {
-    const int a = u[e], b = v[e];
-    sorted = a >= 0 && a < b && b < n &&
-             (e == 0 || a > u[e - 1] || (a == u[e - 1] && b > v[e - 1]));
-  }
-  if (sorted) {
-    ou.assign(u, u + m);
-    ov.assign(v, v + m);
-    return true;
-  }
-  std::vector<int32_t> start((size_t)n + 1, 0);
-  for (int e = 0; e < m; ++e) {
-    const int a = u[e], b = v[e];
-    if (a < 0 || b < 0 || a >= n || b >= n || a == b) return false;
-    start[std::min(a, b) + 1]++;
-  }
-  for (int i = 0; i < n; ++i) start[i + 1] += start[i];
-  std::vector<int32_t> hi((size_t)m), fill(start.begin(), start.end() - 1);
-  for (int e = 0; e < m; ++e) hi[fill[std::min(u[e], v[e])]++] = std::max(u[e], v[e]);
-  ou.clear();
-  ov.clear();
-  ou.reserve((size_t)m);
-  ov.reserve((size_t)m);
-  for (int a = 0; a < n; ++a) {
-    const auto first = hi.begin() + start[a], last = hi.begin() + start[a + 1];
-    if (first == last) continue;
-    std::sort(first, last);
-    for (auto it = first; it != last; ++it)
-      if (it == first || *it != *(it - 1)) {
-        ou.push_back(a);
-        ov.push_back(*it);
-      }
-  }
-  return true;
-}
-
-// Adjacency with neighbours ascending (edges come sorted by (min,max)).
-void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
-         std::vector<int32_t> &ptr, std::vector<int32_t> &adj) {
-  ptr.assign((size_t)n + 1, 0);
-  for (size_t e = 0; e < u.size(); ++e) { ptr[u[e] + 1]++; ptr[v[e] + 1]++; }
-  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-  adj.resize(2 * u.size());
-  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
-  // smaller neighbours of x arrive (as u of edges (u,x)) in ascending u, then
-  // larger ones (as v of edges (x,v)) in ascending v -- but interleaved in
-  // edge order; two passes keep each list sorted.
-  for (size_t e = 0; e < u.size(); ++e) adj[fill[v[e]]++] = u[e];
-  for (size_t e = 0; e < u.size(); ++e) adj[fill[u[e]]++] = v[e];
 }
 
 // Biconnected blocks of one component (MPLD_BICONNECTED), appended in the
@@ -441,6 +384,80 @@ void parallel_strided(int count, int lanes, F f) {
   });
 }
 
+// ---- steps of the host build, each on the host pool with the same result
+// as one thread would give
+
+// (min,max)-normalised, sorted, unique edges; returns false on a bad edge.
+// Input already in that form (u < v, strictly ascending pairs) is checked
+// and copied in chunks.  Otherwise the larger endpoints are bucketed by the
+// smaller one (a counting sort), then each (short) bucket is sorted and
+// deduplicated.
+bool normalise(int n, int m, const int32_t *u, const int32_t *v, std::vector<int32_t> &ou,
+               std::vector<int32_t> &ov) {
+  constexpr int G = 1 << 15;
+  const int chunks = (m + G - 1) / G;
+  std::atomic<bool> sorted{true};
+  parallel_for(chunks, 1, [&](int q) {
+    for (int e = q * G, end = std::min(m, (q + 1) * G); e < end; ++e) {
+      const int a = u[e], b = v[e];
+      if (!(a >= 0 && a < b && b < n &&
+            (e == 0 || a > u[e - 1] || (a == u[e - 1] && b > v[e - 1])))) {
+        sorted.store(false, std::memory_order_relaxed);
+        return;
+      }
+    }
+  });
+  if (sorted.load()) {
+    ou.resize((size_t)m);
+    ov.resize((size_t)m);
+    parallel_for(chunks, 1, [&](int q) {
+      const size_t e0 = (size_t)q * G, e1 = std::min((size_t)m, e0 + G);
+      std::memcpy(ou.data() + e0, u + e0, (e1 - e0) * sizeof(int32_t));
+      std::memcpy(ov.data() + e0, v + e0, (e1 - e0) * sizeof(int32_t));
+    });
+    return true;
+  }
+  std::vector<int32_t> start((size_t)n + 1, 0);
+  for (int e = 0; e < m; ++e) {
+    const int a = u[e], b = v[e];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) return false;
+    start[std::min(a, b) + 1]++;
+  }
+  for (int i = 0; i < n; ++i) start[i + 1] += start[i];
+  std::vector<int32_t> hi((size_t)m), fill(start.begin(), start.end() - 1);
+  for (int e = 0; e < m; ++e) hi[fill[std::min(u[e], v[e])]++] = std::max(u[e], v[e]);
+  ou.clear();
+  ov.clear();
+  ou.reserve((size_t)m);
+  ov.reserve((size_t)m);
+  for (int a = 0; a < n; ++a) {
+    const auto first = hi.begin() + start[a], last = hi.begin() + start[a + 1];
+    if (first == last) continue;
+    std::sort(first, last);
+    for (auto it = first; it != last; ++it)
+      if (it == first || *it != *(it - 1)) {
+        ou.push_back(a);
+        ov.push_back(*it);
+      }
+  }
+  return true;
+}
+
+// Adjacency with neighbours ascending (edges come sorted by (min,max)).
+void csr(int n, const std::vector<int32_t> &u, const std::vector<int32_t> &v,
+         std::vector<int32_t> &ptr, std::vector<int32_t> &adj) {
+  ptr.assign((size_t)n + 1, 0);
+  for (size_t e = 0; e < u.size(); ++e) { ptr[u[e] + 1]++; ptr[v[e] + 1]++; }
+  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+  adj.resize(2 * u.size());
+  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+  // smaller neighbours of x arrive (as u of edges (u,x)) in ascending u, then
+  // larger ones (as v of edges (x,v)) in ascending v -- but interleaved in
+  // edge order; two passes keep each list sorted.
+  for (size_t e = 0; e < u.size(); ++e) adj[fill[v[e]]++] = u[e];
+  for (size_t e = 0; e < u.size(); ++e) adj[fill[u[e]]++] = v[e];
+}
+
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MPLD_OK : MPLD_E_CUDA; }
 
 std::mutex g_tune_mu;
@@ -498,17 +515,18 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
   p->Cs = g->cost_stitch;
   p->flags = params ? params->flags : 0u;
   try {
-    // conflict edges are normalised and put in CSR form on one thread while
-    // another does the same for the stitch edges and then builds the units
-    // (polygons merged along stitch edges, id = lowest segment), which need
-    // nothing else
+    // the conflict edges normalised (checked and copied in chunks when they
+    // come sorted); then their CSR form on one thread while another
+    // normalises the stitch edges, puts them in CSR form and builds the
+    // units (polygons merged along stitch edges, id = lowest segment), which
+    // need nothing else
     std::vector<int32_t> sptr, sadj;
     std::vector<int32_t> parent((size_t)n);
     bool ok[2] = {true, true};
-    parallel_for(2, 1, [&](int which) {
+    ok[0] = normalise(n, g->n_conf, g->conf_u, g->conf_v, p->cu, p->cv);
+    if (ok[0]) parallel_for(2, 1, [&](int which) {
       if (which == 0) {
-        ok[0] = normalise(n, g->n_conf, g->conf_u, g->conf_v, p->cu, p->cv);
-        if (ok[0]) csr(n, p->cu, p->cv, p->cptr, p->cadj);
+        csr(n, p->cu, p->cv, p->cptr, p->cadj);
         return;
       }
       ok[1] = normalise(n, g->n_stitch, g->st_u, g->st_v, p->su, p->sv);
@@ -623,35 +641,62 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     }
     p->comp_of.assign((size_t)n, -1);
     {
-      // ids: the roots (lowest alive segments) in ascending order
-      std::vector<int32_t> id_of((size_t)n, -1);
-      int single_id = -1;
-      for (int s = 0; s < n; ++s) {
-        if (!alive[s]) continue;
-        if (single) {
-          if (single_id < 0) single_id = p->n_comp++;
-        } else if (parent[s] == s) {
-          id_of[s] = p->n_comp++;
+      // ids: the roots (lowest alive segments) in ascending order, counted
+      // per chunk and numbered from each chunk's offset
+      constexpr int G = 1 << 15;
+      const int chunks = (n + G - 1) / G;
+      std::vector<int32_t> roots((size_t)chunks + 1, 0), live((size_t)chunks + 1, 0);
+      parallel_for(chunks, 1, [&](int q) {
+        int r = 0, a = 0;
+        for (int s = q * G, e = std::min(n, (q + 1) * G); s < e; ++s) {
+          if (!alive[s]) continue;
+          ++a;
+          r += parent[s] == s;
         }
-      }
-      parallel_for(n, 1 << 15, [&](int s) {
-        if (alive[s]) p->comp_of[s] = single ? single_id : id_of[parent[s]];
+        roots[q + 1] = r;
+        live[q + 1] = a;
       });
+      for (int q = 0; q < chunks; ++q) {
+        roots[q + 1] += roots[q];
+        live[q + 1] += live[q];
+      }
+      const int n_alive = live[chunks];
+      p->n_comp = single ? (n_alive > 0 ? 1 : 0) : roots[chunks];
+      // every segment is either in a removed unit or in an instance
+      p->n_removed_segments = n - n_alive;
+      std::vector<int32_t> id_of(single ? 0 : (size_t)n, -1);
+      if (!single)
+        parallel_for(chunks, 1, [&](int q) {
+          int id = roots[q];
+          for (int s = q * G, e = std::min(n, (q + 1) * G); s < e; ++s)
+            if (alive[s] && parent[s] == s) id_of[s] = id++;
+        });
+      parallel_for(n, 1 << 15, [&](int s) {
+        if (alive[s]) p->comp_of[s] = single ? 0 : id_of[parent[s]];
+      });
+      // each instance's segments ascending: in order per chunk for a single
+      // instance, else one pass in segment order (one counter per instance:
+      // a giant instance would have every thread increment the same one)
+      const int C0 = p->n_comp;
+      p->comp_ptr.assign((size_t)C0 + 1, 0);
+      p->comp_seg.resize((size_t)n_alive);
+      if (single) {
+        if (C0) p->comp_ptr[1] = n_alive;
+        parallel_for(chunks, 1, [&](int q) {
+          int t = live[q];
+          for (int s = q * G, e = std::min(n, (q + 1) * G); s < e; ++s)
+            if (alive[s]) p->comp_seg[t++] = s;
+        });
+      } else {
+        for (int s = 0; s < n; ++s)
+          if (alive[s]) p->comp_ptr[p->comp_of[s] + 1]++;
+        for (int c = 0; c < C0; ++c) p->comp_ptr[c + 1] += p->comp_ptr[c];
+        std::vector<int32_t> fill(p->comp_ptr.begin(), p->comp_ptr.end() - 1);
+        for (int s = 0; s < n; ++s)
+          if (alive[s]) p->comp_seg[fill[p->comp_of[s]]++] = s;
+      }
     }
-    // every segment is either in a removed unit or in an instance
-    p->n_removed_segments = n;
-    for (int s = 0; s < n; ++s) p->n_removed_segments -= alive[s];
     int C = p->n_comp;
-    p->comp_ptr.assign((size_t)C + 1, 0);
-    for (int s = 0; s < n; ++s)
-      if (p->comp_of[s] >= 0) p->comp_ptr[p->comp_of[s] + 1]++;
-    for (int c = 0; c < C; ++c) p->comp_ptr[c + 1] += p->comp_ptr[c];
-    p->comp_seg.resize((size_t)p->comp_ptr[C]);
-    {
-      std::vector<int32_t> fill(p->comp_ptr.begin(), p->comp_ptr.end() - 1);
-      for (int s = 0; s < n; ++s)
-        if (p->comp_of[s] >= 0) p->comp_seg[fill[p->comp_of[s]]++] = s;
-    }
     if (p->flags & MPLD_BICONNECTED) {
       // the search instances become the biconnected blocks of each component
       std::vector<int32_t> iptr{0}, iseg, iatt, loc((size_t)n, -1);
@@ -685,9 +730,10 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
     std::vector<int32_t> lid_of;
     if (!blocks) {
       lid_of.assign((size_t)n, -1);
-      for (int c = 0; c < C; ++c)
+      parallel_for(C, 1 << 10, [&](int c) {
         for (int t = p->comp_ptr[c]; t < p->comp_ptr[c + 1]; ++t)
           lid_of[p->comp_seg[t]] = t - p->comp_ptr[c];
+      });
     }
     auto local_of = [&](int c, int g) -> int {
       if (!blocks) return p->comp_of[g] == c ? lid_of[g] : -1;
