@@ -87,6 +87,17 @@ int pfind(int32_t *par, int x) {
     x = gx;
   }
 }
+// The root of x once every union is done, without writing on the way: run
+// by every thread at once to store each entry's root, it never stores
+// anything but a root, so no entry can lose its root to another thread's
+// path halving (which would store a grandparent over it).
+int proot(const int32_t *par, int x) {
+  for (;;) {
+    const int px = __atomic_load_n(par + x, __ATOMIC_RELAXED);
+    if (px == x) return x;
+    x = px;
+  }
+}
 void punite(int32_t *par, int a, int b) {
   for (;;) {
     a = pfind(par, a);
@@ -637,7 +648,7 @@ extern "C" int mpld_build_matrix(const mpld_graph *g, const mpld_params *params,
         }
       });
       // every entry its root
-      parallel_for(n, 1 << 15, [&](int x) { __atomic_store_n(par + x, pfind(par, x), __ATOMIC_RELAXED); });
+      parallel_for(n, 1 << 15, [&](int x) { __atomic_store_n(par + x, proot(par, x), __ATOMIC_RELAXED); });
     }
     p->comp_of.assign((size_t)n, -1);
     {

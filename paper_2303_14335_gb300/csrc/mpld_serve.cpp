@@ -570,10 +570,18 @@ extern "C" void mpld_server_destroy(mpld_server *s) {
   for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
   for (auto &r : s->inflight)
     if (r->done) cudaEventDestroy(r->done);
+  // a request still waiting to be finished is also in the map: each
+  // problem is freed once
   for (auto &kv : s->reqs)
-    if (kv.second->p) mpld_free(kv.second->p);
+    if (kv.second->p) {
+      mpld_free(kv.second->p);
+      kv.second->p = nullptr;
+    }
   for (auto &r : s->finish_q)
-    if (r->p) mpld_free(r->p);
+    if (r->p) {
+      mpld_free(r->p);
+      r->p = nullptr;
+    }
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   if (s->d_arena) cudaFree(s->d_arena);
   if (s->h_pool) cudaFreeHost(s->h_pool);
