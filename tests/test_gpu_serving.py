@@ -203,3 +203,27 @@ def test_density_balance_served(torch_cuda):
         rc, mask, res = got[t]
         ref = oracle.decompose(L, flags=oracle.DENSITY_BALANCE, budget=BUDGET, nthreads=NTHREADS)
         assert np.array_equal(mask, ref.mask) and res.cost == ref.cost and res.nodes == ref.nodes
+
+
+def test_destroy_with_requests_in_every_state(torch_cuda):
+    # a server destroyed while its layouts are queued, being built, on the
+    # device and waiting to be finished frees each of them once; a server
+    # created afterwards serves as before
+    Ls = requests(12, seed=91, n_max=60000)
+    for polls in (0, 3, 40):
+        srv = mpld.mpld_server_create(
+            mpld.mpld_server_config(max_in_flight=4, streams=2, worker_threads=2),
+            mpld.make_params(node_budget=BUDGET, flags=mpld.MPLD_SPLIT_BUDGET))
+        for L in Ls:
+            mpld.mpld_server_submit(srv, L)
+        for _ in range(polls):
+            mpld.mpld_server_poll(srv)
+            time.sleep(0.002)
+        srv.close()
+    with mpld.mpld_server_create(None, mpld.make_params(node_budget=BUDGET)) as srv:
+        tickets = [mpld.mpld_server_submit(srv, L) for L in Ls[:3]]
+        got = drain(srv, tickets)
+    for t, L in zip(tickets, Ls[:3]):
+        rc, mask, res = got[t]
+        ref = oracle.decompose(L, budget=BUDGET, nthreads=NTHREADS)
+        assert np.array_equal(mask, ref.mask) and res.cost == ref.cost
