@@ -397,7 +397,7 @@ typedef struct {
   int32_t max_in_flight;      /* layouts on the device at once; 0 = 64 */
   int32_t streams;            /* CUDA streams the launches rotate over; 0 = 8 */
   int32_t warps_per_cta;      /* batched kernel shape; 0 = 4 */
-  int32_t worker_threads;     /* host build / recovery threads; 0 = half the hardware threads */
+  int32_t worker_threads;     /* host build / recovery threads; 0 = three quarters of the hardware threads */
 } mpld_server_config;
 
 typedef struct {

@@ -348,8 +348,10 @@ extern "C" int mpld_server_create(const mpld_server_config *cfg_in, const mpld_p
   if (!cfg.max_in_flight) cfg.max_in_flight = 64;
   if (!cfg.streams) cfg.streams = 8;
   if (!cfg.warps_per_cta) cfg.warps_per_cta = 4;
+  // three quarters of the hardware threads: under load every worker builds
+  // one layout on its own thread, and the host pool's loops take the rest
   if (!cfg.worker_threads)
-    cfg.worker_threads = (int32_t)std::max(1u, std::thread::hardware_concurrency() / 2);
+    cfg.worker_threads = (int32_t)std::max(1u, 3u * std::thread::hardware_concurrency() / 4);
 
   mpld_server *s = new (std::nothrow) mpld_server();
   if (!s) return MPLD_E_OOM;
