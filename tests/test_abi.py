@@ -277,6 +277,32 @@ def test_builds_are_identical_alone_and_concurrent():
     assert all(o == ref for o in out)
 
 
+def test_instance_ids_are_valid_on_every_pooled_build():
+    # the components' union-find runs on the host pool; its last pass stores
+    # every segment's root.  Over repeated builds of a layout that keeps a
+    # 12,000-segment component: every kept segment has an instance id, the
+    # ids follow the instances' lowest segments, and the sizes agree
+    L = synth.serving_request(2023, 9)
+    ref = None
+    for _ in range(12):
+        p = host_only(L)
+        info = mpld.mpld_problem_info(p)
+        comp_of = mpld.mpld_component_results(p, results=False)[3]
+        sizes = mpld.mpld_instance_sizes(p)
+        p.close()
+        C = info.n_components
+        kept = comp_of >= 0
+        assert np.all(comp_of < C)
+        assert int(kept.sum()) == info.instance_segments == L.n_seg - info.n_removed_segments
+        assert np.array_equal(np.bincount(comp_of[kept], minlength=C), sizes)
+        first = np.full(C, L.n_seg)
+        np.minimum.at(first, comp_of[kept], np.flatnonzero(kept))
+        assert np.all(np.diff(first) > 0)
+        if ref is None:
+            ref = comp_of.copy()
+        assert np.array_equal(comp_of, ref)
+
+
 def test_density_balance_finish_on_the_host_matches_the_oracle():
     # host-only handle: the oracle's per-instance results go through the
     # library's own finish (scatter, balance, recovery, counts)
